@@ -1,0 +1,419 @@
+"""Solver-level pins of the CPU oracle: invariants, conservation, convergence
+orders, symmetry and an exact Riemann solution. CPU only."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2403_05910_b300 import cases
+from oracle.xfo import Oracle
+
+
+def _with_case(c, **kw):
+    o = Oracle(c, **kw)
+    U, T = o.prim_to_cons()
+    return o, U, T
+
+
+def _nv_slices(c):
+    dim = c.dim
+    return {"rho": [0], "mom": list(range(1, 1 + dim)), "E": [1 + dim],
+            "Y": list(range(2 + dim, c.n_v))}
+
+
+# ---------------------------------------------------------------- uniform --
+
+@pytest.mark.parametrize("dim", [1, 2, 3])
+@pytest.mark.parametrize("bc", [cases.BC_PERIODIC, cases.BC_TRANSMISSIVE])
+def test_uniform_state_has_zero_rhs(dim, bc):
+    n = {1: (16,), 2: (12, 10), 3: (8, 7, 6)}[dim]
+    c = cases.uniform_state(dim, n, 3, seed=dim, bc=bc, viscous=True)
+    o, U, T = _with_case(c)
+    R, T2, st = o.rhs(U, T)
+    assert st == 0
+    scale = np.max(np.abs(U), axis=1)[:, None] / min(c.dx[:dim])
+    assert np.max(np.abs(R) / scale) <= 1e-13
+
+
+# --------------------------------------------------------------- contacts --
+
+def _contact_case(n, sp, rho_jump, seed=0):
+    """Periodic 1D box, uniform p = 1 and u = 0.5, two interfaces."""
+    x = cases._centres(n, 0.0, 1.0)
+    inside = (x > 0.3) & (x < 0.7)
+    N = sp.n
+    rho = np.where(inside, 0.5 if rho_jump else 1.0, 1.0)
+    Y = np.zeros((N, n))
+    Y[0] = np.where(inside, 1.0, 0.0)
+    Y[1] = 1.0 - Y[0]
+    prim = cases._pack(1, rho, [np.full(n, 0.5)], np.ones(n), Y)
+    return cases.Case("contact", 1, (n, 1, 1), (0.0,) * 3, (1.0,) * 3,
+                      ((1, 1), (0, 0), (0, 0)), sp, cases.R_U * 300 / 0.028, 1.0, 1.0,
+                      False, 0.5, prim)
+
+
+def _pu_after(o, U, T, steps):
+    dt = o.dt(U, T)
+    for _ in range(steps):
+        o.step(U, T, dt)
+    P, T, st = o.cons_to_prim(U, T)
+    return P, st
+
+
+@pytest.mark.parametrize("cal_perfect,rho_jump", [(False, False), (True, True)])
+def test_passive_scalar_contact_keeps_p_and_u(cal_perfect, rho_jump):
+    """Two species with identical W and c_p: the jump in U lies along fixed
+    eigenvectors, so pressure and velocity stay uniform to round-off."""
+    rng = np.random.default_rng(7)
+    sp1 = cases._draw_species(rng, np.array([0.028]), cal_perfect)
+    sp = cases.Species(W=np.array([0.028, 0.028]), cp_coef=np.repeat(sp1.cp_coef, 2, 0),
+                       h_off=np.zeros(2), mu_coef=np.repeat(sp1.mu_coef, 2, 0),
+                       kappa_coef=np.repeat(sp1.kappa_coef, 2, 0))
+    c = _contact_case(100, sp, rho_jump)
+    o, U, T = _with_case(c)
+    P, st = _pu_after(o, U, T, 100)
+    assert st == 0
+    assert np.max(np.abs(P[2] - 1.0)) <= 1e-12
+    assert np.max(np.abs(P[1] - 0.5)) <= 1e-12
+
+
+def test_general_contact_pressure_error_is_small():
+    """Different molar masses (28 vs 4 g/mol): a fully conservative scheme is not
+    exactly pressure-equilibrium preserving; the error is reported and bounded."""
+    rng = np.random.default_rng(8)
+    sp = cases._draw_species(rng, np.array([0.028, 0.004]))
+    c = _contact_case(100, sp, rho_jump=False)
+    o, U, T = _with_case(c)
+    P, st = _pu_after(o, U, T, 100)
+    assert st == 0
+    dp = np.max(np.abs(P[2] - 1.0))
+    assert dp <= 5e-2, dp
+
+
+# ----------------------------------------------------------- conservation --
+
+@pytest.mark.parametrize("dim,n", [(1, (40,)), (2, (24, 20)), (3, (10, 9, 8))])
+def test_discrete_conservation_periodic_viscous(dim, n):
+    c = cases.smooth_periodic(dim, n, 3, seed=11 + dim, amp=0.2, viscous=True)
+    o, U, T = _with_case(c)
+    tot0 = U.sum(axis=1)
+    scale = np.abs(U).sum(axis=1)
+    dt = o.dt(U, T)
+    steps = 4
+    for _ in range(steps):
+        _, st = o.step(U, T, dt)
+        assert st == 0
+    drift = np.abs(U.sum(axis=1) - tot0) / scale
+    assert np.max(drift) <= 1e-13 * steps * 10, drift
+
+
+# --------------------------------------------------------- design order ---
+
+def test_design_order_density_wave():
+    """rho = 1 + 0.2 sin(2 pi x) advected at u = 1 with p = 1: the L1 error at
+    t = 0.1 shrinks at the design order (dt ~ dx^(5/3) keeps RK3 below WENO5)."""
+    errs = []
+    ns = (40, 80, 160)
+    for n in ns:
+        c = cases.density_wave(n)
+        o, U, T = _with_case(c)
+        t_end = 0.1
+        dt0 = 0.4 * (1.0 / n) ** (5.0 / 3.0)
+        steps = int(math.ceil(t_end / dt0))
+        dt = t_end / steps
+        for _ in range(steps):
+            o.step(U, T, dt)
+        x = cases._centres(n, 0.0, 1.0)
+        exact = 1.0 + 0.2 * np.sin(2 * np.pi * (x - t_end))
+        errs.append(np.mean(np.abs(U[0] - exact)))
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(len(ns) - 1)]
+    assert orders[-1] >= 4.5, (errs, orders)
+
+
+# -------------------------------------------------------- viscous order ---
+
+def _viscous_rhs(c):
+    o, U, T = _with_case(c, convective=False)
+    R, _, st = o.rhs(U, T)
+    assert st == 0
+    return o, U, T, R
+
+
+def _identical_species(N=2, cal_perfect=True, seed=9):
+    rng = np.random.default_rng(seed)
+    sp1 = cases._draw_species(rng, np.array([0.028]), cal_perfect)
+    return cases.Species(W=np.full(N, 0.028), cp_coef=np.repeat(sp1.cp_coef, N, 0),
+                         h_off=np.zeros(N), mu_coef=np.repeat(sp1.mu_coef, N, 0),
+                         kappa_coef=np.repeat(sp1.kappa_coef, N, 0))
+
+
+def test_viscous_order_constant_coefficients_1d():
+    """Constant mu, kappa, identical species, rho = 1: momentum and species
+    diffusion reduce to constant-coefficient second derivatives, which the face
+    scheme approximates at fourth order."""
+    sp = cases.constant_transport(_identical_species(), 2e-5, 3e-2)
+    errs_m, errs_y = [], []
+    for n in (16, 32, 64):
+        x = cases._centres(n, 0.0, 1.0)
+        u = 0.1 * np.sin(2 * np.pi * x)
+        Y0 = 0.5 + 0.2 * np.sin(2 * np.pi * x + 0.3)
+        Y = np.stack([Y0, 1 - Y0])
+        prim = cases._pack(1, np.ones(n), [u], np.ones(n), Y)
+        c = cases.Case("v", 1, (n, 1, 1), (0.0,) * 3, (1.0,) * 3, ((1, 1), (0, 0), (0, 0)),
+                       sp, cases.R_U * 300 / 0.028, 1.0, 1.0, True, 0.5, prim)
+        o, U, T, R = _viscous_rhs(c)
+        mu, ka, D = o.transport(T[0], 1.0, Y[:, 0])
+        # with p = rho = 1 and identical species T is uniform, so D and mu are too
+        ex_m = -(4.0 / 3.0) * mu * 0.1 * (2 * np.pi) ** 2 * np.sin(2 * np.pi * x)
+        ex_y = -D * 0.2 * (2 * np.pi) ** 2 * np.sin(2 * np.pi * x + 0.3)
+        errs_m.append(np.max(np.abs(R[1] - ex_m)) / np.max(np.abs(ex_m)))
+        errs_y.append(np.max(np.abs(R[3] - ex_y)) / np.max(np.abs(ex_y)))
+    om = math.log2(errs_m[-2] / errs_m[-1])
+    oy = math.log2(errs_y[-2] / errs_y[-1])
+    assert om >= 3.8 and oy >= 3.8, (errs_m, errs_y)
+
+
+def test_viscous_order_shear_2d():
+    """u = a sin(2 pi y), v = b sin(2 pi x), constant mu: the viscous momentum
+    terms are mu u_yy and mu v_xx (tau_xx = tau_yy = 0), fourth order."""
+    sp = cases.constant_transport(_identical_species(), 2e-5, 3e-2)
+    errs = []
+    for n in (16, 32, 64):
+        xs = cases._centres(n, 0.0, 1.0)
+        Yg, X = np.meshgrid(xs, xs, indexing="ij")
+        u = 0.1 * np.sin(2 * np.pi * Yg)
+        v = 0.07 * np.sin(2 * np.pi * X + 0.4)
+        Y = np.stack([np.full_like(X, 0.4), np.full_like(X, 0.6)])
+        prim = cases._pack(2, np.ones_like(X), [u, v], np.ones_like(X), Y)
+        c = cases.Case("s", 2, (n, n, 1), (0.0,) * 3, (1.0,) * 3, ((1, 1), (1, 1), (0, 0)),
+                       sp, cases.R_U * 300 / 0.028, 1.0, 1.0, True, 0.5, prim)
+        o, U, T, R = _viscous_rhs(c)
+        mu = o.transport(T[0], 1.0, np.array([0.4, 0.6]))[0]
+        ex_u = -mu * 0.1 * (2 * np.pi) ** 2 * np.sin(2 * np.pi * Yg)
+        ex_v = -mu * 0.07 * (2 * np.pi) ** 2 * np.sin(2 * np.pi * X + 0.4)
+        e = max(np.max(np.abs(R[1] - ex_u.ravel())), np.max(np.abs(R[2] - ex_v.ravel())))
+        errs.append(e / np.max(np.abs(ex_u)))
+    assert math.log2(errs[-2] / errs[-1]) >= 3.8, errs
+
+
+def _spectral_dx(f, L=1.0):
+    n = f.shape[-1]
+    k = np.fft.fftfreq(n, d=L / n) * 2 * np.pi
+    return np.real(np.fft.ifft(1j * k * np.fft.fft(f, axis=-1), axis=-1))
+
+
+def _spectral_eval(f, x0, x):
+    n = f.shape[-1]
+    k = np.fft.fftfreq(n, d=1.0 / n) * 2 * np.pi
+    fh = np.fft.fft(f, axis=-1) / n
+    ph = np.exp(1j * np.outer(x - x0, k))  # [len(x), n]
+    return np.real(fh @ ph.T)
+
+
+def test_viscous_full_1d_against_spectral_flux_divergence():
+    """General 1D viscous + diffusion RHS (T-dependent Eq. 29 transport, Wilke
+    mixing, distinct species, enthalpy diffusion) against the divergence of the
+    continuous viscous flux, differentiated spectrally on a fine grid. The
+    face-interpolated products make the scheme second order overall."""
+    rng = np.random.default_rng(12)
+    sp = cases._draw_species(rng, np.array([0.028, 0.004, 0.131]))
+    N = 3
+
+    def fields(x):
+        rho = 1.0 + 0.2 * np.sin(2 * np.pi * x)
+        u = 0.3 * np.sin(2 * np.pi * x + 1.0)
+        p = 1.0 + 0.15 * np.sin(2 * np.pi * x + 2.0)
+        w = np.stack([np.exp(0.5 * np.sin(2 * np.pi * x + s)) for s in range(N)])
+        return rho, u, p, w / w.sum(0)
+
+    def mk(n):
+        x = cases._centres(n, 0.0, 1.0)
+        rho, u, p, Y = fields(x)
+        prim = cases._pack(1, rho, [u], p, Y)
+        return cases.Case("vf", 1, (n, 1, 1), (0.0,) * 3, (1.0,) * 3,
+                          ((1, 1), (0, 0), (0, 0)), sp, cases.R_U * 300 / 0.028, 1.0, 1.0,
+                          True, 0.5, prim), x
+
+    # continuous viscous flux on a fine grid
+    nf = 1024
+    cf, xf = mk(nf)
+    of, Uf, Tf = _with_case(cf)
+    rho, u, p, Y = fields(xf)
+    ux, Tx = _spectral_dx(u), _spectral_dx(Tf)
+    Yx = _spectral_dx(Y)
+    Gf = np.zeros((cf.n_v, nf))
+    for i in range(nf):
+        mu, ka, D = of.transport(Tf[i], rho[i], Y[:, i])
+        hs = of.thermo(Tf[i], Y[:, i])[4]
+        corr = np.sum(D * Yx[:, i])
+        J = -rho[i] * (D * Yx[:, i] - Y[:, i] * corr)
+        tau = (4.0 / 3.0) * mu * ux[i]
+        Gf[1, i] = tau
+        Gf[2, i] = tau * u[i] + ka * Tx[i] - np.sum(hs * J)
+        Gf[3:, i] = -J[:N - 1]
+    Rf = _spectral_dx(Gf)
+    errs = []
+    for n in (32, 64, 128):
+        c, x = mk(n)
+        o, U, T, R = _viscous_rhs(c)
+        # fine-grid centres are not the coarse centres: evaluate the Fourier
+        # series of the fine-grid divergence at the coarse centres
+        ex = _spectral_eval(Rf, xf[0], x)
+        errs.append([np.max(np.abs(R[v] - ex[v])) / max(np.max(np.abs(ex[v])), 1e-300)
+                     for v in range(1, c.n_v)])
+    errs = np.array(errs)
+    orders = np.log2(errs[-2] / errs[-1])
+    assert np.all(orders >= 1.8), (errs, orders)
+    assert np.all(errs[-1] < 2e-2), errs
+
+
+# ------------------------------------------------------------- symmetry ---
+
+def test_axis_permutation_symmetry_3d():
+    c = cases.smooth_periodic(3, (8, 8, 8), 3, seed=21, amp=0.2, viscous=True)
+    o, U, T = _with_case(c)
+    R, _, _ = o.rhs(U, T)
+    # swap x and y: arrays are [v][z][y][x]; momentum rows 1 and 2 trade places
+    perm = [0, 2, 1, 3, 4, 5, 6]
+    Up = U.reshape(7, 8, 8, 8).transpose(0, 1, 3, 2)[perm].reshape(7, -1).copy()
+    Tp = T.reshape(8, 8, 8).transpose(0, 2, 1).reshape(-1).copy()
+    Rp, _, _ = o.rhs(Up, Tp)
+    Rback = Rp.reshape(7, 8, 8, 8)[perm].transpose(0, 1, 3, 2).reshape(7, -1)
+    scale = np.max(np.abs(R), axis=1, keepdims=True)
+    assert np.max(np.abs(Rback - R) / scale) <= 1e-13
+
+
+@pytest.mark.parametrize("viscous", [False, True])
+def test_multi_d_reduces_to_1d(viscous):
+    rng = np.random.default_rng(22)
+    sp = cases._draw_species(rng, np.array([0.028, 0.032, 0.131]))
+    n = 24
+    x = cases._centres(n, 0.0, 1.0)
+    rho = 1.0 + 0.3 * np.sin(2 * np.pi * x)
+    u = 0.2 * np.cos(2 * np.pi * x)
+    p = 1.0 + 0.2 * np.sin(2 * np.pi * x + 1)
+    w = np.stack([np.exp(np.sin(2 * np.pi * x + s)) for s in range(3)])
+    Y = w / w.sum(0)
+    c1 = cases.Case("r1", 1, (n, 1, 1), (0.0,) * 3, (1.0,) * 3, ((1, 1), (0, 0), (0, 0)),
+                    sp, cases.R_U * 300 / 0.028, 1.0, 1.0, viscous, 0.5,
+                    cases._pack(1, rho, [u], p, Y))
+    o1, U1, T1 = _with_case(c1)
+    R1, _, _ = o1.rhs(U1, T1)
+    ny = 5
+    tile = lambda a: np.tile(a, (ny, 1))
+    prim2 = cases._pack(2, tile(rho), [tile(u), np.zeros((ny, n))], tile(p),
+                        np.stack([tile(Y[s]) for s in range(3)]))
+    c2 = cases.Case("r2", 2, (n, ny, 1), (0.0,) * 3, (1.0,) * 3, ((1, 1), (1, 1), (0, 0)),
+                    sp, cases.R_U * 300 / 0.028, 1.0, 1.0, viscous, 0.5, prim2)
+    o2, U2, T2 = _with_case(c2)
+    R2, _, _ = o2.rhs(U2, T2)
+    R2 = R2.reshape(c2.n_v, ny, n)
+    rows = [0, 1, 3, 4, 5]  # rho, m_x, E, rhoY_1, rhoY_2 in the 2D layout
+    for j in range(ny):
+        assert np.max(np.abs(R2[rows, j, :] - R1)) <= 1e-13 * np.max(np.abs(R1))
+    assert np.max(np.abs(R2[2])) <= 1e-13 * np.max(np.abs(R1))
+
+
+# ------------------------------------------------------- exact Riemann ----
+
+def _exact_riemann(WL, WR, gL, gR, x, t, x0=0.5):
+    """Exact solution of the 1D Riemann problem for two calorically perfect
+    gases (pressure-function iteration of the standard textbook solver)."""
+    rL, uL, pL = WL
+    rR, uR, pR = WR
+    cL, cR = math.sqrt(gL * pL / rL), math.sqrt(gR * pR / rR)
+
+    def f(p, r, pk, g, ck):
+        if p > pk:
+            A, B = 2 / ((g + 1) * r), (g - 1) / (g + 1) * pk
+            return (p - pk) * math.sqrt(A / (p + B)), math.sqrt(A / (B + p)) * (1 - (p - pk) / (2 * (B + p)))
+        pr = p / pk
+        return 2 * ck / (g - 1) * (pr ** ((g - 1) / (2 * g)) - 1), 1 / (r * ck) * pr ** (-(g + 1) / (2 * g))
+
+    p = 0.5 * (pL + pR)
+    for _ in range(100):
+        fL, dL = f(p, rL, pL, gL, cL)
+        fR, dR = f(p, rR, pR, gR, cR)
+        dp = (fL + fR + uR - uL) / (dL + dR)
+        p = max(p - dp, 1e-12)
+        if abs(dp) < 1e-15 * p:
+            break
+    fL, _ = f(p, rL, pL, gL, cL)
+    fR, _ = f(p, rR, pR, gR, cR)
+    us = 0.5 * (uL + uR) + 0.5 * (fR - fL)
+    rho = np.zeros_like(x)
+    for i, xi in enumerate(x):
+        s = (xi - x0) / t
+        if s < us:  # left of the contact
+            g, r, pk, uk, ck = gL, rL, pL, uL, cL
+            if p > pk:
+                S = uk - ck * math.sqrt((g + 1) / (2 * g) * p / pk + (g - 1) / (2 * g))
+                rho[i] = r * ((p / pk + (g - 1) / (g + 1)) / ((g - 1) / (g + 1) * p / pk + 1)) if s > S else r
+            else:
+                cs = ck * (p / pk) ** ((g - 1) / (2 * g))
+                if s < uk - ck:
+                    rho[i] = r
+                elif s > us - cs:
+                    rho[i] = r * (p / pk) ** (1 / g)
+                else:
+                    rho[i] = r * (2 / (g + 1) + (g - 1) / ((g + 1) * ck) * (uk - s)) ** (2 / (g - 1))
+        else:
+            g, r, pk, uk, ck = gR, rR, pR, uR, cR
+            if p > pk:
+                S = uk + ck * math.sqrt((g + 1) / (2 * g) * p / pk + (g - 1) / (2 * g))
+                rho[i] = r * ((p / pk + (g - 1) / (g + 1)) / ((g - 1) / (g + 1) * p / pk + 1)) if s < S else r
+            else:
+                cs = ck * (p / pk) ** ((g - 1) / (2 * g))
+                if s > uk + ck:
+                    rho[i] = r
+                elif s < us + cs:
+                    rho[i] = r * (p / pk) ** (1 / g)
+                else:
+                    rho[i] = r * (2 / (g + 1) - (g - 1) / ((g + 1) * ck) * (uk - s)) ** (2 / (g - 1))
+    return rho
+
+
+@pytest.mark.slow
+def test_shock_tube_converges_to_exact_riemann_solution():
+    errs = []
+    for n in (400, 800, 1600):
+        c = cases.shock_tube(0, n=n, calorically_perfect=True)
+        o, U, T = _with_case(c)
+        nsteps, st = o.run_to(U, T, 0.2)
+        assert st == 0
+        a0 = c.species.cp_coef[:, 0]
+        g = a0 / (a0 - 1.0)
+        x = cases._centres(n, 0.0, 1.0)
+        ex = _exact_riemann((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), g[0], g[1], x, 0.2)
+        errs.append(np.sum(np.abs(U[0] - ex)) / np.sum(np.abs(ex)))
+    ratios = [errs[i] / errs[i + 1] for i in range(2)]
+    assert min(ratios) >= 1.5, (errs, ratios)
+    assert errs[-1] <= 0.02, errs
+
+
+# ------------------------------------------------------ initial states ----
+
+def test_rankine_hugoniot_post_shock_state():
+    """Eq. 33 post-shock state satisfies the mass, momentum and energy jump
+    conditions of a calorically perfect gas with the ambient gamma."""
+    for Ma in (1.22, 1.5, 2.83):
+        c = cases.shock_bubble(2, (64, 32), 3, Ma, 0.15, seed=1)
+        g = c.params["gamma_amb"]
+        r1, u1, p1 = c.params["post"]
+        r0, u0, p0 = 1.0, 0.0, 1.0
+        s = Ma * math.sqrt(g * p0 / r0)
+        assert r0 * s == pytest.approx(r1 * (s - u1), rel=1e-14)
+        assert p0 + r0 * s * s == pytest.approx(p1 + r1 * (s - u1) ** 2, rel=1e-14)
+        h = lambda p, r: g / (g - 1) * p / r
+        assert h(p0, r0) + 0.5 * s * s == pytest.approx(h(p1, r1) + 0.5 * (s - u1) ** 2, rel=1e-14)
+
+
+def test_shock_bubble_interface_profile():
+    c = cases.shock_bubble(2, (128, 64), 3, 1.22, 0.15, seed=0)
+    N = 3
+    Y3 = 1.0 - c.prim[4] - c.prim[5]  # rows: rho, u, v, p, Y_1, Y_2
+    assert Y3.min() >= -1e-15 and Y3.max() <= 1.0
+    # inside the bubble centre Y_3 ~ 1 - zeta-level; far away ~ 0
+    grid = Y3.reshape(64, 128)
+    assert grid[0, 32] > 0.99  # x = 0.504, y ~ 0: bubble centre
+    assert grid[-1, -1] < 1e-3
