@@ -1,0 +1,165 @@
+/* xf.h -- C-ABI of the B300 (sm_103a) multicomponent RHS / SSP-RK3 library.
+ *
+ * The library advances the multicomponent compressible Navier-Stokes system of
+ * arXiv 2403.05910 (XFluids), Sec. II.A Eq. 1-7, on a uniform structured grid,
+ * in FP64, on one GPU. One right-hand-side evaluation L(U) (Eq. 13) consists of
+ *   - primitive recovery with the Newton temperature solve of Eq. 21;
+ *   - per direction, characteristic-space WENO5 reconstruction (Eq. 14-15) with
+ *     local Lax-Friedrichs splitting, the multicomponent eigensystem at a
+ *     Roe-averaged face state, and the partial eigensystem reconstruction (PER,
+ *     Sec. III.D.3: one eigenvalue, one left row and one right column per field);
+ *   - 4th-order central viscous and species-diffusion fluxes (Eq. 3-6, Eq. 22,
+ *     Eq. 29 transport fits, constant Lewis number);
+ *   - the conservative flux difference (Eq. 13) and the SSP-RK3 stages (Eq. 16).
+ *
+ * Conventions (all entry points):
+ *   - FP64 throughout. Field arrays are structure-of-arrays [n_v][nz][ny][nx]
+ *     (i fastest), interior cells only, n_v = dim + 2 + (N - 1) rows:
+ *     conserved  U = (rho, rho u_1..rho u_dim, E, rho Y_1..rho Y_{N-1});
+ *     primitive  P = (rho, u_1..u_dim, p, Y_1..Y_{N-1});  Y_N = 1 - sum.
+ *     All quantities are dimensionless (rho/rho_ref, u/a_ref, p/(rho_ref a_ref^2),
+ *     x/L_ref); temperatures are in kelvin.
+ *   - Ownership: the caller owns every pointer it passes and may free it when
+ *     the call returns (copies are enqueued on `stream`; keep host memory alive
+ *     and unmodified until the stream reaches that point). The handle owns its
+ *     internal device buffers (state, stage state, temperatures, per-cell
+ *     primitives, face fluxes, time step, status word).
+ *   - Pointers marked "host or device" may point to either (copies use
+ *     unified addressing); all others must be device pointers.
+ *   - Asynchrony: every call enqueues work on `stream` (a cudaStream_t, NULL =
+ *     the legacy default stream) and returns without synchronising, except
+ *     xf_get_status.
+ *   - Errors: argument errors return XF_ERR_ARG immediately and enqueue
+ *     nothing; CUDA launch/copy failures return XF_ERR_CUDA (xf_last_error
+ *     gives the message). Physical faults detected on the device (NaN, rho <= 0,
+ *     p <= 0, T <= 0, a non-converged Newton solve, a non-positive face sound
+ *     speed) are OR-ed into a device status word and reported by xf_get_status;
+ *     device code never traps.
+ */
+#ifndef XF_H
+#define XF_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define XF_MAX_SPECIES 5
+
+typedef enum {
+  XF_OK = 0,
+  XF_ERR_ARG = 1,     /* invalid argument; nothing was enqueued */
+  XF_ERR_CUDA = 2,    /* a CUDA call failed (see xf_last_error) */
+  XF_ERR_NONPHYS = 3, /* device saw NaN/inf, rho <= 0, p <= 0 or T <= 0 */
+  XF_ERR_NEWTON = 4,  /* the temperature Newton solve did not converge */
+  XF_ERR_EIGEN = 5,   /* a face sound speed squared was <= 0 */
+  XF_ERR_TIMEOUT = 6, /* a bounded device wait gave up */
+  XF_ERR_OOM = 7      /* device allocation failed */
+} xf_status;
+
+/* bits of the device status word (xf_get_status) */
+#define XF_FLAG_NONPHYS 1u
+#define XF_FLAG_NEWTON 2u
+#define XF_FLAG_EIGEN 4u
+#define XF_FLAG_TIMEOUT 8u
+
+/* boundary conditions, per axis and side (applied to 3 ghost layers) */
+#define XF_BC_TRANSMISSIVE 0 /* zero-gradient copy of the boundary cell */
+#define XF_BC_PERIODIC 1     /* both sides of an axis must be periodic */
+#define XF_BC_SYMMETRIC 2    /* mirror; the normal momentum changes sign */
+
+/* Uniform cell-centred grid. dim in {1,2,3}; n[a] >= 3 for active axes
+ * (n[a] is ignored for a >= dim); [lo, hi] is the dimensionless extent. */
+typedef struct xf_grid {
+  int dim;
+  int64_t n[3];
+  double lo[3], hi[3];
+  int bc[3][2];
+} xf_grid;
+
+/* Species tables (copied at xf_create; host pointers), N = 2..XF_MAX_SPECIES.
+ *  W[N]             molar masses, kg/mol (Eq. 7)
+ *  T_lo, T_hi       range of the c_p polynomials, K
+ *  cp_coef[N][5]    c_p,s/R_s = sum_j cp_coef[s][j] tau^j, tau = (T-T_lo)/(T_hi-T_lo),
+ *                   held at its end value outside [T_lo, T_hi]
+ *  h_off[N]         h_s/R_s at T_lo, K (enthalpy continues linearly outside)
+ *  mu_coef[N][4]    ln mu_s [Pa s]   = sum_n mu_coef[s][n] (ln T)^n   (Eq. 29)
+ *  kappa_coef[N][4] ln kappa_s [W/(m K)] likewise
+ *  lewis            constant Lewis number: D_s = kappa/(rho c_p Le) for all s
+ *  a_ref2, rho_ref, L_ref  reference scales (m^2/s^2, kg/m^3, m) */
+typedef struct xf_thermo {
+  int n_species;
+  const double *W;
+  double T_lo, T_hi;
+  const double *cp_coef;
+  const double *h_off;
+  const double *mu_coef;
+  const double *kappa_coef;
+  double lewis;
+  double a_ref2, rho_ref, L_ref;
+} xf_thermo;
+
+/* Numerical options. weno must be 5 and split 0 (LLF); viscous switches the
+ * viscous + diffusion fluxes; convective switches the inviscid fluxes (off only
+ * for testing the viscous operator); newton_max/newton_rtol bound the Newton
+ * solve (stop when |dT| <= rtol T); weno_eps is the WENO5-JS epsilon. */
+typedef struct xf_opts {
+  double cfl;
+  int weno;
+  int split;
+  int viscous;
+  int convective;
+  int newton_max;
+  double newton_rtol;
+  double weno_eps;
+} xf_opts;
+
+typedef struct xf_handle xf_handle;
+
+/* Allocate a solver for one grid (Eq. 1-2 on that grid). Returns XF_ERR_ARG on
+ * a bad grid/table/option, XF_ERR_OOM if device memory runs out. */
+xf_status xf_create(const xf_grid *grid, const xf_thermo *thermo,
+                    const xf_opts *opts, xf_handle **out);
+void xf_destroy(xf_handle *h);
+
+int xf_nv(const xf_handle *h);        /* n_v */
+int64_t xf_cells(const xf_handle *h); /* interior cells */
+
+/* Load the state from conserved U [n_v][cells] (host or device); T_guess
+ * [cells] (host or device, nullable: 300 K) seeds the Newton warm start. */
+xf_status xf_set_state(xf_handle *h, const double *U, const double *T_guess,
+                       void *stream);
+/* Load the state from primitives P [n_v][cells] (host or device) with the
+ * ideal-gas EOS (Eq. 7): T = p/(rho R), E = rho (e(T, Y) + |u|^2/2). */
+xf_status xf_set_primitive(xf_handle *h, const double *P, void *stream);
+/* Copy the state out: U [n_v][cells] and/or T [cells] (host or device,
+ * nullable). */
+xf_status xf_get_state(xf_handle *h, double *U, double *T, void *stream);
+
+/* dUdt = L(U) (Eq. 13) for device arrays U, dUdt [n_v][cells]. The handle's
+ * state is untouched; its temperature warm start is refreshed from U. */
+xf_status xf_rhs(xf_handle *h, const double *U, double *dUdt, void *stream);
+
+/* Time step of the current state (reading of the CFL condition of Eq. 17):
+ * dt = CFL / max_cells sum_d (|u_d| + c)/dx_d and, when viscous, also
+ * <= CFL dx_min^2 / (2 dim max(4 mu/(3 rho), kappa/(rho c_v), D)).
+ * Written to dt_dev (device). */
+xf_status xf_compute_dt(xf_handle *h, double *dt_dev, void *stream);
+
+/* One SSP-RK3 step (Eq. 16) of the handle's state. dt > 0: that step; dt <= 0:
+ * the CFL step of U^n computed on the device. dt_dev_out (device, nullable)
+ * receives the step used. No host synchronisation. */
+xf_status xf_step_rk3(xf_handle *h, double dt, double *dt_dev_out, void *stream);
+
+/* Synchronise `stream` and return the OR of device status bits since the last
+ * xf_clear_status; the return value maps the lowest set bit to an xf_status. */
+xf_status xf_get_status(xf_handle *h, uint32_t *flags, void *stream);
+xf_status xf_clear_status(xf_handle *h, void *stream);
+
+const char *xf_status_str(xf_status s);
+const char *xf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

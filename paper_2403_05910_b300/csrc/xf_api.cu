@@ -1,0 +1,423 @@
+// xf_api.cu -- C-ABI entry points (include/xf.h) and kernel dispatch.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "xf.h"
+#include "xf_device.cuh"
+
+namespace {
+
+thread_local std::string g_err;
+
+void set_err(const char* what, cudaError_t e) {
+  char buf[256];
+  snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
+  g_err = buf;
+}
+
+#define XF_CUDA(call)        \
+  do {                       \
+    cudaError_t e_ = (call); \
+    if (e_ != cudaSuccess) { \
+      set_err(#call, e_);    \
+      return XF_ERR_CUDA;    \
+    }                        \
+  } while (0)
+
+inline unsigned blocks(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+using PrimFn = void (*)(const xf::Params&, const double*, const double*, double*, double*,
+                        uint32_t*, unsigned long long*, int, cudaStream_t);
+using GradFn = void (*)(const xf::Params&, double*, cudaStream_t);
+using FaceFn = void (*)(const xf::Params&, const double*, double*, uint32_t*, cudaStream_t);
+using UpdFn = void (*)(const xf::Params&, const double*, const double*, const double*,
+                       const double*, const double*, double*, const double*, int, cudaStream_t);
+using FromPrimFn = void (*)(const xf::Params&, const double*, double*, double*, cudaStream_t);
+
+struct Table {
+  PrimFn prim;
+  GradFn grad;
+  FaceFn face[3];
+  UpdFn update;
+  FromPrimFn from_prim;
+  int nq;
+};
+
+template <int DIM, int NS>
+struct Launch {
+  static void prim(const xf::Params& p, const double* U, const double* Tin, double* Tout,
+                   double* Q, uint32_t* fl, unsigned long long* red, int cfl, cudaStream_t s) {
+    xf::k_prim<DIM, NS><<<blocks(p.pcells, 256), 256, 0, s>>>(p, U, Tin, Tout, Q, fl, red, cfl);
+  }
+  static void grad(const xf::Params& p, double* Q, cudaStream_t s) {
+    xf::k_grad<DIM, NS><<<blocks(p.pcells, 256), 256, 0, s>>>(p, Q);
+  }
+  template <int D>
+  static void face(const xf::Params& p, const double* Q, double* G, uint32_t* fl, cudaStream_t s) {
+    if constexpr (D < DIM) {
+      const long long nf =
+          (long long)(p.n[0] + (D == 0)) * (p.n[1] + (D == 1)) * (p.n[2] + (D == 2));
+      xf::k_face<DIM, NS, D><<<blocks(nf, 128), 128, 0, s>>>(p, Q, G, fl);
+    }
+  }
+  static void update(const xf::Params& p, const double* Gx, const double* Gy, const double* Gz,
+                     const double* Un, const double* Us, double* out, const double* dt, int mode,
+                     cudaStream_t s) {
+    xf::k_update<DIM, NS><<<blocks(p.cells, 256), 256, 0, s>>>(p, Gx, Gy, Gz, Un, Us, out, dt,
+                                                              mode);
+  }
+  static void from_prim(const xf::Params& p, const double* P, double* U, double* T,
+                        cudaStream_t s) {
+    xf::k_from_prim<DIM, NS><<<blocks(p.cells, 256), 256, 0, s>>>(p, P, U, T);
+  }
+  static Table table() {
+    return Table{prim, grad, {face<0>, face<1>, face<2>}, update, from_prim, xf::Lay<DIM, NS>::NQ};
+  }
+};
+
+template <int DIM>
+bool pick_n(int N, Table* t) {
+  switch (N) {
+    case 2: *t = Launch<DIM, 2>::table(); return true;
+    case 3: *t = Launch<DIM, 3>::table(); return true;
+    case 4: *t = Launch<DIM, 4>::table(); return true;
+    case 5: *t = Launch<DIM, 5>::table(); return true;
+    default: return false;
+  }
+}
+
+bool pick(int dim, int N, Table* t) {
+  switch (dim) {
+    case 1: return pick_n<1>(N, t);
+    case 2: return pick_n<2>(N, t);
+    case 3: return pick_n<3>(N, t);
+    default: return false;
+  }
+}
+
+__global__ void k_fill(double* p, long long n, double v) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
+bool is_device_ptr(const void* ptr) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+struct xf_handle {
+  xf::Params p;
+  Table tab;
+  int tcur = 0;  // which temperature buffer holds the latest warm start
+  long long nf[3] = {0, 0, 0};
+  double* U = nullptr;   // U^n
+  double* Us = nullptr;  // stage state (also staging for host primitives)
+  double* T[2] = {nullptr, nullptr};
+  double* Q = nullptr;   // padded per-cell fields
+  double* G[3] = {nullptr, nullptr, nullptr};  // per-direction face fluxes
+  double* dt = nullptr;
+  unsigned long long* red = nullptr;
+  uint32_t* flags = nullptr;
+};
+
+namespace {
+
+xf_status fill_params(const xf_grid* g, const xf_thermo* th, const xf_opts* o, xf::Params* p) {
+  if (!g || !th || !o) return XF_ERR_ARG;
+  if (g->dim < 1 || g->dim > 3) return XF_ERR_ARG;
+  if (th->n_species < 2 || th->n_species > XF_MAX_SPECIES) return XF_ERR_ARG;
+  if (o->weno != 5 || o->split != 0) return XF_ERR_ARG;
+  if (!(o->cfl > 0.0) || o->newton_max < 1 || !(o->newton_rtol > 0.0) || !(o->weno_eps > 0.0))
+    return XF_ERR_ARG;
+  if (!th->W || !th->cp_coef || !th->h_off) return XF_ERR_ARG;
+  if (o->viscous && (!th->mu_coef || !th->kappa_coef || !(th->lewis > 0.0))) return XF_ERR_ARG;
+  if (!(th->T_hi > th->T_lo) || !(th->a_ref2 > 0.0) || !(th->rho_ref > 0.0) || !(th->L_ref > 0.0))
+    return XF_ERR_ARG;
+  std::memset(p, 0, sizeof *p);
+  const int dim = g->dim, N = th->n_species;
+  p->dim = dim;
+  p->N = N;
+  p->nv = dim + 2 + N - 1;
+  long long cells = 1, pcells = 1;
+  double hmin = 1e300;
+  for (int a = 0; a < 3; ++a) {
+    if (a < dim) {
+      if (g->n[a] < 3 || g->n[a] > (1 << 24)) return XF_ERR_ARG;
+      if (!(g->hi[a] > g->lo[a])) return XF_ERR_ARG;
+      for (int s = 0; s < 2; ++s)
+        if (g->bc[a][s] < 0 || g->bc[a][s] > 2) return XF_ERR_ARG;
+      if ((g->bc[a][0] == XF_BC_PERIODIC) != (g->bc[a][1] == XF_BC_PERIODIC)) return XF_ERR_ARG;
+      p->n[a] = (int)g->n[a];
+      p->np[a] = p->n[a] + 2 * xf::G;
+      p->go[a] = xf::G;
+      const double dx = (g->hi[a] - g->lo[a]) / (double)g->n[a];
+      p->inv_dx[a] = 1.0 / dx;
+      hmin = std::fmin(hmin, dx);
+      p->bc[a][0] = g->bc[a][0];
+      p->bc[a][1] = g->bc[a][1];
+    } else {
+      p->n[a] = 1;
+      p->np[a] = 1;
+      p->go[a] = 0;
+      p->inv_dx[a] = 0.0;
+    }
+    cells *= p->n[a];
+    pcells *= p->np[a];
+  }
+  if (pcells > (1ll << 31)) return XF_ERR_ARG;
+  p->cells = cells;
+  p->pcells = pcells;
+  p->hmin2_over_2dim = hmin * hmin / (2.0 * dim);
+  const double Ru = 8.314462618;
+  p->T_lo = th->T_lo;
+  p->span = th->T_hi - th->T_lo;
+  p->inv_span = 1.0 / p->span;
+  for (int s = 0; s < N; ++s) {
+    if (!(th->W[s] > 0.0)) return XF_ERR_ARG;
+    const double r = Ru / th->W[s] / th->a_ref2;
+    p->r[s] = r;
+    for (int j = 0; j < 5; ++j) {
+      const double cj = th->cp_coef[s * 5 + j];
+      p->rcp[s][j] = r * cj;
+      p->rh[s][j] = r * p->span * cj / (j + 1);
+    }
+    p->rhoff[s] = r * th->h_off[s];
+    p->invW[s] = 1.0 / th->W[s];
+    if (o->viscous) {
+      for (int j = 0; j < 4; ++j) {
+        p->lnmu[s][j] = th->mu_coef[s * 4 + j];
+        p->lnka[s][j] = th->kappa_coef[s * 4 + j];
+      }
+    }
+  }
+  for (int s = 0; s < N; ++s)
+    for (int t = 0; t < N; ++t) {
+      p->wA[s][t] = (1.0 / std::sqrt(8.0)) * std::pow(1.0 + th->W[s] / th->W[t], -0.5);
+      p->wB[s][t] = std::pow(th->W[t] / th->W[s], 0.25);
+    }
+  const double a_ref = std::sqrt(th->a_ref2);
+  p->fmu = 1.0 / (th->rho_ref * a_ref * th->L_ref);
+  p->fka = 1.0 / (th->rho_ref * a_ref * th->a_ref2 * th->L_ref);
+  p->inv_lewis = o->viscous ? 1.0 / th->lewis : 0.0;
+  p->cfl = o->cfl;
+  p->weno_eps = o->weno_eps;
+  p->newton_rtol = o->newton_rtol;
+  p->newton_max = o->newton_max;
+  p->viscous = o->viscous ? 1 : 0;
+  p->convective = o->convective ? 1 : 0;
+  return XF_OK;
+}
+
+// Primitive recovery + (viscous) nodal gradients + every face flux of Uin.
+xf_status stage_fluxes(xf_handle* h, const double* Uin, int do_cfl, cudaStream_t s) {
+  const xf::Params& p = h->p;
+  h->tab.prim(p, Uin, h->T[h->tcur], h->T[1 - h->tcur], h->Q, h->flags, h->red, do_cfl, s);
+  h->tcur = 1 - h->tcur;
+  if (do_cfl) xf::k_dt_finalize<<<1, 1, 0, s>>>(p, h->red, h->dt, nullptr);
+  if (p.viscous) h->tab.grad(p, h->Q, s);
+  for (int d = 0; d < p.dim; ++d) h->tab.face[d](p, h->Q, h->G[d], h->flags, s);
+  XF_CUDA(cudaGetLastError());
+  return XF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* xf_status_str(xf_status s) {
+  switch (s) {
+    case XF_OK: return "ok";
+    case XF_ERR_ARG: return "invalid argument";
+    case XF_ERR_CUDA: return "CUDA error";
+    case XF_ERR_NONPHYS: return "non-physical state (NaN/inf, rho<=0, p<=0 or T<=0)";
+    case XF_ERR_NEWTON: return "temperature Newton solve did not converge";
+    case XF_ERR_EIGEN: return "face sound speed squared <= 0";
+    case XF_ERR_TIMEOUT: return "bounded device wait gave up";
+    case XF_ERR_OOM: return "out of device memory";
+  }
+  return "unknown status";
+}
+
+const char* xf_last_error(void) { return g_err.c_str(); }
+
+xf_status xf_create(const xf_grid* grid, const xf_thermo* thermo, const xf_opts* opts,
+                    xf_handle** out) {
+  if (!out) return XF_ERR_ARG;
+  *out = nullptr;
+  xf::Params p;
+  xf_status st = fill_params(grid, thermo, opts, &p);
+  if (st != XF_OK) return st;
+  Table tab;
+  if (!pick(p.dim, p.N, &tab)) return XF_ERR_ARG;
+  xf_handle* h = new xf_handle();
+  h->p = p;
+  h->tab = tab;
+  auto alloc = [&](void** ptr, size_t bytes) -> bool {
+    if (cudaMalloc(ptr, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    return true;
+  };
+  const size_t st_bytes = sizeof(double) * (size_t)p.nv * p.cells;
+  bool ok = alloc((void**)&h->U, st_bytes) && alloc((void**)&h->Us, st_bytes) &&
+            alloc((void**)&h->T[0], sizeof(double) * p.cells) &&
+            alloc((void**)&h->T[1], sizeof(double) * p.cells) &&
+            alloc((void**)&h->Q, sizeof(double) * (size_t)tab.nq * p.pcells) &&
+            alloc((void**)&h->dt, sizeof(double)) &&
+            alloc((void**)&h->red, 2 * sizeof(unsigned long long)) &&
+            alloc((void**)&h->flags, sizeof(uint32_t));
+  for (int d = 0; ok && d < p.dim; ++d) {
+    h->nf[d] = (long long)(p.n[0] + (d == 0)) * (p.n[1] + (d == 1)) * (p.n[2] + (d == 2));
+    ok = alloc((void**)&h->G[d], sizeof(double) * (size_t)p.nv * h->nf[d]);
+  }
+  if (!ok) {
+    xf_destroy(h);
+    g_err = "cudaMalloc failed";
+    return XF_ERR_OOM;
+  }
+  if (cudaMemset(h->red, 0, 2 * sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMemset(h->flags, 0, sizeof(uint32_t)) != cudaSuccess ||
+      cudaMemset(h->dt, 0, sizeof(double)) != cudaSuccess ||
+      cudaMemset(h->Q, 0, sizeof(double) * (size_t)tab.nq * p.pcells) != cudaSuccess) {
+    xf_destroy(h);
+    g_err = "cudaMemset failed";
+    return XF_ERR_CUDA;
+  }
+  k_fill<<<blocks(p.cells, 256), 256>>>(h->T[0], p.cells, 300.0);
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    xf_destroy(h);
+    g_err = "initialisation failed";
+    return XF_ERR_CUDA;
+  }
+  *out = h;
+  return XF_OK;
+}
+
+void xf_destroy(xf_handle* h) {
+  if (!h) return;
+  cudaFree(h->U);
+  cudaFree(h->Us);
+  cudaFree(h->T[0]);
+  cudaFree(h->T[1]);
+  cudaFree(h->Q);
+  for (int d = 0; d < 3; ++d) cudaFree(h->G[d]);
+  cudaFree(h->dt);
+  cudaFree(h->red);
+  cudaFree(h->flags);
+  delete h;
+}
+
+int xf_nv(const xf_handle* h) { return h ? h->p.nv : 0; }
+int64_t xf_cells(const xf_handle* h) { return h ? h->p.cells : 0; }
+
+xf_status xf_set_state(xf_handle* h, const double* U, const double* T_guess, void* stream) {
+  if (!h || !U) return XF_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const xf::Params& p = h->p;
+  XF_CUDA(cudaMemcpyAsync(h->U, U, sizeof(double) * (size_t)p.nv * p.cells, cudaMemcpyDefault, s));
+  if (T_guess) {
+    XF_CUDA(cudaMemcpyAsync(h->T[h->tcur], T_guess, sizeof(double) * p.cells, cudaMemcpyDefault, s));
+  } else {
+    k_fill<<<blocks(p.cells, 256), 256, 0, s>>>(h->T[h->tcur], p.cells, 300.0);
+    XF_CUDA(cudaGetLastError());
+  }
+  return XF_OK;
+}
+
+xf_status xf_set_primitive(xf_handle* h, const double* P, void* stream) {
+  if (!h || !P) return XF_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const xf::Params& p = h->p;
+  const double* src = P;
+  if (!is_device_ptr(P)) {
+    XF_CUDA(cudaMemcpyAsync(h->Us, P, sizeof(double) * (size_t)p.nv * p.cells, cudaMemcpyDefault, s));
+    src = h->Us;
+  }
+  h->tab.from_prim(p, src, h->U, h->T[h->tcur], s);
+  XF_CUDA(cudaGetLastError());
+  return XF_OK;
+}
+
+xf_status xf_get_state(xf_handle* h, double* U, double* T, void* stream) {
+  if (!h) return XF_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const xf::Params& p = h->p;
+  if (U) XF_CUDA(cudaMemcpyAsync(U, h->U, sizeof(double) * (size_t)p.nv * p.cells, cudaMemcpyDefault, s));
+  if (T) XF_CUDA(cudaMemcpyAsync(T, h->T[h->tcur], sizeof(double) * p.cells, cudaMemcpyDefault, s));
+  return XF_OK;
+}
+
+xf_status xf_rhs(xf_handle* h, const double* U, double* dUdt, void* stream) {
+  if (!h || !U || !dUdt) return XF_ERR_ARG;
+  if (!is_device_ptr(U) || !is_device_ptr(dUdt)) return XF_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  xf_status st = stage_fluxes(h, U, 0, s);
+  if (st != XF_OK) return st;
+  const xf::Params& p = h->p;
+  h->tab.update(p, h->G[0], h->G[1], h->G[2], nullptr, nullptr, dUdt, h->dt, 0, s);
+  XF_CUDA(cudaGetLastError());
+  return XF_OK;
+}
+
+xf_status xf_compute_dt(xf_handle* h, double* dt_dev, void* stream) {
+  if (!h || !dt_dev) return XF_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const xf::Params& p = h->p;
+  h->tab.prim(p, h->U, h->T[h->tcur], h->T[1 - h->tcur], h->Q, h->flags, h->red, 1, s);
+  h->tcur = 1 - h->tcur;
+  xf::k_dt_finalize<<<1, 1, 0, s>>>(p, h->red, h->dt, dt_dev);
+  XF_CUDA(cudaGetLastError());
+  return XF_OK;
+}
+
+xf_status xf_step_rk3(xf_handle* h, double dt, double* dt_dev_out, void* stream) {
+  if (!h || !(dt == dt)) return XF_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const xf::Params& p = h->p;
+  const bool cfl = !(dt > 0.0);
+  if (!cfl) xf::k_set_scalar<<<1, 1, 0, s>>>(h->dt, dt);
+  // Eq. 16: three stages, U^n kept in U, stages in Us
+  xf_status st = stage_fluxes(h, h->U, cfl ? 1 : 0, s);
+  if (st != XF_OK) return st;
+  h->tab.update(p, h->G[0], h->G[1], h->G[2], h->U, h->U, h->Us, h->dt, 1, s);
+  st = stage_fluxes(h, h->Us, 0, s);
+  if (st != XF_OK) return st;
+  h->tab.update(p, h->G[0], h->G[1], h->G[2], h->U, h->Us, h->Us, h->dt, 2, s);
+  st = stage_fluxes(h, h->Us, 0, s);
+  if (st != XF_OK) return st;
+  h->tab.update(p, h->G[0], h->G[1], h->G[2], h->U, h->Us, h->U, h->dt, 3, s);
+  XF_CUDA(cudaGetLastError());
+  if (dt_dev_out)
+    XF_CUDA(cudaMemcpyAsync(dt_dev_out, h->dt, sizeof(double), cudaMemcpyDeviceToDevice, s));
+  return XF_OK;
+}
+
+xf_status xf_get_status(xf_handle* h, uint32_t* flags, void* stream) {
+  if (!h) return XF_ERR_ARG;
+  uint32_t f = 0;
+  XF_CUDA(cudaMemcpyAsync(&f, h->flags, sizeof f, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+  XF_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  if (flags) *flags = f;
+  if (f & XF_FLAG_NONPHYS) return XF_ERR_NONPHYS;
+  if (f & XF_FLAG_NEWTON) return XF_ERR_NEWTON;
+  if (f & XF_FLAG_EIGEN) return XF_ERR_EIGEN;
+  if (f & XF_FLAG_TIMEOUT) return XF_ERR_TIMEOUT;
+  return XF_OK;
+}
+
+xf_status xf_clear_status(xf_handle* h, void* stream) {
+  if (!h) return XF_ERR_ARG;
+  XF_CUDA(cudaMemsetAsync(h->flags, 0, sizeof(uint32_t), (cudaStream_t)stream));
+  return XF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,708 @@
+// xf_device.cuh -- sm_103a kernels of the multicomponent RHS / SSP-RK3 stage.
+//
+// Design (FP64 on B300 is the binding resource, HBM is not):
+//  * k_prim: one thread per padded cell (interior + 3 ghost layers, boundary
+//    conditions applied by index mapping). Newton temperature solve (Eq. 21)
+//    on mixture-level polynomial coefficients, EOS (Eq. 7), sound speed,
+//    total enthalpy and, when viscous, the Eq. 29 / Eq. 22 mixture transport.
+//    Every per-cell quantity that the faces need is computed exactly once and
+//    stored, so no FP64 work is repeated per face. Stage 1 fuses the CFL
+//    max-reduction (warp shuffles, one atomic per block on ordered bits).
+//  * k_grad: nodal 4th-order velocity derivatives (tangential terms of Eq. 3).
+//  * k_face<D>: one thread per face of direction D. Roe-averaged face state,
+//    the multicomponent eigensystem in the partial form of Sec. III.D.3 (per
+//    field only its eigenvalue, its left row and its right column, all in
+//    closed sparse form), LLF splitting (Eq. 14), two WENO5-JS reconstructions
+//    per field with a single division each, back-projection (Eq. 15), and the
+//    viscous face flux. Writes G = F_hat - F_v per face.
+//  * k_update: conservative difference (Eq. 13) and the SSP-RK3 combination
+//    (Eq. 16), or the plain RHS.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace xf {
+
+constexpr int G = 3;  // ghost layers (6-point WENO5 stencil)
+constexpr int MAXN = 5;
+
+struct Params {
+  int dim, N, nv;
+  int n[3];      // interior cells per axis (1 if inactive)
+  int np[3];     // padded extents
+  int go[3];     // ghost offset per axis (G or 0)
+  int bc[3][2];
+  long long cells, pcells;
+  double inv_dx[3];
+  // thermo, dimensionless (R_s / a_ref^2 pre-multiplied)
+  double T_lo, span, inv_span;
+  double r[MAXN];         // R_s / a_ref^2
+  double rcp[MAXN][5];    // r_s cp_j: c_p,s = sum_j rcp[s][j] tau^j
+  double rh[MAXN][5];     // r_s span cp_j/(j+1): h_s = rhoff_s + sum_j rh[s][j] tau^(j+1)
+  double rhoff[MAXN];     // r_s h_off_s
+  // transport
+  double lnmu[MAXN][4], lnka[MAXN][4];
+  double wA[MAXN][MAXN], wB[MAXN][MAXN];  // Wilke: A = (1+W_s/W_t)^-1/2 / sqrt 8, B = (W_t/W_s)^1/4
+  double invW[MAXN];
+  double fmu, fka, inv_lewis;
+  // numerics
+  double cfl, weno_eps, newton_rtol;
+  int viscous, convective, newton_max;
+  double hmin2_over_2dim;
+};
+
+// Padded per-cell field layout (SoA, stride pcells).
+template <int DIM, int NS>
+struct Lay {
+  static constexpr int NV = DIM + 1 + NS;
+  static constexpr int U = 0;           // conserved, BC applied
+  static constexpr int UN = NV;         // velocity u_a
+  static constexpr int P = UN + DIM;    // pressure
+  static constexpr int C = P + 1;       // sound speed
+  static constexpr int SR = C + 1;      // sqrt(rho)
+  static constexpr int H = SR + 1;      // total enthalpy
+  static constexpr int T = H + 1;       // temperature (K)
+  static constexpr int Y = T + 1;       // Y_1..Y_N
+  static constexpr int MU = Y + NS;     // mixture viscosity
+  static constexpr int KA = MU + 1;     // mixture conductivity
+  static constexpr int DF = KA + 1;     // diffusivity
+  static constexpr int GU = DF + 1;     // nodal d u_a / d x_b at GU + a*DIM + b
+  static constexpr int NQ = GU + DIM * DIM;
+};
+
+__device__ __forceinline__ double ld(const double* p) { return __ldg(p); }
+
+// max of two non-negative doubles through their ordered bit patterns (integer
+// pipe; the FP64 pipe is the scarce unit)
+__device__ __forceinline__ double pmax(double a, double b) {
+  long long x = __double_as_longlong(a), y = __double_as_longlong(b);
+  return __longlong_as_double(x > y ? x : y);
+}
+
+// Boundary mapping of one axis (mirrors XF_BC_*): returns the interior index
+// that feeds padded index i and sets *flip for a symmetric mirror.
+__device__ __forceinline__ int map_axis(int i, int n, int lo, int hi, bool* flip) {
+  *flip = false;
+  if (i >= 0 && i < n) return i;
+  int bc = i < 0 ? lo : hi;
+  if (bc == 1) return i < 0 ? i + n : i - n;
+  if (bc == 2) { *flip = true; return i < 0 ? -1 - i : 2 * n - 1 - i; }
+  return i < 0 ? 0 : n - 1;
+}
+
+// ------------------------------------------------------------ thermo ------
+// c_p,s(T) and h_s(T) of one species at a clamped tau, with the enthalpy
+// continued linearly (slope c_p at the end point) outside [T_lo, T_hi].
+struct TauPt {
+  double tc;   // clamped tau
+  double ext;  // span * (tau - tc)
+};
+__device__ __forceinline__ TauPt tau_of(const Params& p, double T) {
+  double tau = (T - p.T_lo) * p.inv_span;
+  double tc = fmin(fmax(tau, 0.0), 1.0);
+  TauPt r;
+  r.tc = tc;
+  r.ext = p.span * (tau - tc);
+  return r;
+}
+__device__ __forceinline__ double cp_s(const Params& p, int s, double tc) {
+  const double* a = p.rcp[s];
+  return fma(fma(fma(fma(a[4], tc, a[3]), tc, a[2]), tc, a[1]), tc, a[0]);
+}
+__device__ __forceinline__ double h_s(const Params& p, int s, const TauPt& t, double cps) {
+  const double* a = p.rh[s];
+  double poly = fma(fma(fma(fma(a[4], t.tc, a[3]), t.tc, a[2]), t.tc, a[1]), t.tc, a[0]);
+  return fma(poly, t.tc, p.rhoff[s]) + cps * t.ext;
+}
+
+// ------------------------------------------------------------ status ------
+__device__ __forceinline__ void raise(uint32_t* flags, uint32_t bits) {
+  if (bits) atomicOr(flags, bits);
+}
+
+// ================================================================ k_prim ===
+// One thread per padded cell. Reads conserved U (interior, BC by mapping),
+// writes the padded per-cell fields. Stage-1 launches also reduce the CFL
+// maxima over interior cells into red[0] (sum_d (|u_d|+c)/dx_d) and red[1]
+// (viscous diffusivity), as ordered bit patterns of non-negative doubles.
+template <int DIM, int NS>
+__global__ void __launch_bounds__(256)
+k_prim(const __grid_constant__ Params p, const double* __restrict__ U,
+       const double* __restrict__ Tin, double* __restrict__ Tout,
+       double* __restrict__ Q, uint32_t* __restrict__ flags,
+       unsigned long long* __restrict__ red, int do_cfl) {
+  using L = Lay<DIM, NS>;
+  constexpr int NV = L::NV;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long PC = p.pcells;
+  double s_cfl = 0.0, s_nu = 0.0;
+  if (t < PC) {
+    const int ip = (int)(t % p.np[0]);
+    const int jp = (int)((t / p.np[0]) % p.np[1]);
+    const int kp = (int)(t / ((long long)p.np[0] * p.np[1]));
+    const int i = ip - p.go[0], j = jp - p.go[1], k = kp - p.go[2];
+    bool f0 = false, f1 = false, f2 = false;
+    const int si = map_axis(i, p.n[0], p.bc[0][0], p.bc[0][1], &f0);
+    const int sj = DIM > 1 ? map_axis(j, p.n[1], p.bc[1][0], p.bc[1][1], &f1) : 0;
+    const int sk = DIM > 2 ? map_axis(k, p.n[2], p.bc[2][0], p.bc[2][1], &f2) : 0;
+    const bool interior = (si == i) && (sj == j) && (sk == k);
+    const long long src = ((long long)sk * p.n[1] + sj) * p.n[0] + si;
+    const long long C = p.cells;
+    double u[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) u[v] = ld(U + v * C + src);
+    if (f0) u[1] = -u[1];
+    if (DIM > 1 && f1) u[2] = -u[2];
+    if (DIM > 2 && f2) u[3] = -u[3];
+    uint32_t st = 0;
+    bool finite = true;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) finite = finite && isfinite(u[v]);
+    const double rho = u[0];
+    const double irho = 1.0 / rho;
+    double vel[DIM], ke = 0.0;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) { vel[a] = u[1 + a] * irho; ke = fma(vel[a], vel[a], ke); }
+    const double E = u[DIM + 1];
+    double Y[NS], ysum = 0.0;
+#pragma unroll
+    for (int s = 0; s < NS - 1; ++s) { Y[s] = u[DIM + 2 + s] * irho; ysum += Y[s]; }
+    Y[NS - 1] = 1.0 - ysum;
+    const double e = fma(E, irho, -0.5 * ke);
+    // mixture polynomial coefficients: c_p(tau) = sum A_j tau^j,
+    // h(tau) = B + sum Ah_j tau^(j+1), R = Rm
+    double A[5], Ah[5], Rm = 0.0, B = 0.0;
+#pragma unroll
+    for (int jj = 0; jj < 5; ++jj) { A[jj] = 0.0; Ah[jj] = 0.0; }
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      Rm = fma(Y[s], p.r[s], Rm);
+      B = fma(Y[s], p.rhoff[s], B);
+#pragma unroll
+      for (int jj = 0; jj < 5; ++jj) {
+        A[jj] = fma(Y[s], p.rcp[s][jj], A[jj]);
+        Ah[jj] = fma(Y[s], p.rh[s][jj], Ah[jj]);
+      }
+    }
+    // Newton (Eq. 21): T <- T + (e - e(T)) / c_v(T), stop at |dT| <= rtol T;
+    // a non-positive iterate is replaced by half the previous one
+    double T = ld(Tin + src);
+    bool conv = false;
+    for (int it = 0; it < p.newton_max; ++it) {
+      const TauPt tp = tau_of(p, T);
+      const double cpm = fma(fma(fma(fma(A[4], tp.tc, A[3]), tp.tc, A[2]), tp.tc, A[1]), tp.tc, A[0]);
+      const double hp = fma(fma(fma(fma(fma(Ah[4], tp.tc, Ah[3]), tp.tc, Ah[2]), tp.tc, Ah[1]), tp.tc, Ah[0]), tp.tc, B);
+      const double eT = fma(cpm, tp.ext, hp) - Rm * T;
+      double Tn = T + (e - eT) / (cpm - Rm);
+      if (!(Tn > 0.0)) Tn = 0.5 * T;
+      conv = fabs(Tn - T) <= p.newton_rtol * Tn;
+      T = Tn;
+      if (conv) break;
+    }
+    if (!conv) st |= 2u;
+    const TauPt tp = tau_of(p, T);
+    const double cpm = fma(fma(fma(fma(A[4], tp.tc, A[3]), tp.tc, A[2]), tp.tc, A[1]), tp.tc, A[0]);
+    const double cvm = cpm - Rm;
+    const double RT = Rm * T;
+    const double pr = rho * RT;
+    const double c2 = cpm * RT / cvm;
+    const double c = sqrt(c2);
+    const double H = (E + pr) * irho;
+    if (!finite || !(rho > 0.0) || !(pr > 0.0) || !(T > 0.0)) st |= 1u;
+    double* q = Q + t;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) q[(L::U + v) * PC] = u[v];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) q[(L::UN + a) * PC] = vel[a];
+    q[L::P * PC] = pr;
+    q[L::C * PC] = c;
+    q[L::SR * PC] = sqrt(rho);
+    q[L::H * PC] = H;
+    q[L::T * PC] = T;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) q[(L::Y + s) * PC] = Y[s];
+    double mu = 0.0, ka = 0.0, Dd = 0.0;
+    if (p.viscous) {
+      // Eq. 29 fits; sqrt(mu_s) = exp(ln mu_s / 2) feeds the Wilke ratios (Eq. 22)
+      const double lnT = log(T);
+      double smu[NS], ska[NS], ismu[NS], iska[NS], X[NS], xs = 0.0;
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        const double lm = fma(fma(fma(p.lnmu[s][3], lnT, p.lnmu[s][2]), lnT, p.lnmu[s][1]), lnT, p.lnmu[s][0]);
+        const double lk = fma(fma(fma(p.lnka[s][3], lnT, p.lnka[s][2]), lnT, p.lnka[s][1]), lnT, p.lnka[s][0]);
+        smu[s] = exp(0.5 * lm);
+        ska[s] = exp(0.5 * lk);
+        ismu[s] = 1.0 / smu[s];
+        iska[s] = 1.0 / ska[s];
+        X[s] = Y[s] * p.invW[s];
+        xs += X[s];
+      }
+      const double ixs = 1.0 / xs;
+#pragma unroll
+      for (int s = 0; s < NS; ++s) X[s] *= ixs;
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        double dm = 0.0, dk = 0.0;
+#pragma unroll
+        for (int tt = 0; tt < NS; ++tt) {
+          const double bm = fma(smu[s] * ismu[tt], p.wB[s][tt], 1.0);
+          const double bk = fma(ska[s] * iska[tt], p.wB[s][tt], 1.0);
+          const double xa = X[tt] * p.wA[s][tt];
+          dm = fma(xa, bm * bm, dm);
+          dk = fma(xa, bk * bk, dk);
+        }
+        mu = fma(X[s] * smu[s] * smu[s], 1.0 / dm, mu);
+        ka = fma(X[s] * ska[s] * ska[s], 1.0 / dk, ka);
+      }
+      mu *= p.fmu;
+      ka *= p.fka;
+      Dd = ka * p.inv_lewis / (rho * cpm);
+      q[L::MU * PC] = mu;
+      q[L::KA * PC] = ka;
+      q[L::DF * PC] = Dd;
+    }
+    if (interior) {
+      Tout[src] = T;
+      if (do_cfl) {
+        double sc = 0.0;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) sc = fma(fabs(vel[a]) + c, p.inv_dx[a], sc);
+        s_cfl = sc;
+        if (p.viscous) {
+          const double nu1 = (4.0 / 3.0) * mu * irho;
+          const double nu2 = ka * irho / cvm;
+          s_nu = pmax(pmax(nu1, nu2), Dd);
+        }
+      }
+    }
+    raise(flags, st);
+  }
+  if (do_cfl) {
+    unsigned long long a = (unsigned long long)__double_as_longlong(s_cfl);
+    unsigned long long b = (unsigned long long)__double_as_longlong(s_nu);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long a2 = __shfl_xor_sync(0xffffffffu, a, o);
+      const unsigned long long b2 = __shfl_xor_sync(0xffffffffu, b, o);
+      a = a2 > a ? a2 : a;
+      b = b2 > b ? b2 : b;
+    }
+    __shared__ unsigned long long sa[8], sb[8];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) { sa[w] = a; sb[w] = b; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+        a = sa[k] > a ? sa[k] : a;
+        b = sb[k] > b ? sb[k] : b;
+      }
+      atomicMax(red + 0, a);
+      atomicMax(red + 1, b);
+    }
+  }
+}
+
+// dt from the reduced maxima (one thread); resets the accumulators.
+__global__ void k_dt_finalize(const __grid_constant__ Params p, unsigned long long* red,
+                              double* dt_out, double* dt_copy) {
+  const double smax = __longlong_as_double((long long)red[0]);
+  const double numax = __longlong_as_double((long long)red[1]);
+  double dt = p.cfl / smax;
+  if (p.viscous && numax > 0.0) dt = fmin(dt, p.cfl * p.hmin2_over_2dim / numax);
+  *dt_out = dt;
+  if (dt_copy) *dt_copy = dt;
+  red[0] = 0ull;
+  red[1] = 0ull;
+}
+
+__global__ void k_set_scalar(double* dst, double v) { *dst = v; }
+
+// ================================================================ k_grad ===
+// Nodal (1,-8,0,8,-1)/(12 dx) velocity derivatives along every active axis b,
+// wherever the +-2 neighbours along b lie inside the padded box.
+template <int DIM, int NS>
+__global__ void __launch_bounds__(256)
+k_grad(const __grid_constant__ Params p, double* __restrict__ Q) {
+  using L = Lay<DIM, NS>;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= p.pcells) return;
+  const long long PC = p.pcells;
+  int idx[3];
+  idx[0] = (int)(t % p.np[0]);
+  idx[1] = (int)((t / p.np[0]) % p.np[1]);
+  idx[2] = (int)(t / ((long long)p.np[0] * p.np[1]));
+  const long long stride[3] = {1, p.np[0], (long long)p.np[0] * p.np[1]};
+#pragma unroll
+  for (int b = 0; b < DIM; ++b) {
+    if (idx[b] < 2 || idx[b] >= p.np[b] - 2) continue;
+    const long long sb = stride[b];
+    const double w = p.inv_dx[b] * (1.0 / 12.0);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      const double* ua = Q + (L::UN + a) * PC + t;
+      const double g = ((ld(ua - 2 * sb) - ld(ua + 2 * sb)) + 8.0 * (ld(ua + sb) - ld(ua - sb))) * w;
+      Q[(L::GU + a * DIM + b) * PC + t] = g;
+    }
+  }
+}
+
+// ================================================================= WENO5 ===
+// WENO5-JS at i+1/2 from f0..f4 = f_{i-2..i+2}. The nonlinear weights
+// d_k/(eps+b_k)^2 are scaled by prod_j (eps+b_j)^2 so that one division
+// normalises them.
+__device__ __forceinline__ double weno5(double f0, double f1, double f2, double f3, double f4,
+                                        double eps) {
+  const double t0 = fma(-2.0, f1, f0) + f2;
+  const double u0 = fma(-4.0, f1, f0) + 3.0 * f2;
+  const double t1 = fma(-2.0, f2, f1) + f3;
+  const double u1 = f1 - f3;
+  const double t2 = fma(-2.0, f3, f2) + f4;
+  const double u2 = fma(-4.0, f3, 3.0 * f2) + f4;
+  const double k13 = 13.0 / 12.0;
+  const double s0 = eps + fma(k13 * t0, t0, 0.25 * u0 * u0);
+  const double s1 = eps + fma(k13 * t1, t1, 0.25 * u1 * u1);
+  const double s2 = eps + fma(k13 * t2, t2, 0.25 * u2 * u2);
+  const double p12 = s1 * s2, p02 = s0 * s2, p01 = s0 * s1;
+  const double a0 = 0.1 * p12 * p12;
+  const double a1 = 0.6 * p02 * p02;
+  const double a2 = 0.3 * p01 * p01;
+  const double q0 = fma(11.0 / 6.0, f2, fma(-7.0 / 6.0, f1, (1.0 / 3.0) * f0));
+  const double q1 = fma(1.0 / 3.0, f3, fma(5.0 / 6.0, f2, (-1.0 / 6.0) * f1));
+  const double q2 = fma(-1.0 / 6.0, f4, fma(5.0 / 6.0, f3, (1.0 / 3.0) * f2));
+  return fma(a0, q0, fma(a1, q1, a2 * q2)) / (a0 + a1 + a2);
+}
+
+// ================================================================= k_face ===
+// One thread per face of direction D (faces i = 0..n_D, left cell i-1).
+template <int DIM, int NS, int D>
+__global__ void __launch_bounds__(128)
+k_face(const __grid_constant__ Params p, const double* __restrict__ Q,
+       double* __restrict__ Gf, uint32_t* __restrict__ flags) {
+  using L = Lay<DIM, NS>;
+  constexpr int NV = L::NV;
+  constexpr int IE = DIM + 1;
+  const int nf0 = p.n[0] + (D == 0), nf1 = p.n[1] + (D == 1), nf2 = p.n[2] + (D == 2);
+  const long long nfaces = (long long)nf0 * nf1 * nf2;
+  const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= nfaces) return;
+  int id[3];
+  id[0] = (int)(f % nf0);
+  id[1] = (int)((f / nf0) % nf1);
+  id[2] = (int)(f / ((long long)nf0 * nf1));
+  id[D] -= 1;  // left cell
+  const long long PC = p.pcells;
+  const long long sy = p.np[0], sz = (long long)p.np[0] * p.np[1];
+  const long long c0 = (id[2] + p.go[2]) * sz + (id[1] + p.go[1]) * sy + (id[0] + p.go[0]);
+  const long long sd = D == 0 ? 1 : (D == 1 ? sy : sz);
+  const double* q0 = Q + c0;
+#define QF(field, m) ld(q0 + (long long)(field) * PC + (long long)(m) * sd)
+  double Gout[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Gout[v] = 0.0;
+  uint32_t st = 0;
+
+  if (p.convective) {
+    // ---- Roe-averaged face state (sqrt(rho) weights)
+    const double sL = QF(L::SR, 0), sR = QF(L::SR, 1);
+    const double iw = 1.0 / (sL + sR);
+    const double tL = sL * iw, tR = sR * iw;
+    double ub[DIM], q2 = 0.0;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      ub[a] = fma(tL, QF(L::UN + a, 0), tR * QF(L::UN + a, 1));
+      q2 = fma(ub[a], ub[a], q2);
+    }
+    const double Hb = fma(tL, QF(L::H, 0), tR * QF(L::H, 1));
+    const double Tb = fma(tL, QF(L::T, 0), tR * QF(L::T, 1));
+    double Yb[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) Yb[s] = fma(tL, QF(L::Y + s, 0), tR * QF(L::Y + s, 1));
+    const TauPt tp = tau_of(p, Tb);
+    double es[NS], Rb = 0.0, cvb = 0.0;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      const double cps = cp_s(p, s, tp.tc);
+      es[s] = h_s(p, s, tp, cps) - p.r[s] * Tb;
+      Rb = fma(Yb[s], p.r[s], Rb);
+      cvb = fma(Yb[s], cps - p.r[s], cvb);
+    }
+    const double Gam = Rb / cvb;
+    const double hq2 = 0.5 * q2;
+    double phi[NS], c2 = 0.0;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      phi[s] = fma(p.r[s], Tb, -Gam * (es[s] - hq2));
+      c2 = fma(Yb[s], phi[s], c2);
+    }
+    c2 = fma(Gam, Hb - q2, c2);
+    if (!(c2 > 0.0)) {
+      st |= 4u;
+      const double cl = QF(L::C, 0), cr = QF(L::C, 1);
+      c2 = 0.5 * (cl * cl + cr * cr);
+    }
+    const double c = sqrt(c2);
+    const double ic2 = 1.0 / c2;
+    const double hic2 = 0.5 * ic2;
+    const double iGam = cvb / Rb;
+    const double un = ub[D];
+    // ---- stencil m = i-2..i+3 (offsets -2..3 from the left cell): rho, u_n,
+    //      p, g.U and the LLF maxima of |u-c|, |u+c|, |u|
+    double rho_m[6], un_m[6], p_m[6], gU[6];
+    double am = 0.0, ap = 0.0, a0 = 0.0;
+    const double phiN = phi[NS - 1];
+#pragma unroll
+    for (int m = 0; m < 6; ++m) {
+      const int o = m - 2;
+      rho_m[m] = QF(L::U, o);
+      un_m[m] = QF(L::UN + D, o);
+      p_m[m] = QF(L::P, o);
+      const double cm = QF(L::C, o);
+      am = pmax(am, fabs(un_m[m] - cm));
+      ap = pmax(ap, fabs(un_m[m] + cm));
+      a0 = pmax(a0, fabs(un_m[m]));
+      double g = phiN * rho_m[m];
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) g = fma(-Gam * ub[a], QF(L::U + 1 + a, o), g);
+      g = fma(Gam, QF(L::U + IE, o), g);
+#pragma unroll
+      for (int s = 0; s < NS - 1; ++s) g = fma(phi[s] - phiN, QF(L::U + IE + 1 + s, o), g);
+      gU[m] = g;
+    }
+    const double eps = p.weno_eps;
+    // ---- PER: one characteristic field at a time; l.F_m = u_m (l.U_m) +
+    //      p_m (l[m_n] + u_m l[E]) for the sparse rows below
+    double Fk_m, Fk_p, Fk_e;
+    {
+      double wp[6], wm[6];
+      // u - c: l = (g - c (-u_n e_rho + e_mn)) / (2 c^2)
+      {
+        const double lmn = (-Gam * un - c) * hic2, lE = Gam * hic2;
+        const double ha = 0.5 * am;
+#pragma unroll
+        for (int m = 0; m < 6; ++m) {
+          const double nU = fma(-un, rho_m[m], QF(L::U + 1 + D, m - 2));
+          const double LU = fma(-c, nU, gU[m]) * hic2;
+          const double LF = fma(un_m[m], LU, p_m[m] * fma(un_m[m], lE, lmn));
+          wp[m] = fma(ha, LU, 0.5 * LF);
+          wm[m] = fma(-ha, LU, 0.5 * LF);
+        }
+        Fk_m = weno5(wp[0], wp[1], wp[2], wp[3], wp[4], eps) +
+               weno5(wm[5], wm[4], wm[3], wm[2], wm[1], eps);
+      }
+      // u + c
+      {
+        const double lmn = (-Gam * un + c) * hic2, lE = Gam * hic2;
+        const double ha = 0.5 * ap;
+#pragma unroll
+        for (int m = 0; m < 6; ++m) {
+          const double nU = fma(-un, rho_m[m], QF(L::U + 1 + D, m - 2));
+          const double LU = fma(c, nU, gU[m]) * hic2;
+          const double LF = fma(un_m[m], LU, p_m[m] * fma(un_m[m], lE, lmn));
+          wp[m] = fma(ha, LU, 0.5 * LF);
+          wm[m] = fma(-ha, LU, 0.5 * LF);
+        }
+        Fk_p = weno5(wp[0], wp[1], wp[2], wp[3], wp[4], eps) +
+               weno5(wm[5], wm[4], wm[3], wm[2], wm[1], eps);
+      }
+      // entropy: l = e_rho - g / c^2
+      {
+        const double lmn = Gam * un * ic2, lE = -Gam * ic2;
+        const double ha = 0.5 * a0;
+#pragma unroll
+        for (int m = 0; m < 6; ++m) {
+          const double LU = fma(-gU[m], ic2, rho_m[m]);
+          const double LF = fma(un_m[m], LU, p_m[m] * fma(un_m[m], lE, lmn));
+          wp[m] = fma(ha, LU, 0.5 * LF);
+          wm[m] = fma(-ha, LU, 0.5 * LF);
+        }
+        Fk_e = weno5(wp[0], wp[1], wp[2], wp[3], wp[4], eps) +
+               weno5(wm[5], wm[4], wm[3], wm[2], wm[1], eps);
+      }
+    }
+    // back-projection of the three dense right columns (Eq. 15)
+    {
+      const double S = Fk_m + Fk_p + Fk_e;
+      const double Dl = Fk_p - Fk_m;
+      Gout[0] = S;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) Gout[1 + a] = ub[a] * S;
+      Gout[1 + D] = fma(c, Dl, Gout[1 + D]);
+      Gout[IE] = fma(Hb, S, fma(un * c, Dl, -c2 * iGam * Fk_e));
+#pragma unroll
+      for (int s = 0; s < NS - 1; ++s) Gout[IE + 1 + s] = Yb[s] * S;
+    }
+    const double ha0 = 0.5 * a0;
+    // tangential momenta: l = (-u_t, e_{m_t}), r = e_{m_t} + u_t e_E
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      if (a == D) continue;
+      double wp[6], wm[6];
+#pragma unroll
+      for (int m = 0; m < 6; ++m) {
+        const double LU = fma(-ub[a], rho_m[m], QF(L::U + 1 + a, m - 2));
+        const double LF = un_m[m] * LU;
+        wp[m] = fma(ha0, LU, 0.5 * LF);
+        wm[m] = fma(-ha0, LU, 0.5 * LF);
+      }
+      const double Fk = weno5(wp[0], wp[1], wp[2], wp[3], wp[4], eps) +
+                        weno5(wm[5], wm[4], wm[3], wm[2], wm[1], eps);
+      Gout[1 + a] += Fk;
+      Gout[IE] = fma(ub[a], Fk, Gout[IE]);
+    }
+    // species: l = (-Y_s, e_{rhoY_s}), r = e_{rhoY_s} - (phi_s - phi_N)/Gamma e_E
+#pragma unroll
+    for (int s = 0; s < NS - 1; ++s) {
+      double wp[6], wm[6];
+#pragma unroll
+      for (int m = 0; m < 6; ++m) {
+        const double LU = fma(-Yb[s], rho_m[m], QF(L::U + IE + 1 + s, m - 2));
+        const double LF = un_m[m] * LU;
+        wp[m] = fma(ha0, LU, 0.5 * LF);
+        wm[m] = fma(-ha0, LU, 0.5 * LF);
+      }
+      const double Fk = weno5(wp[0], wp[1], wp[2], wp[3], wp[4], eps) +
+                        weno5(wm[5], wm[4], wm[3], wm[2], wm[1], eps);
+      Gout[IE + 1 + s] += Fk;
+      Gout[IE] = fma(-(phi[s] - phiN) * iGam, Fk, Gout[IE]);
+    }
+  }
+
+  if (p.viscous) {
+    // face values (-1, 9, 9, -1)/16, normal derivatives (1, -15, 15, -1)/(12 dx)
+    const double wi = 1.0 / 16.0;
+    const double wd = p.inv_dx[D] * (1.0 / 12.0);
+#define FI(field) ((9.0 * (QF(field, 0) + QF(field, 1)) - (QF(field, -1) + QF(field, 2))) * wi)
+#define FD(field) ((15.0 * (QF(field, 1) - QF(field, 0)) - (QF(field, 2) - QF(field, -1))) * wd)
+    const double mu = FI(L::MU), ka = FI(L::KA), Df = FI(L::DF), rf = FI(L::U), Tf = FI(L::T);
+    double uf[DIM], gr[DIM][DIM];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      uf[a] = FI(L::UN + a);
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) gr[a][b] = (b == D) ? FD(L::UN + a) : FI(L::GU + a * DIM + b);
+    }
+    double div = 0.0;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) div += gr[a][a];
+    double work = 0.0;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      double tau = mu * (gr[D][a] + gr[a][D]);
+      if (a == D) tau = fma(-2.0 / 3.0 * mu, div, tau);
+      Gout[1 + a] -= tau;
+      work = fma(tau, uf[a], work);
+    }
+    double dY[NS], Yf[NS], sdY = 0.0;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) { dY[s] = FD(L::Y + s); Yf[s] = FI(L::Y + s); sdY += dY[s]; }
+    const double corr = Df * sdY;
+    const TauPt tp = tau_of(p, Tf);
+    double qd = 0.0;
+    double J[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      J[s] = -rf * fma(Df, dY[s], -Yf[s] * corr);
+      const double hs = h_s(p, s, tp, cp_s(p, s, tp.tc));
+      qd = fma(hs, J[s], qd);
+    }
+    const double dT = FD(L::T);
+    Gout[IE] -= fma(ka, dT, work) - qd;
+#pragma unroll
+    for (int s = 0; s < NS - 1; ++s) Gout[IE + 1 + s] += J[s];
+#undef FI
+#undef FD
+  }
+#undef QF
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Gf[v * nfaces + f] = Gout[v];
+  raise(flags, st);
+}
+
+// =============================================================== k_update ===
+// Conservative difference (Eq. 13) and SSP-RK3 (Eq. 16).
+//   mode 0: out = L(U)                   (plain RHS)
+//   mode 1: out = Un + dt L              (stage 1)
+//   mode 2: out = 3/4 Un + 1/4 (Us + dt L)
+//   mode 3: out = 1/3 Un + 2/3 (Us + dt L)
+template <int DIM, int NS>
+__global__ void __launch_bounds__(256)
+k_update(const __grid_constant__ Params p, const double* __restrict__ Gx,
+         const double* __restrict__ Gy, const double* __restrict__ Gz,
+         const double* Un, const double* Us, double* out, const double* __restrict__ dtp,
+         int mode) {
+  constexpr int NV = DIM + 1 + NS;
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= p.cells) return;
+  const int i = (int)(c % p.n[0]);
+  const int j = (int)((c / p.n[0]) % p.n[1]);
+  const int k = (int)(c / ((long long)p.n[0] * p.n[1]));
+  const long long C = p.cells;
+  long long fy = 0, fz = 0, NFY = 0, NFZ = 0, sy = 0, sz = 0;
+  const long long NFX = (long long)(p.n[0] + 1) * p.n[1] * p.n[2];
+  const long long fx = ((long long)k * p.n[1] + j) * (p.n[0] + 1) + i;
+  if (DIM > 1) {
+    NFY = (long long)p.n[0] * (p.n[1] + 1) * p.n[2];
+    fy = ((long long)k * (p.n[1] + 1) + j) * p.n[0] + i;
+    sy = p.n[0];
+  }
+  if (DIM > 2) {
+    NFZ = (long long)p.n[0] * p.n[1] * (p.n[2] + 1);
+    fz = c;
+    sz = (long long)p.n[0] * p.n[1];
+  }
+  const double dt = mode ? *dtp : 0.0;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    double R = -(ld(Gx + v * NFX + fx + 1) - ld(Gx + v * NFX + fx)) * p.inv_dx[0];
+    if (DIM > 1) R = fma(-(ld(Gy + v * NFY + fy + sy) - ld(Gy + v * NFY + fy)), p.inv_dx[1], R);
+    if (DIM > 2) R = fma(-(ld(Gz + v * NFZ + fz + sz) - ld(Gz + v * NFZ + fz)), p.inv_dx[2], R);
+    double o;
+    if (mode == 0) {
+      o = R;
+    } else if (mode == 1) {
+      o = fma(dt, R, Un[v * C + c]);
+    } else if (mode == 2) {
+      o = fma(0.75, Un[v * C + c], 0.25 * fma(dt, R, Us[v * C + c]));
+    } else {
+      o = fma(1.0 / 3.0, Un[v * C + c], (2.0 / 3.0) * fma(dt, R, Us[v * C + c]));
+    }
+    out[v * C + c] = o;
+  }
+}
+
+// ============================================================ k_from_prim ===
+// Primitive (rho, u, p, Y) -> conserved U and T with the EOS (Eq. 7).
+template <int DIM, int NS>
+__global__ void __launch_bounds__(256)
+k_from_prim(const __grid_constant__ Params p, const double* __restrict__ P,
+            double* __restrict__ U, double* __restrict__ T) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= p.cells) return;
+  const long long C = p.cells;
+  const double rho = P[c];
+  double Y[NS], ys = 0.0, Rm = 0.0;
+#pragma unroll
+  for (int s = 0; s < NS - 1; ++s) { Y[s] = P[(DIM + 2 + s) * C + c]; ys += Y[s]; }
+  Y[NS - 1] = 1.0 - ys;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) Rm = fma(Y[s], p.r[s], Rm);
+  const double pr = P[(DIM + 1) * C + c];
+  const double Tc = pr / (rho * Rm);
+  const TauPt tp = tau_of(p, Tc);
+  double e = 0.0, ke = 0.0;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) e = fma(Y[s], h_s(p, s, tp, cp_s(p, s, tp.tc)) - p.r[s] * Tc, e);
+  U[c] = rho;
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    const double u = P[(1 + a) * C + c];
+    U[(1 + a) * C + c] = rho * u;
+    ke = fma(u, u, ke);
+  }
+  U[(DIM + 1) * C + c] = rho * fma(0.5, ke, e);
+#pragma unroll
+  for (int s = 0; s < NS - 1; ++s) U[(DIM + 2 + s) * C + c] = rho * Y[s];
+  T[c] = Tc;
+}
+
+}  // namespace xf

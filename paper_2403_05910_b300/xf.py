@@ -1,0 +1,198 @@
+"""ctypes binding of the C-ABI library ``libxf.so`` (include/xf.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels behind the C-ABI. Device memory and streams come from PyTorch. There
+is no CPU fallback: if the library cannot be loaded, importing this module
+raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libxf.so")
+
+(XF_OK, XF_ERR_ARG, XF_ERR_CUDA, XF_ERR_NONPHYS, XF_ERR_NEWTON, XF_ERR_EIGEN, XF_ERR_TIMEOUT,
+ XF_ERR_OOM) = range(8)
+FLAG_NONPHYS, FLAG_NEWTON, FLAG_EIGEN, FLAG_TIMEOUT = 1, 2, 4, 8
+BC_TRANSMISSIVE, BC_PERIODIC, BC_SYMMETRIC = 0, 1, 2
+
+
+class Grid(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n", C.c_int64 * 3), ("lo", C.c_double * 3),
+                ("hi", C.c_double * 3), ("bc", (C.c_int * 2) * 3)]
+
+
+class Thermo(C.Structure):
+    _fields_ = [("n_species", C.c_int), ("W", C.POINTER(C.c_double)), ("T_lo", C.c_double),
+                ("T_hi", C.c_double), ("cp_coef", C.POINTER(C.c_double)),
+                ("h_off", C.POINTER(C.c_double)), ("mu_coef", C.POINTER(C.c_double)),
+                ("kappa_coef", C.POINTER(C.c_double)), ("lewis", C.c_double),
+                ("a_ref2", C.c_double), ("rho_ref", C.c_double), ("L_ref", C.c_double)]
+
+
+class Opts(C.Structure):
+    _fields_ = [("cfl", C.c_double), ("weno", C.c_int), ("split", C.c_int), ("viscous", C.c_int),
+                ("convective", C.c_int), ("newton_max", C.c_int), ("newton_rtol", C.c_double),
+                ("weno_eps", C.c_double)]
+
+
+# every symbol declared in include/xf.h
+EXPORTS = ["xf_create", "xf_destroy", "xf_nv", "xf_cells", "xf_set_state", "xf_set_primitive",
+           "xf_get_state", "xf_rhs", "xf_compute_dt", "xf_step_rk3", "xf_get_status",
+           "xf_clear_status", "xf_status_str", "xf_last_error"]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libxf.so is not built ({LIB_PATH}); run paper_2403_05910_b300/build.py")
+    L = C.CDLL(LIB_PATH)
+    vp = C.c_void_p
+    L.xf_create.argtypes = [C.POINTER(Grid), C.POINTER(Thermo), C.POINTER(Opts), C.POINTER(vp)]
+    L.xf_destroy.argtypes = [vp]
+    L.xf_destroy.restype = None
+    L.xf_nv.argtypes = [vp]
+    L.xf_cells.argtypes = [vp]
+    L.xf_cells.restype = C.c_int64
+    L.xf_set_state.argtypes = [vp, vp, vp, vp]
+    L.xf_set_primitive.argtypes = [vp, vp, vp]
+    L.xf_get_state.argtypes = [vp, vp, vp, vp]
+    L.xf_rhs.argtypes = [vp, vp, vp, vp]
+    L.xf_compute_dt.argtypes = [vp, vp, vp]
+    L.xf_step_rk3.argtypes = [vp, C.c_double, vp, vp]
+    L.xf_get_status.argtypes = [vp, C.POINTER(C.c_uint32), vp]
+    L.xf_clear_status.argtypes = [vp, vp]
+    L.xf_status_str.argtypes = [C.c_int]
+    L.xf_status_str.restype = C.c_char_p
+    L.xf_last_error.restype = C.c_char_p
+    return L
+
+
+lib = _load()
+
+
+class XFError(RuntimeError):
+    def __init__(self, code, what=""):
+        msg = lib.xf_status_str(code).decode()
+        if code == XF_ERR_CUDA:
+            msg += ": " + lib.xf_last_error().decode()
+        super().__init__(f"{what}: {msg}" if what else msg)
+        self.code = code
+
+
+def check(code, what=""):
+    if code != XF_OK:
+        raise XFError(code, what)
+
+
+def _dptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def structs(case, viscous=None, convective=True, cfl=None, newton_max=50, newton_rtol=1e-13,
+            weno_eps=1e-6):
+    """(Grid, Thermo, Opts, keepalive) from a generator ``Case``."""
+    g = Grid()
+    g.dim = case.dim
+    for a in range(3):
+        g.n[a] = case.n[a]
+        g.lo[a] = case.lo[a]
+        g.hi[a] = case.hi[a]
+        g.bc[a][0], g.bc[a][1] = case.bc[a]
+    sp = case.species
+    keep = [np.ascontiguousarray(sp.W, dtype=np.float64),
+            np.ascontiguousarray(sp.cp_coef, dtype=np.float64),
+            np.ascontiguousarray(sp.h_off, dtype=np.float64),
+            np.ascontiguousarray(sp.mu_coef, dtype=np.float64),
+            np.ascontiguousarray(sp.kappa_coef, dtype=np.float64)]
+    t = Thermo()
+    t.n_species = sp.n
+    t.W, t.cp_coef, t.h_off, t.mu_coef, t.kappa_coef = (_dptr(k) for k in keep)
+    t.T_lo, t.T_hi = sp.T_lo, sp.T_hi
+    t.lewis = sp.lewis
+    t.a_ref2, t.rho_ref, t.L_ref = case.a_ref2, case.rho_ref, case.L_ref
+    o = Opts()
+    o.cfl = case.cfl if cfl is None else cfl
+    o.weno = 5
+    o.split = 0
+    o.viscous = int(case.viscous if viscous is None else viscous)
+    o.convective = int(convective)
+    o.newton_max = newton_max
+    o.newton_rtol = newton_rtol
+    o.weno_eps = weno_eps
+    return g, t, o, keep
+
+
+def stream_ptr(stream=None):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def ptr(x):
+    """Raw address of a torch tensor or numpy array (None passes through)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return C.c_void_p(x.ctypes.data)
+    return C.c_void_p(x.data_ptr())
+
+
+class Solver:
+    """One grid's solver state behind an ``xf_handle``.
+
+    Arguments are torch float64 tensors (CUDA, or CPU for the host-or-device
+    entry points) or numpy arrays where the C-ABI accepts host memory.
+    """
+
+    def __init__(self, case, **kw):
+        g, t, o, keep = structs(case, **kw)
+        self.case = case
+        self.nv = case.n_v
+        self.cells = case.cells
+        h = C.c_void_p()
+        check(lib.xf_create(C.byref(g), C.byref(t), C.byref(o), C.byref(h)), "xf_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.xf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, U, T=None, stream=None):
+        check(lib.xf_set_state(self.h, ptr(U), ptr(T), stream_ptr(stream)), "xf_set_state")
+
+    def set_primitive(self, P, stream=None):
+        check(lib.xf_set_primitive(self.h, ptr(P), stream_ptr(stream)), "xf_set_primitive")
+
+    def get_state(self, U=None, T=None, stream=None):
+        check(lib.xf_get_state(self.h, ptr(U), ptr(T), stream_ptr(stream)), "xf_get_state")
+
+    def rhs(self, U, dUdt, stream=None):
+        check(lib.xf_rhs(self.h, ptr(U), ptr(dUdt), stream_ptr(stream)), "xf_rhs")
+
+    def compute_dt(self, dt_dev, stream=None):
+        check(lib.xf_compute_dt(self.h, ptr(dt_dev), stream_ptr(stream)), "xf_compute_dt")
+
+    def step(self, dt=0.0, dt_dev=None, stream=None):
+        check(lib.xf_step_rk3(self.h, float(dt), ptr(dt_dev), stream_ptr(stream)), "xf_step_rk3")
+
+    def status(self, stream=None):
+        f = C.c_uint32(0)
+        code = lib.xf_get_status(self.h, C.byref(f), stream_ptr(stream))
+        if code == XF_ERR_CUDA:
+            check(code, "xf_get_status")
+        return f.value
+
+    def clear_status(self, stream=None):
+        check(lib.xf_clear_status(self.h, stream_ptr(stream)), "xf_clear_status")
