@@ -156,6 +156,25 @@ xf_status xf_step_rk3(xf_handle *h, double dt, double *dt_dev_out, void *stream)
 xf_status xf_get_status(xf_handle *h, uint32_t *flags, void *stream);
 xf_status xf_clear_status(xf_handle *h, void *stream);
 
+/* Per-kernel tracing. While enabled, every kernel the handle launches is
+ * bracketed by two CUDA events on its stream (no synchronisation). Reading
+ * synchronises on the recorded events, returns the summed milliseconds and
+ * launch counts per kernel class (arrays of XF_PROF_SLOTS) and resets them. */
+#define XF_PROF_SLOTS 8
+#define XF_PROF_PRIM 0   /* primitive recovery + transport (+ CFL reduction) */
+#define XF_PROF_DT 1     /* time-step finalisation */
+#define XF_PROF_GRAD 2   /* nodal velocity derivatives */
+#define XF_PROF_FACE_X 3 /* face fluxes, x (y = 4, z = 5) */
+#define XF_PROF_UPDATE 6 /* conservative difference + RK3 combination */
+xf_status xf_profile_enable(xf_handle *h, int on);
+xf_status xf_profile_read(xf_handle *h, double *ms, int64_t *launches);
+
+/* FP64 FMA throughput of the current device (eight independent fma chains
+ * per thread, `blocks_per_sm` blocks of 256 threads per SM, `iters` steps),
+ * in TFLOP/s counting an FMA as two flops. Synchronises the device. Used to
+ * state the measured FP64 ceiling beside the nominal one. */
+xf_status xf_probe_fp64(int64_t iters, int blocks_per_sm, double *tflops);
+
 const char *xf_status_str(xf_status s);
 const char *xf_last_error(void);
 

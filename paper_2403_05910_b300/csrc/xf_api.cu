@@ -3,6 +3,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "xf.h"
 #include "xf_device.cuh"
@@ -126,6 +127,11 @@ struct xf_handle {
   double* dt = nullptr;
   unsigned long long* red = nullptr;
   uint32_t* flags = nullptr;
+  // per-kernel event timing (xf_profile_enable / xf_profile_read)
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  struct Rec { int slot; cudaEvent_t a, b; };
+  std::vector<Rec> recs;
 };
 
 namespace {
@@ -216,16 +222,57 @@ xf_status fill_params(const xf_grid* g, const xf_thermo* th, const xf_opts* o, x
   return XF_OK;
 }
 
+cudaEvent_t pool_event(xf_handle* h) {
+  if (!h->ev_pool.empty()) {
+    cudaEvent_t e = h->ev_pool.back();
+    h->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Launch `fn` on stream s; with profiling on, bracket it by two events that
+// xf_profile_read later turns into a duration for `slot` (XF_PROF_*).
+template <class F>
+void timed(xf_handle* h, int slot, cudaStream_t s, F&& fn) {
+  if (!h->prof) {
+    fn();
+    return;
+  }
+  xf_handle::Rec r{slot, pool_event(h), pool_event(h)};
+  cudaEventRecord(r.a, s);
+  fn();
+  cudaEventRecord(r.b, s);
+  h->recs.push_back(r);
+}
+
 // Primitive recovery + (viscous) nodal gradients + every face flux of Uin.
 xf_status stage_fluxes(xf_handle* h, const double* Uin, int do_cfl, cudaStream_t s) {
   const xf::Params& p = h->p;
-  h->tab.prim(p, Uin, h->T[h->tcur], h->T[1 - h->tcur], h->Q, h->flags, h->red, do_cfl, s);
+  timed(h, XF_PROF_PRIM, s, [&] {
+    h->tab.prim(p, Uin, h->T[h->tcur], h->T[1 - h->tcur], h->Q, h->flags, h->red, do_cfl, s);
+  });
   h->tcur = 1 - h->tcur;
-  if (do_cfl) xf::k_dt_finalize<<<1, 1, 0, s>>>(p, h->red, h->dt, nullptr);
-  if (p.viscous) h->tab.grad(p, h->Q, s);
-  for (int d = 0; d < p.dim; ++d) h->tab.face[d](p, h->Q, h->G[d], h->flags, s);
+  if (do_cfl)
+    timed(h, XF_PROF_DT, s, [&] { xf::k_dt_finalize<<<1, 1, 0, s>>>(p, h->red, h->dt, nullptr); });
+  if (p.viscous) timed(h, XF_PROF_GRAD, s, [&] { h->tab.grad(p, h->Q, s); });
+  for (int d = 0; d < p.dim; ++d)
+    timed(h, XF_PROF_FACE_X + d, s, [&] { h->tab.face[d](p, h->Q, h->G[d], h->flags, s); });
   XF_CUDA(cudaGetLastError());
   return XF_OK;
+}
+
+__global__ void k_probe_fp64(double* out, long long iters, double a) {
+  double x0 = threadIdx.x * 1e-3, x1 = x0 + 1, x2 = x0 + 2, x3 = x0 + 3, x4 = x0 + 4,
+         x5 = x0 + 5, x6 = x0 + 6, x7 = x0 + 7;
+  for (long long i = 0; i < iters; ++i) {
+    x0 = fma(x0, a, -a); x1 = fma(x1, a, -a); x2 = fma(x2, a, -a); x3 = fma(x3, a, -a);
+    x4 = fma(x4, a, -a); x5 = fma(x5, a, -a); x6 = fma(x6, a, -a); x7 = fma(x7, a, -a);
+  }
+  const double r = ((x0 + x1) + (x2 + x3)) + ((x4 + x5) + (x6 + x7));
+  if (r == 12345.678) out[0] = r;  // keeps the chains live; never true in practice
 }
 
 }  // namespace
@@ -313,6 +360,8 @@ void xf_destroy(xf_handle* h) {
   cudaFree(h->dt);
   cudaFree(h->red);
   cudaFree(h->flags);
+  for (auto& r : h->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+  for (auto e : h->ev_pool) cudaEventDestroy(e);
   delete h;
 }
 
@@ -363,7 +412,9 @@ xf_status xf_rhs(xf_handle* h, const double* U, double* dUdt, void* stream) {
   xf_status st = stage_fluxes(h, U, 0, s);
   if (st != XF_OK) return st;
   const xf::Params& p = h->p;
-  h->tab.update(p, h->G[0], h->G[1], h->G[2], nullptr, nullptr, dUdt, h->dt, 0, s);
+  timed(h, XF_PROF_UPDATE, s, [&] {
+    h->tab.update(p, h->G[0], h->G[1], h->G[2], nullptr, nullptr, dUdt, h->dt, 0, s);
+  });
   XF_CUDA(cudaGetLastError());
   return XF_OK;
 }
@@ -388,13 +439,19 @@ xf_status xf_step_rk3(xf_handle* h, double dt, double* dt_dev_out, void* stream)
   // Eq. 16: three stages, U^n kept in U, stages in Us
   xf_status st = stage_fluxes(h, h->U, cfl ? 1 : 0, s);
   if (st != XF_OK) return st;
-  h->tab.update(p, h->G[0], h->G[1], h->G[2], h->U, h->U, h->Us, h->dt, 1, s);
+  timed(h, XF_PROF_UPDATE, s, [&] {
+    h->tab.update(p, h->G[0], h->G[1], h->G[2], h->U, h->U, h->Us, h->dt, 1, s);
+  });
   st = stage_fluxes(h, h->Us, 0, s);
   if (st != XF_OK) return st;
-  h->tab.update(p, h->G[0], h->G[1], h->G[2], h->U, h->Us, h->Us, h->dt, 2, s);
+  timed(h, XF_PROF_UPDATE, s, [&] {
+    h->tab.update(p, h->G[0], h->G[1], h->G[2], h->U, h->Us, h->Us, h->dt, 2, s);
+  });
   st = stage_fluxes(h, h->Us, 0, s);
   if (st != XF_OK) return st;
-  h->tab.update(p, h->G[0], h->G[1], h->G[2], h->U, h->Us, h->U, h->dt, 3, s);
+  timed(h, XF_PROF_UPDATE, s, [&] {
+    h->tab.update(p, h->G[0], h->G[1], h->G[2], h->U, h->Us, h->U, h->dt, 3, s);
+  });
   XF_CUDA(cudaGetLastError());
   if (dt_dev_out)
     XF_CUDA(cudaMemcpyAsync(dt_dev_out, h->dt, sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -417,6 +474,65 @@ xf_status xf_get_status(xf_handle* h, uint32_t* flags, void* stream) {
 xf_status xf_clear_status(xf_handle* h, void* stream) {
   if (!h) return XF_ERR_ARG;
   XF_CUDA(cudaMemsetAsync(h->flags, 0, sizeof(uint32_t), (cudaStream_t)stream));
+  return XF_OK;
+}
+
+xf_status xf_profile_enable(xf_handle* h, int on) {
+  if (!h) return XF_ERR_ARG;
+  h->prof = on != 0;
+  return XF_OK;
+}
+
+xf_status xf_profile_read(xf_handle* h, double* ms, int64_t* launches) {
+  if (!h || !ms || !launches) return XF_ERR_ARG;
+  for (int k = 0; k < XF_PROF_SLOTS; ++k) { ms[k] = 0.0; launches[k] = 0; }
+  xf_status st = XF_OK;
+  for (auto& r : h->recs) {
+    float t = 0.f;
+    cudaError_t e = cudaEventSynchronize(r.b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, r.a, r.b);
+    if (e != cudaSuccess) {
+      set_err("xf_profile_read", e);
+      st = XF_ERR_CUDA;
+    } else {
+      ms[r.slot] += t;
+      launches[r.slot] += 1;
+    }
+    h->ev_pool.push_back(r.a);
+    h->ev_pool.push_back(r.b);
+  }
+  h->recs.clear();
+  return st;
+}
+
+xf_status xf_probe_fp64(int64_t iters, int blocks_per_sm, double* tflops) {
+  if (iters < 1 || blocks_per_sm < 1 || !tflops) return XF_ERR_ARG;
+  int dev = 0, sms = 0;
+  XF_CUDA(cudaGetDevice(&dev));
+  XF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  double* out = nullptr;
+  XF_CUDA(cudaMalloc(&out, sizeof(double)));
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  const int threads = 256;
+  const long long nb = (long long)sms * blocks_per_sm;
+  k_probe_fp64<<<(unsigned)nb, threads>>>(out, iters / 10 + 1, 1.0 - 1e-9);  // warm-up
+  cudaEventRecord(a);
+  k_probe_fp64<<<(unsigned)nb, threads>>>(out, iters, 1.0 - 1e-9);
+  cudaEventRecord(b);
+  cudaError_t e = cudaEventSynchronize(b);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFree(out);
+  if (e != cudaSuccess) {
+    set_err("xf_probe_fp64", e);
+    return XF_ERR_CUDA;
+  }
+  const double flops = 2.0 * 8.0 * (double)iters * (double)(nb * threads);
+  *tflops = flops / (ms * 1e-3) / 1e12;
   return XF_OK;
 }
 

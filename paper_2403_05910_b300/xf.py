@@ -43,7 +43,10 @@ class Opts(C.Structure):
 # every symbol declared in include/xf.h
 EXPORTS = ["xf_create", "xf_destroy", "xf_nv", "xf_cells", "xf_set_state", "xf_set_primitive",
            "xf_get_state", "xf_rhs", "xf_compute_dt", "xf_step_rk3", "xf_get_status",
-           "xf_clear_status", "xf_status_str", "xf_last_error"]
+           "xf_clear_status", "xf_status_str", "xf_last_error", "xf_profile_enable",
+           "xf_profile_read", "xf_probe_fp64"]
+PROF_SLOTS = 8
+PROF_NAMES = ["prim", "dt", "grad", "face_x", "face_y", "face_z", "update", "spare"]
 
 
 def _load():
@@ -68,6 +71,9 @@ def _load():
     L.xf_status_str.argtypes = [C.c_int]
     L.xf_status_str.restype = C.c_char_p
     L.xf_last_error.restype = C.c_char_p
+    L.xf_profile_enable.argtypes = [vp, C.c_int]
+    L.xf_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+    L.xf_probe_fp64.argtypes = [C.c_int64, C.c_int, C.POINTER(C.c_double)]
     return L
 
 
@@ -196,3 +202,20 @@ class Solver:
 
     def clear_status(self, stream=None):
         check(lib.xf_clear_status(self.h, stream_ptr(stream)), "xf_clear_status")
+
+    def profile(self, on=True):
+        check(lib.xf_profile_enable(self.h, int(on)), "xf_profile_enable")
+
+    def profile_read(self):
+        """{kernel class: (total ms, launches)} since the last read."""
+        ms = (C.c_double * PROF_SLOTS)()
+        n = (C.c_int64 * PROF_SLOTS)()
+        check(lib.xf_profile_read(self.h, ms, n), "xf_profile_read")
+        return {PROF_NAMES[k]: (ms[k], n[k]) for k in range(PROF_SLOTS) if n[k]}
+
+
+def probe_fp64(iters=20000, blocks_per_sm=8):
+    """Measured FP64 FMA throughput (TFLOP/s) of the current device."""
+    t = C.c_double(0.0)
+    check(lib.xf_probe_fp64(int(iters), int(blocks_per_sm), C.byref(t)), "xf_probe_fp64")
+    return t.value
