@@ -1,0 +1,69 @@
+"""Algorithmic FP64 operation counts of one RHS stage (roofline numerators).
+
+Counted from the operations the method needs as the kernels evaluate them:
+an add, multiply, divide, square root, exp or log counts 1, a fused
+multiply-add counts 2 (the convention of the FP64 peak). Library expansions
+of divide / sqrt / exp / log into several FP64 instructions are NOT counted,
+so achieved rates computed from these numbers are lower bounds on the FP64
+pipe's occupancy. d = dimension, N = species count, n_v = d + N + 1.
+"""
+
+WENO5 = 68          # one WENO5-JS reconstruction (smoothness, weights, candidates)
+NEWTON_ITER = 35    # one Newton temperature iteration on mixture coefficients
+NEWTON_ITERS = 3    # nominal iterations per cell with the warm start
+
+
+def face_convective(d: int, N: int) -> int:
+    """Roe state + PER projection + LLF + 2 WENO5 per field + back-projection."""
+    nv = d + N + 1
+    return 218 + 71 * d + 103 * N + 2 * WENO5 * nv
+
+
+def face_viscous(d: int, N: int) -> int:
+    """4th-order face values / derivatives, stress, heat and diffusion fluxes."""
+    return 41 + 11 * d + 5 * d * d + 38 * N
+
+
+def face(d: int, N: int, viscous: bool) -> int:
+    return face_convective(d, N) + (face_viscous(d, N) if viscous else 0)
+
+
+def prim_cell(d: int, N: int, viscous: bool) -> int:
+    """Primitive recovery (Newton, EOS, sound speed) + mixture transport."""
+    base = 21 + 24 * N + NEWTON_ITERS * NEWTON_ITER + 24
+    return base + ((7 + 31 * N + 13 * N * N) if viscous else 0)
+
+
+def grad_cell(d: int, viscous: bool) -> int:
+    return 5 * d * d if viscous else 0
+
+
+def update_cell(d: int, N: int) -> int:
+    nv = d + N + 1
+    return nv * (3 * d + 3)
+
+
+def per_cell_stage(case) -> dict:
+    """Flops of one stage over the whole grid, split by kernel class."""
+    d, N, vis = case.dim, case.n_species, bool(case.viscous)
+    n = case.n
+    cells = case.cells
+    pcells = 1
+    for a in range(3):
+        pcells *= (n[a] + 6) if a < d else 1
+    nfaces = [((n[0] + (a == 0)) * (n[1] + (a == 1)) * (n[2] + (a == 2))) for a in range(d)]
+    out = {
+        "prim": prim_cell(d, N, vis) * pcells,
+        "grad": grad_cell(d, vis) * pcells,
+        "face": face(d, N, vis) * sum(nfaces),
+        "update": update_cell(d, N) * cells,
+    }
+    out["total"] = sum(out.values())
+    return out
+
+
+def hbm_bytes_per_cell_stage(case, stage: int) -> int:
+    """Minimal traffic of one stage: read U^(s), read U^n (stages 2, 3), write
+    U^(s+1), read + write T (the Newton warm start)."""
+    nv = case.n_v
+    return 8 * (nv + (nv if stage > 0 else 0) + nv + 2)
