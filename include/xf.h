@@ -175,6 +175,38 @@ xf_status xf_profile_read(xf_handle *h, double *ms, int64_t *launches);
  * state the measured FP64 ceiling beside the nominal one. */
 xf_status xf_probe_fp64(int64_t iters, int blocks_per_sm, double *tflops);
 
+/* Allocation-free RHS. The paper has no counterpart: this entry point exists
+ * for callers that may not allocate device memory -- for example a host that
+ * hands all device memory to its own pool or caching allocator and forbids
+ * other cudaMalloc calls, or a latency-critical loop where an allocation would
+ * synchronise the device. It computes dUdt = L(U) exactly like xf_rhs, but
+ * without a handle: its scratch (padded per-cell fields, face fluxes,
+ * temperature warm start, status word) is one fixed array in the library's
+ * device memory, xf_rhs_static_capacity_bytes() bytes (32 MiB) per GPU, held
+ * by every GPU that loads the library until the process exits. It calls no
+ * cudaMalloc, cudaFree or other allocating routine.
+ *   grid, thermo, opts: as for xf_create (host structs).
+ *   U [n_v][cells], dUdt [n_v][cells]: device arrays owned by the caller.
+ *   T_guess [cells]: device array seeding the Newton warm start (nullable:
+ *     300 K); it is read, not updated.
+ *   flags_out: host pointer (nullable). When given, the call synchronises
+ *     `stream` and stores the device status bits (XF_FLAG_*) of this call.
+ * Returns XF_ERR_ARG, with the required and available sizes in
+ * xf_last_error(), when the grid's scratch exceeds the capacity (about
+ * 4.5e4 cells in 3D with 5 species, 1e5 cells in 2D with 3 species), or for
+ * non-device U / dUdt / T_guess.
+ * The first call on each device looks up the array's device address (with
+ * that device current) and caches it; make that first call before any stream
+ * capture. Every call on a device shares the one array and leaves its contents
+ * behind (the status word and accumulators are cleared at the start of each
+ * call): calls that overlap on the GPU -- on different streams or from
+ * different threads -- race and must not be issued. */
+xf_status xf_rhs_static(const xf_grid *grid, const xf_thermo *thermo,
+                        const xf_opts *opts, const double *U,
+                        const double *T_guess, double *dUdt,
+                        uint32_t *flags_out, void *stream);
+int64_t xf_rhs_static_capacity_bytes(void);
+
 const char *xf_status_str(xf_status s);
 const char *xf_last_error(void);
 

@@ -2,6 +2,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -533,6 +534,114 @@ xf_status xf_probe_fp64(int64_t iters, int blocks_per_sm, double* tflops) {
   }
   const double flops = 2.0 * 8.0 * (double)iters * (double)(nb * threads);
   *tflops = flops / (ms * 1e-3) / 1e12;
+  return XF_OK;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// Allocation-free right-hand side (xf_rhs_static). Scratch for the padded
+// per-cell fields, the face fluxes, the temperature warm start and the status
+// word lives in one file-scope device array of fixed size instead of memory
+// obtained from cudaMalloc. Host code never uses the array's name as a device
+// address: each device's address comes from cudaGetSymbolAddress, looked up on
+// that device's first call and cached.
+namespace {
+
+constexpr size_t kStaticScratchDoubles = size_t(4) << 20;  // 32 MiB per device
+static __device__ __align__(256) double xf_static_scratch[kStaticScratchDoubles];
+
+constexpr int kStaticMaxDevices = 64;
+std::mutex g_static_mu;
+double* g_static_ptr[kStaticMaxDevices] = {nullptr};
+
+// Device address of the scratch array on the current device (set-up on first use).
+xf_status static_scratch(double** out) {
+  int dev = 0;
+  XF_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kStaticMaxDevices) {
+    g_err = "xf_rhs_static: device ordinal beyond the supported range";
+    return XF_ERR_ARG;
+  }
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void* ptr = nullptr;
+    XF_CUDA(cudaGetSymbolAddress(&ptr, xf_static_scratch));
+    g_static_ptr[dev] = static_cast<double*>(ptr);
+  }
+  *out = g_static_ptr[dev];
+  return XF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t xf_rhs_static_capacity_bytes(void) {
+  return (int64_t)(kStaticScratchDoubles * sizeof(double));
+}
+
+xf_status xf_rhs_static(const xf_grid* grid, const xf_thermo* thermo, const xf_opts* opts,
+                        const double* U, const double* T_guess, double* dUdt,
+                        uint32_t* flags_out, void* stream) {
+  if (!U || !dUdt) return XF_ERR_ARG;
+  xf::Params p;
+  xf_status st = fill_params(grid, thermo, opts, &p);
+  if (st != XF_OK) return st;
+  Table tab;
+  if (!pick(p.dim, p.N, &tab)) return XF_ERR_ARG;
+  if (!is_device_ptr(U) || !is_device_ptr(dUdt) || (T_guess && !is_device_ptr(T_guess)))
+    return XF_ERR_ARG;
+  // scratch plan (in doubles): Q | G_x | G_y | G_z | T_in | T_out | dt | red[2] | flags
+  long long nf[3] = {0, 0, 0};
+  size_t need = (size_t)tab.nq * p.pcells;
+  for (int d = 0; d < p.dim; ++d) {
+    nf[d] = (long long)(p.n[0] + (d == 0)) * (p.n[1] + (d == 1)) * (p.n[2] + (d == 2));
+    need += (size_t)p.nv * nf[d];
+  }
+  need += 2 * (size_t)p.cells + 1 + 2 + 1;
+  if (need > kStaticScratchDoubles) {
+    char buf[256];
+    snprintf(buf, sizeof buf,
+             "xf_rhs_static: this grid needs %zu bytes of scratch; the static scratch holds "
+             "%zu bytes",
+             need * sizeof(double), kStaticScratchDoubles * sizeof(double));
+    g_err = buf;
+    return XF_ERR_ARG;
+  }
+  double* base = nullptr;
+  st = static_scratch(&base);
+  if (st != XF_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  double* Q = base;
+  double* cur = Q + (size_t)tab.nq * p.pcells;
+  double* G[3] = {nullptr, nullptr, nullptr};
+  for (int d = 0; d < p.dim; ++d) {
+    G[d] = cur;
+    cur += (size_t)p.nv * nf[d];
+  }
+  double* Tin = cur;
+  double* Tout = Tin + p.cells;
+  double* dt = Tout + p.cells;
+  unsigned long long* red = reinterpret_cast<unsigned long long*>(dt + 1);
+  uint32_t* flags = reinterpret_cast<uint32_t*>(dt + 3);
+  // the array keeps the previous call's contents: zero the accumulators
+  XF_CUDA(cudaMemsetAsync(red, 0, 2 * sizeof(unsigned long long), s));
+  XF_CUDA(cudaMemsetAsync(flags, 0, sizeof(uint32_t), s));
+  if (T_guess) {
+    XF_CUDA(cudaMemcpyAsync(Tin, T_guess, sizeof(double) * p.cells, cudaMemcpyDeviceToDevice, s));
+  } else {
+    k_fill<<<blocks(p.cells, 256), 256, 0, s>>>(Tin, p.cells, 300.0);
+  }
+  tab.prim(p, U, Tin, Tout, Q, flags, red, 0, s);
+  if (p.viscous) tab.grad(p, Q, s);
+  for (int d = 0; d < p.dim; ++d) tab.face[d](p, Q, G[d], flags, s);
+  tab.update(p, G[0], G[1], G[2], nullptr, nullptr, dUdt, dt, 0, s);
+  XF_CUDA(cudaGetLastError());
+  if (flags_out) {
+    XF_CUDA(cudaMemcpyAsync(flags_out, flags, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    XF_CUDA(cudaStreamSynchronize(s));
+  }
   return XF_OK;
 }
 

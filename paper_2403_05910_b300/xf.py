@@ -44,7 +44,7 @@ class Opts(C.Structure):
 EXPORTS = ["xf_create", "xf_destroy", "xf_nv", "xf_cells", "xf_set_state", "xf_set_primitive",
            "xf_get_state", "xf_rhs", "xf_compute_dt", "xf_step_rk3", "xf_get_status",
            "xf_clear_status", "xf_status_str", "xf_last_error", "xf_profile_enable",
-           "xf_profile_read", "xf_probe_fp64"]
+           "xf_profile_read", "xf_probe_fp64", "xf_rhs_static", "xf_rhs_static_capacity_bytes"]
 PROF_SLOTS = 8
 PROF_NAMES = ["prim", "dt", "grad", "face_x", "face_y", "face_z", "update", "spare"]
 
@@ -74,6 +74,9 @@ def _load():
     L.xf_profile_enable.argtypes = [vp, C.c_int]
     L.xf_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
     L.xf_probe_fp64.argtypes = [C.c_int64, C.c_int, C.POINTER(C.c_double)]
+    L.xf_rhs_static.argtypes = [C.POINTER(Grid), C.POINTER(Thermo), C.POINTER(Opts), vp, vp, vp,
+                                C.POINTER(C.c_uint32), vp]
+    L.xf_rhs_static_capacity_bytes.restype = C.c_int64
     return L
 
 
@@ -219,3 +222,18 @@ def probe_fp64(iters=20000, blocks_per_sm=8):
     t = C.c_double(0.0)
     check(lib.xf_probe_fp64(int(iters), int(blocks_per_sm), C.byref(t)), "xf_probe_fp64")
     return t.value
+
+
+def rhs_static(case, U, dUdt, T=None, flags=True, stream=None, **kw):
+    """dUdt = L(U) through the allocation-free entry point (no handle, no
+    device allocation; scratch is the library's fixed device array). Returns
+    the status bits when ``flags`` is true (that synchronises the stream)."""
+    g, t, o, keep = structs(case, **kw)
+    f = C.c_uint32(0)
+    check(lib.xf_rhs_static(C.byref(g), C.byref(t), C.byref(o), ptr(U), ptr(T), ptr(dUdt),
+                            C.byref(f) if flags else None, stream_ptr(stream)), "xf_rhs_static")
+    return f.value if flags else None
+
+
+def rhs_static_capacity_bytes():
+    return int(lib.xf_rhs_static_capacity_bytes())
