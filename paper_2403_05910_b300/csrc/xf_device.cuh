@@ -13,7 +13,7 @@
 //    the multicomponent eigensystem in the partial form of Sec. III.D.3 (per
 //    field only its eigenvalue, its left row and its right column, all in
 //    closed sparse form), LLF splitting (Eq. 14), two WENO5-JS reconstructions
-//    per field with a single division each, back-projection (Eq. 15), and the
+//    per field normalised by one division per field, back-projection (Eq. 15), and the
 //    viscous face flux. Writes G = F_hat - F_v per face.
 //  * k_update: conservative difference (Eq. 13) and the SSP-RK3 combination
 //    (Eq. 16), or the plain RHS.
@@ -347,35 +347,49 @@ k_grad(const __grid_constant__ Params p, double* __restrict__ Q) {
 }
 
 // ================================================================= WENO5 ===
-// WENO5-JS at i+1/2 from f0..f4 = f_{i-2..i+2}. The nonlinear weights
-// d_k/(eps+b_k)^2 are scaled by prod_j (eps+b_j)^2 so that one division
-// normalises them.
-__device__ __forceinline__ double weno5(double f0, double f1, double f2, double f3, double f4,
-                                        double eps) {
-  const double t0 = fma(-2.0, f1, f0) + f2;
-  const double u0 = fma(-4.0, f1, f0) + 3.0 * f2;
-  const double t1 = fma(-2.0, f2, f1) + f3;
-  const double u1 = f1 - f3;
-  const double t2 = fma(-2.0, f3, f2) + f4;
-  const double u2 = fma(-4.0, f3, 3.0 * f2) + f4;
-  const double k13 = 13.0 / 12.0;
-  const double s0 = eps + fma(k13 * t0, t0, 0.25 * u0 * u0);
-  const double s1 = eps + fma(k13 * t1, t1, 0.25 * u1 * u1);
-  const double s2 = eps + fma(k13 * t2, t2, 0.25 * u2 * u2);
+// WENO5-JS at i+1/2 from f0..f4 = f_{i-2..i+2}, returned as F = f2 + num/den.
+// Written on first differences a..d: the smoothness indicators are scaled by
+// 12 (12 b_k = 13 t_k^2 + 3 u_k^2, with 12 eps) -- a common factor that leaves
+// the weights unchanged -- and the nonlinear weights d_k/(eps + b_k)^2 are
+// scaled by prod_j (eps + b_j)^2, so no division is needed until the end.
+// The candidates enter as q_k - f2.
+__device__ __forceinline__ void weno5_nd(double f0, double f1, double f2, double f3, double f4,
+                                         double eps12, double& num, double& den) {
+  const double a = f1 - f0, b = f2 - f1, c = f3 - f2, d = f4 - f3;
+  const double t0 = b - a, u0 = fma(3.0, b, -a);
+  const double t1 = c - b, u1 = b + c;
+  const double t2 = d - c, u2 = fma(-3.0, c, d);
+  const double s0 = fma(13.0 * t0, t0, fma(3.0 * u0, u0, eps12));
+  const double s1 = fma(13.0 * t1, t1, fma(3.0 * u1, u1, eps12));
+  const double s2 = fma(13.0 * t2, t2, fma(3.0 * u2, u2, eps12));
   const double p12 = s1 * s2, p02 = s0 * s2, p01 = s0 * s1;
-  const double a0 = 0.1 * p12 * p12;
-  const double a1 = 0.6 * p02 * p02;
-  const double a2 = 0.3 * p01 * p01;
-  const double q0 = fma(11.0 / 6.0, f2, fma(-7.0 / 6.0, f1, (1.0 / 3.0) * f0));
-  const double q1 = fma(1.0 / 3.0, f3, fma(5.0 / 6.0, f2, (-1.0 / 6.0) * f1));
-  const double q2 = fma(-1.0 / 6.0, f4, fma(5.0 / 6.0, f3, (1.0 / 3.0) * f2));
-  return fma(a0, q0, fma(a1, q1, a2 * q2)) / (a0 + a1 + a2);
+  const double w0 = (0.1 * p12) * p12;
+  const double w1 = (0.6 * p02) * p02;
+  const double w2 = (0.3 * p01) * p01;
+  const double q0 = fma(5.0 / 6.0, b, (-1.0 / 3.0) * a);   // q_0 - f2
+  const double q1 = fma(1.0 / 3.0, c, (1.0 / 6.0) * b);    // q_1 - f2
+  const double q2 = fma(2.0 / 3.0, c, (-1.0 / 6.0) * d);   // q_2 - f2
+  num = fma(w0, q0, fma(w1, q1, w2 * q2));
+  den = (w0 + w1) + w2;
+}
+
+// F^+ + F^- of one characteristic field (Eq. 15): the upwind reconstruction
+// of w^+ from i-2..i+2 and the mirrored one of w^- from i+3..i-1, normalised
+// by a single division.
+__device__ __forceinline__ double weno5_pair(const double* wp, const double* wm, double eps12) {
+  double np, dp, nm, dm;
+  weno5_nd(wp[0], wp[1], wp[2], wp[3], wp[4], eps12, np, dp);
+  weno5_nd(wm[5], wm[4], wm[3], wm[2], wm[1], eps12, nm, dm);
+  return (wp[2] + wm[3]) + fma(np, dm, nm * dp) / (dp * dm);
 }
 
 // ================================================================= k_face ===
 // One thread per face of direction D (faces i = 0..n_D, left cell i-1).
+#ifndef XF_FACE_MIN_BLOCKS
+#define XF_FACE_MIN_BLOCKS 2
+#endif
 template <int DIM, int NS, int D>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, XF_FACE_MIN_BLOCKS)
 k_face(const __grid_constant__ Params p, const double* __restrict__ Q,
        double* __restrict__ Gf, uint32_t* __restrict__ flags) {
   using L = Lay<DIM, NS>;
@@ -445,78 +459,86 @@ k_face(const __grid_constant__ Params p, const double* __restrict__ Q,
     const double hic2 = 0.5 * ic2;
     const double iGam = cvb / Rb;
     const double un = ub[D];
-    // ---- stencil m = i-2..i+3 (offsets -2..3 from the left cell): rho, u_n,
-    //      p, g.U and the LLF maxima of |u-c|, |u+c|, |u|
-    double rho_m[6], un_m[6], p_m[6], gU[6];
-    double am = 0.0, ap = 0.0, a0 = 0.0;
+    // ---- stencil m = i-2..i+3 (offsets -2..3 from the left cell). Per cell:
+    //      rho, p, u_n/2, g.U/(2c^2) and the LLF maxima of |u-c|, |u+c|, |u|.
+    //      The 1/2 of Eq. 14 and the 1/(2c^2) of the acoustic rows are folded
+    //      into per-face coefficients.
     const double phiN = phi[NS - 1];
+    double gm[DIM], dphi[NS > 1 ? NS - 1 : 1], gs[NS > 1 ? NS - 1 : 1];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) gm[a] = -Gam * ub[a] * hic2;
+#pragma unroll
+    for (int s = 0; s < NS - 1; ++s) { dphi[s] = phi[s] - phiN; gs[s] = dphi[s] * hic2; }
+    const double gr = phiN * hic2, gE = Gam * hic2;
+    double rho_m[6], p_m[6], hun[6], gUh[6];
+    double am = 0.0, ap = 0.0, a0 = 0.0;
 #pragma unroll
     for (int m = 0; m < 6; ++m) {
       const int o = m - 2;
       rho_m[m] = QF(L::U, o);
-      un_m[m] = QF(L::UN + D, o);
+      const double unm = QF(L::UN + D, o);
       p_m[m] = QF(L::P, o);
       const double cm = QF(L::C, o);
-      am = pmax(am, fabs(un_m[m] - cm));
-      ap = pmax(ap, fabs(un_m[m] + cm));
-      a0 = pmax(a0, fabs(un_m[m]));
-      double g = phiN * rho_m[m];
+      am = pmax(am, fabs(unm - cm));
+      ap = pmax(ap, fabs(unm + cm));
+      a0 = pmax(a0, fabs(unm));
+      hun[m] = 0.5 * unm;
+      double g = gr * rho_m[m];
 #pragma unroll
-      for (int a = 0; a < DIM; ++a) g = fma(-Gam * ub[a], QF(L::U + 1 + a, o), g);
-      g = fma(Gam, QF(L::U + IE, o), g);
+      for (int a = 0; a < DIM; ++a) g = fma(gm[a], QF(L::U + 1 + a, o), g);
+      g = fma(gE, QF(L::U + IE, o), g);
 #pragma unroll
-      for (int s = 0; s < NS - 1; ++s) g = fma(phi[s] - phiN, QF(L::U + IE + 1 + s, o), g);
-      gU[m] = g;
+      for (int s = 0; s < NS - 1; ++s) g = fma(gs[s], QF(L::U + IE + 1 + s, o), g);
+      gUh[m] = g;
     }
-    const double eps = p.weno_eps;
-    // ---- PER: one characteristic field at a time; l.F_m = u_m (l.U_m) +
-    //      p_m (l[m_n] + u_m l[E]) for the sparse rows below
+    const double eps12 = 12.0 * p.weno_eps;
+    const double chc = c * hic2;
+    // ---- PER: one characteristic field at a time. With w = (1/2)(l.F_m +- a l.U_m)
+    //      and l.F_m = u_m (l.U_m) + p_m (l[m_n] + u_m l[E]):
+    //      w^+- = (u_m/2 +- a/2) l.U_m + p_m (l[m_n]/2 + (u_m/2) l[E]).
     double Fk_m, Fk_p, Fk_e;
     {
       double wp[6], wm[6];
-      // u - c: l = (g - c (-u_n e_rho + e_mn)) / (2 c^2)
+      // u - c: l.U = (g.U - c (m_n - u_n rho)) / (2c^2)
       {
-        const double lmn = (-Gam * un - c) * hic2, lE = Gam * hic2;
+        const double hlmn = 0.5 * (-Gam * un - c) * hic2, lE = Gam * hic2;
         const double ha = 0.5 * am;
 #pragma unroll
         for (int m = 0; m < 6; ++m) {
           const double nU = fma(-un, rho_m[m], QF(L::U + 1 + D, m - 2));
-          const double LU = fma(-c, nU, gU[m]) * hic2;
-          const double LF = fma(un_m[m], LU, p_m[m] * fma(un_m[m], lE, lmn));
-          wp[m] = fma(ha, LU, 0.5 * LF);
-          wm[m] = fma(-ha, LU, 0.5 * LF);
+          const double LU = fma(-chc, nU, gUh[m]);
+          const double pq = p_m[m] * fma(hun[m], lE, hlmn);
+          wp[m] = fma(hun[m] + ha, LU, pq);
+          wm[m] = fma(hun[m] - ha, LU, pq);
         }
-        Fk_m = weno5(wp[0], wp[1], wp[2], wp[3], wp[4], eps) +
-               weno5(wm[5], wm[4], wm[3], wm[2], wm[1], eps);
+        Fk_m = weno5_pair(wp, wm, eps12);
       }
       // u + c
       {
-        const double lmn = (-Gam * un + c) * hic2, lE = Gam * hic2;
+        const double hlmn = 0.5 * (-Gam * un + c) * hic2, lE = Gam * hic2;
         const double ha = 0.5 * ap;
 #pragma unroll
         for (int m = 0; m < 6; ++m) {
           const double nU = fma(-un, rho_m[m], QF(L::U + 1 + D, m - 2));
-          const double LU = fma(c, nU, gU[m]) * hic2;
-          const double LF = fma(un_m[m], LU, p_m[m] * fma(un_m[m], lE, lmn));
-          wp[m] = fma(ha, LU, 0.5 * LF);
-          wm[m] = fma(-ha, LU, 0.5 * LF);
+          const double LU = fma(chc, nU, gUh[m]);
+          const double pq = p_m[m] * fma(hun[m], lE, hlmn);
+          wp[m] = fma(hun[m] + ha, LU, pq);
+          wm[m] = fma(hun[m] - ha, LU, pq);
         }
-        Fk_p = weno5(wp[0], wp[1], wp[2], wp[3], wp[4], eps) +
-               weno5(wm[5], wm[4], wm[3], wm[2], wm[1], eps);
+        Fk_p = weno5_pair(wp, wm, eps12);
       }
       // entropy: l = e_rho - g / c^2
       {
-        const double lmn = Gam * un * ic2, lE = -Gam * ic2;
+        const double hlmn = 0.5 * Gam * un * ic2, lE = -Gam * ic2;
         const double ha = 0.5 * a0;
 #pragma unroll
         for (int m = 0; m < 6; ++m) {
-          const double LU = fma(-gU[m], ic2, rho_m[m]);
-          const double LF = fma(un_m[m], LU, p_m[m] * fma(un_m[m], lE, lmn));
-          wp[m] = fma(ha, LU, 0.5 * LF);
-          wm[m] = fma(-ha, LU, 0.5 * LF);
+          const double LU = fma(-2.0, gUh[m], rho_m[m]);
+          const double pq = p_m[m] * fma(hun[m], lE, hlmn);
+          wp[m] = fma(hun[m] + ha, LU, pq);
+          wm[m] = fma(hun[m] - ha, LU, pq);
         }
-        Fk_e = weno5(wp[0], wp[1], wp[2], wp[3], wp[4], eps) +
-               weno5(wm[5], wm[4], wm[3], wm[2], wm[1], eps);
+        Fk_e = weno5_pair(wp, wm, eps12);
       }
     }
     // back-projection of the three dense right columns (Eq. 15)
@@ -531,7 +553,11 @@ k_face(const __grid_constant__ Params p, const double* __restrict__ Q,
 #pragma unroll
       for (int s = 0; s < NS - 1; ++s) Gout[IE + 1 + s] = Yb[s] * S;
     }
+    // the remaining fields all have eigenvalue u and no pressure term
     const double ha0 = 0.5 * a0;
+    double hp0[6], hm0[6];
+#pragma unroll
+    for (int m = 0; m < 6; ++m) { hp0[m] = hun[m] + ha0; hm0[m] = hun[m] - ha0; }
     // tangential momenta: l = (-u_t, e_{m_t}), r = e_{m_t} + u_t e_E
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
@@ -540,12 +566,10 @@ k_face(const __grid_constant__ Params p, const double* __restrict__ Q,
 #pragma unroll
       for (int m = 0; m < 6; ++m) {
         const double LU = fma(-ub[a], rho_m[m], QF(L::U + 1 + a, m - 2));
-        const double LF = un_m[m] * LU;
-        wp[m] = fma(ha0, LU, 0.5 * LF);
-        wm[m] = fma(-ha0, LU, 0.5 * LF);
+        wp[m] = hp0[m] * LU;
+        wm[m] = hm0[m] * LU;
       }
-      const double Fk = weno5(wp[0], wp[1], wp[2], wp[3], wp[4], eps) +
-                        weno5(wm[5], wm[4], wm[3], wm[2], wm[1], eps);
+      const double Fk = weno5_pair(wp, wm, eps12);
       Gout[1 + a] += Fk;
       Gout[IE] = fma(ub[a], Fk, Gout[IE]);
     }
@@ -556,14 +580,12 @@ k_face(const __grid_constant__ Params p, const double* __restrict__ Q,
 #pragma unroll
       for (int m = 0; m < 6; ++m) {
         const double LU = fma(-Yb[s], rho_m[m], QF(L::U + IE + 1 + s, m - 2));
-        const double LF = un_m[m] * LU;
-        wp[m] = fma(ha0, LU, 0.5 * LF);
-        wm[m] = fma(-ha0, LU, 0.5 * LF);
+        wp[m] = hp0[m] * LU;
+        wm[m] = hm0[m] * LU;
       }
-      const double Fk = weno5(wp[0], wp[1], wp[2], wp[3], wp[4], eps) +
-                        weno5(wm[5], wm[4], wm[3], wm[2], wm[1], eps);
+      const double Fk = weno5_pair(wp, wm, eps12);
       Gout[IE + 1 + s] += Fk;
-      Gout[IE] = fma(-(phi[s] - phiN) * iGam, Fk, Gout[IE]);
+      Gout[IE] = fma(-dphi[s] * iGam, Fk, Gout[IE]);
     }
   }
 
