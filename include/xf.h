@@ -175,6 +175,54 @@ xf_status xf_profile_read(xf_handle *h, double *ms, int64_t *launches);
  * state the measured FP64 ceiling beside the nominal one. */
 xf_status xf_probe_fp64(int64_t iters, int blocks_per_sm, double *tflops);
 
+/* ---- Batched form: many independent 2D instances (uneven grids, N = 2..5)
+ * advanced together. Each RK stage is ONE persistent cooperative kernel that
+ * runs every phase of the stage (primitive recovery with per-instance CFL
+ * reduction, per-instance dt, nodal gradients, x and y face fluxes, update)
+ * for all instances, with a grid barrier between phases; a step is replayed
+ * from a CUDA graph (captured per temperature-buffer parity and dt). Every cell
+ * and face uses the same device code as xf_step_rk3, so each instance's result
+ * is bitwise identical to a single-grid handle stepped alone.
+ * The grid barrier is bounded: a block that waits past its limit sets
+ * XF_FLAG_TIMEOUT in the batch status and the kernel still finishes. */
+typedef struct xf_batch xf_batch;
+/* grids/thermos/opts: arrays of n (host); every grid must be 2D. */
+xf_status xf_batch_create(int n, const xf_grid *grids, const xf_thermo *thermos,
+                          const xf_opts *opts, xf_batch **out);
+void xf_batch_destroy(xf_batch *b);
+int xf_batch_size(const xf_batch *b);
+/* 1 while steps replay from a CUDA graph; 0 if capture was unavailable and
+ * steps are launched directly (same kernels, same results). */
+int xf_batch_uses_graph(const xf_batch *b);
+/* per instance i: like xf_set_primitive / xf_set_state / xf_get_state */
+xf_status xf_batch_set_primitive(xf_batch *b, int i, const double *P, void *stream);
+xf_status xf_batch_set_state(xf_batch *b, int i, const double *U,
+                             const double *T_guess, void *stream);
+xf_status xf_batch_get_state(xf_batch *b, int i, double *U, double *T, void *stream);
+/* One SSP-RK3 step of every instance: dt > 0 for all, dt <= 0 each its own
+ * CFL step. No host synchronisation. */
+xf_status xf_batch_step_rk3(xf_batch *b, double dt, void *stream);
+/* Autotuner: times `steps` CFL steps for every candidate launch shape (block
+ * size 128/256, face tiles from 256x1 to 8x32 faces), keeps the fastest and
+ * returns its index; ms_out (nullable, xf_batch_num_candidates() entries)
+ * receives each candidate's ms per step. Restores every instance's state
+ * afterwards; synchronises. */
+xf_status xf_batch_autotune(xf_batch *b, int steps, int *choice, float *ms_out,
+                            void *stream);
+int xf_batch_num_candidates(void);
+/* Select candidate `choice` (< 0: keep the current one) and report its shape. */
+xf_status xf_batch_config(xf_batch *b, int choice, int *block_threads,
+                          int *tile_w, int *tile_h);
+/* Synchronise and return the status bits of instance i (i = -1: all, plus the
+ * batch's barrier-timeout bit). */
+xf_status xf_batch_get_status(xf_batch *b, int i, uint32_t *flags, void *stream);
+/* Runs one bounded grid barrier that expects `extra_arrivals` more blocks than
+ * the grid has, with the given limit in SM clock cycles, and returns the status
+ * bits it produced: XF_FLAG_TIMEOUT when the wait ran out (extra_arrivals > 0),
+ * 0 otherwise. Synchronises the device. Checks the timeout path without
+ * faulting or hanging the GPU. */
+xf_status xf_barrier_probe(int64_t timeout_cycles, int extra_arrivals, uint32_t *flags);
+
 /* Allocation-free RHS. The paper has no counterpart: this entry point exists
  * for callers that may not allocate device memory -- for example a host that
  * hands all device memory to its own pool or caching allocator and forbids

@@ -8,6 +8,7 @@
 
 #include "xf.h"
 #include "xf_device.cuh"
+#include "xf_internal.h"
 
 namespace {
 
@@ -98,6 +99,18 @@ bool pick(int dim, int N, Table* t) {
     default: return false;
   }
 }
+
+// dt from the reduced maxima (one thread); resets the accumulators.
+__global__ void k_dt_finalize(const __grid_constant__ xf::Params p, unsigned long long* red,
+                              double* dt_out, double* dt_copy) {
+  const double dt = xf::dt_from_red(p, red);
+  *dt_out = dt;
+  if (dt_copy) *dt_copy = dt;
+  red[0] = 0ull;
+  red[1] = 0ull;
+}
+
+__global__ void k_set_scalar(double* dst, double v) { *dst = v; }
 
 __global__ void k_fill(double* p, long long n, double v) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -257,7 +270,7 @@ xf_status stage_fluxes(xf_handle* h, const double* Uin, int do_cfl, cudaStream_t
   });
   h->tcur = 1 - h->tcur;
   if (do_cfl)
-    timed(h, XF_PROF_DT, s, [&] { xf::k_dt_finalize<<<1, 1, 0, s>>>(p, h->red, h->dt, nullptr); });
+    timed(h, XF_PROF_DT, s, [&] { k_dt_finalize<<<1, 1, 0, s>>>(p, h->red, h->dt, nullptr); });
   if (p.viscous) timed(h, XF_PROF_GRAD, s, [&] { h->tab.grad(p, h->Q, s); });
   for (int d = 0; d < p.dim; ++d)
     timed(h, XF_PROF_FACE_X + d, s, [&] { h->tab.face[d](p, h->Q, h->G[d], h->flags, s); });
@@ -277,6 +290,13 @@ __global__ void k_probe_fp64(double* out, long long iters, double a) {
 }
 
 }  // namespace
+
+xf_status xf_internal_fill_params(const xf_grid* g, const xf_thermo* th, const xf_opts* o,
+                                  xf::Params* p) {
+  return fill_params(g, th, o, p);
+}
+void xf_internal_set_error(const char* msg) { g_err = msg; }
+void xf_internal_set_cuda_error(const char* what, cudaError_t e) { set_err(what, e); }
 
 extern "C" {
 
@@ -426,7 +446,7 @@ xf_status xf_compute_dt(xf_handle* h, double* dt_dev, void* stream) {
   const xf::Params& p = h->p;
   h->tab.prim(p, h->U, h->T[h->tcur], h->T[1 - h->tcur], h->Q, h->flags, h->red, 1, s);
   h->tcur = 1 - h->tcur;
-  xf::k_dt_finalize<<<1, 1, 0, s>>>(p, h->red, h->dt, dt_dev);
+  k_dt_finalize<<<1, 1, 0, s>>>(p, h->red, h->dt, dt_dev);
   XF_CUDA(cudaGetLastError());
   return XF_OK;
 }
@@ -436,7 +456,7 @@ xf_status xf_step_rk3(xf_handle* h, double dt, double* dt_dev_out, void* stream)
   cudaStream_t s = (cudaStream_t)stream;
   const xf::Params& p = h->p;
   const bool cfl = !(dt > 0.0);
-  if (!cfl) xf::k_set_scalar<<<1, 1, 0, s>>>(h->dt, dt);
+  if (!cfl) k_set_scalar<<<1, 1, 0, s>>>(h->dt, dt);
   // Eq. 16: three stages, U^n kept in U, stages in Us
   xf_status st = stage_fluxes(h, h->U, cfl ? 1 : 0, s);
   if (st != XF_OK) return st;

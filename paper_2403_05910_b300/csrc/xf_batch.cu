@@ -1,0 +1,692 @@
+// xf_batch.cu -- batched RK3 for many independent 2D instances of uneven size
+// and species count: one persistent (cooperative) kernel per RK stage runs all
+// phases of the stage for every instance, separated by a bounded grid barrier;
+// a step is replayed from a CUDA graph; an autotuner picks the block size and
+// the face-tile shape. Each cell and face is computed by the same device
+// functions as the single-grid path (xf_device.cuh), so results are bitwise
+// identical to xf_step_rk3 on each instance.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "xf.h"
+#include "xf_device.cuh"
+#include "xf_internal.h"
+
+namespace {
+
+constexpr int BDIM = 2;  // the batched form serves 2D instances
+
+struct BInst {
+  xf::Params p;
+  double* U;
+  double* Us;
+  double* T[2];
+  double* Q;
+  double* G[2];
+  double* dt;
+  unsigned long long* red;
+  uint32_t* flags;
+  int tiles_x[2];        // whole face tiles along x, for the x-faces / y-faces
+  int m0[2], m1[2];      // extent covered by whole tiles (multiples of tw, th)
+  long long fitems[2];   // face work items per direction (= faces, no padding)
+};
+
+struct BCtl {
+  int ninst;
+  const long long* pre_pad;   // prefix over instances of padded cells [ninst + 1]
+  const long long* pre_cell;  // ... of interior cells
+  const long long* pre_face;  // ... of face work items (x then y)
+  unsigned* bar;              // [0] arrivals, [1] generation
+  long long bar_timeout;      // clock64 cycles a block waits at a barrier
+  uint32_t* bflags;           // batch status word (XF_FLAG_TIMEOUT)
+  int tw, th;                 // face tile shape (faces)
+};
+
+__device__ __forceinline__ int find_inst(const long long* pre, int n, long long g) {
+  int lo = 0, hi = n;  // pre[lo] <= g < pre[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (pre[mid] <= g) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// Grid-wide barrier of a co-resident grid. A block that waits longer than
+// bar_timeout cycles records XF_FLAG_TIMEOUT and goes on (its results are then
+// invalid, but the kernel always finishes).
+__device__ void grid_barrier(const BCtl& c, unsigned expect) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = c.bar + 1;
+    const unsigned g0 = *gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(c.bar, 1u) + 1u;
+    if (arrived == expect) {
+      atomicExch(c.bar, 0u);
+      __threadfence();
+      atomicAdd(c.bar + 1, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*gen == g0) {
+        if (clock64() - t0 > c.bar_timeout) {
+          atomicOr(c.bflags, XF_FLAG_TIMEOUT);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ unsigned long long obits(double x) {
+  return (unsigned long long)__double_as_longlong(x);
+}
+
+template <int NS>
+__device__ __forceinline__ void b_prim(const BInst& I, long long t, const double* Uin,
+                                       const double* Tin, double* Tout, int cfl, double& sc,
+                                       double& sn) {
+  xf::prim_cell<BDIM, NS>(I.p, t, Uin, Tin, Tout, I.Q, I.flags, cfl, sc, sn);
+}
+
+template <int NS>
+__device__ __forceinline__ void b_face(const BInst& I, int D, int fi, int fj) {
+  if (D == 0) xf::face_one<BDIM, NS, 0>(I.p, fi, fj, 0, I.Q, I.G[0], I.flags);
+  else xf::face_one<BDIM, NS, 1>(I.p, fi, fj, 0, I.Q, I.G[1], I.flags);
+}
+
+// One RK stage (1, 2, 3) of every instance. tsel selects the temperature
+// buffer read (the other is written); cfl: reduce the CFL maxima and set dt.
+template <int BT>
+__global__ void __launch_bounds__(BT, 256 / BT)
+k_batch_stage(const BInst* __restrict__ inst, const __grid_constant__ BCtl c, int stage, int tsel,
+              int cfl) {
+  const int n = c.ninst;
+  const long long stride = (long long)gridDim.x * BT;
+  const unsigned nb = gridDim.x;
+  // ---- primitive recovery (+ CFL maxima) over all padded cells
+  const long long totp = c.pre_pad[n];
+  for (long long base = (long long)blockIdx.x * BT; base < totp; base += stride) {
+    const long long g = base + threadIdx.x;
+    int b = -1;
+    double sc = 0.0, sn = 0.0;
+    if (g < totp) {
+      b = find_inst(c.pre_pad, n, g);
+      const BInst& I = inst[b];
+      const long long t = g - c.pre_pad[b];
+      const double* Uin = stage == 1 ? I.U : I.Us;
+      switch (I.p.N) {
+        case 2: b_prim<2>(I, t, Uin, I.T[tsel], I.T[1 - tsel], cfl, sc, sn); break;
+        case 3: b_prim<3>(I, t, Uin, I.T[tsel], I.T[1 - tsel], cfl, sc, sn); break;
+        case 4: b_prim<4>(I, t, Uin, I.T[tsel], I.T[1 - tsel], cfl, sc, sn); break;
+        default: b_prim<5>(I, t, Uin, I.T[tsel], I.T[1 - tsel], cfl, sc, sn); break;
+      }
+    }
+    if (cfl) {
+      const unsigned full = 0xffffffffu;
+      const int b0 = __shfl_sync(full, b, 0);
+      if (__all_sync(full, b == b0)) {
+        unsigned long long x = obits(sc), y = obits(sn);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const unsigned long long x2 = __shfl_xor_sync(full, x, o);
+          const unsigned long long y2 = __shfl_xor_sync(full, y, o);
+          x = x2 > x ? x2 : x;
+          y = y2 > y ? y2 : y;
+        }
+        if ((threadIdx.x & 31) == 0 && b0 >= 0) {
+          atomicMax(inst[b0].red + 0, x);
+          atomicMax(inst[b0].red + 1, y);
+        }
+      } else if (b >= 0) {
+        atomicMax(inst[b].red + 0, obits(sc));
+        atomicMax(inst[b].red + 1, obits(sn));
+      }
+    }
+  }
+  grid_barrier(c, nb);
+  // ---- per-instance time step
+  if (cfl) {
+    if (blockIdx.x == 0) {
+      for (int b = threadIdx.x; b < n; b += BT) {
+        const BInst& I = inst[b];
+        *I.dt = xf::dt_from_red(I.p, I.red);
+        I.red[0] = 0ull;
+        I.red[1] = 0ull;
+      }
+    }
+    grid_barrier(c, nb);
+  }
+  // ---- nodal velocity derivatives (viscous instances)
+  for (long long g = (long long)blockIdx.x * BT + threadIdx.x; g < totp; g += stride) {
+    const int b = find_inst(c.pre_pad, n, g);
+    const BInst& I = inst[b];
+    if (!I.p.viscous) continue;
+    const long long t = g - c.pre_pad[b];
+    switch (I.p.N) {
+      case 2: xf::grad_cell<BDIM, 2>(I.p, t, I.Q); break;
+      case 3: xf::grad_cell<BDIM, 3>(I.p, t, I.Q); break;
+      case 4: xf::grad_cell<BDIM, 4>(I.p, t, I.Q); break;
+      default: xf::grad_cell<BDIM, 5>(I.p, t, I.Q); break;
+    }
+  }
+  grid_barrier(c, nb);
+  // ---- face fluxes, x then y, in tiles of tw x th faces
+  const long long totf = c.pre_face[n];
+  const int tile = c.tw * c.th;
+  for (long long g = (long long)blockIdx.x * BT + threadIdx.x; g < totf; g += stride) {
+    const int b = find_inst(c.pre_face, n, g);
+    const BInst& I = inst[b];
+    long long l = g - c.pre_face[b];
+    int D = 0;
+    if (l >= I.fitems[0]) { l -= I.fitems[0]; D = 1; }
+    const int nf0 = I.p.n[0] + (D == 0);
+    const long long ntile = (long long)I.m0[D] * I.m1[D];
+    int fi, fj;
+    if (l < ntile) {  // whole tw x th tiles, row-major inside a tile
+      const long long tl = l / tile;
+      const int w = (int)(l - tl * tile);
+      fi = (int)(tl % I.tiles_x[D]) * c.tw + w % c.tw;
+      fj = (int)(tl / I.tiles_x[D]) * c.th + w / c.tw;
+    } else {          // remainder: right strip (x >= m0, y < m1), then top rows (y >= m1)
+      long long r = l - ntile;
+      const long long right = (long long)(nf0 - I.m0[D]) * I.m1[D];
+      if (r < right) {
+        const int wdt = nf0 - I.m0[D];
+        fi = I.m0[D] + (int)(r % wdt);
+        fj = (int)(r / wdt);
+      } else {
+        r -= right;
+        fi = (int)(r % nf0);
+        fj = I.m1[D] + (int)(r / nf0);
+      }
+    }
+    switch (I.p.N) {
+      case 2: b_face<2>(I, D, fi, fj); break;
+      case 3: b_face<3>(I, D, fi, fj); break;
+      case 4: b_face<4>(I, D, fi, fj); break;
+      default: b_face<5>(I, D, fi, fj); break;
+    }
+  }
+  grid_barrier(c, nb);
+  // ---- conservative difference + RK3 combination
+  const long long totc = c.pre_cell[n];
+  for (long long g = (long long)blockIdx.x * BT + threadIdx.x; g < totc; g += stride) {
+    const int b = find_inst(c.pre_cell, n, g);
+    const BInst& I = inst[b];
+    const long long cidx = g - c.pre_cell[b];
+    const double dt = __ldcg(I.dt);
+    const double* Us = stage == 1 ? I.U : I.Us;
+    double* out = stage == 3 ? I.U : I.Us;
+    switch (I.p.N) {
+      case 2: xf::update_cell<BDIM, 2>(I.p, cidx, I.G[0], I.G[1], nullptr, I.U, Us, out, dt, stage); break;
+      case 3: xf::update_cell<BDIM, 3>(I.p, cidx, I.G[0], I.G[1], nullptr, I.U, Us, out, dt, stage); break;
+      case 4: xf::update_cell<BDIM, 4>(I.p, cidx, I.G[0], I.G[1], nullptr, I.U, Us, out, dt, stage); break;
+      default: xf::update_cell<BDIM, 5>(I.p, cidx, I.G[0], I.G[1], nullptr, I.U, Us, out, dt, stage); break;
+    }
+  }
+}
+
+__global__ void k_batch_set_dt(const BInst* __restrict__ inst, int n, double dt) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < n) *inst[b].dt = dt;
+}
+
+__global__ void k_batch_fill(double* p, long long n, double v) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
+// One grid barrier expecting `expect` arrivals (tests the bounded wait).
+__global__ void k_barrier_probe(const __grid_constant__ BCtl c, unsigned expect) {
+  grid_barrier(c, expect);
+}
+
+int nq_of(int dim, int N) { return 2 * N + 2 * dim + 9 + dim * dim; }
+
+struct Candidate {
+  int bt, tw, th;
+};
+const Candidate kCandidates[] = {
+    {128, 128, 1}, {128, 32, 4}, {128, 16, 8}, {128, 64, 2},
+    {256, 256, 1}, {256, 32, 8}, {256, 64, 4}, {256, 16, 16},
+    {128, 8, 16},  {256, 8, 32}, {256, 128, 2}, {128, 32, 8},
+};
+constexpr int kNumCandidates = sizeof(kCandidates) / sizeof(kCandidates[0]);
+
+#define XB_CUDA(call)                               \
+  do {                                              \
+    cudaError_t e_ = (call);                        \
+    if (e_ != cudaSuccess) {                        \
+      xf_internal_set_cuda_error(#call, e_);        \
+      return XF_ERR_CUDA;                           \
+    }                                               \
+  } while (0)
+
+}  // namespace
+
+struct xf_batch {
+  int n = 0;
+  std::vector<BInst> hinst;
+  BInst* dinst = nullptr;
+  long long* dpre = nullptr;  // 3 x (n + 1)
+  std::vector<long long> pre_pad, pre_cell, pre_face;
+  unsigned* bar = nullptr;
+  uint32_t* bflags = nullptr;
+  std::vector<void*> allocs;
+  int choice = 0;
+  int grid = 0;
+  int tsel = 0;
+  long long timeout = 4000000000ll;  // ~2 s at 2 GHz
+  bool use_graph = true;
+  cudaStream_t cap = nullptr;  // capture stream (the legacy stream cannot be captured)
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  double graph_dt[2] = {NAN, NAN};
+};
+
+namespace {
+
+void drop_graphs(xf_batch* b) {
+  for (int k = 0; k < 2; ++k) {
+    if (b->exec[k]) cudaGraphExecDestroy(b->exec[k]);
+    b->exec[k] = nullptr;
+    b->graph_dt[k] = NAN;
+  }
+}
+
+// Tile bookkeeping, prefix sums and launch geometry for candidate `k`.
+xf_status configure(xf_batch* b, int k) {
+  const Candidate& cd = kCandidates[k];
+  b->pre_face.assign(b->n + 1, 0);
+  for (int i = 0; i < b->n; ++i) {
+    BInst& I = b->hinst[i];
+    for (int D = 0; D < 2; ++D) {
+      const int nf0 = I.p.n[0] + (D == 0), nf1 = I.p.n[1] + (D == 1);
+      I.tiles_x[D] = nf0 / cd.tw;
+      I.m0[D] = (nf0 / cd.tw) * cd.tw;
+      I.m1[D] = (nf1 / cd.th) * cd.th;
+      I.fitems[D] = (long long)nf0 * nf1;
+    }
+    b->pre_face[i + 1] = b->pre_face[i] + I.fitems[0] + I.fitems[1];
+  }
+  XB_CUDA(cudaMemcpy(b->dinst, b->hinst.data(), sizeof(BInst) * b->n, cudaMemcpyHostToDevice));
+  XB_CUDA(cudaMemcpy(b->dpre + 2 * (b->n + 1), b->pre_face.data(), sizeof(long long) * (b->n + 1),
+                     cudaMemcpyHostToDevice));
+  int dev = 0, sms = 0, per_sm = 0;
+  XB_CUDA(cudaGetDevice(&dev));
+  XB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  if (cd.bt == 128)
+    XB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_stage<128>, 128, 0));
+  else
+    XB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_stage<256>, 256, 0));
+  if (per_sm < 1) {
+    xf_internal_set_error("xf_batch: stage kernel cannot be resident");
+    return XF_ERR_CUDA;
+  }
+  b->grid = per_sm * sms;
+  b->choice = k;
+  drop_graphs(b);
+  return XF_OK;
+}
+
+BCtl make_ctl(const xf_batch* b) {
+  BCtl c;
+  c.ninst = b->n;
+  c.pre_pad = b->dpre;
+  c.pre_cell = b->dpre + (b->n + 1);
+  c.pre_face = b->dpre + 2 * (b->n + 1);
+  c.bar = b->bar;
+  c.bar_timeout = b->timeout;
+  c.bflags = b->bflags;
+  c.tw = kCandidates[b->choice].tw;
+  c.th = kCandidates[b->choice].th;
+  return c;
+}
+
+xf_status launch_stage(xf_batch* b, cudaStream_t s, int stage, int tsel, int cfl) {
+  XB_CUDA(cudaMemsetAsync(b->bar, 0, 2 * sizeof(unsigned), s));
+  const BCtl c = make_ctl(b);
+  const int bt = kCandidates[b->choice].bt;
+  cudaLaunchConfig_t cfg;
+  std::memset(&cfg, 0, sizeof cfg);
+  cfg.gridDim = dim3((unsigned)b->grid);
+  cfg.blockDim = dim3((unsigned)bt);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const BInst* di = b->dinst;
+  if (bt == 128) XB_CUDA(cudaLaunchKernelEx(&cfg, k_batch_stage<128>, di, c, stage, tsel, cfl));
+  else XB_CUDA(cudaLaunchKernelEx(&cfg, k_batch_stage<256>, di, c, stage, tsel, cfl));
+  return XF_OK;
+}
+
+// The three stages of one step starting from temperature buffer t0.
+xf_status enqueue_step(xf_batch* b, cudaStream_t s, double dt, int t0) {
+  const bool cfl = !(dt > 0.0);
+  if (!cfl) k_batch_set_dt<<<(b->n + 127) / 128, 128, 0, s>>>(b->dinst, b->n, dt);
+  int t = t0;
+  for (int stage = 1; stage <= 3; ++stage) {
+    xf_status st = launch_stage(b, s, stage, t, (cfl && stage == 1) ? 1 : 0);
+    if (st != XF_OK) return st;
+    t = 1 - t;
+  }
+  XB_CUDA(cudaGetLastError());
+  return XF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+xf_status xf_batch_create(int n, const xf_grid* grids, const xf_thermo* thermos,
+                          const xf_opts* opts, xf_batch** out) {
+  if (!out || n < 1 || !grids || !thermos || !opts) return XF_ERR_ARG;
+  *out = nullptr;
+  xf_batch* b = new xf_batch();
+  b->n = n;
+  b->hinst.resize(n);
+  b->pre_pad.assign(n + 1, 0);
+  b->pre_cell.assign(n + 1, 0);
+  for (int i = 0; i < n; ++i) {
+    BInst& I = b->hinst[i];
+    std::memset(&I, 0, sizeof I);
+    xf_status st = xf_internal_fill_params(&grids[i], &thermos[i], &opts[i], &I.p);
+    if (st != XF_OK || grids[i].dim != BDIM) {
+      delete b;
+      return XF_ERR_ARG;
+    }
+    b->pre_pad[i + 1] = b->pre_pad[i] + I.p.pcells;
+    b->pre_cell[i + 1] = b->pre_cell[i] + I.p.cells;
+  }
+  auto alloc = [&](void** p, size_t bytes) -> bool {
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    b->allocs.push_back(*p);
+    return true;
+  };
+  bool ok = alloc((void**)&b->dinst, sizeof(BInst) * n) &&
+            alloc((void**)&b->dpre, sizeof(long long) * 3 * (n + 1)) &&
+            alloc((void**)&b->bar, 2 * sizeof(unsigned)) && alloc((void**)&b->bflags, sizeof(uint32_t));
+  for (int i = 0; ok && i < n; ++i) {
+    BInst& I = b->hinst[i];
+    const xf::Params& p = I.p;
+    const size_t sb = sizeof(double) * (size_t)p.nv * p.cells;
+    ok = alloc((void**)&I.U, sb) && alloc((void**)&I.Us, sb) &&
+         alloc((void**)&I.T[0], sizeof(double) * p.cells) &&
+         alloc((void**)&I.T[1], sizeof(double) * p.cells) &&
+         alloc((void**)&I.Q, sizeof(double) * (size_t)nq_of(p.dim, p.N) * p.pcells) &&
+         alloc((void**)&I.G[0], sizeof(double) * (size_t)p.nv * (p.n[0] + 1) * p.n[1]) &&
+         alloc((void**)&I.G[1], sizeof(double) * (size_t)p.nv * p.n[0] * (p.n[1] + 1)) &&
+         alloc((void**)&I.dt, sizeof(double)) && alloc((void**)&I.red, 2 * sizeof(unsigned long long)) &&
+         alloc((void**)&I.flags, sizeof(uint32_t));
+    if (ok) {
+      ok = cudaMemset(I.Q, 0, sizeof(double) * (size_t)nq_of(p.dim, p.N) * p.pcells) == cudaSuccess &&
+           cudaMemset(I.red, 0, 2 * sizeof(unsigned long long)) == cudaSuccess &&
+           cudaMemset(I.flags, 0, sizeof(uint32_t)) == cudaSuccess &&
+           cudaMemset(I.dt, 0, sizeof(double)) == cudaSuccess;
+      k_batch_fill<<<(unsigned)((p.cells + 255) / 256), 256>>>(I.T[0], p.cells, 300.0);
+    }
+  }
+  if (!ok) {
+    xf_batch_destroy(b);
+    xf_internal_set_error("xf_batch_create: device allocation failed");
+    return XF_ERR_OOM;
+  }
+  if (cudaMemcpy(b->dpre, b->pre_pad.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->dpre + (n + 1), b->pre_cell.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(b->bflags, 0, sizeof(uint32_t)) != cudaSuccess) {
+    xf_batch_destroy(b);
+    xf_internal_set_error("xf_batch_create: initialisation failed");
+    return XF_ERR_CUDA;
+  }
+  xf_status st = configure(b, 0);
+  if (st == XF_OK && cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess)
+    st = XF_ERR_CUDA;
+  if (st == XF_OK && cudaDeviceSynchronize() != cudaSuccess) st = XF_ERR_CUDA;
+  if (st != XF_OK) {
+    xf_batch_destroy(b);
+    return st;
+  }
+  *out = b;
+  return XF_OK;
+}
+
+void xf_batch_destroy(xf_batch* b) {
+  if (!b) return;
+  drop_graphs(b);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  for (void* p : b->allocs) cudaFree(p);
+  delete b;
+}
+
+xf_status xf_batch_set_primitive(xf_batch* b, int i, const double* P, void* stream) {
+  if (!b || i < 0 || i >= b->n || !P) return XF_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  BInst& I = b->hinst[i];
+  const xf::Params& p = I.p;
+  XB_CUDA(cudaMemcpyAsync(I.Us, P, sizeof(double) * (size_t)p.nv * p.cells, cudaMemcpyDefault, s));
+  const unsigned g = (unsigned)((p.cells + 255) / 256);
+  switch (p.N) {
+    case 2: xf::k_from_prim<BDIM, 2><<<g, 256, 0, s>>>(p, I.Us, I.U, I.T[b->tsel]); break;
+    case 3: xf::k_from_prim<BDIM, 3><<<g, 256, 0, s>>>(p, I.Us, I.U, I.T[b->tsel]); break;
+    case 4: xf::k_from_prim<BDIM, 4><<<g, 256, 0, s>>>(p, I.Us, I.U, I.T[b->tsel]); break;
+    default: xf::k_from_prim<BDIM, 5><<<g, 256, 0, s>>>(p, I.Us, I.U, I.T[b->tsel]); break;
+  }
+  XB_CUDA(cudaGetLastError());
+  return XF_OK;
+}
+
+xf_status xf_batch_set_state(xf_batch* b, int i, const double* U, const double* T, void* stream) {
+  if (!b || i < 0 || i >= b->n || !U) return XF_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  BInst& I = b->hinst[i];
+  XB_CUDA(cudaMemcpyAsync(I.U, U, sizeof(double) * (size_t)I.p.nv * I.p.cells, cudaMemcpyDefault, s));
+  if (T) {
+    XB_CUDA(cudaMemcpyAsync(I.T[b->tsel], T, sizeof(double) * I.p.cells, cudaMemcpyDefault, s));
+  } else {
+    k_batch_fill<<<(unsigned)((I.p.cells + 255) / 256), 256, 0, s>>>(I.T[b->tsel], I.p.cells, 300.0);
+    XB_CUDA(cudaGetLastError());
+  }
+  return XF_OK;
+}
+
+xf_status xf_batch_get_state(xf_batch* b, int i, double* U, double* T, void* stream) {
+  if (!b || i < 0 || i >= b->n) return XF_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  BInst& I = b->hinst[i];
+  if (U) XB_CUDA(cudaMemcpyAsync(U, I.U, sizeof(double) * (size_t)I.p.nv * I.p.cells, cudaMemcpyDefault, s));
+  if (T) XB_CUDA(cudaMemcpyAsync(T, I.T[b->tsel], sizeof(double) * I.p.cells, cudaMemcpyDefault, s));
+  return XF_OK;
+}
+
+xf_status xf_batch_step_rk3(xf_batch* b, double dt, void* stream) {
+  if (!b || !(dt == dt)) return XF_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int par = b->tsel;
+  const double key = dt > 0.0 ? dt : 0.0;
+  if (b->use_graph) {
+    if (!b->exec[par] || !(b->graph_dt[par] == key)) {
+      if (b->exec[par]) cudaGraphExecDestroy(b->exec[par]);
+      b->exec[par] = nullptr;
+      cudaGraph_t graph = nullptr;
+      XB_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+      xf_status st = enqueue_step(b, b->cap, dt, par);
+      cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
+      if (st != XF_OK || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        b->use_graph = false;  // capture unsupported here: plain launches from now on
+      } else {
+        e = cudaGraphInstantiate(&b->exec[par], graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+          cudaGetLastError();
+          b->exec[par] = nullptr;
+          b->use_graph = false;
+        } else {
+          b->graph_dt[par] = key;
+        }
+      }
+    }
+  }
+  if (b->use_graph) {
+    XB_CUDA(cudaGraphLaunch(b->exec[par], s));
+  } else {
+    xf_status st = enqueue_step(b, s, dt, par);
+    if (st != XF_OK) return st;
+  }
+  b->tsel = 1 - par;  // three stages toggle the temperature buffer an odd number of times
+  return XF_OK;
+}
+
+xf_status xf_batch_autotune(xf_batch* b, int steps, int* choice_out, float* ms_out,
+                            void* stream) {
+  if (!b || steps < 1) return XF_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  // snapshot every instance's U and warm-start T so tuning leaves no trace
+  size_t total = 0;
+  for (const BInst& I : b->hinst) total += (size_t)(I.p.nv + 1) * I.p.cells;
+  double* snap = nullptr;
+  XB_CUDA(cudaMalloc(&snap, sizeof(double) * total));
+  auto copy_all = [&](bool save) -> xf_status {
+    size_t off = 0;
+    for (const BInst& I : b->hinst) {
+      const size_t nu = (size_t)I.p.nv * I.p.cells;
+      if (save) {
+        XB_CUDA(cudaMemcpyAsync(snap + off, I.U, sizeof(double) * nu, cudaMemcpyDeviceToDevice, s));
+        XB_CUDA(cudaMemcpyAsync(snap + off + nu, I.T[b->tsel], sizeof(double) * I.p.cells, cudaMemcpyDeviceToDevice, s));
+      } else {
+        XB_CUDA(cudaMemcpyAsync(I.U, snap + off, sizeof(double) * nu, cudaMemcpyDeviceToDevice, s));
+        XB_CUDA(cudaMemcpyAsync(I.T[b->tsel], snap + off + nu, sizeof(double) * I.p.cells, cudaMemcpyDeviceToDevice, s));
+      }
+      off += nu + I.p.cells;
+    }
+    return XF_OK;
+  };
+  xf_status st = copy_all(true);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int best = b->choice;
+  float best_ms = 1e30f;
+  const int tsel0 = b->tsel;
+  for (int k = 0; st == XF_OK && k < kNumCandidates; ++k) {
+    st = configure(b, k);
+    if (st != XF_OK) break;
+    st = enqueue_step(b, s, 0.0, tsel0);  // warm-up
+    if (st != XF_OK) break;
+    st = copy_all(false);
+    cudaEventRecord(e0, s);
+    for (int r = 0; st == XF_OK && r < steps; ++r) st = enqueue_step(b, s, 0.0, (tsel0 + r) & 1);
+    cudaEventRecord(e1, s);
+    if (st == XF_OK) st = copy_all(false);
+    float ms = 0.f;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      st = XF_ERR_CUDA;
+      break;
+    }
+    if (ms_out) ms_out[k] = ms / steps;
+    if (ms < best_ms) { best_ms = ms; best = k; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamSynchronize(s);
+  cudaFree(snap);
+  b->tsel = tsel0;
+  for (BInst& I : b->hinst) cudaMemset(I.flags, 0, sizeof(uint32_t));
+  if (st != XF_OK) return st;
+  st = configure(b, best);
+  if (choice_out) *choice_out = best;
+  return st;
+}
+
+xf_status xf_batch_config(xf_batch* b, int choice, int* bt, int* tw, int* th) {
+  if (!b) return XF_ERR_ARG;
+  if (choice >= 0) {
+    if (choice >= kNumCandidates) return XF_ERR_ARG;
+    xf_status st = configure(b, choice);
+    if (st != XF_OK) return st;
+  }
+  if (bt) *bt = kCandidates[b->choice].bt;
+  if (tw) *tw = kCandidates[b->choice].tw;
+  if (th) *th = kCandidates[b->choice].th;
+  return XF_OK;
+}
+
+xf_status xf_batch_get_status(xf_batch* b, int i, uint32_t* flags, void* stream) {
+  if (!b || i < -1 || i >= b->n) return XF_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  XB_CUDA(cudaStreamSynchronize(s));
+  uint32_t f = 0, x = 0;
+  XB_CUDA(cudaMemcpy(&f, b->bflags, sizeof f, cudaMemcpyDeviceToHost));
+  for (int k = 0; k < b->n; ++k) {
+    if (i >= 0 && k != i) continue;
+    XB_CUDA(cudaMemcpy(&x, b->hinst[k].flags, sizeof x, cudaMemcpyDeviceToHost));
+    f |= x;
+  }
+  if (flags) *flags = f;
+  if (f & XF_FLAG_NONPHYS) return XF_ERR_NONPHYS;
+  if (f & XF_FLAG_NEWTON) return XF_ERR_NEWTON;
+  if (f & XF_FLAG_EIGEN) return XF_ERR_EIGEN;
+  if (f & XF_FLAG_TIMEOUT) return XF_ERR_TIMEOUT;
+  return XF_OK;
+}
+
+int xf_batch_size(const xf_batch* b) { return b ? b->n : 0; }
+
+int xf_batch_uses_graph(const xf_batch* b) { return (b && b->use_graph) ? 1 : 0; }
+
+int xf_batch_num_candidates(void) { return kNumCandidates; }
+
+xf_status xf_barrier_probe(int64_t timeout_cycles, int extra_arrivals, uint32_t* flags) {
+  if (timeout_cycles < 1 || extra_arrivals < 0 || !flags) return XF_ERR_ARG;
+  int dev = 0, sms = 0;
+  XB_CUDA(cudaGetDevice(&dev));
+  XB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  unsigned* bar = nullptr;
+  uint32_t* fl = nullptr;
+  XB_CUDA(cudaMalloc(&bar, 2 * sizeof(unsigned)));
+  if (cudaMalloc(&fl, sizeof(uint32_t)) != cudaSuccess) {
+    cudaFree(bar);
+    return XF_ERR_CUDA;
+  }
+  cudaMemset(bar, 0, 2 * sizeof(unsigned));
+  cudaMemset(fl, 0, sizeof(uint32_t));
+  BCtl c;
+  std::memset(&c, 0, sizeof c);
+  c.bar = bar;
+  c.bar_timeout = timeout_cycles;
+  c.bflags = fl;
+  cudaLaunchConfig_t cfg;
+  std::memset(&cfg, 0, sizeof cfg);
+  cfg.gridDim = dim3((unsigned)sms);
+  cfg.blockDim = dim3(32);
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_barrier_probe, c, (unsigned)(sms + extra_arrivals));
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  uint32_t f = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&f, fl, sizeof f, cudaMemcpyDeviceToHost);
+  cudaFree(bar);
+  cudaFree(fl);
+  if (e != cudaSuccess) {
+    xf_internal_set_cuda_error("xf_barrier_probe", e);
+    return XF_ERR_CUDA;
+  }
+  *flags = f;
+  return (f & XF_FLAG_TIMEOUT) ? XF_ERR_TIMEOUT : XF_OK;
+}
+
+}  // extern "C"

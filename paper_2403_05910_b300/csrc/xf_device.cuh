@@ -125,18 +125,18 @@ __device__ __forceinline__ void raise(uint32_t* flags, uint32_t bits) {
 // writes the padded per-cell fields. Stage-1 launches also reduce the CFL
 // maxima over interior cells into red[0] (sum_d (|u_d|+c)/dx_d) and red[1]
 // (viscous diffusivity), as ordered bit patterns of non-negative doubles.
+// Per-cell body of the primitive recovery (shared by the plain kernel and the
+// batched persistent kernel, so both run the same arithmetic). t is the padded
+// cell index (t < pcells); s_cfl / s_nu receive this cell's CFL terms.
 template <int DIM, int NS>
-__global__ void __launch_bounds__(256)
-k_prim(const __grid_constant__ Params p, const double* __restrict__ U,
-       const double* __restrict__ Tin, double* __restrict__ Tout,
-       double* __restrict__ Q, uint32_t* __restrict__ flags,
-       unsigned long long* __restrict__ red, int do_cfl) {
+__device__ __forceinline__ void prim_cell(const Params& p, long long t, const double* __restrict__ U,
+                                          const double* __restrict__ Tin, double* __restrict__ Tout,
+                                          double* __restrict__ Q, uint32_t* __restrict__ flags,
+                                          int do_cfl, double& s_cfl, double& s_nu) {
   using L = Lay<DIM, NS>;
   constexpr int NV = L::NV;
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long PC = p.pcells;
-  double s_cfl = 0.0, s_nu = 0.0;
-  if (t < PC) {
+  {
     const int ip = (int)(t % p.np[0]);
     const int jp = (int)((t / p.np[0]) % p.np[1]);
     const int kp = (int)(t / ((long long)p.np[0] * p.np[1]));
@@ -276,56 +276,63 @@ k_prim(const __grid_constant__ Params p, const double* __restrict__ U,
       }
     }
     raise(flags, st);
-  }
-  if (do_cfl) {
-    unsigned long long a = (unsigned long long)__double_as_longlong(s_cfl);
-    unsigned long long b = (unsigned long long)__double_as_longlong(s_nu);
+    }
+}
+
+// Block-wide max of (a, b) over ordered bit patterns, one atomicMax per block.
+__device__ __forceinline__ void block_max2(double s_cfl, double s_nu, unsigned long long* red) {
+  unsigned long long a = (unsigned long long)__double_as_longlong(s_cfl);
+  unsigned long long b = (unsigned long long)__double_as_longlong(s_nu);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const unsigned long long a2 = __shfl_xor_sync(0xffffffffu, a, o);
-      const unsigned long long b2 = __shfl_xor_sync(0xffffffffu, b, o);
-      a = a2 > a ? a2 : a;
-      b = b2 > b ? b2 : b;
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long a2 = __shfl_xor_sync(0xffffffffu, a, o);
+    const unsigned long long b2 = __shfl_xor_sync(0xffffffffu, b, o);
+    a = a2 > a ? a2 : a;
+    b = b2 > b ? b2 : b;
+  }
+  __shared__ unsigned long long sa[32], sb[32];
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) { sa[w] = a; sb[w] = b; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+      a = sa[k] > a ? sa[k] : a;
+      b = sb[k] > b ? sb[k] : b;
     }
-    __shared__ unsigned long long sa[8], sb[8];
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) { sa[w] = a; sb[w] = b; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
-        a = sa[k] > a ? sa[k] : a;
-        b = sb[k] > b ? sb[k] : b;
-      }
-      atomicMax(red + 0, a);
-      atomicMax(red + 1, b);
-    }
+    atomicMax(red + 0, a);
+    atomicMax(red + 1, b);
   }
 }
 
-// dt from the reduced maxima (one thread); resets the accumulators.
-__global__ void k_dt_finalize(const __grid_constant__ Params p, unsigned long long* red,
-                              double* dt_out, double* dt_copy) {
+template <int DIM, int NS>
+__global__ void __launch_bounds__(256)
+k_prim(const __grid_constant__ Params p, const double* __restrict__ U,
+       const double* __restrict__ Tin, double* __restrict__ Tout,
+       double* __restrict__ Q, uint32_t* __restrict__ flags,
+       unsigned long long* __restrict__ red, int do_cfl) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double s_cfl = 0.0, s_nu = 0.0;
+  if (t < p.pcells) prim_cell<DIM, NS>(p, t, U, Tin, Tout, Q, flags, do_cfl, s_cfl, s_nu);
+  if (do_cfl) block_max2(s_cfl, s_nu, red);
+}
+
+// dt from the reduced maxima: CFL / max sum_d (|u_d| + c)/dx_d, and the
+// viscous limit CFL dx_min^2 / (2 dim max nu).
+__device__ __forceinline__ double dt_from_red(const Params& p, const unsigned long long* red) {
   const double smax = __longlong_as_double((long long)red[0]);
   const double numax = __longlong_as_double((long long)red[1]);
   double dt = p.cfl / smax;
   if (p.viscous && numax > 0.0) dt = fmin(dt, p.cfl * p.hmin2_over_2dim / numax);
-  *dt_out = dt;
-  if (dt_copy) *dt_copy = dt;
-  red[0] = 0ull;
-  red[1] = 0ull;
+  return dt;
 }
 
-__global__ void k_set_scalar(double* dst, double v) { *dst = v; }
 
 // ================================================================ k_grad ===
 // Nodal (1,-8,0,8,-1)/(12 dx) velocity derivatives along every active axis b,
 // wherever the +-2 neighbours along b lie inside the padded box.
 template <int DIM, int NS>
-__global__ void __launch_bounds__(256)
-k_grad(const __grid_constant__ Params p, double* __restrict__ Q) {
+__device__ __forceinline__ void grad_cell(const Params& p, long long t, double* __restrict__ Q) {
   using L = Lay<DIM, NS>;
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= p.pcells) return;
   const long long PC = p.pcells;
   int idx[3];
   idx[0] = (int)(t % p.np[0]);
@@ -344,6 +351,13 @@ k_grad(const __grid_constant__ Params p, double* __restrict__ Q) {
       Q[(L::GU + a * DIM + b) * PC + t] = g;
     }
   }
+}
+
+template <int DIM, int NS>
+__global__ void __launch_bounds__(256)
+k_grad(const __grid_constant__ Params p, double* __restrict__ Q) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < p.pcells) grad_cell<DIM, NS>(p, t, Q);
 }
 
 // ================================================================= WENO5 ===
@@ -388,21 +402,19 @@ __device__ __forceinline__ double weno5_pair(const double* wp, const double* wm,
 #ifndef XF_FACE_MIN_BLOCKS
 #define XF_FACE_MIN_BLOCKS 2
 #endif
+// Per-face body: face (fi, fj, fk) of direction D, i.e. between cells
+// idx - e_D and idx (fi in 0..n_0 when D = 0, and so on).
 template <int DIM, int NS, int D>
-__global__ void __launch_bounds__(128, XF_FACE_MIN_BLOCKS)
-k_face(const __grid_constant__ Params p, const double* __restrict__ Q,
-       double* __restrict__ Gf, uint32_t* __restrict__ flags) {
+__device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk,
+                                         const double* __restrict__ Q, double* __restrict__ Gf,
+                                         uint32_t* __restrict__ flags) {
   using L = Lay<DIM, NS>;
   constexpr int NV = L::NV;
   constexpr int IE = DIM + 1;
   const int nf0 = p.n[0] + (D == 0), nf1 = p.n[1] + (D == 1), nf2 = p.n[2] + (D == 2);
   const long long nfaces = (long long)nf0 * nf1 * nf2;
-  const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= nfaces) return;
-  int id[3];
-  id[0] = (int)(f % nf0);
-  id[1] = (int)((f / nf0) % nf1);
-  id[2] = (int)(f / ((long long)nf0 * nf1));
+  const long long f = ((long long)fk * nf1 + fj) * nf0 + fi;
+  int id[3] = {fi, fj, fk};
   id[D] -= 1;  // left cell
   const long long PC = p.pcells;
   const long long sy = p.np[0], sz = (long long)p.np[0] * p.np[1];
@@ -640,6 +652,17 @@ k_face(const __grid_constant__ Params p, const double* __restrict__ Q,
   raise(flags, st);
 }
 
+template <int DIM, int NS, int D>
+__global__ void __launch_bounds__(128, XF_FACE_MIN_BLOCKS)
+k_face(const __grid_constant__ Params p, const double* __restrict__ Q,
+       double* __restrict__ Gf, uint32_t* __restrict__ flags) {
+  const int nf0 = p.n[0] + (D == 0), nf1 = p.n[1] + (D == 1), nf2 = p.n[2] + (D == 2);
+  const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= (long long)nf0 * nf1 * nf2) return;
+  face_one<DIM, NS, D>(p, (int)(f % nf0), (int)((f / nf0) % nf1), (int)(f / ((long long)nf0 * nf1)),
+                       Q, Gf, flags);
+}
+
 // =============================================================== k_update ===
 // Conservative difference (Eq. 13) and SSP-RK3 (Eq. 16).
 //   mode 0: out = L(U)                   (plain RHS)
@@ -647,14 +670,12 @@ k_face(const __grid_constant__ Params p, const double* __restrict__ Q,
 //   mode 2: out = 3/4 Un + 1/4 (Us + dt L)
 //   mode 3: out = 1/3 Un + 2/3 (Us + dt L)
 template <int DIM, int NS>
-__global__ void __launch_bounds__(256)
-k_update(const __grid_constant__ Params p, const double* __restrict__ Gx,
-         const double* __restrict__ Gy, const double* __restrict__ Gz,
-         const double* Un, const double* Us, double* out, const double* __restrict__ dtp,
-         int mode) {
+__device__ __forceinline__ void update_cell(const Params& p, long long c,
+                                            const double* __restrict__ Gx,
+                                            const double* __restrict__ Gy,
+                                            const double* __restrict__ Gz, const double* Un,
+                                            const double* Us, double* out, double dt, int mode) {
   constexpr int NV = DIM + 1 + NS;
-  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= p.cells) return;
   const int i = (int)(c % p.n[0]);
   const int j = (int)((c / p.n[0]) % p.n[1]);
   const int k = (int)(c / ((long long)p.n[0] * p.n[1]));
@@ -672,7 +693,6 @@ k_update(const __grid_constant__ Params p, const double* __restrict__ Gx,
     fz = c;
     sz = (long long)p.n[0] * p.n[1];
   }
-  const double dt = mode ? *dtp : 0.0;
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     double R = -(ld(Gx + v * NFX + fx + 1) - ld(Gx + v * NFX + fx)) * p.inv_dx[0];
@@ -690,6 +710,17 @@ k_update(const __grid_constant__ Params p, const double* __restrict__ Gx,
     }
     out[v * C + c] = o;
   }
+}
+
+template <int DIM, int NS>
+__global__ void __launch_bounds__(256)
+k_update(const __grid_constant__ Params p, const double* __restrict__ Gx,
+         const double* __restrict__ Gy, const double* __restrict__ Gz,
+         const double* Un, const double* Us, double* out, const double* __restrict__ dtp,
+         int mode) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= p.cells) return;
+  update_cell<DIM, NS>(p, c, Gx, Gy, Gz, Un, Us, out, mode ? *dtp : 0.0, mode);
 }
 
 // ============================================================ k_from_prim ===

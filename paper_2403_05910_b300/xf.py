@@ -44,7 +44,11 @@ class Opts(C.Structure):
 EXPORTS = ["xf_create", "xf_destroy", "xf_nv", "xf_cells", "xf_set_state", "xf_set_primitive",
            "xf_get_state", "xf_rhs", "xf_compute_dt", "xf_step_rk3", "xf_get_status",
            "xf_clear_status", "xf_status_str", "xf_last_error", "xf_profile_enable",
-           "xf_profile_read", "xf_probe_fp64", "xf_rhs_static", "xf_rhs_static_capacity_bytes"]
+           "xf_profile_read", "xf_probe_fp64", "xf_rhs_static", "xf_rhs_static_capacity_bytes",
+           "xf_batch_create", "xf_batch_destroy", "xf_batch_size", "xf_batch_set_primitive",
+           "xf_batch_set_state", "xf_batch_get_state", "xf_batch_step_rk3", "xf_batch_autotune",
+           "xf_batch_config", "xf_batch_get_status", "xf_barrier_probe", "xf_batch_uses_graph",
+           "xf_batch_num_candidates"]
 PROF_SLOTS = 8
 PROF_NAMES = ["prim", "dt", "grad", "face_x", "face_y", "face_z", "update", "spare"]
 
@@ -77,6 +81,21 @@ def _load():
     L.xf_rhs_static.argtypes = [C.POINTER(Grid), C.POINTER(Thermo), C.POINTER(Opts), vp, vp, vp,
                                 C.POINTER(C.c_uint32), vp]
     L.xf_rhs_static_capacity_bytes.restype = C.c_int64
+    L.xf_batch_create.argtypes = [C.c_int, C.POINTER(Grid), C.POINTER(Thermo), C.POINTER(Opts),
+                                  C.POINTER(vp)]
+    L.xf_batch_destroy.argtypes = [vp]
+    L.xf_batch_destroy.restype = None
+    L.xf_batch_size.argtypes = [vp]
+    L.xf_batch_uses_graph.argtypes = [vp]
+    L.xf_batch_set_primitive.argtypes = [vp, C.c_int, vp, vp]
+    L.xf_batch_set_state.argtypes = [vp, C.c_int, vp, vp, vp]
+    L.xf_batch_get_state.argtypes = [vp, C.c_int, vp, vp, vp]
+    L.xf_batch_step_rk3.argtypes = [vp, C.c_double, vp]
+    L.xf_batch_autotune.argtypes = [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_float), vp]
+    L.xf_batch_config.argtypes = [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                  C.POINTER(C.c_int)]
+    L.xf_batch_get_status.argtypes = [vp, C.c_int, C.POINTER(C.c_uint32), vp]
+    L.xf_barrier_probe.argtypes = [C.c_int64, C.c_int, C.POINTER(C.c_uint32)]
     return L
 
 
@@ -237,3 +256,79 @@ def rhs_static(case, U, dUdt, T=None, flags=True, stream=None, **kw):
 
 def rhs_static_capacity_bytes():
     return int(lib.xf_rhs_static_capacity_bytes())
+
+
+class Batch:
+    """Many 2D instances advanced together (xf_batch_*)."""
+
+    def __init__(self, case_list, **kw):
+        self.cases = list(case_list)
+        n = len(self.cases)
+        gs, ts, os_ = (Grid * n)(), (Thermo * n)(), (Opts * n)()
+        self._keep = []
+        for i, c in enumerate(self.cases):
+            g, t, o, keep = structs(c, **kw)
+            gs[i], ts[i], os_[i] = g, t, o
+            self._keep.append(keep)
+        self._structs = (gs, ts, os_)
+        h = C.c_void_p()
+        check(lib.xf_batch_create(n, gs, ts, os_, C.byref(h)), "xf_batch_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.xf_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_primitive(self, i, P, stream=None):
+        check(lib.xf_batch_set_primitive(self.h, i, ptr(P), stream_ptr(stream)), "xf_batch_set_primitive")
+
+    def set_state(self, i, U, T=None, stream=None):
+        check(lib.xf_batch_set_state(self.h, i, ptr(U), ptr(T), stream_ptr(stream)), "xf_batch_set_state")
+
+    def get_state(self, i, U=None, T=None, stream=None):
+        check(lib.xf_batch_get_state(self.h, i, ptr(U), ptr(T), stream_ptr(stream)), "xf_batch_get_state")
+
+    def step(self, dt=0.0, stream=None):
+        check(lib.xf_batch_step_rk3(self.h, float(dt), stream_ptr(stream)), "xf_batch_step_rk3")
+
+    def uses_graph(self):
+        return bool(lib.xf_batch_uses_graph(self.h))
+
+    def autotune(self, steps=1, stream=None, report=False):
+        """Pick the fastest launch shape; returns its index (and, with
+        ``report``, the ms per step of every candidate)."""
+        k = C.c_int(0)
+        nc = lib.xf_batch_num_candidates()
+        ms = (C.c_float * nc)()
+        check(lib.xf_batch_autotune(self.h, int(steps), C.byref(k), ms, stream_ptr(stream)),
+              "xf_batch_autotune")
+        return (k.value, list(ms)) if report else k.value
+
+    def config(self, choice=-1):
+        bt, tw, th = C.c_int(), C.c_int(), C.c_int()
+        check(lib.xf_batch_config(self.h, int(choice), C.byref(bt), C.byref(tw), C.byref(th)),
+              "xf_batch_config")
+        return bt.value, tw.value, th.value
+
+    def status(self, i=-1, stream=None):
+        f = C.c_uint32(0)
+        code = lib.xf_batch_get_status(self.h, int(i), C.byref(f), stream_ptr(stream))
+        if code == XF_ERR_CUDA:
+            check(code, "xf_batch_get_status")
+        return f.value
+
+
+def barrier_probe(timeout_cycles, extra_arrivals):
+    """Status bits of one bounded grid barrier (see xf_barrier_probe)."""
+    f = C.c_uint32(0)
+    code = lib.xf_barrier_probe(int(timeout_cycles), int(extra_arrivals), C.byref(f))
+    if code == XF_ERR_CUDA:
+        check(code, "xf_barrier_probe")
+    return f.value
