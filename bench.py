@@ -148,6 +148,59 @@ def run_reference(args):
     return 0
 
 
+def _batched_vs_per_instance(args, dev, stream):
+    """The 64-instance 2D shock-bubble ensemble: one persistent kernel per stage
+    (autotuned, CUDA graph) against per-instance xf_step_rk3 launches on the
+    same stream; aggregate cell-stage updates/s of each."""
+    import torch
+    from paper_2403_05910_b300 import cases
+    from paper_2403_05910_b300.xf import Batch, Solver
+    cs = cases.batch(0)
+    cells = sum(c.cells for c in cs)
+    b = Batch(cs)
+    for i, c in enumerate(cs):
+        b.set_primitive(i, torch.from_numpy(c.prim).to(dev))
+    choice, ms_cand = b.autotune(steps=1, report=True)
+    shape = b.config()
+
+    def timed(fn, k):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    for _ in range(args.warmup):
+        b.step(0.0)
+    ms_b = timed(lambda: b.step(0.0), args.steps)
+    st_b = b.status()
+    graph = b.uses_graph()
+    b.close()
+    ss = [Solver(c) for c in cs]
+    for sv, c in zip(ss, cs):
+        sv.set_primitive(torch.from_numpy(c.prim).to(dev))
+
+    def per():
+        for sv in ss:
+            sv.step(0.0)
+
+    for _ in range(args.warmup):
+        per()
+    ms_p = timed(per, args.steps)
+    for sv in ss:
+        sv.close()
+    return {"workload": "64 2D viscous shock-bubble instances, 128x64..768x384, N 3-5, seed 0",
+            "instances": len(cs), "cells": cells, "unit": UNIT,
+            "value": cells * 3 / (ms_b * 1e-3), "per_instance_value": cells * 3 / (ms_p * 1e-3),
+            "speedup": ms_p / ms_b, "ms_per_step": ms_b, "per_instance_ms_per_step": ms_p,
+            "autotuned_shape": {"block_threads": shape[0], "tile_w": shape[1], "tile_h": shape[2]},
+            "candidates_ms_per_step": [round(x, 2) for x in ms_cand],
+            "cuda_graph": graph, "status_flags": st_b}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -242,6 +295,8 @@ def run_ours(args):
         e2e_s = float(t.item())
     e2e_val = ws * case.cells * 3 * e2e_steps / e2e_s
     io_bytes = (case.n_v + 1) * case.cells * 8
+    s.close()
+    batched = None if args.no_batch else _batched_vs_per_instance(args, dev, stream)
 
     if rank == 0:
         cpu = None
@@ -282,8 +337,9 @@ def run_ours(args):
         }
         if cpu is not None:
             line["cpu_baseline"] = cpu
+        if batched is not None:
+            line["batched"] = batched
         print(json.dumps(line), flush=True)
-    s.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
@@ -297,6 +353,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="sbi3d_n5")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-per-instance leg")
     ap.add_argument("--grid", default="", help="override the grid, e.g. 160,80,80 (profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)  # at least three untimed warm-up steps
