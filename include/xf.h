@@ -151,6 +151,30 @@ xf_status xf_compute_dt(xf_handle *h, double *dt_dev, void *stream);
  * receives the step used. No host synchronisation. */
 xf_status xf_step_rk3(xf_handle *h, double dt, double *dt_dev_out, void *stream);
 
+/* ---- Adjoint (vector-Jacobian products). All arrays are device
+ * arrays [n_v][cells]; results ACCUMULATE into the bar arrays (gradient
+ * convention). Non-smooth points follow fixed conventions: the LLF maximum
+ * passes its adjoint to the first maximal stencil cell, d|x|/dx = 0 at 0.
+ *
+ * U_bar += (dL/dU)^T dUdt_bar at the state U (Eq. 13-15, 3-6 reversed, the
+ * Newton temperature of Eq. 21 through the implicit-function theorem). The
+ * handle's state is untouched. Allocates the adjoint buffers on first use. */
+xf_status xf_rhs_adjoint(xf_handle *h, const double *U, const double *dUdt_bar,
+                         double *U_bar, void *stream);
+/* Reverse of one fixed-dt SSP-RK3 step (Eq. 16) taken from the handle's
+ * current state U^n: on entry U_bar holds dJ/dU^{n+1}, on return dJ/dU^n.
+ * Recomputes the two intermediate stage states itself; dt > 0 (the adjoint
+ * assumes the frozen time step). */
+xf_status xf_step_rk3_adjoint(xf_handle *h, double dt, double *U_bar, void *stream);
+/* Mixing measure J = sum_cells Y_s (1 - Y_s) dV of species `species` (0-based)
+ * for the state U: J_dev (device, one double) = J, U_bar = dJ/dU (overwritten). */
+xf_status xf_objective_mixing(xf_handle *h, const double *U, int species,
+                              double *J_dev, double *U_bar, void *stream);
+/* Reverse of xf_set_primitive's EOS conversion at primitives P:
+ * P_bar = (dU/dP)^T U_bar (overwritten). */
+xf_status xf_set_primitive_adjoint(xf_handle *h, const double *P, const double *U_bar,
+                                   double *P_bar, void *stream);
+
 /* Synchronise `stream` and return the OR of device status bits since the last
  * xf_clear_status; the return value maps the lowest set bit to an xf_status. */
 xf_status xf_get_status(xf_handle *h, uint32_t *flags, void *stream);
@@ -160,12 +184,14 @@ xf_status xf_clear_status(xf_handle *h, void *stream);
  * bracketed by two CUDA events on its stream (no synchronisation). Reading
  * synchronises on the recorded events, returns the summed milliseconds and
  * launch counts per kernel class (arrays of XF_PROF_SLOTS) and resets them. */
-#define XF_PROF_SLOTS 8
+#define XF_PROF_SLOTS 10
 #define XF_PROF_PRIM 0   /* primitive recovery + transport (+ CFL reduction) */
 #define XF_PROF_DT 1     /* time-step finalisation */
 #define XF_PROF_GRAD 2   /* nodal velocity derivatives */
 #define XF_PROF_FACE_X 3 /* face fluxes, x (y = 4, z = 5) */
 #define XF_PROF_UPDATE 6 /* conservative difference + RK3 combination */
+#define XF_PROF_FACE_ADJ 7 /* face-flux adjoints (all directions) */
+#define XF_PROF_PRIM_ADJ 8 /* primitive-recovery adjoint */
 xf_status xf_profile_enable(xf_handle *h, int on);
 xf_status xf_profile_read(xf_handle *h, double *ms, int64_t *launches);
 

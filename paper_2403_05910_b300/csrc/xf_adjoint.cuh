@@ -1,0 +1,986 @@
+// xf_adjoint.cuh -- reverse mode (vector-Jacobian product) of the RHS stage.
+//
+// Ubar += scale * (dL/dU)^T Rbar, written by hand in the reverse order of the
+// forward kernels in xf_device.cuh:
+//   k_face_adj<D>: per face, recompute the forward face quantities, then walk
+//     back through the back-projection (Eq. 15), the two WENO5-JS
+//     reconstructions of every field (weights included), the PER projection
+//     and LLF splitting (Eq. 14, alpha through the arg-max cell, first maximum
+//     on ties, d|x|/dx = 0 at 0), the Roe-averaged face state and its thermo,
+//     and the viscous face flux; adjoints of the per-cell fields are
+//     scattered with atomicAdd into Qbar (same layout as Q).
+//   k_grad_adj: gather form of the nodal-derivative adjoint (no atomics).
+//   k_prim_adj: per padded cell, the adjoint of primitive recovery: transport
+//     (Eq. 29, Wilke Eq. 22), EOS (Eq. 7), sound speed, and the Newton
+//     temperature through the implicit-function theorem (dT = (de - sum_s e_s
+//     dY_s)/c_v); scattered into Ubar through the boundary mapping.
+#pragma once
+#include "xf_device.cuh"
+
+namespace xf {
+
+// ------------------------------------------------------------ WENO5 adjoint
+// Reverse of weno5_nd: given (nbar, dbar) for (num, den), add df.
+__device__ __forceinline__ void weno5_nd_adj(const double* f, double eps12, double nbar,
+                                             double dbar, double* fb) {
+  const double a = f[1] - f[0], b = f[2] - f[1], c = f[3] - f[2], d = f[4] - f[3];
+  const double t0 = b - a, u0 = fma(3.0, b, -a);
+  const double t1 = c - b, u1 = b + c;
+  const double t2 = d - c, u2 = fma(-3.0, c, d);
+  const double s0 = fma(13.0 * t0, t0, fma(3.0 * u0, u0, eps12));
+  const double s1 = fma(13.0 * t1, t1, fma(3.0 * u1, u1, eps12));
+  const double s2 = fma(13.0 * t2, t2, fma(3.0 * u2, u2, eps12));
+  const double p12 = s1 * s2, p02 = s0 * s2, p01 = s0 * s1;
+  const double w0 = (0.1 * p12) * p12, w1 = (0.6 * p02) * p02, w2 = (0.3 * p01) * p01;
+  const double q0 = fma(5.0 / 6.0, b, (-1.0 / 3.0) * a);
+  const double q1 = fma(1.0 / 3.0, c, (1.0 / 6.0) * b);
+  const double q2 = fma(2.0 / 3.0, c, (-1.0 / 6.0) * d);
+  const double w0b = fma(nbar, q0, dbar), w1b = fma(nbar, q1, dbar), w2b = fma(nbar, q2, dbar);
+  const double q0b = nbar * w0, q1b = nbar * w1, q2b = nbar * w2;
+  const double p12b = w0b * 0.2 * p12, p02b = w1b * 1.2 * p02, p01b = w2b * 0.6 * p01;
+  const double s0b = fma(p02b, s2, p01b * s1);
+  const double s1b = fma(p12b, s2, p01b * s0);
+  const double s2b = fma(p12b, s1, p02b * s0);
+  const double t0b = 26.0 * t0 * s0b, u0b = 6.0 * u0 * s0b;
+  const double t1b = 26.0 * t1 * s1b, u1b = 6.0 * u1 * s1b;
+  const double t2b = 26.0 * t2 * s2b, u2b = 6.0 * u2 * s2b;
+  const double ab = -t0b - u0b - (1.0 / 3.0) * q0b;
+  const double bb = t0b + 3.0 * u0b - t1b + u1b + (5.0 / 6.0) * q0b + (1.0 / 6.0) * q1b;
+  const double cb = t1b + u1b - t2b - 3.0 * u2b + (1.0 / 3.0) * q1b + (2.0 / 3.0) * q2b;
+  const double db = t2b + u2b - (1.0 / 6.0) * q2b;
+  fb[0] -= ab;
+  fb[1] += ab - bb;
+  fb[2] += bb - cb;
+  fb[3] += cb - db;
+  fb[4] += db;
+}
+
+// Reverse of weno5_pair (F = wp2 + wm3 + np/dp + nm/dm): adds to wpb[0..5], wmb[0..5].
+__device__ __forceinline__ void weno5_pair_adj(const double* wp, const double* wm, double eps12,
+                                               double Fb, double* wpb, double* wmb) {
+  double np, dp, nm, dm;
+  weno5_nd(wp[0], wp[1], wp[2], wp[3], wp[4], eps12, np, dp);
+  weno5_nd(wm[5], wm[4], wm[3], wm[2], wm[1], eps12, nm, dm);
+  const double idp = 1.0 / dp, idm = 1.0 / dm;
+  double fb[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  weno5_nd_adj(wp, eps12, Fb * idp, -Fb * np * idp * idp, fb);
+  for (int k = 0; k < 5; ++k) wpb[k] += fb[k];
+  wpb[2] += Fb;
+  const double fm[5] = {wm[5], wm[4], wm[3], wm[2], wm[1]};
+  double gb[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  weno5_nd_adj(fm, eps12, Fb * idm, -Fb * nm * idm * idm, gb);
+  wmb[5] += gb[0];
+  wmb[4] += gb[1];
+  wmb[3] += gb[2] + Fb;
+  wmb[2] += gb[3];
+  wmb[1] += gb[4];
+}
+
+// d c_p,s / dT at a clamped tau (0 outside the polynomial range)
+__device__ __forceinline__ double dcp_s(const Params& p, int s, double T) {
+  const double tau = (T - p.T_lo) * p.inv_span;
+  if (!(tau > 0.0 && tau < 1.0)) return 0.0;
+  const double* a = p.rcp[s];
+  return fma(fma(fma(4.0 * a[4], tau, 3.0 * a[3]), tau, 2.0 * a[2]), tau, a[1]) * p.inv_span;
+}
+
+__device__ __forceinline__ void aadd(double* p, double v) {
+  if (v != 0.0) atomicAdd(p, v);
+}
+
+
+// ================================================================ k_face_adj
+// Per face of direction D: Gbar = scale (Rbar_right - Rbar_left)/dx (Rbar = 0
+// outside the interior), then the reverse of face_one.
+template <int DIM, int NS, int D>
+__device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk,
+                                         const double* __restrict__ Q,
+                                         const double* __restrict__ Rbar, double scale,
+                                         double* __restrict__ Qb) {
+  using L = Lay<DIM, NS>;
+  constexpr int NV = L::NV;
+  constexpr int IE = DIM + 1;
+  int id[3] = {fi, fj, fk};
+  id[D] -= 1;  // left cell
+  const long long PC = p.pcells;
+  const long long sy = p.np[0], sz = (long long)p.np[0] * p.np[1];
+  const long long c0 = (id[2] + p.go[2]) * sz + (id[1] + p.go[1]) * sy + (id[0] + p.go[0]);
+  const long long sd = D == 0 ? 1 : (D == 1 ? sy : sz);
+  // ---- Gbar from the residual adjoint of the two neighbouring cells
+  double Gb[NV];
+  {
+    const long long C = p.cells;
+    const long long ci = ((long long)id[2] * p.n[1] + id[1]) * p.n[0] + id[0];
+    const long long cstep = D == 0 ? 1 : (D == 1 ? p.n[0] : (long long)p.n[0] * p.n[1]);
+    const bool lin = id[D] >= 0, rin = id[D] + 1 < p.n[D];
+    const double w = scale * p.inv_dx[D];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const double rr = rin ? Rbar[v * C + ci + cstep] : 0.0;
+      const double rl = lin ? Rbar[v * C + ci] : 0.0;
+      Gb[v] = (rr - rl) * w;
+    }
+  }
+  const double* q0 = Q + c0;
+  double* qb0 = Qb + c0;
+#define QF(field, m) ld(q0 + (long long)(field) * PC + (long long)(m) * sd)
+#define QB(field, m, val) aadd(qb0 + (long long)(field) * PC + (long long)(m) * sd, (val))
+  if (p.convective) {
+    // ================= forward recomputation =================
+    const double sL = QF(L::SR, 0), sR = QF(L::SR, 1);
+    const double iw = 1.0 / (sL + sR);
+    const double tL = sL * iw, tR = sR * iw;
+    double uL[DIM], uR[DIM], ub[DIM], q2 = 0.0;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      uL[a] = QF(L::UN + a, 0);
+      uR[a] = QF(L::UN + a, 1);
+      ub[a] = fma(tL, uL[a], tR * uR[a]);
+      q2 = fma(ub[a], ub[a], q2);
+    }
+    const double HL = QF(L::H, 0), HR = QF(L::H, 1), TL = QF(L::T, 0), TR = QF(L::T, 1);
+    const double Hb = fma(tL, HL, tR * HR);
+    const double Tb = fma(tL, TL, tR * TR);
+    double YL[NS], YR[NS], Yb[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      YL[s] = QF(L::Y + s, 0);
+      YR[s] = QF(L::Y + s, 1);
+      Yb[s] = fma(tL, YL[s], tR * YR[s]);
+    }
+    const TauPt tp = tau_of(p, Tb);
+    double es[NS], cps[NS], Rb = 0.0, cvb = 0.0;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      cps[s] = cp_s(p, s, tp.tc);
+      es[s] = h_s(p, s, tp, cps[s]) - p.r[s] * Tb;
+      Rb = fma(Yb[s], p.r[s], Rb);
+      cvb = fma(Yb[s], cps[s] - p.r[s], cvb);
+    }
+    const double Gam = Rb / cvb;
+    const double hq2 = 0.5 * q2;
+    double phi[NS], c2 = 0.0;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      phi[s] = fma(p.r[s], Tb, -Gam * (es[s] - hq2));
+      c2 = fma(Yb[s], phi[s], c2);
+    }
+    c2 = fma(Gam, Hb - q2, c2);
+    bool fallback = false;
+    double cl = 0.0, cr = 0.0;
+    if (!(c2 > 0.0)) {
+      fallback = true;
+      cl = QF(L::C, 0);
+      cr = QF(L::C, 1);
+      c2 = 0.5 * (cl * cl + cr * cr);
+    }
+    const double c = sqrt(c2);
+    const double ic2 = 1.0 / c2;
+    const double hic2 = 0.5 * ic2;
+    const double iGam = cvb / Rb;
+    const double un = ub[D];
+    const double phiN = phi[NS - 1];
+    double gm[DIM], dphi[NS > 1 ? NS - 1 : 1], gs[NS > 1 ? NS - 1 : 1];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) gm[a] = -Gam * ub[a] * hic2;
+#pragma unroll
+    for (int s = 0; s < NS - 1; ++s) { dphi[s] = phi[s] - phiN; gs[s] = dphi[s] * hic2; }
+    const double gr = phiN * hic2, gE = Gam * hic2;
+    double rho_m[6], p_m[6], hun[6], gUh[6], unm[6], cmv[6];
+    double am = 0.0, ap = 0.0, a0 = 0.0;
+    int im = 0, ipp = 0, i0 = 0;
+#pragma unroll
+    for (int m = 0; m < 6; ++m) {
+      const int o = m - 2;
+      rho_m[m] = QF(L::U, o);
+      unm[m] = QF(L::UN + D, o);
+      p_m[m] = QF(L::P, o);
+      cmv[m] = QF(L::C, o);
+      const double xm = fabs(unm[m] - cmv[m]), xp = fabs(unm[m] + cmv[m]), x0 = fabs(unm[m]);
+      if (m == 0 || xm > am) { am = xm; im = m; }
+      if (m == 0 || xp > ap) { ap = xp; ipp = m; }
+      if (m == 0 || x0 > a0) { a0 = x0; i0 = m; }
+      hun[m] = 0.5 * unm[m];
+      double g = gr * rho_m[m];
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) g = fma(gm[a], QF(L::U + 1 + a, o), g);
+      g = fma(gE, QF(L::U + IE, o), g);
+#pragma unroll
+      for (int s = 0; s < NS - 1; ++s) g = fma(gs[s], QF(L::U + IE + 1 + s, o), g);
+      gUh[m] = g;
+    }
+    const double eps12 = 12.0 * p.weno_eps;
+    const double chc = c * hic2;
+    const double ha_m = 0.5 * am, ha_p = 0.5 * ap, ha0 = 0.5 * a0;
+    const double hlmn_m = 0.5 * (-Gam * un - c) * hic2, hlmn_p = 0.5 * (-Gam * un + c) * hic2;
+    const double lE_a = Gam * hic2;
+    const double hlmn_e = 0.5 * Gam * un * ic2, lE_e = -Gam * ic2;
+    double wp[6], wm[6];
+    // the three dense fields' reconstructions (needed by the back-projection adjoint)
+    double Fm, Fp, Fe;
+    for (int fld = 0; fld < 3; ++fld) {
+      const double ha = fld == 0 ? ha_m : (fld == 1 ? ha_p : ha0);
+      const double hl = fld == 0 ? hlmn_m : (fld == 1 ? hlmn_p : hlmn_e);
+      const double lE = fld == 2 ? lE_e : lE_a;
+#pragma unroll
+      for (int m = 0; m < 6; ++m) {
+        double LU;
+        if (fld == 2) {
+          LU = fma(-2.0, gUh[m], rho_m[m]);
+        } else {
+          const double nU = fma(-un, rho_m[m], QF(L::U + 1 + D, m - 2));
+          LU = fma(fld == 0 ? -chc : chc, nU, gUh[m]);
+        }
+        const double pq = p_m[m] * fma(hun[m], lE, hl);
+        wp[m] = fma(hun[m] + ha, LU, pq);
+        wm[m] = fma(hun[m] - ha, LU, pq);
+      }
+      const double F = weno5_pair(wp, wm, eps12);
+      if (fld == 0) Fm = F; else if (fld == 1) Fp = F; else Fe = F;
+    }
+    // ================= reverse =================
+    // back-projection of the dense columns
+    const double S = Fm + Fp + Fe, Dl = Fp - Fm;
+    double Sb = Gb[0] + Hb * Gb[IE];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) Sb = fma(ub[a], Gb[1 + a], Sb);
+#pragma unroll
+    for (int s = 0; s < NS - 1; ++s) Sb = fma(Yb[s], Gb[IE + 1 + s], Sb);
+    const double Dlb = c * Gb[1 + D] + un * c * Gb[IE];
+    double ubb[DIM], Ybb[NS];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) ubb[a] = S * Gb[1 + a];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) Ybb[s] = 0.0;
+#pragma unroll
+    for (int s = 0; s < NS - 1; ++s) Ybb[s] = S * Gb[IE + 1 + s];
+    double cb = Dl * Gb[1 + D] + un * Dl * Gb[IE];
+    double Hbb = S * Gb[IE];
+    double unb = c * Dl * Gb[IE];
+    double c2b = -iGam * Fe * Gb[IE];
+    double iGamb = -c2 * Fe * Gb[IE];
+    const double Fmb = Sb - Dlb, Fpb = Sb + Dlb, Feb = Sb - c2 * iGam * Gb[IE];
+    // per-field reverse; stencil adjoints accumulated here
+    double rhob[6], pb[6], hunb[6], gUhb[6], mnb[6];
+#pragma unroll
+    for (int m = 0; m < 6; ++m) { rhob[m] = 0.0; pb[m] = 0.0; hunb[m] = 0.0; gUhb[m] = 0.0; mnb[m] = 0.0; }
+    double hamb = 0.0, hapb = 0.0, ha0b = 0.0, chcb = 0.0, Gamb = 0.0, hic2b = 0.0, ic2b = 0.0;
+    for (int fld = 0; fld < 3; ++fld) {
+      const double ha = fld == 0 ? ha_m : (fld == 1 ? ha_p : ha0);
+      const double hl = fld == 0 ? hlmn_m : (fld == 1 ? hlmn_p : hlmn_e);
+      const double lE = fld == 2 ? lE_e : lE_a;
+      const double Fb = fld == 0 ? Fmb : (fld == 1 ? Fpb : Feb);
+      double LUv[6], nUv[6];
+#pragma unroll
+      for (int m = 0; m < 6; ++m) {
+        double LU, nU = 0.0;
+        if (fld == 2) {
+          LU = fma(-2.0, gUh[m], rho_m[m]);
+        } else {
+          nU = fma(-un, rho_m[m], QF(L::U + 1 + D, m - 2));
+          LU = fma(fld == 0 ? -chc : chc, nU, gUh[m]);
+        }
+        LUv[m] = LU;
+        nUv[m] = nU;
+        const double pq = p_m[m] * fma(hun[m], lE, hl);
+        wp[m] = fma(hun[m] + ha, LU, pq);
+        wm[m] = fma(hun[m] - ha, LU, pq);
+      }
+      double wpb[6] = {0, 0, 0, 0, 0, 0}, wmb[6] = {0, 0, 0, 0, 0, 0};
+      weno5_pair_adj(wp, wm, eps12, Fb, wpb, wmb);
+      double hab = 0.0, hlb = 0.0, lEb = 0.0;
+#pragma unroll
+      for (int m = 0; m < 6; ++m) {
+        const double LUb = wpb[m] * (hun[m] + ha) + wmb[m] * (hun[m] - ha);
+        const double pqb = wpb[m] + wmb[m];
+        hunb[m] += pqb * LUv[m] + pqb * p_m[m] * lE;
+        hab += (wpb[m] - wmb[m]) * LUv[m];
+        pb[m] += pqb * fma(hun[m], lE, hl);
+        lEb += pqb * p_m[m] * hun[m];
+        hlb += pqb * p_m[m];
+        if (fld == 2) {
+          rhob[m] += LUb;
+          gUhb[m] -= 2.0 * LUb;
+        } else {
+          const double sgn = fld == 0 ? -1.0 : 1.0;
+          gUhb[m] += LUb;
+          chcb += sgn * LUb * nUv[m];
+          const double nUb = sgn * chc * LUb;
+          mnb[m] += nUb;
+          unb -= nUb * rho_m[m];
+          rhob[m] -= nUb * un;
+        }
+      }
+      if (fld == 2) {
+        ha0b += hab;
+        // hl = Gam un ic2 / 2, lE = -Gam ic2
+        Gamb += hlb * 0.5 * un * ic2 - lEb * ic2;
+        unb += hlb * 0.5 * Gam * ic2;
+        ic2b += hlb * 0.5 * Gam * un - lEb * Gam;
+      } else {
+        const double sgn = fld == 0 ? -1.0 : 1.0;
+        if (fld == 0) hamb += hab; else hapb += hab;
+        // hl = (-Gam un + sgn c) hic2 / 2, lE = Gam hic2
+        Gamb += hlb * (-0.5 * un * hic2) + lEb * hic2;
+        unb += hlb * (-0.5 * Gam * hic2);
+        cb += hlb * 0.5 * sgn * hic2;
+        hic2b += hlb * 0.5 * (-Gam * un + sgn * c) + lEb * Gam;
+      }
+    }
+    // tangential momenta and species (eigenvalue u, no pressure term)
+    double hp0b[6], hm0b[6];
+#pragma unroll
+    for (int m = 0; m < 6; ++m) { hp0b[m] = 0.0; hm0b[m] = 0.0; }
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      if (a == D) continue;
+      const double Fb = Gb[1 + a] + ub[a] * Gb[IE];
+      double LUv[6];
+#pragma unroll
+      for (int m = 0; m < 6; ++m) {
+        LUv[m] = fma(-ub[a], rho_m[m], QF(L::U + 1 + a, m - 2));
+        wp[m] = (hun[m] + ha0) * LUv[m];
+        wm[m] = (hun[m] - ha0) * LUv[m];
+      }
+      const double Fk = weno5_pair(wp, wm, eps12);
+      ubb[a] += Fk * Gb[IE];
+      double wpb[6] = {0, 0, 0, 0, 0, 0}, wmb[6] = {0, 0, 0, 0, 0, 0};
+      weno5_pair_adj(wp, wm, eps12, Fb, wpb, wmb);
+#pragma unroll
+      for (int m = 0; m < 6; ++m) {
+        const double LUb = wpb[m] * (hun[m] + ha0) + wmb[m] * (hun[m] - ha0);
+        hp0b[m] += wpb[m] * LUv[m];
+        hm0b[m] += wmb[m] * LUv[m];
+        QB(L::U + 1 + a, m - 2, LUb);
+        ubb[a] -= LUb * rho_m[m];
+        rhob[m] -= LUb * ub[a];
+      }
+    }
+    double dphib[NS > 1 ? NS - 1 : 1];
+#pragma unroll
+    for (int s = 0; s < NS - 1; ++s) {
+      const double Fb = Gb[IE + 1 + s] - dphi[s] * iGam * Gb[IE];
+      double LUv[6];
+#pragma unroll
+      for (int m = 0; m < 6; ++m) {
+        LUv[m] = fma(-Yb[s], rho_m[m], QF(L::U + IE + 1 + s, m - 2));
+        wp[m] = (hun[m] + ha0) * LUv[m];
+        wm[m] = (hun[m] - ha0) * LUv[m];
+      }
+      const double Fk = weno5_pair(wp, wm, eps12);
+      dphib[s] = -iGam * Fk * Gb[IE];
+      iGamb -= dphi[s] * Fk * Gb[IE];
+      double wpb[6] = {0, 0, 0, 0, 0, 0}, wmb[6] = {0, 0, 0, 0, 0, 0};
+      weno5_pair_adj(wp, wm, eps12, Fb, wpb, wmb);
+#pragma unroll
+      for (int m = 0; m < 6; ++m) {
+        const double LUb = wpb[m] * (hun[m] + ha0) + wmb[m] * (hun[m] - ha0);
+        hp0b[m] += wpb[m] * LUv[m];
+        hm0b[m] += wmb[m] * LUv[m];
+        QB(L::U + IE + 1 + s, m - 2, LUb);
+        Ybb[s] -= LUb * rho_m[m];
+        rhob[m] -= LUb * Yb[s];
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < 6; ++m) {
+      hunb[m] += hp0b[m] + hm0b[m];
+      ha0b += hp0b[m] - hm0b[m];
+    }
+    // stencil preparation
+    cb += chcb * hic2;
+    hic2b += chcb * c;
+    double grb = 0.0, gEb = 0.0, gmb[DIM], gsb[NS > 1 ? NS - 1 : 1];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) gmb[a] = 0.0;
+#pragma unroll
+    for (int s = 0; s < NS - 1; ++s) gsb[s] = 0.0;
+#pragma unroll
+    for (int m = 0; m < 6; ++m) {
+      const int o = m - 2;
+      const double g = gUhb[m];
+      grb += g * rho_m[m];
+      rhob[m] += g * gr;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        gmb[a] += g * QF(L::U + 1 + a, o);
+        double v = g * gm[a];
+        if (a == D) v += mnb[m];
+        QB(L::U + 1 + a, o, v);
+      }
+      gEb += g * QF(L::U + IE, o);
+      QB(L::U + IE, o, g * gE);
+#pragma unroll
+      for (int s = 0; s < NS - 1; ++s) {
+        gsb[s] += g * QF(L::U + IE + 1 + s, o);
+        QB(L::U + IE + 1 + s, o, g * gs[s]);
+      }
+      QB(L::U, o, rhob[m]);
+      QB(L::P, o, pb[m]);
+      double unmb = 0.5 * hunb[m];
+      double cmb = 0.0;
+      if (m == im) { const double sg = unm[m] - cmv[m] > 0.0 ? 1.0 : (unm[m] - cmv[m] < 0.0 ? -1.0 : 0.0); unmb += 0.5 * hamb * sg; cmb -= 0.5 * hamb * sg; }
+      if (m == ipp) { const double sg = unm[m] + cmv[m] > 0.0 ? 1.0 : (unm[m] + cmv[m] < 0.0 ? -1.0 : 0.0); unmb += 0.5 * hapb * sg; cmb += 0.5 * hapb * sg; }
+      if (m == i0) { const double sg = unm[m] > 0.0 ? 1.0 : (unm[m] < 0.0 ? -1.0 : 0.0); unmb += 0.5 * ha0b * sg; }
+      QB(L::UN + D, o, unmb);
+      QB(L::C, o, cmb);
+    }
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      Gamb -= gmb[a] * ub[a] * hic2;
+      ubb[a] -= gmb[a] * Gam * hic2;
+      hic2b -= gmb[a] * Gam * ub[a];
+    }
+    double phib[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) phib[s] = 0.0;
+#pragma unroll
+    for (int s = 0; s < NS - 1; ++s) {
+      const double db = dphib[s] + gsb[s] * hic2;
+      hic2b += gsb[s] * dphi[s];
+      phib[s] += db;
+      phib[NS - 1] -= db;
+    }
+    phib[NS - 1] += grb * hic2;
+    hic2b += grb * phiN + gEb * Gam;
+    Gamb += gEb * hic2;
+    // Roe state
+    ic2b += 0.5 * hic2b;
+    c2b -= ic2b * ic2 * ic2;
+    double cvbb = iGamb / Rb, Rbb = -iGamb * cvb / (Rb * Rb);
+    c2b += cb * 0.5 / c;
+    ubb[D] += unb;
+    double Tbb = 0.0, q2b = 0.0;
+    if (fallback) {
+      QB(L::C, 0, c2b * cl);
+      QB(L::C, 1, c2b * cr);
+    } else {
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        Ybb[s] += c2b * phi[s];
+        phib[s] += c2b * Yb[s];
+      }
+      Gamb += c2b * (Hb - q2);
+      Hbb += c2b * Gam;
+      q2b -= c2b * Gam;
+    }
+    double hq2b = 0.0;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      Tbb += phib[s] * p.r[s];
+      Gamb -= phib[s] * (es[s] - hq2);
+      hq2b += phib[s] * Gam;
+      const double esb = -phib[s] * Gam;
+      Tbb += esb * (cps[s] - p.r[s]);
+    }
+    q2b += 0.5 * hq2b;
+    Rbb += Gamb / cvb;
+    cvbb -= Gamb * Gam / cvb;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      Ybb[s] += Rbb * p.r[s] + cvbb * (cps[s] - p.r[s]);
+      Tbb += cvbb * Yb[s] * dcp_s(p, s, Tb);
+    }
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) ubb[a] += 2.0 * ub[a] * q2b;
+    double tLb = 0.0, tRb = 0.0;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      QB(L::UN + a, 0, tL * ubb[a]);
+      QB(L::UN + a, 1, tR * ubb[a]);
+      tLb += ubb[a] * uL[a];
+      tRb += ubb[a] * uR[a];
+    }
+    QB(L::H, 0, tL * Hbb);
+    QB(L::H, 1, tR * Hbb);
+    tLb += Hbb * HL;
+    tRb += Hbb * HR;
+    QB(L::T, 0, tL * Tbb);
+    QB(L::T, 1, tR * Tbb);
+    tLb += Tbb * TL;
+    tRb += Tbb * TR;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      QB(L::Y + s, 0, tL * Ybb[s]);
+      QB(L::Y + s, 1, tR * Ybb[s]);
+      tLb += Ybb[s] * YL[s];
+      tRb += Ybb[s] * YR[s];
+    }
+    const double iwb = tLb * sL + tRb * sR;
+    QB(L::SR, 0, tLb * iw - iwb * iw * iw);
+    QB(L::SR, 1, tRb * iw - iwb * iw * iw);
+  }
+
+  if (p.viscous) {
+    const double wi = 1.0 / 16.0;
+    const double wd = p.inv_dx[D] * (1.0 / 12.0);
+    // face interpolation / normal derivative coefficients for cells -1..2
+    const double ci[4] = {-wi, 9.0 * wi, 9.0 * wi, -wi};
+    const double cd[4] = {wd, -15.0 * wd, 15.0 * wd, -wd};
+#define FI(field) ((9.0 * (QF(field, 0) + QF(field, 1)) - (QF(field, -1) + QF(field, 2))) * wi)
+#define FD(field) ((15.0 * (QF(field, 1) - QF(field, 0)) - (QF(field, 2) - QF(field, -1))) * wd)
+#define BI(field, val) { const double v_ = (val); for (int m_ = 0; m_ < 4; ++m_) QB(field, m_ - 1, ci[m_] * v_); }
+#define BD(field, val) { const double v_ = (val); for (int m_ = 0; m_ < 4; ++m_) QB(field, m_ - 1, cd[m_] * v_); }
+    const double mu = FI(L::MU), ka = FI(L::KA), Df = FI(L::DF), rf = FI(L::U), Tf = FI(L::T);
+    double uf[DIM], gr[DIM][DIM];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      uf[a] = FI(L::UN + a);
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) gr[a][b] = (b == D) ? FD(L::UN + a) : FI(L::GU + a * DIM + b);
+    }
+    double div = 0.0;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) div += gr[a][a];
+    double tau[DIM];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      tau[a] = mu * (gr[D][a] + gr[a][D]);
+      if (a == D) tau[a] = fma(-2.0 / 3.0 * mu, div, tau[a]);
+    }
+    double dY[NS], Yf[NS], sdY = 0.0;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) { dY[s] = FD(L::Y + s); Yf[s] = FI(L::Y + s); sdY += dY[s]; }
+    const double corr = Df * sdY;
+    const TauPt tp = tau_of(p, Tf);
+    const double dT = FD(L::T);
+    // reverse: Gout[IE] -= ka dT + work - qd; Gout[1+a] -= tau_a; Gout[IE+1+s] += J_s
+    const double workb = -Gb[IE], kab = -Gb[IE] * dT, dTb = -Gb[IE] * ka, qdb = Gb[IE];
+    double Tfb = 0.0, rfb = 0.0, Dfb = 0.0, corrb = 0.0, mub = 0.0, divb = 0.0;
+    double dYb[NS], Yfb[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      const double J = -rf * fma(Df, dY[s], -Yf[s] * corr);
+      const double cps = cp_s(p, s, tp.tc);
+      const double hs = h_s(p, s, tp, cps);
+      double Jb = qdb * hs + (s < NS - 1 ? Gb[IE + 1 + s] : 0.0);
+      Tfb += qdb * J * cps;
+      rfb -= Jb * (Df * dY[s] - Yf[s] * corr);
+      Dfb -= Jb * rf * dY[s];
+      dYb[s] = -Jb * rf * Df;
+      Yfb[s] = Jb * rf * corr;
+      corrb += Jb * rf * Yf[s];
+    }
+    Dfb += corrb * sdY;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) dYb[s] += corrb * Df;
+    double grb[DIM][DIM];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a)
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) grb[a][b] = 0.0;
+    double ufb[DIM];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      const double taub = workb * uf[a] - Gb[1 + a];
+      ufb[a] = workb * tau[a];
+      mub += taub * (gr[D][a] + gr[a][D]);
+      grb[D][a] += taub * mu;
+      grb[a][D] += taub * mu;
+      if (a == D) {
+        mub -= (2.0 / 3.0) * taub * div;
+        divb -= (2.0 / 3.0) * mu * taub;
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) grb[a][a] += divb;
+    BI(L::MU, mub);
+    BI(L::KA, kab);
+    BI(L::DF, Dfb);
+    BI(L::U, rfb);
+    BI(L::T, Tfb);
+    BD(L::T, dTb);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      BI(L::UN + a, ufb[a]);
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) {
+        if (b == D) { BD(L::UN + a, grb[a][b]); }
+        else { BI(L::GU + a * DIM + b, grb[a][b]); }
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      BD(L::Y + s, dYb[s]);
+      BI(L::Y + s, Yfb[s]);
+    }
+#undef FI
+#undef FD
+#undef BI
+#undef BD
+  }
+#undef QF
+#undef QB
+}
+
+template <int DIM, int NS, int D>
+__global__ void __launch_bounds__(128)
+k_face_adj(const __grid_constant__ Params p, const double* __restrict__ Q,
+           const double* __restrict__ Rbar, double scale, double* __restrict__ Qb) {
+  const int nf0 = p.n[0] + (D == 0), nf1 = p.n[1] + (D == 1), nf2 = p.n[2] + (D == 2);
+  const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= (long long)nf0 * nf1 * nf2) return;
+  face_adj<DIM, NS, D>(p, (int)(f % nf0), (int)((f / nf0) % nf1), (int)(f / ((long long)nf0 * nf1)),
+                       Q, Rbar, scale, Qb);
+}
+
+// ================================================================ k_prim_adj
+// Per padded cell t: Qbar (all fields of this cell) -> Ubar of its interior
+// source cell (with the symmetric-mirror sign flips).
+template <int DIM, int NS>
+__device__ __forceinline__ void prim_adj_cell(const Params& p, long long t,
+                                              const double* __restrict__ Q,
+                                              const double* __restrict__ Qb,
+                                              double* __restrict__ Ubar) {
+  using L = Lay<DIM, NS>;
+  constexpr int NV = L::NV;
+  const long long PC = p.pcells;
+  const int ip = (int)(t % p.np[0]);
+  const int jp = (int)((t / p.np[0]) % p.np[1]);
+  const int kp = (int)(t / ((long long)p.np[0] * p.np[1]));
+  const int i = ip - p.go[0], j = jp - p.go[1], k = kp - p.go[2];
+  bool f0 = false, f1 = false, f2 = false;
+  const int si = map_axis(i, p.n[0], p.bc[0][0], p.bc[0][1], &f0);
+  const int sj = DIM > 1 ? map_axis(j, p.n[1], p.bc[1][0], p.bc[1][1], &f1) : 0;
+  const int sk = DIM > 2 ? map_axis(k, p.n[2], p.bc[2][0], p.bc[2][1], &f2) : 0;
+  const long long src = ((long long)sk * p.n[1] + sj) * p.n[0] + si;
+  const double* q = Q + t;
+  const double* qb = Qb + t;
+  // forward values of this cell
+  double u[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) u[v] = q[(L::U + v) * PC];
+  const double rho = u[0], irho = 1.0 / rho, E = u[DIM + 1];
+  double vel[DIM];
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) vel[a] = q[(L::UN + a) * PC];
+  double Y[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) Y[s] = q[(L::Y + s) * PC];
+  const double T = q[L::T * PC], pr = q[L::P * PC], c = q[L::C * PC];
+  const TauPt tp = tau_of(p, T);
+  double Rm = 0.0, cpm = 0.0, dcpm = 0.0, es[NS], cps[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    cps[s] = cp_s(p, s, tp.tc);
+    es[s] = h_s(p, s, tp, cps[s]) - p.r[s] * T;
+    Rm = fma(Y[s], p.r[s], Rm);
+    cpm = fma(Y[s], cps[s], cpm);
+    dcpm = fma(Y[s], dcp_s(p, s, T), dcpm);
+  }
+  const double cvm = cpm - Rm, RT = Rm * T;
+  // adjoint accumulators
+  double ub[NV], Yb[NS], velb[DIM];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) ub[v] = qb[(L::U + v) * PC];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) Yb[s] = qb[(L::Y + s) * PC];
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) velb[a] = qb[(L::UN + a) * PC];
+  double Tb = qb[L::T * PC], prb = qb[L::P * PC], cb = qb[L::C * PC];
+  double rhob = 0.0, Eb = 0.0, irhob = 0.0, cpmb = 0.0, Rmb = 0.0;
+  if (p.viscous) {
+    const double mub = qb[L::MU * PC], kab = qb[L::KA * PC], Db = qb[L::DF * PC];
+    // D = ka / (Le rho cp)
+    const double ka = q[L::KA * PC], Dd = q[L::DF * PC];
+    double kabar = kab + Db * p.inv_lewis / (rho * cpm);
+    rhob -= Db * Dd / rho;
+    cpmb -= Db * Dd / cpm;
+    // Wilke mixtures, recomputed
+    const double lnT = log(T);
+    double smu[NS], ska[NS], ismu[NS], iska[NS], X[NS], xs = 0.0, dlm[NS], dlk[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      const double lm = fma(fma(fma(p.lnmu[s][3], lnT, p.lnmu[s][2]), lnT, p.lnmu[s][1]), lnT, p.lnmu[s][0]);
+      const double lk = fma(fma(fma(p.lnka[s][3], lnT, p.lnka[s][2]), lnT, p.lnka[s][1]), lnT, p.lnka[s][0]);
+      dlm[s] = fma(fma(3.0 * p.lnmu[s][3], lnT, 2.0 * p.lnmu[s][2]), lnT, p.lnmu[s][1]);
+      dlk[s] = fma(fma(3.0 * p.lnka[s][3], lnT, 2.0 * p.lnka[s][2]), lnT, p.lnka[s][1]);
+      smu[s] = exp(0.5 * lm);
+      ska[s] = exp(0.5 * lk);
+      ismu[s] = 1.0 / smu[s];
+      iska[s] = 1.0 / ska[s];
+      X[s] = Y[s] * p.invW[s];
+      xs += X[s];
+    }
+    const double ixs = 1.0 / xs;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) X[s] *= ixs;
+    const double mtot = mub * p.fmu, ktot = kabar * p.fka;
+    double Xb[NS], smub[NS], skab[NS], ismub[NS], iskab[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) { Xb[s] = 0.0; smub[s] = 0.0; skab[s] = 0.0; ismub[s] = 0.0; iskab[s] = 0.0; }
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      double dm = 0.0, dk = 0.0;
+#pragma unroll
+      for (int tt = 0; tt < NS; ++tt) {
+        const double bm = fma(smu[s] * ismu[tt], p.wB[s][tt], 1.0);
+        const double bk = fma(ska[s] * iska[tt], p.wB[s][tt], 1.0);
+        const double xa = X[tt] * p.wA[s][tt];
+        dm = fma(xa, bm * bm, dm);
+        dk = fma(xa, bk * bk, dk);
+      }
+      // term_s = X_s smu_s^2 / dm_s
+      const double idm = 1.0 / dm, idk = 1.0 / dk;
+      const double tm = X[s] * smu[s] * smu[s] * idm, tk = X[s] * ska[s] * ska[s] * idk;
+      Xb[s] += mtot * smu[s] * smu[s] * idm + ktot * ska[s] * ska[s] * idk;
+      smub[s] += mtot * 2.0 * X[s] * smu[s] * idm;
+      skab[s] += ktot * 2.0 * X[s] * ska[s] * idk;
+      const double dmb = -mtot * tm * idm, dkb = -ktot * tk * idk;
+#pragma unroll
+      for (int tt = 0; tt < NS; ++tt) {
+        const double bm = fma(smu[s] * ismu[tt], p.wB[s][tt], 1.0);
+        const double bk = fma(ska[s] * iska[tt], p.wB[s][tt], 1.0);
+        Xb[tt] += p.wA[s][tt] * (dmb * bm * bm + dkb * bk * bk);
+        const double bmb = dmb * X[tt] * p.wA[s][tt] * 2.0 * bm;
+        const double bkb = dkb * X[tt] * p.wA[s][tt] * 2.0 * bk;
+        smub[s] += bmb * ismu[tt] * p.wB[s][tt];
+        ismub[tt] += bmb * smu[s] * p.wB[s][tt];
+        skab[s] += bkb * iska[tt] * p.wB[s][tt];
+        iskab[tt] += bkb * ska[s] * p.wB[s][tt];
+      }
+    }
+    double lnTb = 0.0, xdot = 0.0;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      smub[s] -= ismub[s] * ismu[s] * ismu[s];
+      skab[s] -= iskab[s] * iska[s] * iska[s];
+      lnTb += 0.5 * (smub[s] * smu[s] * dlm[s] + skab[s] * ska[s] * dlk[s]);
+      xdot += Xb[s] * X[s];
+    }
+#pragma unroll
+    for (int s = 0; s < NS; ++s) Yb[s] += (Xb[s] - xdot) * ixs * p.invW[s];
+    Tb += lnTb / T;
+  }
+  // H = (E + p) / rho; sqrt(rho)
+  const double Hb = qb[L::H * PC];
+  Eb += Hb * irho;
+  prb += Hb * irho;
+  irhob += Hb * (E + pr);
+  rhob += qb[L::SR * PC] * 0.5 / sqrt(rho);
+  // c = sqrt(cp R T / cv)
+  const double c2b = cb * 0.5 / c;
+  cpmb += c2b * (-RT * Rm / (cvm * cvm));
+  Rmb += c2b * cpm * RT / (cvm * cvm);
+  double RTb = c2b * cpm / cvm;
+  // p = rho R T
+  rhob += prb * RT;
+  RTb += prb * rho;
+  Rmb += RTb * T;
+  Tb += RTb * Rm;
+  // mixture cp and R
+  Tb += cpmb * dcpm;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) Yb[s] += cpmb * cps[s] + Rmb * p.r[s];
+  // Newton temperature through the implicit-function theorem
+  const double eb = Tb / cvm;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) Yb[s] -= Tb * es[s] / cvm;
+  // Y_N = 1 - sum_{s<N} Y_s
+#pragma unroll
+  for (int s = 0; s < NS - 1; ++s) Yb[s] -= Yb[NS - 1];
+  // e = E/rho - |u|^2/2
+  Eb += eb * irho;
+  irhob += eb * E;
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) velb[a] -= eb * vel[a];
+  // u_a = m_a / rho, Y_s = rhoY_s / rho
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    ub[1 + a] += velb[a] * irho;
+    irhob += velb[a] * u[1 + a];
+  }
+#pragma unroll
+  for (int s = 0; s < NS - 1; ++s) {
+    ub[DIM + 2 + s] += Yb[s] * irho;
+    irhob += Yb[s] * u[DIM + 2 + s];
+  }
+  rhob -= irhob * irho * irho;
+  ub[0] += rhob;
+  ub[DIM + 1] += Eb;
+  if (f0) ub[1] = -ub[1];
+  if (DIM > 1 && f1) ub[2] = -ub[2];
+  if (DIM > 2 && f2) ub[3] = -ub[3];
+  const long long C = p.cells;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) aadd(Ubar + v * C + src, ub[v]);
+  (void)E;
+}
+
+template <int DIM, int NS>
+__global__ void __launch_bounds__(128)
+k_prim_adj(const __grid_constant__ Params p, const double* __restrict__ Q,
+           const double* __restrict__ Qb, double* __restrict__ Ubar) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < p.pcells) prim_adj_cell<DIM, NS>(p, t, Q, Qb, Ubar);
+}
+
+// ================================================================ k_grad_adj
+// Gather form: GU_ab[t] = w (u_a[t-2] - u_a[t+2] + 8 (u_a[t+1] - u_a[t-1])) along b,
+// so ubar_a[t'] += sum_j coef_j GUbar_ab[t' - j] over the cells where GU was formed.
+template <int DIM, int NS>
+__global__ void __launch_bounds__(256)
+k_grad_adj(const __grid_constant__ Params p, double* __restrict__ Qb) {
+  using L = Lay<DIM, NS>;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= p.pcells) return;
+  const long long PC = p.pcells;
+  int idx[3];
+  idx[0] = (int)(t % p.np[0]);
+  idx[1] = (int)((t / p.np[0]) % p.np[1]);
+  idx[2] = (int)(t / ((long long)p.np[0] * p.np[1]));
+  const long long stride[3] = {1, p.np[0], (long long)p.np[0] * p.np[1]};
+  const int js[4] = {-2, -1, 1, 2};
+  const double cj[4] = {1.0, -8.0, 8.0, -1.0};  // coefficient of u[t + j] in GU[t]
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    double acc = 0.0;
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) {
+      const double w = p.inv_dx[b] * (1.0 / 12.0);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int src = idx[b] - js[q];  // the GU cell whose stencil holds t at offset j
+        if (src < 2 || src >= p.np[b] - 2) continue;
+        acc = fma(cj[q] * w, Qb[(L::GU + a * DIM + b) * PC + t - js[q] * stride[b]], acc);
+      }
+    }
+    Qb[(L::UN + a) * PC + t] += acc;
+  }
+}
+
+// ============================================================ objective ===
+// J = sum_cells Y_s (1 - Y_s) dV (the mixing measure); per-block partial sums
+// (deterministic two-pass reduction) and the gradient dJ/dU.
+template <int DIM, int NS>
+__global__ void __launch_bounds__(256)
+k_mixing(const __grid_constant__ Params p, const double* __restrict__ U, int sp, double dV,
+         double* __restrict__ part, double* __restrict__ Ubar) {
+  constexpr int NV = DIM + 1 + NS;
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long C = p.cells;
+  double j = 0.0;
+  if (c < C) {
+    const double rho = U[c], irho = 1.0 / rho;
+    double Y;
+    if (sp < NS - 1) {
+      Y = U[(DIM + 2 + sp) * C + c] * irho;
+    } else {
+      double ys = 0.0;
+#pragma unroll
+      for (int s = 0; s < NS - 1; ++s) ys += U[(DIM + 2 + s) * C + c];
+      Y = 1.0 - ys * irho;
+    }
+    j = Y * (1.0 - Y) * dV;
+    const double gY = (1.0 - 2.0 * Y) * dV;  // dJ/dY
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Ubar[v * C + c] = 0.0;
+    if (sp < NS - 1) {
+      Ubar[(DIM + 2 + sp) * C + c] = gY * irho;
+      Ubar[c] = -gY * Y * irho;
+    } else {
+#pragma unroll
+      for (int s = 0; s < NS - 1; ++s) Ubar[(DIM + 2 + s) * C + c] = -gY * irho;
+      Ubar[c] = gY * (1.0 - Y) * irho;
+    }
+  }
+  __shared__ double sh[256];
+  sh[threadIdx.x] = j;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void k_sum_partials(const double* __restrict__ part, int n, double* out) {
+  __shared__ double sh[256];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += part[i];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sh[0];
+}
+
+// ====================================================== k_from_prim_adj ===
+// Reverse of k_from_prim: Ubar -> Pbar (overwritten).
+template <int DIM, int NS>
+__global__ void __launch_bounds__(256)
+k_from_prim_adj(const __grid_constant__ Params p, const double* __restrict__ P,
+                const double* __restrict__ Ub, double* __restrict__ Pb) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= p.cells) return;
+  const long long C = p.cells;
+  const double rho = P[c];
+  double Y[NS], ys = 0.0, Rm = 0.0;
+#pragma unroll
+  for (int s = 0; s < NS - 1; ++s) { Y[s] = P[(DIM + 2 + s) * C + c]; ys += Y[s]; }
+  Y[NS - 1] = 1.0 - ys;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) Rm = fma(Y[s], p.r[s], Rm);
+  const double pr = P[(DIM + 1) * C + c];
+  const double T = pr / (rho * Rm);
+  const TauPt tp = tau_of(p, T);
+  double e = 0.0, cv = 0.0, es[NS], ke = 0.0, u[DIM];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    const double cps = cp_s(p, s, tp.tc);
+    es[s] = h_s(p, s, tp, cps) - p.r[s] * T;
+    e = fma(Y[s], es[s], e);
+    cv = fma(Y[s], cps - p.r[s], cv);
+  }
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) { u[a] = P[(1 + a) * C + c]; ke = fma(u[a], u[a], ke); }
+  const double UbE = Ub[(DIM + 1) * C + c];
+  double rhob = Ub[c] + UbE * fma(0.5, ke, e);
+  double ub[DIM];
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    const double m = Ub[(1 + a) * C + c];
+    rhob = fma(m, u[a], rhob);
+    ub[a] = m * rho + UbE * rho * u[a];
+  }
+  double Yb[NS];
+#pragma unroll
+  for (int s = 0; s < NS - 1; ++s) {
+    const double g = Ub[(DIM + 2 + s) * C + c];
+    rhob = fma(g, Y[s], rhob);
+    Yb[s] = g * rho;
+  }
+  Yb[NS - 1] = 0.0;
+  const double eb = UbE * rho;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) Yb[s] += eb * es[s];
+  const double Tb = eb * cv;
+  const double prb = Tb / (rho * Rm);
+  rhob -= Tb * T / rho;
+  const double Rmb = -Tb * T / Rm;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) Yb[s] += Rmb * p.r[s];
+#pragma unroll
+  for (int s = 0; s < NS - 1; ++s) Yb[s] -= Yb[NS - 1];
+  Pb[c] = rhob;
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) Pb[(1 + a) * C + c] = ub[a];
+  Pb[(DIM + 1) * C + c] = prb;
+#pragma unroll
+  for (int s = 0; s < NS - 1; ++s) Pb[(DIM + 2 + s) * C + c] = Yb[s];
+}
+
+// out = a x + b y + c z (elementwise; any of x, y, z may alias out)
+__global__ void k_lincomb(long long n, double a, const double* x, double b, const double* y,
+                          double c, const double* z, double* out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double r = a * x[i];
+  if (y) r = fma(b, y[i], r);
+  if (z) r = fma(c, z[i], r);
+  out[i] = r;
+}
+
+}  // namespace xf

@@ -9,6 +9,7 @@
 #include "xf.h"
 #include "xf_device.cuh"
 #include "xf_internal.h"
+#include "xf_adjoint.cuh"
 
 namespace {
 
@@ -38,6 +39,12 @@ using FaceFn = void (*)(const xf::Params&, const double*, double*, uint32_t*, cu
 using UpdFn = void (*)(const xf::Params&, const double*, const double*, const double*,
                        const double*, const double*, double*, const double*, int, cudaStream_t);
 using FromPrimFn = void (*)(const xf::Params&, const double*, double*, double*, cudaStream_t);
+using FaceAdjFn = void (*)(const xf::Params&, const double*, const double*, double, double*,
+                           cudaStream_t);
+using CellAdjFn = void (*)(const xf::Params&, const double*, const double*, double*, cudaStream_t);
+using GradAdjFn = void (*)(const xf::Params&, double*, cudaStream_t);
+using MixFn = void (*)(const xf::Params&, const double*, int, double, double*, double*,
+                       cudaStream_t);
 
 struct Table {
   PrimFn prim;
@@ -46,6 +53,11 @@ struct Table {
   UpdFn update;
   FromPrimFn from_prim;
   int nq;
+  FaceAdjFn face_adj[3];
+  GradAdjFn grad_adj;
+  CellAdjFn prim_adj;
+  CellAdjFn from_prim_adj;
+  MixFn mixing;
 };
 
 template <int DIM, int NS>
@@ -75,8 +87,34 @@ struct Launch {
                         cudaStream_t s) {
     xf::k_from_prim<DIM, NS><<<blocks(p.cells, 256), 256, 0, s>>>(p, P, U, T);
   }
+  template <int D>
+  static void face_adj(const xf::Params& p, const double* Q, const double* Rb, double scale,
+                       double* Qb, cudaStream_t s) {
+    if constexpr (D < DIM) {
+      const long long nf =
+          (long long)(p.n[0] + (D == 0)) * (p.n[1] + (D == 1)) * (p.n[2] + (D == 2));
+      xf::k_face_adj<DIM, NS, D><<<blocks(nf, 128), 128, 0, s>>>(p, Q, Rb, scale, Qb);
+    }
+  }
+  static void grad_adj(const xf::Params& p, double* Qb, cudaStream_t s) {
+    xf::k_grad_adj<DIM, NS><<<blocks(p.pcells, 256), 256, 0, s>>>(p, Qb);
+  }
+  static void prim_adj(const xf::Params& p, const double* Q, const double* Qb, double* Ub,
+                       cudaStream_t s) {
+    xf::k_prim_adj<DIM, NS><<<blocks(p.pcells, 128), 128, 0, s>>>(p, Q, Qb, Ub);
+  }
+  static void from_prim_adj(const xf::Params& p, const double* P, const double* Ub, double* Pb,
+                            cudaStream_t s) {
+    xf::k_from_prim_adj<DIM, NS><<<blocks(p.cells, 256), 256, 0, s>>>(p, P, Ub, Pb);
+  }
+  static void mixing(const xf::Params& p, const double* U, int sp, double dV, double* part,
+                     double* Ub, cudaStream_t s) {
+    xf::k_mixing<DIM, NS><<<blocks(p.cells, 256), 256, 0, s>>>(p, U, sp, dV, part, Ub);
+  }
   static Table table() {
-    return Table{prim, grad, {face<0>, face<1>, face<2>}, update, from_prim, xf::Lay<DIM, NS>::NQ};
+    return Table{prim, grad, {face<0>, face<1>, face<2>}, update, from_prim, xf::Lay<DIM, NS>::NQ,
+                 {face_adj<0>, face_adj<1>, face_adj<2>}, grad_adj, prim_adj, from_prim_adj,
+                 mixing};
   }
 };
 
@@ -141,6 +179,14 @@ struct xf_handle {
   double* dt = nullptr;
   unsigned long long* red = nullptr;
   uint32_t* flags = nullptr;
+  // adjoint buffers (allocated on first use): per-cell adjoint fields, the two
+  // stage states and two stage adjoints of xf_step_rk3_adjoint, reduction partials
+  double* Qb = nullptr;
+  double* A1 = nullptr;
+  double* A2 = nullptr;
+  double* B1 = nullptr;
+  double* B2 = nullptr;
+  double* part = nullptr;
   // per-kernel event timing (xf_profile_enable / xf_profile_read)
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -278,6 +324,65 @@ xf_status stage_fluxes(xf_handle* h, const double* Uin, int do_cfl, cudaStream_t
   return XF_OK;
 }
 
+// Per-cell fields (and nodal gradients) of Uin, without the faces.
+xf_status cell_fields(xf_handle* h, const double* Uin, cudaStream_t s) {
+  const xf::Params& p = h->p;
+  timed(h, XF_PROF_PRIM, s, [&] {
+    h->tab.prim(p, Uin, h->T[h->tcur], h->T[1 - h->tcur], h->Q, h->flags, h->red, 0, s);
+  });
+  h->tcur = 1 - h->tcur;
+  if (p.viscous) timed(h, XF_PROF_GRAD, s, [&] { h->tab.grad(p, h->Q, s); });
+  XF_CUDA(cudaGetLastError());
+  return XF_OK;
+}
+
+xf_status ensure_adjoint_buffers(xf_handle* h) {
+  if (h->Qb) return XF_OK;
+  const xf::Params& p = h->p;
+  const size_t sb = sizeof(double) * (size_t)p.nv * p.cells;
+  void* ptrs[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  const size_t bytes[6] = {sizeof(double) * (size_t)h->tab.nq * p.pcells, sb, sb, sb, sb,
+                           sizeof(double) * (size_t)blocks(p.cells, 256)};
+  for (int k = 0; k < 6; ++k) {
+    if (cudaMalloc(&ptrs[k], bytes[k]) != cudaSuccess) {
+      cudaGetLastError();
+      for (int j = 0; j < k; ++j) cudaFree(ptrs[j]);
+      g_err = "adjoint buffers: cudaMalloc failed";
+      return XF_ERR_OOM;
+    }
+  }
+  h->Qb = (double*)ptrs[0];
+  h->A1 = (double*)ptrs[1];
+  h->A2 = (double*)ptrs[2];
+  h->B1 = (double*)ptrs[3];
+  h->B2 = (double*)ptrs[4];
+  h->part = (double*)ptrs[5];
+  return XF_OK;
+}
+
+// Ubar += scale (dL/dU)^T Rbar at the state U.
+xf_status rhs_adjoint_impl(xf_handle* h, const double* U, const double* Rbar, double scale,
+                           double* Ubar, cudaStream_t s) {
+  xf_status st = ensure_adjoint_buffers(h);
+  if (st != XF_OK) return st;
+  st = cell_fields(h, U, s);
+  if (st != XF_OK) return st;
+  const xf::Params& p = h->p;
+  XF_CUDA(cudaMemsetAsync(h->Qb, 0, sizeof(double) * (size_t)h->tab.nq * p.pcells, s));
+  for (int d = 0; d < p.dim; ++d)
+    timed(h, XF_PROF_FACE_ADJ, s, [&] { h->tab.face_adj[d](p, h->Q, Rbar, scale, h->Qb, s); });
+  if (p.viscous) timed(h, XF_PROF_GRAD, s, [&] { h->tab.grad_adj(p, h->Qb, s); });
+  timed(h, XF_PROF_PRIM_ADJ, s, [&] { h->tab.prim_adj(p, h->Q, h->Qb, Ubar, s); });
+  XF_CUDA(cudaGetLastError());
+  return XF_OK;
+}
+
+void lincomb(const xf_handle* h, double a, const double* x, double b, const double* y, double c,
+             const double* z, double* out, cudaStream_t s) {
+  const long long n = (long long)h->p.nv * h->p.cells;
+  xf::k_lincomb<<<blocks(n, 256), 256, 0, s>>>(n, a, x, b, y, c, z, out);
+}
+
 __global__ void k_probe_fp64(double* out, long long iters, double a) {
   double x0 = threadIdx.x * 1e-3, x1 = x0 + 1, x2 = x0 + 2, x3 = x0 + 3, x4 = x0 + 4,
          x5 = x0 + 5, x6 = x0 + 6, x7 = x0 + 7;
@@ -381,6 +486,12 @@ void xf_destroy(xf_handle* h) {
   cudaFree(h->dt);
   cudaFree(h->red);
   cudaFree(h->flags);
+  cudaFree(h->Qb);
+  cudaFree(h->A1);
+  cudaFree(h->A2);
+  cudaFree(h->B1);
+  cudaFree(h->B2);
+  cudaFree(h->part);
   for (auto& r : h->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto e : h->ev_pool) cudaEventDestroy(e);
   delete h;
@@ -495,6 +606,68 @@ xf_status xf_get_status(xf_handle* h, uint32_t* flags, void* stream) {
 xf_status xf_clear_status(xf_handle* h, void* stream) {
   if (!h) return XF_ERR_ARG;
   XF_CUDA(cudaMemsetAsync(h->flags, 0, sizeof(uint32_t), (cudaStream_t)stream));
+  return XF_OK;
+}
+
+xf_status xf_rhs_adjoint(xf_handle* h, const double* U, const double* dUdt_bar, double* U_bar,
+                         void* stream) {
+  if (!h || !U || !dUdt_bar || !U_bar) return XF_ERR_ARG;
+  if (!is_device_ptr(U) || !is_device_ptr(dUdt_bar) || !is_device_ptr(U_bar)) return XF_ERR_ARG;
+  return rhs_adjoint_impl(h, U, dUdt_bar, 1.0, U_bar, (cudaStream_t)stream);
+}
+
+xf_status xf_step_rk3_adjoint(xf_handle* h, double dt, double* U_bar, void* stream) {
+  if (!h || !U_bar || !(dt > 0.0)) return XF_ERR_ARG;
+  if (!is_device_ptr(U_bar)) return XF_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  xf_status st = ensure_adjoint_buffers(h);
+  if (st != XF_OK) return st;
+  const xf::Params& p = h->p;
+  k_set_scalar<<<1, 1, 0, s>>>(h->dt, dt);
+  // forward stage states U1 (A1) and U2 (A2) from U^n (h->U)
+  st = stage_fluxes(h, h->U, 0, s);
+  if (st != XF_OK) return st;
+  h->tab.update(p, h->G[0], h->G[1], h->G[2], h->U, h->U, h->A1, h->dt, 1, s);
+  st = stage_fluxes(h, h->A1, 0, s);
+  if (st != XF_OK) return st;
+  h->tab.update(p, h->G[0], h->G[1], h->G[2], h->U, h->A1, h->A2, h->dt, 2, s);
+  // reverse of U3 = U/3 + 2/3 (U2 + dt L(U2)), U2 = 3/4 U + 1/4 (U1 + dt L(U1)),
+  // U1 = U + dt L(U); a = Ubar(U3) on entry
+  lincomb(h, 2.0 / 3.0, U_bar, 0.0, nullptr, 0.0, nullptr, h->B2, s);
+  st = rhs_adjoint_impl(h, h->A2, U_bar, 2.0 / 3.0 * dt, h->B2, s);
+  if (st != XF_OK) return st;
+  lincomb(h, 0.25, h->B2, 0.0, nullptr, 0.0, nullptr, h->B1, s);
+  st = rhs_adjoint_impl(h, h->A1, h->B2, 0.25 * dt, h->B1, s);
+  if (st != XF_OK) return st;
+  lincomb(h, 1.0 / 3.0, U_bar, 0.75, h->B2, 1.0, h->B1, U_bar, s);
+  st = rhs_adjoint_impl(h, h->U, h->B1, dt, U_bar, s);
+  if (st != XF_OK) return st;
+  XF_CUDA(cudaGetLastError());
+  return XF_OK;
+}
+
+xf_status xf_objective_mixing(xf_handle* h, const double* U, int species, double* J_dev,
+                              double* U_bar, void* stream) {
+  if (!h || !U || !J_dev || !U_bar || species < 0 || species >= h->p.N) return XF_ERR_ARG;
+  if (!is_device_ptr(U) || !is_device_ptr(J_dev) || !is_device_ptr(U_bar)) return XF_ERR_ARG;
+  xf_status st = ensure_adjoint_buffers(h);
+  if (st != XF_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const xf::Params& p = h->p;
+  double dV = 1.0;
+  for (int a = 0; a < p.dim; ++a) dV /= p.inv_dx[a];
+  h->tab.mixing(p, U, species, dV, h->part, U_bar, s);
+  xf::k_sum_partials<<<1, 256, 0, s>>>(h->part, (int)blocks(p.cells, 256), J_dev);
+  XF_CUDA(cudaGetLastError());
+  return XF_OK;
+}
+
+xf_status xf_set_primitive_adjoint(xf_handle* h, const double* P, const double* U_bar,
+                                   double* P_bar, void* stream) {
+  if (!h || !P || !U_bar || !P_bar) return XF_ERR_ARG;
+  if (!is_device_ptr(P) || !is_device_ptr(U_bar) || !is_device_ptr(P_bar)) return XF_ERR_ARG;
+  h->tab.from_prim_adj(h->p, P, U_bar, P_bar, (cudaStream_t)stream);
+  XF_CUDA(cudaGetLastError());
   return XF_OK;
 }
 

@@ -48,9 +48,11 @@ EXPORTS = ["xf_create", "xf_destroy", "xf_nv", "xf_cells", "xf_set_state", "xf_s
            "xf_batch_create", "xf_batch_destroy", "xf_batch_size", "xf_batch_set_primitive",
            "xf_batch_set_state", "xf_batch_get_state", "xf_batch_step_rk3", "xf_batch_autotune",
            "xf_batch_config", "xf_batch_get_status", "xf_barrier_probe", "xf_batch_uses_graph",
-           "xf_batch_num_candidates"]
-PROF_SLOTS = 8
-PROF_NAMES = ["prim", "dt", "grad", "face_x", "face_y", "face_z", "update", "spare"]
+           "xf_batch_num_candidates", "xf_rhs_adjoint", "xf_step_rk3_adjoint",
+           "xf_objective_mixing", "xf_set_primitive_adjoint"]
+PROF_SLOTS = 10
+PROF_NAMES = ["prim", "dt", "grad", "face_x", "face_y", "face_z", "update", "face_adj", "prim_adj",
+              "spare"]
 
 
 def _load():
@@ -81,6 +83,10 @@ def _load():
     L.xf_rhs_static.argtypes = [C.POINTER(Grid), C.POINTER(Thermo), C.POINTER(Opts), vp, vp, vp,
                                 C.POINTER(C.c_uint32), vp]
     L.xf_rhs_static_capacity_bytes.restype = C.c_int64
+    L.xf_rhs_adjoint.argtypes = [vp, vp, vp, vp, vp]
+    L.xf_step_rk3_adjoint.argtypes = [vp, C.c_double, vp, vp]
+    L.xf_objective_mixing.argtypes = [vp, vp, C.c_int, vp, vp, vp]
+    L.xf_set_primitive_adjoint.argtypes = [vp, vp, vp, vp, vp]
     L.xf_batch_create.argtypes = [C.c_int, C.POINTER(Grid), C.POINTER(Thermo), C.POINTER(Opts),
                                   C.POINTER(vp)]
     L.xf_batch_destroy.argtypes = [vp]
@@ -224,6 +230,24 @@ class Solver:
 
     def clear_status(self, stream=None):
         check(lib.xf_clear_status(self.h, stream_ptr(stream)), "xf_clear_status")
+
+    def rhs_adjoint(self, U, dUdt_bar, U_bar, stream=None):
+        """U_bar += (dL/dU)^T dUdt_bar at U (device tensors)."""
+        check(lib.xf_rhs_adjoint(self.h, ptr(U), ptr(dUdt_bar), ptr(U_bar), stream_ptr(stream)),
+              "xf_rhs_adjoint")
+
+    def step_adjoint(self, dt, U_bar, stream=None):
+        """Reverse of one fixed-dt RK3 step from the current state (U_bar in/out)."""
+        check(lib.xf_step_rk3_adjoint(self.h, float(dt), ptr(U_bar), stream_ptr(stream)),
+              "xf_step_rk3_adjoint")
+
+    def objective_mixing(self, U, species, J_dev, U_bar, stream=None):
+        check(lib.xf_objective_mixing(self.h, ptr(U), int(species), ptr(J_dev), ptr(U_bar),
+                                      stream_ptr(stream)), "xf_objective_mixing")
+
+    def set_primitive_adjoint(self, P, U_bar, P_bar, stream=None):
+        check(lib.xf_set_primitive_adjoint(self.h, ptr(P), ptr(U_bar), ptr(P_bar), stream_ptr(stream)),
+              "xf_set_primitive_adjoint")
 
     def profile(self, on=True):
         check(lib.xf_profile_enable(self.h, int(on)), "xf_profile_enable")

@@ -1,0 +1,139 @@
+"""The hand-written adjoint against exact forward-mode derivatives of the
+oracle (dual numbers) and against central finite differences of the CUDA
+forward path.
+
+<w, J^T-product(v)> identities: for random directions V and weights W,
+sum(Ubar * V_k) computed by xf_rhs_adjoint (Ubar = J^T W) must equal
+sum(W * (J V_k)) from the oracle's dual-number JVP.
+"""
+import numpy as np
+import pytest
+
+from paper_2403_05910_b300 import cases
+from oracle.xfo import Oracle
+
+from gpu_util import dev, gpu_solver
+
+pytestmark = pytest.mark.gpu
+
+
+def _cases():
+    return {
+        "sbi2d_n4_visc": cases.config(4, n=(24, 14)),
+        "sbi2d_n3_visc": cases.config(1, n=(20, 12)),
+        "smooth2d_n3_periodic": cases.smooth_periodic(2, (14, 12), 3, seed=5, amp=0.3),
+        "sbi3d_n5_visc": cases.config(2, n=(12, 8, 8)),
+        "tube1d_n2": cases.shock_tube(0, n=64),
+        "smooth1d_n4_inviscid": cases.smooth_periodic(1, (40,), 4, seed=2, amp=0.3, viscous=False),
+    }
+
+
+CASES = _cases()
+
+
+def _dirs(rng, U, k, rel=1.0):
+    """k random directions scaled per field like U."""
+    sc = np.max(np.abs(U), axis=1, keepdims=True) + 1e-3
+    return rng.normal(size=(k,) + U.shape) * sc * rel
+
+
+def _dot_check(lhs, rhs, tol):
+    lhs, rhs = np.asarray(lhs), np.asarray(rhs)
+    assert np.all(np.abs(lhs - rhs) <= tol * (np.abs(rhs) + np.abs(lhs)).max()), (lhs, rhs)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_rhs_adjoint_matches_oracle_jvp(name):
+    import torch
+    case = CASES[name]
+    o = Oracle(case)
+    U, T = o.prim_to_cons()
+    rng = np.random.default_rng(11)
+    V = _dirs(rng, U, 8)
+    R, JV, _, st = o.rhs_jvp(U, V, T.copy())
+    W = rng.normal(size=U.shape)
+    s = gpu_solver(case)
+    s.set_state(dev(U), dev(T))
+    Ub = torch.zeros((case.n_v, case.cells), dtype=torch.float64, device="cuda")
+    s.rhs_adjoint(dev(U), dev(W), Ub)
+    torch.cuda.synchronize()
+    assert s.status() == 0
+    Ubar = Ub.cpu().numpy()
+    lhs = [np.sum(Ubar * V[k]) for k in range(8)]
+    rhs = [np.sum(W * JV[k]) for k in range(8)]
+    _dot_check(lhs, rhs, 1e-10)
+    s.close()
+
+
+@pytest.mark.parametrize("name", ["sbi2d_n4_visc", "sbi3d_n5_visc", "tube1d_n2"])
+def test_step_adjoint_matches_oracle_jvp(name):
+    import torch
+    case = CASES[name]
+    o = Oracle(case)
+    U, T = o.prim_to_cons()
+    dt = 0.5 * o.dt(U, T.copy())
+    rng = np.random.default_rng(12)
+    V = _dirs(rng, U, 8)
+    U1, JV, _, _ = o.rk3_jvp(U, V, T.copy(), dt, 1)
+    W = rng.normal(size=U.shape)
+    s = gpu_solver(case)
+    s.set_state(dev(U), dev(T))
+    Ub = dev(W).clone()
+    s.step_adjoint(dt, Ub)
+    torch.cuda.synchronize()
+    Ubar = Ub.cpu().numpy()
+    lhs = [np.sum(Ubar * V[k]) for k in range(8)]
+    rhs = [np.sum(W * JV[k]) for k in range(8)]
+    _dot_check(lhs, rhs, 1e-10)
+    s.close()
+
+
+def test_rhs_adjoint_accumulates_and_matches_gpu_fd():
+    """Central differences of the CUDA RHS itself (h = 1e-6 relative)."""
+    import torch
+    case = CASES["sbi2d_n4_visc"]
+    U, T = Oracle(case).prim_to_cons()
+    rng = np.random.default_rng(13)
+    V = _dirs(rng, U, 1)[0]
+    W = rng.normal(size=U.shape)
+    s = gpu_solver(case)
+    s.set_state(dev(U), dev(T))
+    h = 1e-6
+    Rp, Rm = torch.empty_like(dev(U)), torch.empty_like(dev(U))
+    s.rhs(dev(U + h * V), Rp)
+    s.rhs(dev(U - h * V), Rm)
+    fd = np.sum(W * (Rp.cpu().numpy() - Rm.cpu().numpy()) / (2 * h))
+    Ub = dev(np.ones_like(U))  # accumulates on top of this
+    s.rhs_adjoint(dev(U), dev(W), Ub)
+    adj = np.sum((Ub.cpu().numpy() - 1.0) * V)
+    assert abs(adj - fd) <= 1e-6 * abs(fd)
+    s.close()
+
+
+def test_objective_and_primitive_adjoints_match_fd():
+    import torch
+    case = CASES["sbi2d_n4_visc"]
+    s = gpu_solver(case)
+    P = case.prim.copy()
+    rng = np.random.default_rng(14)
+    dP = rng.normal(size=P.shape) * (np.max(np.abs(P), axis=1, keepdims=True) + 1e-3) * 1e-2
+
+    def J_of(Pv):
+        s.set_primitive(dev(Pv))
+        U = torch.empty((case.n_v, case.cells), dtype=torch.float64, device="cuda")
+        s.get_state(U)
+        Jd = torch.zeros(1, dtype=torch.float64, device="cuda")
+        Ub = torch.empty_like(U)
+        s.objective_mixing(U, 2, Jd, Ub)
+        torch.cuda.synchronize()
+        return Jd.item(), U, Ub
+
+    J0, U, Ub = J_of(P)
+    Pb = torch.empty_like(U)
+    s.set_primitive_adjoint(dev(P), Ub, Pb)
+    adj = float(np.sum(Pb.cpu().numpy() * dP))
+    h = 1e-5
+    fd = (J_of(P + h * dP)[0] - J_of(P - h * dP)[0]) / (2 * h)
+    assert J0 > 0
+    assert abs(adj - fd) <= 1e-6 * abs(fd), (adj, fd)
+    s.close()
