@@ -65,8 +65,18 @@ def test_rhs_adjoint_matches_oracle_jvp(name):
     s.close()
 
 
-@pytest.mark.parametrize("name", ["sbi2d_n4_visc", "sbi3d_n5_visc", "tube1d_n2"])
-def test_step_adjoint_matches_oracle_jvp(name):
+@pytest.mark.parametrize("name,tol", [("smooth2d_n3_periodic", 1e-10),
+                                      ("smooth1d_n4_inviscid", 1e-10),
+                                      ("tube1d_n2", 1e-9),
+                                      ("sbi2d_n4_visc", 1e-5),
+                                      ("sbi3d_n5_visc", 1e-5)])
+def test_step_adjoint_matches_oracle_jvp(name, tol):
+    """Reverse of one RK3 step against the oracle's exact JVP. On smooth
+    fields this is a round-off identity. Shock-bubble states hold exact ties
+    of the LLF maxima in their uniform regions; after a stage, cells at the
+    edge of those regions carry near-ties that GPU and oracle (equal to ~1e-13)
+    can resolve to different cells, which moves a kink's one-sided derivative:
+    those states are held to 1e-5."""
     import torch
     case = CASES[name]
     o = Oracle(case)
@@ -84,21 +94,25 @@ def test_step_adjoint_matches_oracle_jvp(name):
     Ubar = Ub.cpu().numpy()
     lhs = [np.sum(Ubar * V[k]) for k in range(8)]
     rhs = [np.sum(W * JV[k]) for k in range(8)]
-    _dot_check(lhs, rhs, 1e-10)
+    _dot_check(lhs, rhs, tol)
     s.close()
 
 
 def test_rhs_adjoint_accumulates_and_matches_gpu_fd():
-    """Central differences of the CUDA RHS itself (h = 1e-6 relative)."""
+    """Central differences of the CUDA RHS itself. A smooth random field:
+    uniform regions (as in the shock-bubble state) hold exact ties in the LLF
+    maxima, where the RHS has a kink. Per-cell random directions excite the
+    WENO weights' curvature, so the difference step is 1e-7 (its truncation
+    error scales as h^2: 5.5e-6 relative at 1e-6, 5.5e-8 at 1e-7)."""
     import torch
-    case = CASES["sbi2d_n4_visc"]
+    case = CASES["smooth2d_n3_periodic"]
     U, T = Oracle(case).prim_to_cons()
     rng = np.random.default_rng(13)
     V = _dirs(rng, U, 1)[0]
     W = rng.normal(size=U.shape)
     s = gpu_solver(case)
     s.set_state(dev(U), dev(T))
-    h = 1e-6
+    h = 1e-7
     Rp, Rm = torch.empty_like(dev(U)), torch.empty_like(dev(U))
     s.rhs(dev(U + h * V), Rp)
     s.rhs(dev(U - h * V), Rm)
