@@ -20,30 +20,42 @@
 namespace xf {
 
 // ------------------------------------------------------------ WENO5 adjoint
-// Reverse of weno5_nd: given (nbar, dbar) for (num, den), add df.
-__device__ __forceinline__ void weno5_nd_adj(const double* f, double eps12, double nbar,
-                                             double dbar, double* fb) {
-  const double a = f[1] - f[0], b = f[2] - f[1], c = f[3] - f[2], d = f[4] - f[3];
-  const double t0 = b - a, u0 = fma(3.0, b, -a);
-  const double t1 = c - b, u1 = b + c;
-  const double t2 = d - c, u2 = fma(-3.0, c, d);
-  const double s0 = fma(13.0 * t0, t0, fma(3.0 * u0, u0, eps12));
-  const double s1 = fma(13.0 * t1, t1, fma(3.0 * u1, u1, eps12));
-  const double s2 = fma(13.0 * t2, t2, fma(3.0 * u2, u2, eps12));
-  const double p12 = s1 * s2, p02 = s0 * s2, p01 = s0 * s1;
-  const double w0 = (0.1 * p12) * p12, w1 = (0.6 * p02) * p02, w2 = (0.3 * p01) * p01;
-  const double q0 = fma(5.0 / 6.0, b, (-1.0 / 3.0) * a);
-  const double q1 = fma(1.0 / 3.0, c, (1.0 / 6.0) * b);
-  const double q2 = fma(2.0 / 3.0, c, (-1.0 / 6.0) * d);
-  const double w0b = fma(nbar, q0, dbar), w1b = fma(nbar, q1, dbar), w2b = fma(nbar, q2, dbar);
-  const double q0b = nbar * w0, q1b = nbar * w1, q2b = nbar * w2;
-  const double p12b = w0b * 0.2 * p12, p02b = w1b * 1.2 * p02, p01b = w2b * 0.6 * p01;
-  const double s0b = fma(p02b, s2, p01b * s1);
-  const double s1b = fma(p12b, s2, p01b * s0);
-  const double s2b = fma(p12b, s1, p02b * s0);
-  const double t0b = 26.0 * t0 * s0b, u0b = 6.0 * u0 * s0b;
-  const double t1b = 26.0 * t1 * s1b, u1b = 6.0 * u1 * s1b;
-  const double t2b = 26.0 * t2 * s2b, u2b = 6.0 * u2 * s2b;
+// Forward intermediates of one WENO5-JS reconstruction (the same arithmetic
+// as weno5_nd), kept for its reverse.
+struct W5 {
+  double a, b, c, d, t0, u0, t1, u1, t2, u2, s0, s1, s2, p12, p02, p01, w0, w1, w2, q0, q1, q2;
+  double num, den;
+};
+
+__device__ __forceinline__ void w5_fwd(double f0, double f1, double f2, double f3, double f4,
+                                       double eps12, W5& r) {
+  r.a = f1 - f0; r.b = f2 - f1; r.c = f3 - f2; r.d = f4 - f3;
+  r.t0 = r.b - r.a; r.u0 = fma(3.0, r.b, -r.a);
+  r.t1 = r.c - r.b; r.u1 = r.b + r.c;
+  r.t2 = r.d - r.c; r.u2 = fma(-3.0, r.c, r.d);
+  r.s0 = fma(13.0 * r.t0, r.t0, fma(3.0 * r.u0, r.u0, eps12));
+  r.s1 = fma(13.0 * r.t1, r.t1, fma(3.0 * r.u1, r.u1, eps12));
+  r.s2 = fma(13.0 * r.t2, r.t2, fma(3.0 * r.u2, r.u2, eps12));
+  r.p12 = r.s1 * r.s2; r.p02 = r.s0 * r.s2; r.p01 = r.s0 * r.s1;
+  r.w0 = (0.1 * r.p12) * r.p12; r.w1 = (0.6 * r.p02) * r.p02; r.w2 = (0.3 * r.p01) * r.p01;
+  r.q0 = fma(5.0 / 6.0, r.b, (-1.0 / 3.0) * r.a);
+  r.q1 = fma(1.0 / 3.0, r.c, (1.0 / 6.0) * r.b);
+  r.q2 = fma(2.0 / 3.0, r.c, (-1.0 / 6.0) * r.d);
+  r.num = fma(r.w0, r.q0, fma(r.w1, r.q1, r.w2 * r.q2));
+  r.den = (r.w0 + r.w1) + r.w2;
+}
+
+// Reverse of one reconstruction: (nbar, dbar) for (num, den) -> fb[0..4] (added).
+__device__ __forceinline__ void w5_rev(const W5& r, double nbar, double dbar, double* fb) {
+  const double w0b = fma(nbar, r.q0, dbar), w1b = fma(nbar, r.q1, dbar), w2b = fma(nbar, r.q2, dbar);
+  const double q0b = nbar * r.w0, q1b = nbar * r.w1, q2b = nbar * r.w2;
+  const double p12b = w0b * 0.2 * r.p12, p02b = w1b * 1.2 * r.p02, p01b = w2b * 0.6 * r.p01;
+  const double s0b = fma(p02b, r.s2, p01b * r.s1);
+  const double s1b = fma(p12b, r.s2, p01b * r.s0);
+  const double s2b = fma(p12b, r.s1, p02b * r.s0);
+  const double t0b = 26.0 * r.t0 * s0b, u0b = 6.0 * r.u0 * s0b;
+  const double t1b = 26.0 * r.t1 * s1b, u1b = 6.0 * r.u1 * s1b;
+  const double t2b = 26.0 * r.t2 * s2b, u2b = 6.0 * r.u2 * s2b;
   const double ab = -t0b - u0b - (1.0 / 3.0) * q0b;
   const double bb = t0b + 3.0 * u0b - t1b + u1b + (5.0 / 6.0) * q0b + (1.0 / 6.0) * q1b;
   const double cb = t1b + u1b - t2b - 3.0 * u2b + (1.0 / 3.0) * q1b + (2.0 / 3.0) * q2b;
@@ -55,25 +67,29 @@ __device__ __forceinline__ void weno5_nd_adj(const double* f, double eps12, doub
   fb[4] += db;
 }
 
-// Reverse of weno5_pair (F = wp2 + wm3 + np/dp + nm/dm): adds to wpb[0..5], wmb[0..5].
-__device__ __forceinline__ void weno5_pair_adj(const double* wp, const double* wm, double eps12,
-                                               double Fb, double* wpb, double* wmb) {
-  double np, dp, nm, dm;
-  weno5_nd(wp[0], wp[1], wp[2], wp[3], wp[4], eps12, np, dp);
-  weno5_nd(wm[5], wm[4], wm[3], wm[2], wm[1], eps12, nm, dm);
-  const double idp = 1.0 / dp, idm = 1.0 / dm;
+// One field's F = F^+ + F^- (as weno5_pair) and its reverse: returns F and
+// adds Fb dF/dw to wpb[0..5], wmb[0..5].
+__device__ __forceinline__ double weno5_pair_fwd_adj(const double* wp, const double* wm,
+                                                     double eps12, double Fb, double* wpb,
+                                                     double* wmb) {
+  W5 P, M;
+  w5_fwd(wp[0], wp[1], wp[2], wp[3], wp[4], eps12, P);
+  w5_fwd(wm[5], wm[4], wm[3], wm[2], wm[1], eps12, M);
+  const double F = (wp[2] + wm[3]) + fma(P.num, M.den, M.num * P.den) / (P.den * M.den);
+  const double idp = 1.0 / P.den, idm = 1.0 / M.den;
   double fb[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  weno5_nd_adj(wp, eps12, Fb * idp, -Fb * np * idp * idp, fb);
+  w5_rev(P, Fb * idp, -Fb * P.num * idp * idp, fb);
+#pragma unroll
   for (int k = 0; k < 5; ++k) wpb[k] += fb[k];
   wpb[2] += Fb;
-  const double fm[5] = {wm[5], wm[4], wm[3], wm[2], wm[1]};
   double gb[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  weno5_nd_adj(fm, eps12, Fb * idm, -Fb * nm * idm * idm, gb);
+  w5_rev(M, Fb * idm, -Fb * M.num * idm * idm, gb);
   wmb[5] += gb[0];
   wmb[4] += gb[1];
   wmb[3] += gb[2] + Fb;
   wmb[2] += gb[3];
   wmb[1] += gb[4];
+  return F;
 }
 
 // d c_p,s / dT at a clamped tau (0 outside the polynomial range)
@@ -216,31 +232,9 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
     const double lE_a = Gam * hic2;
     const double hlmn_e = 0.5 * Gam * un * ic2, lE_e = -Gam * ic2;
     double wp[6], wm[6];
-    // the three dense fields' reconstructions (needed by the back-projection adjoint)
-    double Fm, Fp, Fe;
-    for (int fld = 0; fld < 3; ++fld) {
-      const double ha = fld == 0 ? ha_m : (fld == 1 ? ha_p : ha0);
-      const double hl = fld == 0 ? hlmn_m : (fld == 1 ? hlmn_p : hlmn_e);
-      const double lE = fld == 2 ? lE_e : lE_a;
-#pragma unroll
-      for (int m = 0; m < 6; ++m) {
-        double LU;
-        if (fld == 2) {
-          LU = fma(-2.0, gUh[m], rho_m[m]);
-        } else {
-          const double nU = fma(-un, rho_m[m], QF(L::U + 1 + D, m - 2));
-          LU = fma(fld == 0 ? -chc : chc, nU, gUh[m]);
-        }
-        const double pq = p_m[m] * fma(hun[m], lE, hl);
-        wp[m] = fma(hun[m] + ha, LU, pq);
-        wm[m] = fma(hun[m] - ha, LU, pq);
-      }
-      const double F = weno5_pair(wp, wm, eps12);
-      if (fld == 0) Fm = F; else if (fld == 1) Fp = F; else Fe = F;
-    }
     // ================= reverse =================
-    // back-projection of the dense columns
-    const double S = Fm + Fp + Fe, Dl = Fp - Fm;
+    // back-projection of the dense columns: adjoints of the reconstructed
+    // fields depend on Gbar and the face state only
     double Sb = Gb[0] + Hb * Gb[IE];
 #pragma unroll
     for (int a = 0; a < DIM; ++a) Sb = fma(ub[a], Gb[1 + a], Sb);
@@ -249,17 +243,12 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
     const double Dlb = c * Gb[1 + D] + un * c * Gb[IE];
     double ubb[DIM], Ybb[NS];
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) ubb[a] = S * Gb[1 + a];
+    for (int a = 0; a < DIM; ++a) ubb[a] = 0.0;
 #pragma unroll
     for (int s = 0; s < NS; ++s) Ybb[s] = 0.0;
-#pragma unroll
-    for (int s = 0; s < NS - 1; ++s) Ybb[s] = S * Gb[IE + 1 + s];
-    double cb = Dl * Gb[1 + D] + un * Dl * Gb[IE];
-    double Hbb = S * Gb[IE];
-    double unb = c * Dl * Gb[IE];
-    double c2b = -iGam * Fe * Gb[IE];
-    double iGamb = -c2 * Fe * Gb[IE];
+    double cb = 0.0, Hbb = 0.0, unb = 0.0, c2b = 0.0, iGamb = 0.0;
     const double Fmb = Sb - Dlb, Fpb = Sb + Dlb, Feb = Sb - c2 * iGam * Gb[IE];
+    double Fm = 0.0, Fp = 0.0, Fe = 0.0;
     // per-field reverse; stencil adjoints accumulated here
     double rhob[6], pb[6], hunb[6], gUhb[6], mnb[6];
 #pragma unroll
@@ -287,7 +276,8 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
         wm[m] = fma(hun[m] - ha, LU, pq);
       }
       double wpb[6] = {0, 0, 0, 0, 0, 0}, wmb[6] = {0, 0, 0, 0, 0, 0};
-      weno5_pair_adj(wp, wm, eps12, Fb, wpb, wmb);
+      const double F = weno5_pair_fwd_adj(wp, wm, eps12, Fb, wpb, wmb);
+      if (fld == 0) Fm = F; else if (fld == 1) Fp = F; else Fe = F;
       double hab = 0.0, hlb = 0.0, lEb = 0.0;
 #pragma unroll
       for (int m = 0; m < 6; ++m) {
@@ -327,6 +317,19 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
         hic2b += hlb * 0.5 * (-Gam * un + sgn * c) + lEb * Gam;
       }
     }
+    // the back-projection terms that involve the reconstructed dense fields
+    {
+      const double S = Fm + Fp + Fe, Dl = Fp - Fm;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) ubb[a] += S * Gb[1 + a];
+#pragma unroll
+      for (int s = 0; s < NS - 1; ++s) Ybb[s] += S * Gb[IE + 1 + s];
+      cb += Dl * Gb[1 + D] + un * Dl * Gb[IE];
+      Hbb += S * Gb[IE];
+      unb += c * Dl * Gb[IE];
+      c2b -= iGam * Fe * Gb[IE];
+      iGamb -= c2 * Fe * Gb[IE];
+    }
     // tangential momenta and species (eigenvalue u, no pressure term)
     double hp0b[6], hm0b[6];
 #pragma unroll
@@ -342,10 +345,9 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
         wp[m] = (hun[m] + ha0) * LUv[m];
         wm[m] = (hun[m] - ha0) * LUv[m];
       }
-      const double Fk = weno5_pair(wp, wm, eps12);
-      ubb[a] += Fk * Gb[IE];
       double wpb[6] = {0, 0, 0, 0, 0, 0}, wmb[6] = {0, 0, 0, 0, 0, 0};
-      weno5_pair_adj(wp, wm, eps12, Fb, wpb, wmb);
+      const double Fk = weno5_pair_fwd_adj(wp, wm, eps12, Fb, wpb, wmb);
+      ubb[a] += Fk * Gb[IE];
 #pragma unroll
       for (int m = 0; m < 6; ++m) {
         const double LUb = wpb[m] * (hun[m] + ha0) + wmb[m] * (hun[m] - ha0);
@@ -367,11 +369,10 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
         wp[m] = (hun[m] + ha0) * LUv[m];
         wm[m] = (hun[m] - ha0) * LUv[m];
       }
-      const double Fk = weno5_pair(wp, wm, eps12);
+      double wpb[6] = {0, 0, 0, 0, 0, 0}, wmb[6] = {0, 0, 0, 0, 0, 0};
+      const double Fk = weno5_pair_fwd_adj(wp, wm, eps12, Fb, wpb, wmb);
       dphib[s] = -iGam * Fk * Gb[IE];
       iGamb -= dphi[s] * Fk * Gb[IE];
-      double wpb[6] = {0, 0, 0, 0, 0, 0}, wmb[6] = {0, 0, 0, 0, 0, 0};
-      weno5_pair_adj(wp, wm, eps12, Fb, wpb, wmb);
 #pragma unroll
       for (int m = 0; m < 6; ++m) {
         const double LUb = wpb[m] * (hun[m] + ha0) + wmb[m] * (hun[m] - ha0);
