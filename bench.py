@@ -95,6 +95,23 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def reduce_max(value, device=None):
+    """Maximum of a float over all ranks (the value itself when not distributed)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, seconds_max, world):
+    """Units processed by all ranks (each rank does the same replica) per second
+    of the slowest rank."""
+    return world * units_per_rank / seconds_max
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -201,6 +218,53 @@ def _batched_vs_per_instance(args, dev, stream):
             "cuda_graph": graph, "status_flags": st_b}
 
 
+def _adjoint_vs_forward(args, dev, stream):
+    """The differentiated workload (2D shock-bubble, 512x256, 4 species): time
+    of one RHS adjoint against one forward RHS, and of one RK3-step adjoint
+    (which recomputes the two intermediate stage states) against one step."""
+    import torch
+    from paper_2403_05910_b300 import cases
+    from paper_2403_05910_b300.xf import Solver
+    c = cases.config(4)
+    s = Solver(c)
+    s.set_primitive(torch.from_numpy(c.prim).to(dev))
+    for _ in range(args.warmup):
+        s.step(0.0)
+    dtd = torch.zeros(1, dtype=torch.float64, device=dev)
+    s.compute_dt(dtd)
+    dt = 0.9 * float(dtd.item())
+    U = torch.empty((c.n_v, c.cells), dtype=torch.float64, device=dev)
+    s.get_state(U)
+    R = torch.empty_like(U)
+    W = torch.randn(U.shape, dtype=torch.float64, generator=torch.Generator().manual_seed(0)).to(dev)
+    Ub = torch.zeros_like(U)
+
+    def timed(fn, k):
+        fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    k = max(args.steps, 5)
+    f = timed(lambda: s.rhs(U, R), k)
+    a = timed(lambda: s.rhs_adjoint(U, W, Ub), k)
+    fs = timed(lambda: s.step(dt), k)
+    s.set_state(U)
+    as_ = timed(lambda: s.step_adjoint(dt, Ub), k)
+    st = s.status()
+    s.close()
+    return {"workload": "sbi2d_n4_adjoint: 512x256, 4 species, viscous, fixed dt",
+            "rhs_ms": f, "rhs_adjoint_ms": a, "rhs_ratio": a / f,
+            "step_ms": fs, "step_adjoint_ms": as_, "step_ratio": as_ / fs,
+            "note": "step adjoint includes recomputing the two intermediate stage states",
+            "status_flags": st}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -246,14 +310,10 @@ def run_ours(args):
     prof = s.profile_read()
     s.profile(False)
     ms = ev0.elapsed_time(ev1)
-    ms_all = ms
-    if ws > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_all = float(t.item())
+    ms_all = reduce_max(ms, dev)
     status = s.status()
     cell_stages = case.cells * 3 * args.steps
-    value = ws * cell_stages / (ms_all * 1e-3)
+    value = whole_job_rate(cell_stages, ms_all * 1e-3, ws)
     launches = sum(n for _, n in prof.values())
 
     # ---- roofline of the dominant kernel class (the face-flux kernels)
@@ -288,15 +348,12 @@ def run_ours(args):
         s.step(0.0)
         s.get_state(Uh, Th)
         torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if ws > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_val = ws * case.cells * 3 * e2e_steps / e2e_s
+    e2e_s = reduce_max(time.perf_counter() - t0, dev)
+    e2e_val = whole_job_rate(case.cells * 3 * e2e_steps, e2e_s, ws)
     io_bytes = (case.n_v + 1) * case.cells * 8
     s.close()
     batched = None if args.no_batch else _batched_vs_per_instance(args, dev, stream)
+    adjoint = None if args.no_adjoint else _adjoint_vs_forward(args, dev, stream)
 
     if rank == 0:
         cpu = None
@@ -339,6 +396,8 @@ def run_ours(args):
             line["cpu_baseline"] = cpu
         if batched is not None:
             line["batched"] = batched
+        if adjoint is not None:
+            line["adjoint"] = adjoint
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -354,6 +413,7 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="sbi3d_n5")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-per-instance leg")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-vs-forward leg")
     ap.add_argument("--grid", default="", help="override the grid, e.g. 160,80,80 (profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)  # at least three untimed warm-up steps
