@@ -20,8 +20,8 @@
 namespace xf {
 
 // ------------------------------------------------------------ WENO5 adjoint
-// Forward intermediates of one WENO5-JS reconstruction (the same arithmetic
-// as weno5_nd), kept for its reverse.
+// Forward intermediates of one WENO5-JS reconstruction (the same function as
+// weno5_nd, with the linear weights applied explicitly), kept for its reverse.
 struct W5 {
   double a, b, c, d, t0, u0, t1, u1, t2, u2, s0, s1, s2, p12, p02, p01, w0, w1, w2, q0, q1, q2;
   double num, den;

@@ -268,6 +268,8 @@ xf_status fill_params(const xf_grid* g, const xf_thermo* th, const xf_opts* o, x
     for (int t = 0; t < N; ++t) {
       p->wA[s][t] = (1.0 / std::sqrt(8.0)) * std::pow(1.0 + th->W[s] / th->W[t], -0.5);
       p->wB[s][t] = std::pow(th->W[t] / th->W[s], 0.25);
+      p->wAB[s][t] = p->wA[s][t] * p->wB[s][t];
+      p->wABB[s][t] = p->wA[s][t] * p->wB[s][t] * p->wB[s][t];
     }
   const double a_ref = std::sqrt(th->a_ref2);
   p->fmu = 1.0 / (th->rho_ref * a_ref * th->L_ref);

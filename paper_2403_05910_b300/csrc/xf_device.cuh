@@ -43,6 +43,7 @@ struct Params {
   // transport
   double lnmu[MAXN][4], lnka[MAXN][4];
   double wA[MAXN][MAXN], wB[MAXN][MAXN];  // Wilke: A = (1+W_s/W_t)^-1/2 / sqrt 8, B = (W_t/W_s)^1/4
+  double wAB[MAXN][MAXN], wABB[MAXN][MAXN];  // A B and A B^2
   double invW[MAXN];
   double fmu, fka, inv_lewis;
   // numerics
@@ -238,21 +239,35 @@ __device__ __forceinline__ void prim_cell(const Params& p, long long t, const do
         xs += X[s];
       }
       const double ixs = 1.0 / xs;
-#pragma unroll
-      for (int s = 0; s < NS; ++s) X[s] *= ixs;
+      // Wilke denominators sum_t X_t A_st (1 + r_st B_st)^2 with r_st = (a_s/a_t)^(1/2),
+      // expanded: S0_s + 2 sqrt(a_s) S1_s + a_s S2_s, where S0_s = sum_t X_t A_st,
+      // S1_s = sum_t X_t a_t^(-1/2) A_st B_st, S2_s = sum_t X_t a_t^(-1) A_st B_st^2
+      // (all terms positive); S0 is shared by mu and kappa.
+      double xm1[NS], xm2[NS], xk1[NS], xk2[NS];
 #pragma unroll
       for (int s = 0; s < NS; ++s) {
-        double dm = 0.0, dk = 0.0;
+        X[s] *= ixs;
+        xm1[s] = X[s] * ismu[s];
+        xm2[s] = xm1[s] * ismu[s];
+        xk1[s] = X[s] * iska[s];
+        xk2[s] = xk1[s] * iska[s];
+      }
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        double s0 = 0.0, m1 = 0.0, m2 = 0.0, k1 = 0.0, k2 = 0.0;
 #pragma unroll
         for (int tt = 0; tt < NS; ++tt) {
-          const double bm = fma(smu[s] * ismu[tt], p.wB[s][tt], 1.0);
-          const double bk = fma(ska[s] * iska[tt], p.wB[s][tt], 1.0);
-          const double xa = X[tt] * p.wA[s][tt];
-          dm = fma(xa, bm * bm, dm);
-          dk = fma(xa, bk * bk, dk);
+          s0 = fma(X[tt], p.wA[s][tt], s0);
+          m1 = fma(xm1[tt], p.wAB[s][tt], m1);
+          m2 = fma(xm2[tt], p.wABB[s][tt], m2);
+          k1 = fma(xk1[tt], p.wAB[s][tt], k1);
+          k2 = fma(xk2[tt], p.wABB[s][tt], k2);
         }
-        mu = fma(X[s] * smu[s] * smu[s], 1.0 / dm, mu);
-        ka = fma(X[s] * ska[s] * ska[s], 1.0 / dk, ka);
+        const double mus = smu[s] * smu[s], kas = ska[s] * ska[s];
+        const double dm = fma(mus, m2, fma(2.0 * smu[s], m1, s0));
+        const double dk = fma(kas, k2, fma(2.0 * ska[s], k1, s0));
+        mu = fma(X[s] * mus, 1.0 / dm, mu);
+        ka = fma(X[s] * kas, 1.0 / dk, ka);
       }
       mu *= p.fmu;
       ka *= p.fka;
@@ -366,20 +381,25 @@ k_grad(const __grid_constant__ Params p, double* __restrict__ Q) {
 // 12 (12 b_k = 13 t_k^2 + 3 u_k^2, with 12 eps) -- a common factor that leaves
 // the weights unchanged -- and the nonlinear weights d_k/(eps + b_k)^2 are
 // scaled by prod_j (eps + b_j)^2, so no division is needed until the end.
-// The candidates enter as q_k - f2.
+// The linear weights d = (0.1, 0.6, 0.3) are folded into the indicators:
+// with s_k scaled by c_k = (d_i d_j / d_k)^(1/4) ({i, j, k} = {0, 1, 2}),
+// (s_i s_j)^2 already carries the factor d_k. The candidates enter as q_k - f2.
+constexpr double kWc0 = 1.158292185288269;   // (0.6 * 0.3 / 0.1)^(1/4)
+constexpr double kWc1 = 0.4728708045015879;  // (0.1 * 0.3 / 0.6)^(1/4)
+constexpr double kWc2 = 0.668740304976422;   // (0.1 * 0.6 / 0.3)^(1/4)
+
+// e12c[k] = 12 eps c_k (per face)
 __device__ __forceinline__ void weno5_nd(double f0, double f1, double f2, double f3, double f4,
-                                         double eps12, double& num, double& den) {
+                                         const double* e12c, double& num, double& den) {
   const double a = f1 - f0, b = f2 - f1, c = f3 - f2, d = f4 - f3;
   const double t0 = b - a, u0 = fma(3.0, b, -a);
   const double t1 = c - b, u1 = b + c;
   const double t2 = d - c, u2 = fma(-3.0, c, d);
-  const double s0 = fma(13.0 * t0, t0, fma(3.0 * u0, u0, eps12));
-  const double s1 = fma(13.0 * t1, t1, fma(3.0 * u1, u1, eps12));
-  const double s2 = fma(13.0 * t2, t2, fma(3.0 * u2, u2, eps12));
+  const double s0 = fma((13.0 * kWc0) * t0, t0, fma((3.0 * kWc0) * u0, u0, e12c[0]));
+  const double s1 = fma((13.0 * kWc1) * t1, t1, fma((3.0 * kWc1) * u1, u1, e12c[1]));
+  const double s2 = fma((13.0 * kWc2) * t2, t2, fma((3.0 * kWc2) * u2, u2, e12c[2]));
   const double p12 = s1 * s2, p02 = s0 * s2, p01 = s0 * s1;
-  const double w0 = (0.1 * p12) * p12;
-  const double w1 = (0.6 * p02) * p02;
-  const double w2 = (0.3 * p01) * p01;
+  const double w0 = p12 * p12, w1 = p02 * p02, w2 = p01 * p01;
   const double q0 = fma(5.0 / 6.0, b, (-1.0 / 3.0) * a);   // q_0 - f2
   const double q1 = fma(1.0 / 3.0, c, (1.0 / 6.0) * b);    // q_1 - f2
   const double q2 = fma(2.0 / 3.0, c, (-1.0 / 6.0) * d);   // q_2 - f2
@@ -390,10 +410,10 @@ __device__ __forceinline__ void weno5_nd(double f0, double f1, double f2, double
 // F^+ + F^- of one characteristic field (Eq. 15): the upwind reconstruction
 // of w^+ from i-2..i+2 and the mirrored one of w^- from i+3..i-1, normalised
 // by a single division.
-__device__ __forceinline__ double weno5_pair(const double* wp, const double* wm, double eps12) {
+__device__ __forceinline__ double weno5_pair(const double* wp, const double* wm, const double* e12c) {
   double np, dp, nm, dm;
-  weno5_nd(wp[0], wp[1], wp[2], wp[3], wp[4], eps12, np, dp);
-  weno5_nd(wm[5], wm[4], wm[3], wm[2], wm[1], eps12, nm, dm);
+  weno5_nd(wp[0], wp[1], wp[2], wp[3], wp[4], e12c, np, dp);
+  weno5_nd(wm[5], wm[4], wm[3], wm[2], wm[1], e12c, nm, dm);
   return (wp[2] + wm[3]) + fma(np, dm, nm * dp) / (dp * dm);
 }
 
@@ -504,6 +524,7 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
       gUh[m] = g;
     }
     const double eps12 = 12.0 * p.weno_eps;
+    const double e12c[3] = {eps12 * kWc0, eps12 * kWc1, eps12 * kWc2};
     const double chc = c * hic2;
     // ---- PER: one characteristic field at a time. With w = (1/2)(l.F_m +- a l.U_m)
     //      and l.F_m = u_m (l.U_m) + p_m (l[m_n] + u_m l[E]):
@@ -523,7 +544,7 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
           wp[m] = fma(hun[m] + ha, LU, pq);
           wm[m] = fma(hun[m] - ha, LU, pq);
         }
-        Fk_m = weno5_pair(wp, wm, eps12);
+        Fk_m = weno5_pair(wp, wm, e12c);
       }
       // u + c
       {
@@ -537,7 +558,7 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
           wp[m] = fma(hun[m] + ha, LU, pq);
           wm[m] = fma(hun[m] - ha, LU, pq);
         }
-        Fk_p = weno5_pair(wp, wm, eps12);
+        Fk_p = weno5_pair(wp, wm, e12c);
       }
       // entropy: l = e_rho - g / c^2
       {
@@ -550,7 +571,7 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
           wp[m] = fma(hun[m] + ha, LU, pq);
           wm[m] = fma(hun[m] - ha, LU, pq);
         }
-        Fk_e = weno5_pair(wp, wm, eps12);
+        Fk_e = weno5_pair(wp, wm, e12c);
       }
     }
     // back-projection of the three dense right columns (Eq. 15)
@@ -581,7 +602,7 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
         wp[m] = hp0[m] * LU;
         wm[m] = hm0[m] * LU;
       }
-      const double Fk = weno5_pair(wp, wm, eps12);
+      const double Fk = weno5_pair(wp, wm, e12c);
       Gout[1 + a] += Fk;
       Gout[IE] = fma(ub[a], Fk, Gout[IE]);
     }
@@ -595,7 +616,7 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
         wp[m] = hp0[m] * LU;
         wm[m] = hm0[m] * LU;
       }
-      const double Fk = weno5_pair(wp, wm, eps12);
+      const double Fk = weno5_pair(wp, wm, e12c);
       Gout[IE + 1 + s] += Fk;
       Gout[IE] = fma(-dphi[s] * iGam, Fk, Gout[IE]);
     }
