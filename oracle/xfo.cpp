@@ -485,8 +485,54 @@ void viscous_face(const Layout& L, const Thermo& th, const std::vector<Prim<S>>&
   for (int s = 0; s < N - 1; ++s) Fv[L.iY(s)] = -J[s];
 }
 
+// Positivity-preserving blend of one face (Eq. 17-20; reading): the blended
+// flux F* = (1 - theta) F_LF + theta F_hat, with F_LF the local Lax-Friedrichs
+// flux of Eq. 19 (alpha = max over the two cells of |u_d| + c), keeps every
+// partial density rho Y_s (s = 1..N) of the two one-sided states
+// U_i - 2 lam F* and U_{i+1} + 2 lam F* (Eq. 18) at or above
+// eps = min(pos_eps, its value with F_LF); lam = dim dt / dx_d. theta is the
+// smallest admissible value over those 2N conditions.
 template <class S>
-void rhs_impl(const xfo_params& p, const S* U, double* T, S* dUdt, uint32_t* st) {
+void positivity_blend(const Layout& L, const xfo_params& p, const Prim<S>& a, const Prim<S>& b,
+                      int d, double lam, S* Fh) {
+  int nv = L.nv, N = L.N;
+  S Fa[XFO_MAXV], Fb[XFO_MAXV];
+  phys_flux(L, a, d, Fa);
+  phys_flux(L, b, d, Fb);
+  S al = max_first(S(fabs(a.u[d]) + a.c), S(fabs(b.u[d]) + b.c));
+  S Flf[XFO_MAXV];
+  for (int v = 0; v < nv; ++v) Flf[v] = 0.5 * (Fa[v] + Fb[v] + al * (a.U[v] - b.U[v]));
+  S theta(1.0);
+  for (int s = 0; s < N; ++s) {
+    // partial density s and its flux components (the last one from rho - sum)
+    S qa, qb, fh, fl;
+    if (s < N - 1) {
+      qa = a.U[L.iY(s)]; qb = b.U[L.iY(s)]; fh = Fh[L.iY(s)]; fl = Flf[L.iY(s)];
+    } else {
+      qa = a.U[0]; qb = b.U[0]; fh = Fh[0]; fl = Flf[0];
+      for (int k = 0; k < N - 1; ++k) {
+        qa = qa - a.U[L.iY(k)]; qb = qb - b.U[L.iY(k)];
+        fh = fh - Fh[L.iY(k)]; fl = fl - Flf[L.iY(k)];
+      }
+    }
+    for (int side = 0; side < 2; ++side) {
+      double sg = side == 0 ? -2.0 * lam : 2.0 * lam;  // left cell: q - 2 lam F, right: q + 2 lam F
+      S q = side == 0 ? qa : qb;
+      S hi = q + sg * fh, lo = q + sg * fl;
+      S eps = lo < p.pos_eps ? lo : S(p.pos_eps);
+      if (hi < eps) {
+        S th = (lo - eps) / (lo - hi);
+        if (th < 0.0) th = S(0.0);
+        if (th < theta) theta = th;
+      }
+    }
+  }
+  if (theta < 1.0)
+    for (int v = 0; v < nv; ++v) Fh[v] = (1.0 - theta) * Flf[v] + theta * Fh[v];
+}
+
+template <class S>
+void rhs_impl(const xfo_params& p, const S* U, double* T, S* dUdt, uint32_t* st, double dt = 0.0) {
   Layout L(p);
   Thermo th(p);
   int nv = L.nv, dim = L.dim;
@@ -546,6 +592,8 @@ void rhs_impl(const xfo_params& p, const S* U, double* T, S* dUdt, uint32_t* st)
           for (int kk = 0; kk < nv; ++kk) a = a + Rm[j * nv + kk] * Fc[kk];
           Ft[j] = a;
         }
+        if (p.positivity && dt > 0.0)
+          positivity_blend(L, p, q[c0], q[c0 + sd], d, L.dim * dt / L.dx[d], Ft);
       }
       if (p.viscous) {
         S Fv[XFO_MAXV];
@@ -579,11 +627,11 @@ void rk3_impl(const xfo_params& p, S* U, double* T, double dt, uint32_t* st) {
   int64_t n = (int64_t)L.nv * L.cells;
   std::vector<S> U0(U, U + n), U1(n), U2(n), R(n);
   // Eq. 16
-  rhs_impl(p, U0.data(), T, R.data(), st);
+  rhs_impl(p, U0.data(), T, R.data(), st, dt);
   for (int64_t i = 0; i < n; ++i) U1[i] = U0[i] + dt * R[i];
-  rhs_impl(p, U1.data(), T, R.data(), st);
+  rhs_impl(p, U1.data(), T, R.data(), st, dt);
   for (int64_t i = 0; i < n; ++i) U2[i] = 0.75 * U0[i] + 0.25 * (U1[i] + dt * R[i]);
-  rhs_impl(p, U2.data(), T, R.data(), st);
+  rhs_impl(p, U2.data(), T, R.data(), st, dt);
   for (int64_t i = 0; i < n; ++i) U[i] = (1.0 / 3.0) * U0[i] + (2.0 / 3.0) * (U2[i] + dt * R[i]);
 }
 

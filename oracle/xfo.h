@@ -59,6 +59,8 @@ typedef struct {
   double newton_rtol;
   double weno_eps;
   int threads;                    /* OpenMP threads, 0 = default */
+  int positivity;                 /* positivity-preserving flux blend (Eq. 17-20) */
+  double pos_eps;                 /* target floor of the partial densities */
 } xfo_params;
 
 int xfo_nv(const xfo_params *p);

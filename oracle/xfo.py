@@ -26,6 +26,7 @@ class Params(C.Structure):
         ("rho_ref", C.c_double), ("L_ref", C.c_double), ("cfl", C.c_double),
         ("viscous", C.c_int), ("convective", C.c_int), ("newton_max", C.c_int),
         ("newton_rtol", C.c_double), ("weno_eps", C.c_double), ("threads", C.c_int),
+        ("positivity", C.c_int), ("pos_eps", C.c_double),
     ]
 
 
@@ -68,7 +69,7 @@ def _p(a: np.ndarray):
 
 
 def params(case, viscous=None, convective=True, threads=0, newton_max=50,
-           newton_rtol=1e-13, weno_eps=1e-6) -> Params:
+           newton_rtol=1e-13, weno_eps=1e-6, positivity=False, pos_eps=1e-13) -> Params:
     """Build the oracle parameter block from a generator ``Case``."""
     sp = case.species
     p = Params()
@@ -97,6 +98,8 @@ def params(case, viscous=None, convective=True, threads=0, newton_max=50,
     p.newton_rtol = newton_rtol
     p.weno_eps = weno_eps
     p.threads = threads
+    p.positivity = int(positivity)
+    p.pos_eps = pos_eps
     return p
 
 

@@ -417,3 +417,58 @@ def test_shock_bubble_interface_profile():
     grid = Y3.reshape(64, 128)
     assert grid[0, 32] > 0.99  # x = 0.504, y ~ 0: bubble centre
     assert grid[-1, -1] < 1e-3
+
+
+# ------------------------------------------------- positivity (Eq. 17-20) --
+
+def _double_rarefaction(n=200, uabs=2.0, bc=0):
+    """Two species meeting at x = 0.5 and pulled apart at |u| = uabs: the
+    expansion drives the interface towards vacuum."""
+    rng = np.random.default_rng(0)
+    sp = cases._draw_species(rng, np.array([0.028, 0.004]))
+    x = cases._centres(n, 0.0, 1.0)
+    left = x < 0.5
+    Y = np.stack([np.where(left, 1.0, 0.0), np.where(left, 0.0, 1.0)])
+    prim = cases._pack(1, np.ones(n), [np.where(left, -uabs, uabs)], np.full(n, 0.4), Y)
+    return cases.Case("rarefaction", 1, (n, 1, 1), (0.0,) * 3, (1.0,) * 3,
+                      ((bc, bc), (0, 0), (0, 0)), sp, cases.R_U * 300 / 0.028, 1.0, 1.0,
+                      False, 0.5, prim)
+
+
+def _min_partial(U):
+    return min(U[3].min(), (U[0] - U[3]).min())
+
+
+def test_positivity_blend_keeps_partial_densities_nonnegative():
+    c = _double_rarefaction()
+    mins = {}
+    for pos in (False, True):
+        o, U, T = _with_case(c, positivity=pos)
+        m = np.inf
+        for _ in range(150):
+            o.step(U, T, 0.0)
+            m = min(m, _min_partial(U))
+        mins[pos] = m
+    assert mins[False] < -1e-6          # the unblended scheme undershoots
+    assert mins[True] >= 0.0            # the blend keeps rho Y_s >= 0
+
+
+def test_positivity_blend_is_inactive_on_smooth_flow():
+    c = cases.smooth_periodic(2, (20, 16), 3, seed=31, amp=0.2)
+    out = []
+    for pos in (False, True):
+        o, U, T = _with_case(c, positivity=pos)
+        for _ in range(3):
+            o.step(U, T, 0.0)
+        out.append(U)
+    assert np.array_equal(out[0], out[1])
+
+
+def test_positivity_blend_is_conservative():
+    c = _double_rarefaction(n=120, uabs=3.0, bc=cases.BC_PERIODIC)
+    o, U, T = _with_case(c, positivity=True)
+    tot0 = U.sum(axis=1)
+    for _ in range(60):
+        o.step(U, T, 0.0)
+    assert np.max(np.abs(U.sum(axis=1) - tot0) / np.abs(U).sum(axis=1)) <= 1e-13
+    assert _min_partial(U) >= 0.0
