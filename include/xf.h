@@ -102,7 +102,14 @@ typedef struct xf_thermo {
 /* Numerical options. weno must be 5 and split 0 (LLF); viscous switches the
  * viscous + diffusion fluxes; convective switches the inviscid fluxes (off only
  * for testing the viscous operator); newton_max/newton_rtol bound the Newton
- * solve (stop when |dT| <= rtol T); weno_eps is the WENO5-JS epsilon. */
+ * solve (stop when |dT| <= rtol T); weno_eps is the WENO5-JS epsilon.
+ * positivity switches the positivity-preserving flux blend of Eq. 17-20 inside
+ * RK stages: F* = (1 - theta) F_LF + theta F_hat per face, with the local LF
+ * flux of Eq. 19 (alpha = max(|u_d| + c) of the two cells) and the smallest
+ * theta in [0, 1] that keeps every partial density rho Y_s of the one-sided
+ * states U_i - 2 lam F*, U_{i+1} + 2 lam F* (Eq. 18, lam = dim dt/dx_d) at or
+ * above min(pos_eps, its LF value). xf_rhs (no dt) never blends; the adjoint
+ * entry points reject handles with positivity on. */
 typedef struct xf_opts {
   double cfl;
   int weno;
@@ -112,6 +119,8 @@ typedef struct xf_opts {
   int newton_max;
   double newton_rtol;
   double weno_eps;
+  int positivity;
+  double pos_eps;
 } xf_opts;
 
 typedef struct xf_handle xf_handle;

@@ -35,7 +35,8 @@ inline unsigned blocks(long long n, int bs) { return (unsigned)((n + bs - 1) / b
 using PrimFn = void (*)(const xf::Params&, const double*, const double*, double*, double*,
                         uint32_t*, unsigned long long*, int, cudaStream_t);
 using GradFn = void (*)(const xf::Params&, double*, cudaStream_t);
-using FaceFn = void (*)(const xf::Params&, const double*, double*, uint32_t*, cudaStream_t);
+using FaceFn = void (*)(const xf::Params&, const double*, double*, uint32_t*, const double*,
+                        cudaStream_t);
 using UpdFn = void (*)(const xf::Params&, const double*, const double*, const double*,
                        const double*, const double*, double*, const double*, int, cudaStream_t);
 using FromPrimFn = void (*)(const xf::Params&, const double*, double*, double*, cudaStream_t);
@@ -70,11 +71,12 @@ struct Launch {
     xf::k_grad<DIM, NS><<<blocks(p.pcells, 256), 256, 0, s>>>(p, Q);
   }
   template <int D>
-  static void face(const xf::Params& p, const double* Q, double* G, uint32_t* fl, cudaStream_t s) {
+  static void face(const xf::Params& p, const double* Q, double* G, uint32_t* fl, const double* dt,
+                   cudaStream_t s) {
     if constexpr (D < DIM) {
       const long long nf =
           (long long)(p.n[0] + (D == 0)) * (p.n[1] + (D == 1)) * (p.n[2] + (D == 2));
-      xf::k_face<DIM, NS, D><<<blocks(nf, 128), 128, 0, s>>>(p, Q, G, fl);
+      xf::k_face<DIM, NS, D><<<blocks(nf, 128), 128, 0, s>>>(p, Q, G, fl, dt);
     }
   }
   static void update(const xf::Params& p, const double* Gx, const double* Gy, const double* Gz,
@@ -281,6 +283,9 @@ xf_status fill_params(const xf_grid* g, const xf_thermo* th, const xf_opts* o, x
   p->newton_max = o->newton_max;
   p->viscous = o->viscous ? 1 : 0;
   p->convective = o->convective ? 1 : 0;
+  p->positivity = o->positivity ? 1 : 0;
+  if (o->positivity && !(o->pos_eps >= 0.0)) return XF_ERR_ARG;
+  p->pos_eps = o->pos_eps;
   return XF_OK;
 }
 
@@ -311,7 +316,10 @@ void timed(xf_handle* h, int slot, cudaStream_t s, F&& fn) {
 }
 
 // Primitive recovery + (viscous) nodal gradients + every face flux of Uin.
-xf_status stage_fluxes(xf_handle* h, const double* Uin, int do_cfl, cudaStream_t s) {
+// Inside an RK stage (`stepping`) the face kernels see the stage dt, which the
+// positivity-preserving blend needs; a plain RHS has no dt.
+xf_status stage_fluxes(xf_handle* h, const double* Uin, int do_cfl, cudaStream_t s,
+                       bool stepping = false) {
   const xf::Params& p = h->p;
   timed(h, XF_PROF_PRIM, s, [&] {
     h->tab.prim(p, Uin, h->T[h->tcur], h->T[1 - h->tcur], h->Q, h->flags, h->red, do_cfl, s);
@@ -321,7 +329,8 @@ xf_status stage_fluxes(xf_handle* h, const double* Uin, int do_cfl, cudaStream_t
     timed(h, XF_PROF_DT, s, [&] { k_dt_finalize<<<1, 1, 0, s>>>(p, h->red, h->dt, nullptr); });
   if (p.viscous) timed(h, XF_PROF_GRAD, s, [&] { h->tab.grad(p, h->Q, s); });
   for (int d = 0; d < p.dim; ++d)
-    timed(h, XF_PROF_FACE_X + d, s, [&] { h->tab.face[d](p, h->Q, h->G[d], h->flags, s); });
+    timed(h, XF_PROF_FACE_X + d, s,
+          [&] { h->tab.face[d](p, h->Q, h->G[d], h->flags, stepping ? h->dt : nullptr, s); });
   XF_CUDA(cudaGetLastError());
   return XF_OK;
 }
@@ -571,17 +580,17 @@ xf_status xf_step_rk3(xf_handle* h, double dt, double* dt_dev_out, void* stream)
   const bool cfl = !(dt > 0.0);
   if (!cfl) k_set_scalar<<<1, 1, 0, s>>>(h->dt, dt);
   // Eq. 16: three stages, U^n kept in U, stages in Us
-  xf_status st = stage_fluxes(h, h->U, cfl ? 1 : 0, s);
+  xf_status st = stage_fluxes(h, h->U, cfl ? 1 : 0, s, true);
   if (st != XF_OK) return st;
   timed(h, XF_PROF_UPDATE, s, [&] {
     h->tab.update(p, h->G[0], h->G[1], h->G[2], h->U, h->U, h->Us, h->dt, 1, s);
   });
-  st = stage_fluxes(h, h->Us, 0, s);
+  st = stage_fluxes(h, h->Us, 0, s, true);
   if (st != XF_OK) return st;
   timed(h, XF_PROF_UPDATE, s, [&] {
     h->tab.update(p, h->G[0], h->G[1], h->G[2], h->U, h->Us, h->Us, h->dt, 2, s);
   });
-  st = stage_fluxes(h, h->Us, 0, s);
+  st = stage_fluxes(h, h->Us, 0, s, true);
   if (st != XF_OK) return st;
   timed(h, XF_PROF_UPDATE, s, [&] {
     h->tab.update(p, h->G[0], h->G[1], h->G[2], h->U, h->Us, h->U, h->dt, 3, s);
@@ -613,13 +622,13 @@ xf_status xf_clear_status(xf_handle* h, void* stream) {
 
 xf_status xf_rhs_adjoint(xf_handle* h, const double* U, const double* dUdt_bar, double* U_bar,
                          void* stream) {
-  if (!h || !U || !dUdt_bar || !U_bar) return XF_ERR_ARG;
+  if (!h || !U || !dUdt_bar || !U_bar || h->p.positivity) return XF_ERR_ARG;
   if (!is_device_ptr(U) || !is_device_ptr(dUdt_bar) || !is_device_ptr(U_bar)) return XF_ERR_ARG;
   return rhs_adjoint_impl(h, U, dUdt_bar, 1.0, U_bar, (cudaStream_t)stream);
 }
 
 xf_status xf_step_rk3_adjoint(xf_handle* h, double dt, double* U_bar, void* stream) {
-  if (!h || !U_bar || !(dt > 0.0)) return XF_ERR_ARG;
+  if (!h || !U_bar || !(dt > 0.0) || h->p.positivity) return XF_ERR_ARG;
   if (!is_device_ptr(U_bar)) return XF_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   xf_status st = ensure_adjoint_buffers(h);
@@ -830,7 +839,7 @@ xf_status xf_rhs_static(const xf_grid* grid, const xf_thermo* thermo, const xf_o
   }
   tab.prim(p, U, Tin, Tout, Q, flags, red, 0, s);
   if (p.viscous) tab.grad(p, Q, s);
-  for (int d = 0; d < p.dim; ++d) tab.face[d](p, Q, G[d], flags, s);
+  for (int d = 0; d < p.dim; ++d) tab.face[d](p, Q, G[d], flags, nullptr, s);
   tab.update(p, G[0], G[1], G[2], nullptr, nullptr, dUdt, dt, 0, s);
   XF_CUDA(cudaGetLastError());
   if (flags_out) {

@@ -94,9 +94,9 @@ __device__ __forceinline__ void b_prim(const BInst& I, long long t, const double
 }
 
 template <int NS>
-__device__ __forceinline__ void b_face(const BInst& I, int D, int fi, int fj) {
-  if (D == 0) xf::face_one<BDIM, NS, 0>(I.p, fi, fj, 0, I.Q, I.G[0], I.flags);
-  else xf::face_one<BDIM, NS, 1>(I.p, fi, fj, 0, I.Q, I.G[1], I.flags);
+__device__ __forceinline__ void b_face(const BInst& I, int D, int fi, int fj, double dt) {
+  if (D == 0) xf::face_one<BDIM, NS, 0>(I.p, fi, fj, 0, I.Q, I.G[0], I.flags, dt);
+  else xf::face_one<BDIM, NS, 1>(I.p, fi, fj, 0, I.Q, I.G[1], I.flags, dt);
 }
 
 // One RK stage (1, 2, 3) of every instance. tsel selects the temperature
@@ -205,11 +205,12 @@ k_batch_stage(const BInst* __restrict__ inst, const __grid_constant__ BCtl c, in
         fj = I.m1[D] + (int)(r / nf0);
       }
     }
+    const double dt = I.p.positivity ? __ldcg(I.dt) : 0.0;
     switch (I.p.N) {
-      case 2: b_face<2>(I, D, fi, fj); break;
-      case 3: b_face<3>(I, D, fi, fj); break;
-      case 4: b_face<4>(I, D, fi, fj); break;
-      default: b_face<5>(I, D, fi, fj); break;
+      case 2: b_face<2>(I, D, fi, fj, dt); break;
+      case 3: b_face<3>(I, D, fi, fj, dt); break;
+      case 4: b_face<4>(I, D, fi, fj, dt); break;
+      default: b_face<5>(I, D, fi, fj, dt); break;
     }
   }
   grid_barrier(c, nb);

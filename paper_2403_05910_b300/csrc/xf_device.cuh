@@ -49,6 +49,8 @@ struct Params {
   // numerics
   double cfl, weno_eps, newton_rtol;
   int viscous, convective, newton_max;
+  int positivity;    // positivity-preserving blend of the convective flux (Eq. 17-20)
+  double pos_eps;
   double hmin2_over_2dim;
 };
 
@@ -427,7 +429,7 @@ __device__ __forceinline__ double weno5_pair(const double* wp, const double* wm,
 template <int DIM, int NS, int D>
 __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk,
                                          const double* __restrict__ Q, double* __restrict__ Gf,
-                                         uint32_t* __restrict__ flags) {
+                                         uint32_t* __restrict__ flags, double dt) {
   using L = Lay<DIM, NS>;
   constexpr int NV = L::NV;
   constexpr int IE = DIM + 1;
@@ -622,6 +624,53 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
     }
   }
 
+  if (p.convective && p.positivity && dt > 0.0) {
+    // Positivity-preserving blend (Eq. 17-20): F* = (1 - theta) F_LF + theta F_hat
+    // with the local LF flux of Eq. 19 (alpha = max(|u_d| + c) of the two cells);
+    // theta keeps every partial density of U_i - 2 lam F* and U_{i+1} + 2 lam F*
+    // (Eq. 18, lam = dim dt / dx_d) at or above min(pos_eps, its LF value).
+    const double lam2 = 2.0 * DIM * dt * p.inv_dx[D];
+    double Fa[NV], Fb[NV], Ua[NV], Ub[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) { Ua[v] = QF(L::U + v, 0); Ub[v] = QF(L::U + v, 1); }
+    const double una = QF(L::UN + D, 0), unb = QF(L::UN + D, 1);
+    const double pa = QF(L::P, 0), pb = QF(L::P, 1);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) { Fa[v] = una * Ua[v]; Fb[v] = unb * Ub[v]; }
+    Fa[1 + D] += pa; Fb[1 + D] += pb;
+    Fa[IE] += pa * una; Fb[IE] += pb * unb;
+    const double al = fmax(fabs(una) + QF(L::C, 0), fabs(unb) + QF(L::C, 1));
+    double Flf[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Flf[v] = 0.5 * (Fa[v] + Fb[v] + al * (Ua[v] - Ub[v]));
+    double theta = 1.0;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      double qa, qb, fh, fl;
+      if (s < NS - 1) {
+        qa = Ua[IE + 1 + s]; qb = Ub[IE + 1 + s]; fh = Gout[IE + 1 + s]; fl = Flf[IE + 1 + s];
+      } else {
+        qa = Ua[0]; qb = Ub[0]; fh = Gout[0]; fl = Flf[0];
+#pragma unroll
+        for (int k = 0; k < NS - 1; ++k) {
+          qa -= Ua[IE + 1 + k]; qb -= Ub[IE + 1 + k]; fh -= Gout[IE + 1 + k]; fl -= Flf[IE + 1 + k];
+        }
+      }
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        const double sg = side == 0 ? -lam2 : lam2;
+        const double q = side == 0 ? qa : qb;
+        const double hi = fma(sg, fh, q), lo = fma(sg, fl, q);
+        const double eps = fmin(lo, p.pos_eps);
+        if (hi < eps) theta = fmin(theta, fmax((lo - eps) / (lo - hi), 0.0));
+      }
+    }
+    if (theta < 1.0) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Gout[v] = fma(theta, Gout[v] - Flf[v], Flf[v]);
+    }
+  }
+
   if (p.viscous) {
     // face values (-1, 9, 9, -1)/16, normal derivatives (1, -15, 15, -1)/(12 dx)
     const double wi = 1.0 / 16.0;
@@ -676,12 +725,12 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
 template <int DIM, int NS, int D>
 __global__ void __launch_bounds__(128, XF_FACE_MIN_BLOCKS)
 k_face(const __grid_constant__ Params p, const double* __restrict__ Q,
-       double* __restrict__ Gf, uint32_t* __restrict__ flags) {
+       double* __restrict__ Gf, uint32_t* __restrict__ flags, const double* __restrict__ dtp) {
   const int nf0 = p.n[0] + (D == 0), nf1 = p.n[1] + (D == 1), nf2 = p.n[2] + (D == 2);
   const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= (long long)nf0 * nf1 * nf2) return;
   face_one<DIM, NS, D>(p, (int)(f % nf0), (int)((f / nf0) % nf1), (int)(f / ((long long)nf0 * nf1)),
-                       Q, Gf, flags);
+                       Q, Gf, flags, dtp ? *dtp : 0.0);
 }
 
 // =============================================================== k_update ===

@@ -37,7 +37,7 @@ class Thermo(C.Structure):
 class Opts(C.Structure):
     _fields_ = [("cfl", C.c_double), ("weno", C.c_int), ("split", C.c_int), ("viscous", C.c_int),
                 ("convective", C.c_int), ("newton_max", C.c_int), ("newton_rtol", C.c_double),
-                ("weno_eps", C.c_double)]
+                ("weno_eps", C.c_double), ("positivity", C.c_int), ("pos_eps", C.c_double)]
 
 
 # every symbol declared in include/xf.h
@@ -128,7 +128,7 @@ def _dptr(a: np.ndarray):
 
 
 def structs(case, viscous=None, convective=True, cfl=None, newton_max=50, newton_rtol=1e-13,
-            weno_eps=1e-6):
+            weno_eps=1e-6, positivity=False, pos_eps=1e-13):
     """(Grid, Thermo, Opts, keepalive) from a generator ``Case``."""
     g = Grid()
     g.dim = case.dim
@@ -158,6 +158,8 @@ def structs(case, viscous=None, convective=True, cfl=None, newton_max=50, newton
     o.newton_max = newton_max
     o.newton_rtol = newton_rtol
     o.weno_eps = weno_eps
+    o.positivity = int(positivity)
+    o.pos_eps = pos_eps
     return g, t, o, keep
 
 
