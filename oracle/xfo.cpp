@@ -380,6 +380,56 @@ S weno5(const S* f, double eps) {
   return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
 }
 
+// WENO-CU6 at i+1/2 from f[0..5] = f_{i-2..i+3} (central-upwind, ref. 34).
+// Reading: candidates q_0..q_2 of WENO5 plus the downwind q_3 on {i+1, i+2,
+// i+3}; linear weights (1, 9, 9, 1)/20 (they make the 6-point central
+// scheme); beta_0..beta_2 the Jiang-Shu indicators; beta_3 = beta_6, the
+// Jiang-Shu indicator of the degree-5 polynomial on the whole stencil (integer
+// table below, /120960); tau_6 = beta_6 - (beta_0 + beta_2 + 4 beta_1)/6;
+// alpha_k = d_k (C + tau_6/(beta_k + eps)) with C = 20 and q = 1. The paper
+// gives no eps; the one of WENO5 is used (absolute, 1e-6 by default). With
+// the original 1e-40 the scheme is central wherever beta_k vanish to
+// round-off, and odd-even round-off modes of a smooth periodic wave grow
+// without bound over thousands of steps; 1e-6 keeps sixth order there.
+template <class S>
+S cu6_beta6(const S* f) {
+  static const int e[21][2] = {{0,0},{0,1},{0,2},{0,3},{0,4},{0,5},{1,1},{1,2},{1,3},{1,4},{1,5},
+                               {2,2},{2,3},{2,4},{2,5},{3,3},{3,4},{3,5},{4,4},{4,5},{5,5}};
+  static const double c[21] = {271779, -2380800, 4086352, -3462252, 1458762, -245620, 5653317,
+                               -20427884, 17905032, -7727988, 1325006, 19510972, -35817664,
+                               15929912, -2792660, 17195652, -15880404, 2863984, 3824847,
+                               -1429976, 139633};
+  S b(0.0);
+  for (int k = 0; k < 21; ++k) b = b + c[k] * f[e[k][0]] * f[e[k][1]];
+  return b / 120960.0;
+}
+
+template <class S>
+S weno_cu6(const S* f, double eps) {
+  const double C = 20.0, d[4] = {0.05, 0.45, 0.45, 0.05};
+  S b[4];
+  b[0] = (13.0 / 12.0) * (f[0] - 2.0 * f[1] + f[2]) * (f[0] - 2.0 * f[1] + f[2]) +
+         0.25 * (f[0] - 4.0 * f[1] + 3.0 * f[2]) * (f[0] - 4.0 * f[1] + 3.0 * f[2]);
+  b[1] = (13.0 / 12.0) * (f[1] - 2.0 * f[2] + f[3]) * (f[1] - 2.0 * f[2] + f[3]) +
+         0.25 * (f[1] - f[3]) * (f[1] - f[3]);
+  b[2] = (13.0 / 12.0) * (f[2] - 2.0 * f[3] + f[4]) * (f[2] - 2.0 * f[3] + f[4]) +
+         0.25 * (3.0 * f[2] - 4.0 * f[3] + f[4]) * (3.0 * f[2] - 4.0 * f[3] + f[4]);
+  b[3] = cu6_beta6(f);
+  S tau = b[3] - (b[0] + b[2] + 4.0 * b[1]) / 6.0;
+  S q[4];
+  q[0] = (2.0 * f[0] - 7.0 * f[1] + 11.0 * f[2]) / 6.0;
+  q[1] = (-f[1] + 5.0 * f[2] + 2.0 * f[3]) / 6.0;
+  q[2] = (2.0 * f[2] + 5.0 * f[3] - f[4]) / 6.0;
+  q[3] = (11.0 * f[3] - 7.0 * f[4] + 2.0 * f[5]) / 6.0;
+  S a[4], as(0.0), aq(0.0);
+  for (int k = 0; k < 4; ++k) {
+    a[k] = d[k] * (C + tau / (b[k] + eps));
+    as = as + a[k];
+    aq = aq + a[k] * q[k];
+  }
+  return aq / as;
+}
+
 // ------------------------------------------------------------ the RHS -----
 template <class S>
 struct Work {
@@ -580,12 +630,15 @@ void rhs_impl(const xfo_params& p, const S* U, double* T, S* dUdt, uint32_t* st,
         S Fc[XFO_MAXV];
         for (int kk = 0; kk < nv; ++kk) {
           S al = amax[lt[kk]];
-          S wp[5], wm[5];
-          for (int m = 0; m < 5; ++m) {
+          S wp[6], wm[6];
+          for (int m = 0; m < 6; ++m) {
             wp[m] = 0.5 * (LF[m][kk] + al * LU[m][kk]);           // m -> i-2+m
             wm[m] = 0.5 * (LF[5 - m][kk] - al * LU[5 - m][kk]);   // mirrored: i+3-m
           }
-          Fc[kk] = weno5(wp, p.weno_eps) + weno5(wm, p.weno_eps);
+          if (p.weno == 6)
+            Fc[kk] = weno_cu6(wp, p.weno_eps) + weno_cu6(wm, p.weno_eps);
+          else
+            Fc[kk] = weno5(wp, p.weno_eps) + weno5(wm, p.weno_eps);
         }
         for (int j = 0; j < nv; ++j) {  // back-projection (Eq. 15)
           S a(0.0);
@@ -637,6 +690,7 @@ void rk3_impl(const xfo_params& p, S* U, double* T, double dt, uint32_t* st) {
 
 int check(const xfo_params* p) {
   if (!p || p->dim < 1 || p->dim > 3 || p->N < 2 || p->N > XFO_MAXN) return -1;
+  if (p->weno != 5 && p->weno != 6) return -1;
   for (int a = 0; a < p->dim; ++a) if (p->n[a] < 1) return -1;
   for (int a = 0; a < p->dim; ++a)
     for (int s = 0; s < 2; ++s)
@@ -821,6 +875,8 @@ int xfo_flux(const xfo_params* p, int d, const double* U1, double T, double* F, 
 }
 
 double xfo_weno5(const double* f) { return weno5(f, 1e-6); }
+double xfo_weno_cu6(const double* f, double eps) { return weno_cu6(f, eps); }
+double xfo_cu6_beta6(const double* f) { return cu6_beta6(f); }
 
 int xfo_transport(const xfo_params* p, double T, double rho, const double* Y, double* mu,
                   double* kappa, double* D) {

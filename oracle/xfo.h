@@ -60,6 +60,7 @@ typedef struct {
   double weno_eps;
   int threads;                    /* OpenMP threads, 0 = default */
   int positivity;                 /* positivity-preserving flux blend (Eq. 17-20) */
+  int weno;                       /* 5: WENO5-JS, 6: WENO-CU6 */
   double pos_eps;                 /* target floor of the partial densities */
 } xfo_params;
 
@@ -96,6 +97,9 @@ int xfo_eigen(const xfo_params *p, int d, const double *UL, const double *UR,
 int xfo_flux(const xfo_params *p, int d, const double *U1, double T, double *F,
              uint32_t *status);
 double xfo_weno5(const double *f);
+/* WENO-CU6 at i+1/2 from f[0..5] = f_{i-2..i+3}; beta6 of the 6-point stencil */
+double xfo_weno_cu6(const double *f, double eps);
+double xfo_cu6_beta6(const double *f);
 /* per-cell mixture transport (dimensionless mu, kappa, D) */
 int xfo_transport(const xfo_params *p, double T, double rho, const double *Y,
                   double *mu, double *kappa, double *D);

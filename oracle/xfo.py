@@ -26,7 +26,7 @@ class Params(C.Structure):
         ("rho_ref", C.c_double), ("L_ref", C.c_double), ("cfl", C.c_double),
         ("viscous", C.c_int), ("convective", C.c_int), ("newton_max", C.c_int),
         ("newton_rtol", C.c_double), ("weno_eps", C.c_double), ("threads", C.c_int),
-        ("positivity", C.c_int), ("pos_eps", C.c_double),
+        ("positivity", C.c_int), ("weno", C.c_int), ("pos_eps", C.c_double),
     ]
 
 
@@ -56,6 +56,10 @@ def lib():
         L.xfo_flux.argtypes = [P, C.c_int, dp, C.c_double, dp, up]
         L.xfo_weno5.argtypes = [dp]
         L.xfo_weno5.restype = C.c_double
+        L.xfo_weno_cu6.argtypes = [dp, C.c_double]
+        L.xfo_weno_cu6.restype = C.c_double
+        L.xfo_cu6_beta6.argtypes = [dp]
+        L.xfo_cu6_beta6.restype = C.c_double
         L.xfo_transport.argtypes = [P, C.c_double, C.c_double, dp, dp, dp, dp]
         L.xfo_rhs_jvp.argtypes = [P, dp, dp, dp, dp, dp, up]
         L.xfo_rk3_jvp.argtypes = [P, dp, dp, dp, C.c_double, C.c_int, up]
@@ -69,7 +73,8 @@ def _p(a: np.ndarray):
 
 
 def params(case, viscous=None, convective=True, threads=0, newton_max=50,
-           newton_rtol=1e-13, weno_eps=1e-6, positivity=False, pos_eps=1e-13) -> Params:
+           newton_rtol=1e-13, weno_eps=1e-6, positivity=False, pos_eps=1e-13,
+           weno=5) -> Params:
     """Build the oracle parameter block from a generator ``Case``."""
     sp = case.species
     p = Params()
@@ -100,6 +105,7 @@ def params(case, viscous=None, convective=True, threads=0, newton_max=50,
     p.threads = threads
     p.positivity = int(positivity)
     p.pos_eps = pos_eps
+    p.weno = int(weno)
     return p
 
 
@@ -222,3 +228,13 @@ class Oracle:
 def weno5(f) -> float:
     f = np.ascontiguousarray(f, dtype=np.float64)
     return lib().xfo_weno5(_p(f))
+
+
+def weno_cu6(f, eps=1e-6) -> float:
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    return lib().xfo_weno_cu6(_p(f), eps)
+
+
+def cu6_beta6(f) -> float:
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    return lib().xfo_cu6_beta6(_p(f))

@@ -255,3 +255,70 @@ def test_roe_property_single_calorically_perfect_gas():
             lhs = R @ np.diag(lam) @ L @ (URs - ULs)
             rhs = o.flux(d, URs, TR) - o.flux(d, ULs, TL)
             assert np.allclose(lhs, rhs, rtol=1e-10, atol=1e-10 * np.max(np.abs(rhs)))
+
+
+# -------------------------------------------------------------- WENO-CU6 --
+
+def _beta6_from_definition():
+    """Jiang-Shu indicator of the degree-5 polynomial whose cell averages on
+    cells i-2..i+3 are f (dx = 1): sum_l int_{cell i} (p^(l))^2, derived here."""
+    import sympy as sp
+    x = sp.symbols("x")
+    f = sp.symbols("f0:6")
+    c = sp.symbols("c0:6")
+    p = sum(c[k] * x ** k for k in range(6))
+    half = sp.Rational(1, 2)
+    sol = sp.solve([sp.integrate(p, (x, j - half, j + half)) - f[j + 2] for j in range(-2, 4)], c)
+    p = p.subs(sol)
+    beta = sum(sp.integrate(sp.diff(p, x, l) ** 2, (x, -half, half)) for l in range(1, 6))
+    return sp.lambdify(f, sp.expand(beta), "math")
+
+
+def test_cu6_beta6_matches_its_definition():
+    from oracle.xfo import cu6_beta6
+    b6 = _beta6_from_definition()
+    rng = np.random.default_rng(41)
+    for _ in range(200):
+        f = rng.normal(size=6) * 10 ** rng.uniform(-2, 2)
+        ref = b6(*f)
+        assert cu6_beta6(f) == pytest.approx(ref, rel=1e-12, abs=1e-14 * np.max(f ** 2))
+
+
+def test_cu6_constant_and_linear():
+    from oracle.xfo import weno_cu6
+    rng = np.random.default_rng(42)
+    for _ in range(100):
+        a, b = rng.uniform(-5, 5, size=2)
+        assert weno_cu6(np.full(6, a)) == pytest.approx(a, rel=1e-15, abs=1e-15)
+        f = a + b * np.arange(-2, 4)
+        # linear data: tau_6 = 0, so the weights are (1, 9, 9, 1)/20 and the
+        # result is the 6-point central reconstruction
+        central = (f[0] - 8 * f[1] + 37 * f[2] + 37 * f[3] - 8 * f[4] + f[5]) / 60.0
+        assert weno_cu6(f) == pytest.approx(central, rel=1e-13, abs=1e-13)
+
+
+def test_cu6_sixth_order_flux_difference():
+    from oracle.xfo import weno_cu6
+    errs = []
+    for n in (20, 40, 80):
+        h = 1.0 / n
+        x = np.arange(-3, n + 4) * h
+        f = 2.0 + np.sin(2 * np.pi * x)
+        Fh = np.array([weno_cu6(f[i - 2:i + 4]) for i in range(2, n + 3)])
+        d = (Fh[1:] - Fh[:-1]) / h
+        ex = 2 * np.pi * np.cos(2 * np.pi * x[3:n + 3])
+        errs.append(np.max(np.abs(d - ex)))
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert orders[-1] > 5.5, (errs, orders)
+
+
+def test_cu6_picks_smooth_stencils_at_a_jump():
+    from oracle.xfo import weno_cu6
+    # jump between f_i and f_{i+1}: the flat stencil {i-2, i-1, i} (beta_0 = 0)
+    # outweighs every stencil that crosses the jump by ~1/eps, so the value
+    # stays O(eps) away from the upwind one (0) instead of the central 1/2
+    for eps in (1e-6, 1e-10):
+        v = weno_cu6(np.array([0.0, 0.0, 0.0, 1.0, 1.0, 1.0]), eps)
+        assert 0.0 <= v < 10 * eps, (eps, v)
+        w = weno_cu6(np.array([1.0, 1.0, 1.0, 0.0, 0.0, 0.0]), eps)
+        assert 0.0 <= 1.0 - w < 10 * eps, (eps, w)

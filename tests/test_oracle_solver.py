@@ -130,6 +130,30 @@ def test_design_order_density_wave():
     assert orders[-1] >= 4.5, (errs, orders)
 
 
+def test_design_order_density_wave_cu6():
+    """The same wave with WENO-CU6: sixth order on both refinements (dt ~ dx^2
+    keeps RK3 at dx^6). This also pins the regularising epsilon: with a
+    vanishing one (1e-40) the weights turn fully central where the
+    characteristic fields are flat to round-off, odd-even round-off modes grow
+    and the n = 160 error rises above the n = 80 one."""
+    errs = []
+    ns = (40, 80, 160)
+    for n in ns:
+        c = cases.density_wave(n)
+        o, U, T = _with_case(c, weno=6)
+        t_end = 0.1
+        dt0 = 0.4 * (1.0 / n) ** 2
+        steps = int(math.ceil(t_end / dt0))
+        dt = t_end / steps
+        for _ in range(steps):
+            o.step(U, T, dt)
+        x = cases._centres(n, 0.0, 1.0)
+        exact = 1.0 + 0.2 * np.sin(2 * np.pi * (x - t_end))
+        errs.append(np.mean(np.abs(U[0] - exact)))
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(len(ns) - 1)]
+    assert min(orders) >= 5.5, (errs, orders)
+
+
 # -------------------------------------------------------- viscous order ---
 
 def _viscous_rhs(c):
