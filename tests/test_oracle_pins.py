@@ -5,6 +5,7 @@ forms, algebraic identities, brute-force differences, exact solutions and
 conservation. None of them needs a GPU.
 """
 import math
+from fractions import Fraction
 
 import numpy as np
 import pytest
@@ -271,17 +272,35 @@ def _beta6_from_definition():
     sol = sp.solve([sp.integrate(p, (x, j - half, j + half)) - f[j + 2] for j in range(-2, 4)], c)
     p = p.subs(sol)
     beta = sum(sp.integrate(sp.diff(p, x, l) ** 2, (x, -half, half)) for l in range(1, 6))
-    return sp.lambdify(f, sp.expand(beta), "math")
+    terms = [(m, Fraction(int(cf.p), int(cf.q))) for m, cf in sp.Poly(beta, *f).terms()]
+
+    def exact(*v):
+        """beta_6 of the (binary-exact) inputs in rational arithmetic"""
+        fv = [Fraction(float(a)) for a in v]
+        tot = Fraction(0)
+        for m, cf in terms:
+            t = cf
+            for a, e in zip(fv, m):
+                t *= a ** e
+            tot += t
+        return float(tot)
+    return exact
 
 
 def test_cu6_beta6_matches_its_definition():
+    """Against the indicator derived above, evaluated exactly: on mean-free data
+    of any scale, and on small variations about an offset (smooth data), where
+    evaluating the quadratic form on raw values would lose most digits to
+    cancellation."""
     from oracle.xfo import cu6_beta6
     b6 = _beta6_from_definition()
     rng = np.random.default_rng(41)
     for _ in range(200):
         f = rng.normal(size=6) * 10 ** rng.uniform(-2, 2)
-        ref = b6(*f)
-        assert cu6_beta6(f) == pytest.approx(ref, rel=1e-12, abs=1e-14 * np.max(f ** 2))
+        assert cu6_beta6(f) == pytest.approx(b6(*f), rel=1e-12, abs=0.0)
+    for _ in range(200):
+        f = rng.uniform(-3, 3) + rng.normal(size=6) * 10 ** rng.uniform(-7, -1)
+        assert cu6_beta6(f) == pytest.approx(b6(*f), rel=1e-12, abs=0.0)
 
 
 def test_cu6_constant_and_linear():

@@ -132,10 +132,11 @@ def test_design_order_density_wave():
 
 def test_design_order_density_wave_cu6():
     """The same wave with WENO-CU6: sixth order on both refinements (dt ~ dx^2
-    keeps RK3 at dx^6). This also pins the regularising epsilon: with a
-    vanishing one (1e-40) the weights turn fully central where the
-    characteristic fields are flat to round-off, odd-even round-off modes grow
-    and the n = 160 error rises above the n = 80 one."""
+    keeps RK3 at dx^6). This also pins the regularising epsilon (with a
+    vanishing one, 1e-40, the weights leave their linear values near the
+    wave's extrema and the order drops to ~3.8) and the beta_6 evaluation
+    (on raw values it loses ~1e-3 of itself to cancellation on this wave,
+    and the n = 160 error rises above the n = 80 one)."""
     errs = []
     ns = (40, 80, 160)
     for n in ns:
