@@ -99,10 +99,14 @@ typedef struct xf_thermo {
   double a_ref2, rho_ref, L_ref;
 } xf_thermo;
 
-/* Numerical options. weno must be 5 and split 0 (LLF); viscous switches the
- * viscous + diffusion fluxes; convective switches the inviscid fluxes (off only
- * for testing the viscous operator); newton_max/newton_rtol bound the Newton
- * solve (stop when |dT| <= rtol T); weno_eps is the WENO5-JS epsilon.
+/* Numerical options. weno selects the reconstruction REC of Eq. 15: 5 for
+ * WENO5-JS (ref. 35), 6 for WENO-CU6 (ref. 34: linear weights (1,9,9,1)/20,
+ * C = 20, q = 1, tau = beta_6 - (beta_0 + beta_2 + 4 beta_1)/6); split must be
+ * 0 (LLF); viscous switches the viscous + diffusion fluxes; convective switches
+ * the inviscid fluxes (off only for testing the viscous operator);
+ * newton_max/newton_rtol bound the Newton solve (stop when |dT| <= rtol T);
+ * weno_eps is the absolute epsilon of both reconstructions. The batched form
+ * and the adjoint entry points support weno = 5 only (XF_ERR_ARG otherwise).
  * positivity switches the positivity-preserving flux blend of Eq. 17-20 inside
  * RK stages: F* = (1 - theta) F_LF + theta F_hat per face, with the local LF
  * flux of Eq. 19 (alpha = max(|u_d| + c) of the two cells) and the smallest

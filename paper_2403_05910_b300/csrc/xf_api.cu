@@ -51,6 +51,7 @@ struct Table {
   PrimFn prim;
   GradFn grad;
   FaceFn face[3];
+  FaceFn face6[3];  // WENO-CU6 reconstruction
   UpdFn update;
   FromPrimFn from_prim;
   int nq;
@@ -70,13 +71,13 @@ struct Launch {
   static void grad(const xf::Params& p, double* Q, cudaStream_t s) {
     xf::k_grad<DIM, NS><<<blocks(p.pcells, 256), 256, 0, s>>>(p, Q);
   }
-  template <int D>
+  template <int D, int REC = 5>
   static void face(const xf::Params& p, const double* Q, double* G, uint32_t* fl, const double* dt,
                    cudaStream_t s) {
     if constexpr (D < DIM) {
       const long long nf =
           (long long)(p.n[0] + (D == 0)) * (p.n[1] + (D == 1)) * (p.n[2] + (D == 2));
-      xf::k_face<DIM, NS, D><<<blocks(nf, 128), 128, 0, s>>>(p, Q, G, fl, dt);
+      xf::k_face<DIM, NS, D, REC><<<blocks(nf, 128), 128, 0, s>>>(p, Q, G, fl, dt);
     }
   }
   static void update(const xf::Params& p, const double* Gx, const double* Gy, const double* Gz,
@@ -114,7 +115,8 @@ struct Launch {
     xf::k_mixing<DIM, NS><<<blocks(p.cells, 256), 256, 0, s>>>(p, U, sp, dV, part, Ub);
   }
   static Table table() {
-    return Table{prim, grad, {face<0>, face<1>, face<2>}, update, from_prim, xf::Lay<DIM, NS>::NQ,
+    return Table{prim, grad, {face<0>, face<1>, face<2>}, {face<0, 6>, face<1, 6>, face<2, 6>},
+                 update, from_prim, xf::Lay<DIM, NS>::NQ,
                  {face_adj<0>, face_adj<1>, face_adj<2>}, grad_adj, prim_adj, from_prim_adj,
                  mixing};
   }
@@ -202,7 +204,7 @@ xf_status fill_params(const xf_grid* g, const xf_thermo* th, const xf_opts* o, x
   if (!g || !th || !o) return XF_ERR_ARG;
   if (g->dim < 1 || g->dim > 3) return XF_ERR_ARG;
   if (th->n_species < 2 || th->n_species > XF_MAX_SPECIES) return XF_ERR_ARG;
-  if (o->weno != 5 || o->split != 0) return XF_ERR_ARG;
+  if ((o->weno != 5 && o->weno != 6) || o->split != 0) return XF_ERR_ARG;
   if (!(o->cfl > 0.0) || o->newton_max < 1 || !(o->newton_rtol > 0.0) || !(o->weno_eps > 0.0))
     return XF_ERR_ARG;
   if (!th->W || !th->cp_coef || !th->h_off) return XF_ERR_ARG;
@@ -279,6 +281,7 @@ xf_status fill_params(const xf_grid* g, const xf_thermo* th, const xf_opts* o, x
   p->inv_lewis = o->viscous ? 1.0 / th->lewis : 0.0;
   p->cfl = o->cfl;
   p->weno_eps = o->weno_eps;
+  p->weno = o->weno;
   p->newton_rtol = o->newton_rtol;
   p->newton_max = o->newton_max;
   p->viscous = o->viscous ? 1 : 0;
@@ -330,7 +333,10 @@ xf_status stage_fluxes(xf_handle* h, const double* Uin, int do_cfl, cudaStream_t
   if (p.viscous) timed(h, XF_PROF_GRAD, s, [&] { h->tab.grad(p, h->Q, s); });
   for (int d = 0; d < p.dim; ++d)
     timed(h, XF_PROF_FACE_X + d, s,
-          [&] { h->tab.face[d](p, h->Q, h->G[d], h->flags, stepping ? h->dt : nullptr, s); });
+          [&] {
+            (p.weno == 6 ? h->tab.face6 : h->tab.face)[d](p, h->Q, h->G[d], h->flags,
+                                                          stepping ? h->dt : nullptr, s);
+          });
   XF_CUDA(cudaGetLastError());
   return XF_OK;
 }
@@ -622,13 +628,13 @@ xf_status xf_clear_status(xf_handle* h, void* stream) {
 
 xf_status xf_rhs_adjoint(xf_handle* h, const double* U, const double* dUdt_bar, double* U_bar,
                          void* stream) {
-  if (!h || !U || !dUdt_bar || !U_bar || h->p.positivity) return XF_ERR_ARG;
+  if (!h || !U || !dUdt_bar || !U_bar || h->p.positivity || h->p.weno != 5) return XF_ERR_ARG;
   if (!is_device_ptr(U) || !is_device_ptr(dUdt_bar) || !is_device_ptr(U_bar)) return XF_ERR_ARG;
   return rhs_adjoint_impl(h, U, dUdt_bar, 1.0, U_bar, (cudaStream_t)stream);
 }
 
 xf_status xf_step_rk3_adjoint(xf_handle* h, double dt, double* U_bar, void* stream) {
-  if (!h || !U_bar || !(dt > 0.0) || h->p.positivity) return XF_ERR_ARG;
+  if (!h || !U_bar || !(dt > 0.0) || h->p.positivity || h->p.weno != 5) return XF_ERR_ARG;
   if (!is_device_ptr(U_bar)) return XF_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   xf_status st = ensure_adjoint_buffers(h);

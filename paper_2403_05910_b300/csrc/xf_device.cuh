@@ -49,6 +49,7 @@ struct Params {
   // numerics
   double cfl, weno_eps, newton_rtol;
   int viscous, convective, newton_max;
+  int weno;          // 5: WENO5-JS, 6: WENO-CU6
   int positivity;    // positivity-preserving blend of the convective flux (Eq. 17-20)
   double pos_eps;
   double hmin2_over_2dim;
@@ -419,6 +420,76 @@ __device__ __forceinline__ double weno5_pair(const double* wp, const double* wm,
   return (wp[2] + wm[3]) + fma(np, dm, nm * dp) / (dp * dm);
 }
 
+// WENO-CU6 (central-upwind, ref. 34): candidates q_0..q_2 of WENO5 and the
+// downwind q_3 on {i+1, i+2, i+3}, linear weights (1, 9, 9, 1)/20, beta_3 the
+// Jiang-Shu indicator beta_6 of the degree-5 polynomial on all six cells,
+// tau = beta_6 - (beta_0 + beta_2 + 4 beta_1)/6 and
+// alpha_k = d_k (C + tau/(beta_k + eps)), C = 20.
+// Everything is scaled by 12 as in WENO5 and multiplied through by
+// prod_j s_j (s_j = 12 (beta_j + eps)): alpha_k ~ d_k (C s_k + 12 tau) prod_{j!=k} s_j,
+// so one division per field pair remains. beta_6 is evaluated on the first
+// differences x = (f1-f0, .., f5-f4) as sum_k D_k y_k^2, y = L^T x, the LDL^T
+// factorisation of its quadratic form (exact rationals, rounded to double);
+// on differences it keeps its digits on smooth data with a large offset.
+constexpr double kB6D[5] = {12.0 * 2.2468501984126985, 12.0 * 3.6320275079835525,
+                            12.0 * 4.2138861378223531, 12.0 * 1.0316113515772065,
+                            12.0 * 0.038978122273068759};
+constexpr double kB6L10 = -3.3800293620919937, kB6L20 = 4.1377553085411307,
+                 kB6L30 = -2.2318538224071762, kB6L40 = 0.45187450097321719;
+constexpr double kB6L21 = -1.8788632502196132, kB6L31 = 1.2398246217680282,
+                 kB6L41 = -0.28359452031236648;
+constexpr double kB6L32 = -0.86413844801584661, kB6L42 = 0.22441845180562248;
+constexpr double kB6L43 = -0.38419782506660333;
+
+// e12 = 12 eps
+__device__ __forceinline__ void cu6_nd(double f0, double f1, double f2, double f3, double f4,
+                                       double f5, double e12, double& num, double& den) {
+  const double a = f1 - f0, b = f2 - f1, c = f3 - f2, d = f4 - f3, e = f5 - f4;
+  const double t0 = b - a, u0 = fma(3.0, b, -a);
+  const double t1 = c - b, u1 = b + c;
+  const double t2 = d - c, u2 = fma(-3.0, c, d);
+  const double b0 = fma(13.0 * t0, t0, 3.0 * u0 * u0);   // 12 beta_0
+  const double b1 = fma(13.0 * t1, t1, 3.0 * u1 * u1);
+  const double b2 = fma(13.0 * t2, t2, 3.0 * u2 * u2);
+  const double y4 = e;
+  const double y3 = fma(kB6L43, e, d);
+  const double y2 = fma(kB6L42, e, fma(kB6L32, d, c));
+  const double y1 = fma(kB6L41, e, fma(kB6L31, d, fma(kB6L21, c, b)));
+  const double y0 = fma(kB6L40, e, fma(kB6L30, d, fma(kB6L20, c, fma(kB6L10, b, a))));
+  const double b6 = fma(kB6D[0] * y0, y0, fma(kB6D[1] * y1, y1, fma(kB6D[2] * y2, y2,
+                    fma(kB6D[3] * y3, y3, kB6D[4] * y4 * y4))));
+  const double tau = b6 - (b0 + b2 + 4.0 * b1) * (1.0 / 6.0);   // 12 tau
+  const double s0 = b0 + e12, s1 = b1 + e12, s2 = b2 + e12, s3 = b6 + e12;
+  const double p01 = s0 * s1, p23 = s2 * s3;
+  const double w0 = 0.05 * fma(20.0, s0, tau) * (s1 * p23);
+  const double w1 = 0.45 * fma(20.0, s1, tau) * (s0 * p23);
+  const double w2 = 0.45 * fma(20.0, s2, tau) * (p01 * s3);
+  const double w3 = 0.05 * fma(20.0, s3, tau) * (p01 * s2);
+  const double q0 = fma(5.0 / 6.0, b, (-1.0 / 3.0) * a);    // q_0 - f2
+  const double q1 = fma(1.0 / 3.0, c, (1.0 / 6.0) * b);     // q_1 - f2
+  const double q2 = fma(2.0 / 3.0, c, (-1.0 / 6.0) * d);    // q_2 - f2
+  const double q3 = fma(1.0 / 3.0, e, fma(-5.0 / 6.0, d, c));  // q_3 - f2
+  num = fma(w0, q0, fma(w1, q1, fma(w2, q2, w3 * q3)));
+  den = (w0 + w1) + (w2 + w3);
+}
+
+// F^+ + F^- of one characteristic field with WENO-CU6: w^+ from i-2..i+3 and
+// the mirrored w^- from i+3..i-2; e4[3] = 12 eps.
+__device__ __forceinline__ double cu6_pair(const double* wp, const double* wm, const double* e4) {
+  double np, dp, nm, dm;
+  cu6_nd(wp[0], wp[1], wp[2], wp[3], wp[4], wp[5], e4[3], np, dp);
+  cu6_nd(wm[5], wm[4], wm[3], wm[2], wm[1], wm[0], e4[3], nm, dm);
+  return (wp[2] + wm[3]) + fma(np, dm, nm * dp) / (dp * dm);
+}
+
+// the reconstruction of Eq. 15 selected by REC (5: WENO5-JS, 6: WENO-CU6);
+// e4 = {12 eps c_0, 12 eps c_1, 12 eps c_2, 12 eps}
+template <int REC>
+__device__ __forceinline__ double rec_pair(const double* wp, const double* wm, const double* e4) {
+  if constexpr (REC == 6) return cu6_pair(wp, wm, e4);
+  else return weno5_pair(wp, wm, e4);
+}
+
 // ================================================================= k_face ===
 // One thread per face of direction D (faces i = 0..n_D, left cell i-1).
 #ifndef XF_FACE_MIN_BLOCKS
@@ -426,7 +497,7 @@ __device__ __forceinline__ double weno5_pair(const double* wp, const double* wm,
 #endif
 // Per-face body: face (fi, fj, fk) of direction D, i.e. between cells
 // idx - e_D and idx (fi in 0..n_0 when D = 0, and so on).
-template <int DIM, int NS, int D>
+template <int DIM, int NS, int D, int REC = 5>
 __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk,
                                          const double* __restrict__ Q, double* __restrict__ Gf,
                                          uint32_t* __restrict__ flags, double dt) {
@@ -526,7 +597,7 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
       gUh[m] = g;
     }
     const double eps12 = 12.0 * p.weno_eps;
-    const double e12c[3] = {eps12 * kWc0, eps12 * kWc1, eps12 * kWc2};
+    const double e12c[4] = {eps12 * kWc0, eps12 * kWc1, eps12 * kWc2, eps12};
     const double chc = c * hic2;
     // ---- PER: one characteristic field at a time. With w = (1/2)(l.F_m +- a l.U_m)
     //      and l.F_m = u_m (l.U_m) + p_m (l[m_n] + u_m l[E]):
@@ -546,7 +617,7 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
           wp[m] = fma(hun[m] + ha, LU, pq);
           wm[m] = fma(hun[m] - ha, LU, pq);
         }
-        Fk_m = weno5_pair(wp, wm, e12c);
+        Fk_m = rec_pair<REC>(wp, wm, e12c);
       }
       // u + c
       {
@@ -560,7 +631,7 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
           wp[m] = fma(hun[m] + ha, LU, pq);
           wm[m] = fma(hun[m] - ha, LU, pq);
         }
-        Fk_p = weno5_pair(wp, wm, e12c);
+        Fk_p = rec_pair<REC>(wp, wm, e12c);
       }
       // entropy: l = e_rho - g / c^2
       {
@@ -573,7 +644,7 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
           wp[m] = fma(hun[m] + ha, LU, pq);
           wm[m] = fma(hun[m] - ha, LU, pq);
         }
-        Fk_e = weno5_pair(wp, wm, e12c);
+        Fk_e = rec_pair<REC>(wp, wm, e12c);
       }
     }
     // back-projection of the three dense right columns (Eq. 15)
@@ -604,7 +675,7 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
         wp[m] = hp0[m] * LU;
         wm[m] = hm0[m] * LU;
       }
-      const double Fk = weno5_pair(wp, wm, e12c);
+      const double Fk = rec_pair<REC>(wp, wm, e12c);
       Gout[1 + a] += Fk;
       Gout[IE] = fma(ub[a], Fk, Gout[IE]);
     }
@@ -618,7 +689,7 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
         wp[m] = hp0[m] * LU;
         wm[m] = hm0[m] * LU;
       }
-      const double Fk = weno5_pair(wp, wm, e12c);
+      const double Fk = rec_pair<REC>(wp, wm, e12c);
       Gout[IE + 1 + s] += Fk;
       Gout[IE] = fma(-dphi[s] * iGam, Fk, Gout[IE]);
     }
@@ -722,14 +793,14 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
   raise(flags, st);
 }
 
-template <int DIM, int NS, int D>
+template <int DIM, int NS, int D, int REC = 5>
 __global__ void __launch_bounds__(128, XF_FACE_MIN_BLOCKS)
 k_face(const __grid_constant__ Params p, const double* __restrict__ Q,
        double* __restrict__ Gf, uint32_t* __restrict__ flags, const double* __restrict__ dtp) {
   const int nf0 = p.n[0] + (D == 0), nf1 = p.n[1] + (D == 1), nf2 = p.n[2] + (D == 2);
   const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= (long long)nf0 * nf1 * nf2) return;
-  face_one<DIM, NS, D>(p, (int)(f % nf0), (int)((f / nf0) % nf1), (int)(f / ((long long)nf0 * nf1)),
+  face_one<DIM, NS, D, REC>(p, (int)(f % nf0), (int)((f / nf0) % nf1), (int)(f / ((long long)nf0 * nf1)),
                        Q, Gf, flags, dtp ? *dtp : 0.0);
 }
 

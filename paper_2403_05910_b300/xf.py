@@ -128,8 +128,9 @@ def _dptr(a: np.ndarray):
 
 
 def structs(case, viscous=None, convective=True, cfl=None, newton_max=50, newton_rtol=1e-13,
-            weno_eps=1e-6, positivity=False, pos_eps=1e-13):
-    """(Grid, Thermo, Opts, keepalive) from a generator ``Case``."""
+            weno_eps=1e-6, positivity=False, pos_eps=1e-13, weno=5):
+    """(Grid, Thermo, Opts, keepalive) from a generator ``Case``. ``weno``: 5
+    for WENO5-JS, 6 for WENO-CU6."""
     g = Grid()
     g.dim = case.dim
     for a in range(3):
@@ -151,7 +152,7 @@ def structs(case, viscous=None, convective=True, cfl=None, newton_max=50, newton
     t.a_ref2, t.rho_ref, t.L_ref = case.a_ref2, case.rho_ref, case.L_ref
     o = Opts()
     o.cfl = case.cfl if cfl is None else cfl
-    o.weno = 5
+    o.weno = int(weno)
     o.split = 0
     o.viscous = int(case.viscous if viscous is None else viscous)
     o.convective = int(convective)

@@ -1,0 +1,116 @@
+"""WENO-CU6 reconstruction (ref. 34, one of the REC choices of Eq. 15) on the
+GPU: parity with the oracle's CU6 on the RHS, one step and ten steps; sixth
+order on the advected density wave; and the entry points that support WENO5
+only (the adjoint and the batched form) refuse a CU6 handle.
+
+Tolerances as for WENO5: 1e-11 for one RHS and one step, 1e-8 after ten steps
+(per-field max |gpu - ref| / max |ref|).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2403_05910_b300 import cases
+from oracle.xfo import Oracle
+
+from gpu_util import dev, field_err, gpu_rhs, gpu_solver, gpu_steps
+
+pytestmark = pytest.mark.gpu
+
+
+def _cases():
+    return {
+        "tube1d_n2": cases.shock_tube(0, n=400),
+        "tube1d_n2_ragged": cases.shock_tube(3, n=301),
+        "sbi2d_n3_visc": cases.config(1, n=(96, 48)),
+        "sbi3d_n5_visc": cases.config(2, n=(40, 20, 20)),
+        "sbi2d_n5_inviscid": cases.shock_bubble(2, (61, 37), 5, 2.2, 0.2, seed=4, viscous=False),
+        "smooth2d_n3_periodic": cases.smooth_periodic(2, (33, 29), 3, seed=5, amp=0.3),
+    }
+
+
+CASES = _cases()
+
+
+def _oracle(case, **kw):
+    o = Oracle(case, weno=6, **kw)
+    U, T = o.prim_to_cons()
+    return o, U, T
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_cu6_rhs(name):
+    case = CASES[name]
+    o, U, T = _oracle(case)
+    R, To, st = o.rhs(U, T.copy())
+    Rg, Tg, stg = gpu_rhs(case, U, T, weno=6)
+    assert np.max(field_err(Rg, R, case.dim)) <= 1e-11
+    assert stg == st == 0
+    # and it is a different scheme from WENO5 on these states
+    R5, _, _ = Oracle(case).rhs(U, T.copy())
+    assert np.max(field_err(R5, R, case.dim)) > 1e-8
+
+
+@pytest.mark.parametrize("name,steps,tol", [("tube1d_n2", 1, 1e-11), ("sbi2d_n3_visc", 1, 1e-11),
+                                            ("sbi3d_n5_visc", 1, 1e-11), ("tube1d_n2", 10, 1e-8),
+                                            ("sbi2d_n5_inviscid", 10, 1e-8),
+                                            ("smooth2d_n3_periodic", 10, 1e-8)])
+def test_cu6_steps(name, steps, tol):
+    case = CASES[name]
+    o, U, T = _oracle(case)
+    U1, T1 = U.copy(), T.copy()
+    dts = []
+    for _ in range(steps):
+        dt, st = o.step(U1, T1, 0.0)
+        assert st == 0
+        dts.append(dt)
+    Ug, Tg, stg, dtg = gpu_steps(case, U, T, steps, weno=6)
+    assert stg == 0
+    assert np.max(np.abs(np.array(dtg) - dts) / np.array(dts)) <= tol
+    assert np.max(field_err(Ug, U1, case.dim)) <= tol
+
+
+def test_cu6_with_positivity_blend():
+    """CU6 feeding the blend of Eq. 17-20 (one step, shock-bubble state)."""
+    case = cases.config(4, n=(48, 24))
+    o, U, T = _oracle(case, positivity=True)
+    U1, T1 = U.copy(), T.copy()
+    o.step(U1, T1, 0.0)
+    Ug, _, st, _ = gpu_steps(case, U, T, 1, weno=6, positivity=True)
+    assert st == 0
+    assert np.max(field_err(Ug, U1, case.dim)) <= 1e-11
+
+
+def test_cu6_sixth_order_density_wave():
+    """rho = 1 + 0.2 sin(2 pi x) advected to t = 0.1 with dt ~ dx^2: the L1
+    error of the CUDA path falls at sixth order, as the oracle's does."""
+    errs = []
+    for n in (40, 80, 160):
+        c = cases.density_wave(n)
+        U, T = Oracle(c).prim_to_cons()
+        dt0 = 0.4 * (1.0 / n) ** 2
+        steps = int(math.ceil(0.1 / dt0))
+        Ug, _, st, _ = gpu_steps(c, U, T, steps, dt=0.1 / steps, weno=6)
+        assert st == 0
+        x = cases._centres(n, 0.0, 1.0)
+        errs.append(np.mean(np.abs(Ug[0] - (1.0 + 0.2 * np.sin(2 * np.pi * (x - 0.1))))))
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert min(orders) >= 5.5, (errs, orders)
+
+
+def test_cu6_refused_where_unsupported():
+    import torch
+    from paper_2403_05910_b300.xf import Batch, XFError
+    case = cases.config(1, n=(24, 12))
+    U, T = Oracle(case).prim_to_cons()
+    s = gpu_solver(case, weno=6)
+    s.set_state(dev(U), dev(T))
+    Ub = torch.zeros((case.n_v, case.cells), dtype=torch.float64, device="cuda")
+    with pytest.raises(XFError):
+        s.rhs_adjoint(dev(U), dev(U), Ub)
+    with pytest.raises(XFError):
+        s.step_adjoint(1e-5, Ub)
+    s.close()
+    with pytest.raises(XFError):
+        Batch([case], weno=6)
