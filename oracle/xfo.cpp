@@ -20,7 +20,9 @@
 namespace {
 
 constexpr double kRu = 8.314462618;  // J/(mol K), Eq. 7
-constexpr int G = 3;                 // ghost layers for the 6-point WENO5 stencil
+// ghost layers: the flux at i+1/2 reads cells i-G+1 .. i+G (WENO5 and
+// WENO-CU6: 6 cells; WENO7: 8 cells)
+inline int ghosts(int weno) { return weno == 7 ? 4 : 3; }
 
 // ------------------------------------------------------------ dual numbers --
 template <int K>
@@ -82,13 +84,13 @@ template <class S> S max_first(const S& a, const S& b) { return (b > a) ? b : a;
 
 // ------------------------------------------------------------ layout -------
 struct Layout {
-  int dim, N, nv;
+  int dim, N, nv, G;
   int64_t n[3], np[3], cells, pcells;
   double dx[3];
   int iE() const { return 1 + dim; }
   int iY(int s) const { return 2 + dim + s; }
   explicit Layout(const xfo_params& p) {
-    dim = p.dim; N = p.N; nv = dim + 2 + N - 1;
+    dim = p.dim; N = p.N; nv = dim + 2 + N - 1; G = ghosts(p.weno);
     cells = 1; pcells = 1;
     for (int a = 0; a < 3; ++a) {
       n[a] = (a < dim) ? p.n[a] : 1;
@@ -435,6 +437,51 @@ S weno_cu6(const S* f, double eps) {
   return aq / as;
 }
 
+// WENO7-JS at i+1/2 from f[0..6] = f_{i-3..i+3} (ref. 36; reading): the four
+// cubic candidates on {i-3+k .. i+k}, linear weights (1, 12, 18, 4)/35 (they
+// make the 7-point upwind scheme), Jiang-Shu indicators of the cubics (the
+// integer tables below, /240), alpha_k = d_k/(eps + beta_k)^2 with the WENO5
+// epsilon. The indicators are evaluated on f - f_i (they integrate derivatives
+// only).
+template <class S>
+S weno7_beta(const S* g, int k) {
+  // beta_0 on g[0..3]; beta_3 is beta_0 mirrored (g[6..3]); beta_2 mirrors beta_1
+  static const int e[10][2] = {{0,0},{0,1},{0,2},{0,3},{1,1},{1,2},{1,3},{2,2},{2,3},{3,3}};
+  static const double c0[10] = {547, -3882, 4642, -1854, 7043, -17246, 7042, 11003, -9402, 2107};
+  static const double c1[10] = {267, -1642, 1602, -494, 2843, -5966, 1922, 3443, -2522, 547};
+  S h[4];
+  for (int m = 0; m < 4; ++m) {
+    if (k == 0) h[m] = g[m];
+    else if (k == 1) h[m] = g[1 + m];
+    else if (k == 2) h[m] = g[5 - m];
+    else h[m] = g[6 - m];
+  }
+  const double* c = (k == 0 || k == 3) ? c0 : c1;
+  S b(0.0);
+  for (int t = 0; t < 10; ++t) b = b + c[t] * h[e[t][0]] * h[e[t][1]];
+  return b / 240.0;
+}
+
+template <class S>
+S weno7(const S* f, double eps) {
+  const double d[4] = {1.0 / 35.0, 12.0 / 35.0, 18.0 / 35.0, 4.0 / 35.0};
+  S g[7];
+  for (int m = 0; m < 7; ++m) g[m] = f[m] - f[3];
+  S q[4];
+  q[0] = (-3.0 * f[0] + 13.0 * f[1] - 23.0 * f[2] + 25.0 * f[3]) / 12.0;
+  q[1] = (f[1] - 5.0 * f[2] + 13.0 * f[3] + 3.0 * f[4]) / 12.0;
+  q[2] = (-f[2] + 7.0 * f[3] + 7.0 * f[4] - f[5]) / 12.0;
+  q[3] = (3.0 * f[3] + 13.0 * f[4] - 5.0 * f[5] + f[6]) / 12.0;
+  S as(0.0), aq(0.0);
+  for (int k = 0; k < 4; ++k) {
+    S b = weno7_beta(g, k);
+    S a = d[k] / ((eps + b) * (eps + b));
+    as = as + a;
+    aq = aq + a * q[k];
+  }
+  return aq / as;
+}
+
 // ------------------------------------------------------------ the RHS -----
 template <class S>
 struct Work {
@@ -447,7 +494,7 @@ void fill_padded(const Layout& L, const Thermo& th, const xfo_params& p, const S
   q.resize(L.pcells);
   uint32_t s_all = 0;
   int64_t lo[3], hi[3];
-  for (int a = 0; a < 3; ++a) { lo[a] = (a < L.dim) ? -G : 0; hi[a] = (a < L.dim) ? L.n[a] + G : 1; }
+  for (int a = 0; a < 3; ++a) { lo[a] = (a < L.dim) ? -L.G : 0; hi[a] = (a < L.dim) ? L.n[a] + L.G : 1; }
   int64_t nx = hi[0] - lo[0], ny = hi[1] - lo[1], nz = hi[2] - lo[2];
 #pragma omp parallel for schedule(static) reduction(| : s_all)
   for (int64_t t = 0; t < nx * ny * nz; ++t) {
@@ -616,10 +663,11 @@ void rhs_impl(const xfo_params& p, const S* U, double* T, S* dUdt, uint32_t* st,
         int lt[XFO_MAXV];
         eigen(L, th, q[c0], q[c0 + sd], d, Lm, Rm, lam, lt, &c2, &sl);
         // stencil m = i-2 .. i+3: characteristic projections (Eq. 14)
-        S LU[6][XFO_MAXV], LF[6][XFO_MAXV];
+        const int W = 2 * L.G;  // stencil cells i-G+1 .. i+G
+        S LU[8][XFO_MAXV], LF[8][XFO_MAXV];
         S amax[3] = {S(0.0), S(0.0), S(0.0)};
-        for (int m = 0; m < 6; ++m) {
-          const Prim<S>& cm = q[c0 + (m - 2) * sd];
+        for (int m = 0; m < W; ++m) {
+          const Prim<S>& cm = q[c0 + (m - L.G + 1) * sd];
           S F[XFO_MAXV];
           phys_flux(L, cm, d, F);
           for (int kk = 0; kk < nv; ++kk) {
@@ -635,12 +683,14 @@ void rhs_impl(const xfo_params& p, const S* U, double* T, S* dUdt, uint32_t* st,
         S Fc[XFO_MAXV];
         for (int kk = 0; kk < nv; ++kk) {
           S al = amax[lt[kk]];
-          S wp[6], wm[6];
-          for (int m = 0; m < 6; ++m) {
-            wp[m] = 0.5 * (LF[m][kk] + al * LU[m][kk]);           // m -> i-2+m
-            wm[m] = 0.5 * (LF[5 - m][kk] - al * LU[5 - m][kk]);   // mirrored: i+3-m
+          S wp[8], wm[8];
+          for (int m = 0; m < W; ++m) {
+            wp[m] = 0.5 * (LF[m][kk] + al * LU[m][kk]);                   // m -> i-G+1+m
+            wm[m] = 0.5 * (LF[W - 1 - m][kk] - al * LU[W - 1 - m][kk]);   // mirrored: i+G-m
           }
-          if (p.weno == 6)
+          if (p.weno == 7)
+            Fc[kk] = weno7(wp, p.weno_eps) + weno7(wm, p.weno_eps);
+          else if (p.weno == 6)
             Fc[kk] = weno_cu6(wp, p.weno_eps) + weno_cu6(wm, p.weno_eps);
           else
             Fc[kk] = weno5(wp, p.weno_eps) + weno5(wm, p.weno_eps);
@@ -695,11 +745,11 @@ void rk3_impl(const xfo_params& p, S* U, double* T, double dt, uint32_t* st) {
 
 int check(const xfo_params* p) {
   if (!p || p->dim < 1 || p->dim > 3 || p->N < 2 || p->N > XFO_MAXN) return -1;
-  if (p->weno != 5 && p->weno != 6) return -1;
+  if (p->weno != 5 && p->weno != 6 && p->weno != 7) return -1;
   for (int a = 0; a < p->dim; ++a) if (p->n[a] < 1) return -1;
   for (int a = 0; a < p->dim; ++a)
     for (int s = 0; s < 2; ++s)
-      if (p->bc[a][s] == XFO_BC_PERIODIC && p->n[a] < G) return -1;
+      if (p->bc[a][s] != XFO_BC_TRANSMISSIVE && p->n[a] < ghosts(p->weno)) return -1;
 #ifdef _OPENMP
   if (p->threads > 0) omp_set_num_threads(p->threads);
 #endif
@@ -881,6 +931,7 @@ int xfo_flux(const xfo_params* p, int d, const double* U1, double T, double* F, 
 
 double xfo_weno5(const double* f) { return weno5(f, 1e-6); }
 double xfo_weno_cu6(const double* f, double eps) { return weno_cu6(f, eps); }
+double xfo_weno7(const double* f, double eps) { return weno7(f, eps); }
 double xfo_cu6_beta6(const double* f) { return cu6_beta6(f); }
 
 int xfo_transport(const xfo_params* p, double T, double rho, const double* Y, double* mu,

@@ -60,7 +60,7 @@ typedef struct {
   double weno_eps;
   int threads;                    /* OpenMP threads, 0 = default */
   int positivity;                 /* positivity-preserving flux blend (Eq. 17-20) */
-  int weno;                       /* 5: WENO5-JS, 6: WENO-CU6 */
+  int weno;                       /* 5: WENO5-JS, 6: WENO-CU6, 7: WENO7-JS */
   double pos_eps;                 /* target floor of the partial densities */
 } xfo_params;
 
@@ -100,6 +100,8 @@ double xfo_weno5(const double *f);
 /* WENO-CU6 at i+1/2 from f[0..5] = f_{i-2..i+3}; beta6 of the 6-point stencil */
 double xfo_weno_cu6(const double *f, double eps);
 double xfo_cu6_beta6(const double *f);
+/* WENO7-JS at i+1/2 from f[0..6] = f_{i-3..i+3} */
+double xfo_weno7(const double *f, double eps);
 /* per-cell mixture transport (dimensionless mu, kappa, D) */
 int xfo_transport(const xfo_params *p, double T, double rho, const double *Y,
                   double *mu, double *kappa, double *D);

@@ -58,6 +58,8 @@ def lib():
         L.xfo_weno5.restype = C.c_double
         L.xfo_weno_cu6.argtypes = [dp, C.c_double]
         L.xfo_weno_cu6.restype = C.c_double
+        L.xfo_weno7.argtypes = [dp, C.c_double]
+        L.xfo_weno7.restype = C.c_double
         L.xfo_cu6_beta6.argtypes = [dp]
         L.xfo_cu6_beta6.restype = C.c_double
         L.xfo_transport.argtypes = [P, C.c_double, C.c_double, dp, dp, dp, dp]
@@ -233,6 +235,11 @@ def weno5(f) -> float:
 def weno_cu6(f, eps=1e-6) -> float:
     f = np.ascontiguousarray(f, dtype=np.float64)
     return lib().xfo_weno_cu6(_p(f), eps)
+
+
+def weno7(f, eps=1e-6) -> float:
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    return lib().xfo_weno7(_p(f), eps)
 
 
 def cu6_beta6(f) -> float:

@@ -341,3 +341,97 @@ def test_cu6_picks_smooth_stencils_at_a_jump():
         assert 0.0 <= v < 10 * eps, (eps, v)
         w = weno_cu6(np.array([1.0, 1.0, 1.0, 0.0, 0.0, 0.0]), eps)
         assert 0.0 <= 1.0 - w < 10 * eps, (eps, w)
+
+
+# ---------------------------------------------------------------- WENO7 --
+
+def _weno7_parts():
+    """Candidates, 7-point upwind value and Jiang-Shu indicators of the cubics
+    on {i-3+k .. i+k} (cell averages f_0..f_6 = f_{i-3..i+3}, dx = 1), derived
+    here from their definitions."""
+    import sympy as sp
+    x = sp.symbols("x")
+    f = sp.symbols("f0:7")
+    half = sp.Rational(1, 2)
+
+    def poly_on(cells):
+        c = sp.symbols("c0:%d" % len(cells))
+        p = sum(c[k] * x ** k for k in range(len(cells)))
+        sol = sp.solve([sp.integrate(p, (x, j - half, j + half)) - f[j + 3] for j in cells], c)
+        return p.subs(sol)
+
+    betas = []
+    for k in range(4):
+        p = poly_on(list(range(-3 + k, 1 + k)))
+        b = sp.expand(sum(sp.integrate(sp.diff(p, x, l) ** 2, (x, -half, half)) for l in range(1, 4)))
+        betas.append([(m, Fraction(int(cf.p), int(cf.q))) for m, cf in sp.Poly(b, *f).terms()])
+    full = sp.expand(poly_on(list(range(-3, 4))).subs(x, half))
+    return betas, sp.lambdify(f, full, "math")
+
+
+def _exact_form(terms, v):
+    fv = [Fraction(float(a)) for a in v]
+    tot = Fraction(0)
+    for m, cf in terms:
+        t = cf
+        for a, e in zip(fv, m):
+            t *= a ** e
+        tot += t
+    return tot
+
+
+def test_weno7_weights_follow_the_indicators():
+    """With the indicators computed exactly from their definition, the weights
+    d_k/(eps + beta_k)^2 (d = (1, 12, 18, 4)/35) and the cubic candidates give
+    the oracle's value; probes both smooth data about an offset and rough data."""
+    from oracle.xfo import weno7
+    betas, _ = _weno7_parts()
+    d = [Fraction(1, 35), Fraction(12, 35), Fraction(18, 35), Fraction(4, 35)]
+    cand = [(-3, 13, -23, 25, 0, 0, 0), (0, 1, -5, 13, 3, 0, 0), (0, 0, -1, 7, 7, -1, 0),
+            (0, 0, 0, 3, 13, -5, 1)]
+    rng = np.random.default_rng(43)
+    eps = Fraction(1, 10 ** 6)
+    for scale in (1e-4, 1e-2, 1.0, 10.0):
+        for _ in range(40):
+            f = rng.uniform(-2, 2) + rng.normal(size=7) * scale
+            fv = [Fraction(float(a)) for a in f]
+            al = [d[k] / (eps + _exact_form(betas[k], f)) ** 2 for k in range(4)]
+            q = [sum(Fraction(c) * a for c, a in zip(cand[k], fv)) / 12 for k in range(4)]
+            ref = float(sum(a * b for a, b in zip(al, q)) / sum(al))
+            assert weno7(f) == pytest.approx(ref, rel=1e-12, abs=1e-14 * np.max(np.abs(f)))
+
+
+def test_weno7_exact_for_cubics_and_seventh_order():
+    """Cell averages of a cubic: every candidate is exact, so is the scheme.
+    Smooth data with eps far above every indicator (weights at their linear
+    values): the flux difference converges at seventh order, which fixes the
+    linear weights. (With eps = 1e-6 the Jiang-Shu weights lose order at the
+    extrema in the max norm, as WENO-JS schemes do.)"""
+    from oracle.xfo import weno7
+    rng = np.random.default_rng(44)
+    for _ in range(50):
+        c = rng.normal(size=4)
+        P = lambda t: c[0] * t + c[1] * t ** 2 / 2 + c[2] * t ** 3 / 3 + c[3] * t ** 4 / 4
+        avg = np.array([P(j + 0.5) - P(j - 0.5) for j in range(-3, 4)])
+        exact = c[0] + c[1] * 0.5 + c[2] * 0.25 + c[3] * 0.125
+        assert weno7(avg) == pytest.approx(exact, rel=1e-12, abs=1e-12)
+    errs = []
+    for n in (20, 40, 80):
+        h = 1.0 / n
+        x = np.arange(-4, n + 5) * h
+        f = 2.0 + np.sin(2 * np.pi * x)
+        Fh = np.array([weno7(f[i - 3:i + 4], 1e6) for i in range(3, n + 5)])
+        dd = (Fh[1:] - Fh[:-1]) / h
+        ex = 2 * np.pi * np.cos(2 * np.pi * x[4:n + 5])
+        errs.append(np.max(np.abs(dd - ex)))
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert orders[-1] > 6.5, (errs, orders)
+
+
+def test_weno7_picks_the_smooth_stencil_at_a_jump():
+    from oracle.xfo import weno7
+    for eps in (1e-6, 1e-10):
+        v = weno7(np.array([0.0, 0.0, 0.0, 0.0, 1.0, 1.0, 1.0]), eps)
+        assert 0.0 <= v < 10 * eps ** 2 * 1e6, (eps, v)
+        w = weno7(np.array([1.0, 1.0, 1.0, 1.0, 0.0, 0.0, 0.0]), eps)
+        assert 0.0 <= 1.0 - w < 10 * eps ** 2 * 1e6, (eps, w)

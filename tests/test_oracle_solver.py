@@ -1,5 +1,6 @@
 """Solver-level pins of the CPU oracle: invariants, conservation, convergence
 orders, symmetry and an exact Riemann solution. CPU only."""
+import dataclasses
 import math
 
 import numpy as np
@@ -23,12 +24,13 @@ def _nv_slices(c):
 
 # ---------------------------------------------------------------- uniform --
 
+@pytest.mark.parametrize("weno", [5, 6, 7])
 @pytest.mark.parametrize("dim", [1, 2, 3])
 @pytest.mark.parametrize("bc", [cases.BC_PERIODIC, cases.BC_TRANSMISSIVE])
-def test_uniform_state_has_zero_rhs(dim, bc):
+def test_uniform_state_has_zero_rhs(dim, bc, weno):
     n = {1: (16,), 2: (12, 10), 3: (8, 7, 6)}[dim]
     c = cases.uniform_state(dim, n, 3, seed=dim, bc=bc, viscous=True)
-    o, U, T = _with_case(c)
+    o, U, T = _with_case(c, weno=weno)
     R, T2, st = o.rhs(U, T)
     assert st == 0
     scale = np.max(np.abs(U), axis=1)[:, None] / min(c.dx[:dim])
@@ -92,10 +94,11 @@ def test_general_contact_pressure_error_is_small():
 
 # ----------------------------------------------------------- conservation --
 
+@pytest.mark.parametrize("weno", [5, 6, 7])
 @pytest.mark.parametrize("dim,n", [(1, (40,)), (2, (24, 20)), (3, (10, 9, 8))])
-def test_discrete_conservation_periodic_viscous(dim, n):
+def test_discrete_conservation_periodic_viscous(dim, n, weno):
     c = cases.smooth_periodic(dim, n, 3, seed=11 + dim, amp=0.2, viscous=True)
-    o, U, T = _with_case(c)
+    o, U, T = _with_case(c, weno=weno)
     tot0 = U.sum(axis=1)
     scale = np.abs(U).sum(axis=1)
     dt = o.dt(U, T)
@@ -153,6 +156,27 @@ def test_design_order_density_wave_cu6():
         errs.append(np.mean(np.abs(U[0] - exact)))
     orders = [math.log2(errs[i] / errs[i + 1]) for i in range(len(ns) - 1)]
     assert min(orders) >= 5.5, (errs, orders)
+
+
+def test_design_order_density_wave_weno7():
+    """The same wave with WENO7-JS (8-cell stencil, 4 ghost layers) on 20, 40
+    and 80 cells with dt ~ dx^(7/3): orders 6.2 and 6.3, approaching 7."""
+    errs = []
+    ns = (20, 40, 80)
+    for n in ns:
+        c = cases.density_wave(n)
+        o, U, T = _with_case(c, weno=7)
+        t_end = 0.1
+        dt0 = 0.4 * (1.0 / n) ** (7.0 / 3.0)
+        steps = int(math.ceil(t_end / dt0))
+        dt = t_end / steps
+        for _ in range(steps):
+            o.step(U, T, dt)
+        x = cases._centres(n, 0.0, 1.0)
+        exact = 1.0 + 0.2 * np.sin(2 * np.pi * (x - t_end))
+        errs.append(np.mean(np.abs(U[0] - exact)))
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(len(ns) - 1)]
+    assert min(orders) >= 6.0, (errs, orders)
 
 
 # -------------------------------------------------------- viscous order ---
@@ -306,6 +330,33 @@ def test_axis_permutation_symmetry_3d():
     Rback = Rp.reshape(7, 8, 8, 8)[perm].transpose(0, 1, 3, 2).reshape(7, -1)
     scale = np.max(np.abs(R), axis=1, keepdims=True)
     assert np.max(np.abs(Rback - R) / scale) <= 1e-13
+
+
+@pytest.mark.parametrize("weno", [5, 6, 7])
+@pytest.mark.parametrize("bc", [cases.BC_PERIODIC, cases.BC_TRANSMISSIVE])
+def test_reflection_symmetry_1d(weno, bc):
+    """x -> L - x (cells reversed, u negated) maps the RHS onto itself
+    reflected: the mirrored reconstruction of w^- must be the exact image of
+    the upwind one of w^+, for every scheme (a shifted or reversed stencil
+    breaks it). A random rough state, so that every weight is exercised."""
+    rng = np.random.default_rng(31 + weno)
+    c = cases.smooth_periodic(1, (37,), 3, seed=31, amp=0.2, viscous=True)
+    P = c.prim.copy()
+    P *= 1.0 + 0.1 * rng.uniform(-1, 1, size=P.shape) * (np.arange(P.shape[0]) != 1)[:, None]
+    P[1] += 0.3 * rng.normal(size=P.shape[1])
+    P[3:] = np.abs(P[3:]) / (np.abs(P[3:]).sum(axis=0) + 0.2)
+    c = dataclasses.replace(c, prim=P, bc=((bc, bc), (0, 0), (0, 0)))
+    o, U, T = _with_case(c, weno=weno)
+    R, _, st = o.rhs(U, T.copy())
+    assert st == 0
+    Ur, Tr = U[:, ::-1].copy(), T[::-1].copy()
+    Ur[1] = -Ur[1]
+    Rr, _, st = o.rhs(Ur, Tr)
+    assert st == 0
+    Rr = Rr[:, ::-1].copy()
+    Rr[1] = -Rr[1]
+    scale = np.max(np.abs(R), axis=1, keepdims=True)
+    assert np.max(np.abs(Rr - R) / scale) <= 1e-12
 
 
 @pytest.mark.parametrize("viscous", [False, True])
