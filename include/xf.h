@@ -68,7 +68,7 @@ typedef enum {
 #define XF_BC_PERIODIC 1     /* both sides of an axis must be periodic */
 #define XF_BC_SYMMETRIC 2    /* mirror; the normal momentum changes sign */
 
-/* Uniform cell-centred grid. dim in {1,2,3}; n[a] >= 3 for active axes
+/* Uniform cell-centred grid. dim in {1,2,3}; n[a] >= 3 (>= 4 with WENO7) for active axes
  * (n[a] is ignored for a >= dim); [lo, hi] is the dimensionless extent. */
 typedef struct xf_grid {
   int dim;
@@ -101,7 +101,9 @@ typedef struct xf_thermo {
 
 /* Numerical options. weno selects the reconstruction REC of Eq. 15: 5 for
  * WENO5-JS (ref. 35), 6 for WENO-CU6 (ref. 34: linear weights (1,9,9,1)/20,
- * C = 20, q = 1, tau = beta_6 - (beta_0 + beta_2 + 4 beta_1)/6); split must be
+ * C = 20, q = 1, tau = beta_6 - (beta_0 + beta_2 + 4 beta_1)/6), 7 for
+ * WENO7-JS (ref. 36: linear weights (1,12,18,4)/35; 8-cell stencil, 4 ghost
+ * layers, so every axis needs n >= 4, else n >= 3); split must be
  * 0 (LLF); viscous switches the viscous + diffusion fluxes; convective switches
  * the inviscid fluxes (off only for testing the viscous operator);
  * newton_max/newton_rtol bound the Newton solve (stop when |dT| <= rtol T);

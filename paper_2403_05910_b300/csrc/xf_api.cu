@@ -50,8 +50,9 @@ using MixFn = void (*)(const xf::Params&, const double*, int, double, double*, d
 struct Table {
   PrimFn prim;
   GradFn grad;
-  FaceFn face[3];
-  FaceFn face6[3];  // WENO-CU6 reconstruction
+  FaceFn face[3];   // WENO5-JS reconstruction
+  FaceFn face6[3];  // WENO-CU6
+  FaceFn face7[3];  // WENO7-JS
   UpdFn update;
   FromPrimFn from_prim;
   int nq;
@@ -116,11 +117,16 @@ struct Launch {
   }
   static Table table() {
     return Table{prim, grad, {face<0>, face<1>, face<2>}, {face<0, 6>, face<1, 6>, face<2, 6>},
-                 update, from_prim, xf::Lay<DIM, NS>::NQ,
+                 {face<0, 7>, face<1, 7>, face<2, 7>}, update, from_prim, xf::Lay<DIM, NS>::NQ,
                  {face_adj<0>, face_adj<1>, face_adj<2>}, grad_adj, prim_adj, from_prim_adj,
                  mixing};
   }
 };
+
+// face-flux launchers of the handle's reconstruction
+inline const FaceFn* faces_of(const Table& t, int weno) {
+  return weno == 7 ? t.face7 : (weno == 6 ? t.face6 : t.face);
+}
 
 template <int DIM>
 bool pick_n(int N, Table* t) {
@@ -204,7 +210,7 @@ xf_status fill_params(const xf_grid* g, const xf_thermo* th, const xf_opts* o, x
   if (!g || !th || !o) return XF_ERR_ARG;
   if (g->dim < 1 || g->dim > 3) return XF_ERR_ARG;
   if (th->n_species < 2 || th->n_species > XF_MAX_SPECIES) return XF_ERR_ARG;
-  if ((o->weno != 5 && o->weno != 6) || o->split != 0) return XF_ERR_ARG;
+  if (o->weno < 5 || o->weno > 7 || o->split != 0) return XF_ERR_ARG;
   if (!(o->cfl > 0.0) || o->newton_max < 1 || !(o->newton_rtol > 0.0) || !(o->weno_eps > 0.0))
     return XF_ERR_ARG;
   if (!th->W || !th->cp_coef || !th->h_off) return XF_ERR_ARG;
@@ -220,14 +226,15 @@ xf_status fill_params(const xf_grid* g, const xf_thermo* th, const xf_opts* o, x
   double hmin = 1e300;
   for (int a = 0; a < 3; ++a) {
     if (a < dim) {
-      if (g->n[a] < 3 || g->n[a] > (1 << 24)) return XF_ERR_ARG;
+      const int G = xf::ghosts(o->weno);
+      if (g->n[a] < G || g->n[a] > (1 << 24)) return XF_ERR_ARG;
       if (!(g->hi[a] > g->lo[a])) return XF_ERR_ARG;
       for (int s = 0; s < 2; ++s)
         if (g->bc[a][s] < 0 || g->bc[a][s] > 2) return XF_ERR_ARG;
       if ((g->bc[a][0] == XF_BC_PERIODIC) != (g->bc[a][1] == XF_BC_PERIODIC)) return XF_ERR_ARG;
       p->n[a] = (int)g->n[a];
-      p->np[a] = p->n[a] + 2 * xf::G;
-      p->go[a] = xf::G;
+      p->np[a] = p->n[a] + 2 * G;
+      p->go[a] = G;
       const double dx = (g->hi[a] - g->lo[a]) / (double)g->n[a];
       p->inv_dx[a] = 1.0 / dx;
       hmin = std::fmin(hmin, dx);
@@ -334,8 +341,8 @@ xf_status stage_fluxes(xf_handle* h, const double* Uin, int do_cfl, cudaStream_t
   for (int d = 0; d < p.dim; ++d)
     timed(h, XF_PROF_FACE_X + d, s,
           [&] {
-            (p.weno == 6 ? h->tab.face6 : h->tab.face)[d](p, h->Q, h->G[d], h->flags,
-                                                          stepping ? h->dt : nullptr, s);
+            faces_of(h->tab, p.weno)[d](p, h->Q, h->G[d], h->flags, stepping ? h->dt : nullptr,
+                                        s);
           });
   XF_CUDA(cudaGetLastError());
   return XF_OK;
@@ -845,7 +852,7 @@ xf_status xf_rhs_static(const xf_grid* grid, const xf_thermo* thermo, const xf_o
   }
   tab.prim(p, U, Tin, Tout, Q, flags, red, 0, s);
   if (p.viscous) tab.grad(p, Q, s);
-  for (int d = 0; d < p.dim; ++d) tab.face[d](p, Q, G[d], flags, nullptr, s);
+  for (int d = 0; d < p.dim; ++d) faces_of(tab, p.weno)[d](p, Q, G[d], flags, nullptr, s);
   tab.update(p, G[0], G[1], G[2], nullptr, nullptr, dUdt, dt, 0, s);
   XF_CUDA(cudaGetLastError());
   if (flags_out) {

@@ -23,7 +23,8 @@
 
 namespace xf {
 
-constexpr int G = 3;  // ghost layers (6-point WENO5 stencil)
+// ghost layers: 3 for the 6-cell stencils of WENO5 and CU6, 4 for WENO7
+inline int ghosts(int weno) { return weno == 7 ? 4 : 3; }
 constexpr int MAXN = 5;
 
 struct Params {
@@ -482,11 +483,64 @@ __device__ __forceinline__ double cu6_pair(const double* wp, const double* wm, c
   return (wp[2] + wm[3]) + fma(np, dm, nm * dp) / (dp * dm);
 }
 
-// the reconstruction of Eq. 15 selected by REC (5: WENO5-JS, 6: WENO-CU6);
-// e4 = {12 eps c_0, 12 eps c_1, 12 eps c_2, 12 eps}
+// WENO7-JS (ref. 36) at i+1/2 from f0..f6 = f_{i-3..i+3}: cubic candidates on
+// {i-3+k .. i+k}, linear weights d = (1, 12, 18, 4)/35, Jiang-Shu indicators
+// of the cubics. As in WENO5, the indicators are scaled (by 240) and written
+// on first differences x_j = f_{j+1} - f_j, as the LDL^T sums of squares of
+// their quadratic forms: 240 beta_0 = Q0(x0, x1, x2), 240 beta_1 = Q1(x1, x2, x3),
+// and by mirror symmetry 240 beta_2 = Q1(x4, x3, x2), 240 beta_3 = Q0(x5, x4, x3).
+// The weights d_k/(eps + beta_k)^2 are multiplied through by prod_j s_j^2;
+// scaling s_k by c_k = (35/d_k)^(1/2) makes prod_{j!=k} s_j^2 carry d_k.
+constexpr double kW7c0 = 5.9160797830996161, kW7c1 = 1.707825127659933,
+                 kW7c2 = 1.3944333775567925, kW7c3 = 2.9580398915498081;
+__device__ __forceinline__ double w7_q0(double y0, double y1, double y2) {
+  const double A = fma(1.6946983546617915, y2, fma(-2.5484460694698354, y1, y0));
+  const double B = fma(-1.4896519285042333, y2, y1);
+  return fma(547.0 * A, A, fma(155.46617915904935 * B, B, 191.02539981185325 * y2 * y2));
+}
+__device__ __forceinline__ double w7_q1(double y0, double y1, double y2) {
+  const double A = fma(0.92509363295880154, y2, fma(-2.0749063670411987, y1, y0));
+  const double B = fma(-0.6326434619002822, y2, y1);
+  return fma(267.0 * A, A, fma(318.50187265917606 * B, B, 191.02539981185325 * y2 * y2));
+}
+
+// ec[k] = 240 eps c_k
+__device__ __forceinline__ void weno7_nd(double f0, double f1, double f2, double f3, double f4,
+                                         double f5, double f6, const double* ec, double& num,
+                                         double& den) {
+  const double x0 = f1 - f0, x1 = f2 - f1, x2 = f3 - f2, x3 = f4 - f3, x4 = f5 - f4,
+               x5 = f6 - f5;
+  const double s0 = fma(kW7c0, w7_q0(x0, x1, x2), ec[0]);
+  const double s1 = fma(kW7c1, w7_q1(x1, x2, x3), ec[1]);
+  const double s2 = fma(kW7c2, w7_q1(x4, x3, x2), ec[2]);
+  const double s3 = fma(kW7c3, w7_q0(x5, x4, x3), ec[3]);
+  const double p01 = s0 * s1, p23 = s2 * s3;
+  const double r0 = s1 * p23, r1 = s0 * p23, r2 = p01 * s3, r3 = p01 * s2;
+  const double w0 = r0 * r0, w1 = r1 * r1, w2 = r2 * r2, w3 = r3 * r3;
+  // candidates minus f3
+  const double q0 = fma(0.25, x0, fma(-5.0 / 6.0, x1, (13.0 / 12.0) * x2));
+  const double q1 = fma(-1.0 / 12.0, x1, fma(1.0 / 3.0, x2, 0.25 * x3));
+  const double q2 = fma(1.0 / 12.0, x2, fma(0.5, x3, (-1.0 / 12.0) * x4));
+  const double q3 = fma(0.75, x3, fma(-1.0 / 3.0, x4, (1.0 / 12.0) * x5));
+  num = fma(w0, q0, fma(w1, q1, fma(w2, q2, w3 * q3)));
+  den = (w0 + w1) + (w2 + w3);
+}
+
+// F^+ + F^- with WENO7: w^+ from i-3..i+3 and the mirrored w^- from i+4..i-2
+__device__ __forceinline__ double weno7_pair(const double* wp, const double* wm, const double* ec) {
+  double np, dp, nm, dm;
+  weno7_nd(wp[0], wp[1], wp[2], wp[3], wp[4], wp[5], wp[6], ec, np, dp);
+  weno7_nd(wm[7], wm[6], wm[5], wm[4], wm[3], wm[2], wm[1], ec, nm, dm);
+  return (wp[3] + wm[4]) + fma(np, dm, nm * dp) / (dp * dm);
+}
+
+// the reconstruction of Eq. 15 selected by REC (5: WENO5-JS, 6: WENO-CU6,
+// 7: WENO7-JS); e4 = {12 eps c_0, 12 eps c_1, 12 eps c_2, 12 eps} for 5 and 6,
+// {240 eps c_k} for 7
 template <int REC>
 __device__ __forceinline__ double rec_pair(const double* wp, const double* wm, const double* e4) {
-  if constexpr (REC == 6) return cu6_pair(wp, wm, e4);
+  if constexpr (REC == 7) return weno7_pair(wp, wm, e4);
+  else if constexpr (REC == 6) return cu6_pair(wp, wm, e4);
   else return weno5_pair(wp, wm, e4);
 }
 
@@ -503,6 +557,8 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
                                          uint32_t* __restrict__ flags, double dt) {
   using L = Lay<DIM, NS>;
   constexpr int NV = L::NV;
+  constexpr int SO = REC == 7 ? 3 : 2;  // stencil cells left of the left cell
+  constexpr int SW = 2 * SO + 2;        // stencil width
   constexpr int IE = DIM + 1;
   const int nf0 = p.n[0] + (D == 0), nf1 = p.n[1] + (D == 1), nf2 = p.n[2] + (D == 2);
   const long long nfaces = (long long)nf0 * nf1 * nf2;
@@ -564,7 +620,8 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
     const double hic2 = 0.5 * ic2;
     const double iGam = cvb / Rb;
     const double un = ub[D];
-    // ---- stencil m = i-2..i+3 (offsets -2..3 from the left cell). Per cell:
+    // ---- stencil m = i-SO..i+SO+1 (SW cells: i-2..i+3 for WENO5 and CU6,
+    //      i-3..i+4 for WENO7; offsets from the left cell). Per cell:
     //      rho, p, u_n/2, g.U/(2c^2) and the LLF maxima of |u-c|, |u+c|, |u|.
     //      The 1/2 of Eq. 14 and the 1/(2c^2) of the acoustic rows are folded
     //      into per-face coefficients.
@@ -575,11 +632,11 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
 #pragma unroll
     for (int s = 0; s < NS - 1; ++s) { dphi[s] = phi[s] - phiN; gs[s] = dphi[s] * hic2; }
     const double gr = phiN * hic2, gE = Gam * hic2;
-    double rho_m[6], p_m[6], hun[6], gUh[6];
+    double rho_m[SW], p_m[SW], hun[SW], gUh[SW];
     double am = 0.0, ap = 0.0, a0 = 0.0;
 #pragma unroll
-    for (int m = 0; m < 6; ++m) {
-      const int o = m - 2;
+    for (int m = 0; m < SW; ++m) {
+      const int o = m - SO;
       rho_m[m] = QF(L::U, o);
       const double unm = QF(L::UN + D, o);
       p_m[m] = QF(L::P, o);
@@ -597,21 +654,28 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
       gUh[m] = g;
     }
     const double eps12 = 12.0 * p.weno_eps;
-    const double e12c[4] = {eps12 * kWc0, eps12 * kWc1, eps12 * kWc2, eps12};
+    double e12c[4];
+    if constexpr (REC == 7) {
+      const double e240 = 240.0 * p.weno_eps;
+      e12c[0] = e240 * kW7c0; e12c[1] = e240 * kW7c1;
+      e12c[2] = e240 * kW7c2; e12c[3] = e240 * kW7c3;
+    } else {
+      e12c[0] = eps12 * kWc0; e12c[1] = eps12 * kWc1; e12c[2] = eps12 * kWc2; e12c[3] = eps12;
+    }
     const double chc = c * hic2;
     // ---- PER: one characteristic field at a time. With w = (1/2)(l.F_m +- a l.U_m)
     //      and l.F_m = u_m (l.U_m) + p_m (l[m_n] + u_m l[E]):
     //      w^+- = (u_m/2 +- a/2) l.U_m + p_m (l[m_n]/2 + (u_m/2) l[E]).
     double Fk_m, Fk_p, Fk_e;
     {
-      double wp[6], wm[6];
+      double wp[SW], wm[SW];
       // u - c: l.U = (g.U - c (m_n - u_n rho)) / (2c^2)
       {
         const double hlmn = 0.5 * (-Gam * un - c) * hic2, lE = Gam * hic2;
         const double ha = 0.5 * am;
 #pragma unroll
-        for (int m = 0; m < 6; ++m) {
-          const double nU = fma(-un, rho_m[m], QF(L::U + 1 + D, m - 2));
+        for (int m = 0; m < SW; ++m) {
+          const double nU = fma(-un, rho_m[m], QF(L::U + 1 + D, m - SO));
           const double LU = fma(-chc, nU, gUh[m]);
           const double pq = p_m[m] * fma(hun[m], lE, hlmn);
           wp[m] = fma(hun[m] + ha, LU, pq);
@@ -624,8 +688,8 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
         const double hlmn = 0.5 * (-Gam * un + c) * hic2, lE = Gam * hic2;
         const double ha = 0.5 * ap;
 #pragma unroll
-        for (int m = 0; m < 6; ++m) {
-          const double nU = fma(-un, rho_m[m], QF(L::U + 1 + D, m - 2));
+        for (int m = 0; m < SW; ++m) {
+          const double nU = fma(-un, rho_m[m], QF(L::U + 1 + D, m - SO));
           const double LU = fma(chc, nU, gUh[m]);
           const double pq = p_m[m] * fma(hun[m], lE, hlmn);
           wp[m] = fma(hun[m] + ha, LU, pq);
@@ -638,7 +702,7 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
         const double hlmn = 0.5 * Gam * un * ic2, lE = -Gam * ic2;
         const double ha = 0.5 * a0;
 #pragma unroll
-        for (int m = 0; m < 6; ++m) {
+        for (int m = 0; m < SW; ++m) {
           const double LU = fma(-2.0, gUh[m], rho_m[m]);
           const double pq = p_m[m] * fma(hun[m], lE, hlmn);
           wp[m] = fma(hun[m] + ha, LU, pq);
@@ -661,17 +725,17 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
     }
     // the remaining fields all have eigenvalue u and no pressure term
     const double ha0 = 0.5 * a0;
-    double hp0[6], hm0[6];
+    double hp0[SW], hm0[SW];
 #pragma unroll
-    for (int m = 0; m < 6; ++m) { hp0[m] = hun[m] + ha0; hm0[m] = hun[m] - ha0; }
+    for (int m = 0; m < SW; ++m) { hp0[m] = hun[m] + ha0; hm0[m] = hun[m] - ha0; }
     // tangential momenta: l = (-u_t, e_{m_t}), r = e_{m_t} + u_t e_E
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
       if (a == D) continue;
-      double wp[6], wm[6];
+      double wp[SW], wm[SW];
 #pragma unroll
-      for (int m = 0; m < 6; ++m) {
-        const double LU = fma(-ub[a], rho_m[m], QF(L::U + 1 + a, m - 2));
+      for (int m = 0; m < SW; ++m) {
+        const double LU = fma(-ub[a], rho_m[m], QF(L::U + 1 + a, m - SO));
         wp[m] = hp0[m] * LU;
         wm[m] = hm0[m] * LU;
       }
@@ -682,10 +746,10 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
     // species: l = (-Y_s, e_{rhoY_s}), r = e_{rhoY_s} - (phi_s - phi_N)/Gamma e_E
 #pragma unroll
     for (int s = 0; s < NS - 1; ++s) {
-      double wp[6], wm[6];
+      double wp[SW], wm[SW];
 #pragma unroll
-      for (int m = 0; m < 6; ++m) {
-        const double LU = fma(-Yb[s], rho_m[m], QF(L::U + IE + 1 + s, m - 2));
+      for (int m = 0; m < SW; ++m) {
+        const double LU = fma(-Yb[s], rho_m[m], QF(L::U + IE + 1 + s, m - SO));
         wp[m] = hp0[m] * LU;
         wm[m] = hm0[m] * LU;
       }

@@ -50,9 +50,10 @@ def test_argument_errors_need_no_device():
     good = xf.structs(c)
     h = C.c_void_p()
     # a bad option, a bad grid and a bad species count are all rejected up front
-    g, t, o, keep = xf.structs(c)
-    o.weno = 7
-    assert xf.lib.xf_create(C.byref(g), C.byref(t), C.byref(o), C.byref(h)) == xf.XF_ERR_ARG
+    for bad in (4, 8):
+        g, t, o, keep = xf.structs(c)
+        o.weno = bad
+        assert xf.lib.xf_create(C.byref(g), C.byref(t), C.byref(o), C.byref(h)) == xf.XF_ERR_ARG
     g, t, o, keep = xf.structs(c)
     g.n[0] = 2
     assert xf.lib.xf_create(C.byref(g), C.byref(t), C.byref(o), C.byref(h)) == xf.XF_ERR_ARG

@@ -1,7 +1,8 @@
-"""WENO-CU6 reconstruction (ref. 34, one of the REC choices of Eq. 15) on the
-GPU: parity with the oracle's CU6 on the RHS, one step and ten steps; sixth
-order on the advected density wave; and the entry points that support WENO5
-only (the adjoint and the batched form) refuse a CU6 handle.
+"""The other reconstructions REC of Eq. 15 on the GPU: WENO-CU6 (ref. 34,
+weno = 6) and WENO7-JS (ref. 36, weno = 7, 8-cell stencil and 4 ghost
+layers). Parity with the oracle's same scheme on the RHS, one step and ten
+steps; the design order on the advected density wave; and the entry points
+that support WENO5 only (the adjoint and the batched form) refuse them.
 
 Tolerances as for WENO5: 1e-11 for one RHS and one step, 1e-8 after ten steps
 (per-field max |gpu - ref| / max |ref|).
@@ -33,18 +34,22 @@ def _cases():
 CASES = _cases()
 
 
-def _oracle(case, **kw):
-    o = Oracle(case, weno=6, **kw)
+WENOS = [6, 7]
+
+
+def _oracle(case, weno, **kw):
+    o = Oracle(case, weno=weno, **kw)
     U, T = o.prim_to_cons()
     return o, U, T
 
 
+@pytest.mark.parametrize("weno", WENOS)
 @pytest.mark.parametrize("name", list(CASES))
-def test_cu6_rhs(name):
+def test_rhs(name, weno):
     case = CASES[name]
-    o, U, T = _oracle(case)
+    o, U, T = _oracle(case, weno)
     R, To, st = o.rhs(U, T.copy())
-    Rg, Tg, stg = gpu_rhs(case, U, T, weno=6)
+    Rg, Tg, stg = gpu_rhs(case, U, T, weno=weno)
     assert np.max(field_err(Rg, R, case.dim)) <= 1e-11
     assert stg == st == 0
     # and it is a different scheme from WENO5 on these states
@@ -52,59 +57,65 @@ def test_cu6_rhs(name):
     assert np.max(field_err(R5, R, case.dim)) > 1e-8
 
 
+@pytest.mark.parametrize("weno", WENOS)
 @pytest.mark.parametrize("name,steps,tol", [("tube1d_n2", 1, 1e-11), ("sbi2d_n3_visc", 1, 1e-11),
                                             ("sbi3d_n5_visc", 1, 1e-11), ("tube1d_n2", 10, 1e-8),
                                             ("sbi2d_n5_inviscid", 10, 1e-8),
                                             ("smooth2d_n3_periodic", 10, 1e-8)])
-def test_cu6_steps(name, steps, tol):
+def test_steps(name, steps, tol, weno):
     case = CASES[name]
-    o, U, T = _oracle(case)
+    o, U, T = _oracle(case, weno)
     U1, T1 = U.copy(), T.copy()
     dts = []
     for _ in range(steps):
         dt, st = o.step(U1, T1, 0.0)
         assert st == 0
         dts.append(dt)
-    Ug, Tg, stg, dtg = gpu_steps(case, U, T, steps, weno=6)
+    Ug, Tg, stg, dtg = gpu_steps(case, U, T, steps, weno=weno)
     assert stg == 0
     assert np.max(np.abs(np.array(dtg) - dts) / np.array(dts)) <= tol
     assert np.max(field_err(Ug, U1, case.dim)) <= tol
 
 
-def test_cu6_with_positivity_blend():
-    """CU6 feeding the blend of Eq. 17-20 (one step, shock-bubble state)."""
+@pytest.mark.parametrize("weno", WENOS)
+def test_with_positivity_blend(weno):
+    """The scheme feeding the blend of Eq. 17-20 (one step, shock-bubble state)."""
     case = cases.config(4, n=(48, 24))
-    o, U, T = _oracle(case, positivity=True)
+    o, U, T = _oracle(case, weno, positivity=True)
     U1, T1 = U.copy(), T.copy()
     o.step(U1, T1, 0.0)
-    Ug, _, st, _ = gpu_steps(case, U, T, 1, weno=6, positivity=True)
+    Ug, _, st, _ = gpu_steps(case, U, T, 1, weno=weno, positivity=True)
     assert st == 0
     assert np.max(field_err(Ug, U1, case.dim)) <= 1e-11
 
 
-def test_cu6_sixth_order_density_wave():
-    """rho = 1 + 0.2 sin(2 pi x) advected to t = 0.1 with dt ~ dx^2: the L1
-    error of the CUDA path falls at sixth order, as the oracle's does."""
+@pytest.mark.parametrize("weno,ns,power,order", [(6, (40, 80, 160), 2.0, 5.5),
+                                                (7, (20, 40, 80), 7.0 / 3.0, 6.0)])
+def test_design_order_density_wave(weno, ns, power, order):
+    """rho = 1 + 0.2 sin(2 pi x) advected to t = 0.1 with dt ~ dx^power (RK3
+    below the spatial error): the L1 error of the CUDA path falls at the
+    oracle's rate (CU6: 5.98, 5.98; WENO7: 6.2, 6.3)."""
     errs = []
-    for n in (40, 80, 160):
+    for n in ns:
         c = cases.density_wave(n)
         U, T = Oracle(c).prim_to_cons()
-        dt0 = 0.4 * (1.0 / n) ** 2
+        dt0 = 0.4 * (1.0 / n) ** power
         steps = int(math.ceil(0.1 / dt0))
-        Ug, _, st, _ = gpu_steps(c, U, T, steps, dt=0.1 / steps, weno=6)
+        Ug, _, st, _ = gpu_steps(c, U, T, steps, dt=0.1 / steps, weno=weno)
         assert st == 0
         x = cases._centres(n, 0.0, 1.0)
         errs.append(np.mean(np.abs(Ug[0] - (1.0 + 0.2 * np.sin(2 * np.pi * (x - 0.1))))))
     orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
-    assert min(orders) >= 5.5, (errs, orders)
+    assert min(orders) >= order, (errs, orders)
 
 
-def test_cu6_refused_where_unsupported():
+@pytest.mark.parametrize("weno", WENOS)
+def test_refused_where_unsupported(weno):
     import torch
     from paper_2403_05910_b300.xf import Batch, XFError
     case = cases.config(1, n=(24, 12))
     U, T = Oracle(case).prim_to_cons()
-    s = gpu_solver(case, weno=6)
+    s = gpu_solver(case, weno=weno)
     s.set_state(dev(U), dev(T))
     Ub = torch.zeros((case.n_v, case.cells), dtype=torch.float64, device="cuda")
     with pytest.raises(XFError):
@@ -113,4 +124,12 @@ def test_cu6_refused_where_unsupported():
         s.step_adjoint(1e-5, Ub)
     s.close()
     with pytest.raises(XFError):
-        Batch([case], weno=6)
+        Batch([case], weno=weno)
+
+
+def test_weno7_needs_four_cells_per_axis():
+    from paper_2403_05910_b300.xf import XFError
+    case = cases.shock_tube(0, n=3)
+    gpu_solver(case, weno=5).close()
+    with pytest.raises(XFError):
+        gpu_solver(case, weno=7)
