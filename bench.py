@@ -265,6 +265,52 @@ def _adjoint_vs_forward(args, dev, stream):
             "status_flags": st}
 
 
+VARIANTS = (("weno5+positivity", {"positivity": True}), ("weno_cu6", {"weno": 6}),
+            ("weno7", {"weno": 7}))
+
+
+def _variants(args, dev, stream, case):
+    """The same workload and step with the other options of the path: WENO5
+    with the positivity-preserving blend (Eq. 17-20), WENO-CU6 and WENO7.
+    Rate and the face kernels' FP64 rate from the library's own events."""
+    import torch
+    from paper_2403_05910_b300 import flops
+    from paper_2403_05910_b300.xf import Solver
+    steps = max(1, min(args.steps, 5))
+    out = {}
+    for name, kw in VARIANTS:
+        s = Solver(case, **kw)
+        P = torch.from_numpy(case.prim).to(dev)
+        s.set_primitive(P)
+        del P
+        for _ in range(args.warmup):
+            s.step(0.0)
+        s.profile(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            s.step(0.0)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        prof = s.profile_read()
+        ms = e0.elapsed_time(e1)
+        st = s.status()
+        s.close()
+        fl = flops.per_cell_stage(case, weno=kw.get("weno", 5), positivity=kw.get("positivity", False))
+        face_ms = sum(prof[k][0] for k in ("face_x", "face_y", "face_z") if k in prof)
+        face_n = sum(prof[k][1] for k in ("face_x", "face_y", "face_z") if k in prof)
+        face_tf = fl["face"] / case.dim / (face_ms / face_n * 1e-3) / 1e12
+        out[name] = {"value": case.cells * 3 * steps / (ms * 1e-3), "unit": UNIT,
+                     "ms_per_step": ms / steps, "steps": steps,
+                     "face_fp64_tflops": face_tf, "face_frac": face_tf / FP64_NOMINAL_TFLOPS,
+                     "flops_per_face": flops.face(case.dim, case.n_species, case.viscous,
+                                                  kw.get("weno", 5), kw.get("positivity", False)),
+                     "kernels_ms_per_step": {k: v[0] / steps for k, v in prof.items()},
+                     "status_flags": st}
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -352,6 +398,7 @@ def run_ours(args):
     e2e_val = whole_job_rate(case.cells * 3 * e2e_steps, e2e_s, ws)
     io_bytes = (case.n_v + 1) * case.cells * 8
     s.close()
+    variants = None if args.no_variants else _variants(args, dev, stream, case)
     batched = None if args.no_batch else _batched_vs_per_instance(args, dev, stream)
     adjoint = None if args.no_adjoint else _adjoint_vs_forward(args, dev, stream)
 
@@ -394,6 +441,8 @@ def run_ours(args):
         }
         if cpu is not None:
             line["cpu_baseline"] = cpu
+        if variants is not None:
+            line["variants"] = variants
         if batched is not None:
             line["batched"] = batched
         if adjoint is not None:
@@ -414,6 +463,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-per-instance leg")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-vs-forward leg")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the positivity / WENO-CU6 / WENO7 leg")
     ap.add_argument("--grid", default="", help="override the grid, e.g. 160,80,80 (profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)  # at least three untimed warm-up steps

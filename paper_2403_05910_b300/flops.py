@@ -9,14 +9,26 @@ pipe's occupancy. d = dimension, N = species count, n_v = d + N + 1.
 """
 
 WENO5 = 68          # one WENO5-JS reconstruction (smoothness, weights, candidates)
+# one reconstruction of each scheme in its plain form (indicators as quadratic
+# forms of the stencil values, weights, candidates, normalisation)
+RECON = {5: WENO5, 6: 156, 7: 178}
 NEWTON_ITER = 35    # one Newton temperature iteration on mixture coefficients
 NEWTON_ITERS = 3    # nominal iterations per cell with the warm start
 
 
-def face_convective(d: int, N: int) -> int:
-    """Roe state + PER projection + LLF + 2 WENO5 per field + back-projection."""
+def face_convective(d: int, N: int, weno: int = 5) -> int:
+    """Roe state + PER projection + LLF + 2 reconstructions per field +
+    back-projection. The projection is counted for the 6-cell stencil (the
+    two extra cells of WENO7 are not counted: a lower bound)."""
     nv = d + N + 1
-    return 218 + 71 * d + 103 * N + 2 * WENO5 * nv
+    return 218 + 71 * d + 103 * N + 2 * RECON[weno] * nv
+
+
+def face_positivity(d: int, N: int) -> int:
+    """Blend of Eq. 17-20: both cells' physical fluxes, the LF flux, theta
+    over the 2N one-sided partial densities (the blend itself is rare)."""
+    nv = d + N + 1
+    return 7 * nv + 8 + 16 * N
 
 
 def face_viscous(d: int, N: int) -> int:
@@ -24,8 +36,9 @@ def face_viscous(d: int, N: int) -> int:
     return 41 + 11 * d + 5 * d * d + 38 * N
 
 
-def face(d: int, N: int, viscous: bool) -> int:
-    return face_convective(d, N) + (face_viscous(d, N) if viscous else 0)
+def face(d: int, N: int, viscous: bool, weno: int = 5, positivity: bool = False) -> int:
+    return (face_convective(d, N, weno) + (face_viscous(d, N) if viscous else 0) +
+            (face_positivity(d, N) if positivity else 0))
 
 
 def prim_cell(d: int, N: int, viscous: bool) -> int:
@@ -43,19 +56,20 @@ def update_cell(d: int, N: int) -> int:
     return nv * (3 * d + 3)
 
 
-def per_cell_stage(case) -> dict:
+def per_cell_stage(case, weno: int = 5, positivity: bool = False) -> dict:
     """Flops of one stage over the whole grid, split by kernel class."""
     d, N, vis = case.dim, case.n_species, bool(case.viscous)
     n = case.n
     cells = case.cells
+    ghosts = 4 if weno == 7 else 3
     pcells = 1
     for a in range(3):
-        pcells *= (n[a] + 6) if a < d else 1
+        pcells *= (n[a] + 2 * ghosts) if a < d else 1
     nfaces = [((n[0] + (a == 0)) * (n[1] + (a == 1)) * (n[2] + (a == 2))) for a in range(d)]
     out = {
         "prim": prim_cell(d, N, vis) * pcells,
         "grad": grad_cell(d, vis) * pcells,
-        "face": face(d, N, vis) * sum(nfaces),
+        "face": face(d, N, vis, weno, positivity) * sum(nfaces),
         "update": update_cell(d, N) * cells,
     }
     out["total"] = sum(out.values())
