@@ -186,6 +186,7 @@ struct Prim {
   S rho, u[3], p, T, c2, c, H, E, cv, cp, Rm;
   S Y[XFO_MAXN];
   S mu, kap, D;
+  S Ds[XFO_MAXN];  // per-species diffusion coefficients of the selected model
   S U[XFO_MAXV];  // conserved values of this (possibly ghost) cell
 };
 
@@ -223,8 +224,13 @@ void recover(const Layout& L, const Thermo& th, const xfo_params& p, const S* Uc
 }
 
 // Mixture transport of one cell: Eq. 29 fits for mu_s and kappa_s, the Wilke
-// rule of Eq. 22 for mu and kappa, and a constant-Lewis-number diffusivity
-// D = kappa/(rho c_p Le) for every species. Returned dimensionless.
+// rule of Eq. 22 for mu and kappa, and the species diffusivities D_s: either
+// a constant-Lewis-number D = kappa/(rho c_p Le) for every species, or the
+// mixture-averaged D_sm of Eq. 26 from the binary D_st of Eq. 25 (fits of
+// ln(p D_st) in ln T, the form of Eq. 29). Reading for Eq. 26: the mole
+// fractions enter as X~_t = (max(X_t, 0) + 1e-12) normalised to sum 1, which
+// keeps D_sm finite in pure species s (where Eq. 26 is 0/0) and changes
+// nothing above round-off elsewhere. Returned dimensionless.
 template <class S>
 void transport(const Thermo& th, const xfo_params& p, Prim<S>& q) {
   int N = th.N;
@@ -256,6 +262,30 @@ void transport(const Thermo& th, const xfo_params& p, Prim<S>& q) {
   q.mu = wilke(mus) / (p.rho_ref * a_ref * p.L_ref);
   q.kap = wilke(kas) / (p.rho_ref * a_ref * p.a_ref2 * p.L_ref);
   q.D = q.kap / (q.rho * q.cp * p.lewis);
+  if (p.diffusion == 1) {
+    S Xt[XFO_MAXN], xs(0.0);
+    for (int t = 0; t < N; ++t) {
+      Xt[t] = (X[t] > 0.0 ? X[t] : S(0.0)) + 1e-12;
+      xs = xs + Xt[t];
+    }
+    S Wb(0.0);
+    for (int t = 0; t < N; ++t) { Xt[t] = Xt[t] / xs; Wb = Wb + Xt[t] * th.W[t]; }
+    S pd = q.rho * q.Rm * q.T * (p.rho_ref * p.a_ref2);  // pressure in Pa
+    for (int s = 0; s < N; ++s) {
+      S num(0.0), den(0.0);
+      for (int t = 0; t < N; ++t) {
+        if (t == s) continue;
+        S l(0.0), pw(1.0);
+        for (int j = 0; j < 4; ++j) { l = l + p.dbin[s][t][j] * pw; pw = pw * lnT; }
+        S Dst = exp(l) / pd;  // m^2/s
+        num = num + Xt[t] * th.W[t];
+        den = den + Xt[t] / Dst;
+      }
+      q.Ds[s] = num / (Wb * den) / (a_ref * p.L_ref);
+    }
+  } else {
+    for (int s = 0; s < N; ++s) q.Ds[s] = q.D;
+  }
 }
 
 // Physical flux of direction d (Eq. 2) from the cell primitives.
@@ -538,7 +568,8 @@ void viscous_face(const Layout& L, const Thermo& th, const std::vector<Prim<S>>&
   auto Dn = [&](auto get) { return (get(*c[0]) - 15.0 * get(*c[1]) + 15.0 * get(*c[2]) - get(*c[3])) / (12.0 * h); };
   S mu = I([](const Prim<S>& x) { return x.mu; });
   S kap = I([](const Prim<S>& x) { return x.kap; });
-  S Df = I([](const Prim<S>& x) { return x.D; });
+  S Dsf[XFO_MAXN];
+  for (int s = 0; s < N; ++s) Dsf[s] = I([s](const Prim<S>& x) { return x.Ds[s]; });
   S rho = I([](const Prim<S>& x) { return x.rho; });
   S T = I([](const Prim<S>& x) { return x.T; });
   S u[3], Yf[XFO_MAXN], dY[XFO_MAXN];
@@ -573,11 +604,11 @@ void viscous_face(const Layout& L, const Thermo& th, const std::vector<Prim<S>>&
     tau[a] = mu * (grad[d][a] + grad[a][d]);
     if (a == d) tau[a] = tau[a] - (2.0 / 3.0) * mu * div;
   }
-  // species diffusion with the mixture correction (Eq. 6), D_s = D for all s
+  // species diffusion with the mixture correction (Eq. 6)
   S corr(0.0);
-  for (int s = 0; s < N; ++s) corr = corr + Df * dY[s];
+  for (int s = 0; s < N; ++s) corr = corr + Dsf[s] * dY[s];
   S J[XFO_MAXN];
-  for (int s = 0; s < N; ++s) J[s] = -rho * (Df * dY[s] - Yf[s] * corr);
+  for (int s = 0; s < N; ++s) J[s] = -rho * (Dsf[s] * dY[s] - Yf[s] * corr);
   Fv[0] = S(0.0);
   S work(0.0);
   for (int a = 0; a < dim; ++a) { Fv[1 + a] = tau[a]; work = work + tau[a] * u[a]; }
@@ -746,6 +777,7 @@ void rk3_impl(const xfo_params& p, S* U, double* T, double dt, uint32_t* st) {
 int check(const xfo_params* p) {
   if (!p || p->dim < 1 || p->dim > 3 || p->N < 2 || p->N > XFO_MAXN) return -1;
   if (p->weno != 5 && p->weno != 6 && p->weno != 7) return -1;
+  if (p->diffusion != 0 && p->diffusion != 1) return -1;
   for (int a = 0; a < p->dim; ++a) if (p->n[a] < 1) return -1;
   for (int a = 0; a < p->dim; ++a)
     for (int s = 0; s < 2; ++s)
@@ -834,7 +866,8 @@ double xfo_dt(const xfo_params* p, const double* U, double* T, uint32_t* status)
     smax = std::max(smax, s);
     if (p->viscous) {
       transport(th, *p, q);
-      double nu = std::max(std::max(4.0 * q.mu / (3.0 * q.rho), q.kap / (q.rho * q.cv)), q.D);
+      double nu = std::max(4.0 * q.mu / (3.0 * q.rho), q.kap / (q.rho * q.cv));
+      for (int k = 0; k < p->N; ++k) nu = std::max(nu, q.Ds[k]);
       numax = std::max(numax, nu);
     }
   }
@@ -934,15 +967,29 @@ double xfo_weno_cu6(const double* f, double eps) { return weno_cu6(f, eps); }
 double xfo_weno7(const double* f, double eps) { return weno7(f, eps); }
 double xfo_cu6_beta6(const double* f) { return cu6_beta6(f); }
 
+int xfo_species_diffusion(const xfo_params* p, double T, double rho, const double* Y,
+                          double* Ds) {
+  if (check(p)) return -1;
+  Thermo th(*p);
+  Prim<double> q;
+  q.T = T; q.rho = rho;
+  double cp = 0.0, Rm = 0.0;
+  for (int s = 0; s < p->N; ++s) { q.Y[s] = Y[s]; cp += Y[s] * th.cp_s(s, T); Rm += Y[s] * th.Rs[s]; }
+  q.cp = cp; q.Rm = Rm;
+  transport(th, *p, q);
+  for (int s = 0; s < p->N; ++s) Ds[s] = q.Ds[s];
+  return 0;
+}
+
 int xfo_transport(const xfo_params* p, double T, double rho, const double* Y, double* mu,
                   double* kappa, double* D) {
   if (check(p)) return -1;
   Thermo th(*p);
   Prim<double> q;
   q.T = T; q.rho = rho;
-  double cp = 0.0;
-  for (int s = 0; s < p->N; ++s) { q.Y[s] = Y[s]; cp += Y[s] * th.cp_s(s, T); }
-  q.cp = cp;
+  double cp = 0.0, Rm = 0.0;
+  for (int s = 0; s < p->N; ++s) { q.Y[s] = Y[s]; cp += Y[s] * th.cp_s(s, T); Rm += Y[s] * th.Rs[s]; }
+  q.cp = cp; q.Rm = Rm;
   transport(th, *p, q);
   *mu = q.mu; *kappa = q.kap; *D = q.D;
   return 0;

@@ -62,6 +62,9 @@ typedef struct {
   int positivity;                 /* positivity-preserving flux blend (Eq. 17-20) */
   int weno;                       /* 5: WENO5-JS, 6: WENO-CU6, 7: WENO7-JS */
   double pos_eps;                 /* target floor of the partial densities */
+  int diffusion;                  /* 0: D = kappa/(rho c_p Le) for every species;
+                                     1: mixture-averaged D_sm (Eq. 25-26) */
+  double dbin[XFO_MAXN][XFO_MAXN][4]; /* ln(p D_st [Pa m^2/s]) cubic in ln T */
 } xfo_params;
 
 int xfo_nv(const xfo_params *p);
@@ -102,6 +105,10 @@ double xfo_weno_cu6(const double *f, double eps);
 double xfo_cu6_beta6(const double *f);
 /* WENO7-JS at i+1/2 from f[0..6] = f_{i-3..i+3} */
 double xfo_weno7(const double *f, double eps);
+/* per-species diffusion coefficients D_s (dimensionless) of the selected
+ * model at (T, rho, Y): the mixture-averaged D_sm of Eq. 26 or the common D */
+int xfo_species_diffusion(const xfo_params *p, double T, double rho, const double *Y,
+                          double *Ds);
 /* per-cell mixture transport (dimensionless mu, kappa, D) */
 int xfo_transport(const xfo_params *p, double T, double rho, const double *Y,
                   double *mu, double *kappa, double *D);

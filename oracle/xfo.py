@@ -27,6 +27,7 @@ class Params(C.Structure):
         ("viscous", C.c_int), ("convective", C.c_int), ("newton_max", C.c_int),
         ("newton_rtol", C.c_double), ("weno_eps", C.c_double), ("threads", C.c_int),
         ("positivity", C.c_int), ("weno", C.c_int), ("pos_eps", C.c_double),
+        ("diffusion", C.c_int), ("dbin", ((C.c_double * 4) * MAXN) * MAXN),
     ]
 
 
@@ -58,6 +59,7 @@ def lib():
         L.xfo_weno5.restype = C.c_double
         L.xfo_weno_cu6.argtypes = [dp, C.c_double]
         L.xfo_weno_cu6.restype = C.c_double
+        L.xfo_species_diffusion.argtypes = [P, C.c_double, C.c_double, dp, dp]
         L.xfo_weno7.argtypes = [dp, C.c_double]
         L.xfo_weno7.restype = C.c_double
         L.xfo_cu6_beta6.argtypes = [dp]
@@ -76,8 +78,10 @@ def _p(a: np.ndarray):
 
 def params(case, viscous=None, convective=True, threads=0, newton_max=50,
            newton_rtol=1e-13, weno_eps=1e-6, positivity=False, pos_eps=1e-13,
-           weno=5) -> Params:
-    """Build the oracle parameter block from a generator ``Case``."""
+           weno=5, diffusion=0) -> Params:
+    """Build the oracle parameter block from a generator ``Case``.
+    ``diffusion``: 0 for D = kappa/(rho c_p Le) for every species, 1 for the
+    mixture-averaged D_sm of Eq. 26 (needs ``species.dbin_coef``)."""
     sp = case.species
     p = Params()
     p.dim = case.dim
@@ -108,6 +112,14 @@ def params(case, viscous=None, convective=True, threads=0, newton_max=50,
     p.positivity = int(positivity)
     p.pos_eps = pos_eps
     p.weno = int(weno)
+    p.diffusion = int(diffusion)
+    if diffusion:
+        if sp.dbin_coef is None:
+            raise ValueError("the mixture-averaged model needs binary diffusion fits")
+        for s in range(sp.n):
+            for t in range(sp.n):
+                for j in range(4):
+                    p.dbin[s][t][j] = sp.dbin_coef[s, t, j]
     return p
 
 
@@ -199,6 +211,14 @@ class Oracle:
         self.L.xfo_transport(C.byref(self.p), float(T), float(rho),
                              _p(np.ascontiguousarray(Y, dtype=np.float64)), _p(mu), _p(ka), _p(D))
         return mu[0], ka[0], D[0]
+
+    def species_diffusion(self, T, rho, Y):
+        """Per-species D_s (dimensionless) of the selected diffusion model."""
+        Ds = np.zeros(self.case.n_species)
+        rc = self.L.xfo_species_diffusion(C.byref(self.p), float(T), float(rho),
+                                          _p(np.ascontiguousarray(Y, dtype=np.float64)), _p(Ds))
+        assert rc == 0
+        return Ds
 
     def rhs_jvp(self, U, V, T):
         """V: [k <= KDIR, n_v*cells] tangents; returns (dU/dt, J V[k], T, status)."""

@@ -14,6 +14,8 @@ What it generates (the workloads of the XFluids paper, arXiv 2403.05910):
   the frozen-gamma Rankine-Hugoniot post-shock state of Eq. 33 and a bubble
   whose interface follows the tanh profile of Eq. 32 in molar fraction;
 * a batched ensemble of uneven 2D shock-bubble instances;
+* the 1D multicomponent diffusion case (Sec. VI.B, Table IV) with seeded
+  binary diffusion fits for the mixture-averaged model of Eq. 25-26;
 * small smooth periodic fields used by the tests.
 
 Species data is synthetic (no thermochemistry tables exist offline):
@@ -50,6 +52,9 @@ class Species:
     h_off[s]: h_s/R_s at T_lo (K).
     mu_coef[s, n], kappa_coef[s, n]: ln(mu [Pa s]) and ln(kappa [W/(m K)])
     as cubic polynomials in ln(T) (Eq. 29 with four terms).
+    dbin_coef[s, t, n] (optional, symmetric in s, t): ln(p D_st [Pa m^2/s]) as
+    a cubic polynomial in ln(T), the binary diffusion coefficients of Eq. 25
+    in the fit form of Eq. 29 (p D_st depends on T only).
     """
     W: np.ndarray
     cp_coef: np.ndarray
@@ -59,6 +64,7 @@ class Species:
     T_lo: float = T_LO
     T_hi: float = T_HI
     lewis: float = 1.0
+    dbin_coef: np.ndarray = None
 
     @property
     def n(self) -> int:
@@ -148,6 +154,36 @@ def _draw_species(rng: np.random.Generator, W: np.ndarray, calorically_perfect=F
         mu[s] = [math.log(mu300) - (m2 * L + m3 * L * L + m4 * L ** 3), m2, m3, m4]
         ka[s] = [math.log(k300) - (k2 * L + k3 * L * L + k4 * L ** 3), k2, k3, k4]
     return Species(W=W.astype(np.float64), cp_coef=cp, h_off=np.zeros(N), mu_coef=mu, kappa_coef=ka)
+
+
+def draw_binary_diffusion(rng: np.random.Generator, W: np.ndarray) -> np.ndarray:
+    """ln(p D_st) fits (Eq. 25 in the form of Eq. 29) for every pair s < t, in
+    that order: D_st(300 K, 1 atm) = 2e-5 m^2/s * (0.0145 kg/mol / W_st)^(1/2)
+    * U[0.8, 1.25] (the Chapman-Enskog scaling with the reduced mass
+    W_st = W_s W_t/(W_s + W_t)), a temperature exponent U[1.6, 1.8] and small
+    curvature terms. The diagonal holds the self-diffusion fit of the same
+    form (unused by the mixture rule of Eq. 26)."""
+    N = W.shape[0]
+    c = np.zeros((N, N, 4))
+    L = math.log(300.0)
+    for s in range(N):
+        for t in range(s, N):
+            Wst = W[s] * W[t] / (W[s] + W[t])
+            D300 = 2.0e-5 * math.sqrt(0.0145 / Wst) * rng.uniform(0.8, 1.25)
+            e1, e2, e3 = rng.uniform(1.6, 1.8), rng.uniform(-5e-3, 5e-3), rng.uniform(-5e-4, 5e-4)
+            row = [math.log(P0_SBI * D300) - (e1 * L + e2 * L * L + e3 * L ** 3), e1, e2, e3]
+            c[s, t] = row
+            c[t, s] = row
+    return c
+
+
+def with_binary_diffusion(case: "Case", seed: int = 0) -> "Case":
+    """Copy of ``case`` whose species carry seeded binary diffusion fits (an
+    RNG of their own, so every other input stays as drawn)."""
+    import dataclasses
+    rng = np.random.default_rng([seed, 25])
+    sp = dataclasses.replace(case.species, dbin_coef=draw_binary_diffusion(rng, case.species.W))
+    return dataclasses.replace(case, species=sp, name=case.name + "_dsm")
 
 
 def constant_transport(sp: Species, mu: float, kappa: float) -> Species:
@@ -355,6 +391,42 @@ def batch(seed: int = 0, count: int = 64, scale: int = 1) -> list:
 
 
 # ------------------------------------------------------------ test inputs ---
+
+# species of the multicomponent diffusion case (Table IV order); the molar
+# masses of O2, N2, H2O and CH4 (kg/mol), the thermo and transport synthetic
+DIFF_W = (0.032, 0.028, 0.018, 0.016)
+DIFF_T = (320.0, 1350.0)                        # K, fuel / oxidizer side (Table IV)
+DIFF_Y = ((0.195, 0.591, 0.0, 0.214),           # fuel side
+          (0.142, 0.758, 0.1, 0.0))             # oxidizer side
+
+
+def multicomponent_diffusion(n: int = 200, seed: int = 0, length: float = 0.05,
+                             d: float = 0.0025, x0: float = 0.025) -> Case:
+    """1D multicomponent diffusion (Sec. VI.B, Eq. 30, Table IV) with synthetic
+    species data: a periodic domain of ``length`` metres on ``n`` cells,
+    p = 1 atm, u = 0, and T, Y_k = oxidizer value + (fuel - oxidizer) f(x) with
+    f(x) = 1 - 0.5 exp(-(x - x0)^2/d^2) (reading: the printed exponent lost its
+    square). Binary diffusion fits are drawn (``draw_binary_diffusion``): the
+    case is meant for the mixture-averaged diffusion model of Eq. 26.
+    Scales: L_ref = length, rho_ref = the fuel-side density, a_ref^2 = p/rho_ref."""
+    rng = np.random.default_rng(seed)
+    W = np.array(DIFF_W)
+    sp = _draw_species(rng, W)
+    sp.dbin_coef = draw_binary_diffusion(np.random.default_rng([seed, 25]), W)
+    x = _centres(n, 0.0, length)
+    f = 1.0 - 0.5 * np.exp(-((x - x0) / d) ** 2)
+    Tf, To = DIFF_T
+    Yf, Yo = np.array(DIFF_Y[0]), np.array(DIFF_Y[1])
+    T = To + (Tf - To) * f
+    Y = Yo[:, None] + (Yf - Yo)[:, None] * f[None, :]
+    rho = P0_SBI / (R_U * np.sum(Y / W[:, None], axis=0) * T)
+    rho_ref = P0_SBI / (R_U * np.sum(Yf / W) * Tf)
+    a_ref2 = P0_SBI / rho_ref
+    prim = _pack(1, rho / rho_ref, [np.zeros(n)], np.ones(n), Y)
+    return Case("diffusion1d_n4", 1, (n, 1, 1), (0.0,) * 3, (1.0,) * 3,
+                ((BC_PERIODIC, BC_PERIODIC), (0, 0), (0, 0)), sp, a_ref2, rho_ref, length,
+                True, 0.5, prim, {"T": T, "f": f})
+
 
 def uniform_state(dim: int, n: tuple, N: int, seed: int = 0, bc=BC_PERIODIC,
                   viscous: bool = True) -> Case:
