@@ -86,7 +86,13 @@ typedef struct xf_grid {
  *  mu_coef[N][4]    ln mu_s [Pa s]   = sum_n mu_coef[s][n] (ln T)^n   (Eq. 29)
  *  kappa_coef[N][4] ln kappa_s [W/(m K)] likewise
  *  lewis            constant Lewis number: D_s = kappa/(rho c_p Le) for all s
- *  a_ref2, rho_ref, L_ref  reference scales (m^2/s^2, kg/m^3, m) */
+ *                   (xf_opts.diffusion = 0)
+ *  a_ref2, rho_ref, L_ref  reference scales (m^2/s^2, kg/m^3, m)
+ *  dbin_coef[N][N][4]  ln(p D_st [Pa m^2/s]) = sum_n dbin_coef[s][t][n] (ln T)^n,
+ *                   the binary diffusion coefficients of Eq. 25 in the fit form
+ *                   of Eq. 29 (entries s != t are used; the caller keeps them
+ *                   symmetric); required with xf_opts.diffusion = 1, else may
+ *                   be NULL */
 typedef struct xf_thermo {
   int n_species;
   const double *W;
@@ -97,6 +103,7 @@ typedef struct xf_thermo {
   const double *kappa_coef;
   double lewis;
   double a_ref2, rho_ref, L_ref;
+  const double *dbin_coef;
 } xf_thermo;
 
 /* Numerical options. weno selects the reconstruction REC of Eq. 15: 5 for
@@ -107,8 +114,13 @@ typedef struct xf_thermo {
  * 0 (LLF); viscous switches the viscous + diffusion fluxes; convective switches
  * the inviscid fluxes (off only for testing the viscous operator);
  * newton_max/newton_rtol bound the Newton solve (stop when |dT| <= rtol T);
- * weno_eps is the absolute epsilon of both reconstructions. The batched form
- * and the adjoint entry points support weno = 5 only (XF_ERR_ARG otherwise).
+ * weno_eps is the absolute epsilon of the reconstructions. diffusion selects
+ * the species diffusivities of Eq. 6: 0 for D_s = kappa/(rho c_p Le) for every
+ * species, 1 for the mixture-averaged D_sm of Eq. 26 from the binary D_st of
+ * Eq. 25 (xf_thermo.dbin_coef), with the mole fractions regularised as
+ * X~_t = (max(X_t, 0) + 1e-12) / sum so that a pure species keeps a finite
+ * D_sm. The batched form and the adjoint entry points support weno = 5 and
+ * diffusion = 0 only (XF_ERR_ARG otherwise).
  * positivity switches the positivity-preserving flux blend of Eq. 17-20 inside
  * RK stages: F* = (1 - theta) F_LF + theta F_hat per face, with the local LF
  * flux of Eq. 19 (alpha = max(|u_d| + c) of the two cells) and the smallest
@@ -127,6 +139,7 @@ typedef struct xf_opts {
   double weno_eps;
   int positivity;
   double pos_eps;
+  int diffusion;
 } xf_opts;
 
 typedef struct xf_handle xf_handle;

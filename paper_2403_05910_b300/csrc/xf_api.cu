@@ -296,7 +296,22 @@ xf_status fill_params(const xf_grid* g, const xf_thermo* th, const xf_opts* o, x
   p->positivity = o->positivity ? 1 : 0;
   if (o->positivity && !(o->pos_eps >= 0.0)) return XF_ERR_ARG;
   p->pos_eps = o->pos_eps;
+  if (o->diffusion != 0 && o->diffusion != 1) return XF_ERR_ARG;
+  p->diffusion = (o->viscous && o->diffusion == 1) ? 1 : 0;
+  if (p->diffusion) {
+    if (!th->dbin_coef) return XF_ERR_ARG;
+    for (int s = 0; s < N; ++s)
+      for (int t = 0; t < N; ++t)
+        for (int j = 0; j < 4; ++j) p->dbin[s][t][j] = th->dbin_coef[(s * N + t) * 4 + j];
+  }
+  p->fdsm = th->rho_ref * th->a_ref2 * a_ref * th->L_ref;
   return XF_OK;
+}
+
+// per-cell fields of a handle's padded block (the D_sm fields ride along
+// only with the mixture-averaged model)
+inline size_t nq_of(const Table& t, const xf::Params& p) {
+  return (size_t)t.nq + (p.diffusion ? (size_t)p.N : 0);
 }
 
 cudaEvent_t pool_event(xf_handle* h) {
@@ -468,7 +483,7 @@ xf_status xf_create(const xf_grid* grid, const xf_thermo* thermo, const xf_opts*
   bool ok = alloc((void**)&h->U, st_bytes) && alloc((void**)&h->Us, st_bytes) &&
             alloc((void**)&h->T[0], sizeof(double) * p.cells) &&
             alloc((void**)&h->T[1], sizeof(double) * p.cells) &&
-            alloc((void**)&h->Q, sizeof(double) * (size_t)tab.nq * p.pcells) &&
+            alloc((void**)&h->Q, sizeof(double) * nq_of(tab, p) * p.pcells) &&
             alloc((void**)&h->dt, sizeof(double)) &&
             alloc((void**)&h->red, 2 * sizeof(unsigned long long)) &&
             alloc((void**)&h->flags, sizeof(uint32_t));
@@ -484,7 +499,7 @@ xf_status xf_create(const xf_grid* grid, const xf_thermo* thermo, const xf_opts*
   if (cudaMemset(h->red, 0, 2 * sizeof(unsigned long long)) != cudaSuccess ||
       cudaMemset(h->flags, 0, sizeof(uint32_t)) != cudaSuccess ||
       cudaMemset(h->dt, 0, sizeof(double)) != cudaSuccess ||
-      cudaMemset(h->Q, 0, sizeof(double) * (size_t)tab.nq * p.pcells) != cudaSuccess) {
+      cudaMemset(h->Q, 0, sizeof(double) * nq_of(tab, p) * p.pcells) != cudaSuccess) {
     xf_destroy(h);
     g_err = "cudaMemset failed";
     return XF_ERR_CUDA;
@@ -635,13 +650,15 @@ xf_status xf_clear_status(xf_handle* h, void* stream) {
 
 xf_status xf_rhs_adjoint(xf_handle* h, const double* U, const double* dUdt_bar, double* U_bar,
                          void* stream) {
-  if (!h || !U || !dUdt_bar || !U_bar || h->p.positivity || h->p.weno != 5) return XF_ERR_ARG;
+  if (!h || !U || !dUdt_bar || !U_bar || h->p.positivity || h->p.weno != 5 || h->p.diffusion)
+    return XF_ERR_ARG;
   if (!is_device_ptr(U) || !is_device_ptr(dUdt_bar) || !is_device_ptr(U_bar)) return XF_ERR_ARG;
   return rhs_adjoint_impl(h, U, dUdt_bar, 1.0, U_bar, (cudaStream_t)stream);
 }
 
 xf_status xf_step_rk3_adjoint(xf_handle* h, double dt, double* U_bar, void* stream) {
-  if (!h || !U_bar || !(dt > 0.0) || h->p.positivity || h->p.weno != 5) return XF_ERR_ARG;
+  if (!h || !U_bar || !(dt > 0.0) || h->p.positivity || h->p.weno != 5 || h->p.diffusion)
+    return XF_ERR_ARG;
   if (!is_device_ptr(U_bar)) return XF_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   xf_status st = ensure_adjoint_buffers(h);
@@ -811,7 +828,7 @@ xf_status xf_rhs_static(const xf_grid* grid, const xf_thermo* thermo, const xf_o
     return XF_ERR_ARG;
   // scratch plan (in doubles): Q | G_x | G_y | G_z | T_in | T_out | dt | red[2] | flags
   long long nf[3] = {0, 0, 0};
-  size_t need = (size_t)tab.nq * p.pcells;
+  size_t need = nq_of(tab, p) * p.pcells;
   for (int d = 0; d < p.dim; ++d) {
     nf[d] = (long long)(p.n[0] + (d == 0)) * (p.n[1] + (d == 1)) * (p.n[2] + (d == 2));
     need += (size_t)p.nv * nf[d];
@@ -831,7 +848,7 @@ xf_status xf_rhs_static(const xf_grid* grid, const xf_thermo* thermo, const xf_o
   if (st != XF_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   double* Q = base;
-  double* cur = Q + (size_t)tab.nq * p.pcells;
+  double* cur = Q + nq_of(tab, p) * p.pcells;
   double* G[3] = {nullptr, nullptr, nullptr};
   for (int d = 0; d < p.dim; ++d) {
     G[d] = cur;

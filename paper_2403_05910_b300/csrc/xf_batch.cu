@@ -399,7 +399,7 @@ xf_status xf_batch_create(int n, const xf_grid* grids, const xf_thermo* thermos,
     BInst& I = b->hinst[i];
     std::memset(&I, 0, sizeof I);
     xf_status st = xf_internal_fill_params(&grids[i], &thermos[i], &opts[i], &I.p);
-    if (st != XF_OK || grids[i].dim != BDIM || opts[i].weno != 5) {
+    if (st != XF_OK || grids[i].dim != BDIM || opts[i].weno != 5 || I.p.diffusion) {
       delete b;
       return XF_ERR_ARG;
     }

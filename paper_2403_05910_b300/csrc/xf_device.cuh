@@ -47,6 +47,9 @@ struct Params {
   double wAB[MAXN][MAXN], wABB[MAXN][MAXN];  // A B and A B^2
   double invW[MAXN];
   double fmu, fka, inv_lewis;
+  int diffusion;                 // 0: D = kappa/(rho c_p Le); 1: mixture-averaged D_sm (Eq. 26)
+  double dbin[MAXN][MAXN][4];    // ln(p D_st [Pa m^2/s]) cubic in ln T (Eq. 25, form of Eq. 29)
+  double fdsm;                   // rho_ref a_ref^3 L_ref: 1/D*_st = p* fdsm exp(-ln(p D_st))
   // numerics
   double cfl, weno_eps, newton_rtol;
   int viscous, convective, newton_max;
@@ -73,6 +76,8 @@ struct Lay {
   static constexpr int DF = KA + 1;     // diffusivity
   static constexpr int GU = DF + 1;     // nodal d u_a / d x_b at GU + a*DIM + b
   static constexpr int NQ = GU + DIM * DIM;
+  static constexpr int DS = NQ;         // D_sm of species 1..N, present (and
+                                        // allocated) only with diffusion = 1
 };
 
 __device__ __forceinline__ double ld(const double* p) { return __ldg(p); }
@@ -279,6 +284,49 @@ __device__ __forceinline__ void prim_cell(const Params& p, long long t, const do
       q[L::MU * PC] = mu;
       q[L::KA * PC] = ka;
       q[L::DF * PC] = Dd;
+      if (p.diffusion == 1) {
+        // Eq. 25-26: D_sm = sum_{t!=s} X~_t W_t / (W~ sum_{t!=s} X~_t / D_st) with
+        // X~ = (max(X, 0) + 1e-12) normalised and W~ = sum_t X~_t W_t; the fits
+        // give 1/D*_st = p* fdsm exp(-l_st(ln T)), one exp per pair.
+        double Xt[NS], xts = 0.0;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) { Xt[s] = fmax(X[s], 0.0) + 1e-12; xts += Xt[s]; }
+        const double ixts = 1.0 / xts;
+        double Wt = 0.0, XW[NS];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+          Xt[s] *= ixts;
+          XW[s] = Xt[s] / p.invW[s];
+          Wt += XW[s];
+        }
+        double den[NS];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) den[s] = 0.0;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+#pragma unroll
+          for (int tt = s + 1; tt < NS; ++tt) {
+            const double* b = p.dbin[s][tt];
+            const double l = fma(fma(fma(b[3], lnT, b[2]), lnT, b[1]), lnT, b[0]);
+            const double iD = exp(-l);
+            den[s] = fma(Xt[tt], iD, den[s]);
+            den[tt] = fma(Xt[s], iD, den[tt]);
+          }
+        }
+        const double sc = 1.0 / (Wt * pr * p.fdsm);
+        double Dmax = 0.0;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+          double num = 0.0;
+#pragma unroll
+          for (int tt = 0; tt < NS; ++tt)
+            if (tt != s) num += XW[tt];
+          const double Ds = num * sc / den[s];
+          q[(L::DS + s) * PC] = Ds;
+          Dmax = fmax(Dmax, Ds);
+        }
+        Dd = Dmax;  // the CFL limit takes the largest species diffusivity
+      }
     }
     if (interior) {
       Tout[src] = T;
@@ -812,7 +860,7 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
     const double wd = p.inv_dx[D] * (1.0 / 12.0);
 #define FI(field) ((9.0 * (QF(field, 0) + QF(field, 1)) - (QF(field, -1) + QF(field, 2))) * wi)
 #define FD(field) ((15.0 * (QF(field, 1) - QF(field, 0)) - (QF(field, 2) - QF(field, -1))) * wd)
-    const double mu = FI(L::MU), ka = FI(L::KA), Df = FI(L::DF), rf = FI(L::U), Tf = FI(L::T);
+    const double mu = FI(L::MU), ka = FI(L::KA), rf = FI(L::U), Tf = FI(L::T);
     double uf[DIM], gr[DIM][DIM];
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
@@ -831,16 +879,28 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
       Gout[1 + a] -= tau;
       work = fma(tau, uf[a], work);
     }
-    double dY[NS], Yf[NS], sdY = 0.0;
+    // species fluxes of Eq. 6 with the mixture correction: D_s = D for every
+    // species (diffusion = 0) or the face values of the cells' D_sm
+    double dY[NS], Yf[NS], Dsf[NS], corr = 0.0;
+    if (p.diffusion == 1) {
 #pragma unroll
-    for (int s = 0; s < NS; ++s) { dY[s] = FD(L::Y + s); Yf[s] = FI(L::Y + s); sdY += dY[s]; }
-    const double corr = Df * sdY;
+      for (int s = 0; s < NS; ++s) {
+        dY[s] = FD(L::Y + s); Yf[s] = FI(L::Y + s); Dsf[s] = FI(L::DS + s);
+        corr = fma(Dsf[s], dY[s], corr);
+      }
+    } else {
+      const double Df = FI(L::DF);
+      double sdY = 0.0;
+#pragma unroll
+      for (int s = 0; s < NS; ++s) { dY[s] = FD(L::Y + s); Yf[s] = FI(L::Y + s); sdY += dY[s]; Dsf[s] = Df; }
+      corr = Df * sdY;
+    }
     const TauPt tp = tau_of(p, Tf);
     double qd = 0.0;
     double J[NS];
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-      J[s] = -rf * fma(Df, dY[s], -Yf[s] * corr);
+      J[s] = -rf * fma(Dsf[s], dY[s], -Yf[s] * corr);
       const double hs = h_s(p, s, tp, cp_s(p, s, tp.tc));
       qd = fma(hs, J[s], qd);
     }

@@ -31,13 +31,15 @@ class Thermo(C.Structure):
                 ("T_hi", C.c_double), ("cp_coef", C.POINTER(C.c_double)),
                 ("h_off", C.POINTER(C.c_double)), ("mu_coef", C.POINTER(C.c_double)),
                 ("kappa_coef", C.POINTER(C.c_double)), ("lewis", C.c_double),
-                ("a_ref2", C.c_double), ("rho_ref", C.c_double), ("L_ref", C.c_double)]
+                ("a_ref2", C.c_double), ("rho_ref", C.c_double), ("L_ref", C.c_double),
+                ("dbin_coef", C.POINTER(C.c_double))]
 
 
 class Opts(C.Structure):
     _fields_ = [("cfl", C.c_double), ("weno", C.c_int), ("split", C.c_int), ("viscous", C.c_int),
                 ("convective", C.c_int), ("newton_max", C.c_int), ("newton_rtol", C.c_double),
-                ("weno_eps", C.c_double), ("positivity", C.c_int), ("pos_eps", C.c_double)]
+                ("weno_eps", C.c_double), ("positivity", C.c_int), ("pos_eps", C.c_double),
+                ("diffusion", C.c_int)]
 
 
 # every symbol declared in include/xf.h
@@ -128,9 +130,11 @@ def _dptr(a: np.ndarray):
 
 
 def structs(case, viscous=None, convective=True, cfl=None, newton_max=50, newton_rtol=1e-13,
-            weno_eps=1e-6, positivity=False, pos_eps=1e-13, weno=5):
+            weno_eps=1e-6, positivity=False, pos_eps=1e-13, weno=5, diffusion=0):
     """(Grid, Thermo, Opts, keepalive) from a generator ``Case``. ``weno``: 5
-    for WENO5-JS, 6 for WENO-CU6."""
+    for WENO5-JS, 6 for WENO-CU6, 7 for WENO7-JS. ``diffusion``: 0 for a
+    common D = kappa/(rho c_p Le), 1 for the mixture-averaged D_sm of Eq. 26
+    (the species need binary diffusion fits)."""
     g = Grid()
     g.dim = case.dim
     for a in range(3):
@@ -150,6 +154,11 @@ def structs(case, viscous=None, convective=True, cfl=None, newton_max=50, newton
     t.T_lo, t.T_hi = sp.T_lo, sp.T_hi
     t.lewis = sp.lewis
     t.a_ref2, t.rho_ref, t.L_ref = case.a_ref2, case.rho_ref, case.L_ref
+    if sp.dbin_coef is not None:
+        keep.append(np.ascontiguousarray(sp.dbin_coef, dtype=np.float64))
+        t.dbin_coef = _dptr(keep[-1])
+    elif diffusion:
+        raise ValueError("the mixture-averaged model needs binary diffusion fits")
     o = Opts()
     o.cfl = case.cfl if cfl is None else cfl
     o.weno = int(weno)
@@ -161,6 +170,7 @@ def structs(case, viscous=None, convective=True, cfl=None, newton_max=50, newton
     o.weno_eps = weno_eps
     o.positivity = int(positivity)
     o.pos_eps = pos_eps
+    o.diffusion = int(diffusion)
     return g, t, o, keep
 
 

@@ -3,19 +3,20 @@ compare with the oracle field by field."""
 import numpy as np
 
 
-def field_err(gpu, ref, dim=None):
+def field_err(gpu, ref, dim=None, mom_floor=0.0):
     """Per-field max |gpu - ref| / max |ref| (the parity metric).
 
     With ``dim`` given, the momentum rows 1..dim share one scale, the largest
     momentum magnitude: a component that vanishes in exact arithmetic (v in a
     y-uniform planar shock) carries only round-off of the momentum flux and
-    has no scale of its own."""
+    has no scale of its own. ``mom_floor`` bounds that scale from below, for
+    states at rest whose momentum is round-off altogether."""
     ref = np.asarray(ref)
     gpu = np.asarray(gpu).reshape(ref.shape[0], -1)
     ref = ref.reshape(ref.shape[0], -1)
     scale = np.max(np.abs(ref), axis=1)
     if dim:
-        scale[1:1 + dim] = np.max(scale[1:1 + dim])
+        scale[1:1 + dim] = max(np.max(scale[1:1 + dim]), mom_floor)
     scale = np.maximum(scale, 1e-300)
     return np.max(np.abs(gpu - ref), axis=1) / scale
 
