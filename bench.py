@@ -33,7 +33,8 @@ FP64_NOMINAL_TFLOPS = 1.25   # B300 dense FP64 (nominal)
 # DRAM bytes per face of k_face from an ncu capture, keyed by the first 16 hex
 # digits of the sha256 of the kernel source it was taken on; any other source
 # reports traffic null (the counters no longer describe the kernel).
-FACE_TRAFFIC_B_PER_FACE = {"aab342d14388773d": 294.0, "7aa2c6f72cd106cc": 294.2}
+FACE_TRAFFIC_B_PER_FACE = {"aab342d14388773d": 294.0, "7aa2c6f72cd106cc": 294.2,
+                           "69f88d1a3ee86fc1": 293.6}
 CPU_SAMPLE_GRID = (96, 48, 48)
 
 
@@ -142,6 +143,29 @@ def _cpu_baseline(steps=None, warmup=0, budget_s=15.0):
     return {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{n} RK3 step(s) of the same 3D 5-species shock-bubble setup on a "
                       f"{'x'.join(map(str, CPU_SAMPLE_GRID))} grid ({case.cells} cells)",
+            "seconds": el}
+
+
+def _cpu_single_core(budget_s=6.0):
+    """The oracle on one host core (the kind of CPU figure GPU speed-ups are
+    usually quoted against), on a smaller sample of the same workload."""
+    from paper_2403_05910_b300 import cases
+    from oracle.xfo import Oracle
+    grid = (48, 24, 24)
+    case = cases.config(2, n=grid)
+    o = Oracle(case, threads=1)
+    U, T = o.prim_to_cons()
+    dt = o.dt(U, T)
+    o.step(U, T, dt)
+    n, t0 = 0, time.perf_counter()
+    while True:
+        o.step(U, T, dt)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or n >= 10:
+            break
+    return {"value": case.cells * 3 * n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} RK3 step(s) on a {'x'.join(map(str, grid))} grid ({case.cells} cells)",
             "seconds": el}
 
 
@@ -266,20 +290,23 @@ def _adjoint_vs_forward(args, dev, stream):
 
 
 VARIANTS = (("weno5+positivity", {"positivity": True}), ("weno_cu6", {"weno": 6}),
-            ("weno7", {"weno": 7}))
+            ("weno7", {"weno": 7}), ("mixture_averaged_diffusion", {"diffusion": 1}))
 
 
 def _variants(args, dev, stream, case):
     """The same workload and step with the other options of the path: WENO5
-    with the positivity-preserving blend (Eq. 17-20), WENO-CU6 and WENO7.
-    Rate and the face kernels' FP64 rate from the library's own events."""
+    with the positivity-preserving blend (Eq. 17-20), WENO-CU6, WENO7, and
+    the mixture-averaged diffusion of Eq. 25-26 (seeded binary fits added to
+    the same species). Rate and the face kernels' FP64 rate from the
+    library's own events."""
     import torch
-    from paper_2403_05910_b300 import flops
+    from paper_2403_05910_b300 import cases, flops
     from paper_2403_05910_b300.xf import Solver
     steps = max(1, min(args.steps, 5))
     out = {}
+    case_dsm = cases.with_binary_diffusion(case)
     for name, kw in VARIANTS:
-        s = Solver(case, **kw)
+        s = Solver(case_dsm if kw.get("diffusion") else case, **kw)
         P = torch.from_numpy(case.prim).to(dev)
         s.set_primitive(P)
         del P
@@ -297,7 +324,8 @@ def _variants(args, dev, stream, case):
         ms = e0.elapsed_time(e1)
         st = s.status()
         s.close()
-        fl = flops.per_cell_stage(case, weno=kw.get("weno", 5), positivity=kw.get("positivity", False))
+        fl = flops.per_cell_stage(case, weno=kw.get("weno", 5), positivity=kw.get("positivity", False),
+                                  diffusion=kw.get("diffusion", 0))
         face_ms = sum(prof[k][0] for k in ("face_x", "face_y", "face_z") if k in prof)
         face_n = sum(prof[k][1] for k in ("face_x", "face_y", "face_z") if k in prof)
         face_tf = fl["face"] / case.dim / (face_ms / face_n * 1e-3) / 1e12
@@ -305,7 +333,8 @@ def _variants(args, dev, stream, case):
                      "ms_per_step": ms / steps, "steps": steps,
                      "face_fp64_tflops": face_tf, "face_frac": face_tf / FP64_NOMINAL_TFLOPS,
                      "flops_per_face": flops.face(case.dim, case.n_species, case.viscous,
-                                                  kw.get("weno", 5), kw.get("positivity", False)),
+                                                  kw.get("weno", 5), kw.get("positivity", False),
+                                                  kw.get("diffusion", 0)),
                      "kernels_ms_per_step": {k: v[0] / steps for k, v in prof.items()},
                      "status_flags": st}
     return out
@@ -408,6 +437,7 @@ def run_ours(args):
             from oracle import build as ob
             ob.build()
             cpu = _cpu_baseline()
+            cpu["single_core"] = _cpu_single_core()
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_all / args.steps, "higher_is_better": True,
@@ -464,7 +494,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-per-instance leg")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-vs-forward leg")
     ap.add_argument("--no-variants", action="store_true",
-                    help="skip the positivity / WENO-CU6 / WENO7 leg")
+                    help="skip the positivity / WENO-CU6 / WENO7 / mixture-diffusion leg")
     ap.add_argument("--grid", default="", help="override the grid, e.g. 160,80,80 (profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)  # at least three untimed warm-up steps

@@ -31,20 +31,24 @@ def face_positivity(d: int, N: int) -> int:
     return 7 * nv + 8 + 16 * N
 
 
-def face_viscous(d: int, N: int) -> int:
-    """4th-order face values / derivatives, stress, heat and diffusion fluxes."""
-    return 41 + 11 * d + 5 * d * d + 38 * N
+def face_viscous(d: int, N: int, diffusion: int = 0) -> int:
+    """4th-order face values / derivatives, stress, heat and diffusion fluxes
+    (diffusion = 1: a face value of D_sm per species and its own product)."""
+    return 41 + 11 * d + 5 * d * d + 38 * N + (6 * N if diffusion else 0)
 
 
-def face(d: int, N: int, viscous: bool, weno: int = 5, positivity: bool = False) -> int:
-    return (face_convective(d, N, weno) + (face_viscous(d, N) if viscous else 0) +
+def face(d: int, N: int, viscous: bool, weno: int = 5, positivity: bool = False,
+         diffusion: int = 0) -> int:
+    return (face_convective(d, N, weno) + (face_viscous(d, N, diffusion) if viscous else 0) +
             (face_positivity(d, N) if positivity else 0))
 
 
-def prim_cell(d: int, N: int, viscous: bool) -> int:
-    """Primitive recovery (Newton, EOS, sound speed) + mixture transport."""
+def prim_cell(d: int, N: int, viscous: bool, diffusion: int = 0) -> int:
+    """Primitive recovery (Newton, EOS, sound speed) + mixture transport
+    (diffusion = 1 adds the binary fits, one exp per pair, and Eq. 26)."""
     base = 21 + 24 * N + NEWTON_ITERS * NEWTON_ITER + 24
-    return base + ((7 + 31 * N + 13 * N * N) if viscous else 0)
+    dsm = (11 * N * (N - 1) // 2 + N * (N + 6)) if (viscous and diffusion) else 0
+    return base + ((7 + 31 * N + 13 * N * N) if viscous else 0) + dsm
 
 
 def grad_cell(d: int, viscous: bool) -> int:
@@ -56,7 +60,7 @@ def update_cell(d: int, N: int) -> int:
     return nv * (3 * d + 3)
 
 
-def per_cell_stage(case, weno: int = 5, positivity: bool = False) -> dict:
+def per_cell_stage(case, weno: int = 5, positivity: bool = False, diffusion: int = 0) -> dict:
     """Flops of one stage over the whole grid, split by kernel class."""
     d, N, vis = case.dim, case.n_species, bool(case.viscous)
     n = case.n
@@ -67,9 +71,9 @@ def per_cell_stage(case, weno: int = 5, positivity: bool = False) -> dict:
         pcells *= (n[a] + 2 * ghosts) if a < d else 1
     nfaces = [((n[0] + (a == 0)) * (n[1] + (a == 1)) * (n[2] + (a == 2))) for a in range(d)]
     out = {
-        "prim": prim_cell(d, N, vis) * pcells,
+        "prim": prim_cell(d, N, vis, diffusion) * pcells,
         "grad": grad_cell(d, vis) * pcells,
-        "face": face(d, N, vis, weno, positivity) * sum(nfaces),
+        "face": face(d, N, vis, weno, positivity, diffusion) * sum(nfaces),
         "update": update_cell(d, N) * cells,
     }
     out["total"] = sum(out.values())
