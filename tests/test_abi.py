@@ -63,6 +63,25 @@ def test_argument_errors_need_no_device():
     g, t, o, keep = xf.structs(c)
     g.bc[0][0], g.bc[0][1] = xf.BC_PERIODIC, xf.BC_TRANSMISSIVE
     assert xf.lib.xf_create(C.byref(g), C.byref(t), C.byref(o), C.byref(h)) == xf.XF_ERR_ARG
+    # a grid whose padded block would exceed the 2^31-cell index range, a
+    # zero-sized axis and an out-of-range dimension
+    g, t, o, keep = xf.structs(c)
+    g.dim, g.n[0], g.n[1], g.n[2] = 3, 2048, 1024, 1024
+    assert xf.lib.xf_create(C.byref(g), C.byref(t), C.byref(o), C.byref(h)) == xf.XF_ERR_ARG
+    g, t, o, keep = xf.structs(c)
+    g.n[0] = 0
+    assert xf.lib.xf_create(C.byref(g), C.byref(t), C.byref(o), C.byref(h)) == xf.XF_ERR_ARG
+    g, t, o, keep = xf.structs(c)
+    g.dim = 4
+    assert xf.lib.xf_create(C.byref(g), C.byref(t), C.byref(o), C.byref(h)) == xf.XF_ERR_ARG
+    # WENO7 needs four cells per axis; the mixture-averaged model needs fits
+    g, t, o, keep = xf.structs(cases.shock_tube(0, n=3))
+    o.weno = 7
+    assert xf.lib.xf_create(C.byref(g), C.byref(t), C.byref(o), C.byref(h)) == xf.XF_ERR_ARG
+    g, t, o, keep = xf.structs(c)
+    o.viscous, o.diffusion = 1, 1
+    t.mu_coef, t.kappa_coef = keep[3].ctypes.data_as(C.POINTER(C.c_double)), keep[4].ctypes.data_as(C.POINTER(C.c_double))
+    assert xf.lib.xf_create(C.byref(g), C.byref(t), C.byref(o), C.byref(h)) == xf.XF_ERR_ARG
     assert xf.lib.xf_step_rk3(None, 0.0, None, None) == xf.XF_ERR_ARG
     assert xf.lib.xf_rhs(None, None, None, None) == xf.XF_ERR_ARG
     assert xf.lib.xf_status_str(xf.XF_ERR_NEWTON).decode().startswith("temperature")
