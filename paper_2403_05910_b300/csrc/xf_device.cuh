@@ -125,6 +125,15 @@ __device__ __forceinline__ double h_s(const Params& p, int s, const TauPt& t, do
   return fma(poly, t.tc, p.rhoff[s]) + cps * t.ext;
 }
 
+// h_s alone: the c_p term of the linear continuation is evaluated only when T
+// lies outside [T_lo, T_hi] (ext != 0); inside, the result is the same bits.
+__device__ __forceinline__ double h_s_in(const Params& p, int s, const TauPt& t) {
+  const double* a = p.rh[s];
+  const double poly = fma(fma(fma(fma(a[4], t.tc, a[3]), t.tc, a[2]), t.tc, a[1]), t.tc, a[0]);
+  const double h = fma(poly, t.tc, p.rhoff[s]);
+  return t.ext != 0.0 ? fma(cp_s(p, s, t.tc), t.ext, h) : h;
+}
+
 // ------------------------------------------------------------ status ------
 __device__ __forceinline__ void raise(uint32_t* flags, uint32_t bits) {
   if (bits) atomicOr(flags, bits);
@@ -242,10 +251,25 @@ __device__ __forceinline__ void prim_cell(const Params& p, long long t, const do
         const double lk = fma(fma(fma(p.lnka[s][3], lnT, p.lnka[s][2]), lnT, p.lnka[s][1]), lnT, p.lnka[s][0]);
         smu[s] = exp(0.5 * lm);
         ska[s] = exp(0.5 * lk);
-        ismu[s] = 1.0 / smu[s];
-        iska[s] = 1.0 / ska[s];
         X[s] = Y[s] * p.invW[s];
         xs += X[s];
+      }
+      // the 2N reciprocals 1/sqrt(mu_s), 1/sqrt(kappa_s) from one division
+      // (running products: 1/v_k = (prod_{j<k} v_j) / (prod_{j<=k} v_j))
+      {
+        double pre[2 * NS];
+        pre[0] = smu[0];
+#pragma unroll
+        for (int k = 1; k < 2 * NS; ++k) pre[k] = pre[k - 1] * (k < NS ? smu[k] : ska[k - NS]);
+        double inv = 1.0 / pre[2 * NS - 1];
+#pragma unroll
+        for (int k = 2 * NS - 1; k > 0; --k) {
+          const double v = k < NS ? smu[k] : ska[k - NS];
+          const double r = inv * pre[k - 1];
+          if (k < NS) ismu[k] = r; else iska[k - NS] = r;
+          inv *= v;
+        }
+        ismu[0] = inv;
       }
       const double ixs = 1.0 / xs;
       // Wilke denominators sum_t X_t A_st (1 + r_st B_st)^2 with r_st = (a_s/a_t)^(1/2),
@@ -261,6 +285,7 @@ __device__ __forceinline__ void prim_cell(const Params& p, long long t, const do
         xk1[s] = X[s] * iska[s];
         xk2[s] = xk1[s] * iska[s];
       }
+      double dm[NS], dk[NS];
 #pragma unroll
       for (int s = 0; s < NS; ++s) {
         double s0 = 0.0, m1 = 0.0, m2 = 0.0, k1 = 0.0, k2 = 0.0;
@@ -272,11 +297,30 @@ __device__ __forceinline__ void prim_cell(const Params& p, long long t, const do
           k1 = fma(xk1[tt], p.wAB[s][tt], k1);
           k2 = fma(xk2[tt], p.wABB[s][tt], k2);
         }
-        const double mus = smu[s] * smu[s], kas = ska[s] * ska[s];
-        const double dm = fma(mus, m2, fma(2.0 * smu[s], m1, s0));
-        const double dk = fma(kas, k2, fma(2.0 * ska[s], k1, s0));
-        mu = fma(X[s] * mus, 1.0 / dm, mu);
-        ka = fma(X[s] * kas, 1.0 / dk, ka);
+        dm[s] = fma(smu[s] * smu[s], m2, fma(2.0 * smu[s], m1, s0));
+        dk[s] = fma(ska[s] * ska[s], k2, fma(2.0 * ska[s], k1, s0));
+      }
+      // the 2N Wilke denominators inverted with one division, as above
+      {
+        double pre[2 * NS];
+        pre[0] = dm[0];
+#pragma unroll
+        for (int k = 1; k < 2 * NS; ++k) pre[k] = pre[k - 1] * (k < NS ? dm[k] : dk[k - NS]);
+        double inv = 1.0 / pre[2 * NS - 1];
+        double idm[NS], idk[NS];
+#pragma unroll
+        for (int k = 2 * NS - 1; k > 0; --k) {
+          const double v = k < NS ? dm[k] : dk[k - NS];
+          const double r = inv * pre[k - 1];
+          if (k < NS) idm[k] = r; else idk[k - NS] = r;
+          inv *= v;
+        }
+        idm[0] = inv;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+          mu = fma(X[s] * (smu[s] * smu[s]), idm[s], mu);
+          ka = fma(X[s] * (ska[s] * ska[s]), idk[s], ka);
+        }
       }
       mu *= p.fmu;
       ka *= p.fka;
@@ -459,15 +503,6 @@ __device__ __forceinline__ void weno5_nd(double f0, double f1, double f2, double
   den = (w0 + w1) + w2;
 }
 
-// F^+ + F^- of one characteristic field (Eq. 15): the upwind reconstruction
-// of w^+ from i-2..i+2 and the mirrored one of w^- from i+3..i-1, normalised
-// by a single division.
-__device__ __forceinline__ double weno5_pair(const double* wp, const double* wm, const double* e12c) {
-  double np, dp, nm, dm;
-  weno5_nd(wp[0], wp[1], wp[2], wp[3], wp[4], e12c, np, dp);
-  weno5_nd(wm[5], wm[4], wm[3], wm[2], wm[1], e12c, nm, dm);
-  return (wp[2] + wm[3]) + fma(np, dm, nm * dp) / (dp * dm);
-}
 
 // WENO-CU6 (central-upwind, ref. 34): candidates q_0..q_2 of WENO5 and the
 // downwind q_3 on {i+1, i+2, i+3}, linear weights (1, 9, 9, 1)/20, beta_3 the
@@ -522,14 +557,6 @@ __device__ __forceinline__ void cu6_nd(double f0, double f1, double f2, double f
   den = (w0 + w1) + (w2 + w3);
 }
 
-// F^+ + F^- of one characteristic field with WENO-CU6: w^+ from i-2..i+3 and
-// the mirrored w^- from i+3..i-2; e4[3] = 12 eps.
-__device__ __forceinline__ double cu6_pair(const double* wp, const double* wm, const double* e4) {
-  double np, dp, nm, dm;
-  cu6_nd(wp[0], wp[1], wp[2], wp[3], wp[4], wp[5], e4[3], np, dp);
-  cu6_nd(wm[5], wm[4], wm[3], wm[2], wm[1], wm[0], e4[3], nm, dm);
-  return (wp[2] + wm[3]) + fma(np, dm, nm * dp) / (dp * dm);
-}
 
 // WENO7-JS (ref. 36) at i+1/2 from f0..f6 = f_{i-3..i+3}: cubic candidates on
 // {i-3+k .. i+k}, linear weights d = (1, 12, 18, 4)/35, Jiang-Shu indicators
@@ -574,22 +601,41 @@ __device__ __forceinline__ void weno7_nd(double f0, double f1, double f2, double
   den = (w0 + w1) + (w2 + w3);
 }
 
-// F^+ + F^- with WENO7: w^+ from i-3..i+3 and the mirrored w^- from i+4..i-2
-__device__ __forceinline__ double weno7_pair(const double* wp, const double* wm, const double* ec) {
-  double np, dp, nm, dm;
-  weno7_nd(wp[0], wp[1], wp[2], wp[3], wp[4], wp[5], wp[6], ec, np, dp);
-  weno7_nd(wm[7], wm[6], wm[5], wm[4], wm[3], wm[2], wm[1], ec, nm, dm);
-  return (wp[3] + wm[4]) + fma(np, dm, nm * dp) / (dp * dm);
-}
-
-// the reconstruction of Eq. 15 selected by REC (5: WENO5-JS, 6: WENO-CU6,
-// 7: WENO7-JS); e4 = {12 eps c_0, 12 eps c_1, 12 eps c_2, 12 eps} for 5 and 6,
-// {240 eps c_k} for 7
+// F^+ + F^- of one characteristic field (Eq. 15) with the reconstruction REC
+// (5: WENO5-JS, 6: WENO-CU6, 7: WENO7-JS): the upwind reconstruction of w^+
+// and the mirrored one of w^- about the face, as b + n/d with the division
+// left to the caller (two fields share one). Stencils: w^+ from i-2..i+2
+// (i-3..i+3 for WENO7, i-2..i+3 for CU6), w^- mirrored from i+3 (i+4).
+// e4 = {12 eps c_0, 12 eps c_1, 12 eps c_2, 12 eps} for 5 and 6, {240 eps c_k} for 7.
+struct RecND {
+  double b, n, d;
+};
 template <int REC>
-__device__ __forceinline__ double rec_pair(const double* wp, const double* wm, const double* e4) {
-  if constexpr (REC == 7) return weno7_pair(wp, wm, e4);
-  else if constexpr (REC == 6) return cu6_pair(wp, wm, e4);
-  else return weno5_pair(wp, wm, e4);
+__device__ __forceinline__ RecND rec_nd(const double* wp, const double* wm, const double* e4) {
+  double np, dp, nm, dm, b;
+  if constexpr (REC == 7) {
+    weno7_nd(wp[0], wp[1], wp[2], wp[3], wp[4], wp[5], wp[6], e4, np, dp);
+    weno7_nd(wm[7], wm[6], wm[5], wm[4], wm[3], wm[2], wm[1], e4, nm, dm);
+    b = wp[3] + wm[4];
+  } else if constexpr (REC == 6) {
+    cu6_nd(wp[0], wp[1], wp[2], wp[3], wp[4], wp[5], e4[3], np, dp);
+    cu6_nd(wm[5], wm[4], wm[3], wm[2], wm[1], wm[0], e4[3], nm, dm);
+    b = wp[2] + wm[3];
+  } else {
+    weno5_nd(wp[0], wp[1], wp[2], wp[3], wp[4], e4, np, dp);
+    weno5_nd(wm[5], wm[4], wm[3], wm[2], wm[1], e4, nm, dm);
+    b = wp[2] + wm[3];
+  }
+  return RecND{b, fma(np, dm, nm * dp), dp * dm};
+}
+__device__ __forceinline__ double rec_div1(const RecND& x) { return x.b + x.n / x.d; }
+// two fields with one division: 1/d_x = d_y / (d_x d_y). The weights are
+// scaled by the indicators' products (section above), so d_x d_y stays far
+// inside the double range for any finite stencil data the solver meets.
+__device__ __forceinline__ void rec_div2(const RecND& x, const RecND& y, double& fx, double& fy) {
+  const double r = 1.0 / (x.d * y.d);
+  fx = fma(x.n, r * y.d, x.b);
+  fy = fma(y.n, r * x.d, y.b);
 }
 
 // ================================================================= k_face ===
@@ -649,7 +695,9 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
       Rb = fma(Yb[s], p.r[s], Rb);
       cvb = fma(Yb[s], cps - p.r[s], cvb);
     }
-    const double Gam = Rb / cvb;
+    // one division for Gamma = R/c_v and its inverse
+    const double rRc = 1.0 / (Rb * cvb);
+    const double Gam = Rb * Rb * rRc;
     const double hq2 = 0.5 * q2;
     double phi[NS], c2 = 0.0;
 #pragma unroll
@@ -663,10 +711,11 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
       const double cl = QF(L::C, 0), cr = QF(L::C, 1);
       c2 = 0.5 * (cl * cl + cr * cr);
     }
-    const double c = sqrt(c2);
-    const double ic2 = 1.0 / c2;
+    const double rsc = rsqrt(c2);
+    const double c = c2 * rsc;
+    const double ic2 = rsc * rsc;
     const double hic2 = 0.5 * ic2;
-    const double iGam = cvb / Rb;
+    const double iGam = cvb * cvb * rRc;
     const double un = ub[D];
     // ---- stencil m = i-SO..i+SO+1 (SW cells: i-2..i+3 for WENO5 and CU6,
     //      i-3..i+4 for WENO7; offsets from the left cell). Per cell:
@@ -714,9 +763,37 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
     // ---- PER: one characteristic field at a time. With w = (1/2)(l.F_m +- a l.U_m)
     //      and l.F_m = u_m (l.U_m) + p_m (l[m_n] + u_m l[E]):
     //      w^+- = (u_m/2 +- a/2) l.U_m + p_m (l[m_n]/2 + (u_m/2) l[E]).
-    double Fk_m, Fk_p, Fk_e;
+    // the passive fields (eigenvalue u, no pressure term): tangential momenta,
+    // l = (-u_t, e_{m_t}), r = e_{m_t} + u_t e_E; species, l = (-Y_s, e_{rhoY_s}),
+    // r = e_{rhoY_s} - (phi_s - phi_N)/Gamma e_E. Passive field k < DIM-1 is the
+    // tangential axis k (skipping D), the rest the species k - (DIM-1).
+    constexpr int NPASS = DIM - 1 + NS - 1;
+    double hp0[SW], hm0[SW];
+    auto passive_nd = [&](int k) -> RecND {
+      double wp[SW], wm[SW];
+      if (k < DIM - 1) {
+        const int a = k < D ? k : k + 1;
+#pragma unroll
+        for (int m = 0; m < SW; ++m) {
+          const double LU = fma(-ub[a], rho_m[m], QF(L::U + 1 + a, m - SO));
+          wp[m] = hp0[m] * LU;
+          wm[m] = hm0[m] * LU;
+        }
+      } else {
+        const int s = k - (DIM - 1);
+#pragma unroll
+        for (int m = 0; m < SW; ++m) {
+          const double LU = fma(-Yb[s], rho_m[m], QF(L::U + IE + 1 + s, m - SO));
+          wp[m] = hp0[m] * LU;
+          wm[m] = hm0[m] * LU;
+        }
+      }
+      return rec_nd<REC>(wp, wm, e12c);
+    };
+    double Fk_m, Fk_p, Fk_e, Fk_first = 0.0;
     {
       double wp[SW], wm[SW];
+      RecND ndm, ndp, nde;
       // u - c: l.U = (g.U - c (m_n - u_n rho)) / (2c^2)
       {
         const double hlmn = 0.5 * (-Gam * un - c) * hic2, lE = Gam * hic2;
@@ -729,7 +806,7 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
           wp[m] = fma(hun[m] + ha, LU, pq);
           wm[m] = fma(hun[m] - ha, LU, pq);
         }
-        Fk_m = rec_pair<REC>(wp, wm, e12c);
+        ndm = rec_nd<REC>(wp, wm, e12c);
       }
       // u + c
       {
@@ -743,8 +820,9 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
           wp[m] = fma(hun[m] + ha, LU, pq);
           wm[m] = fma(hun[m] - ha, LU, pq);
         }
-        Fk_p = rec_pair<REC>(wp, wm, e12c);
+        ndp = rec_nd<REC>(wp, wm, e12c);
       }
+      rec_div2(ndm, ndp, Fk_m, Fk_p);
       // entropy: l = e_rho - g / c^2
       {
         const double hlmn = 0.5 * Gam * un * ic2, lE = -Gam * ic2;
@@ -756,8 +834,14 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
           wp[m] = fma(hun[m] + ha, LU, pq);
           wm[m] = fma(hun[m] - ha, LU, pq);
         }
-        Fk_e = rec_pair<REC>(wp, wm, e12c);
+        nde = rec_nd<REC>(wp, wm, e12c);
       }
+      const double ha0 = 0.5 * a0;
+#pragma unroll
+      for (int m = 0; m < SW; ++m) { hp0[m] = hun[m] + ha0; hm0[m] = hun[m] - ha0; }
+      // the entropy field shares its division with the first passive field
+      if constexpr (NPASS > 0) rec_div2(nde, passive_nd(0), Fk_e, Fk_first);
+      else Fk_e = rec_div1(nde);
     }
     // back-projection of the three dense right columns (Eq. 15)
     {
@@ -771,39 +855,30 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
 #pragma unroll
       for (int s = 0; s < NS - 1; ++s) Gout[IE + 1 + s] = Yb[s] * S;
     }
-    // the remaining fields all have eigenvalue u and no pressure term
-    const double ha0 = 0.5 * a0;
-    double hp0[SW], hm0[SW];
-#pragma unroll
-    for (int m = 0; m < SW; ++m) { hp0[m] = hun[m] + ha0; hm0[m] = hun[m] - ha0; }
-    // tangential momenta: l = (-u_t, e_{m_t}), r = e_{m_t} + u_t e_E
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) {
-      if (a == D) continue;
-      double wp[SW], wm[SW];
-#pragma unroll
-      for (int m = 0; m < SW; ++m) {
-        const double LU = fma(-ub[a], rho_m[m], QF(L::U + 1 + a, m - SO));
-        wp[m] = hp0[m] * LU;
-        wm[m] = hm0[m] * LU;
+    // the passive fields' right columns, in order, two fields per division
+    auto passive_add = [&](int k, double Fk) {
+      if (k < DIM - 1) {
+        const int a = k < D ? k : k + 1;
+        Gout[1 + a] += Fk;
+        Gout[IE] = fma(ub[a], Fk, Gout[IE]);
+      } else {
+        const int s = k - (DIM - 1);
+        Gout[IE + 1 + s] += Fk;
+        Gout[IE] = fma(-dphi[s] * iGam, Fk, Gout[IE]);
       }
-      const double Fk = rec_pair<REC>(wp, wm, e12c);
-      Gout[1 + a] += Fk;
-      Gout[IE] = fma(ub[a], Fk, Gout[IE]);
-    }
-    // species: l = (-Y_s, e_{rhoY_s}), r = e_{rhoY_s} - (phi_s - phi_N)/Gamma e_E
+    };
+    if constexpr (NPASS > 0) passive_add(0, Fk_first);
 #pragma unroll
-    for (int s = 0; s < NS - 1; ++s) {
-      double wp[SW], wm[SW];
-#pragma unroll
-      for (int m = 0; m < SW; ++m) {
-        const double LU = fma(-Yb[s], rho_m[m], QF(L::U + IE + 1 + s, m - SO));
-        wp[m] = hp0[m] * LU;
-        wm[m] = hm0[m] * LU;
+    for (int k = 1; k < NPASS; k += 2) {
+      const RecND x = passive_nd(k);
+      if (k + 1 < NPASS) {
+        double fx, fy;
+        rec_div2(x, passive_nd(k + 1), fx, fy);
+        passive_add(k, fx);
+        passive_add(k + 1, fy);
+      } else {
+        passive_add(k, rec_div1(x));
       }
-      const double Fk = rec_pair<REC>(wp, wm, e12c);
-      Gout[IE + 1 + s] += Fk;
-      Gout[IE] = fma(-dphi[s] * iGam, Fk, Gout[IE]);
     }
   }
 
@@ -901,7 +976,7 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
       J[s] = -rf * fma(Dsf[s], dY[s], -Yf[s] * corr);
-      const double hs = h_s(p, s, tp, cp_s(p, s, tp.tc));
+      const double hs = h_s_in(p, s, tp);
       qd = fma(hs, J[s], qd);
     }
     const double dT = FD(L::T);
