@@ -472,7 +472,7 @@ k_grad(const __grid_constant__ Params p, double* __restrict__ Q) {
 }
 
 // ================================================================= WENO5 ===
-// WENO5-JS at i+1/2 from f0..f4 = f_{i-2..i+2}, returned as F = f2 + num/den.
+// WENO5-JS at i+1/2 from f0..f4 = f_{i-2..i+2}, returned as F = f2 + num/(6 den).
 // Written on first differences a..d: the smoothness indicators are scaled by
 // 12 (12 b_k = 13 t_k^2 + 3 u_k^2, with 12 eps) -- a common factor that leaves
 // the weights unchanged -- and the nonlinear weights d_k/(eps + b_k)^2 are
@@ -496,9 +496,11 @@ __device__ __forceinline__ void weno5_nd(double f0, double f1, double f2, double
   const double s2 = fma((13.0 * kWc2) * t2, t2, fma((3.0 * kWc2) * u2, u2, e12c[2]));
   const double p12 = s1 * s2, p02 = s0 * s2, p01 = s0 * s1;
   const double w0 = p12 * p12, w1 = p02 * p02, w2 = p01 * p01;
-  const double q0 = fma(5.0 / 6.0, b, (-1.0 / 3.0) * a);   // q_0 - f2
-  const double q1 = fma(1.0 / 3.0, c, (1.0 / 6.0) * b);    // q_1 - f2
-  const double q2 = fma(2.0 / 3.0, c, (-1.0 / 6.0) * d);   // q_2 - f2
+  // 6 (q_k - f2): 5b - 2a = 2 u0 - b, 2c + b, 4c - d; the factor 6 goes to
+  // the denominator of the field pair (kRecScale)
+  const double q0 = fma(2.0, u0, -b);
+  const double q1 = fma(2.0, c, b);
+  const double q2 = fma(4.0, c, -d);
   num = fma(w0, q0, fma(w1, q1, w2 * q2));
   den = (w0 + w1) + w2;
 }
@@ -549,10 +551,11 @@ __device__ __forceinline__ void cu6_nd(double f0, double f1, double f2, double f
   const double w1 = 0.45 * fma(20.0, s1, tau) * (s0 * p23);
   const double w2 = 0.45 * fma(20.0, s2, tau) * (p01 * s3);
   const double w3 = 0.05 * fma(20.0, s3, tau) * (p01 * s2);
-  const double q0 = fma(5.0 / 6.0, b, (-1.0 / 3.0) * a);    // q_0 - f2
-  const double q1 = fma(1.0 / 3.0, c, (1.0 / 6.0) * b);     // q_1 - f2
-  const double q2 = fma(2.0 / 3.0, c, (-1.0 / 6.0) * d);    // q_2 - f2
-  const double q3 = fma(1.0 / 3.0, e, fma(-5.0 / 6.0, d, c));  // q_3 - f2
+  // 6 (q_k - f2), as in weno5_nd; q_3: 6c - 5d + 2e
+  const double q0 = fma(2.0, u0, -b);
+  const double q1 = fma(2.0, c, b);
+  const double q2 = fma(4.0, c, -d);
+  const double q3 = fma(6.0, c, fma(-5.0, d, 2.0 * e));
   num = fma(w0, q0, fma(w1, q1, fma(w2, q2, w3 * q3)));
   den = (w0 + w1) + (w2 + w3);
 }
@@ -626,7 +629,9 @@ __device__ __forceinline__ RecND rec_nd(const double* wp, const double* wm, cons
     weno5_nd(wm[5], wm[4], wm[3], wm[2], wm[1], e4, nm, dm);
     b = wp[2] + wm[3];
   }
-  return RecND{b, fma(np, dm, nm * dp), dp * dm};
+  // the WENO5 and CU6 numerators carry a factor 6 (weno5_nd, cu6_nd)
+  constexpr double kRecScale = REC == 7 ? 1.0 : 6.0;
+  return RecND{b, fma(np, dm, nm * dp), kRecScale * (dp * dm)};
 }
 __device__ __forceinline__ double rec_div1(const RecND& x) { return x.b + x.n / x.d; }
 // two fields with one division: 1/d_x = d_y / (d_x d_y). The weights are
@@ -691,7 +696,7 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
       const double cps = cp_s(p, s, tp.tc);
-      es[s] = h_s(p, s, tp, cps) - p.r[s] * Tb;
+      es[s] = h_s_in(p, s, tp) - p.r[s] * Tb;
       Rb = fma(Yb[s], p.r[s], Rb);
       cvb = fma(Yb[s], cps - p.r[s], cvb);
     }
