@@ -446,9 +446,13 @@ __device__ __forceinline__ void grad_cell(const Params& p, long long t, double* 
   using L = Lay<DIM, NS>;
   const long long PC = p.pcells;
   int idx[3];
-  idx[0] = (int)(t % p.np[0]);
-  idx[1] = (int)((t / p.np[0]) % p.np[1]);
-  idx[2] = (int)(t / ((long long)p.np[0] * p.np[1]));
+  {
+    const unsigned tu = (unsigned)t, m0 = (unsigned)p.np[0], m1 = (unsigned)p.np[1];
+    const unsigned q0 = tu / m0;
+    idx[0] = (int)(tu - q0 * m0);
+    idx[1] = (int)(q0 % m1);
+    idx[2] = (int)(q0 / m1);
+  }
   const long long stride[3] = {1, p.np[0], (long long)p.np[0] * p.np[1]};
 #pragma unroll
   for (int b = 0; b < DIM; ++b) {
@@ -1021,9 +1025,12 @@ __device__ __forceinline__ void update_cell(const Params& p, long long c,
                                             const double* __restrict__ Gz, const double* Un,
                                             const double* Us, double* out, double dt, int mode) {
   constexpr int NV = DIM + 1 + NS;
-  const int i = (int)(c % p.n[0]);
-  const int j = (int)((c / p.n[0]) % p.n[1]);
-  const int k = (int)(c / ((long long)p.n[0] * p.n[1]));
+  // 32-bit index arithmetic: a handle's padded block holds < 2^31 cells
+  const unsigned cu = (unsigned)c, n0 = (unsigned)p.n[0], n1 = (unsigned)p.n[1];
+  const unsigned q0 = cu / n0;
+  const int i = (int)(cu - q0 * n0);
+  const int j = (int)(q0 % n1);
+  const int k = (int)(q0 / n1);
   const long long C = p.cells;
   long long fy = 0, fz = 0, NFY = 0, NFZ = 0, sy = 0, sz = 0;
   const long long NFX = (long long)(p.n[0] + 1) * p.n[1] * p.n[2];

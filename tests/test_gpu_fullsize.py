@@ -72,10 +72,16 @@ def _windows(case, w):
     return out
 
 
+_INPUTS = {}
+
+
 def _full_inputs(case):
-    o = Oracle(case)
-    U, T = o.prim_to_cons()
-    return U, T
+    """U, T of a full-size case (cached: the conversion of 33.5 M cells takes
+    the oracle a while and several tests share it)."""
+    key = (case.name, case.n)
+    if key not in _INPUTS:
+        _INPUTS[key] = Oracle(case).prim_to_cons()
+    return _INPUTS[key]
 
 
 def _rel(pairs, dim):
@@ -138,6 +144,40 @@ def test_fullsize_one_step_windows(cfg, w, dt):
         o.step(Uw, Tw, dt)
         ref = Uw.reshape(case.n_v, sub.n[2], sub.n[1], sub.n[0])[(slice(None),) + core]
         got = Ug[(slice(None),) + tuple(slice(l, h) for l, h in zip(lo[::-1], hi[::-1]))]
+        pairs.append((got, ref))
+    err = _rel(pairs, case.dim)
+    assert np.max(err) <= 1e-11, err
+
+
+@pytest.mark.parametrize("kw,margin", [({"weno": 6}, 3), ({"weno": 7}, 4),
+                                       ({"diffusion": 1}, 3), ({"positivity": True}, 3)])
+def test_fullsize_variants_rhs_windows(kw, margin):
+    """The other options of the path on the bench's 512x256x256 workload, in
+    the launch configuration of bench.py's variants leg: one RHS per option,
+    compared on the sampled windows (WENO7's 8-cell stencil needs a margin of
+    4; the blend does not act in a plain RHS, which must equal the unblended
+    one). The binary diffusion fits come from their own RNG, so the inputs are
+    the bench's."""
+    import torch
+    base = cases.config(2)
+    case = cases.with_binary_diffusion(base) if kw.get("diffusion") else base
+    U, T = _full_inputs(base)
+    s = gpu_solver(case, **kw)
+    Ud = dev(U)
+    s.set_state(Ud, dev(T))
+    R = torch.empty_like(Ud)
+    s.rhs(Ud, R)
+    torch.cuda.synchronize()
+    assert s.status() == 0
+    Rg = R.cpu().numpy().reshape(case.n_v, case.n[2], case.n[1], case.n[0])
+    s.close()
+    del Ud, R
+    pairs = []
+    for lo, hi in _windows(case, 12):
+        sub, Uw, Tw, core, sl = _window(case, U, T, lo, hi, margin)
+        Rw, _, st = Oracle(sub, **kw).rhs(Uw, Tw)
+        ref = Rw.reshape(case.n_v, sub.n[2], sub.n[1], sub.n[0])[(slice(None),) + core]
+        got = Rg[(slice(None),) + tuple(slice(l, h) for l, h in zip(lo[::-1], hi[::-1]))]
         pairs.append((got, ref))
     err = _rel(pairs, case.dim)
     assert np.max(err) <= 1e-11, err
