@@ -20,46 +20,49 @@
 namespace xf {
 
 // ------------------------------------------------------------ WENO5 adjoint
-// Forward intermediates of one WENO5-JS reconstruction (the same function as
-// weno5_nd, with the linear weights applied explicitly), kept for its reverse.
+// Forward intermediates of one WENO5-JS reconstruction, computed exactly as
+// weno5_nd (indicators scaled by 12 c_k with the linear weights folded in,
+// candidates as 6 (q_k - f2)), kept for its reverse. F = f2 + num/den with
+// the factor 6 carried by den.
 struct W5 {
   double a, b, c, d, t0, u0, t1, u1, t2, u2, s0, s1, s2, p12, p02, p01, w0, w1, w2, q0, q1, q2;
   double num, den;
 };
 
 __device__ __forceinline__ void w5_fwd(double f0, double f1, double f2, double f3, double f4,
-                                       double eps12, W5& r) {
+                                       const double* e12c, W5& r) {
   r.a = f1 - f0; r.b = f2 - f1; r.c = f3 - f2; r.d = f4 - f3;
   r.t0 = r.b - r.a; r.u0 = fma(3.0, r.b, -r.a);
   r.t1 = r.c - r.b; r.u1 = r.b + r.c;
   r.t2 = r.d - r.c; r.u2 = fma(-3.0, r.c, r.d);
-  r.s0 = fma(13.0 * r.t0, r.t0, fma(3.0 * r.u0, r.u0, eps12));
-  r.s1 = fma(13.0 * r.t1, r.t1, fma(3.0 * r.u1, r.u1, eps12));
-  r.s2 = fma(13.0 * r.t2, r.t2, fma(3.0 * r.u2, r.u2, eps12));
+  r.s0 = fma((13.0 * kWc0) * r.t0, r.t0, fma((3.0 * kWc0) * r.u0, r.u0, e12c[0]));
+  r.s1 = fma((13.0 * kWc1) * r.t1, r.t1, fma((3.0 * kWc1) * r.u1, r.u1, e12c[1]));
+  r.s2 = fma((13.0 * kWc2) * r.t2, r.t2, fma((3.0 * kWc2) * r.u2, r.u2, e12c[2]));
   r.p12 = r.s1 * r.s2; r.p02 = r.s0 * r.s2; r.p01 = r.s0 * r.s1;
-  r.w0 = (0.1 * r.p12) * r.p12; r.w1 = (0.6 * r.p02) * r.p02; r.w2 = (0.3 * r.p01) * r.p01;
-  r.q0 = fma(5.0 / 6.0, r.b, (-1.0 / 3.0) * r.a);
-  r.q1 = fma(1.0 / 3.0, r.c, (1.0 / 6.0) * r.b);
-  r.q2 = fma(2.0 / 3.0, r.c, (-1.0 / 6.0) * r.d);
+  r.w0 = r.p12 * r.p12; r.w1 = r.p02 * r.p02; r.w2 = r.p01 * r.p01;
+  r.q0 = fma(2.0, r.u0, -r.b);
+  r.q1 = fma(2.0, r.c, r.b);
+  r.q2 = fma(4.0, r.c, -r.d);
   r.num = fma(r.w0, r.q0, fma(r.w1, r.q1, r.w2 * r.q2));
-  r.den = (r.w0 + r.w1) + r.w2;
+  r.den = 6.0 * ((r.w0 + r.w1) + r.w2);
 }
 
 // Reverse of one reconstruction: (nbar, dbar) for (num, den) -> fb[0..4] (added).
 __device__ __forceinline__ void w5_rev(const W5& r, double nbar, double dbar, double* fb) {
-  const double w0b = fma(nbar, r.q0, dbar), w1b = fma(nbar, r.q1, dbar), w2b = fma(nbar, r.q2, dbar);
+  const double d6 = 6.0 * dbar;
+  const double w0b = fma(nbar, r.q0, d6), w1b = fma(nbar, r.q1, d6), w2b = fma(nbar, r.q2, d6);
   const double q0b = nbar * r.w0, q1b = nbar * r.w1, q2b = nbar * r.w2;
-  const double p12b = w0b * 0.2 * r.p12, p02b = w1b * 1.2 * r.p02, p01b = w2b * 0.6 * r.p01;
+  const double p12b = 2.0 * w0b * r.p12, p02b = 2.0 * w1b * r.p02, p01b = 2.0 * w2b * r.p01;
   const double s0b = fma(p02b, r.s2, p01b * r.s1);
   const double s1b = fma(p12b, r.s2, p01b * r.s0);
   const double s2b = fma(p12b, r.s1, p02b * r.s0);
-  const double t0b = 26.0 * r.t0 * s0b, u0b = 6.0 * r.u0 * s0b;
-  const double t1b = 26.0 * r.t1 * s1b, u1b = 6.0 * r.u1 * s1b;
-  const double t2b = 26.0 * r.t2 * s2b, u2b = 6.0 * r.u2 * s2b;
-  const double ab = -t0b - u0b - (1.0 / 3.0) * q0b;
-  const double bb = t0b + 3.0 * u0b - t1b + u1b + (5.0 / 6.0) * q0b + (1.0 / 6.0) * q1b;
-  const double cb = t1b + u1b - t2b - 3.0 * u2b + (1.0 / 3.0) * q1b + (2.0 / 3.0) * q2b;
-  const double db = t2b + u2b - (1.0 / 6.0) * q2b;
+  const double t0b = (26.0 * kWc0) * r.t0 * s0b, u0b = fma((6.0 * kWc0) * r.u0, s0b, 2.0 * q0b);
+  const double t1b = (26.0 * kWc1) * r.t1 * s1b, u1b = (6.0 * kWc1) * r.u1 * s1b;
+  const double t2b = (26.0 * kWc2) * r.t2 * s2b, u2b = (6.0 * kWc2) * r.u2 * s2b;
+  const double ab = -t0b - u0b;
+  const double bb = t0b + 3.0 * u0b - t1b + u1b - q0b + q1b;
+  const double cb = t1b + u1b - t2b - 3.0 * u2b + 2.0 * q1b + 4.0 * q2b;
+  const double db = t2b + u2b - q2b;
   fb[0] -= ab;
   fb[1] += ab - bb;
   fb[2] += bb - cb;
@@ -67,16 +70,18 @@ __device__ __forceinline__ void w5_rev(const W5& r, double nbar, double dbar, do
   fb[4] += db;
 }
 
-// One field's F = F^+ + F^- (as weno5_pair) and its reverse: returns F and
-// adds Fb dF/dw to wpb[0..5], wmb[0..5].
+// One field's F = F^+ + F^- (as rec_nd with WENO5) and its reverse: returns F
+// and adds Fb dF/dw to wpb[0..5], wmb[0..5].
 __device__ __forceinline__ double weno5_pair_fwd_adj(const double* wp, const double* wm,
-                                                     double eps12, double Fb, double* wpb,
+                                                     const double* e12c, double Fb, double* wpb,
                                                      double* wmb) {
   W5 P, M;
-  w5_fwd(wp[0], wp[1], wp[2], wp[3], wp[4], eps12, P);
-  w5_fwd(wm[5], wm[4], wm[3], wm[2], wm[1], eps12, M);
-  const double F = (wp[2] + wm[3]) + fma(P.num, M.den, M.num * P.den) / (P.den * M.den);
-  const double idp = 1.0 / P.den, idm = 1.0 / M.den;
+  w5_fwd(wp[0], wp[1], wp[2], wp[3], wp[4], e12c, P);
+  w5_fwd(wm[5], wm[4], wm[3], wm[2], wm[1], e12c, M);
+  // both reciprocals from one division; F from them
+  const double rpm = 1.0 / (P.den * M.den);
+  const double idp = rpm * M.den, idm = rpm * P.den;
+  const double F = (wp[2] + wm[3]) + fma(P.num, idp, M.num * idm);
   double fb[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
   w5_rev(P, Fb * idp, -Fb * P.num * idp * idp, fb);
 #pragma unroll
@@ -173,7 +178,8 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
       Rb = fma(Yb[s], p.r[s], Rb);
       cvb = fma(Yb[s], cps[s] - p.r[s], cvb);
     }
-    const double Gam = Rb / cvb;
+    const double rRc = 1.0 / (Rb * cvb);
+    const double Gam = Rb * Rb * rRc;
     const double hq2 = 0.5 * q2;
     double phi[NS], c2 = 0.0;
 #pragma unroll
@@ -190,10 +196,11 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
       cr = QF(L::C, 1);
       c2 = 0.5 * (cl * cl + cr * cr);
     }
-    const double c = sqrt(c2);
-    const double ic2 = 1.0 / c2;
+    const double rsc = rsqrt(c2);
+    const double c = c2 * rsc;
+    const double ic2 = rsc * rsc;
     const double hic2 = 0.5 * ic2;
-    const double iGam = cvb / Rb;
+    const double iGam = cvb * cvb * rRc;
     const double un = ub[D];
     const double phiN = phi[NS - 1];
     double gm[DIM], dphi[NS > 1 ? NS - 1 : 1], gs[NS > 1 ? NS - 1 : 1];
@@ -226,6 +233,7 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
       gUh[m] = g;
     }
     const double eps12 = 12.0 * p.weno_eps;
+    const double e12c[3] = {eps12 * kWc0, eps12 * kWc1, eps12 * kWc2};
     const double chc = c * hic2;
     const double ha_m = 0.5 * am, ha_p = 0.5 * ap, ha0 = 0.5 * a0;
     const double hlmn_m = 0.5 * (-Gam * un - c) * hic2, hlmn_p = 0.5 * (-Gam * un + c) * hic2;
@@ -254,12 +262,14 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
 #pragma unroll
     for (int m = 0; m < 6; ++m) { rhob[m] = 0.0; pb[m] = 0.0; hunb[m] = 0.0; gUhb[m] = 0.0; mnb[m] = 0.0; }
     double hamb = 0.0, hapb = 0.0, ha0b = 0.0, chcb = 0.0, Gamb = 0.0, hic2b = 0.0, ic2b = 0.0;
+#pragma unroll
     for (int fld = 0; fld < 3; ++fld) {
       const double ha = fld == 0 ? ha_m : (fld == 1 ? ha_p : ha0);
       const double hl = fld == 0 ? hlmn_m : (fld == 1 ? hlmn_p : hlmn_e);
       const double lE = fld == 2 ? lE_e : lE_a;
       const double Fb = fld == 0 ? Fmb : (fld == 1 ? Fpb : Feb);
-      double LUv[6], nUv[6];
+      const double schc = fld == 0 ? -chc : chc;
+      double LUv[6], nUv[6], pqr[6];
 #pragma unroll
       for (int m = 0; m < 6; ++m) {
         double LU, nU = 0.0;
@@ -267,38 +277,42 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
           LU = fma(-2.0, gUh[m], rho_m[m]);
         } else {
           nU = fma(-un, rho_m[m], QF(L::U + 1 + D, m - 2));
-          LU = fma(fld == 0 ? -chc : chc, nU, gUh[m]);
+          LU = fma(schc, nU, gUh[m]);
         }
         LUv[m] = LU;
         nUv[m] = nU;
-        const double pq = p_m[m] * fma(hun[m], lE, hl);
+        pqr[m] = fma(hun[m], lE, hl);
+        const double pq = p_m[m] * pqr[m];
         wp[m] = fma(hun[m] + ha, LU, pq);
         wm[m] = fma(hun[m] - ha, LU, pq);
       }
       double wpb[6] = {0, 0, 0, 0, 0, 0}, wmb[6] = {0, 0, 0, 0, 0, 0};
-      const double F = weno5_pair_fwd_adj(wp, wm, eps12, Fb, wpb, wmb);
+      const double F = weno5_pair_fwd_adj(wp, wm, e12c, Fb, wpb, wmb);
       if (fld == 0) Fm = F; else if (fld == 1) Fp = F; else Fe = F;
       double hab = 0.0, hlb = 0.0, lEb = 0.0;
 #pragma unroll
       for (int m = 0; m < 6; ++m) {
-        const double LUb = wpb[m] * (hun[m] + ha) + wmb[m] * (hun[m] - ha);
-        const double pqb = wpb[m] + wmb[m];
-        hunb[m] += pqb * LUv[m] + pqb * p_m[m] * lE;
-        hab += (wpb[m] - wmb[m]) * LUv[m];
-        pb[m] += pqb * fma(hun[m], lE, hl);
-        lEb += pqb * p_m[m] * hun[m];
-        hlb += pqb * p_m[m];
+        // w+- = (hun +- ha) LU + p pqr: with s = wb+ + wb-, d = wb+ - wb-,
+        // LUb = hun s + ha d, hunb += s (LU + p lE), hab += d LU, pb += s pqr,
+        // and (lE, hl) take s p (hun, 1)
+        const double sb = wpb[m] + wmb[m], db = wpb[m] - wmb[m];
+        const double LUb = fma(hun[m], sb, ha * db);
+        hunb[m] = fma(sb, fma(p_m[m], lE, LUv[m]), hunb[m]);
+        hab = fma(db, LUv[m], hab);
+        pb[m] = fma(sb, pqr[m], pb[m]);
+        const double sp = sb * p_m[m];
+        lEb = fma(sp, hun[m], lEb);
+        hlb += sp;
         if (fld == 2) {
           rhob[m] += LUb;
-          gUhb[m] -= 2.0 * LUb;
+          gUhb[m] = fma(-2.0, LUb, gUhb[m]);
         } else {
-          const double sgn = fld == 0 ? -1.0 : 1.0;
           gUhb[m] += LUb;
-          chcb += sgn * LUb * nUv[m];
-          const double nUb = sgn * chc * LUb;
+          chcb = fma(fld == 0 ? -LUb : LUb, nUv[m], chcb);
+          const double nUb = schc * LUb;
           mnb[m] += nUb;
-          unb -= nUb * rho_m[m];
-          rhob[m] -= nUb * un;
+          unb = fma(-nUb, rho_m[m], unb);
+          rhob[m] = fma(-nUb, un, rhob[m]);
         }
       }
       if (fld == 2) {
@@ -346,7 +360,7 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
         wm[m] = (hun[m] - ha0) * LUv[m];
       }
       double wpb[6] = {0, 0, 0, 0, 0, 0}, wmb[6] = {0, 0, 0, 0, 0, 0};
-      const double Fk = weno5_pair_fwd_adj(wp, wm, eps12, Fb, wpb, wmb);
+      const double Fk = weno5_pair_fwd_adj(wp, wm, e12c, Fb, wpb, wmb);
       ubb[a] += Fk * Gb[IE];
 #pragma unroll
       for (int m = 0; m < 6; ++m) {
@@ -370,7 +384,7 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
         wm[m] = (hun[m] - ha0) * LUv[m];
       }
       double wpb[6] = {0, 0, 0, 0, 0, 0}, wmb[6] = {0, 0, 0, 0, 0, 0};
-      const double Fk = weno5_pair_fwd_adj(wp, wm, eps12, Fb, wpb, wmb);
+      const double Fk = weno5_pair_fwd_adj(wp, wm, e12c, Fb, wpb, wmb);
       dphib[s] = -iGam * Fk * Gb[IE];
       iGamb -= dphi[s] * Fk * Gb[IE];
 #pragma unroll
@@ -448,8 +462,9 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
     // Roe state
     ic2b += 0.5 * hic2b;
     c2b -= ic2b * ic2 * ic2;
-    double cvbb = iGamb / Rb, Rbb = -iGamb * cvb / (Rb * Rb);
-    c2b += cb * 0.5 / c;
+    const double iRb = cvb * rRc, icv = Rb * rRc;  // 1/R, 1/c_v
+    double cvbb = iGamb * iRb, Rbb = -iGamb * iGam * iRb;
+    c2b += cb * 0.5 * rsc;
     ubb[D] += unb;
     double Tbb = 0.0, q2b = 0.0;
     if (fallback) {
@@ -475,8 +490,8 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
       Tbb += esb * (cps[s] - p.r[s]);
     }
     q2b += 0.5 * hq2b;
-    Rbb += Gamb / cvb;
-    cvbb -= Gamb * Gam / cvb;
+    Rbb += Gamb * icv;
+    cvbb -= Gamb * Gam * icv;
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
       Ybb[s] += Rbb * p.r[s] + cvbb * (cps[s] - p.r[s]);
@@ -515,13 +530,14 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
   if (p.viscous) {
     const double wi = 1.0 / 16.0;
     const double wd = p.inv_dx[D] * (1.0 / 12.0);
-    // face interpolation / normal derivative coefficients for cells -1..2
-    const double ci[4] = {-wi, 9.0 * wi, 9.0 * wi, -wi};
-    const double cd[4] = {wd, -15.0 * wd, 15.0 * wd, -wd};
 #define FI(field) ((9.0 * (QF(field, 0) + QF(field, 1)) - (QF(field, -1) + QF(field, 2))) * wi)
 #define FD(field) ((15.0 * (QF(field, 1) - QF(field, 0)) - (QF(field, 2) - QF(field, -1))) * wd)
-#define BI(field, val) { const double v_ = (val); for (int m_ = 0; m_ < 4; ++m_) QB(field, m_ - 1, ci[m_] * v_); }
-#define BD(field, val) { const double v_ = (val); for (int m_ = 0; m_ < 4; ++m_) QB(field, m_ - 1, cd[m_] * v_); }
+// adjoints of FI / FD scattered to cells -1..2 (the stencils are symmetric
+// up to sign, so two products serve the four cells)
+#define BI(field, val) { const double a_ = wi * (val), b_ = 9.0 * a_; \
+    QB(field, -1, -a_); QB(field, 0, b_); QB(field, 1, b_); QB(field, 2, -a_); }
+#define BD(field, val) { const double a_ = wd * (val), b_ = 15.0 * a_; \
+    QB(field, -1, a_); QB(field, 0, -b_); QB(field, 1, b_); QB(field, 2, -a_); }
     const double mu = FI(L::MU), ka = FI(L::KA), Df = FI(L::DF), rf = FI(L::U), Tf = FI(L::T);
     double uf[DIM], gr[DIM][DIM];
 #pragma unroll
@@ -651,7 +667,7 @@ __device__ __forceinline__ void prim_adj_cell(const Params& p, long long t,
   double u[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) u[v] = q[(L::U + v) * PC];
-  const double rho = u[0], irho = 1.0 / rho, E = u[DIM + 1];
+  const double rho = u[0], E = u[DIM + 1];
   double vel[DIM];
 #pragma unroll
   for (int a = 0; a < DIM; ++a) vel[a] = q[(L::UN + a) * PC];
@@ -670,6 +686,10 @@ __device__ __forceinline__ void prim_adj_cell(const Params& p, long long t,
     dcpm = fma(Y[s], dcp_s(p, s, T), dcpm);
   }
   const double cvm = cpm - Rm, RT = Rm * T;
+  // reciprocals: 1/rho and 1/c_p from one division, 1/c_v from another
+  const double irc = 1.0 / (rho * cpm);
+  const double irho = cpm * irc, icpm = rho * irc;
+  const double icvm = 1.0 / cvm;
   // adjoint accumulators
   double ub[NV], Yb[NS], velb[DIM];
 #pragma unroll
@@ -684,9 +704,9 @@ __device__ __forceinline__ void prim_adj_cell(const Params& p, long long t,
     const double mub = qb[L::MU * PC], kab = qb[L::KA * PC], Db = qb[L::DF * PC];
     // D = ka / (Le rho cp)
     const double ka = q[L::KA * PC], Dd = q[L::DF * PC];
-    double kabar = kab + Db * p.inv_lewis / (rho * cpm);
-    rhob -= Db * Dd / rho;
-    cpmb -= Db * Dd / cpm;
+    double kabar = fma(Db * p.inv_lewis, irc, kab);
+    rhob -= Db * Dd * irho;
+    cpmb -= Db * Dd * icpm;
     // Wilke mixtures, recomputed
     const double lnT = log(T);
     double smu[NS], ska[NS], ismu[NS], iska[NS], X[NS], xs = 0.0, dlm[NS], dlk[NS];
@@ -698,10 +718,24 @@ __device__ __forceinline__ void prim_adj_cell(const Params& p, long long t,
       dlk[s] = fma(fma(3.0 * p.lnka[s][3], lnT, 2.0 * p.lnka[s][2]), lnT, p.lnka[s][1]);
       smu[s] = exp(0.5 * lm);
       ska[s] = exp(0.5 * lk);
-      ismu[s] = 1.0 / smu[s];
-      iska[s] = 1.0 / ska[s];
       X[s] = Y[s] * p.invW[s];
       xs += X[s];
+    }
+    // the 2N reciprocals from one division (running products, as in k_prim)
+    {
+      double pre[2 * NS];
+      pre[0] = smu[0];
+#pragma unroll
+      for (int k = 1; k < 2 * NS; ++k) pre[k] = pre[k - 1] * (k < NS ? smu[k] : ska[k - NS]);
+      double inv = 1.0 / pre[2 * NS - 1];
+#pragma unroll
+      for (int k = 2 * NS - 1; k > 0; --k) {
+        const double v = k < NS ? smu[k] : ska[k - NS];
+        const double r = inv * pre[k - 1];
+        if (k < NS) ismu[k] = r; else iska[k - NS] = r;
+        inv *= v;
+      }
+      ismu[0] = inv;
     }
     const double ixs = 1.0 / xs;
 #pragma unroll
@@ -712,33 +746,37 @@ __device__ __forceinline__ void prim_adj_cell(const Params& p, long long t,
     for (int s = 0; s < NS; ++s) { Xb[s] = 0.0; smub[s] = 0.0; skab[s] = 0.0; ismub[s] = 0.0; iskab[s] = 0.0; }
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-      double dm = 0.0, dk = 0.0;
+      // forward: b_t = 1 + sqrt(a_s / a_t) B_st, d_s = sum_t X_t A_st b_t^2,
+      // term_s = X_s a_s / d_s (a = mu or kappa); the b_t and X_t A_st stay
+      // in registers for the reverse
+      double bm[NS], bk[NS], xa[NS], dm = 0.0, dk = 0.0;
 #pragma unroll
       for (int tt = 0; tt < NS; ++tt) {
-        const double bm = fma(smu[s] * ismu[tt], p.wB[s][tt], 1.0);
-        const double bk = fma(ska[s] * iska[tt], p.wB[s][tt], 1.0);
-        const double xa = X[tt] * p.wA[s][tt];
-        dm = fma(xa, bm * bm, dm);
-        dk = fma(xa, bk * bk, dk);
+        bm[tt] = fma(smu[s] * ismu[tt], p.wB[s][tt], 1.0);
+        bk[tt] = fma(ska[s] * iska[tt], p.wB[s][tt], 1.0);
+        xa[tt] = X[tt] * p.wA[s][tt];
+        dm = fma(xa[tt], bm[tt] * bm[tt], dm);
+        dk = fma(xa[tt], bk[tt] * bk[tt], dk);
       }
-      // term_s = X_s smu_s^2 / dm_s
-      const double idm = 1.0 / dm, idk = 1.0 / dk;
-      const double tm = X[s] * smu[s] * smu[s] * idm, tk = X[s] * ska[s] * ska[s] * idk;
-      Xb[s] += mtot * smu[s] * smu[s] * idm + ktot * ska[s] * ska[s] * idk;
+      const double rd = 1.0 / (dm * dk);
+      const double idm = rd * dk, idk = rd * dm;
+      const double sm2 = smu[s] * smu[s], sk2 = ska[s] * ska[s];
+      const double tm = X[s] * sm2 * idm, tk = X[s] * sk2 * idk;
+      Xb[s] += fma(mtot * sm2, idm, ktot * sk2 * idk);
       smub[s] += mtot * 2.0 * X[s] * smu[s] * idm;
       skab[s] += ktot * 2.0 * X[s] * ska[s] * idk;
       const double dmb = -mtot * tm * idm, dkb = -ktot * tk * idk;
+      const double dmb2 = 2.0 * dmb, dkb2 = 2.0 * dkb;
 #pragma unroll
       for (int tt = 0; tt < NS; ++tt) {
-        const double bm = fma(smu[s] * ismu[tt], p.wB[s][tt], 1.0);
-        const double bk = fma(ska[s] * iska[tt], p.wB[s][tt], 1.0);
-        Xb[tt] += p.wA[s][tt] * (dmb * bm * bm + dkb * bk * bk);
-        const double bmb = dmb * X[tt] * p.wA[s][tt] * 2.0 * bm;
-        const double bkb = dkb * X[tt] * p.wA[s][tt] * 2.0 * bk;
-        smub[s] += bmb * ismu[tt] * p.wB[s][tt];
-        ismub[tt] += bmb * smu[s] * p.wB[s][tt];
-        skab[s] += bkb * iska[tt] * p.wB[s][tt];
-        iskab[tt] += bkb * ska[s] * p.wB[s][tt];
+        Xb[tt] = fma(p.wA[s][tt], fma(dmb, bm[tt] * bm[tt], dkb * (bk[tt] * bk[tt])), Xb[tt]);
+        // adjoints of b_t, times B_st
+        const double bmw = dmb2 * xa[tt] * bm[tt] * p.wB[s][tt];
+        const double bkw = dkb2 * xa[tt] * bk[tt] * p.wB[s][tt];
+        smub[s] = fma(bmw, ismu[tt], smub[s]);
+        ismub[tt] = fma(bmw, smu[s], ismub[tt]);
+        skab[s] = fma(bkw, iska[tt], skab[s]);
+        iskab[tt] = fma(bkw, ska[s], iskab[tt]);
       }
     }
     double lnTb = 0.0, xdot = 0.0;
@@ -758,12 +796,12 @@ __device__ __forceinline__ void prim_adj_cell(const Params& p, long long t,
   Eb += Hb * irho;
   prb += Hb * irho;
   irhob += Hb * (E + pr);
-  rhob += qb[L::SR * PC] * 0.5 / sqrt(rho);
+  rhob += qb[L::SR * PC] * 0.5 * q[L::SR * PC] * irho;   // d sqrt(rho) = 1/(2 sqrt(rho))
   // c = sqrt(cp R T / cv)
   const double c2b = cb * 0.5 / c;
-  cpmb += c2b * (-RT * Rm / (cvm * cvm));
-  Rmb += c2b * cpm * RT / (cvm * cvm);
-  double RTb = c2b * cpm / cvm;
+  cpmb += c2b * (-RT * Rm * (icvm * icvm));
+  Rmb += c2b * cpm * RT * (icvm * icvm);
+  double RTb = c2b * cpm * icvm;
   // p = rho R T
   rhob += prb * RT;
   RTb += prb * rho;
@@ -774,9 +812,9 @@ __device__ __forceinline__ void prim_adj_cell(const Params& p, long long t,
 #pragma unroll
   for (int s = 0; s < NS; ++s) Yb[s] += cpmb * cps[s] + Rmb * p.r[s];
   // Newton temperature through the implicit-function theorem
-  const double eb = Tb / cvm;
+  const double eb = Tb * icvm;
 #pragma unroll
-  for (int s = 0; s < NS; ++s) Yb[s] -= Tb * es[s] / cvm;
+  for (int s = 0; s < NS; ++s) Yb[s] -= eb * es[s];
   // Y_N = 1 - sum_{s<N} Y_s
 #pragma unroll
   for (int s = 0; s < NS - 1; ++s) Yb[s] -= Yb[NS - 1];
