@@ -803,14 +803,17 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
     {
       double wp[SW], wm[SW];
       RecND ndm, ndp, nde;
+      // normal momentum relative to the face velocity, shared by u -+ c
+      double nUv[SW];
+#pragma unroll
+      for (int m = 0; m < SW; ++m) nUv[m] = fma(-un, rho_m[m], QF(L::U + 1 + D, m - SO));
       // u - c: l.U = (g.U - c (m_n - u_n rho)) / (2c^2)
       {
         const double hlmn = 0.5 * (-Gam * un - c) * hic2, lE = Gam * hic2;
         const double ha = 0.5 * am;
 #pragma unroll
         for (int m = 0; m < SW; ++m) {
-          const double nU = fma(-un, rho_m[m], QF(L::U + 1 + D, m - SO));
-          const double LU = fma(-chc, nU, gUh[m]);
+          const double LU = fma(-chc, nUv[m], gUh[m]);
           const double pq = p_m[m] * fma(hun[m], lE, hlmn);
           wp[m] = fma(hun[m] + ha, LU, pq);
           wm[m] = fma(hun[m] - ha, LU, pq);
@@ -823,8 +826,7 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
         const double ha = 0.5 * ap;
 #pragma unroll
         for (int m = 0; m < SW; ++m) {
-          const double nU = fma(-un, rho_m[m], QF(L::U + 1 + D, m - SO));
-          const double LU = fma(chc, nU, gUh[m]);
+          const double LU = fma(chc, nUv[m], gUh[m]);
           const double pq = p_m[m] * fma(hun[m], lE, hlmn);
           wp[m] = fma(hun[m] + ha, LU, pq);
           wm[m] = fma(hun[m] - ha, LU, pq);
