@@ -9,6 +9,17 @@
  * mixture-averaged transport (Eq. 22, Eq. 29), viscous and species-diffusion
  * fluxes (Eq. 3-6), the conservative difference (Eq. 13) and SSP-RK3 (Eq. 16).
  *
+ * Also: WENO-CU6 and WENO7-JS reconstructions (refs. 34, 36), the
+ * positivity-preserving flux blend (Eq. 17-20) and the mixture-averaged
+ * diffusion of Eq. 25-26.
+ *
+ * Parity unpinned vs the paper: the basis of the degenerate u-eigenspace
+ * (xfo_eigen) and the multicomponent Roe average of the face state; the
+ * paper's choices are in references it only cites. Both are pinned for
+ * self-consistency only (L.R = I, A r = lambda r, the exact single-gas Roe
+ * property), so results that depend on them match the paper's method up to
+ * that choice.
+ *
  * Only tests/, the smoke check and the CPU-baseline leg of the benchmark use
  * this library; the product path never links or calls it. It shares no code
  * with the CUDA path.
