@@ -501,7 +501,7 @@ __device__ __forceinline__ void weno5_nd(double f0, double f1, double f2, double
   const double p12 = s1 * s2, p02 = s0 * s2, p01 = s0 * s1;
   const double w0 = p12 * p12, w1 = p02 * p02, w2 = p01 * p01;
   // 6 (q_k - f2): 5b - 2a = 2 u0 - b, 2c + b, 4c - d; the factor 6 goes to
-  // the denominator of the field pair (kRecScale)
+  // the denominator of the field pair (rec_scale)
   const double q0 = fma(2.0, u0, -b);
   const double q1 = fma(2.0, c, b);
   const double q2 = fma(4.0, c, -d);
@@ -551,10 +551,11 @@ __device__ __forceinline__ void cu6_nd(double f0, double f1, double f2, double f
   const double tau = b6 - (b0 + b2 + 4.0 * b1) * (1.0 / 6.0);   // 12 tau
   const double s0 = b0 + e12, s1 = b1 + e12, s2 = b2 + e12, s3 = b6 + e12;
   const double p01 = s0 * s1, p23 = s2 * s3;
-  const double w0 = 0.05 * fma(20.0, s0, tau) * (s1 * p23);
-  const double w1 = 0.45 * fma(20.0, s1, tau) * (s0 * p23);
-  const double w2 = 0.45 * fma(20.0, s2, tau) * (p01 * s3);
-  const double w3 = 0.05 * fma(20.0, s3, tau) * (p01 * s2);
+  const double t05 = 0.05 * tau, t45 = 0.45 * tau;   // d_k tau
+  const double w0 = fma(0.05 * 20.0, s0, t05) * (s1 * p23);
+  const double w1 = fma(0.45 * 20.0, s1, t45) * (s0 * p23);
+  const double w2 = fma(0.45 * 20.0, s2, t45) * (p01 * s3);
+  const double w3 = fma(0.05 * 20.0, s3, t05) * (p01 * s2);
   // 6 (q_k - f2), as in weno5_nd; q_3: 6c - 5d + 2e
   const double q0 = fma(2.0, u0, -b);
   const double q1 = fma(2.0, c, b);
@@ -575,15 +576,18 @@ __device__ __forceinline__ void cu6_nd(double f0, double f1, double f2, double f
 // scaling s_k by c_k = (35/d_k)^(1/2) makes prod_{j!=k} s_j^2 carry d_k.
 constexpr double kW7c0 = 5.9160797830996161, kW7c1 = 1.707825127659933,
                  kW7c2 = 1.3944333775567925, kW7c3 = 2.9580398915498081;
-__device__ __forceinline__ double w7_q0(double y0, double y1, double y2) {
+// z2 = 191.02539981185325 y2^2, the last square of both forms (shared by the
+// two indicators that end on the same difference)
+constexpr double kW7D3 = 191.02539981185325;
+__device__ __forceinline__ double w7_q0(double y0, double y1, double y2, double z2) {
   const double A = fma(1.6946983546617915, y2, fma(-2.5484460694698354, y1, y0));
   const double B = fma(-1.4896519285042333, y2, y1);
-  return fma(547.0 * A, A, fma(155.46617915904935 * B, B, 191.02539981185325 * y2 * y2));
+  return fma(547.0 * A, A, fma(155.46617915904935 * B, B, z2));
 }
-__device__ __forceinline__ double w7_q1(double y0, double y1, double y2) {
+__device__ __forceinline__ double w7_q1(double y0, double y1, double y2, double z2) {
   const double A = fma(0.92509363295880154, y2, fma(-2.0749063670411987, y1, y0));
   const double B = fma(-0.6326434619002822, y2, y1);
-  return fma(267.0 * A, A, fma(318.50187265917606 * B, B, 191.02539981185325 * y2 * y2));
+  return fma(267.0 * A, A, fma(318.50187265917606 * B, B, z2));
 }
 
 // ec[k] = 240 eps c_k
@@ -592,10 +596,11 @@ __device__ __forceinline__ void weno7_nd(double f0, double f1, double f2, double
                                          double& den) {
   const double x0 = f1 - f0, x1 = f2 - f1, x2 = f3 - f2, x3 = f4 - f3, x4 = f5 - f4,
                x5 = f6 - f5;
-  const double s0 = fma(kW7c0, w7_q0(x0, x1, x2), ec[0]);
-  const double s1 = fma(kW7c1, w7_q1(x1, x2, x3), ec[1]);
-  const double s2 = fma(kW7c2, w7_q1(x4, x3, x2), ec[2]);
-  const double s3 = fma(kW7c3, w7_q0(x5, x4, x3), ec[3]);
+  const double z2 = kW7D3 * x2 * x2, z3 = kW7D3 * x3 * x3;
+  const double s0 = fma(kW7c0, w7_q0(x0, x1, x2, z2), ec[0]);
+  const double s1 = fma(kW7c1, w7_q1(x1, x2, x3, z3), ec[1]);
+  const double s2 = fma(kW7c2, w7_q1(x4, x3, x2, z2), ec[2]);
+  const double s3 = fma(kW7c3, w7_q0(x5, x4, x3, z3), ec[3]);
   const double p01 = s0 * s1, p23 = s2 * s3;
   const double r0 = s1 * p23, r1 = s0 * p23, r2 = p01 * s3, r3 = p01 * s2;
   const double w0 = r0 * r0, w1 = r1 * r1, w2 = r2 * r2, w3 = r3 * r3;
@@ -633,16 +638,22 @@ __device__ __forceinline__ RecND rec_nd(const double* wp, const double* wm, cons
     weno5_nd(wm[5], wm[4], wm[3], wm[2], wm[1], e4, nm, dm);
     b = wp[2] + wm[3];
   }
-  // the WENO5 and CU6 numerators carry a factor 6 (weno5_nd, cu6_nd)
-  constexpr double kRecScale = REC == 7 ? 1.0 : 6.0;
-  return RecND{b, fma(np, dm, nm * dp), kRecScale * (dp * dm)};
+  return RecND{b, fma(np, dm, nm * dp), dp * dm};
 }
-__device__ __forceinline__ double rec_div1(const RecND& x) { return x.b + x.n / x.d; }
+// the WENO5 and CU6 numerators carry a factor 6 (weno5_nd, cu6_nd), taken
+// out at the division
+template <int REC>
+__host__ __device__ constexpr double rec_scale() { return REC == 7 ? 1.0 : 6.0; }
+template <int REC>
+__device__ __forceinline__ double rec_div1(const RecND& x) {
+  return x.b + x.n / (rec_scale<REC>() * x.d);
+}
 // two fields with one division: 1/d_x = d_y / (d_x d_y). The weights are
 // scaled by the indicators' products (section above), so d_x d_y stays far
 // inside the double range for any finite stencil data the solver meets.
+template <int REC>
 __device__ __forceinline__ void rec_div2(const RecND& x, const RecND& y, double& fx, double& fy) {
-  const double r = 1.0 / (x.d * y.d);
+  const double r = 1.0 / ((rec_scale<REC>() * x.d) * y.d);
   fx = fma(x.n, r * y.d, x.b);
   fy = fma(y.n, r * x.d, y.b);
 }
@@ -833,7 +844,7 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
         }
         ndp = rec_nd<REC>(wp, wm, e12c);
       }
-      rec_div2(ndm, ndp, Fk_m, Fk_p);
+      rec_div2<REC>(ndm, ndp, Fk_m, Fk_p);
       // entropy: l = e_rho - g / c^2
       {
         const double hlmn = 0.5 * Gam * un * ic2, lE = -Gam * ic2;
@@ -851,8 +862,8 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
 #pragma unroll
       for (int m = 0; m < SW; ++m) { hp0[m] = hun[m] + ha0; hm0[m] = hun[m] - ha0; }
       // the entropy field shares its division with the first passive field
-      if constexpr (NPASS > 0) rec_div2(nde, passive_nd(0), Fk_e, Fk_first);
-      else Fk_e = rec_div1(nde);
+      if constexpr (NPASS > 0) rec_div2<REC>(nde, passive_nd(0), Fk_e, Fk_first);
+      else Fk_e = rec_div1<REC>(nde);
     }
     // back-projection of the three dense right columns (Eq. 15)
     {
@@ -884,11 +895,11 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
       const RecND x = passive_nd(k);
       if (k + 1 < NPASS) {
         double fx, fy;
-        rec_div2(x, passive_nd(k + 1), fx, fy);
+        rec_div2<REC>(x, passive_nd(k + 1), fx, fy);
         passive_add(k, fx);
         passive_add(k + 1, fy);
       } else {
-        passive_add(k, rec_div1(x));
+        passive_add(k, rec_div1<REC>(x));
       }
     }
   }
