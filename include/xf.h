@@ -192,7 +192,9 @@ xf_status xf_rhs_adjoint(xf_handle *h, const double *U, const double *dUdt_bar,
 /* Reverse of one fixed-dt SSP-RK3 step (Eq. 16) taken from the handle's
  * current state U^n: on entry U_bar holds dJ/dU^{n+1}, on return dJ/dU^n.
  * Recomputes the two intermediate stage states itself; dt > 0 (the adjoint
- * assumes the frozen time step). */
+ * assumes the frozen time step). On its first call it allocates two more
+ * per-cell field blocks (the fields of U^n and U1, kept between the forward
+ * and reverse passes); the temperature warm start is left at that of U2. */
 xf_status xf_step_rk3_adjoint(xf_handle *h, double dt, double *U_bar, void *stream);
 /* Mixing measure J = sum_cells Y_s (1 - Y_s) dV of species `species` (0-based)
  * for the state U: J_dev (device, one double) = J, U_bar = dJ/dU (overwritten). */

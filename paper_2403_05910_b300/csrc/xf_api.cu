@@ -197,6 +197,9 @@ struct xf_handle {
   double* B1 = nullptr;
   double* B2 = nullptr;
   double* part = nullptr;
+  // per-cell fields of U^n and U1 kept by xf_step_rk3_adjoint (allocated on
+  // its first call), so its reverse does not recompute them
+  double* QS[2] = {nullptr, nullptr};
   // per-kernel event timing (xf_profile_enable / xf_profile_read)
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -399,13 +402,16 @@ xf_status ensure_adjoint_buffers(xf_handle* h) {
   return XF_OK;
 }
 
-// Ubar += scale (dL/dU)^T Rbar at the state U.
+// Ubar += scale (dL/dU)^T Rbar at the state U. With fields_ready the block
+// h->Q already holds the per-cell fields of U.
 xf_status rhs_adjoint_impl(xf_handle* h, const double* U, const double* Rbar, double scale,
-                           double* Ubar, cudaStream_t s) {
+                           double* Ubar, cudaStream_t s, bool fields_ready = false) {
   xf_status st = ensure_adjoint_buffers(h);
   if (st != XF_OK) return st;
-  st = cell_fields(h, U, s);
-  if (st != XF_OK) return st;
+  if (!fields_ready) {
+    st = cell_fields(h, U, s);
+    if (st != XF_OK) return st;
+  }
   const xf::Params& p = h->p;
   XF_CUDA(cudaMemsetAsync(h->Qb, 0, sizeof(double) * (size_t)h->tab.nq * p.pcells, s));
   for (int d = 0; d < p.dim; ++d)
@@ -526,6 +532,8 @@ void xf_destroy(xf_handle* h) {
   cudaFree(h->red);
   cudaFree(h->flags);
   cudaFree(h->Qb);
+  cudaFree(h->QS[0]);
+  cudaFree(h->QS[1]);
   cudaFree(h->A1);
   cudaFree(h->A2);
   cudaFree(h->B1);
@@ -664,24 +672,45 @@ xf_status xf_step_rk3_adjoint(xf_handle* h, double dt, double* U_bar, void* stre
   xf_status st = ensure_adjoint_buffers(h);
   if (st != XF_OK) return st;
   const xf::Params& p = h->p;
+  const size_t qbytes = sizeof(double) * nq_of(h->tab, p) * p.pcells;
+  for (int k = 0; k < 2; ++k) {
+    if (!h->QS[k] && cudaMalloc((void**)&h->QS[k], qbytes) != cudaSuccess) {
+      cudaGetLastError();
+      h->QS[k] = nullptr;
+      g_err = "step adjoint buffers: cudaMalloc failed";
+      return XF_ERR_OOM;
+    }
+  }
+  // the forward passes write U^n's and U1's per-cell fields into QS[0], QS[1];
+  // h->Q is restored on every return
+  struct QGuard {
+    xf_handle* h;
+    double* q;
+    ~QGuard() { h->Q = q; }
+  } guard{h, h->Q};
   k_set_scalar<<<1, 1, 0, s>>>(h->dt, dt);
   // forward stage states U1 (A1) and U2 (A2) from U^n (h->U)
+  h->Q = h->QS[0];
   st = stage_fluxes(h, h->U, 0, s);
   if (st != XF_OK) return st;
   h->tab.update(p, h->G[0], h->G[1], h->G[2], h->U, h->U, h->A1, h->dt, 1, s);
+  h->Q = h->QS[1];
   st = stage_fluxes(h, h->A1, 0, s);
   if (st != XF_OK) return st;
   h->tab.update(p, h->G[0], h->G[1], h->G[2], h->U, h->A1, h->A2, h->dt, 2, s);
   // reverse of U3 = U/3 + 2/3 (U2 + dt L(U2)), U2 = 3/4 U + 1/4 (U1 + dt L(U1)),
   // U1 = U + dt L(U); a = Ubar(U3) on entry
   lincomb(h, 2.0 / 3.0, U_bar, 0.0, nullptr, 0.0, nullptr, h->B2, s);
+  h->Q = guard.q;
   st = rhs_adjoint_impl(h, h->A2, U_bar, 2.0 / 3.0 * dt, h->B2, s);
   if (st != XF_OK) return st;
   lincomb(h, 0.25, h->B2, 0.0, nullptr, 0.0, nullptr, h->B1, s);
-  st = rhs_adjoint_impl(h, h->A1, h->B2, 0.25 * dt, h->B1, s);
+  h->Q = h->QS[1];
+  st = rhs_adjoint_impl(h, h->A1, h->B2, 0.25 * dt, h->B1, s, true);
   if (st != XF_OK) return st;
   lincomb(h, 1.0 / 3.0, U_bar, 0.75, h->B2, 1.0, h->B1, U_bar, s);
-  st = rhs_adjoint_impl(h, h->U, h->B1, dt, U_bar, s);
+  h->Q = h->QS[0];
+  st = rhs_adjoint_impl(h, h->U, h->B1, dt, U_bar, s, true);
   if (st != XF_OK) return st;
   XF_CUDA(cudaGetLastError());
   return XF_OK;
