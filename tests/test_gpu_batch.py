@@ -139,3 +139,23 @@ def test_bounded_barrier_reports_timeout():
     # one arrival too many is expected: every block waits ~0.05 s, then reports
     assert barrier_probe(100_000_000, 1) & FLAG_TIMEOUT
     assert barrier_probe(2_000_000_000, 0) == 0   # the device is still usable
+
+
+def test_full_ensemble_is_bitwise_identical_to_single_grid_steps():
+    """The bench's ensemble itself (64 instances, 128x64 .. 768x384, seed 0):
+    one CFL step of the autotuned, graph-captured persistent form equals
+    stepping each instance alone, bit for bit."""
+    cs = cases.batch(0)
+    assert len(cs) == 64
+    ins = _inputs(cs)
+    b = _batch(cs, ins)
+    b.autotune(steps=1)
+    b.step(0.0)
+    got = _read(b, cs)
+    assert b.status() == 0
+    b.close()
+    for c, (U, T), (Ug, Tg) in zip(cs, ins, got):
+        Up, Tp, st = _plain(c, U, T, 1, 0.0)
+        assert st == 0
+        assert np.array_equal(Ug, Up), c.name
+        assert np.array_equal(Tg, Tp), c.name
