@@ -133,3 +133,20 @@ def test_weno7_needs_four_cells_per_axis():
     gpu_solver(case, weno=5).close()
     with pytest.raises(XFError):
         gpu_solver(case, weno=7)
+
+
+@pytest.mark.parametrize("weno", [5, 6, 7])
+def test_all_options_together(weno):
+    """Each reconstruction with the positivity blend and the mixture-averaged
+    diffusion at once (2D and 3D shock-bubble states): one step and ten."""
+    for case, steps, tol in ((cases.with_binary_diffusion(cases.config(4, n=(40, 20)), seed=5), 10, 1e-8),
+                             (cases.with_binary_diffusion(cases.config(2, n=(20, 12, 12)), seed=6), 1, 1e-11)):
+        kw = {"weno": weno, "positivity": True, "diffusion": 1}
+        o, U, T = _oracle(case, weno, positivity=True, diffusion=1)
+        U1, T1 = U.copy(), T.copy()
+        for _ in range(steps):
+            _, st = o.step(U1, T1, 0.0)
+            assert st == 0
+        Ug, _, stg, _ = gpu_steps(case, U, T, steps, **kw)
+        assert stg == 0
+        assert np.max(field_err(Ug, U1, case.dim)) <= tol, case.name

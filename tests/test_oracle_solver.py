@@ -96,11 +96,13 @@ def test_general_contact_pressure_error_is_small():
 
 # ----------------------------------------------------------- conservation --
 
-@pytest.mark.parametrize("weno", [5, 6, 7])
+@pytest.mark.parametrize("weno,diffusion", [(5, 0), (6, 0), (7, 0), (5, 1)])
 @pytest.mark.parametrize("dim,n", [(1, (40,)), (2, (24, 20)), (3, (10, 9, 8))])
-def test_discrete_conservation_periodic_viscous(dim, n, weno):
+def test_discrete_conservation_periodic_viscous(dim, n, weno, diffusion):
     c = cases.smooth_periodic(dim, n, 3, seed=11 + dim, amp=0.2, viscous=True)
-    o, U, T = _with_case(c, weno=weno)
+    if diffusion:
+        c = cases.with_binary_diffusion(c, seed=dim)
+    o, U, T = _with_case(c, weno=weno, diffusion=diffusion)
     tot0 = U.sum(axis=1)
     scale = np.abs(U).sum(axis=1)
     dt = o.dt(U, T)
@@ -327,9 +329,12 @@ def test_viscous_full_1d_against_spectral_flux_divergence(diffusion):
 
 # ------------------------------------------------------------- symmetry ---
 
-def test_axis_permutation_symmetry_3d():
+@pytest.mark.parametrize("weno,diffusion", [(5, 0), (6, 0), (7, 0), (5, 1)])
+def test_axis_permutation_symmetry_3d(weno, diffusion):
     c = cases.smooth_periodic(3, (8, 8, 8), 3, seed=21, amp=0.2, viscous=True)
-    o, U, T = _with_case(c)
+    if diffusion:
+        c = cases.with_binary_diffusion(c, seed=4)
+    o, U, T = _with_case(c, weno=weno, diffusion=diffusion)
     R, _, _ = o.rhs(U, T)
     # swap x and y: arrays are [v][z][y][x]; momentum rows 1 and 2 trade places
     perm = [0, 2, 1, 3, 4, 5, 6]
@@ -368,10 +373,12 @@ def test_reflection_symmetry_1d(weno, bc):
     assert np.max(np.abs(Rr - R) / scale) <= 1e-12
 
 
-@pytest.mark.parametrize("viscous", [False, True])
-def test_multi_d_reduces_to_1d(viscous):
+@pytest.mark.parametrize("viscous,weno,diffusion", [(False, 5, 0), (True, 5, 0), (True, 6, 0),
+                                                    (True, 7, 0), (True, 5, 1)])
+def test_multi_d_reduces_to_1d(viscous, weno, diffusion):
     rng = np.random.default_rng(22)
     sp = cases._draw_species(rng, np.array([0.028, 0.032, 0.131]))
+    sp.dbin_coef = cases.draw_binary_diffusion(np.random.default_rng(23), sp.W)
     n = 24
     x = cases._centres(n, 0.0, 1.0)
     rho = 1.0 + 0.3 * np.sin(2 * np.pi * x)
@@ -382,7 +389,7 @@ def test_multi_d_reduces_to_1d(viscous):
     c1 = cases.Case("r1", 1, (n, 1, 1), (0.0,) * 3, (1.0,) * 3, ((1, 1), (0, 0), (0, 0)),
                     sp, cases.R_U * 300 / 0.028, 1.0, 1.0, viscous, 0.5,
                     cases._pack(1, rho, [u], p, Y))
-    o1, U1, T1 = _with_case(c1)
+    o1, U1, T1 = _with_case(c1, weno=weno, diffusion=diffusion)
     R1, _, _ = o1.rhs(U1, T1)
     ny = 5
     tile = lambda a: np.tile(a, (ny, 1))
@@ -390,7 +397,7 @@ def test_multi_d_reduces_to_1d(viscous):
                         np.stack([tile(Y[s]) for s in range(3)]))
     c2 = cases.Case("r2", 2, (n, ny, 1), (0.0,) * 3, (1.0,) * 3, ((1, 1), (1, 1), (0, 0)),
                     sp, cases.R_U * 300 / 0.028, 1.0, 1.0, viscous, 0.5, prim2)
-    o2, U2, T2 = _with_case(c2)
+    o2, U2, T2 = _with_case(c2, weno=weno, diffusion=diffusion)
     R2, _, _ = o2.rhs(U2, T2)
     R2 = R2.reshape(c2.n_v, ny, n)
     rows = [0, 1, 3, 4, 5]  # rho, m_x, E, rhoY_1, rhoY_2 in the 2D layout
