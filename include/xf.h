@@ -119,8 +119,9 @@ typedef struct xf_thermo {
  * species, 1 for the mixture-averaged D_sm of Eq. 26 from the binary D_st of
  * Eq. 25 (xf_thermo.dbin_coef), with the mole fractions regularised as
  * X~_t = (max(X_t, 0) + 1e-12) / sum so that a pure species keeps a finite
- * D_sm. The batched form and the adjoint entry points support weno = 5 and
- * diffusion = 0 only (XF_ERR_ARG otherwise).
+ * D_sm. The adjoint entry points support weno = 5 and diffusion = 0 without
+ * the blend only (XF_ERR_ARG otherwise); the batched form supports every
+ * option, with one reconstruction (weno) shared by all its instances.
  * positivity switches the positivity-preserving flux blend of Eq. 17-20 inside
  * RK stages: F* = (1 - theta) F_LF + theta F_hat per face, with the local LF
  * flux of Eq. 19 (alpha = max(|u_d| + c) of the two cells) and the smallest
@@ -179,7 +180,7 @@ xf_status xf_compute_dt(xf_handle *h, double *dt_dev, void *stream);
  * receives the step used. No host synchronisation. */
 xf_status xf_step_rk3(xf_handle *h, double dt, double *dt_dev_out, void *stream);
 
-/* ---- Adjoint (vector-Jacobian products; SURVEY a11). All arrays are device
+/* ---- Adjoint (vector-Jacobian products). All arrays are device
  * arrays [n_v][cells]; results ACCUMULATE into the bar arrays (gradient
  * convention). Non-smooth points follow fixed conventions: the LLF maximum
  * passes its adjoint to the first maximal stencil cell, d|x|/dx = 0 at 0.
@@ -238,11 +239,12 @@ xf_status xf_probe_fp64(int64_t iters, int blocks_per_sm, double *tflops);
  * for all instances, with a grid barrier between phases; a step is replayed
  * from a CUDA graph (captured per temperature-buffer parity and dt). Every cell
  * and face uses the same device code as xf_step_rk3, so each instance's result
- * is bitwise identical to a single-grid handle stepped alone (SURVEY a10).
+ * is bitwise identical to a single-grid handle stepped alone.
  * The grid barrier is bounded: a block that waits past its limit sets
  * XF_FLAG_TIMEOUT in the batch status and the kernel still finishes. */
 typedef struct xf_batch xf_batch;
-/* grids/thermos/opts: arrays of n (host); every grid must be 2D. */
+/* grids/thermos/opts: arrays of n (host); every grid must be 2D and every
+ * opts[i].weno the same (XF_ERR_ARG otherwise). */
 xf_status xf_batch_create(int n, const xf_grid *grids, const xf_thermo *thermos,
                           const xf_opts *opts, xf_batch **out);
 void xf_batch_destroy(xf_batch *b);

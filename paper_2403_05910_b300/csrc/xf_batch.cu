@@ -93,15 +93,16 @@ __device__ __forceinline__ void b_prim(const BInst& I, long long t, const double
   xf::prim_cell<BDIM, NS>(I.p, t, Uin, Tin, Tout, I.Q, I.flags, cfl, sc, sn);
 }
 
-template <int NS>
+template <int NS, int REC>
 __device__ __forceinline__ void b_face(const BInst& I, int D, int fi, int fj, double dt) {
-  if (D == 0) xf::face_one<BDIM, NS, 0>(I.p, fi, fj, 0, I.Q, I.G[0], I.flags, dt);
-  else xf::face_one<BDIM, NS, 1>(I.p, fi, fj, 0, I.Q, I.G[1], I.flags, dt);
+  if (D == 0) xf::face_one<BDIM, NS, 0, REC>(I.p, fi, fj, 0, I.Q, I.G[0], I.flags, dt);
+  else xf::face_one<BDIM, NS, 1, REC>(I.p, fi, fj, 0, I.Q, I.G[1], I.flags, dt);
 }
 
 // One RK stage (1, 2, 3) of every instance. tsel selects the temperature
 // buffer read (the other is written); cfl: reduce the CFL maxima and set dt.
-template <int BT>
+// REC: the reconstruction every instance of the batch uses.
+template <int BT, int REC>
 __global__ void __launch_bounds__(BT, 256 / BT)
 k_batch_stage(const BInst* __restrict__ inst, const __grid_constant__ BCtl c, int stage, int tsel,
               int cfl) {
@@ -207,10 +208,10 @@ k_batch_stage(const BInst* __restrict__ inst, const __grid_constant__ BCtl c, in
     }
     const double dt = I.p.positivity ? __ldcg(I.dt) : 0.0;
     switch (I.p.N) {
-      case 2: b_face<2>(I, D, fi, fj, dt); break;
-      case 3: b_face<3>(I, D, fi, fj, dt); break;
-      case 4: b_face<4>(I, D, fi, fj, dt); break;
-      default: b_face<5>(I, D, fi, fj, dt); break;
+      case 2: b_face<2, REC>(I, D, fi, fj, dt); break;
+      case 3: b_face<3, REC>(I, D, fi, fj, dt); break;
+      case 4: b_face<4, REC>(I, D, fi, fj, dt); break;
+      default: b_face<5, REC>(I, D, fi, fj, dt); break;
     }
   }
   grid_barrier(c, nb);
@@ -247,7 +248,11 @@ __global__ void k_barrier_probe(const __grid_constant__ BCtl c, unsigned expect)
   grid_barrier(c, expect);
 }
 
-int nq_of(int dim, int N) { return 2 * N + 2 * dim + 9 + dim * dim; }
+// per-cell fields of an instance (plus D_sm per species with the
+// mixture-averaged diffusion)
+int nq_of(const xf::Params& p) {
+  return 2 * p.N + 2 * p.dim + 9 + p.dim * p.dim + (p.diffusion ? p.N : 0);
+}
 
 struct Candidate {
   int bt, tw, th;
@@ -280,6 +285,7 @@ struct xf_batch {
   uint32_t* bflags = nullptr;
   std::vector<void*> allocs;
   int choice = 0;
+  int rec = 5;  // reconstruction of every instance (xf_opts.weno)
   int grid = 0;
   int tsel = 0;
   long long timeout = 4000000000ll;  // ~2 s at 2 GHz
@@ -320,10 +326,14 @@ xf_status configure(xf_batch* b, int k) {
   int dev = 0, sms = 0, per_sm = 0;
   XB_CUDA(cudaGetDevice(&dev));
   XB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  if (cd.bt == 128)
-    XB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_stage<128>, 128, 0));
-  else
-    XB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_stage<256>, 256, 0));
+#define XB_OCC(BT_, REC_) \
+  XB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_stage<BT_, REC_>, BT_, 0))
+  if (cd.bt == 128) {
+    if (b->rec == 7) XB_OCC(128, 7); else if (b->rec == 6) XB_OCC(128, 6); else XB_OCC(128, 5);
+  } else {
+    if (b->rec == 7) XB_OCC(256, 7); else if (b->rec == 6) XB_OCC(256, 6); else XB_OCC(256, 5);
+  }
+#undef XB_OCC
   if (per_sm < 1) {
     xf_internal_set_error("xf_batch: stage kernel cannot be resident");
     return XF_ERR_CUDA;
@@ -363,8 +373,14 @@ xf_status launch_stage(xf_batch* b, cudaStream_t s, int stage, int tsel, int cfl
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   const BInst* di = b->dinst;
-  if (bt == 128) XB_CUDA(cudaLaunchKernelEx(&cfg, k_batch_stage<128>, di, c, stage, tsel, cfl));
-  else XB_CUDA(cudaLaunchKernelEx(&cfg, k_batch_stage<256>, di, c, stage, tsel, cfl));
+#define XB_LAUNCH(BT_, REC_) \
+  XB_CUDA(cudaLaunchKernelEx(&cfg, k_batch_stage<BT_, REC_>, di, c, stage, tsel, cfl))
+  if (bt == 128) {
+    if (b->rec == 7) XB_LAUNCH(128, 7); else if (b->rec == 6) XB_LAUNCH(128, 6); else XB_LAUNCH(128, 5);
+  } else {
+    if (b->rec == 7) XB_LAUNCH(256, 7); else if (b->rec == 6) XB_LAUNCH(256, 6); else XB_LAUNCH(256, 5);
+  }
+#undef XB_LAUNCH
   return XF_OK;
 }
 
@@ -392,6 +408,7 @@ xf_status xf_batch_create(int n, const xf_grid* grids, const xf_thermo* thermos,
   *out = nullptr;
   xf_batch* b = new xf_batch();
   b->n = n;
+  b->rec = opts[0].weno;
   b->hinst.resize(n);
   b->pre_pad.assign(n + 1, 0);
   b->pre_cell.assign(n + 1, 0);
@@ -399,7 +416,7 @@ xf_status xf_batch_create(int n, const xf_grid* grids, const xf_thermo* thermos,
     BInst& I = b->hinst[i];
     std::memset(&I, 0, sizeof I);
     xf_status st = xf_internal_fill_params(&grids[i], &thermos[i], &opts[i], &I.p);
-    if (st != XF_OK || grids[i].dim != BDIM || opts[i].weno != 5 || I.p.diffusion) {
+    if (st != XF_OK || grids[i].dim != BDIM || opts[i].weno != opts[0].weno) {
       delete b;
       return XF_ERR_ARG;
     }
@@ -424,13 +441,13 @@ xf_status xf_batch_create(int n, const xf_grid* grids, const xf_thermo* thermos,
     ok = alloc((void**)&I.U, sb) && alloc((void**)&I.Us, sb) &&
          alloc((void**)&I.T[0], sizeof(double) * p.cells) &&
          alloc((void**)&I.T[1], sizeof(double) * p.cells) &&
-         alloc((void**)&I.Q, sizeof(double) * (size_t)nq_of(p.dim, p.N) * p.pcells) &&
+         alloc((void**)&I.Q, sizeof(double) * (size_t)nq_of(p) * p.pcells) &&
          alloc((void**)&I.G[0], sizeof(double) * (size_t)p.nv * (p.n[0] + 1) * p.n[1]) &&
          alloc((void**)&I.G[1], sizeof(double) * (size_t)p.nv * p.n[0] * (p.n[1] + 1)) &&
          alloc((void**)&I.dt, sizeof(double)) && alloc((void**)&I.red, 2 * sizeof(unsigned long long)) &&
          alloc((void**)&I.flags, sizeof(uint32_t));
     if (ok) {
-      ok = cudaMemset(I.Q, 0, sizeof(double) * (size_t)nq_of(p.dim, p.N) * p.pcells) == cudaSuccess &&
+      ok = cudaMemset(I.Q, 0, sizeof(double) * (size_t)nq_of(p) * p.pcells) == cudaSuccess &&
            cudaMemset(I.red, 0, 2 * sizeof(unsigned long long)) == cudaSuccess &&
            cudaMemset(I.flags, 0, sizeof(uint32_t)) == cudaSuccess &&
            cudaMemset(I.dt, 0, sizeof(double)) == cudaSuccess;

@@ -101,9 +101,9 @@ def test_diffusion_case_conserves_over_a_long_run():
     assert np.var(ch4(Ug)) < 0.9 * np.var(ch4(U))
 
 
-def test_refused_where_unsupported():
+def test_adjoint_refuses_the_model():
     import torch
-    from paper_2403_05910_b300.xf import Batch, XFError
+    from paper_2403_05910_b300.xf import XFError
     case = cases.with_binary_diffusion(cases.config(1, n=(24, 12)))
     U, T = Oracle(case).prim_to_cons()
     s = gpu_solver(case, diffusion=1)
@@ -114,7 +114,34 @@ def test_refused_where_unsupported():
     with pytest.raises(XFError):
         s.step_adjoint(1e-5, Ub)
     s.close()
-    with pytest.raises(XFError):
-        Batch([case], diffusion=1)
     with pytest.raises(ValueError):
         gpu_solver(cases.config(1, n=(24, 12)), diffusion=1)   # no binary fits
+
+
+
+def test_batch_with_mixture_diffusion_is_bitwise_single_grid():
+    """The batched persistent form with the mixture-averaged model (instances
+    with their own binary fits): bit for bit equal to stepping alone."""
+    import torch
+    from paper_2403_05910_b300.xf import Batch
+    cs = [cases.with_binary_diffusion(c, seed=k) for k, c in enumerate(cases.batch(12, count=5, scale=4))]
+    ins = [Oracle(c).prim_to_cons() for c in cs]
+    b = Batch(cs, diffusion=1)
+    for i, (U, T) in enumerate(ins):
+        b.set_state(i, dev(U), dev(T))
+    for _ in range(2):
+        b.step(0.0)
+    got = []
+    for i, c in enumerate(cs):
+        Ug = torch.empty((c.n_v, c.cells), dtype=torch.float64, device="cuda")
+        Tg = torch.empty(c.cells, dtype=torch.float64, device="cuda")
+        b.get_state(i, Ug, Tg)
+        got.append((Ug, Tg))
+    torch.cuda.synchronize()
+    assert b.status() == 0
+    b.close()
+    for c, (U, T), (Ug, Tg) in zip(cs, ins, got):
+        Up, Tp, st, _ = gpu_steps(c, U, T, 2, diffusion=1)
+        assert st == 0
+        assert np.array_equal(Ug.cpu().numpy(), Up), c.name
+        assert np.array_equal(Tg.cpu().numpy(), Tp), c.name

@@ -1,7 +1,7 @@
 """Parity of the CUDA path (through the C-ABI) with the CPU oracle, element by
 element, on seeded inputs that span several thread blocks with ragged tails.
 
-Tolerances (spec bar, per-field metric max|gpu - ref| / max|ref|):
+Tolerances (per-field metric max|gpu - ref| / max|ref|):
 1e-11 after one RK3 step and for one RHS evaluation, 1e-8 after ten steps.
 """
 import numpy as np

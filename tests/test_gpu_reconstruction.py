@@ -110,9 +110,11 @@ def test_design_order_density_wave(weno, ns, power, order):
 
 
 @pytest.mark.parametrize("weno", WENOS)
-def test_refused_where_unsupported(weno):
+def test_adjoint_refuses_and_batch_needs_one_scheme(weno):
+    import ctypes as C
     import torch
-    from paper_2403_05910_b300.xf import Batch, XFError
+    from paper_2403_05910_b300.xf import (XF_ERR_ARG, Grid, Opts, Thermo, XFError, lib,
+                                          structs)
     case = cases.config(1, n=(24, 12))
     U, T = Oracle(case).prim_to_cons()
     s = gpu_solver(case, weno=weno)
@@ -123,8 +125,13 @@ def test_refused_where_unsupported(weno):
     with pytest.raises(XFError):
         s.step_adjoint(1e-5, Ub)
     s.close()
-    with pytest.raises(XFError):
-        Batch([case], weno=weno)
+    # one batch shares one reconstruction
+    c2 = cases.config(1, n=(20, 10))
+    g5, t5, o5, k5 = structs(c2)
+    g6, t6, o6, k6 = structs(c2, weno=weno)
+    G, Th, O = (Grid * 2)(g5, g6), (Thermo * 2)(t5, t6), (Opts * 2)(o5, o6)
+    h = C.c_void_p()
+    assert lib.xf_batch_create(2, G, Th, O, C.byref(h)) == XF_ERR_ARG
 
 
 def test_weno7_needs_four_cells_per_axis():
@@ -150,3 +157,33 @@ def test_all_options_together(weno):
         Ug, _, stg, _ = gpu_steps(case, U, T, steps, **kw)
         assert stg == 0
         assert np.max(field_err(Ug, U1, case.dim)) <= tol, case.name
+
+
+
+@pytest.mark.parametrize("weno", WENOS)
+def test_batch_with_scheme_is_bitwise_single_grid(weno):
+    """The batched persistent form with CU6 or WENO7 (and the blend on):
+    every instance bit for bit equal to stepping it alone."""
+    from paper_2403_05910_b300.xf import Batch
+    cs = cases.batch(11, count=5, scale=4)
+    ins = [Oracle(c).prim_to_cons() for c in cs]
+    b = Batch(cs, weno=weno, positivity=True)
+    for i, (U, T) in enumerate(ins):
+        b.set_state(i, dev(U), dev(T))
+    for _ in range(2):
+        b.step(0.0)
+    import torch
+    got = []
+    for i, c in enumerate(cs):
+        Ug = torch.empty((c.n_v, c.cells), dtype=torch.float64, device="cuda")
+        Tg = torch.empty(c.cells, dtype=torch.float64, device="cuda")
+        b.get_state(i, Ug, Tg)
+        got.append((Ug, Tg))
+    torch.cuda.synchronize()
+    assert b.status() == 0
+    b.close()
+    for c, (U, T), (Ug, Tg) in zip(cs, ins, got):
+        Up, Tp, st, _ = gpu_steps(c, U, T, 2, weno=weno, positivity=True)
+        assert st == 0
+        assert np.array_equal(Ug.cpu().numpy(), Up), c.name
+        assert np.array_equal(Tg.cpu().numpy(), Tp), c.name
