@@ -19,13 +19,29 @@ def _deps():
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile every source to an object in parallel (one nvcc per source),
+    then link the shared library; rebuilt only when a source is newer."""
     newest = max(os.path.getmtime(f) for f in _deps())
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest:
         return LIB
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [NVCC, *FLAGS, *(["-Xptxas", "-v"] if verbose else []), "-o", tmp, *SOURCES]
-    subprocess.check_call(cmd)
-    os.replace(tmp, LIB)
+    tag = f".tmp{os.getpid()}"
+    objs = [os.path.join(CSRC, os.path.basename(src) + tag + ".o") for src in SOURCES]
+    compile_flags = [f for f in FLAGS if f != "-shared"]
+    procs = [subprocess.Popen([NVCC, *compile_flags, *(["-Xptxas", "-v"] if verbose else []),
+                               "-c", "-o", obj, src])
+             for src, obj in zip(SOURCES, objs)]
+    codes = [p.wait() for p in procs]
+    try:
+        if any(codes):
+            raise subprocess.CalledProcessError(max(codes), "nvcc -c")
+        tmp = LIB + tag
+        subprocess.check_call([NVCC, "-gencode", "arch=compute_103a,code=sm_103a", "-shared",
+                               "-o", tmp, *objs])
+        os.replace(tmp, LIB)
+    finally:
+        for obj in objs:
+            if os.path.exists(obj):
+                os.remove(obj)
     return LIB
 
 
