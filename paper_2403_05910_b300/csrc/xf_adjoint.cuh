@@ -555,32 +555,46 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
       tau[a] = mu * (gr[D][a] + gr[a][D]);
       if (a == D) tau[a] = fma(-2.0 / 3.0 * mu, div, tau[a]);
     }
-    double dY[NS], Yf[NS], sdY = 0.0;
+    // species diffusivities at the face: the common D, or each species' D_sm
+    // (mixture-averaged model)
+    double dY[NS], Yf[NS], Dsf[NS], corr = 0.0;
 #pragma unroll
-    for (int s = 0; s < NS; ++s) { dY[s] = FD(L::Y + s); Yf[s] = FI(L::Y + s); sdY += dY[s]; }
-    const double corr = Df * sdY;
+    for (int s = 0; s < NS; ++s) {
+      dY[s] = FD(L::Y + s);
+      Yf[s] = FI(L::Y + s);
+      Dsf[s] = p.diffusion == 1 ? FI(L::DS + s) : Df;
+      corr = fma(Dsf[s], dY[s], corr);
+    }
     const TauPt tp = tau_of(p, Tf);
     const double dT = FD(L::T);
     // reverse: Gout[IE] -= ka dT + work - qd; Gout[1+a] -= tau_a; Gout[IE+1+s] += J_s
     const double workb = -Gb[IE], kab = -Gb[IE] * dT, dTb = -Gb[IE] * ka, qdb = Gb[IE];
-    double Tfb = 0.0, rfb = 0.0, Dfb = 0.0, corrb = 0.0, mub = 0.0, divb = 0.0;
-    double dYb[NS], Yfb[NS];
+    double Tfb = 0.0, rfb = 0.0, corrb = 0.0, mub = 0.0, divb = 0.0;
+    double dYb[NS], Yfb[NS], Dsfb[NS];
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-      const double J = -rf * fma(Df, dY[s], -Yf[s] * corr);
+      const double J = -rf * fma(Dsf[s], dY[s], -Yf[s] * corr);
       const double cps = cp_s(p, s, tp.tc);
       const double hs = h_s(p, s, tp, cps);
       double Jb = qdb * hs + (s < NS - 1 ? Gb[IE + 1 + s] : 0.0);
       Tfb += qdb * J * cps;
-      rfb -= Jb * (Df * dY[s] - Yf[s] * corr);
-      Dfb -= Jb * rf * dY[s];
-      dYb[s] = -Jb * rf * Df;
+      rfb -= Jb * (Dsf[s] * dY[s] - Yf[s] * corr);
+      Dsfb[s] = -Jb * rf * dY[s];
+      dYb[s] = -Jb * rf * Dsf[s];
       Yfb[s] = Jb * rf * corr;
       corrb += Jb * rf * Yf[s];
     }
-    Dfb += corrb * sdY;
+    // corr = sum_s D_s dY_s
 #pragma unroll
-    for (int s = 0; s < NS; ++s) dYb[s] += corrb * Df;
+    for (int s = 0; s < NS; ++s) {
+      Dsfb[s] = fma(corrb, dY[s], Dsfb[s]);
+      dYb[s] = fma(corrb, Dsf[s], dYb[s]);
+    }
+    double Dfb = 0.0;
+    if (p.diffusion != 1) {
+#pragma unroll
+      for (int s = 0; s < NS; ++s) Dfb += Dsfb[s];
+    }
     double grb[DIM][DIM];
 #pragma unroll
     for (int a = 0; a < DIM; ++a)
@@ -603,7 +617,12 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
     for (int a = 0; a < DIM; ++a) grb[a][a] += divb;
     BI(L::MU, mub);
     BI(L::KA, kab);
-    BI(L::DF, Dfb);
+    if (p.diffusion == 1) {
+#pragma unroll
+      for (int s = 0; s < NS; ++s) BI(L::DS + s, Dsfb[s]);
+    } else {
+      BI(L::DF, Dfb);
+    }
     BI(L::U, rfb);
     BI(L::T, Tfb);
     BD(L::T, dTb);
@@ -780,6 +799,73 @@ __device__ __forceinline__ void prim_adj_cell(const Params& p, long long t,
       }
     }
     double lnTb = 0.0, xdot = 0.0;
+    if (p.diffusion == 1) {
+      // mixture-averaged D_sm (Eq. 25-26), recomputed as in k_prim, then reversed:
+      // X~ = (max(X, 0) + 1e-12)/sum, W~ = sum X~ W, e_st = exp(-l_st(ln T)) = p D_st^-1 (SI),
+      // den_s = sum_{t!=s} X~_t e_st, num_s = sum_{t!=s} X~_t W_t,
+      // D_s = num_s / (W~ den_s p* fdsm)
+      constexpr int NP = NS * (NS - 1) / 2;
+      double m[NS], Xt[NS], XW[NS], den[NS], xts = 0.0, Wt = 0.0;
+      double e[NP > 0 ? NP : 1], dl[NP > 0 ? NP : 1];
+#pragma unroll
+      for (int s = 0; s < NS; ++s) { m[s] = fmax(X[s], 0.0) + 1e-12; xts += m[s]; den[s] = 0.0; }
+      const double ixts = 1.0 / xts;
+#pragma unroll
+      for (int s = 0; s < NS; ++s) { Xt[s] = m[s] * ixts; XW[s] = Xt[s] / p.invW[s]; Wt += XW[s]; }
+      {
+        int k = 0;
+#pragma unroll
+        for (int s = 0; s < NS; ++s)
+#pragma unroll
+          for (int tt = s + 1; tt < NS; ++tt, ++k) {
+            const double* bc = p.dbin[s][tt];
+            const double l = fma(fma(fma(bc[3], lnT, bc[2]), lnT, bc[1]), lnT, bc[0]);
+            dl[k] = fma(fma(3.0 * bc[3], lnT, 2.0 * bc[2]), lnT, bc[1]);
+            e[k] = exp(-l);
+            den[s] = fma(Xt[tt], e[k], den[s]);
+            den[tt] = fma(Xt[s], e[k], den[tt]);
+          }
+      }
+      const double sc = 1.0 / (Wt * pr * p.fdsm);
+      double numb[NS], denb[NS], nbs = 0.0, scb = 0.0;
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        double num = 0.0;
+#pragma unroll
+        for (int tt = 0; tt < NS; ++tt)
+          if (tt != s) num += XW[tt];
+        const double iden = 1.0 / den[s];
+        const double Dsb = qb[(L::DS + s) * PC];
+        const double Ds = num * sc * iden;
+        numb[s] = Dsb * sc * iden;
+        scb = fma(Dsb, num * iden, scb);
+        denb[s] = -Dsb * Ds * iden;
+        nbs += numb[s];
+      }
+      const double Wtb = -scb * sc / Wt;
+      prb -= scb * sc / pr;
+      double Xtb[NS];
+#pragma unroll
+      for (int s = 0; s < NS; ++s) Xtb[s] = (nbs - numb[s] + Wtb) / p.invW[s];
+      {
+        int k = 0;
+#pragma unroll
+        for (int s = 0; s < NS; ++s)
+#pragma unroll
+          for (int tt = s + 1; tt < NS; ++tt, ++k) {
+            Xtb[tt] = fma(denb[s], e[k], Xtb[tt]);
+            Xtb[s] = fma(denb[tt], e[k], Xtb[s]);
+            const double eb = fma(denb[s], Xt[tt], denb[tt] * Xt[s]);
+            lnTb -= eb * e[k] * dl[k];
+          }
+      }
+      double xtd = 0.0;
+#pragma unroll
+      for (int s = 0; s < NS; ++s) xtd = fma(Xtb[s], Xt[s], xtd);
+#pragma unroll
+      for (int s = 0; s < NS; ++s)
+        if (X[s] > 0.0) Xb[s] += (Xtb[s] - xtd) * ixts;
+    }
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
       smub[s] -= ismub[s] * ismu[s] * ismu[s];

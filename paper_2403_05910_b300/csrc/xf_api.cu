@@ -383,7 +383,7 @@ xf_status ensure_adjoint_buffers(xf_handle* h) {
   const xf::Params& p = h->p;
   const size_t sb = sizeof(double) * (size_t)p.nv * p.cells;
   void* ptrs[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-  const size_t bytes[6] = {sizeof(double) * (size_t)h->tab.nq * p.pcells, sb, sb, sb, sb,
+  const size_t bytes[6] = {sizeof(double) * nq_of(h->tab, p) * p.pcells, sb, sb, sb, sb,
                            sizeof(double) * (size_t)blocks(p.cells, 256)};
   for (int k = 0; k < 6; ++k) {
     if (cudaMalloc(&ptrs[k], bytes[k]) != cudaSuccess) {
@@ -413,7 +413,7 @@ xf_status rhs_adjoint_impl(xf_handle* h, const double* U, const double* Rbar, do
     if (st != XF_OK) return st;
   }
   const xf::Params& p = h->p;
-  XF_CUDA(cudaMemsetAsync(h->Qb, 0, sizeof(double) * (size_t)h->tab.nq * p.pcells, s));
+  XF_CUDA(cudaMemsetAsync(h->Qb, 0, sizeof(double) * nq_of(h->tab, p) * p.pcells, s));
   for (int d = 0; d < p.dim; ++d)
     timed(h, XF_PROF_FACE_ADJ, s, [&] { h->tab.face_adj[d](p, h->Q, Rbar, scale, h->Qb, s); });
   if (p.viscous) timed(h, XF_PROF_GRAD, s, [&] { h->tab.grad_adj(p, h->Qb, s); });
@@ -658,15 +658,13 @@ xf_status xf_clear_status(xf_handle* h, void* stream) {
 
 xf_status xf_rhs_adjoint(xf_handle* h, const double* U, const double* dUdt_bar, double* U_bar,
                          void* stream) {
-  if (!h || !U || !dUdt_bar || !U_bar || h->p.positivity || h->p.weno != 5 || h->p.diffusion)
-    return XF_ERR_ARG;
+  if (!h || !U || !dUdt_bar || !U_bar || h->p.positivity || h->p.weno != 5) return XF_ERR_ARG;
   if (!is_device_ptr(U) || !is_device_ptr(dUdt_bar) || !is_device_ptr(U_bar)) return XF_ERR_ARG;
   return rhs_adjoint_impl(h, U, dUdt_bar, 1.0, U_bar, (cudaStream_t)stream);
 }
 
 xf_status xf_step_rk3_adjoint(xf_handle* h, double dt, double* U_bar, void* stream) {
-  if (!h || !U_bar || !(dt > 0.0) || h->p.positivity || h->p.weno != 5 || h->p.diffusion)
-    return XF_ERR_ARG;
+  if (!h || !U_bar || !(dt > 0.0) || h->p.positivity || h->p.weno != 5) return XF_ERR_ARG;
   if (!is_device_ptr(U_bar)) return XF_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   xf_status st = ensure_adjoint_buffers(h);

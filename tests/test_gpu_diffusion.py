@@ -1,8 +1,8 @@
 """Mixture-averaged species diffusion (Eq. 25-26, xf_opts.diffusion = 1) on
 the GPU: parity with the oracle's model on the RHS, one step and ten steps,
 including the 1D multicomponent diffusion case of Sec. VI.B (Table IV,
-synthetic species); conservation over a long run of that case; and refusal
-by the entry points that support the common-D model only.
+synthetic species); conservation over a long run of that case; the batched
+form with the model. Its adjoint is checked in test_gpu_adjoint.py.
 
 Tolerances as for the rest of the path: 1e-11 for one RHS and one step,
 1e-8 after ten steps (per-field max |gpu - ref| / max |ref|).
@@ -101,19 +101,7 @@ def test_diffusion_case_conserves_over_a_long_run():
     assert np.var(ch4(Ug)) < 0.9 * np.var(ch4(U))
 
 
-def test_adjoint_refuses_the_model():
-    import torch
-    from paper_2403_05910_b300.xf import XFError
-    case = cases.with_binary_diffusion(cases.config(1, n=(24, 12)))
-    U, T = Oracle(case).prim_to_cons()
-    s = gpu_solver(case, diffusion=1)
-    s.set_state(dev(U), dev(T))
-    Ub = torch.zeros((case.n_v, case.cells), dtype=torch.float64, device="cuda")
-    with pytest.raises(XFError):
-        s.rhs_adjoint(dev(U), dev(U), Ub)
-    with pytest.raises(XFError):
-        s.step_adjoint(1e-5, Ub)
-    s.close()
+def test_model_needs_binary_fits():
     with pytest.raises(ValueError):
         gpu_solver(cases.config(1, n=(24, 12)), diffusion=1)   # no binary fits
 
