@@ -110,14 +110,162 @@ __device__ __forceinline__ void aadd(double* p, double v) {
 }
 
 
+// ------------------------------------------------- positivity blend adjoint
+// Reverse of pos_blend (Eq. 17-20) for one face inside an RK stage of step dt:
+// recomputes the face's convective flux F_hat (conv_flux, WENO5) and the
+// blend; with theta < 1, F* = F_LF + theta (F_hat - F_LF), so F_hat gets
+// theta Gb and F_LF (1 - theta) Gb, and theta's adjoint goes to the binding
+// partial-density condition (the first one reaching the minimum; none when
+// theta is clipped at 0 or eps = lo, where theta is locally constant) and
+// through F_LF of Eq. 19 (alpha through the cell with the larger |u_d| + c)
+// to U, u_d, p and c of the two cells (scattered into Qb). Gc returns the
+// adjoint of F_hat (Gb itself when the blend is inactive).
+template <int DIM, int NS, int D>
+__device__ __forceinline__ void pos_blend_adj(const Params& p, const double* __restrict__ q0,
+                                              double* __restrict__ qb0, long long PC, long long sd,
+                                              double dt, const double* Gb, double* Gc) {
+  using L = Lay<DIM, NS>;
+  constexpr int NV = L::NV;
+  constexpr int IE = DIM + 1;
+#define QF(field, m) ld(q0 + (long long)(field) * PC + (long long)(m) * sd)
+#define QB(field, m, val) aadd(qb0 + (long long)(field) * PC + (long long)(m) * sd, (val))
+  double Gh[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Gh[v] = 0.0;
+  uint32_t st = 0;
+  conv_flux<DIM, NS, D, 5>(p, q0, PC, sd, Gh, st);
+  const double lam2 = 2.0 * DIM * dt * p.inv_dx[D];
+  double Ua[NV], Ub[NV], Fa[NV], Fb[NV], Flf[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) { Ua[v] = QF(L::U + v, 0); Ub[v] = QF(L::U + v, 1); }
+  const double una = QF(L::UN + D, 0), unb = QF(L::UN + D, 1);
+  const double pa = QF(L::P, 0), pb = QF(L::P, 1);
+  const double ca = QF(L::C, 0), cb = QF(L::C, 1);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) { Fa[v] = una * Ua[v]; Fb[v] = unb * Ub[v]; }
+  Fa[1 + D] += pa; Fb[1 + D] += pb;
+  Fa[IE] += pa * una; Fb[IE] += pb * unb;
+  const double sa = fabs(una) + ca, sbv = fabs(unb) + cb;
+  const double al = fmax(sa, sbv);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Flf[v] = 0.5 * (Fa[v] + Fb[v] + al * (Ua[v] - Ub[v]));
+  // theta and its binding condition
+  double theta = 1.0, lo_s = 0.0, hi_s = 0.0, eps_s = 0.0;
+  int s_s = -1, side_s = 0;
+  bool live = false;  // theta depends on (lo, hi) there
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    double qa, qb, fh, fl;
+    if (s < NS - 1) {
+      qa = Ua[IE + 1 + s]; qb = Ub[IE + 1 + s]; fh = Gh[IE + 1 + s]; fl = Flf[IE + 1 + s];
+    } else {
+      qa = Ua[0]; qb = Ub[0]; fh = Gh[0]; fl = Flf[0];
+#pragma unroll
+      for (int k = 0; k < NS - 1; ++k) {
+        qa -= Ua[IE + 1 + k]; qb -= Ub[IE + 1 + k]; fh -= Gh[IE + 1 + k]; fl -= Flf[IE + 1 + k];
+      }
+    }
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const double sg = side == 0 ? -lam2 : lam2;
+      const double q = side == 0 ? qa : qb;
+      const double hi = fma(sg, fh, q), lo = fma(sg, fl, q);
+      const double eps = fmin(lo, p.pos_eps);
+      if (hi < eps) {
+        const double cand = (lo - eps) / (lo - hi);
+        const double th = fmax(cand, 0.0);
+        if (th < theta) {
+          theta = th;
+          s_s = s; side_s = side; lo_s = lo; hi_s = hi; eps_s = eps;
+          live = cand > 0.0 && lo >= p.pos_eps;
+        }
+      }
+    }
+  }
+  if (!(theta < 1.0)) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Gc[v] = Gb[v];
+    return;
+  }
+  double thetab = 0.0, Flfb[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    thetab = fma(Gh[v] - Flf[v], Gb[v], thetab);
+    Gc[v] = theta * Gb[v];
+    Flfb[v] = (1.0 - theta) * Gb[v];
+  }
+  double Uab[NV], Ubb[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) { Uab[v] = 0.0; Ubb[v] = 0.0; }
+  if (live) {
+    // theta = (lo - eps)/(lo - hi) with eps = pos_eps
+    const double r = 1.0 / (lo_s - hi_s);
+    const double lob = thetab * (eps_s - hi_s) * r * r;
+    const double hib = thetab * (lo_s - eps_s) * r * r;
+    const double sg = side_s == 0 ? -lam2 : lam2;
+    const double qbar = lob + hib, flb = sg * lob, fhb = sg * hib;
+    double* Ut = side_s == 0 ? Uab : Ubb;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      if (s != s_s) continue;
+      if (s < NS - 1) {
+        Ut[IE + 1 + s] += qbar;
+        Flfb[IE + 1 + s] += flb;
+        Gc[IE + 1 + s] += fhb;
+      } else {
+        Ut[0] += qbar; Flfb[0] += flb; Gc[0] += fhb;
+#pragma unroll
+        for (int k = 0; k < NS - 1; ++k) {
+          Ut[IE + 1 + k] -= qbar; Flfb[IE + 1 + k] -= flb; Gc[IE + 1 + k] -= fhb;
+        }
+      }
+    }
+  }
+  // F_LF = (F_a + F_b + alpha (U_a - U_b)) / 2
+  double alb = 0.0, unab = 0.0, unbb = 0.0;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const double h = 0.5 * Flfb[v];
+    alb = fma(h, Ua[v] - Ub[v], alb);
+    Uab[v] = fma(h, al + una, Uab[v]);
+    Ubb[v] = fma(h, unb - al, Ubb[v]);
+    unab = fma(h, Ua[v], unab);
+    unbb = fma(h, Ub[v], unbb);
+  }
+  // pressure terms of the physical fluxes
+  const double hm = 0.5 * Flfb[1 + D], he = 0.5 * Flfb[IE];
+  const double pab = fma(he, una, hm), pbb = fma(he, unb, hm);
+  unab = fma(he, pa, unab);
+  unbb = fma(he, pb, unbb);
+  // alpha = max(|u_a| + c_a, |u_b| + c_b)
+  double cab = 0.0, cbb = 0.0;
+  if (sa >= sbv) {
+    unab += una > 0.0 ? alb : (una < 0.0 ? -alb : 0.0);
+    cab = alb;
+  } else {
+    unbb += unb > 0.0 ? alb : (unb < 0.0 ? -alb : 0.0);
+    cbb = alb;
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v) { QB(L::U + v, 0, Uab[v]); QB(L::U + v, 1, Ubb[v]); }
+  QB(L::UN + D, 0, unab);
+  QB(L::UN + D, 1, unbb);
+  QB(L::P, 0, pab);
+  QB(L::P, 1, pbb);
+  QB(L::C, 0, cab);
+  QB(L::C, 1, cbb);
+#undef QF
+#undef QB
+}
+
 // ================================================================ k_face_adj
 // Per face of direction D: Gbar = scale (Rbar_right - Rbar_left)/dx (Rbar = 0
 // outside the interior), then the reverse of face_one.
-template <int DIM, int NS, int D>
+template <int DIM, int NS, int D, bool POS = false>
 __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk,
                                          const double* __restrict__ Q,
                                          const double* __restrict__ Rbar, double scale,
-                                         double* __restrict__ Qb) {
+                                         double* __restrict__ Qb, double dt = 0.0) {
   using L = Lay<DIM, NS>;
   constexpr int NV = L::NV;
   constexpr int IE = DIM + 1;
@@ -147,6 +295,15 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
 #define QF(field, m) ld(q0 + (long long)(field) * PC + (long long)(m) * sd)
 #define QB(field, m, val) aadd(qb0 + (long long)(field) * PC + (long long)(m) * sd, (val))
   if (p.convective) {
+    // adjoint of the convective flux: Gbar itself, or its share through the
+    // positivity-preserving blend inside an RK stage
+    double Gc[NV];
+    if constexpr (POS) {
+      pos_blend_adj<DIM, NS, D>(p, q0, qb0, PC, sd, dt, Gb, Gc);
+    } else {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Gc[v] = Gb[v];
+    }
     // ================= forward recomputation =================
     const double sL = QF(L::SR, 0), sR = QF(L::SR, 1);
     const double iw = 1.0 / (sL + sR);
@@ -243,19 +400,19 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
     // ================= reverse =================
     // back-projection of the dense columns: adjoints of the reconstructed
     // fields depend on Gbar and the face state only
-    double Sb = Gb[0] + Hb * Gb[IE];
+    double Sb = Gc[0] + Hb * Gc[IE];
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) Sb = fma(ub[a], Gb[1 + a], Sb);
+    for (int a = 0; a < DIM; ++a) Sb = fma(ub[a], Gc[1 + a], Sb);
 #pragma unroll
-    for (int s = 0; s < NS - 1; ++s) Sb = fma(Yb[s], Gb[IE + 1 + s], Sb);
-    const double Dlb = c * Gb[1 + D] + un * c * Gb[IE];
+    for (int s = 0; s < NS - 1; ++s) Sb = fma(Yb[s], Gc[IE + 1 + s], Sb);
+    const double Dlb = c * Gc[1 + D] + un * c * Gc[IE];
     double ubb[DIM], Ybb[NS];
 #pragma unroll
     for (int a = 0; a < DIM; ++a) ubb[a] = 0.0;
 #pragma unroll
     for (int s = 0; s < NS; ++s) Ybb[s] = 0.0;
     double cb = 0.0, Hbb = 0.0, unb = 0.0, c2b = 0.0, iGamb = 0.0;
-    const double Fmb = Sb - Dlb, Fpb = Sb + Dlb, Feb = Sb - c2 * iGam * Gb[IE];
+    const double Fmb = Sb - Dlb, Fpb = Sb + Dlb, Feb = Sb - c2 * iGam * Gc[IE];
     double Fm = 0.0, Fp = 0.0, Fe = 0.0;
     // per-field reverse; stencil adjoints accumulated here
     double rhob[6], pb[6], hunb[6], gUhb[6], mnb[6];
@@ -335,14 +492,14 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
     {
       const double S = Fm + Fp + Fe, Dl = Fp - Fm;
 #pragma unroll
-      for (int a = 0; a < DIM; ++a) ubb[a] += S * Gb[1 + a];
+      for (int a = 0; a < DIM; ++a) ubb[a] += S * Gc[1 + a];
 #pragma unroll
-      for (int s = 0; s < NS - 1; ++s) Ybb[s] += S * Gb[IE + 1 + s];
-      cb += Dl * Gb[1 + D] + un * Dl * Gb[IE];
-      Hbb += S * Gb[IE];
-      unb += c * Dl * Gb[IE];
-      c2b -= iGam * Fe * Gb[IE];
-      iGamb -= c2 * Fe * Gb[IE];
+      for (int s = 0; s < NS - 1; ++s) Ybb[s] += S * Gc[IE + 1 + s];
+      cb += Dl * Gc[1 + D] + un * Dl * Gc[IE];
+      Hbb += S * Gc[IE];
+      unb += c * Dl * Gc[IE];
+      c2b -= iGam * Fe * Gc[IE];
+      iGamb -= c2 * Fe * Gc[IE];
     }
     // tangential momenta and species (eigenvalue u, no pressure term)
     double hp0b[6], hm0b[6];
@@ -351,7 +508,7 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
       if (a == D) continue;
-      const double Fb = Gb[1 + a] + ub[a] * Gb[IE];
+      const double Fb = Gc[1 + a] + ub[a] * Gc[IE];
       double LUv[6];
 #pragma unroll
       for (int m = 0; m < 6; ++m) {
@@ -361,7 +518,7 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
       }
       double wpb[6] = {0, 0, 0, 0, 0, 0}, wmb[6] = {0, 0, 0, 0, 0, 0};
       const double Fk = weno5_pair_fwd_adj(wp, wm, e12c, Fb, wpb, wmb);
-      ubb[a] += Fk * Gb[IE];
+      ubb[a] += Fk * Gc[IE];
 #pragma unroll
       for (int m = 0; m < 6; ++m) {
         const double LUb = wpb[m] * (hun[m] + ha0) + wmb[m] * (hun[m] - ha0);
@@ -375,7 +532,7 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
     double dphib[NS > 1 ? NS - 1 : 1];
 #pragma unroll
     for (int s = 0; s < NS - 1; ++s) {
-      const double Fb = Gb[IE + 1 + s] - dphi[s] * iGam * Gb[IE];
+      const double Fb = Gc[IE + 1 + s] - dphi[s] * iGam * Gc[IE];
       double LUv[6];
 #pragma unroll
       for (int m = 0; m < 6; ++m) {
@@ -385,8 +542,8 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
       }
       double wpb[6] = {0, 0, 0, 0, 0, 0}, wmb[6] = {0, 0, 0, 0, 0, 0};
       const double Fk = weno5_pair_fwd_adj(wp, wm, e12c, Fb, wpb, wmb);
-      dphib[s] = -iGam * Fk * Gb[IE];
-      iGamb -= dphi[s] * Fk * Gb[IE];
+      dphib[s] = -iGam * Fk * Gc[IE];
+      iGamb -= dphi[s] * Fk * Gc[IE];
 #pragma unroll
       for (int m = 0; m < 6; ++m) {
         const double LUb = wpb[m] * (hun[m] + ha0) + wmb[m] * (hun[m] - ha0);
@@ -658,6 +815,20 @@ k_face_adj(const __grid_constant__ Params p, const double* __restrict__ Q,
   if (f >= (long long)nf0 * nf1 * nf2) return;
   face_adj<DIM, NS, D>(p, (int)(f % nf0), (int)((f / nf0) % nf1), (int)(f / ((long long)nf0 * nf1)),
                        Q, Rbar, scale, Qb);
+}
+
+// the same inside an RK stage of a handle with the positivity-preserving
+// blend: dtp holds the stage's time step
+template <int DIM, int NS, int D>
+__global__ void __launch_bounds__(128)
+k_face_adj_pos(const __grid_constant__ Params p, const double* __restrict__ Q,
+               const double* __restrict__ Rbar, double scale, double* __restrict__ Qb,
+               const double* __restrict__ dtp) {
+  const int nf0 = p.n[0] + (D == 0), nf1 = p.n[1] + (D == 1), nf2 = p.n[2] + (D == 2);
+  const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= (long long)nf0 * nf1 * nf2) return;
+  face_adj<DIM, NS, D, true>(p, (int)(f % nf0), (int)((f / nf0) % nf1),
+                             (int)(f / ((long long)nf0 * nf1)), Q, Rbar, scale, Qb, *dtp);
 }
 
 // ================================================================ k_prim_adj

@@ -42,6 +42,8 @@ using UpdFn = void (*)(const xf::Params&, const double*, const double*, const do
 using FromPrimFn = void (*)(const xf::Params&, const double*, double*, double*, cudaStream_t);
 using FaceAdjFn = void (*)(const xf::Params&, const double*, const double*, double, double*,
                            cudaStream_t);
+using FaceAdjPosFn = void (*)(const xf::Params&, const double*, const double*, double, double*,
+                              const double*, cudaStream_t);
 using CellAdjFn = void (*)(const xf::Params&, const double*, const double*, double*, cudaStream_t);
 using GradAdjFn = void (*)(const xf::Params&, double*, cudaStream_t);
 using MixFn = void (*)(const xf::Params&, const double*, int, double, double*, double*,
@@ -57,6 +59,7 @@ struct Table {
   FromPrimFn from_prim;
   int nq;
   FaceAdjFn face_adj[3];
+  FaceAdjPosFn face_adj_pos[3];  // inside an RK stage with the positivity blend
   GradAdjFn grad_adj;
   CellAdjFn prim_adj;
   CellAdjFn from_prim_adj;
@@ -100,6 +103,15 @@ struct Launch {
       xf::k_face_adj<DIM, NS, D><<<blocks(nf, 128), 128, 0, s>>>(p, Q, Rb, scale, Qb);
     }
   }
+  template <int D>
+  static void face_adj_pos(const xf::Params& p, const double* Q, const double* Rb, double scale,
+                           double* Qb, const double* dt, cudaStream_t s) {
+    if constexpr (D < DIM) {
+      const long long nf =
+          (long long)(p.n[0] + (D == 0)) * (p.n[1] + (D == 1)) * (p.n[2] + (D == 2));
+      xf::k_face_adj_pos<DIM, NS, D><<<blocks(nf, 128), 128, 0, s>>>(p, Q, Rb, scale, Qb, dt);
+    }
+  }
   static void grad_adj(const xf::Params& p, double* Qb, cudaStream_t s) {
     xf::k_grad_adj<DIM, NS><<<blocks(p.pcells, 256), 256, 0, s>>>(p, Qb);
   }
@@ -118,8 +130,9 @@ struct Launch {
   static Table table() {
     return Table{prim, grad, {face<0>, face<1>, face<2>}, {face<0, 6>, face<1, 6>, face<2, 6>},
                  {face<0, 7>, face<1, 7>, face<2, 7>}, update, from_prim, xf::Lay<DIM, NS>::NQ,
-                 {face_adj<0>, face_adj<1>, face_adj<2>}, grad_adj, prim_adj, from_prim_adj,
-                 mixing};
+                 {face_adj<0>, face_adj<1>, face_adj<2>},
+                 {face_adj_pos<0>, face_adj_pos<1>, face_adj_pos<2>}, grad_adj, prim_adj,
+                 from_prim_adj, mixing};
   }
 };
 
@@ -403,9 +416,11 @@ xf_status ensure_adjoint_buffers(xf_handle* h) {
 }
 
 // Ubar += scale (dL/dU)^T Rbar at the state U. With fields_ready the block
-// h->Q already holds the per-cell fields of U.
+// h->Q already holds the per-cell fields of U. dtp (device, nullable): the
+// RK stage's time step, for the reverse of the positivity blend.
 xf_status rhs_adjoint_impl(xf_handle* h, const double* U, const double* Rbar, double scale,
-                           double* Ubar, cudaStream_t s, bool fields_ready = false) {
+                           double* Ubar, cudaStream_t s, bool fields_ready = false,
+                           const double* dtp = nullptr) {
   xf_status st = ensure_adjoint_buffers(h);
   if (st != XF_OK) return st;
   if (!fields_ready) {
@@ -415,7 +430,10 @@ xf_status rhs_adjoint_impl(xf_handle* h, const double* U, const double* Rbar, do
   const xf::Params& p = h->p;
   XF_CUDA(cudaMemsetAsync(h->Qb, 0, sizeof(double) * nq_of(h->tab, p) * p.pcells, s));
   for (int d = 0; d < p.dim; ++d)
-    timed(h, XF_PROF_FACE_ADJ, s, [&] { h->tab.face_adj[d](p, h->Q, Rbar, scale, h->Qb, s); });
+    timed(h, XF_PROF_FACE_ADJ, s, [&] {
+      if (p.positivity && dtp) h->tab.face_adj_pos[d](p, h->Q, Rbar, scale, h->Qb, dtp, s);
+      else h->tab.face_adj[d](p, h->Q, Rbar, scale, h->Qb, s);
+    });
   if (p.viscous) timed(h, XF_PROF_GRAD, s, [&] { h->tab.grad_adj(p, h->Qb, s); });
   timed(h, XF_PROF_PRIM_ADJ, s, [&] { h->tab.prim_adj(p, h->Q, h->Qb, Ubar, s); });
   XF_CUDA(cudaGetLastError());
@@ -658,13 +676,13 @@ xf_status xf_clear_status(xf_handle* h, void* stream) {
 
 xf_status xf_rhs_adjoint(xf_handle* h, const double* U, const double* dUdt_bar, double* U_bar,
                          void* stream) {
-  if (!h || !U || !dUdt_bar || !U_bar || h->p.positivity || h->p.weno != 5) return XF_ERR_ARG;
+  if (!h || !U || !dUdt_bar || !U_bar || h->p.weno != 5) return XF_ERR_ARG;
   if (!is_device_ptr(U) || !is_device_ptr(dUdt_bar) || !is_device_ptr(U_bar)) return XF_ERR_ARG;
   return rhs_adjoint_impl(h, U, dUdt_bar, 1.0, U_bar, (cudaStream_t)stream);
 }
 
 xf_status xf_step_rk3_adjoint(xf_handle* h, double dt, double* U_bar, void* stream) {
-  if (!h || !U_bar || !(dt > 0.0) || h->p.positivity || h->p.weno != 5) return XF_ERR_ARG;
+  if (!h || !U_bar || !(dt > 0.0) || h->p.weno != 5) return XF_ERR_ARG;
   if (!is_device_ptr(U_bar)) return XF_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   xf_status st = ensure_adjoint_buffers(h);
@@ -689,26 +707,26 @@ xf_status xf_step_rk3_adjoint(xf_handle* h, double dt, double* U_bar, void* stre
   k_set_scalar<<<1, 1, 0, s>>>(h->dt, dt);
   // forward stage states U1 (A1) and U2 (A2) from U^n (h->U)
   h->Q = h->QS[0];
-  st = stage_fluxes(h, h->U, 0, s);
+  st = stage_fluxes(h, h->U, 0, s, true);
   if (st != XF_OK) return st;
   h->tab.update(p, h->G[0], h->G[1], h->G[2], h->U, h->U, h->A1, h->dt, 1, s);
   h->Q = h->QS[1];
-  st = stage_fluxes(h, h->A1, 0, s);
+  st = stage_fluxes(h, h->A1, 0, s, true);
   if (st != XF_OK) return st;
   h->tab.update(p, h->G[0], h->G[1], h->G[2], h->U, h->A1, h->A2, h->dt, 2, s);
   // reverse of U3 = U/3 + 2/3 (U2 + dt L(U2)), U2 = 3/4 U + 1/4 (U1 + dt L(U1)),
   // U1 = U + dt L(U); a = Ubar(U3) on entry
   lincomb(h, 2.0 / 3.0, U_bar, 0.0, nullptr, 0.0, nullptr, h->B2, s);
   h->Q = guard.q;
-  st = rhs_adjoint_impl(h, h->A2, U_bar, 2.0 / 3.0 * dt, h->B2, s);
+  st = rhs_adjoint_impl(h, h->A2, U_bar, 2.0 / 3.0 * dt, h->B2, s, false, h->dt);
   if (st != XF_OK) return st;
   lincomb(h, 0.25, h->B2, 0.0, nullptr, 0.0, nullptr, h->B1, s);
   h->Q = h->QS[1];
-  st = rhs_adjoint_impl(h, h->A1, h->B2, 0.25 * dt, h->B1, s, true);
+  st = rhs_adjoint_impl(h, h->A1, h->B2, 0.25 * dt, h->B1, s, true, h->dt);
   if (st != XF_OK) return st;
   lincomb(h, 1.0 / 3.0, U_bar, 0.75, h->B2, 1.0, h->B1, U_bar, s);
   h->Q = h->QS[0];
-  st = rhs_adjoint_impl(h, h->U, h->B1, dt, U_bar, s, true);
+  st = rhs_adjoint_impl(h, h->U, h->B1, dt, U_bar, s, true, h->dt);
   if (st != XF_OK) return st;
   XF_CUDA(cudaGetLastError());
   return XF_OK;

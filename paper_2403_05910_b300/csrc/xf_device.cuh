@@ -663,6 +663,288 @@ __device__ __forceinline__ void rec_div2(const RecND& x, const RecND& y, double&
 #ifndef XF_FACE_MIN_BLOCKS
 #define XF_FACE_MIN_BLOCKS 2
 #endif
+// Convective face flux of Eq. 15 (Roe-averaged face state, PER projection,
+// LLF splitting of Eq. 14, reconstruction REC, back-projection) into Gout,
+// for the face between the cells q0 and q0 + sd (stride of direction D).
+template <int DIM, int NS, int D, int REC>
+__device__ __forceinline__ void conv_flux(const Params& p, const double* __restrict__ q0,
+                                          long long PC, long long sd, double* Gout,
+                                          uint32_t& st) {
+  using L = Lay<DIM, NS>;
+  constexpr int SO = REC == 7 ? 3 : 2;  // stencil cells left of the left cell
+  constexpr int SW = 2 * SO + 2;        // stencil width
+  constexpr int IE = DIM + 1;
+#define QF(field, m) ld(q0 + (long long)(field) * PC + (long long)(m) * sd)
+  // ---- Roe-averaged face state (sqrt(rho) weights)
+  const double sL = QF(L::SR, 0), sR = QF(L::SR, 1);
+  const double iw = 1.0 / (sL + sR);
+  const double tL = sL * iw, tR = sR * iw;
+  double ub[DIM], q2 = 0.0;
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    ub[a] = fma(tL, QF(L::UN + a, 0), tR * QF(L::UN + a, 1));
+    q2 = fma(ub[a], ub[a], q2);
+  }
+  const double Hb = fma(tL, QF(L::H, 0), tR * QF(L::H, 1));
+  const double Tb = fma(tL, QF(L::T, 0), tR * QF(L::T, 1));
+  double Yb[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) Yb[s] = fma(tL, QF(L::Y + s, 0), tR * QF(L::Y + s, 1));
+  const TauPt tp = tau_of(p, Tb);
+  double es[NS], Rb = 0.0, cvb = 0.0;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    const double cps = cp_s(p, s, tp.tc);
+    es[s] = h_s_in(p, s, tp) - p.r[s] * Tb;
+    Rb = fma(Yb[s], p.r[s], Rb);
+    cvb = fma(Yb[s], cps - p.r[s], cvb);
+  }
+  // one division for Gamma = R/c_v and its inverse
+  const double rRc = 1.0 / (Rb * cvb);
+  const double Gam = Rb * Rb * rRc;
+  const double hq2 = 0.5 * q2;
+  double phi[NS], c2 = 0.0;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    phi[s] = fma(p.r[s], Tb, -Gam * (es[s] - hq2));
+    c2 = fma(Yb[s], phi[s], c2);
+  }
+  c2 = fma(Gam, Hb - q2, c2);
+  if (!(c2 > 0.0)) {
+    st |= 4u;
+    const double cl = QF(L::C, 0), cr = QF(L::C, 1);
+    c2 = 0.5 * (cl * cl + cr * cr);
+  }
+  const double rsc = rsqrt(c2);
+  const double c = c2 * rsc;
+  const double ic2 = rsc * rsc;
+  const double hic2 = 0.5 * ic2;
+  const double iGam = cvb * cvb * rRc;
+  const double un = ub[D];
+  // ---- stencil m = i-SO..i+SO+1 (SW cells: i-2..i+3 for WENO5 and CU6,
+  //      i-3..i+4 for WENO7; offsets from the left cell). Per cell:
+  //      rho, p, u_n/2, g.U/(2c^2) and the LLF maxima of |u-c|, |u+c|, |u|.
+  //      The 1/2 of Eq. 14 and the 1/(2c^2) of the acoustic rows are folded
+  //      into per-face coefficients.
+  const double phiN = phi[NS - 1];
+  double gm[DIM], dphi[NS > 1 ? NS - 1 : 1], gs[NS > 1 ? NS - 1 : 1];
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) gm[a] = -Gam * ub[a] * hic2;
+#pragma unroll
+  for (int s = 0; s < NS - 1; ++s) { dphi[s] = phi[s] - phiN; gs[s] = dphi[s] * hic2; }
+  const double gr = phiN * hic2, gE = Gam * hic2;
+  double rho_m[SW], p_m[SW], hun[SW], gUh[SW];
+  double am = 0.0, ap = 0.0, a0 = 0.0;
+#pragma unroll
+  for (int m = 0; m < SW; ++m) {
+    const int o = m - SO;
+    rho_m[m] = QF(L::U, o);
+    const double unm = QF(L::UN + D, o);
+    p_m[m] = QF(L::P, o);
+    const double cm = QF(L::C, o);
+    am = pmax(am, fabs(unm - cm));
+    ap = pmax(ap, fabs(unm + cm));
+    a0 = pmax(a0, fabs(unm));
+    hun[m] = 0.5 * unm;
+    double g = gr * rho_m[m];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) g = fma(gm[a], QF(L::U + 1 + a, o), g);
+    g = fma(gE, QF(L::U + IE, o), g);
+#pragma unroll
+    for (int s = 0; s < NS - 1; ++s) g = fma(gs[s], QF(L::U + IE + 1 + s, o), g);
+    gUh[m] = g;
+  }
+  const double eps12 = 12.0 * p.weno_eps;
+  double e12c[4];
+  if constexpr (REC == 7) {
+    const double e240 = 240.0 * p.weno_eps;
+    e12c[0] = e240 * kW7c0; e12c[1] = e240 * kW7c1;
+    e12c[2] = e240 * kW7c2; e12c[3] = e240 * kW7c3;
+  } else {
+    e12c[0] = eps12 * kWc0; e12c[1] = eps12 * kWc1; e12c[2] = eps12 * kWc2; e12c[3] = eps12;
+  }
+  const double chc = c * hic2;
+  // ---- PER: one characteristic field at a time. With w = (1/2)(l.F_m +- a l.U_m)
+  //      and l.F_m = u_m (l.U_m) + p_m (l[m_n] + u_m l[E]):
+  //      w^+- = (u_m/2 +- a/2) l.U_m + p_m (l[m_n]/2 + (u_m/2) l[E]).
+  // the passive fields (eigenvalue u, no pressure term): tangential momenta,
+  // l = (-u_t, e_{m_t}), r = e_{m_t} + u_t e_E; species, l = (-Y_s, e_{rhoY_s}),
+  // r = e_{rhoY_s} - (phi_s - phi_N)/Gamma e_E. Passive field k < DIM-1 is the
+  // tangential axis k (skipping D), the rest the species k - (DIM-1).
+  constexpr int NPASS = DIM - 1 + NS - 1;
+  double hp0[SW], hm0[SW];
+  auto passive_nd = [&](int k) -> RecND {
+    double wp[SW], wm[SW];
+    if (k < DIM - 1) {
+      const int a = k < D ? k : k + 1;
+#pragma unroll
+      for (int m = 0; m < SW; ++m) {
+        const double LU = fma(-ub[a], rho_m[m], QF(L::U + 1 + a, m - SO));
+        wp[m] = hp0[m] * LU;
+        wm[m] = hm0[m] * LU;
+      }
+    } else {
+      const int s = k - (DIM - 1);
+#pragma unroll
+      for (int m = 0; m < SW; ++m) {
+        const double LU = fma(-Yb[s], rho_m[m], QF(L::U + IE + 1 + s, m - SO));
+        wp[m] = hp0[m] * LU;
+        wm[m] = hm0[m] * LU;
+      }
+    }
+    return rec_nd<REC>(wp, wm, e12c);
+  };
+  double Fk_m, Fk_p, Fk_e, Fk_first = 0.0;
+  {
+    double wp[SW], wm[SW];
+    RecND ndm, ndp, nde;
+    // normal momentum relative to the face velocity, shared by u -+ c
+    double nUv[SW];
+#pragma unroll
+    for (int m = 0; m < SW; ++m) nUv[m] = fma(-un, rho_m[m], QF(L::U + 1 + D, m - SO));
+    // u - c: l.U = (g.U - c (m_n - u_n rho)) / (2c^2)
+    {
+      const double hlmn = 0.5 * (-Gam * un - c) * hic2, lE = Gam * hic2;
+      const double ha = 0.5 * am;
+#pragma unroll
+      for (int m = 0; m < SW; ++m) {
+        const double LU = fma(-chc, nUv[m], gUh[m]);
+        const double pq = p_m[m] * fma(hun[m], lE, hlmn);
+        wp[m] = fma(hun[m] + ha, LU, pq);
+        wm[m] = fma(hun[m] - ha, LU, pq);
+      }
+      ndm = rec_nd<REC>(wp, wm, e12c);
+    }
+    // u + c
+    {
+      const double hlmn = 0.5 * (-Gam * un + c) * hic2, lE = Gam * hic2;
+      const double ha = 0.5 * ap;
+#pragma unroll
+      for (int m = 0; m < SW; ++m) {
+        const double LU = fma(chc, nUv[m], gUh[m]);
+        const double pq = p_m[m] * fma(hun[m], lE, hlmn);
+        wp[m] = fma(hun[m] + ha, LU, pq);
+        wm[m] = fma(hun[m] - ha, LU, pq);
+      }
+      ndp = rec_nd<REC>(wp, wm, e12c);
+    }
+    rec_div2<REC>(ndm, ndp, Fk_m, Fk_p);
+    // entropy: l = e_rho - g / c^2
+    {
+      const double hlmn = 0.5 * Gam * un * ic2, lE = -Gam * ic2;
+      const double ha = 0.5 * a0;
+#pragma unroll
+      for (int m = 0; m < SW; ++m) {
+        const double LU = fma(-2.0, gUh[m], rho_m[m]);
+        const double pq = p_m[m] * fma(hun[m], lE, hlmn);
+        wp[m] = fma(hun[m] + ha, LU, pq);
+        wm[m] = fma(hun[m] - ha, LU, pq);
+      }
+      nde = rec_nd<REC>(wp, wm, e12c);
+    }
+    const double ha0 = 0.5 * a0;
+#pragma unroll
+    for (int m = 0; m < SW; ++m) { hp0[m] = hun[m] + ha0; hm0[m] = hun[m] - ha0; }
+    // the entropy field shares its division with the first passive field
+    if constexpr (NPASS > 0) rec_div2<REC>(nde, passive_nd(0), Fk_e, Fk_first);
+    else Fk_e = rec_div1<REC>(nde);
+  }
+  // back-projection of the three dense right columns (Eq. 15)
+  {
+    const double S = Fk_m + Fk_p + Fk_e;
+    const double Dl = Fk_p - Fk_m;
+    Gout[0] = S;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) Gout[1 + a] = ub[a] * S;
+    Gout[1 + D] = fma(c, Dl, Gout[1 + D]);
+    Gout[IE] = fma(Hb, S, fma(un * c, Dl, -c2 * iGam * Fk_e));
+#pragma unroll
+    for (int s = 0; s < NS - 1; ++s) Gout[IE + 1 + s] = Yb[s] * S;
+  }
+  // the passive fields' right columns, in order, two fields per division
+  auto passive_add = [&](int k, double Fk) {
+    if (k < DIM - 1) {
+      const int a = k < D ? k : k + 1;
+      Gout[1 + a] += Fk;
+      Gout[IE] = fma(ub[a], Fk, Gout[IE]);
+    } else {
+      const int s = k - (DIM - 1);
+      Gout[IE + 1 + s] += Fk;
+      Gout[IE] = fma(-dphi[s] * iGam, Fk, Gout[IE]);
+    }
+  };
+  if constexpr (NPASS > 0) passive_add(0, Fk_first);
+#pragma unroll
+  for (int k = 1; k < NPASS; k += 2) {
+    const RecND x = passive_nd(k);
+    if (k + 1 < NPASS) {
+      double fx, fy;
+      rec_div2<REC>(x, passive_nd(k + 1), fx, fy);
+      passive_add(k, fx);
+      passive_add(k + 1, fy);
+    } else {
+      passive_add(k, rec_div1<REC>(x));
+    }
+  }
+#undef QF
+}
+
+// Positivity-preserving blend of one face's convective flux Gout (in place),
+// for the face between the cells q0 and q0 + sd; dt is the stage time step.
+template <int DIM, int NS, int D>
+__device__ __forceinline__ void pos_blend(const Params& p, const double* __restrict__ q0,
+                                          long long PC, long long sd, double dt, double* Gout) {
+  using L = Lay<DIM, NS>;
+  constexpr int NV = L::NV;
+  constexpr int IE = DIM + 1;
+#define QF(field, m) ld(q0 + (long long)(field) * PC + (long long)(m) * sd)
+  // Positivity-preserving blend (Eq. 17-20): F* = (1 - theta) F_LF + theta F_hat
+  // with the local LF flux of Eq. 19 (alpha = max(|u_d| + c) of the two cells);
+  // theta keeps every partial density of U_i - 2 lam F* and U_{i+1} + 2 lam F*
+  // (Eq. 18, lam = dim dt / dx_d) at or above min(pos_eps, its LF value).
+  const double lam2 = 2.0 * DIM * dt * p.inv_dx[D];
+  double Fa[NV], Fb[NV], Ua[NV], Ub[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) { Ua[v] = QF(L::U + v, 0); Ub[v] = QF(L::U + v, 1); }
+  const double una = QF(L::UN + D, 0), unb = QF(L::UN + D, 1);
+  const double pa = QF(L::P, 0), pb = QF(L::P, 1);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) { Fa[v] = una * Ua[v]; Fb[v] = unb * Ub[v]; }
+  Fa[1 + D] += pa; Fb[1 + D] += pb;
+  Fa[IE] += pa * una; Fb[IE] += pb * unb;
+  const double al = fmax(fabs(una) + QF(L::C, 0), fabs(unb) + QF(L::C, 1));
+  double Flf[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Flf[v] = 0.5 * (Fa[v] + Fb[v] + al * (Ua[v] - Ub[v]));
+  double theta = 1.0;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    double qa, qb, fh, fl;
+    if (s < NS - 1) {
+      qa = Ua[IE + 1 + s]; qb = Ub[IE + 1 + s]; fh = Gout[IE + 1 + s]; fl = Flf[IE + 1 + s];
+    } else {
+      qa = Ua[0]; qb = Ub[0]; fh = Gout[0]; fl = Flf[0];
+#pragma unroll
+      for (int k = 0; k < NS - 1; ++k) {
+        qa -= Ua[IE + 1 + k]; qb -= Ub[IE + 1 + k]; fh -= Gout[IE + 1 + k]; fl -= Flf[IE + 1 + k];
+      }
+    }
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const double sg = side == 0 ? -lam2 : lam2;
+      const double q = side == 0 ? qa : qb;
+      const double hi = fma(sg, fh, q), lo = fma(sg, fl, q);
+      const double eps = fmin(lo, p.pos_eps);
+      if (hi < eps) theta = fmin(theta, fmax((lo - eps) / (lo - hi), 0.0));
+    }
+  }
+  if (theta < 1.0) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Gout[v] = fma(theta, Gout[v] - Flf[v], Flf[v]);
+  }
+#undef QF
+}
+
 // Per-face body: face (fi, fj, fk) of direction D, i.e. between cells
 // idx - e_D and idx (fi in 0..n_0 when D = 0, and so on).
 template <int DIM, int NS, int D, int REC = 5>
@@ -671,8 +953,6 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
                                          uint32_t* __restrict__ flags, double dt) {
   using L = Lay<DIM, NS>;
   constexpr int NV = L::NV;
-  constexpr int SO = REC == 7 ? 3 : 2;  // stencil cells left of the left cell
-  constexpr int SW = 2 * SO + 2;        // stencil width
   constexpr int IE = DIM + 1;
   const int nf0 = p.n[0] + (D == 0), nf1 = p.n[1] + (D == 1), nf2 = p.n[2] + (D == 2);
   const long long nfaces = (long long)nf0 * nf1 * nf2;
@@ -690,266 +970,9 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
   for (int v = 0; v < NV; ++v) Gout[v] = 0.0;
   uint32_t st = 0;
 
-  if (p.convective) {
-    // ---- Roe-averaged face state (sqrt(rho) weights)
-    const double sL = QF(L::SR, 0), sR = QF(L::SR, 1);
-    const double iw = 1.0 / (sL + sR);
-    const double tL = sL * iw, tR = sR * iw;
-    double ub[DIM], q2 = 0.0;
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) {
-      ub[a] = fma(tL, QF(L::UN + a, 0), tR * QF(L::UN + a, 1));
-      q2 = fma(ub[a], ub[a], q2);
-    }
-    const double Hb = fma(tL, QF(L::H, 0), tR * QF(L::H, 1));
-    const double Tb = fma(tL, QF(L::T, 0), tR * QF(L::T, 1));
-    double Yb[NS];
-#pragma unroll
-    for (int s = 0; s < NS; ++s) Yb[s] = fma(tL, QF(L::Y + s, 0), tR * QF(L::Y + s, 1));
-    const TauPt tp = tau_of(p, Tb);
-    double es[NS], Rb = 0.0, cvb = 0.0;
-#pragma unroll
-    for (int s = 0; s < NS; ++s) {
-      const double cps = cp_s(p, s, tp.tc);
-      es[s] = h_s_in(p, s, tp) - p.r[s] * Tb;
-      Rb = fma(Yb[s], p.r[s], Rb);
-      cvb = fma(Yb[s], cps - p.r[s], cvb);
-    }
-    // one division for Gamma = R/c_v and its inverse
-    const double rRc = 1.0 / (Rb * cvb);
-    const double Gam = Rb * Rb * rRc;
-    const double hq2 = 0.5 * q2;
-    double phi[NS], c2 = 0.0;
-#pragma unroll
-    for (int s = 0; s < NS; ++s) {
-      phi[s] = fma(p.r[s], Tb, -Gam * (es[s] - hq2));
-      c2 = fma(Yb[s], phi[s], c2);
-    }
-    c2 = fma(Gam, Hb - q2, c2);
-    if (!(c2 > 0.0)) {
-      st |= 4u;
-      const double cl = QF(L::C, 0), cr = QF(L::C, 1);
-      c2 = 0.5 * (cl * cl + cr * cr);
-    }
-    const double rsc = rsqrt(c2);
-    const double c = c2 * rsc;
-    const double ic2 = rsc * rsc;
-    const double hic2 = 0.5 * ic2;
-    const double iGam = cvb * cvb * rRc;
-    const double un = ub[D];
-    // ---- stencil m = i-SO..i+SO+1 (SW cells: i-2..i+3 for WENO5 and CU6,
-    //      i-3..i+4 for WENO7; offsets from the left cell). Per cell:
-    //      rho, p, u_n/2, g.U/(2c^2) and the LLF maxima of |u-c|, |u+c|, |u|.
-    //      The 1/2 of Eq. 14 and the 1/(2c^2) of the acoustic rows are folded
-    //      into per-face coefficients.
-    const double phiN = phi[NS - 1];
-    double gm[DIM], dphi[NS > 1 ? NS - 1 : 1], gs[NS > 1 ? NS - 1 : 1];
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) gm[a] = -Gam * ub[a] * hic2;
-#pragma unroll
-    for (int s = 0; s < NS - 1; ++s) { dphi[s] = phi[s] - phiN; gs[s] = dphi[s] * hic2; }
-    const double gr = phiN * hic2, gE = Gam * hic2;
-    double rho_m[SW], p_m[SW], hun[SW], gUh[SW];
-    double am = 0.0, ap = 0.0, a0 = 0.0;
-#pragma unroll
-    for (int m = 0; m < SW; ++m) {
-      const int o = m - SO;
-      rho_m[m] = QF(L::U, o);
-      const double unm = QF(L::UN + D, o);
-      p_m[m] = QF(L::P, o);
-      const double cm = QF(L::C, o);
-      am = pmax(am, fabs(unm - cm));
-      ap = pmax(ap, fabs(unm + cm));
-      a0 = pmax(a0, fabs(unm));
-      hun[m] = 0.5 * unm;
-      double g = gr * rho_m[m];
-#pragma unroll
-      for (int a = 0; a < DIM; ++a) g = fma(gm[a], QF(L::U + 1 + a, o), g);
-      g = fma(gE, QF(L::U + IE, o), g);
-#pragma unroll
-      for (int s = 0; s < NS - 1; ++s) g = fma(gs[s], QF(L::U + IE + 1 + s, o), g);
-      gUh[m] = g;
-    }
-    const double eps12 = 12.0 * p.weno_eps;
-    double e12c[4];
-    if constexpr (REC == 7) {
-      const double e240 = 240.0 * p.weno_eps;
-      e12c[0] = e240 * kW7c0; e12c[1] = e240 * kW7c1;
-      e12c[2] = e240 * kW7c2; e12c[3] = e240 * kW7c3;
-    } else {
-      e12c[0] = eps12 * kWc0; e12c[1] = eps12 * kWc1; e12c[2] = eps12 * kWc2; e12c[3] = eps12;
-    }
-    const double chc = c * hic2;
-    // ---- PER: one characteristic field at a time. With w = (1/2)(l.F_m +- a l.U_m)
-    //      and l.F_m = u_m (l.U_m) + p_m (l[m_n] + u_m l[E]):
-    //      w^+- = (u_m/2 +- a/2) l.U_m + p_m (l[m_n]/2 + (u_m/2) l[E]).
-    // the passive fields (eigenvalue u, no pressure term): tangential momenta,
-    // l = (-u_t, e_{m_t}), r = e_{m_t} + u_t e_E; species, l = (-Y_s, e_{rhoY_s}),
-    // r = e_{rhoY_s} - (phi_s - phi_N)/Gamma e_E. Passive field k < DIM-1 is the
-    // tangential axis k (skipping D), the rest the species k - (DIM-1).
-    constexpr int NPASS = DIM - 1 + NS - 1;
-    double hp0[SW], hm0[SW];
-    auto passive_nd = [&](int k) -> RecND {
-      double wp[SW], wm[SW];
-      if (k < DIM - 1) {
-        const int a = k < D ? k : k + 1;
-#pragma unroll
-        for (int m = 0; m < SW; ++m) {
-          const double LU = fma(-ub[a], rho_m[m], QF(L::U + 1 + a, m - SO));
-          wp[m] = hp0[m] * LU;
-          wm[m] = hm0[m] * LU;
-        }
-      } else {
-        const int s = k - (DIM - 1);
-#pragma unroll
-        for (int m = 0; m < SW; ++m) {
-          const double LU = fma(-Yb[s], rho_m[m], QF(L::U + IE + 1 + s, m - SO));
-          wp[m] = hp0[m] * LU;
-          wm[m] = hm0[m] * LU;
-        }
-      }
-      return rec_nd<REC>(wp, wm, e12c);
-    };
-    double Fk_m, Fk_p, Fk_e, Fk_first = 0.0;
-    {
-      double wp[SW], wm[SW];
-      RecND ndm, ndp, nde;
-      // normal momentum relative to the face velocity, shared by u -+ c
-      double nUv[SW];
-#pragma unroll
-      for (int m = 0; m < SW; ++m) nUv[m] = fma(-un, rho_m[m], QF(L::U + 1 + D, m - SO));
-      // u - c: l.U = (g.U - c (m_n - u_n rho)) / (2c^2)
-      {
-        const double hlmn = 0.5 * (-Gam * un - c) * hic2, lE = Gam * hic2;
-        const double ha = 0.5 * am;
-#pragma unroll
-        for (int m = 0; m < SW; ++m) {
-          const double LU = fma(-chc, nUv[m], gUh[m]);
-          const double pq = p_m[m] * fma(hun[m], lE, hlmn);
-          wp[m] = fma(hun[m] + ha, LU, pq);
-          wm[m] = fma(hun[m] - ha, LU, pq);
-        }
-        ndm = rec_nd<REC>(wp, wm, e12c);
-      }
-      // u + c
-      {
-        const double hlmn = 0.5 * (-Gam * un + c) * hic2, lE = Gam * hic2;
-        const double ha = 0.5 * ap;
-#pragma unroll
-        for (int m = 0; m < SW; ++m) {
-          const double LU = fma(chc, nUv[m], gUh[m]);
-          const double pq = p_m[m] * fma(hun[m], lE, hlmn);
-          wp[m] = fma(hun[m] + ha, LU, pq);
-          wm[m] = fma(hun[m] - ha, LU, pq);
-        }
-        ndp = rec_nd<REC>(wp, wm, e12c);
-      }
-      rec_div2<REC>(ndm, ndp, Fk_m, Fk_p);
-      // entropy: l = e_rho - g / c^2
-      {
-        const double hlmn = 0.5 * Gam * un * ic2, lE = -Gam * ic2;
-        const double ha = 0.5 * a0;
-#pragma unroll
-        for (int m = 0; m < SW; ++m) {
-          const double LU = fma(-2.0, gUh[m], rho_m[m]);
-          const double pq = p_m[m] * fma(hun[m], lE, hlmn);
-          wp[m] = fma(hun[m] + ha, LU, pq);
-          wm[m] = fma(hun[m] - ha, LU, pq);
-        }
-        nde = rec_nd<REC>(wp, wm, e12c);
-      }
-      const double ha0 = 0.5 * a0;
-#pragma unroll
-      for (int m = 0; m < SW; ++m) { hp0[m] = hun[m] + ha0; hm0[m] = hun[m] - ha0; }
-      // the entropy field shares its division with the first passive field
-      if constexpr (NPASS > 0) rec_div2<REC>(nde, passive_nd(0), Fk_e, Fk_first);
-      else Fk_e = rec_div1<REC>(nde);
-    }
-    // back-projection of the three dense right columns (Eq. 15)
-    {
-      const double S = Fk_m + Fk_p + Fk_e;
-      const double Dl = Fk_p - Fk_m;
-      Gout[0] = S;
-#pragma unroll
-      for (int a = 0; a < DIM; ++a) Gout[1 + a] = ub[a] * S;
-      Gout[1 + D] = fma(c, Dl, Gout[1 + D]);
-      Gout[IE] = fma(Hb, S, fma(un * c, Dl, -c2 * iGam * Fk_e));
-#pragma unroll
-      for (int s = 0; s < NS - 1; ++s) Gout[IE + 1 + s] = Yb[s] * S;
-    }
-    // the passive fields' right columns, in order, two fields per division
-    auto passive_add = [&](int k, double Fk) {
-      if (k < DIM - 1) {
-        const int a = k < D ? k : k + 1;
-        Gout[1 + a] += Fk;
-        Gout[IE] = fma(ub[a], Fk, Gout[IE]);
-      } else {
-        const int s = k - (DIM - 1);
-        Gout[IE + 1 + s] += Fk;
-        Gout[IE] = fma(-dphi[s] * iGam, Fk, Gout[IE]);
-      }
-    };
-    if constexpr (NPASS > 0) passive_add(0, Fk_first);
-#pragma unroll
-    for (int k = 1; k < NPASS; k += 2) {
-      const RecND x = passive_nd(k);
-      if (k + 1 < NPASS) {
-        double fx, fy;
-        rec_div2<REC>(x, passive_nd(k + 1), fx, fy);
-        passive_add(k, fx);
-        passive_add(k + 1, fy);
-      } else {
-        passive_add(k, rec_div1<REC>(x));
-      }
-    }
-  }
+  if (p.convective) conv_flux<DIM, NS, D, REC>(p, q0, PC, sd, Gout, st);
 
-  if (p.convective && p.positivity && dt > 0.0) {
-    // Positivity-preserving blend (Eq. 17-20): F* = (1 - theta) F_LF + theta F_hat
-    // with the local LF flux of Eq. 19 (alpha = max(|u_d| + c) of the two cells);
-    // theta keeps every partial density of U_i - 2 lam F* and U_{i+1} + 2 lam F*
-    // (Eq. 18, lam = dim dt / dx_d) at or above min(pos_eps, its LF value).
-    const double lam2 = 2.0 * DIM * dt * p.inv_dx[D];
-    double Fa[NV], Fb[NV], Ua[NV], Ub[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) { Ua[v] = QF(L::U + v, 0); Ub[v] = QF(L::U + v, 1); }
-    const double una = QF(L::UN + D, 0), unb = QF(L::UN + D, 1);
-    const double pa = QF(L::P, 0), pb = QF(L::P, 1);
-#pragma unroll
-    for (int v = 0; v < NV; ++v) { Fa[v] = una * Ua[v]; Fb[v] = unb * Ub[v]; }
-    Fa[1 + D] += pa; Fb[1 + D] += pb;
-    Fa[IE] += pa * una; Fb[IE] += pb * unb;
-    const double al = fmax(fabs(una) + QF(L::C, 0), fabs(unb) + QF(L::C, 1));
-    double Flf[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) Flf[v] = 0.5 * (Fa[v] + Fb[v] + al * (Ua[v] - Ub[v]));
-    double theta = 1.0;
-#pragma unroll
-    for (int s = 0; s < NS; ++s) {
-      double qa, qb, fh, fl;
-      if (s < NS - 1) {
-        qa = Ua[IE + 1 + s]; qb = Ub[IE + 1 + s]; fh = Gout[IE + 1 + s]; fl = Flf[IE + 1 + s];
-      } else {
-        qa = Ua[0]; qb = Ub[0]; fh = Gout[0]; fl = Flf[0];
-#pragma unroll
-        for (int k = 0; k < NS - 1; ++k) {
-          qa -= Ua[IE + 1 + k]; qb -= Ub[IE + 1 + k]; fh -= Gout[IE + 1 + k]; fl -= Flf[IE + 1 + k];
-        }
-      }
-#pragma unroll
-      for (int side = 0; side < 2; ++side) {
-        const double sg = side == 0 ? -lam2 : lam2;
-        const double q = side == 0 ? qa : qb;
-        const double hi = fma(sg, fh, q), lo = fma(sg, fl, q);
-        const double eps = fmin(lo, p.pos_eps);
-        if (hi < eps) theta = fmin(theta, fmax((lo - eps) / (lo - hi), 0.0));
-      }
-    }
-    if (theta < 1.0) {
-#pragma unroll
-      for (int v = 0; v < NV; ++v) Gout[v] = fma(theta, Gout[v] - Flf[v], Flf[v]);
-    }
-  }
+  if (p.convective && p.positivity && dt > 0.0) pos_blend<DIM, NS, D>(p, q0, PC, sd, dt, Gout);
 
   if (p.viscous) {
     // face values (-1, 9, 9, -1)/16, normal derivatives (1, -15, 15, -1)/(12 dx)

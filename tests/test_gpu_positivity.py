@@ -71,12 +71,21 @@ def test_batch_with_blend_is_bitwise_equal_to_single_grid():
     b.close()
 
 
-def test_adjoint_rejects_blended_handles():
+def test_rhs_adjoint_of_a_blended_handle_is_the_plain_one():
+    """A plain RHS never blends (it has no time step), so neither does its
+    adjoint: a handle with the blend on gives the unblended RHS adjoint (to
+    round-off: the adjoint scatters with atomic adds, whose order varies)."""
     import torch
-    from paper_2403_05910_b300.xf import XFError
     case = cases.config(4, n=(16, 8))
-    s = gpu_solver(case, positivity=True)
-    U = torch.zeros((case.n_v, case.cells), dtype=torch.float64, device="cuda")
-    with pytest.raises(XFError):
-        s.rhs_adjoint(U, U, U)
-    s.close()
+    U, T = Oracle(case).prim_to_cons()
+    W = np.random.default_rng(3).normal(size=U.shape)
+    out = []
+    for pos in (False, True):
+        s = gpu_solver(case, positivity=pos)
+        s.set_state(dev(U), dev(T))
+        Ub = torch.zeros((case.n_v, case.cells), dtype=torch.float64, device="cuda")
+        s.rhs_adjoint(dev(U), dev(W), Ub)
+        torch.cuda.synchronize()
+        out.append(Ub.cpu().numpy())
+        s.close()
+    assert np.max(np.abs(out[0] - out[1])) <= 1e-12 * np.max(np.abs(out[0]))
