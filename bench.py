@@ -34,7 +34,8 @@ FP64_NOMINAL_TFLOPS = 1.25   # B300 dense FP64 (nominal)
 # digits of the sha256 of the kernel source it was taken on; any other source
 # reports traffic null (the counters no longer describe the kernel).
 FACE_TRAFFIC_B_PER_FACE = {"aab342d14388773d": 294.0, "7aa2c6f72cd106cc": 294.2,
-                           "69f88d1a3ee86fc1": 293.6, "e3f39384d86bd1a7": 293.2}
+                           "69f88d1a3ee86fc1": 293.6, "e3f39384d86bd1a7": 293.2,
+                           "5117291dbdc4468e": 293.1}
 CPU_SAMPLE_GRID = (96, 48, 48)
 
 
