@@ -119,9 +119,8 @@ typedef struct xf_thermo {
  * species, 1 for the mixture-averaged D_sm of Eq. 26 from the binary D_st of
  * Eq. 25 (xf_thermo.dbin_coef), with the mole fractions regularised as
  * X~_t = (max(X_t, 0) + 1e-12) / sum so that a pure species keeps a finite
- * D_sm. The adjoint entry points support weno = 5 with every other option
- * (XF_ERR_ARG for weno = 6 or 7); the batched form supports every option,
- * with one reconstruction (weno) shared by all its instances.
+ * D_sm. The adjoint entry points support every option; the batched form
+ * too, with one reconstruction (weno) shared by all its instances.
  * positivity switches the positivity-preserving flux blend of Eq. 17-20 inside
  * RK stages: F* = (1 - theta) F_LF + theta F_hat per face, with the local LF
  * flux of Eq. 19 (alpha = max(|u_d| + c) of the two cells) and the smallest

@@ -7,7 +7,12 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libxf.so")
-SOURCES = [os.path.join(CSRC, "xf_api.cu"), os.path.join(CSRC, "xf_batch.cu")]
+# (source, extra flags): the adjoint launchers compile once per reconstruction
+UNITS = [("xf_api.cu", []), ("xf_batch.cu", []),
+         ("xf_adjoint_launch.cu", ["-DXF_ADJ_REC=5"]),
+         ("xf_adjoint_launch.cu", ["-DXF_ADJ_REC=6"]),
+         ("xf_adjoint_launch.cu", ["-DXF_ADJ_REC=7"])]
+SOURCES = sorted({os.path.join(CSRC, u) for u, _ in UNITS})
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
          "-Xcompiler", "-fPIC", "-shared", "-I", os.path.join(ROOT, "include"), "-I", CSRC]
@@ -25,11 +30,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest:
         return LIB
     tag = f".tmp{os.getpid()}"
-    objs = [os.path.join(CSRC, os.path.basename(src) + tag + ".o") for src in SOURCES]
+    objs = [os.path.join(CSRC, f"{u}.{k}{tag}.o") for k, (u, _) in enumerate(UNITS)]
     compile_flags = [f for f in FLAGS if f != "-shared"]
-    procs = [subprocess.Popen([NVCC, *compile_flags, *(["-Xptxas", "-v"] if verbose else []),
-                               "-c", "-o", obj, src])
-             for src, obj in zip(SOURCES, objs)]
+    procs = [subprocess.Popen([NVCC, *compile_flags, *extra,
+                               *(["-Xptxas", "-v"] if verbose else []),
+                               "-c", "-o", obj, os.path.join(CSRC, u)])
+             for (u, extra), obj in zip(UNITS, objs)]
     codes = [p.wait() for p in procs]
     try:
         if any(codes):

@@ -97,6 +97,210 @@ __device__ __forceinline__ double weno5_pair_fwd_adj(const double* wp, const dou
   return F;
 }
 
+// ---------------------------------------------------------- WENO-CU6 adjoint
+// Forward intermediates of one CU6 reconstruction exactly as cu6_nd (12 beta
+// with beta_6 as its LDL^T sum of squares, weights d_k (C s_k + 12 tau) times
+// the other s_j, candidates 6 (q_k - f2)), and the reverse. den carries the 6.
+struct C6 {
+  double a, b, c, d, e, t0, u0, t1, u1, t2, u2, y0, y1, y2, y3, y4;
+  double s0, s1, s2, s3, p01, p23, g0, g1, g2, g3, w0, w1, w2, w3, q0, q1, q2, q3;
+  double num, den;
+};
+
+__device__ __forceinline__ void c6_fwd(double f0, double f1, double f2, double f3, double f4,
+                                       double f5, double e12, C6& r) {
+  r.a = f1 - f0; r.b = f2 - f1; r.c = f3 - f2; r.d = f4 - f3; r.e = f5 - f4;
+  r.t0 = r.b - r.a; r.u0 = fma(3.0, r.b, -r.a);
+  r.t1 = r.c - r.b; r.u1 = r.b + r.c;
+  r.t2 = r.d - r.c; r.u2 = fma(-3.0, r.c, r.d);
+  const double b0 = fma(13.0 * r.t0, r.t0, 3.0 * r.u0 * r.u0);
+  const double b1 = fma(13.0 * r.t1, r.t1, 3.0 * r.u1 * r.u1);
+  const double b2 = fma(13.0 * r.t2, r.t2, 3.0 * r.u2 * r.u2);
+  r.y4 = r.e;
+  r.y3 = fma(kB6L43, r.e, r.d);
+  r.y2 = fma(kB6L42, r.e, fma(kB6L32, r.d, r.c));
+  r.y1 = fma(kB6L41, r.e, fma(kB6L31, r.d, fma(kB6L21, r.c, r.b)));
+  r.y0 = fma(kB6L40, r.e, fma(kB6L30, r.d, fma(kB6L20, r.c, fma(kB6L10, r.b, r.a))));
+  const double b6 = fma(kB6D[0] * r.y0, r.y0, fma(kB6D[1] * r.y1, r.y1, fma(kB6D[2] * r.y2, r.y2,
+                    fma(kB6D[3] * r.y3, r.y3, kB6D[4] * r.y4 * r.y4))));
+  const double tau = b6 - (b0 + b2 + 4.0 * b1) * (1.0 / 6.0);
+  r.s0 = b0 + e12; r.s1 = b1 + e12; r.s2 = b2 + e12; r.s3 = b6 + e12;
+  r.p01 = r.s0 * r.s1; r.p23 = r.s2 * r.s3;
+  const double t05 = 0.05 * tau, t45 = 0.45 * tau;
+  r.g0 = fma(0.05 * 20.0, r.s0, t05); r.g1 = fma(0.45 * 20.0, r.s1, t45);
+  r.g2 = fma(0.45 * 20.0, r.s2, t45); r.g3 = fma(0.05 * 20.0, r.s3, t05);
+  r.w0 = r.g0 * (r.s1 * r.p23); r.w1 = r.g1 * (r.s0 * r.p23);
+  r.w2 = r.g2 * (r.p01 * r.s3); r.w3 = r.g3 * (r.p01 * r.s2);
+  r.q0 = fma(2.0, r.u0, -r.b); r.q1 = fma(2.0, r.c, r.b); r.q2 = fma(4.0, r.c, -r.d);
+  r.q3 = fma(6.0, r.c, fma(-5.0, r.d, 2.0 * r.e));
+  r.num = fma(r.w0, r.q0, fma(r.w1, r.q1, fma(r.w2, r.q2, r.w3 * r.q3)));
+  r.den = 6.0 * ((r.w0 + r.w1) + (r.w2 + r.w3));
+}
+
+// (nbar, dbar) for (num, den) -> fb[0..5] (added)
+__device__ __forceinline__ void c6_rev(const C6& r, double nbar, double dbar, double* fb) {
+  const double d6 = 6.0 * dbar;
+  const double w0b = fma(nbar, r.q0, d6), w1b = fma(nbar, r.q1, d6);
+  const double w2b = fma(nbar, r.q2, d6), w3b = fma(nbar, r.q3, d6);
+  const double q0b = nbar * r.w0, q1b = nbar * r.w1, q2b = nbar * r.w2, q3b = nbar * r.w3;
+  const double g0b = w0b * (r.s1 * r.p23), g1b = w1b * (r.s0 * r.p23);
+  const double g2b = w2b * (r.p01 * r.s3), g3b = w3b * (r.p01 * r.s2);
+  double s0b = fma(w1b * r.g1, r.p23, g0b), s1b = fma(w0b * r.g0, r.p23, 9.0 * g1b);
+  double s2b = fma(w3b * r.g3, r.p01, 9.0 * g2b), s3b = fma(w2b * r.g2, r.p01, g3b);
+  const double p23b = fma(w0b * r.g0, r.s1, w1b * r.g1 * r.s0);
+  const double p01b = fma(w2b * r.g2, r.s3, w3b * r.g3 * r.s2);
+  s0b = fma(p01b, r.s1, s0b); s1b = fma(p01b, r.s0, s1b);
+  s2b = fma(p23b, r.s3, s2b); s3b = fma(p23b, r.s2, s3b);
+  const double taub = fma(0.05, g0b + g3b, 0.45 * (g1b + g2b));
+  // s_k = b_k + e12; tau = b6 - (b0 + b2 + 4 b1)/6
+  const double b6b = s3b + taub;
+  const double b0b = s0b - taub * (1.0 / 6.0), b2b = s2b - taub * (1.0 / 6.0);
+  const double b1b = s1b - taub * (4.0 / 6.0);
+  const double y0b = 2.0 * kB6D[0] * r.y0 * b6b, y1b = 2.0 * kB6D[1] * r.y1 * b6b;
+  const double y2b = 2.0 * kB6D[2] * r.y2 * b6b, y3b = 2.0 * kB6D[3] * r.y3 * b6b;
+  const double y4b = 2.0 * kB6D[4] * r.y4 * b6b;
+  const double t0b = 26.0 * r.t0 * b0b, u0b = fma(6.0 * r.u0, b0b, 2.0 * q0b);
+  const double t1b = 26.0 * r.t1 * b1b, u1b = 6.0 * r.u1 * b1b;
+  const double t2b = 26.0 * r.t2 * b2b, u2b = 6.0 * r.u2 * b2b;
+  const double ab = y0b - t0b - u0b;
+  const double bb = kB6L10 * y0b + y1b + t0b + 3.0 * u0b - t1b + u1b - q0b + q1b;
+  const double cb = kB6L20 * y0b + kB6L21 * y1b + y2b + t1b + u1b - t2b - 3.0 * u2b + 2.0 * q1b +
+                    4.0 * q2b + 6.0 * q3b;
+  const double db = kB6L30 * y0b + kB6L31 * y1b + kB6L32 * y2b + y3b + t2b + u2b - q2b - 5.0 * q3b;
+  const double eb = kB6L40 * y0b + kB6L41 * y1b + kB6L42 * y2b + kB6L43 * y3b + y4b + 2.0 * q3b;
+  fb[0] -= ab;
+  fb[1] += ab - bb;
+  fb[2] += bb - cb;
+  fb[3] += cb - db;
+  fb[4] += db - eb;
+  fb[5] += eb;
+}
+
+// ------------------------------------------------------------ WENO7 adjoint
+// Forward intermediates of one WENO7 reconstruction exactly as weno7_nd, and
+// the reverse (den without a scale factor).
+struct W7 {
+  double x0, x1, x2, x3, x4, x5, A[4], B[4], s0, s1, s2, s3, p01, p23, r0, r1, r2, r3;
+  double w0, w1, w2, w3, q0, q1, q2, q3, num, den;
+};
+
+__device__ __forceinline__ void w7_fwd(double f0, double f1, double f2, double f3, double f4,
+                                       double f5, double f6, const double* ec, W7& r) {
+  r.x0 = f1 - f0; r.x1 = f2 - f1; r.x2 = f3 - f2; r.x3 = f4 - f3; r.x4 = f5 - f4; r.x5 = f6 - f5;
+  const double z2 = kW7D3 * r.x2 * r.x2, z3 = kW7D3 * r.x3 * r.x3;
+  // A, B of Q0(x0, x1, x2), Q1(x1, x2, x3), Q1(x4, x3, x2), Q0(x5, x4, x3)
+  r.A[0] = fma(1.6946983546617915, r.x2, fma(-2.5484460694698354, r.x1, r.x0));
+  r.B[0] = fma(-1.4896519285042333, r.x2, r.x1);
+  r.A[1] = fma(0.92509363295880154, r.x3, fma(-2.0749063670411987, r.x2, r.x1));
+  r.B[1] = fma(-0.6326434619002822, r.x3, r.x2);
+  r.A[2] = fma(0.92509363295880154, r.x2, fma(-2.0749063670411987, r.x3, r.x4));
+  r.B[2] = fma(-0.6326434619002822, r.x2, r.x3);
+  r.A[3] = fma(1.6946983546617915, r.x3, fma(-2.5484460694698354, r.x4, r.x5));
+  r.B[3] = fma(-1.4896519285042333, r.x3, r.x4);
+  const double Q0 = fma(547.0 * r.A[0], r.A[0], fma(155.46617915904935 * r.B[0], r.B[0], z2));
+  const double Q1 = fma(267.0 * r.A[1], r.A[1], fma(318.50187265917606 * r.B[1], r.B[1], z3));
+  const double Q2 = fma(267.0 * r.A[2], r.A[2], fma(318.50187265917606 * r.B[2], r.B[2], z2));
+  const double Q3 = fma(547.0 * r.A[3], r.A[3], fma(155.46617915904935 * r.B[3], r.B[3], z3));
+  r.s0 = fma(kW7c0, Q0, ec[0]); r.s1 = fma(kW7c1, Q1, ec[1]);
+  r.s2 = fma(kW7c2, Q2, ec[2]); r.s3 = fma(kW7c3, Q3, ec[3]);
+  r.p01 = r.s0 * r.s1; r.p23 = r.s2 * r.s3;
+  r.r0 = r.s1 * r.p23; r.r1 = r.s0 * r.p23; r.r2 = r.p01 * r.s3; r.r3 = r.p01 * r.s2;
+  r.w0 = r.r0 * r.r0; r.w1 = r.r1 * r.r1; r.w2 = r.r2 * r.r2; r.w3 = r.r3 * r.r3;
+  r.q0 = fma(0.25, r.x0, fma(-5.0 / 6.0, r.x1, (13.0 / 12.0) * r.x2));
+  r.q1 = fma(-1.0 / 12.0, r.x1, fma(1.0 / 3.0, r.x2, 0.25 * r.x3));
+  r.q2 = fma(1.0 / 12.0, r.x2, fma(0.5, r.x3, (-1.0 / 12.0) * r.x4));
+  r.q3 = fma(0.75, r.x3, fma(-1.0 / 3.0, r.x4, (1.0 / 12.0) * r.x5));
+  r.num = fma(r.w0, r.q0, fma(r.w1, r.q1, fma(r.w2, r.q2, r.w3 * r.q3)));
+  r.den = (r.w0 + r.w1) + (r.w2 + r.w3);
+}
+
+// (nbar, dbar) for (num, den) -> fb[0..6] (added)
+__device__ __forceinline__ void w7_rev(const W7& r, double nbar, double dbar, double* fb) {
+  const double w0b = fma(nbar, r.q0, dbar), w1b = fma(nbar, r.q1, dbar);
+  const double w2b = fma(nbar, r.q2, dbar), w3b = fma(nbar, r.q3, dbar);
+  const double q0b = nbar * r.w0, q1b = nbar * r.w1, q2b = nbar * r.w2, q3b = nbar * r.w3;
+  const double r0b = 2.0 * r.r0 * w0b, r1b = 2.0 * r.r1 * w1b;
+  const double r2b = 2.0 * r.r2 * w2b, r3b = 2.0 * r.r3 * w3b;
+  const double p23b = fma(r0b, r.s1, r1b * r.s0), p01b = fma(r2b, r.s3, r3b * r.s2);
+  const double s0b = fma(r1b, r.p23, p01b * r.s1), s1b = fma(r0b, r.p23, p01b * r.s0);
+  const double s2b = fma(r3b, r.p01, p23b * r.s3), s3b = fma(r2b, r.p01, p23b * r.s2);
+  const double Qb[4] = {kW7c0 * s0b, kW7c1 * s1b, kW7c2 * s2b, kW7c3 * s3b};
+  double xb[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  // z2 (indicators 0 and 2), z3 (1 and 3)
+  xb[2] += 2.0 * kW7D3 * r.x2 * (Qb[0] + Qb[2]);
+  xb[3] += 2.0 * kW7D3 * r.x3 * (Qb[1] + Qb[3]);
+  {  // Q0(x0, x1, x2)
+    const double Ab = 2.0 * 547.0 * r.A[0] * Qb[0], Bb = 2.0 * 155.46617915904935 * r.B[0] * Qb[0];
+    xb[0] += Ab; xb[1] += fma(-2.5484460694698354, Ab, Bb);
+    xb[2] += fma(1.6946983546617915, Ab, -1.4896519285042333 * Bb);
+  }
+  {  // Q1(x1, x2, x3)
+    const double Ab = 2.0 * 267.0 * r.A[1] * Qb[1], Bb = 2.0 * 318.50187265917606 * r.B[1] * Qb[1];
+    xb[1] += Ab; xb[2] += fma(-2.0749063670411987, Ab, Bb);
+    xb[3] += fma(0.92509363295880154, Ab, -0.6326434619002822 * Bb);
+  }
+  {  // Q1(x4, x3, x2)
+    const double Ab = 2.0 * 267.0 * r.A[2] * Qb[2], Bb = 2.0 * 318.50187265917606 * r.B[2] * Qb[2];
+    xb[4] += Ab; xb[3] += fma(-2.0749063670411987, Ab, Bb);
+    xb[2] += fma(0.92509363295880154, Ab, -0.6326434619002822 * Bb);
+  }
+  {  // Q0(x5, x4, x3)
+    const double Ab = 2.0 * 547.0 * r.A[3] * Qb[3], Bb = 2.0 * 155.46617915904935 * r.B[3] * Qb[3];
+    xb[5] += Ab; xb[4] += fma(-2.5484460694698354, Ab, Bb);
+    xb[3] += fma(1.6946983546617915, Ab, -1.4896519285042333 * Bb);
+  }
+  xb[0] += 0.25 * q0b;
+  xb[1] += (-5.0 / 6.0) * q0b + (-1.0 / 12.0) * q1b;
+  xb[2] += (13.0 / 12.0) * q0b + (1.0 / 3.0) * q1b + (1.0 / 12.0) * q2b;
+  xb[3] += 0.25 * q1b + 0.5 * q2b + 0.75 * q3b;
+  xb[4] += (-1.0 / 12.0) * q2b + (-1.0 / 3.0) * q3b;
+  xb[5] += (1.0 / 12.0) * q3b;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) { fb[j] -= xb[j]; fb[j + 1] += xb[j]; }
+}
+
+// One field's F = F^+ + F^- with the reconstruction REC and its reverse:
+// returns F and adds Fb dF/dw to wpb[0..SW-1], wmb[0..SW-1] (w^- mirrored).
+// e4 as in rec_nd.
+template <int REC>
+__device__ __forceinline__ double rec_pair_fwd_adj(const double* wp, const double* wm,
+                                                   const double* e4, double Fb, double* wpb,
+                                                   double* wmb) {
+  if constexpr (REC == 5) {
+    return weno5_pair_fwd_adj(wp, wm, e4, Fb, wpb, wmb);
+  } else if constexpr (REC == 6) {
+    C6 P, M;
+    c6_fwd(wp[0], wp[1], wp[2], wp[3], wp[4], wp[5], e4[3], P);
+    c6_fwd(wm[5], wm[4], wm[3], wm[2], wm[1], wm[0], e4[3], M);
+    const double rpm = 1.0 / (P.den * M.den);
+    const double idp = rpm * M.den, idm = rpm * P.den;
+    const double F = (wp[2] + wm[3]) + fma(P.num, idp, M.num * idm);
+    double fb[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, gb[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    c6_rev(P, Fb * idp, -Fb * P.num * idp * idp, fb);
+    c6_rev(M, Fb * idm, -Fb * M.num * idm * idm, gb);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) { wpb[k] += fb[k]; wmb[5 - k] += gb[k]; }
+    wpb[2] += Fb;
+    wmb[3] += Fb;
+    return F;
+  } else {
+    W7 P, M;
+    w7_fwd(wp[0], wp[1], wp[2], wp[3], wp[4], wp[5], wp[6], e4, P);
+    w7_fwd(wm[7], wm[6], wm[5], wm[4], wm[3], wm[2], wm[1], e4, M);
+    const double rpm = 1.0 / (P.den * M.den);
+    const double idp = rpm * M.den, idm = rpm * P.den;
+    const double F = (wp[3] + wm[4]) + fma(P.num, idp, M.num * idm);
+    double fb[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, gb[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    w7_rev(P, Fb * idp, -Fb * P.num * idp * idp, fb);
+    w7_rev(M, Fb * idm, -Fb * M.num * idm * idm, gb);
+#pragma unroll
+    for (int k = 0; k < 7; ++k) { wpb[k] += fb[k]; wmb[7 - k] += gb[k]; }
+    wpb[3] += Fb;
+    wmb[4] += Fb;
+    return F;
+  }
+}
+
 // d c_p,s / dT at a clamped tau (0 outside the polynomial range)
 __device__ __forceinline__ double dcp_s(const Params& p, int s, double T) {
   const double tau = (T - p.T_lo) * p.inv_span;
@@ -120,7 +324,7 @@ __device__ __forceinline__ void aadd(double* p, double v) {
 // through F_LF of Eq. 19 (alpha through the cell with the larger |u_d| + c)
 // to U, u_d, p and c of the two cells (scattered into Qb). Gc returns the
 // adjoint of F_hat (Gb itself when the blend is inactive).
-template <int DIM, int NS, int D>
+template <int DIM, int NS, int D, int REC>
 __device__ __forceinline__ void pos_blend_adj(const Params& p, const double* __restrict__ q0,
                                               double* __restrict__ qb0, long long PC, long long sd,
                                               double dt, const double* Gb, double* Gc) {
@@ -133,7 +337,7 @@ __device__ __forceinline__ void pos_blend_adj(const Params& p, const double* __r
 #pragma unroll
   for (int v = 0; v < NV; ++v) Gh[v] = 0.0;
   uint32_t st = 0;
-  conv_flux<DIM, NS, D, 5>(p, q0, PC, sd, Gh, st);
+  conv_flux<DIM, NS, D, REC>(p, q0, PC, sd, Gh, st);
   const double lam2 = 2.0 * DIM * dt * p.inv_dx[D];
   double Ua[NV], Ub[NV], Fa[NV], Fb[NV], Flf[NV];
 #pragma unroll
@@ -261,7 +465,7 @@ __device__ __forceinline__ void pos_blend_adj(const Params& p, const double* __r
 // ================================================================ k_face_adj
 // Per face of direction D: Gbar = scale (Rbar_right - Rbar_left)/dx (Rbar = 0
 // outside the interior), then the reverse of face_one.
-template <int DIM, int NS, int D, bool POS = false>
+template <int DIM, int NS, int D, bool POS = false, int REC = 5>
 __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk,
                                          const double* __restrict__ Q,
                                          const double* __restrict__ Rbar, double scale,
@@ -269,6 +473,8 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
   using L = Lay<DIM, NS>;
   constexpr int NV = L::NV;
   constexpr int IE = DIM + 1;
+  constexpr int SO = REC == 7 ? 3 : 2;  // stencil cells left of the left cell
+  constexpr int SW = 2 * SO + 2;        // stencil width
   int id[3] = {fi, fj, fk};
   id[D] -= 1;  // left cell
   const long long PC = p.pcells;
@@ -299,7 +505,7 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
     // positivity-preserving blend inside an RK stage
     double Gc[NV];
     if constexpr (POS) {
-      pos_blend_adj<DIM, NS, D>(p, q0, qb0, PC, sd, dt, Gb, Gc);
+      pos_blend_adj<DIM, NS, D, REC>(p, q0, qb0, PC, sd, dt, Gb, Gc);
     } else {
 #pragma unroll
       for (int v = 0; v < NV; ++v) Gc[v] = Gb[v];
@@ -366,12 +572,12 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
 #pragma unroll
     for (int s = 0; s < NS - 1; ++s) { dphi[s] = phi[s] - phiN; gs[s] = dphi[s] * hic2; }
     const double gr = phiN * hic2, gE = Gam * hic2;
-    double rho_m[6], p_m[6], hun[6], gUh[6], unm[6], cmv[6];
+    double rho_m[SW], p_m[SW], hun[SW], gUh[SW], unm[SW], cmv[SW];
     double am = 0.0, ap = 0.0, a0 = 0.0;
     int im = 0, ipp = 0, i0 = 0;
 #pragma unroll
-    for (int m = 0; m < 6; ++m) {
-      const int o = m - 2;
+    for (int m = 0; m < SW; ++m) {
+      const int o = m - SO;
       rho_m[m] = QF(L::U, o);
       unm[m] = QF(L::UN + D, o);
       p_m[m] = QF(L::P, o);
@@ -390,13 +596,19 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
       gUh[m] = g;
     }
     const double eps12 = 12.0 * p.weno_eps;
-    const double e12c[3] = {eps12 * kWc0, eps12 * kWc1, eps12 * kWc2};
+    double e12c[4];
+    if constexpr (REC == 7) {
+      const double e240 = 240.0 * p.weno_eps;
+      e12c[0] = e240 * kW7c0; e12c[1] = e240 * kW7c1; e12c[2] = e240 * kW7c2; e12c[3] = e240 * kW7c3;
+    } else {
+      e12c[0] = eps12 * kWc0; e12c[1] = eps12 * kWc1; e12c[2] = eps12 * kWc2; e12c[3] = eps12;
+    }
     const double chc = c * hic2;
     const double ha_m = 0.5 * am, ha_p = 0.5 * ap, ha0 = 0.5 * a0;
     const double hlmn_m = 0.5 * (-Gam * un - c) * hic2, hlmn_p = 0.5 * (-Gam * un + c) * hic2;
     const double lE_a = Gam * hic2;
     const double hlmn_e = 0.5 * Gam * un * ic2, lE_e = -Gam * ic2;
-    double wp[6], wm[6];
+    double wp[SW], wm[SW];
     // ================= reverse =================
     // back-projection of the dense columns: adjoints of the reconstructed
     // fields depend on Gbar and the face state only
@@ -415,9 +627,9 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
     const double Fmb = Sb - Dlb, Fpb = Sb + Dlb, Feb = Sb - c2 * iGam * Gc[IE];
     double Fm = 0.0, Fp = 0.0, Fe = 0.0;
     // per-field reverse; stencil adjoints accumulated here
-    double rhob[6], pb[6], hunb[6], gUhb[6], mnb[6];
+    double rhob[SW], pb[SW], hunb[SW], gUhb[SW], mnb[SW];
 #pragma unroll
-    for (int m = 0; m < 6; ++m) { rhob[m] = 0.0; pb[m] = 0.0; hunb[m] = 0.0; gUhb[m] = 0.0; mnb[m] = 0.0; }
+    for (int m = 0; m < SW; ++m) { rhob[m] = 0.0; pb[m] = 0.0; hunb[m] = 0.0; gUhb[m] = 0.0; mnb[m] = 0.0; }
     double hamb = 0.0, hapb = 0.0, ha0b = 0.0, chcb = 0.0, Gamb = 0.0, hic2b = 0.0, ic2b = 0.0;
 #pragma unroll
     for (int fld = 0; fld < 3; ++fld) {
@@ -426,14 +638,14 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
       const double lE = fld == 2 ? lE_e : lE_a;
       const double Fb = fld == 0 ? Fmb : (fld == 1 ? Fpb : Feb);
       const double schc = fld == 0 ? -chc : chc;
-      double LUv[6], nUv[6], pqr[6];
+      double LUv[SW], nUv[SW], pqr[SW];
 #pragma unroll
-      for (int m = 0; m < 6; ++m) {
+      for (int m = 0; m < SW; ++m) {
         double LU, nU = 0.0;
         if (fld == 2) {
           LU = fma(-2.0, gUh[m], rho_m[m]);
         } else {
-          nU = fma(-un, rho_m[m], QF(L::U + 1 + D, m - 2));
+          nU = fma(-un, rho_m[m], QF(L::U + 1 + D, m - SO));
           LU = fma(schc, nU, gUh[m]);
         }
         LUv[m] = LU;
@@ -443,12 +655,12 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
         wp[m] = fma(hun[m] + ha, LU, pq);
         wm[m] = fma(hun[m] - ha, LU, pq);
       }
-      double wpb[6] = {0, 0, 0, 0, 0, 0}, wmb[6] = {0, 0, 0, 0, 0, 0};
-      const double F = weno5_pair_fwd_adj(wp, wm, e12c, Fb, wpb, wmb);
+      double wpb[SW] = {}, wmb[SW] = {};
+      const double F = rec_pair_fwd_adj<REC>(wp, wm, e12c, Fb, wpb, wmb);
       if (fld == 0) Fm = F; else if (fld == 1) Fp = F; else Fe = F;
       double hab = 0.0, hlb = 0.0, lEb = 0.0;
 #pragma unroll
-      for (int m = 0; m < 6; ++m) {
+      for (int m = 0; m < SW; ++m) {
         // w+- = (hun +- ha) LU + p pqr: with s = wb+ + wb-, d = wb+ - wb-,
         // LUb = hun s + ha d, hunb += s (LU + p lE), hab += d LU, pb += s pqr,
         // and (lE, hl) take s p (hun, 1)
@@ -502,29 +714,29 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
       iGamb -= c2 * Fe * Gc[IE];
     }
     // tangential momenta and species (eigenvalue u, no pressure term)
-    double hp0b[6], hm0b[6];
+    double hp0b[SW], hm0b[SW];
 #pragma unroll
-    for (int m = 0; m < 6; ++m) { hp0b[m] = 0.0; hm0b[m] = 0.0; }
+    for (int m = 0; m < SW; ++m) { hp0b[m] = 0.0; hm0b[m] = 0.0; }
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
       if (a == D) continue;
       const double Fb = Gc[1 + a] + ub[a] * Gc[IE];
-      double LUv[6];
+      double LUv[SW];
 #pragma unroll
-      for (int m = 0; m < 6; ++m) {
-        LUv[m] = fma(-ub[a], rho_m[m], QF(L::U + 1 + a, m - 2));
+      for (int m = 0; m < SW; ++m) {
+        LUv[m] = fma(-ub[a], rho_m[m], QF(L::U + 1 + a, m - SO));
         wp[m] = (hun[m] + ha0) * LUv[m];
         wm[m] = (hun[m] - ha0) * LUv[m];
       }
-      double wpb[6] = {0, 0, 0, 0, 0, 0}, wmb[6] = {0, 0, 0, 0, 0, 0};
-      const double Fk = weno5_pair_fwd_adj(wp, wm, e12c, Fb, wpb, wmb);
+      double wpb[SW] = {}, wmb[SW] = {};
+      const double Fk = rec_pair_fwd_adj<REC>(wp, wm, e12c, Fb, wpb, wmb);
       ubb[a] += Fk * Gc[IE];
 #pragma unroll
-      for (int m = 0; m < 6; ++m) {
+      for (int m = 0; m < SW; ++m) {
         const double LUb = wpb[m] * (hun[m] + ha0) + wmb[m] * (hun[m] - ha0);
         hp0b[m] += wpb[m] * LUv[m];
         hm0b[m] += wmb[m] * LUv[m];
-        QB(L::U + 1 + a, m - 2, LUb);
+        QB(L::U + 1 + a, m - SO, LUb);
         ubb[a] -= LUb * rho_m[m];
         rhob[m] -= LUb * ub[a];
       }
@@ -533,29 +745,29 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
 #pragma unroll
     for (int s = 0; s < NS - 1; ++s) {
       const double Fb = Gc[IE + 1 + s] - dphi[s] * iGam * Gc[IE];
-      double LUv[6];
+      double LUv[SW];
 #pragma unroll
-      for (int m = 0; m < 6; ++m) {
-        LUv[m] = fma(-Yb[s], rho_m[m], QF(L::U + IE + 1 + s, m - 2));
+      for (int m = 0; m < SW; ++m) {
+        LUv[m] = fma(-Yb[s], rho_m[m], QF(L::U + IE + 1 + s, m - SO));
         wp[m] = (hun[m] + ha0) * LUv[m];
         wm[m] = (hun[m] - ha0) * LUv[m];
       }
-      double wpb[6] = {0, 0, 0, 0, 0, 0}, wmb[6] = {0, 0, 0, 0, 0, 0};
-      const double Fk = weno5_pair_fwd_adj(wp, wm, e12c, Fb, wpb, wmb);
+      double wpb[SW] = {}, wmb[SW] = {};
+      const double Fk = rec_pair_fwd_adj<REC>(wp, wm, e12c, Fb, wpb, wmb);
       dphib[s] = -iGam * Fk * Gc[IE];
       iGamb -= dphi[s] * Fk * Gc[IE];
 #pragma unroll
-      for (int m = 0; m < 6; ++m) {
+      for (int m = 0; m < SW; ++m) {
         const double LUb = wpb[m] * (hun[m] + ha0) + wmb[m] * (hun[m] - ha0);
         hp0b[m] += wpb[m] * LUv[m];
         hm0b[m] += wmb[m] * LUv[m];
-        QB(L::U + IE + 1 + s, m - 2, LUb);
+        QB(L::U + IE + 1 + s, m - SO, LUb);
         Ybb[s] -= LUb * rho_m[m];
         rhob[m] -= LUb * Yb[s];
       }
     }
 #pragma unroll
-    for (int m = 0; m < 6; ++m) {
+    for (int m = 0; m < SW; ++m) {
       hunb[m] += hp0b[m] + hm0b[m];
       ha0b += hp0b[m] - hm0b[m];
     }
@@ -568,8 +780,8 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
 #pragma unroll
     for (int s = 0; s < NS - 1; ++s) gsb[s] = 0.0;
 #pragma unroll
-    for (int m = 0; m < 6; ++m) {
-      const int o = m - 2;
+    for (int m = 0; m < SW; ++m) {
+      const int o = m - SO;
       const double g = gUhb[m];
       grb += g * rho_m[m];
       rhob[m] += g * gr;
@@ -806,20 +1018,20 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
 #undef QB
 }
 
-template <int DIM, int NS, int D>
+template <int DIM, int NS, int D, int REC = 5>
 __global__ void __launch_bounds__(128)
 k_face_adj(const __grid_constant__ Params p, const double* __restrict__ Q,
            const double* __restrict__ Rbar, double scale, double* __restrict__ Qb) {
   const int nf0 = p.n[0] + (D == 0), nf1 = p.n[1] + (D == 1), nf2 = p.n[2] + (D == 2);
   const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= (long long)nf0 * nf1 * nf2) return;
-  face_adj<DIM, NS, D>(p, (int)(f % nf0), (int)((f / nf0) % nf1), (int)(f / ((long long)nf0 * nf1)),
-                       Q, Rbar, scale, Qb);
+  face_adj<DIM, NS, D, false, REC>(p, (int)(f % nf0), (int)((f / nf0) % nf1),
+                                   (int)(f / ((long long)nf0 * nf1)), Q, Rbar, scale, Qb);
 }
 
 // the same inside an RK stage of a handle with the positivity-preserving
 // blend: dtp holds the stage's time step
-template <int DIM, int NS, int D>
+template <int DIM, int NS, int D, int REC = 5>
 __global__ void __launch_bounds__(128)
 k_face_adj_pos(const __grid_constant__ Params p, const double* __restrict__ Q,
                const double* __restrict__ Rbar, double scale, double* __restrict__ Qb,
@@ -827,8 +1039,8 @@ k_face_adj_pos(const __grid_constant__ Params p, const double* __restrict__ Q,
   const int nf0 = p.n[0] + (D == 0), nf1 = p.n[1] + (D == 1), nf2 = p.n[2] + (D == 2);
   const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= (long long)nf0 * nf1 * nf2) return;
-  face_adj<DIM, NS, D, true>(p, (int)(f % nf0), (int)((f / nf0) % nf1),
-                             (int)(f / ((long long)nf0 * nf1)), Q, Rbar, scale, Qb, *dtp);
+  face_adj<DIM, NS, D, true, REC>(p, (int)(f % nf0), (int)((f / nf0) % nf1),
+                                  (int)(f / ((long long)nf0 * nf1)), Q, Rbar, scale, Qb, *dtp);
 }
 
 // ================================================================ k_prim_adj
@@ -1190,18 +1402,6 @@ k_mixing(const __grid_constant__ Params p, const double* __restrict__ U, int sp,
   if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
 }
 
-__global__ void k_sum_partials(const double* __restrict__ part, int n, double* out) {
-  __shared__ double sh[256];
-  double acc = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += part[i];
-  sh[threadIdx.x] = acc;
-  __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) *out = sh[0];
-}
 
 // ====================================================== k_from_prim_adj ===
 // Reverse of k_from_prim: Ubar -> Pbar (overwritten).
@@ -1268,15 +1468,5 @@ k_from_prim_adj(const __grid_constant__ Params p, const double* __restrict__ P,
   for (int s = 0; s < NS - 1; ++s) Pb[(DIM + 2 + s) * C + c] = Yb[s];
 }
 
-// out = a x + b y + c z (elementwise; any of x, y, z may alias out)
-__global__ void k_lincomb(long long n, double a, const double* x, double b, const double* y,
-                          double c, const double* z, double* out) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  double r = a * x[i];
-  if (y) r = fma(b, y[i], r);
-  if (z) r = fma(c, z[i], r);
-  out[i] = r;
-}
 
 }  // namespace xf

@@ -9,7 +9,6 @@
 #include "xf.h"
 #include "xf_device.cuh"
 #include "xf_internal.h"
-#include "xf_adjoint.cuh"
 
 namespace {
 
@@ -32,6 +31,32 @@ void set_err(const char* what, cudaError_t e) {
 
 inline unsigned blocks(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
+// reduction of the per-block partial sums of the mixing objective (one block)
+__global__ void k_sum_partials(const double* __restrict__ part, int n, double* out) {
+  __shared__ double sh[256];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += part[i];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sh[0];
+}
+
+// out = a x + b y + c z (elementwise; any of x, y, z may alias out)
+__global__ void k_lincomb(long long n, double a, const double* x, double b, const double* y,
+                          double c, const double* z, double* out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double r = a * x[i];
+  if (y) r = fma(b, y[i], r);
+  if (z) r = fma(c, z[i], r);
+  out[i] = r;
+}
+
+
 using PrimFn = void (*)(const xf::Params&, const double*, const double*, double*, double*,
                         uint32_t*, unsigned long long*, int, cudaStream_t);
 using GradFn = void (*)(const xf::Params&, double*, cudaStream_t);
@@ -40,14 +65,7 @@ using FaceFn = void (*)(const xf::Params&, const double*, double*, uint32_t*, co
 using UpdFn = void (*)(const xf::Params&, const double*, const double*, const double*,
                        const double*, const double*, double*, const double*, int, cudaStream_t);
 using FromPrimFn = void (*)(const xf::Params&, const double*, double*, double*, cudaStream_t);
-using FaceAdjFn = void (*)(const xf::Params&, const double*, const double*, double, double*,
-                           cudaStream_t);
-using FaceAdjPosFn = void (*)(const xf::Params&, const double*, const double*, double, double*,
-                              const double*, cudaStream_t);
-using CellAdjFn = void (*)(const xf::Params&, const double*, const double*, double*, cudaStream_t);
-using GradAdjFn = void (*)(const xf::Params&, double*, cudaStream_t);
-using MixFn = void (*)(const xf::Params&, const double*, int, double, double*, double*,
-                       cudaStream_t);
+
 
 struct Table {
   PrimFn prim;
@@ -58,12 +76,7 @@ struct Table {
   UpdFn update;
   FromPrimFn from_prim;
   int nq;
-  FaceAdjFn face_adj[3];
-  FaceAdjPosFn face_adj_pos[3];  // inside an RK stage with the positivity blend
-  GradAdjFn grad_adj;
-  CellAdjFn prim_adj;
-  CellAdjFn from_prim_adj;
-  MixFn mixing;
+  XfAdjTable adj;  // reverse-mode launchers (xf_adjoint_launch.cu)
 };
 
 template <int DIM, int NS>
@@ -94,45 +107,14 @@ struct Launch {
                         cudaStream_t s) {
     xf::k_from_prim<DIM, NS><<<blocks(p.cells, 256), 256, 0, s>>>(p, P, U, T);
   }
-  template <int D>
-  static void face_adj(const xf::Params& p, const double* Q, const double* Rb, double scale,
-                       double* Qb, cudaStream_t s) {
-    if constexpr (D < DIM) {
-      const long long nf =
-          (long long)(p.n[0] + (D == 0)) * (p.n[1] + (D == 1)) * (p.n[2] + (D == 2));
-      xf::k_face_adj<DIM, NS, D><<<blocks(nf, 128), 128, 0, s>>>(p, Q, Rb, scale, Qb);
-    }
-  }
-  template <int D>
-  static void face_adj_pos(const xf::Params& p, const double* Q, const double* Rb, double scale,
-                           double* Qb, const double* dt, cudaStream_t s) {
-    if constexpr (D < DIM) {
-      const long long nf =
-          (long long)(p.n[0] + (D == 0)) * (p.n[1] + (D == 1)) * (p.n[2] + (D == 2));
-      xf::k_face_adj_pos<DIM, NS, D><<<blocks(nf, 128), 128, 0, s>>>(p, Q, Rb, scale, Qb, dt);
-    }
-  }
-  static void grad_adj(const xf::Params& p, double* Qb, cudaStream_t s) {
-    xf::k_grad_adj<DIM, NS><<<blocks(p.pcells, 256), 256, 0, s>>>(p, Qb);
-  }
-  static void prim_adj(const xf::Params& p, const double* Q, const double* Qb, double* Ub,
-                       cudaStream_t s) {
-    xf::k_prim_adj<DIM, NS><<<blocks(p.pcells, 128), 128, 0, s>>>(p, Q, Qb, Ub);
-  }
-  static void from_prim_adj(const xf::Params& p, const double* P, const double* Ub, double* Pb,
-                            cudaStream_t s) {
-    xf::k_from_prim_adj<DIM, NS><<<blocks(p.cells, 256), 256, 0, s>>>(p, P, Ub, Pb);
-  }
-  static void mixing(const xf::Params& p, const double* U, int sp, double dV, double* part,
-                     double* Ub, cudaStream_t s) {
-    xf::k_mixing<DIM, NS><<<blocks(p.cells, 256), 256, 0, s>>>(p, U, sp, dV, part, Ub);
-  }
   static Table table() {
-    return Table{prim, grad, {face<0>, face<1>, face<2>}, {face<0, 6>, face<1, 6>, face<2, 6>},
-                 {face<0, 7>, face<1, 7>, face<2, 7>}, update, from_prim, xf::Lay<DIM, NS>::NQ,
-                 {face_adj<0>, face_adj<1>, face_adj<2>},
-                 {face_adj_pos<0>, face_adj_pos<1>, face_adj_pos<2>}, grad_adj, prim_adj,
-                 from_prim_adj, mixing};
+    Table t{prim, grad, {face<0>, face<1>, face<2>}, {face<0, 6>, face<1, 6>, face<2, 6>},
+            {face<0, 7>, face<1, 7>, face<2, 7>}, update, from_prim, xf::Lay<DIM, NS>::NQ,
+            XfAdjTable{}};
+    xf_internal_adj_fill5(DIM, NS, &t.adj);
+    xf_internal_adj_fill6(DIM, NS, &t.adj);
+    xf_internal_adj_fill7(DIM, NS, &t.adj);
+    return t;
   }
 };
 
@@ -431,11 +413,12 @@ xf_status rhs_adjoint_impl(xf_handle* h, const double* U, const double* Rbar, do
   XF_CUDA(cudaMemsetAsync(h->Qb, 0, sizeof(double) * nq_of(h->tab, p) * p.pcells, s));
   for (int d = 0; d < p.dim; ++d)
     timed(h, XF_PROF_FACE_ADJ, s, [&] {
-      if (p.positivity && dtp) h->tab.face_adj_pos[d](p, h->Q, Rbar, scale, h->Qb, dtp, s);
-      else h->tab.face_adj[d](p, h->Q, Rbar, scale, h->Qb, s);
+      const int r = p.weno - 5;
+      if (p.positivity && dtp) h->tab.adj.face_adj_pos[r][d](p, h->Q, Rbar, scale, h->Qb, dtp, s);
+      else h->tab.adj.face_adj[r][d](p, h->Q, Rbar, scale, h->Qb, s);
     });
-  if (p.viscous) timed(h, XF_PROF_GRAD, s, [&] { h->tab.grad_adj(p, h->Qb, s); });
-  timed(h, XF_PROF_PRIM_ADJ, s, [&] { h->tab.prim_adj(p, h->Q, h->Qb, Ubar, s); });
+  if (p.viscous) timed(h, XF_PROF_GRAD, s, [&] { h->tab.adj.grad_adj(p, h->Qb, s); });
+  timed(h, XF_PROF_PRIM_ADJ, s, [&] { h->tab.adj.prim_adj(p, h->Q, h->Qb, Ubar, s); });
   XF_CUDA(cudaGetLastError());
   return XF_OK;
 }
@@ -443,7 +426,7 @@ xf_status rhs_adjoint_impl(xf_handle* h, const double* U, const double* Rbar, do
 void lincomb(const xf_handle* h, double a, const double* x, double b, const double* y, double c,
              const double* z, double* out, cudaStream_t s) {
   const long long n = (long long)h->p.nv * h->p.cells;
-  xf::k_lincomb<<<blocks(n, 256), 256, 0, s>>>(n, a, x, b, y, c, z, out);
+  k_lincomb<<<blocks(n, 256), 256, 0, s>>>(n, a, x, b, y, c, z, out);
 }
 
 __global__ void k_probe_fp64(double* out, long long iters, double a) {
@@ -676,13 +659,13 @@ xf_status xf_clear_status(xf_handle* h, void* stream) {
 
 xf_status xf_rhs_adjoint(xf_handle* h, const double* U, const double* dUdt_bar, double* U_bar,
                          void* stream) {
-  if (!h || !U || !dUdt_bar || !U_bar || h->p.weno != 5) return XF_ERR_ARG;
+  if (!h || !U || !dUdt_bar || !U_bar) return XF_ERR_ARG;
   if (!is_device_ptr(U) || !is_device_ptr(dUdt_bar) || !is_device_ptr(U_bar)) return XF_ERR_ARG;
   return rhs_adjoint_impl(h, U, dUdt_bar, 1.0, U_bar, (cudaStream_t)stream);
 }
 
 xf_status xf_step_rk3_adjoint(xf_handle* h, double dt, double* U_bar, void* stream) {
-  if (!h || !U_bar || !(dt > 0.0) || h->p.weno != 5) return XF_ERR_ARG;
+  if (!h || !U_bar || !(dt > 0.0)) return XF_ERR_ARG;
   if (!is_device_ptr(U_bar)) return XF_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   xf_status st = ensure_adjoint_buffers(h);
@@ -742,8 +725,8 @@ xf_status xf_objective_mixing(xf_handle* h, const double* U, int species, double
   const xf::Params& p = h->p;
   double dV = 1.0;
   for (int a = 0; a < p.dim; ++a) dV /= p.inv_dx[a];
-  h->tab.mixing(p, U, species, dV, h->part, U_bar, s);
-  xf::k_sum_partials<<<1, 256, 0, s>>>(h->part, (int)blocks(p.cells, 256), J_dev);
+  h->tab.adj.mixing(p, U, species, dV, h->part, U_bar, s);
+  k_sum_partials<<<1, 256, 0, s>>>(h->part, (int)blocks(p.cells, 256), J_dev);
   XF_CUDA(cudaGetLastError());
   return XF_OK;
 }
@@ -752,7 +735,7 @@ xf_status xf_set_primitive_adjoint(xf_handle* h, const double* P, const double* 
                                    double* P_bar, void* stream) {
   if (!h || !P || !U_bar || !P_bar) return XF_ERR_ARG;
   if (!is_device_ptr(P) || !is_device_ptr(U_bar) || !is_device_ptr(P_bar)) return XF_ERR_ARG;
-  h->tab.from_prim_adj(h->p, P, U_bar, P_bar, (cudaStream_t)stream);
+  h->tab.adj.from_prim_adj(h->p, P, U_bar, P_bar, (cudaStream_t)stream);
   XF_CUDA(cudaGetLastError());
   return XF_OK;
 }

@@ -257,3 +257,55 @@ def test_step_adjoint_with_positivity_blend_matches_oracle_jvp(name, tol):
     rhs = [np.sum(W * JV[k]) for k in range(8)]
     _dot_check(lhs, rhs, tol)
     s.close()
+
+
+
+@pytest.mark.parametrize("weno", [6, 7])
+@pytest.mark.parametrize("name", ["smooth2d_n3_periodic", "sbi2d_n4_visc", "sbi3d_n5_visc",
+                                  "smooth1d_n4_inviscid"])
+def test_rhs_adjoint_with_cu6_and_weno7_matches_oracle_jvp(name, weno):
+    """The reverse of the WENO-CU6 and WENO7 reconstructions (indicators,
+    weights, candidates; CU6's beta_6 and tau) inside the face adjoint,
+    against the oracle's dual-number JVP of the same scheme."""
+    import torch
+    case = CASES[name]
+    o = Oracle(case, weno=weno)
+    U, T = o.prim_to_cons()
+    rng = np.random.default_rng(18 + weno)
+    V = _dirs(rng, U, 8)
+    R, JV, _, st = o.rhs_jvp(U, V, T.copy())
+    W = rng.normal(size=U.shape)
+    s = gpu_solver(case, weno=weno)
+    s.set_state(dev(U), dev(T))
+    Ub = torch.zeros((case.n_v, case.cells), dtype=torch.float64, device="cuda")
+    s.rhs_adjoint(dev(U), dev(W), Ub)
+    torch.cuda.synchronize()
+    assert s.status() == 0
+    Ubar = Ub.cpu().numpy()
+    lhs = [np.sum(Ubar * V[k]) for k in range(8)]
+    rhs = [np.sum(W * JV[k]) for k in range(8)]
+    _dot_check(lhs, rhs, 1e-10)
+    s.close()
+
+
+@pytest.mark.parametrize("weno", [6, 7])
+def test_step_adjoint_with_cu6_and_weno7_matches_oracle_jvp(weno):
+    import torch
+    case = CASES["smooth2d_n3_periodic"]
+    o = Oracle(case, weno=weno)
+    U, T = o.prim_to_cons()
+    dt = 0.5 * o.dt(U, T.copy())
+    rng = np.random.default_rng(20 + weno)
+    V = _dirs(rng, U, 8)
+    U1, JV, _, _ = o.rk3_jvp(U, V, T.copy(), dt, 1)
+    W = rng.normal(size=U.shape)
+    s = gpu_solver(case, weno=weno)
+    s.set_state(dev(U), dev(T))
+    Ub = dev(W).clone()
+    s.step_adjoint(dt, Ub)
+    torch.cuda.synchronize()
+    Ubar = Ub.cpu().numpy()
+    lhs = [np.sum(Ubar * V[k]) for k in range(8)]
+    rhs = [np.sum(W * JV[k]) for k in range(8)]
+    _dot_check(lhs, rhs, 1e-10)
+    s.close()

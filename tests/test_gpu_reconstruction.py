@@ -2,7 +2,8 @@
 weno = 6) and WENO7-JS (ref. 36, weno = 7, 8-cell stencil and 4 ghost
 layers). Parity with the oracle's same scheme on the RHS, one step and ten
 steps; the design order on the advected density wave; and the entry points
-that support WENO5 only (the adjoint and the batched form) refuse them.
+that need one scheme (a batch) refuse a mix. Their adjoints are checked in
+test_gpu_adjoint.py.
 
 Tolerances as for WENO5: 1e-11 for one RHS and one step, 1e-8 after ten steps
 (per-field max |gpu - ref| / max |ref|).
@@ -110,22 +111,12 @@ def test_design_order_density_wave(weno, ns, power, order):
 
 
 @pytest.mark.parametrize("weno", WENOS)
-def test_adjoint_refuses_and_batch_needs_one_scheme(weno):
+def test_batch_needs_one_scheme(weno):
+    """One batch shares one reconstruction: mixing schemes is refused."""
     import ctypes as C
-    import torch
-    from paper_2403_05910_b300.xf import (XF_ERR_ARG, Grid, Opts, Thermo, XFError, lib,
-                                          structs)
-    case = cases.config(1, n=(24, 12))
-    U, T = Oracle(case).prim_to_cons()
-    s = gpu_solver(case, weno=weno)
-    s.set_state(dev(U), dev(T))
-    Ub = torch.zeros((case.n_v, case.cells), dtype=torch.float64, device="cuda")
-    with pytest.raises(XFError):
-        s.rhs_adjoint(dev(U), dev(U), Ub)
-    with pytest.raises(XFError):
-        s.step_adjoint(1e-5, Ub)
-    s.close()
-    # one batch shares one reconstruction
+    from paper_2403_05910_b300 import build
+    build.build()
+    from paper_2403_05910_b300.xf import XF_ERR_ARG, Grid, Opts, Thermo, lib, structs
     c2 = cases.config(1, n=(20, 10))
     g5, t5, o5, k5 = structs(c2)
     g6, t6, o6, k6 = structs(c2, weno=weno)
