@@ -4,13 +4,19 @@
  * arXiv 2403.05910 (XFluids), Sec. II.A Eq. 1-7, on a uniform structured grid,
  * in FP64, on one GPU. One right-hand-side evaluation L(U) (Eq. 13) consists of
  *   - primitive recovery with the Newton temperature solve of Eq. 21;
- *   - per direction, characteristic-space WENO5 reconstruction (Eq. 14-15) with
- *     local Lax-Friedrichs splitting, the multicomponent eigensystem at a
- *     Roe-averaged face state, and the partial eigensystem reconstruction (PER,
- *     Sec. III.D.3: one eigenvalue, one left row and one right column per field);
+ *   - per direction, characteristic-space reconstruction (Eq. 14-15: WENO5-JS,
+ *     WENO-CU6 or WENO7-JS) with local Lax-Friedrichs splitting, the
+ *     multicomponent eigensystem at a Roe-averaged face state, and the partial
+ *     eigensystem reconstruction (PER, Sec. III.D.3: one eigenvalue, one left
+ *     row and one right column per field), optionally blended with the local
+ *     Lax-Friedrichs flux to keep partial densities positive (Eq. 17-20);
  *   - 4th-order central viscous and species-diffusion fluxes (Eq. 3-6, Eq. 22,
- *     Eq. 29 transport fits, constant Lewis number);
+ *     Eq. 29 transport fits, a constant Lewis number or the mixture-averaged
+ *     diffusivities of Eq. 25-26);
  *   - the conservative flux difference (Eq. 13) and the SSP-RK3 stages (Eq. 16).
+ * On top: the reverse mode (vector-Jacobian products) of the RHS and of a
+ * step, and a batched form that advances many 2D grids in one persistent
+ * kernel per stage.
  *
  * Conventions (all entry points):
  *   - FP64 throughout. Field arrays are structure-of-arrays [n_v][nz][ny][nx]
