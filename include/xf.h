@@ -184,6 +184,13 @@ xf_status xf_compute_dt(xf_handle *h, double *dt_dev, void *stream);
  * the CFL step of U^n computed on the device. dt_dev_out (device, nullable)
  * receives the step used. No host synchronisation. */
 xf_status xf_step_rk3(xf_handle *h, double dt, double *dt_dev_out, void *stream);
+/* nsteps steps of xf_step_rk3 (same dt rule, no dt output), replayed from a
+ * CUDA graph of one step that the handle captures on first use (one per
+ * temperature-buffer parity and step size; recaptured when dt changes), so
+ * that small grids are not bound by launch overhead. Results are bitwise
+ * those of nsteps xf_step_rk3 calls. With profiling on, the steps are plain
+ * launches. nsteps >= 0. */
+xf_status xf_step_rk3_n(xf_handle *h, int nsteps, double dt, void *stream);
 
 /* ---- Adjoint (vector-Jacobian products). All arrays are device
  * arrays [n_v][cells]; results ACCUMULATE into the bar arrays (gradient

@@ -31,6 +31,30 @@ void set_err(const char* what, cudaError_t e) {
 
 inline unsigned blocks(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
+// Multiprocessors of the current device (queried once).
+int sm_count() {
+  static const int n = [] {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      return 148;
+    }
+    return v;
+  }();
+  return n;
+}
+
+// Threads per block for n work items: the kernel's usual size, halved (down
+// to one warp) while the grid would give fewer than two blocks per SM. The
+// kernels are FP64-bound, and a single warp issues FP64 work slowly, so on
+// small grids spreading the items over more SMs shortens every launch.
+inline int bsize(long long n, int maxbs) {
+  int bs = maxbs;
+  while (bs > 32 && (n + bs - 1) / bs < 2LL * sm_count()) bs >>= 1;
+  return bs;
+}
+
 // reduction of the per-block partial sums of the mixing objective (one block)
 __global__ void k_sum_partials(const double* __restrict__ part, int n, double* out) {
   __shared__ double sh[256];
@@ -83,10 +107,12 @@ template <int DIM, int NS>
 struct Launch {
   static void prim(const xf::Params& p, const double* U, const double* Tin, double* Tout,
                    double* Q, uint32_t* fl, unsigned long long* red, int cfl, cudaStream_t s) {
-    xf::k_prim<DIM, NS><<<blocks(p.pcells, 256), 256, 0, s>>>(p, U, Tin, Tout, Q, fl, red, cfl);
+    const int bs = bsize(p.pcells, 256);
+    xf::k_prim<DIM, NS><<<blocks(p.pcells, bs), bs, 0, s>>>(p, U, Tin, Tout, Q, fl, red, cfl);
   }
   static void grad(const xf::Params& p, double* Q, cudaStream_t s) {
-    xf::k_grad<DIM, NS><<<blocks(p.pcells, 256), 256, 0, s>>>(p, Q);
+    const int bs = bsize(p.pcells, 256);
+    xf::k_grad<DIM, NS><<<blocks(p.pcells, bs), bs, 0, s>>>(p, Q);
   }
   template <int D, int REC = 5>
   static void face(const xf::Params& p, const double* Q, double* G, uint32_t* fl, const double* dt,
@@ -94,13 +120,15 @@ struct Launch {
     if constexpr (D < DIM) {
       const long long nf =
           (long long)(p.n[0] + (D == 0)) * (p.n[1] + (D == 1)) * (p.n[2] + (D == 2));
-      xf::k_face<DIM, NS, D, REC><<<blocks(nf, 128), 128, 0, s>>>(p, Q, G, fl, dt);
+      const int bs = bsize(nf, 128);
+      xf::k_face<DIM, NS, D, REC><<<blocks(nf, bs), bs, 0, s>>>(p, Q, G, fl, dt);
     }
   }
   static void update(const xf::Params& p, const double* Gx, const double* Gy, const double* Gz,
                      const double* Un, const double* Us, double* out, const double* dt, int mode,
                      cudaStream_t s) {
-    xf::k_update<DIM, NS><<<blocks(p.cells, 256), 256, 0, s>>>(p, Gx, Gy, Gz, Un, Us, out, dt,
+    const int bs = bsize(p.cells, 256);
+    xf::k_update<DIM, NS><<<blocks(p.cells, bs), bs, 0, s>>>(p, Gx, Gy, Gz, Un, Us, out, dt,
                                                               mode);
   }
   static void from_prim(const xf::Params& p, const double* P, double* U, double* T,
@@ -195,6 +223,11 @@ struct xf_handle {
   // per-cell fields of U^n and U1 kept by xf_step_rk3_adjoint (allocated on
   // its first call), so its reverse does not recompute them
   double* QS[2] = {nullptr, nullptr};
+  // xf_step_rk3_n: one captured step per temperature-buffer parity, for the
+  // step size it was captured with (0 = CFL), replayed on the caller's stream
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t step_graph[2] = {nullptr, nullptr};
+  double step_graph_dt[2] = {-1.0, -1.0};
   // per-kernel event timing (xf_profile_enable / xf_profile_read)
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -542,6 +575,9 @@ void xf_destroy(xf_handle* h) {
   cudaFree(h->part);
   for (auto& r : h->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto e : h->ev_pool) cudaEventDestroy(e);
+  for (int k = 0; k < 2; ++k)
+    if (h->step_graph[k]) cudaGraphExecDestroy(h->step_graph[k]);
+  if (h->cap) cudaStreamDestroy(h->cap);
   delete h;
 }
 
@@ -610,9 +646,9 @@ xf_status xf_compute_dt(xf_handle* h, double* dt_dev, void* stream) {
   return XF_OK;
 }
 
-xf_status xf_step_rk3(xf_handle* h, double dt, double* dt_dev_out, void* stream) {
-  if (!h || !(dt == dt)) return XF_ERR_ARG;
-  cudaStream_t s = (cudaStream_t)stream;
+// One SSP-RK3 step (Eq. 16) of the handle's state on stream s (dt <= 0: the
+// CFL step of U^n, computed on the device).
+static xf_status step_impl(xf_handle* h, double dt, double* dt_dev_out, cudaStream_t s) {
   const xf::Params& p = h->p;
   const bool cfl = !(dt > 0.0);
   if (!cfl) k_set_scalar<<<1, 1, 0, s>>>(h->dt, dt);
@@ -637,6 +673,61 @@ xf_status xf_step_rk3(xf_handle* h, double dt, double* dt_dev_out, void* stream)
     XF_CUDA(cudaMemcpyAsync(dt_dev_out, h->dt, sizeof(double), cudaMemcpyDeviceToDevice, s));
   return XF_OK;
 }
+
+xf_status xf_step_rk3(xf_handle* h, double dt, double* dt_dev_out, void* stream) {
+  if (!h || !(dt == dt)) return XF_ERR_ARG;
+  return step_impl(h, dt, dt_dev_out, (cudaStream_t)stream);
+}
+
+xf_status xf_step_rk3_n(xf_handle* h, int nsteps, double dt, void* stream) {
+  if (!h || nsteps < 0 || !(dt == dt)) return XF_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (h->prof) {  // event timing cannot sit inside a graph: plain launches
+    for (int k = 0; k < nsteps; ++k) {
+      xf_status st = step_impl(h, dt, nullptr, s);
+      if (st != XF_OK) return st;
+    }
+    return XF_OK;
+  }
+  const double key = dt > 0.0 ? dt : 0.0;
+  if (!h->cap && cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    h->cap = nullptr;
+    g_err = "xf_step_rk3_n: capture stream";
+    return XF_ERR_CUDA;
+  }
+  for (int k = 0; k < nsteps; ++k) {
+    const int par = h->tcur;
+    if (!h->step_graph[par] || h->step_graph_dt[par] != key) {
+      if (h->step_graph[par]) cudaGraphExecDestroy(h->step_graph[par]);
+      h->step_graph[par] = nullptr;
+      // the capture records one step as it would run from this parity; the
+      // host-side parity it advanced is put back, the replay advances it
+      XF_CUDA(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+      xf_status st = step_impl(h, key, nullptr, h->cap);
+      cudaGraph_t g = nullptr;
+      const cudaError_t ec = cudaStreamEndCapture(h->cap, &g);
+      h->tcur = par;
+      if (st != XF_OK || ec != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return st != XF_OK ? st : XF_ERR_CUDA;
+      }
+      const cudaError_t ei = cudaGraphInstantiate(&h->step_graph[par], g, 0);
+      cudaGraphDestroy(g);
+      if (ei != cudaSuccess) {
+        h->step_graph[par] = nullptr;
+        set_err("cudaGraphInstantiate", ei);
+        return XF_ERR_CUDA;
+      }
+      h->step_graph_dt[par] = key;
+    }
+    XF_CUDA(cudaGraphLaunch(h->step_graph[par], s));
+    h->tcur = 1 - par;  // a step runs three primitive recoveries
+  }
+  return XF_OK;
+}
+
 
 xf_status xf_get_status(xf_handle* h, uint32_t* flags, void* stream) {
   if (!h) return XF_ERR_ARG;

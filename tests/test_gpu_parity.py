@@ -166,3 +166,33 @@ def test_newton_cap_is_flagged():
     R, _, st = o.rhs(U, np.full_like(T, 300.0))
     Rg, Tg, stg = gpu_rhs(case, U, np.full_like(T, 300.0), newton_max=1)
     assert st & FLAG_NEWTON and stg & FLAG_NEWTON
+
+
+@pytest.mark.parametrize("dt", [0.0, 2.0e-4])
+def test_graph_steps_are_bitwise_single_steps(dt):
+    """xf_step_rk3_n (one step captured per temperature-buffer parity, replayed)
+    against the same number of xf_step_rk3 calls: state and warm start bit for
+    bit, over both parities, after a change of step size and with the
+    positivity blend (which reads the stage dt inside the graph)."""
+    import torch
+    case = cases.multicomponent_diffusion(n=200)
+    U, T = Oracle(case, diffusion=1).prim_to_cons()
+    out = []
+    for graph in (False, True):
+        s = gpu_solver(case, diffusion=1, positivity=True)
+        s.set_state(dev(U), dev(T))
+        for n, d in ((5, dt), (4, dt), (3, 0.5 * dt)):
+            if graph:
+                s.steps(n, d)
+            else:
+                for _ in range(n):
+                    s.step(d)
+        Uo = torch.empty((case.n_v, case.cells), dtype=torch.float64, device="cuda")
+        To = torch.empty(case.cells, dtype=torch.float64, device="cuda")
+        s.get_state(Uo, To)
+        torch.cuda.synchronize()
+        assert s.status() == 0
+        out.append((Uo.cpu().numpy(), To.cpu().numpy()))
+        s.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
