@@ -36,7 +36,8 @@ FP64_NOMINAL_TFLOPS = 1.25   # B300 dense FP64 (nominal)
 FACE_TRAFFIC_B_PER_FACE = {"aab342d14388773d": 294.0, "7aa2c6f72cd106cc": 294.2,
                            "69f88d1a3ee86fc1": 293.6, "e3f39384d86bd1a7": 293.2,
                            "5117291dbdc4468e": 293.1}
-CPU_SAMPLE_GRID = (96, 48, 48)
+# bounded oracle samples of each workload (config index -> grid)
+CPU_SAMPLE_GRID = {2: (96, 48, 48), 1: (256, 128)}
 
 
 def _peaks():
@@ -121,13 +122,14 @@ def _dist():
     return ws, rank, local
 
 
-def _cpu_baseline(steps=None, warmup=0, budget_s=15.0):
+def _cpu_baseline(cfg=2, steps=None, warmup=0, budget_s=15.0):
     """Time the oracle on a bounded sample of the workload on the host cores."""
     import numpy as np
     from paper_2403_05910_b300 import cases
     from oracle.xfo import Oracle
     cores = len(os.sched_getaffinity(0))
-    case = cases.config(2, n=CPU_SAMPLE_GRID)
+    grid = CPU_SAMPLE_GRID[cfg]
+    case = cases.config(cfg, n=grid)
     o = Oracle(case, threads=cores)
     U, T = o.prim_to_cons()
     dt = o.dt(U, T)
@@ -142,18 +144,18 @@ def _cpu_baseline(steps=None, warmup=0, budget_s=15.0):
             break
     val = case.cells * 3 * n / el
     return {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{n} RK3 step(s) of the same 3D 5-species shock-bubble setup on a "
-                      f"{'x'.join(map(str, CPU_SAMPLE_GRID))} grid ({case.cells} cells)",
+            "sample": f"{n} RK3 step(s) of the same setup ({case.name}) on a "
+                      f"{'x'.join(map(str, grid))} grid ({case.cells} cells)",
             "seconds": el}
 
 
-def _cpu_single_core(budget_s=6.0):
+def _cpu_single_core(cfg=2, budget_s=6.0):
     """The oracle on one host core (the kind of CPU figure GPU speed-ups are
     usually quoted against), on a smaller sample of the same workload."""
     from paper_2403_05910_b300 import cases
     from oracle.xfo import Oracle
-    grid = (48, 24, 24)
-    case = cases.config(2, n=grid)
+    grid = {2: (48, 24, 24), 1: (128, 64)}[cfg]
+    case = cases.config(cfg, n=grid)
     o = Oracle(case, threads=1)
     U, T = o.prim_to_cons()
     dt = o.dt(U, T)
@@ -170,19 +172,43 @@ def _cpu_single_core(budget_s=6.0):
             "seconds": el}
 
 
+def _config(case, ws):
+    """The workload description both arms print."""
+    return {"workload": f"{case.name}: {'x'.join(str(n) for n in case.n[:case.dim])}, "
+                        f"{case.n_species} species, viscous+diffusion, "
+                        f"Ma={case.params['Ma']:.4f}, r={case.params['r']}H",
+            "cells": case.cells, "n_v": case.n_v,
+            "l2": "working set > 126 MB L2 (state + per-cell fields ~"
+                  f"{(case.n_v * 2 + 34) * case.cells * 8 / 1e9:.0f} GB): no flush needed",
+            "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"}
+
+
+def _workload_meta(args):
+    """Name, grid, species and draws of the workload without building its
+    fields (the draws do not depend on the grid)."""
+    import dataclasses
+    from paper_2403_05910_b300 import cases
+    cfg, grid = WORKLOADS[args.workload]
+    small = cases.config(cfg, n=(8, 4, 4) if cfg == 2 else (8, 4))
+    full = grid or {2: (512, 256, 256), 1: (1024, 512)}[cfg]
+    if args.grid:
+        full = tuple(int(x) for x in args.grid.split(","))
+    n = tuple(list(full) + [1] * (3 - len(full)))
+    return dataclasses.replace(small, n=n, prim=None)
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
     from oracle import build as ob
     ob.build()
-    cb = _cpu_baseline(steps=args.steps, warmup=args.warmup)
+    cb = _cpu_baseline(WORKLOADS[args.workload][0], steps=args.steps, warmup=args.warmup)
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * cb["seconds"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "sbi3d_n5 (bounded CPU sample)",
-                       "grid": list(CPU_SAMPLE_GRID), "species": 5, "viscous": True},
+            "config": _config(_workload_meta(args), ws),
             "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -437,19 +463,13 @@ def run_ours(args):
         if ws == 1 and not args.no_cpu_baseline:
             from oracle import build as ob
             ob.build()
-            cpu = _cpu_baseline()
-            cpu["single_core"] = _cpu_single_core()
+            cpu = _cpu_baseline(cfg)
+            cpu["single_core"] = _cpu_single_core(cfg)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_all / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{case.name}: {'x'.join(str(n) for n in case.n[:case.dim])}, "
-                                   f"{case.n_species} species, viscous+diffusion, "
-                                   f"Ma={case.params['Ma']:.4f}, r={case.params['r']}H",
-                       "cells": case.cells, "n_v": case.n_v,
-                       "l2": "working set > 126 MB L2 (state + per-cell fields ~"
-                             f"{(case.n_v * 2 + 34) * case.cells * 8 / 1e9:.0f} GB): no flush needed",
-                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+            "config": _config(case, ws),
             "roofline": {"bound": "alu", "kernel": "k_face (x, y, z face fluxes)",
                          "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP64_NOMINAL_TFLOPS,
