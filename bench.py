@@ -271,8 +271,9 @@ def _batched_vs_per_instance(args, dev, stream):
 
 def _adjoint_vs_forward(args, dev, stream):
     """The differentiated workload (2D shock-bubble, 512x256, 4 species): time
-    of one RHS adjoint against one forward RHS, and of one RK3-step adjoint
-    (which recomputes the two intermediate stage states) against one step."""
+    of one RHS adjoint against one forward RHS, of one RK3-step adjoint
+    (from taped stage states, and recomputing them) against one step, and of
+    the whole checkpointed gradient against its forward pass."""
     import torch
     from paper_2403_05910_b300 import cases
     from paper_2403_05910_b300.xf import Solver
@@ -306,14 +307,50 @@ def _adjoint_vs_forward(args, dev, stream):
     a = timed(lambda: s.rhs_adjoint(U, W, Ub), k)
     fs = timed(lambda: s.step(dt), k)
     s.set_state(U)
-    as_ = timed(lambda: s.step_adjoint(dt, Ub), k)
+    ar = timed(lambda: s.step_adjoint(dt, Ub), k)
+    U1, U2 = torch.empty_like(U), torch.empty_like(U)
+    s.set_state(U)
+    s.step_tape(dt, U1, U2)
+    s.set_state(U)
+    at = timed(lambda: s.step_adjoint_tape(dt, U1, U2, Ub), k)
     st = s.status()
+    grad = _gradient_timing(s, c, dt, dev, stream)
+    st |= s.status()
     s.close()
     return {"workload": "sbi2d_n4_adjoint: 512x256, 4 species, viscous, fixed dt",
             "rhs_ms": f, "rhs_adjoint_ms": a, "rhs_ratio": a / f,
-            "step_ms": fs, "step_adjoint_ms": as_, "step_ratio": as_ / fs,
-            "note": "step adjoint includes recomputing the two intermediate stage states",
-            "status_flags": st}
+            "step_ms": fs, "step_adjoint_ms": at, "step_ratio": at / fs,
+            "step_adjoint_recompute_ms": ar, "step_ratio_recompute": ar / fs,
+            "note": "step adjoint from the taped stage states (xf_step_rk3_adjoint_tape); "
+                    "the recompute form rebuilds the two intermediate stage states itself",
+            "gradient": grad, "status_flags": st}
+
+
+def _gradient_timing(s, c, dt, dev, stream):
+    """dJ/dP0 of the differentiated workload as specified: 200 fixed-dt RK3
+    steps, a checkpoint every 20, J = sum Y_3 (1 - Y_3) dV, through
+    torch.autograd (taped backward). Forward-only time beside it."""
+    import torch
+    from paper_2403_05910_b300.autodiff import mixing_after_steps
+    steps, every = 200, 20
+
+    def run(n, grad):
+        P0 = torch.from_numpy(c.prim).to(dev).requires_grad_(grad)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        J = mixing_after_steps(P0, s, dt, n, every, 2)
+        if grad:
+            J.backward()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    run(every, True)   # warm-up: allocations, first calls
+    fwd = run(steps, False)
+    both = run(steps, True)
+    return {"steps": steps, "checkpoint_every": every, "forward_ms": fwd,
+            "forward_backward_ms": both, "ratio": both / fwd}
 
 
 VARIANTS = (("weno5+positivity", {"positivity": True}), ("weno_cu6", {"weno": 6}),

@@ -133,7 +133,8 @@ typedef struct xf_thermo {
  * theta in [0, 1] that keeps every partial density rho Y_s of the one-sided
  * states U_i - 2 lam F*, U_{i+1} + 2 lam F* (Eq. 18, lam = dim dt/dx_d) at or
  * above min(pos_eps, its LF value). xf_rhs (no dt) never blends, nor does
- * xf_rhs_adjoint; xf_step_rk3_adjoint reverses the blend of every stage. */
+ * xf_rhs_adjoint; xf_step_rk3_adjoint and its taped form reverse the blend of
+ * every stage. */
 typedef struct xf_opts {
   double cfl;
   int weno;
@@ -209,6 +210,25 @@ xf_status xf_rhs_adjoint(xf_handle *h, const double *U, const double *dUdt_bar,
  * per-cell field blocks (the fields of U^n and U1, kept between the forward
  * and reverse passes); the temperature warm start is left at that of U2. */
 xf_status xf_step_rk3_adjoint(xf_handle *h, double dt, double *U_bar, void *stream);
+/* Taped form of the pair above, for reverse passes that replay the forward
+ * steps anyway (checkpointed segments): xf_step_rk3_tape is one fixed-dt
+ * step (dt > 0; results bitwise those of xf_step_rk3) that also leaves its two
+ * intermediate SSP-RK3 stage states of Eq. 16, U1 = U^n + dt L(U^n) and
+ * U2 = 3/4 U^n + 1/4 (U1 + dt L(U1)), in U1 and U2 (device [n_v][cells],
+ * caller-owned, distinct from each other). xf_step_rk3_adjoint_tape is
+ * xf_step_rk3_adjoint from the handle's state U^n (and its temperature warm
+ * start, as the tape step began from them) with those stage states given
+ * instead of recomputed (same dt, U1/U2 as the tape step wrote them; not
+ * checked): only the per-cell fields of U^n, U1 and U2 are recomputed, in
+ * that order, so every Newton solve starts where the forward step's did and
+ * the reverse sees bitwise the fields the forward faces saw (which matters
+ * where a discrete choice, such as the blend's binding partial density, rests
+ * on round-off). Same U_bar convention, the same two extra field blocks as
+ * xf_step_rk3_adjoint, the warm start left at that of U2; results equal
+ * xf_step_rk3_adjoint's up to the order of its atomic adds. */
+xf_status xf_step_rk3_tape(xf_handle *h, double dt, double *U1, double *U2, void *stream);
+xf_status xf_step_rk3_adjoint_tape(xf_handle *h, double dt, const double *U1, const double *U2,
+                                   double *U_bar, void *stream);
 /* Mixing measure J = sum_cells Y_s (1 - Y_s) dV of species `species` (0-based)
  * for the state U: J_dev (device, one double) = J, U_bar = dJ/dU (overwritten). */
 xf_status xf_objective_mixing(xf_handle *h, const double *U, int species,

@@ -1,15 +1,19 @@
 """torch.autograd bindings of the adjoint (argument marshalling only).
 
 Every derivative is computed by the library's kernels through the C-ABI:
-``xf_set_primitive_adjoint`` (EOS), ``xf_step_rk3_adjoint`` (one SSP-RK3 step,
-Eq. 16, with the hand-written RHS adjoint) and ``xf_objective_mixing``. The
+``xf_set_primitive_adjoint`` (EOS), ``xf_step_rk3_adjoint`` or its taped form
+(one SSP-RK3 step, Eq. 16, with the hand-written RHS adjoint) and
+``xf_objective_mixing``. The
 functions here only move device buffers between those calls:
 
 * ``FromPrimitive``: primitive fields P (rho, u, p, Y) -> conserved U.
 * ``RK3Steps``: ``steps`` fixed-dt SSP-RK3 steps. The forward pass keeps a
   checkpoint (U and the Newton warm start T) every ``every`` steps; the
   backward pass re-runs each segment from its checkpoint to regain the
-  step-start states, then walks the segment's steps in reverse.
+  step-start states, then walks the segment's steps in reverse. With ``tape``
+  the re-run also keeps every step's two intermediate stage states
+  (``xf_step_rk3_tape``, 2 ``every`` extra states per segment) and the reverse
+  steps take them (``xf_step_rk3_adjoint_tape``) instead of recomputing them.
 * ``MixingObjective``: J = sum Y_s (1 - Y_s) dV of one species.
 
 The time step is frozen (a fixed dt), so the discrete map is differentiable
@@ -47,7 +51,7 @@ class FromPrimitive(torch.autograd.Function):
 
 class RK3Steps(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, U0, solver, dt, steps, every):
+    def forward(ctx, U0, solver, dt, steps, every, tape=True):
         U0 = U0.contiguous()
         dev = U0.device
         # keep the solver's current Newton warm start (e.g. the exact T that
@@ -66,7 +70,7 @@ class RK3Steps(torch.autograd.Function):
             solver.step(dt)
         Un = _empty_state(solver, dev)
         solver.get_state(Un)
-        ctx.solver, ctx.dt, ctx.steps, ctx.every = solver, dt, steps, every
+        ctx.solver, ctx.dt, ctx.steps, ctx.every, ctx.tape = solver, dt, steps, every, tape
         ctx.ck = (ck_U, ck_T)
         return Un
 
@@ -85,12 +89,20 @@ class RK3Steps(torch.autograd.Function):
                 U = _empty_state(s, dev)
                 T = torch.empty(s.cells, dtype=torch.float64, device=dev)
                 s.get_state(U, T)
-                states.append((U, T))
-                s.step(dt)
-            for U, T in reversed(states):
-                s.set_state(U, T)
-                s.step_adjoint(dt, Ub)
-        return Ub, None, None, None, None
+                if ctx.tape:
+                    U1, U2 = _empty_state(s, dev), _empty_state(s, dev)
+                    s.step_tape(dt, U1, U2)
+                    states.append((U, T, U1, U2))
+                else:
+                    s.step(dt)
+                    states.append((U, T))
+            for st in reversed(states):
+                s.set_state(st[0], st[1])
+                if ctx.tape:
+                    s.step_adjoint_tape(dt, st[2], st[3], Ub)
+                else:
+                    s.step_adjoint(dt, Ub)
+        return Ub, None, None, None, None, None
 
 
 class MixingObjective(torch.autograd.Function):
@@ -109,8 +121,8 @@ class MixingObjective(torch.autograd.Function):
         return Ubar * gJ, None, None
 
 
-def mixing_after_steps(P0, solver, dt, steps, every, species):
+def mixing_after_steps(P0, solver, dt, steps, every, species, tape=True):
     """J(P0): primitive fields -> EOS -> ``steps`` RK3 steps -> mixing measure."""
     U0 = FromPrimitive.apply(P0, solver)
-    UT = RK3Steps.apply(U0, solver, dt, steps, every)
+    UT = RK3Steps.apply(U0, solver, dt, steps, every, tape)
     return MixingObjective.apply(UT, solver, species)

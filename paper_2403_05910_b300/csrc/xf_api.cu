@@ -648,25 +648,30 @@ xf_status xf_compute_dt(xf_handle* h, double* dt_dev, void* stream) {
 
 // One SSP-RK3 step (Eq. 16) of the handle's state on stream s (dt <= 0: the
 // CFL step of U^n, computed on the device).
-static xf_status step_impl(xf_handle* h, double dt, double* dt_dev_out, cudaStream_t s) {
+// One SSP-RK3 step. The stage states go to U1 and U2 when given (the taped
+// step), else both to the handle's stage buffer.
+static xf_status step_impl(xf_handle* h, double dt, double* dt_dev_out, cudaStream_t s,
+                           double* U1 = nullptr, double* U2 = nullptr) {
   const xf::Params& p = h->p;
   const bool cfl = !(dt > 0.0);
+  double* S1 = U1 ? U1 : h->Us;
+  double* S2 = U2 ? U2 : h->Us;
   if (!cfl) k_set_scalar<<<1, 1, 0, s>>>(h->dt, dt);
-  // Eq. 16: three stages, U^n kept in U, stages in Us
+  // Eq. 16: three stages, U^n kept in U
   xf_status st = stage_fluxes(h, h->U, cfl ? 1 : 0, s, true);
   if (st != XF_OK) return st;
   timed(h, XF_PROF_UPDATE, s, [&] {
-    h->tab.update(p, h->G[0], h->G[1], h->G[2], h->U, h->U, h->Us, h->dt, 1, s);
+    h->tab.update(p, h->G[0], h->G[1], h->G[2], h->U, h->U, S1, h->dt, 1, s);
   });
-  st = stage_fluxes(h, h->Us, 0, s, true);
+  st = stage_fluxes(h, S1, 0, s, true);
   if (st != XF_OK) return st;
   timed(h, XF_PROF_UPDATE, s, [&] {
-    h->tab.update(p, h->G[0], h->G[1], h->G[2], h->U, h->Us, h->Us, h->dt, 2, s);
+    h->tab.update(p, h->G[0], h->G[1], h->G[2], h->U, S1, S2, h->dt, 2, s);
   });
-  st = stage_fluxes(h, h->Us, 0, s, true);
+  st = stage_fluxes(h, S2, 0, s, true);
   if (st != XF_OK) return st;
   timed(h, XF_PROF_UPDATE, s, [&] {
-    h->tab.update(p, h->G[0], h->G[1], h->G[2], h->U, h->Us, h->U, h->dt, 3, s);
+    h->tab.update(p, h->G[0], h->G[1], h->G[2], h->U, S2, h->U, h->dt, 3, s);
   });
   XF_CUDA(cudaGetLastError());
   if (dt_dev_out)
@@ -755,14 +760,10 @@ xf_status xf_rhs_adjoint(xf_handle* h, const double* U, const double* dUdt_bar, 
   return rhs_adjoint_impl(h, U, dUdt_bar, 1.0, U_bar, (cudaStream_t)stream);
 }
 
-xf_status xf_step_rk3_adjoint(xf_handle* h, double dt, double* U_bar, void* stream) {
-  if (!h || !U_bar || !(dt > 0.0)) return XF_ERR_ARG;
-  if (!is_device_ptr(U_bar)) return XF_ERR_ARG;
-  cudaStream_t s = (cudaStream_t)stream;
-  xf_status st = ensure_adjoint_buffers(h);
-  if (st != XF_OK) return st;
-  const xf::Params& p = h->p;
-  const size_t qbytes = sizeof(double) * nq_of(h->tab, p) * p.pcells;
+// The two extra per-cell field blocks of the step adjoints (allocated on
+// first use, kept with the handle).
+static xf_status ensure_stage_fields(xf_handle* h) {
+  const size_t qbytes = sizeof(double) * nq_of(h->tab, h->p) * h->p.pcells;
   for (int k = 0; k < 2; ++k) {
     if (!h->QS[k] && cudaMalloc((void**)&h->QS[k], qbytes) != cudaSuccess) {
       cudaGetLastError();
@@ -771,13 +772,28 @@ xf_status xf_step_rk3_adjoint(xf_handle* h, double dt, double* U_bar, void* stre
       return XF_ERR_OOM;
     }
   }
+  return XF_OK;
+}
+
+// Restores the handle's own field block on every return of a step adjoint.
+struct QGuard {
+  xf_handle* h;
+  double* q;
+  ~QGuard() { h->Q = q; }
+};
+
+xf_status xf_step_rk3_adjoint(xf_handle* h, double dt, double* U_bar, void* stream) {
+  if (!h || !U_bar || !(dt > 0.0)) return XF_ERR_ARG;
+  if (!is_device_ptr(U_bar)) return XF_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  xf_status st = ensure_adjoint_buffers(h);
+  if (st != XF_OK) return st;
+  const xf::Params& p = h->p;
+  st = ensure_stage_fields(h);
+  if (st != XF_OK) return st;
   // the forward passes write U^n's and U1's per-cell fields into QS[0], QS[1];
   // h->Q is restored on every return
-  struct QGuard {
-    xf_handle* h;
-    double* q;
-    ~QGuard() { h->Q = q; }
-  } guard{h, h->Q};
+  QGuard guard{h, h->Q};
   k_set_scalar<<<1, 1, 0, s>>>(h->dt, dt);
   // forward stage states U1 (A1) and U2 (A2) from U^n (h->U)
   h->Q = h->QS[0];
@@ -797,6 +813,51 @@ xf_status xf_step_rk3_adjoint(xf_handle* h, double dt, double* U_bar, void* stre
   lincomb(h, 0.25, h->B2, 0.0, nullptr, 0.0, nullptr, h->B1, s);
   h->Q = h->QS[1];
   st = rhs_adjoint_impl(h, h->A1, h->B2, 0.25 * dt, h->B1, s, true, h->dt);
+  if (st != XF_OK) return st;
+  lincomb(h, 1.0 / 3.0, U_bar, 0.75, h->B2, 1.0, h->B1, U_bar, s);
+  h->Q = h->QS[0];
+  st = rhs_adjoint_impl(h, h->U, h->B1, dt, U_bar, s, true, h->dt);
+  if (st != XF_OK) return st;
+  XF_CUDA(cudaGetLastError());
+  return XF_OK;
+}
+
+xf_status xf_step_rk3_tape(xf_handle* h, double dt, double* U1, double* U2, void* stream) {
+  if (!h || !U1 || !U2 || U1 == U2 || !(dt > 0.0)) return XF_ERR_ARG;
+  if (!is_device_ptr(U1) || !is_device_ptr(U2)) return XF_ERR_ARG;
+  return step_impl(h, dt, nullptr, (cudaStream_t)stream, U1, U2);
+}
+
+xf_status xf_step_rk3_adjoint_tape(xf_handle* h, double dt, const double* U1, const double* U2,
+                                   double* U_bar, void* stream) {
+  if (!h || !U1 || !U2 || !U_bar || !(dt > 0.0)) return XF_ERR_ARG;
+  if (!is_device_ptr(U1) || !is_device_ptr(U2) || !is_device_ptr(U_bar)) return XF_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  xf_status st = ensure_adjoint_buffers(h);
+  if (st != XF_OK) return st;
+  st = ensure_stage_fields(h);
+  if (st != XF_OK) return st;
+  QGuard guard{h, h->Q};
+  k_set_scalar<<<1, 1, 0, s>>>(h->dt, dt);
+  // the three stages' per-cell fields in the forward step's order, so that
+  // each Newton solve starts from the warm start the forward step gave it
+  // and the fields are bitwise those the forward faces saw
+  h->Q = h->QS[0];
+  st = cell_fields(h, h->U, s);
+  if (st != XF_OK) return st;
+  h->Q = h->QS[1];
+  st = cell_fields(h, U1, s);
+  if (st != XF_OK) return st;
+  h->Q = guard.q;
+  st = cell_fields(h, U2, s);
+  if (st != XF_OK) return st;
+  // the reverse of xf_step_rk3_adjoint on those fields
+  lincomb(h, 2.0 / 3.0, U_bar, 0.0, nullptr, 0.0, nullptr, h->B2, s);
+  st = rhs_adjoint_impl(h, U2, U_bar, 2.0 / 3.0 * dt, h->B2, s, true, h->dt);
+  if (st != XF_OK) return st;
+  lincomb(h, 0.25, h->B2, 0.0, nullptr, 0.0, nullptr, h->B1, s);
+  h->Q = h->QS[1];
+  st = rhs_adjoint_impl(h, U1, h->B2, 0.25 * dt, h->B1, s, true, h->dt);
   if (st != XF_OK) return st;
   lincomb(h, 1.0 / 3.0, U_bar, 0.75, h->B2, 1.0, h->B1, U_bar, s);
   h->Q = h->QS[0];
