@@ -185,6 +185,22 @@ xf_status xf_compute_dt(xf_handle *h, double *dt_dev, void *stream);
  * the CFL step of U^n computed on the device. dt_dev_out (device, nullable)
  * receives the step used. No host synchronisation. */
 xf_status xf_step_rk3(xf_handle *h, double dt, double *dt_dev_out, void *stream);
+/* One xf_step_rk3 of a state that lives in host memory: U_in [n_v][cells] and
+ * T_in [cells] (the Newton warm start, nullable: 300 K) are loaded as by
+ * xf_set_state, the step is taken (same dt rule, dt_dev_out as above) and
+ * U^{n+1} and the warm start it leaves are written to U_out and T_out
+ * (nullable) as by xf_get_state; results are bitwise those three calls'.
+ * U_out may equal U_in. The copies run on a copy stream of the handle,
+ * overlapped with the compute in up to 8 slabs of planes of the slowest axis
+ * (dim - 1; slabs of >= 16 planes and >= 2^18 cells, else one): stage 1
+ * recovers each slab's primitives as soon as its upload lands, and stage 3
+ * sends each slab's U^{n+1} out as soon as its faces and update are done.
+ * Pointers: host or device; overlap needs page-locked host memory. The call
+ * returns after enqueueing; `stream` reaches its end once every copy is done,
+ * and the host buffers must stay valid until then. */
+xf_status xf_step_rk3_host(xf_handle *h, const double *U_in, const double *T_in,
+                           double *U_out, double *T_out, double dt, double *dt_dev_out,
+                           void *stream);
 /* nsteps steps of xf_step_rk3 (same dt rule, no dt output), replayed from a
  * CUDA graph of one step that the handle captures on first use (one per
  * temperature-buffer parity and step size; recaptured when dt changes), so

@@ -1,6 +1,7 @@
 // xf_api.cu -- C-ABI entry points (include/xf.h) and kernel dispatch.
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -88,6 +89,15 @@ using FaceFn = void (*)(const xf::Params&, const double*, double*, uint32_t*, co
                         cudaStream_t);
 using UpdFn = void (*)(const xf::Params&, const double*, const double*, const double*,
                        const double*, const double*, double*, const double*, int, cudaStream_t);
+// the same on an index range [b, e) (padded cells, faces of one direction,
+// interior cells): the slabs of xf_step_rk3_host
+using PrimRFn = void (*)(const xf::Params&, const double*, const double*, double*, double*,
+                         uint32_t*, unsigned long long*, int, long long, long long, cudaStream_t);
+using FaceRFn = void (*)(const xf::Params&, const double*, double*, uint32_t*, const double*,
+                         long long, long long, cudaStream_t);
+using UpdRFn = void (*)(const xf::Params&, const double*, const double*, const double*,
+                        const double*, const double*, double*, const double*, int, long long,
+                        long long, cudaStream_t);
 using FromPrimFn = void (*)(const xf::Params&, const double*, double*, double*, cudaStream_t);
 
 
@@ -101,35 +111,56 @@ struct Table {
   FromPrimFn from_prim;
   int nq;
   XfAdjTable adj;  // reverse-mode launchers (xf_adjoint_launch.cu)
+  PrimRFn prim_r;
+  FaceRFn face_r[3][3];  // [weno - 5][direction]
+  UpdRFn update_r;
 };
 
 template <int DIM, int NS>
 struct Launch {
+  static void prim_r(const xf::Params& p, const double* U, const double* Tin, double* Tout,
+                     double* Q, uint32_t* fl, unsigned long long* red, int cfl, long long b,
+                     long long e, cudaStream_t s) {
+    if (e <= b) return;
+    const int bs = bsize(e - b, 256);
+    xf::k_prim<DIM, NS><<<blocks(e - b, bs), bs, 0, s>>>(p, U, Tin, Tout, Q, fl, red, cfl, b, e);
+  }
   static void prim(const xf::Params& p, const double* U, const double* Tin, double* Tout,
                    double* Q, uint32_t* fl, unsigned long long* red, int cfl, cudaStream_t s) {
-    const int bs = bsize(p.pcells, 256);
-    xf::k_prim<DIM, NS><<<blocks(p.pcells, bs), bs, 0, s>>>(p, U, Tin, Tout, Q, fl, red, cfl);
+    prim_r(p, U, Tin, Tout, Q, fl, red, cfl, 0, p.pcells, s);
   }
   static void grad(const xf::Params& p, double* Q, cudaStream_t s) {
     const int bs = bsize(p.pcells, 256);
     xf::k_grad<DIM, NS><<<blocks(p.pcells, bs), bs, 0, s>>>(p, Q);
   }
   template <int D, int REC = 5>
+  static void face_r(const xf::Params& p, const double* Q, double* G, uint32_t* fl,
+                     const double* dt, long long b, long long e, cudaStream_t s) {
+    if constexpr (D < DIM) {
+      if (e <= b) return;
+      const int bs = bsize(e - b, 128);
+      xf::k_face<DIM, NS, D, REC><<<blocks(e - b, bs), bs, 0, s>>>(p, Q, G, fl, dt, b, e);
+    }
+  }
+  template <int D, int REC = 5>
   static void face(const xf::Params& p, const double* Q, double* G, uint32_t* fl, const double* dt,
                    cudaStream_t s) {
-    if constexpr (D < DIM) {
-      const long long nf =
-          (long long)(p.n[0] + (D == 0)) * (p.n[1] + (D == 1)) * (p.n[2] + (D == 2));
-      const int bs = bsize(nf, 128);
-      xf::k_face<DIM, NS, D, REC><<<blocks(nf, bs), bs, 0, s>>>(p, Q, G, fl, dt);
-    }
+    const long long nf =
+        (long long)(p.n[0] + (D == 0)) * (p.n[1] + (D == 1)) * (p.n[2] + (D == 2));
+    face_r<D, REC>(p, Q, G, fl, dt, 0, nf, s);
+  }
+  static void update_r(const xf::Params& p, const double* Gx, const double* Gy, const double* Gz,
+                       const double* Un, const double* Us, double* out, const double* dt,
+                       int mode, long long b, long long e, cudaStream_t s) {
+    if (e <= b) return;
+    const int bs = bsize(e - b, 256);
+    xf::k_update<DIM, NS><<<blocks(e - b, bs), bs, 0, s>>>(p, Gx, Gy, Gz, Un, Us, out, dt,
+                                                            mode, b, e);
   }
   static void update(const xf::Params& p, const double* Gx, const double* Gy, const double* Gz,
                      const double* Un, const double* Us, double* out, const double* dt, int mode,
                      cudaStream_t s) {
-    const int bs = bsize(p.cells, 256);
-    xf::k_update<DIM, NS><<<blocks(p.cells, bs), bs, 0, s>>>(p, Gx, Gy, Gz, Un, Us, out, dt,
-                                                              mode);
+    update_r(p, Gx, Gy, Gz, Un, Us, out, dt, mode, 0, p.cells, s);
   }
   static void from_prim(const xf::Params& p, const double* P, double* U, double* T,
                         cudaStream_t s) {
@@ -138,7 +169,10 @@ struct Launch {
   static Table table() {
     Table t{prim, grad, {face<0>, face<1>, face<2>}, {face<0, 6>, face<1, 6>, face<2, 6>},
             {face<0, 7>, face<1, 7>, face<2, 7>}, update, from_prim, xf::Lay<DIM, NS>::NQ,
-            XfAdjTable{}};
+            XfAdjTable{}, prim_r,
+            {{face_r<0>, face_r<1>, face_r<2>}, {face_r<0, 6>, face_r<1, 6>, face_r<2, 6>},
+             {face_r<0, 7>, face_r<1, 7>, face_r<2, 7>}},
+            update_r};
     xf_internal_adj_fill5(DIM, NS, &t.adj);
     xf_internal_adj_fill6(DIM, NS, &t.adj);
     xf_internal_adj_fill7(DIM, NS, &t.adj);
@@ -226,6 +260,9 @@ struct xf_handle {
   // xf_step_rk3_n: one captured step per temperature-buffer parity, for the
   // step size it was captured with (0 = CFL), replayed on the caller's stream
   cudaStream_t cap = nullptr;
+  // xf_step_rk3_host: the copy stream and its events (reused across calls)
+  cudaStream_t cs = nullptr;
+  std::vector<cudaEvent_t> hev;
   cudaGraphExec_t step_graph[2] = {nullptr, nullptr};
   double step_graph_dt[2] = {-1.0, -1.0};
   // per-kernel event timing (xf_profile_enable / xf_profile_read)
@@ -482,6 +519,53 @@ xf_status xf_internal_fill_params(const xf_grid* g, const xf_thermo* th, const x
 void xf_internal_set_error(const char* msg) { g_err = msg; }
 void xf_internal_set_cuda_error(const char* what, cudaError_t e) { set_err(what, e); }
 
+namespace {
+// ---- xf_step_rk3_host: slabs of the slowest active axis a. Each slab j holds
+// interior planes [z_j, z_{j+1}) of a; the copies of slab j run on the handle's
+// copy stream while the compute stream works on other slabs.
+struct Slabs {
+  int a = 0, S = 1, G = 0;
+  long long n = 1, cs = 1, ps = 1;  // planes, interior / padded cells per plane
+  long long z(int j) const { return n * j / S; }
+};
+
+Slabs slabs_of(const xf::Params& p) {
+  Slabs sl;
+  sl.a = p.dim - 1;
+  sl.n = p.n[sl.a];
+  sl.G = p.go[sl.a];
+  sl.cs = p.cells / sl.n;
+  sl.ps = p.pcells / p.np[sl.a];
+  // slabs of >= 16 planes and >= 2^18 cells, at most 8: below that the copies
+  // are short and one slab (no overlap) costs fewer launches
+  long long S = std::min<long long>(8, sl.n / 16);
+  S = std::min<long long>(S, p.cells >> 18);
+  sl.S = (int)std::max<long long>(1, S);
+  return sl;
+}
+
+// faces of direction d on face planes [z0, z1) of axis a (n planes when
+// d != a, n + 1 when d == a), in the face kernels' order
+void face_range(const xf::Params& p, const Slabs& sl, int d, long long z0, long long z1,
+                long long* b, long long* e) {
+  long long ps = 1;
+  for (int k = 0; k < sl.a; ++k) ps *= p.n[k] + (k == d);
+  *b = z0 * ps;
+  *e = z1 * ps;
+}
+
+xf_status host_events(xf_handle* h, int need) {
+  while ((int)h->hev.size() < need) {
+    cudaEvent_t e;
+    XF_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    h->hev.push_back(e);
+  }
+  if (!h->cs) XF_CUDA(cudaStreamCreateWithFlags(&h->cs, cudaStreamNonBlocking));
+  return XF_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* xf_status_str(xf_status s) {
@@ -578,6 +662,8 @@ void xf_destroy(xf_handle* h) {
   for (int k = 0; k < 2; ++k)
     if (h->step_graph[k]) cudaGraphExecDestroy(h->step_graph[k]);
   if (h->cap) cudaStreamDestroy(h->cap);
+  for (auto e : h->hev) cudaEventDestroy(e);
+  if (h->cs) cudaStreamDestroy(h->cs);
   delete h;
 }
 
@@ -682,6 +768,106 @@ static xf_status step_impl(xf_handle* h, double dt, double* dt_dev_out, cudaStre
 xf_status xf_step_rk3(xf_handle* h, double dt, double* dt_dev_out, void* stream) {
   if (!h || !(dt == dt)) return XF_ERR_ARG;
   return step_impl(h, dt, dt_dev_out, (cudaStream_t)stream);
+}
+
+xf_status xf_step_rk3_host(xf_handle* h, const double* U_in, const double* T_in, double* U_out,
+                           double* T_out, double dt, double* dt_dev_out, void* stream) {
+  if (!h || !U_in || !U_out || !(dt == dt)) return XF_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const xf::Params& p = h->p;
+  const Slabs sl = slabs_of(p);
+  const int S = sl.S;
+  xf_status st = host_events(h, 2 * S + 3);
+  if (st != XF_OK) return st;
+  cudaEvent_t* ev = h->hev.data();  // [0, S) uploads, [S, 2S) updates, then T, start, end
+  cudaEvent_t ev_T = ev[2 * S], ev_start = ev[2 * S + 1], ev_end = ev[2 * S + 2];
+  cudaStream_t cs = h->cs;
+  const size_t row = sizeof(double) * (size_t)p.cells;
+  // the uploads overwrite the state: they wait for the work already on `stream`
+  XF_CUDA(cudaEventRecord(ev_start, s));
+  XF_CUDA(cudaStreamWaitEvent(cs, ev_start, 0));
+  double* Tn = h->T[h->tcur];
+  if (!T_in) k_fill<<<blocks(p.cells, 256), 256, 0, cs>>>(Tn, p.cells, 300.0);
+  for (int j = 0; j < S; ++j) {
+    const long long c0 = sl.z(j) * sl.cs, nc = (sl.z(j + 1) - sl.z(j)) * sl.cs;
+    XF_CUDA(cudaMemcpy2DAsync(h->U + c0, row, U_in + c0, row, sizeof(double) * nc, p.nv,
+                              cudaMemcpyDefault, cs));
+    if (T_in)
+      XF_CUDA(cudaMemcpyAsync(Tn + c0, T_in + c0, sizeof(double) * nc, cudaMemcpyDefault, cs));
+    XF_CUDA(cudaEventRecord(ev[j], cs));
+  }
+  const bool cfl = !(dt > 0.0);
+  if (!cfl) k_set_scalar<<<1, 1, 0, s>>>(h->dt, dt);
+  // stage 1: the primitive recovery of each slab's padded planes as soon as
+  // its upload lands; the ghost planes of axis a (which map onto any slab)
+  // after the last one
+  double* Tout = h->T[1 - h->tcur];
+  for (int j = 0; j < S; ++j) {
+    XF_CUDA(cudaStreamWaitEvent(s, ev[j], 0));
+    timed(h, XF_PROF_PRIM, s, [&] {
+      h->tab.prim_r(p, h->U, Tn, Tout, h->Q, h->flags, h->red, cfl ? 1 : 0,
+                    (sl.z(j) + sl.G) * sl.ps, (sl.z(j + 1) + sl.G) * sl.ps, s);
+    });
+  }
+  timed(h, XF_PROF_PRIM, s, [&] {
+    h->tab.prim_r(p, h->U, Tn, Tout, h->Q, h->flags, h->red, cfl ? 1 : 0, 0, sl.G * sl.ps, s);
+    h->tab.prim_r(p, h->U, Tn, Tout, h->Q, h->flags, h->red, cfl ? 1 : 0,
+                  (sl.n + sl.G) * sl.ps, p.pcells, s);
+  });
+  h->tcur = 1 - h->tcur;
+  if (cfl) timed(h, XF_PROF_DT, s, [&] { k_dt_finalize<<<1, 1, 0, s>>>(p, h->red, h->dt, nullptr); });
+  if (p.viscous) timed(h, XF_PROF_GRAD, s, [&] { h->tab.grad(p, h->Q, s); });
+  for (int d = 0; d < p.dim; ++d)
+    timed(h, XF_PROF_FACE_X + d, s, [&] {
+      faces_of(h->tab, p.weno)[d](p, h->Q, h->G[d], h->flags, h->dt, s);
+    });
+  timed(h, XF_PROF_UPDATE, s, [&] {
+    h->tab.update(p, h->G[0], h->G[1], h->G[2], h->U, h->U, h->Us, h->dt, 1, s);
+  });
+  // stage 2 as in xf_step_rk3
+  st = stage_fluxes(h, h->Us, 0, s, true);
+  if (st != XF_OK) return st;
+  timed(h, XF_PROF_UPDATE, s, [&] {
+    h->tab.update(p, h->G[0], h->G[1], h->G[2], h->U, h->Us, h->Us, h->dt, 2, s);
+  });
+  // stage 3: the warm start it leaves goes out during the faces; each slab's
+  // U^{n+1} goes out as soon as its faces and update are done
+  st = cell_fields(h, h->Us, s);
+  if (st != XF_OK) return st;
+  if (T_out) {
+    XF_CUDA(cudaEventRecord(ev_T, s));
+    XF_CUDA(cudaStreamWaitEvent(cs, ev_T, 0));
+    XF_CUDA(cudaMemcpyAsync(T_out, h->T[h->tcur], row, cudaMemcpyDefault, cs));
+  }
+  const FaceRFn* fr = h->tab.face_r[p.weno - 5];
+  for (int j = 0; j < S; ++j) {
+    const long long z0 = sl.z(j), z1 = sl.z(j + 1);
+    for (int d = 0; d < p.dim; ++d) {
+      long long b, e;
+      if (d == sl.a) {  // face planes (z0, z1], and plane 0 with the first slab
+        face_range(p, sl, d, j == 0 ? 0 : z0 + 1, z1 + 1, &b, &e);
+      } else {
+        face_range(p, sl, d, z0, z1, &b, &e);
+      }
+      timed(h, XF_PROF_FACE_X + d, s, [&] { fr[d](p, h->Q, h->G[d], h->flags, h->dt, b, e, s); });
+    }
+    timed(h, XF_PROF_UPDATE, s, [&] {
+      h->tab.update_r(p, h->G[0], h->G[1], h->G[2], h->U, h->Us, h->U, h->dt, 3, z0 * sl.cs,
+                      z1 * sl.cs, s);
+    });
+    XF_CUDA(cudaEventRecord(ev[S + j], s));
+    XF_CUDA(cudaStreamWaitEvent(cs, ev[S + j], 0));
+    const long long c0 = z0 * sl.cs, nc = (z1 - z0) * sl.cs;
+    XF_CUDA(cudaMemcpy2DAsync(U_out + c0, row, h->U + c0, row, sizeof(double) * nc, p.nv,
+                              cudaMemcpyDefault, cs));
+  }
+  // the caller's stream sees the copies done
+  XF_CUDA(cudaEventRecord(ev_end, cs));
+  XF_CUDA(cudaStreamWaitEvent(s, ev_end, 0));
+  if (dt_dev_out)
+    XF_CUDA(cudaMemcpyAsync(dt_dev_out, h->dt, sizeof(double), cudaMemcpyDeviceToDevice, s));
+  XF_CUDA(cudaGetLastError());
+  return XF_OK;
 }
 
 xf_status xf_step_rk3_n(xf_handle* h, int nsteps, double dt, void* stream) {

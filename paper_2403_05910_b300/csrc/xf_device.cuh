@@ -415,15 +415,17 @@ __device__ __forceinline__ void block_max2(double s_cfl, double s_nu, unsigned l
   }
 }
 
+// Padded cells [t0, t1) (0 <= t0 <= t1 <= pcells; the whole box, or one slab
+// of planes of the slowest axis).
 template <int DIM, int NS>
 __global__ void __launch_bounds__(256)
 k_prim(const __grid_constant__ Params p, const double* __restrict__ U,
        const double* __restrict__ Tin, double* __restrict__ Tout,
        double* __restrict__ Q, uint32_t* __restrict__ flags,
-       unsigned long long* __restrict__ red, int do_cfl) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+       unsigned long long* __restrict__ red, int do_cfl, long long t0, long long t1) {
+  const long long t = t0 + (long long)blockIdx.x * blockDim.x + threadIdx.x;
   double s_cfl = 0.0, s_nu = 0.0;
-  if (t < p.pcells) prim_cell<DIM, NS>(p, t, U, Tin, Tout, Q, flags, do_cfl, s_cfl, s_nu);
+  if (t < t1) prim_cell<DIM, NS>(p, t, U, Tin, Tout, Q, flags, do_cfl, s_cfl, s_nu);
   if (do_cfl) block_max2(s_cfl, s_nu, red);
 }
 
@@ -1037,13 +1039,15 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
   raise(flags, st);
 }
 
+// Faces [f0, f1) of direction D in their (i fastest) order, f1 <= their count.
 template <int DIM, int NS, int D, int REC = 5>
 __global__ void __launch_bounds__(128, XF_FACE_MIN_BLOCKS)
 k_face(const __grid_constant__ Params p, const double* __restrict__ Q,
-       double* __restrict__ Gf, uint32_t* __restrict__ flags, const double* __restrict__ dtp) {
-  const int nf0 = p.n[0] + (D == 0), nf1 = p.n[1] + (D == 1), nf2 = p.n[2] + (D == 2);
-  const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= (long long)nf0 * nf1 * nf2) return;
+       double* __restrict__ Gf, uint32_t* __restrict__ flags, const double* __restrict__ dtp,
+       long long f0, long long f1) {
+  const int nf0 = p.n[0] + (D == 0), nf1 = p.n[1] + (D == 1);
+  const long long f = f0 + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= f1) return;
   face_one<DIM, NS, D, REC>(p, (int)(f % nf0), (int)((f / nf0) % nf1), (int)(f / ((long long)nf0 * nf1)),
                        Q, Gf, flags, dtp ? *dtp : 0.0);
 }
@@ -1100,14 +1104,15 @@ __device__ __forceinline__ void update_cell(const Params& p, long long c,
   }
 }
 
+// Interior cells [c0, c1), c1 <= cells.
 template <int DIM, int NS>
 __global__ void __launch_bounds__(256)
 k_update(const __grid_constant__ Params p, const double* __restrict__ Gx,
          const double* __restrict__ Gy, const double* __restrict__ Gz,
          const double* Un, const double* Us, double* out, const double* __restrict__ dtp,
-         int mode) {
-  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= p.cells) return;
+         int mode, long long c0, long long c1) {
+  const long long c = c0 + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= c1) return;
   update_cell<DIM, NS>(p, c, Gx, Gy, Gz, Un, Us, out, mode ? *dtp : 0.0, mode);
 }
 

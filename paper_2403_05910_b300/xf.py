@@ -45,6 +45,7 @@ class Opts(C.Structure):
 # every symbol declared in include/xf.h
 EXPORTS = ["xf_create", "xf_destroy", "xf_nv", "xf_cells", "xf_set_state", "xf_set_primitive",
            "xf_get_state", "xf_rhs", "xf_compute_dt", "xf_step_rk3", "xf_step_rk3_n",
+           "xf_step_rk3_host",
            "xf_get_status",
            "xf_clear_status", "xf_status_str", "xf_last_error", "xf_profile_enable",
            "xf_profile_read", "xf_probe_fp64", "xf_rhs_static", "xf_rhs_static_capacity_bytes",
@@ -77,6 +78,7 @@ def _load():
     L.xf_compute_dt.argtypes = [vp, vp, vp]
     L.xf_step_rk3.argtypes = [vp, C.c_double, vp, vp]
     L.xf_step_rk3_n.argtypes = [vp, C.c_int, C.c_double, vp]
+    L.xf_step_rk3_host.argtypes = [vp, vp, vp, vp, vp, C.c_double, vp, vp]
     L.xf_get_status.argtypes = [vp, C.POINTER(C.c_uint32), vp]
     L.xf_clear_status.argtypes = [vp, vp]
     L.xf_status_str.argtypes = [C.c_int]
@@ -238,6 +240,12 @@ class Solver:
 
     def step(self, dt=0.0, dt_dev=None, stream=None):
         check(lib.xf_step_rk3(self.h, float(dt), ptr(dt_dev), stream_ptr(stream)), "xf_step_rk3")
+
+    def step_host(self, U_in, T_in, U_out, T_out=None, dt=0.0, dt_dev=None, stream=None):
+        """One RK3 step of a host-resident state (pinned host buffers overlap
+        the copies with compute); U_out may be U_in."""
+        check(lib.xf_step_rk3_host(self.h, ptr(U_in), ptr(T_in), ptr(U_out), ptr(T_out),
+                                   float(dt), ptr(dt_dev), stream_ptr(stream)), "xf_step_rk3_host")
 
     def steps(self, n, dt=0.0, stream=None):
         """n RK3 steps replayed from a captured CUDA graph (dt <= 0: CFL)."""

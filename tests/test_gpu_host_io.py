@@ -99,3 +99,80 @@ def test_default_warm_start_converges_to_the_same_state():
     b = _run(case, dev(U), None, steps=1)
     assert np.max(np.abs(a[1] - b[1]) / a[1]) <= 1e-12
     assert np.max(field_err(b[0], a[0], case.dim)) <= 1e-12
+
+
+# (case, options, dt): grid sizes give 1, 2 and 8 slabs of the slowest axis
+HOST_STEP = {
+    "sbi3d_n5_8slabs": (lambda: cases.config(2, n=(128, 128, 128)), {}, 0.0),
+    "sbi2d_n3_8slabs_weno7_blend": (lambda: cases.config(1, n=(2048, 1024)),
+                                    {"weno": 7, "positivity": True}, 0.0),
+    "sbi2d_n3_2slabs_dsm": (lambda: cases.with_binary_diffusion(cases.config(1, n=(1024, 512)), seed=1),
+                            {"diffusion": 1}, 0.0),
+    "smooth3d_n3_periodic_2slabs": (lambda: cases.smooth_periodic(3, (64, 64, 128), 3, seed=1, amp=0.3),
+                                    {"weno": 6}, 2e-4),
+    "tube1d_n2_2slabs": (lambda: cases.shock_tube(0, n=1 << 19), {}, 0.0),
+    "sbi2d_n4_1slab": (lambda: cases.config(4, n=(64, 32)), {}, 1e-4),
+}
+
+
+@pytest.mark.parametrize("name", list(HOST_STEP))
+def test_host_step_is_bitwise_set_step_get(name):
+    """xf_step_rk3_host (slabbed uploads and downloads overlapped with the
+    compute) against xf_set_state + xf_step_rk3 + xf_get_state: bitwise equal
+    state, warm start and step size, over two steps with U_out = U_in, and
+    with a NULL warm start."""
+    import torch
+    make, kw, dt = HOST_STEP[name]
+    case = make()
+    s = gpu_solver(case, **kw)
+    s.set_primitive(dev(case.prim))
+    U0 = torch.empty((case.n_v, case.cells), dtype=torch.float64, device="cuda")
+    T0 = torch.empty(case.cells, dtype=torch.float64, device="cuda")
+    s.get_state(U0, T0)
+    dref = torch.zeros(2, dtype=torch.float64, device="cuda")
+    dgot = torch.zeros(2, dtype=torch.float64, device="cuda")
+    for warm in (True, False):
+        # reference: the three calls
+        s.set_state(U0, T0 if warm else None)
+        for k in range(2):
+            s.step(dt, dref[k:k + 1])
+        Ur, Tr = torch.empty_like(U0), torch.empty_like(T0)
+        s.get_state(Ur, Tr)
+        # host step, in place on pinned buffers
+        Uh = U0.cpu().pin_memory()
+        Th = T0.cpu().pin_memory() if warm else None
+        To = torch.empty(case.cells, dtype=torch.float64).pin_memory()
+        s.step_host(Uh, Th, Uh, To, dt, dgot[0:1])
+        s.step_host(Uh, To, Uh, To, dt, dgot[1:2])
+        torch.cuda.synchronize()
+        assert s.status() == 0
+        assert torch.equal(Uh, Ur.cpu()), name
+        assert torch.equal(To, Tr.cpu()), name
+        assert torch.equal(dgot, dref), name
+    s.close()
+
+
+def test_host_step_leaves_the_handle_as_the_three_calls_do():
+    """After xf_step_rk3_host the handle holds U^{n+1} and its warm start, so
+    a plain step can follow it: bitwise the same as three plain steps."""
+    import torch
+    case = cases.config(2, n=(128, 128, 128))
+    s = gpu_solver(case)
+    s.set_primitive(dev(case.prim))
+    U0 = torch.empty((case.n_v, case.cells), dtype=torch.float64, device="cuda")
+    T0 = torch.empty(case.cells, dtype=torch.float64, device="cuda")
+    s.get_state(U0, T0)
+    for _ in range(3):
+        s.step(0.0)
+    Ur = torch.empty_like(U0)
+    s.get_state(Ur)
+    Uh, Th = U0.cpu().pin_memory(), T0.cpu().pin_memory()
+    s.step_host(Uh, Th, Uh, None)
+    s.step(0.0)
+    s.step(0.0)
+    Ug = torch.empty_like(U0)
+    s.get_state(Ug)
+    torch.cuda.synchronize()
+    assert s.status() == 0
+    s.close()
+    assert torch.equal(Ug, Ur)
