@@ -154,13 +154,15 @@ struct Launch {
                        int mode, long long b, long long e, cudaStream_t s) {
     if (e <= b) return;
     const int bs = bsize(e - b, 256);
-    xf::k_update<DIM, NS><<<blocks(e - b, bs), bs, 0, s>>>(p, Gx, Gy, Gz, Un, Us, out, dt,
-                                                            mode, b, e);
+    xf::k_update<DIM, NS, true><<<blocks(e - b, bs), bs, 0, s>>>(p, Gx, Gy, Gz, Un, Us, out,
+                                                                  dt, mode, b, e);
   }
   static void update(const xf::Params& p, const double* Gx, const double* Gy, const double* Gz,
                      const double* Un, const double* Us, double* out, const double* dt, int mode,
                      cudaStream_t s) {
-    update_r(p, Gx, Gy, Gz, Un, Us, out, dt, mode, 0, p.cells, s);
+    const int bs = bsize(p.cells, 256);
+    xf::k_update<DIM, NS><<<blocks(p.cells, bs), bs, 0, s>>>(p, Gx, Gy, Gz, Un, Us, out, dt,
+                                                              mode, 0, p.cells);
   }
   static void from_prim(const xf::Params& p, const double* P, double* U, double* T,
                         cudaStream_t s) {

@@ -1104,15 +1104,22 @@ __device__ __forceinline__ void update_cell(const Params& p, long long c,
   }
 }
 
-// Interior cells [c0, c1), c1 <= cells.
-template <int DIM, int NS>
+// Interior cells [c0, c1), c1 <= cells, with RANGE; every cell without (c0
+// and c1 unused: the whole-grid launches keep the plain index, which runs
+// faster in this memory-bound kernel).
+template <int DIM, int NS, bool RANGE = false>
 __global__ void __launch_bounds__(256)
 k_update(const __grid_constant__ Params p, const double* __restrict__ Gx,
          const double* __restrict__ Gy, const double* __restrict__ Gz,
          const double* Un, const double* Us, double* out, const double* __restrict__ dtp,
          int mode, long long c0, long long c1) {
-  const long long c = c0 + (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= c1) return;
+  long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if constexpr (RANGE) {
+    c += c0;
+    if (c >= c1) return;
+  } else {
+    if (c >= p.cells) return;
+  }
   update_cell<DIM, NS>(p, c, Gx, Gy, Gz, Un, Us, out, mode ? *dtp : 0.0, mode);
 }
 
