@@ -21,26 +21,26 @@ namespace xf {
 
 // ------------------------------------------------------------ WENO5 adjoint
 // Forward intermediates of one WENO5-JS reconstruction, computed exactly as
-// weno5_nd (indicators scaled by 12 c_k with the linear weights folded in,
-// candidates as 6 (q_k - f2)), kept for its reverse. F = f2 + num/den with
-// the factor 6 carried by den.
+// weno5_nd (indicators scaled by 12 c_k with the linear weights folded in, as
+// the sums of squares 16 A^2 + 39/4 x^2 of their LDL^T forms, candidates as
+// 6 (q_k - f2)), kept for its reverse. F = f2 + num/den with the factor 6
+// carried by den.
 struct W5 {
-  double a, b, c, d, t0, u0, t1, u1, t2, u2, s0, s1, s2, p12, p02, p01, w0, w1, w2, q0, q1, q2;
+  double a, b, c, d, A0, B1, D2, s0, s1, s2, p12, p02, p01, w0, w1, w2, q0, q1, q2;
   double num, den;
 };
 
 __device__ __forceinline__ void w5_fwd(double f0, double f1, double f2, double f3, double f4,
                                        const double* e12c, W5& r) {
   r.a = f1 - f0; r.b = f2 - f1; r.c = f3 - f2; r.d = f4 - f3;
-  r.t0 = r.b - r.a; r.u0 = fma(3.0, r.b, -r.a);
-  r.t1 = r.c - r.b; r.u1 = r.b + r.c;
-  r.t2 = r.d - r.c; r.u2 = fma(-3.0, r.c, r.d);
-  r.s0 = fma((13.0 * kWc0) * r.t0, r.t0, fma((3.0 * kWc0) * r.u0, r.u0, e12c[0]));
-  r.s1 = fma((13.0 * kWc1) * r.t1, r.t1, fma((3.0 * kWc1) * r.u1, r.u1, e12c[1]));
-  r.s2 = fma((13.0 * kWc2) * r.t2, r.t2, fma((3.0 * kWc2) * r.u2, r.u2, e12c[2]));
+  r.A0 = fma(-1.375, r.b, r.a); r.B1 = fma(-0.625, r.c, r.b); r.D2 = fma(-1.375, r.c, r.d);
+  const double cc = r.c * r.c;
+  r.s0 = fma((16.0 * kWc0) * r.A0, r.A0, fma((9.75 * kWc0) * r.b, r.b, e12c[0]));
+  r.s1 = fma((16.0 * kWc1) * r.B1, r.B1, fma(9.75 * kWc1, cc, e12c[1]));
+  r.s2 = fma((16.0 * kWc2) * r.D2, r.D2, fma(9.75 * kWc2, cc, e12c[2]));
   r.p12 = r.s1 * r.s2; r.p02 = r.s0 * r.s2; r.p01 = r.s0 * r.s1;
   r.w0 = r.p12 * r.p12; r.w1 = r.p02 * r.p02; r.w2 = r.p01 * r.p01;
-  r.q0 = fma(2.0, r.u0, -r.b);
+  r.q0 = fma(-2.0, r.A0, 2.25 * r.b);
   r.q1 = fma(2.0, r.c, r.b);
   r.q2 = fma(4.0, r.c, -r.d);
   r.num = fma(r.w0, r.q0, fma(r.w1, r.q1, r.w2 * r.q2));
@@ -56,13 +56,16 @@ __device__ __forceinline__ void w5_rev(const W5& r, double nbar, double dbar, do
   const double s0b = fma(p02b, r.s2, p01b * r.s1);
   const double s1b = fma(p12b, r.s2, p01b * r.s0);
   const double s2b = fma(p12b, r.s1, p02b * r.s0);
-  const double t0b = (26.0 * kWc0) * r.t0 * s0b, u0b = fma((6.0 * kWc0) * r.u0, s0b, 2.0 * q0b);
-  const double t1b = (26.0 * kWc1) * r.t1 * s1b, u1b = (6.0 * kWc1) * r.u1 * s1b;
-  const double t2b = (26.0 * kWc2) * r.t2 * s2b, u2b = (6.0 * kWc2) * r.u2 * s2b;
-  const double ab = -t0b - u0b;
-  const double bb = t0b + 3.0 * u0b - t1b + u1b - q0b + q1b;
-  const double cb = t1b + u1b - t2b - 3.0 * u2b + 2.0 * q1b + 4.0 * q2b;
-  const double db = t2b + u2b - q2b;
+  // s_k = 16 c_k L_k^2 + 39/4 c_k x_k^2 + e; A0 = a - 11/8 b, B1 = b - 5/8 c,
+  // D2 = d - 11/8 c; q0 = 9/4 b - 2 A0, q1 = 2c + b, q2 = 4c - d
+  const double A0b = fma((32.0 * kWc0) * r.A0, s0b, -2.0 * q0b);
+  const double B1b = (32.0 * kWc1) * r.B1 * s1b;
+  const double D2b = (32.0 * kWc2) * r.D2 * s2b;
+  const double ab = A0b;
+  const double bb = fma((19.5 * kWc0) * r.b, s0b, fma(2.25, q0b, fma(-1.375, A0b, B1b + q1b)));
+  const double cb = fma(r.c, fma(19.5 * kWc1, s1b, (19.5 * kWc2) * s2b),
+                        fma(2.0, q1b, fma(4.0, q2b, fma(-0.625, B1b, -1.375 * D2b))));
+  const double db = D2b - q2b;
   fb[0] -= ab;
   fb[1] += ab - bb;
   fb[2] += bb - cb;
@@ -99,10 +102,11 @@ __device__ __forceinline__ double weno5_pair_fwd_adj(const double* wp, const dou
 
 // ---------------------------------------------------------- WENO-CU6 adjoint
 // Forward intermediates of one CU6 reconstruction exactly as cu6_nd (12 beta
-// with beta_6 as its LDL^T sum of squares, weights d_k (C s_k + 12 tau) times
-// the other s_j, candidates 6 (q_k - f2)), and the reverse. den carries the 6.
+// with beta_0..2 and beta_6 as LDL^T sums of squares, weights d_k (C s_k +
+// 12 tau) times the other s_j, candidates 6 (q_k - f2)), and the reverse. den
+// carries the 6.
 struct C6 {
-  double a, b, c, d, e, t0, u0, t1, u1, t2, u2, y0, y1, y2, y3, y4;
+  double a, b, c, d, e, A0, B1, D2, y0, y1, y2, y3, y4;
   double s0, s1, s2, s3, p01, p23, g0, g1, g2, g3, w0, w1, w2, w3, q0, q1, q2, q3;
   double num, den;
 };
@@ -110,12 +114,11 @@ struct C6 {
 __device__ __forceinline__ void c6_fwd(double f0, double f1, double f2, double f3, double f4,
                                        double f5, double e12, C6& r) {
   r.a = f1 - f0; r.b = f2 - f1; r.c = f3 - f2; r.d = f4 - f3; r.e = f5 - f4;
-  r.t0 = r.b - r.a; r.u0 = fma(3.0, r.b, -r.a);
-  r.t1 = r.c - r.b; r.u1 = r.b + r.c;
-  r.t2 = r.d - r.c; r.u2 = fma(-3.0, r.c, r.d);
-  const double b0 = fma(13.0 * r.t0, r.t0, 3.0 * r.u0 * r.u0);
-  const double b1 = fma(13.0 * r.t1, r.t1, 3.0 * r.u1 * r.u1);
-  const double b2 = fma(13.0 * r.t2, r.t2, 3.0 * r.u2 * r.u2);
+  r.A0 = fma(-1.375, r.b, r.a); r.B1 = fma(-0.625, r.c, r.b); r.D2 = fma(-1.375, r.c, r.d);
+  const double c975 = 9.75 * r.c * r.c;
+  const double b0 = fma(16.0 * r.A0, r.A0, (9.75 * r.b) * r.b);
+  const double b1 = fma(16.0 * r.B1, r.B1, c975);
+  const double b2 = fma(16.0 * r.D2, r.D2, c975);
   r.y4 = r.e;
   r.y3 = fma(kB6L43, r.e, r.d);
   r.y2 = fma(kB6L42, r.e, fma(kB6L32, r.d, r.c));
@@ -131,7 +134,7 @@ __device__ __forceinline__ void c6_fwd(double f0, double f1, double f2, double f
   r.g2 = fma(0.45 * 20.0, r.s2, t45); r.g3 = fma(0.05 * 20.0, r.s3, t05);
   r.w0 = r.g0 * (r.s1 * r.p23); r.w1 = r.g1 * (r.s0 * r.p23);
   r.w2 = r.g2 * (r.p01 * r.s3); r.w3 = r.g3 * (r.p01 * r.s2);
-  r.q0 = fma(2.0, r.u0, -r.b); r.q1 = fma(2.0, r.c, r.b); r.q2 = fma(4.0, r.c, -r.d);
+  r.q0 = fma(-2.0, r.A0, 2.25 * r.b); r.q1 = fma(2.0, r.c, r.b); r.q2 = fma(4.0, r.c, -r.d);
   r.q3 = fma(6.0, r.c, fma(-5.0, r.d, 2.0 * r.e));
   r.num = fma(r.w0, r.q0, fma(r.w1, r.q1, fma(r.w2, r.q2, r.w3 * r.q3)));
   r.den = 6.0 * ((r.w0 + r.w1) + (r.w2 + r.w3));
@@ -159,14 +162,17 @@ __device__ __forceinline__ void c6_rev(const C6& r, double nbar, double dbar, do
   const double y0b = 2.0 * kB6D[0] * r.y0 * b6b, y1b = 2.0 * kB6D[1] * r.y1 * b6b;
   const double y2b = 2.0 * kB6D[2] * r.y2 * b6b, y3b = 2.0 * kB6D[3] * r.y3 * b6b;
   const double y4b = 2.0 * kB6D[4] * r.y4 * b6b;
-  const double t0b = 26.0 * r.t0 * b0b, u0b = fma(6.0 * r.u0, b0b, 2.0 * q0b);
-  const double t1b = 26.0 * r.t1 * b1b, u1b = 6.0 * r.u1 * b1b;
-  const double t2b = 26.0 * r.t2 * b2b, u2b = 6.0 * r.u2 * b2b;
-  const double ab = y0b - t0b - u0b;
-  const double bb = kB6L10 * y0b + y1b + t0b + 3.0 * u0b - t1b + u1b - q0b + q1b;
-  const double cb = kB6L20 * y0b + kB6L21 * y1b + y2b + t1b + u1b - t2b - 3.0 * u2b + 2.0 * q1b +
+  // b0 = 16 A0^2 + 39/4 b^2, b1 = 16 B1^2 + 39/4 c^2, b2 = 16 D2^2 + 39/4 c^2;
+  // A0 = a - 11/8 b, B1 = b - 5/8 c, D2 = d - 11/8 c; q0 = 9/4 b - 2 A0
+  const double A0b = fma(32.0 * r.A0, b0b, -2.0 * q0b);
+  const double B1b = 32.0 * r.B1 * b1b, D2b = 32.0 * r.D2 * b2b;
+  const double ab = y0b + A0b;
+  const double bb = kB6L10 * y0b + y1b + fma(19.5 * r.b, b0b, fma(2.25, q0b, fma(-1.375, A0b, B1b))) +
+                    q1b;
+  const double cb = kB6L20 * y0b + kB6L21 * y1b + y2b +
+                    fma(19.5 * r.c, b1b + b2b, fma(-0.625, B1b, -1.375 * D2b)) + 2.0 * q1b +
                     4.0 * q2b + 6.0 * q3b;
-  const double db = kB6L30 * y0b + kB6L31 * y1b + kB6L32 * y2b + y3b + t2b + u2b - q2b - 5.0 * q3b;
+  const double db = kB6L30 * y0b + kB6L31 * y1b + kB6L32 * y2b + y3b + D2b - q2b - 5.0 * q3b;
   const double eb = kB6L40 * y0b + kB6L41 * y1b + kB6L42 * y2b + kB6L43 * y3b + y4b + 2.0 * q3b;
   fb[0] -= ab;
   fb[1] += ab - bb;

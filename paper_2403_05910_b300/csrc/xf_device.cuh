@@ -486,6 +486,12 @@ k_grad(const __grid_constant__ Params p, double* __restrict__ Q) {
 // The linear weights d = (0.1, 0.6, 0.3) are folded into the indicators:
 // with s_k scaled by c_k = (d_i d_j / d_k)^(1/4) ({i, j, k} = {0, 1, 2}),
 // (s_i s_j)^2 already carries the factor d_k. The candidates enter as q_k - f2.
+// Each 12 b_k is a positive definite quadratic form in two differences,
+// evaluated as its LDL^T sum of squares (exact in these rationals):
+//   12 b_0 = 16 a^2 - 44 ab + 40 b^2 = 16 (a - 11/8 b)^2 + 39/4 b^2
+//   12 b_1 = 16 b^2 - 20 bc + 16 c^2 = 16 (b - 5/8 c)^2 + 39/4 c^2
+//   12 b_2 = 40 c^2 - 44 cd + 16 d^2 = 16 (d - 11/8 c)^2 + 39/4 c^2
+// (b_1 and b_2 share c^2).
 constexpr double kWc0 = 1.158292185288269;   // (0.6 * 0.3 / 0.1)^(1/4)
 constexpr double kWc1 = 0.4728708045015879;  // (0.1 * 0.3 / 0.6)^(1/4)
 constexpr double kWc2 = 0.668740304976422;   // (0.1 * 0.6 / 0.3)^(1/4)
@@ -494,17 +500,16 @@ constexpr double kWc2 = 0.668740304976422;   // (0.1 * 0.6 / 0.3)^(1/4)
 __device__ __forceinline__ void weno5_nd(double f0, double f1, double f2, double f3, double f4,
                                          const double* e12c, double& num, double& den) {
   const double a = f1 - f0, b = f2 - f1, c = f3 - f2, d = f4 - f3;
-  const double t0 = b - a, u0 = fma(3.0, b, -a);
-  const double t1 = c - b, u1 = b + c;
-  const double t2 = d - c, u2 = fma(-3.0, c, d);
-  const double s0 = fma((13.0 * kWc0) * t0, t0, fma((3.0 * kWc0) * u0, u0, e12c[0]));
-  const double s1 = fma((13.0 * kWc1) * t1, t1, fma((3.0 * kWc1) * u1, u1, e12c[1]));
-  const double s2 = fma((13.0 * kWc2) * t2, t2, fma((3.0 * kWc2) * u2, u2, e12c[2]));
+  const double A0 = fma(-1.375, b, a), B1 = fma(-0.625, c, b), D2 = fma(-1.375, c, d);
+  const double cc = c * c;
+  const double s0 = fma((16.0 * kWc0) * A0, A0, fma((9.75 * kWc0) * b, b, e12c[0]));
+  const double s1 = fma((16.0 * kWc1) * B1, B1, fma(9.75 * kWc1, cc, e12c[1]));
+  const double s2 = fma((16.0 * kWc2) * D2, D2, fma(9.75 * kWc2, cc, e12c[2]));
   const double p12 = s1 * s2, p02 = s0 * s2, p01 = s0 * s1;
   const double w0 = p12 * p12, w1 = p02 * p02, w2 = p01 * p01;
-  // 6 (q_k - f2): 5b - 2a = 2 u0 - b, 2c + b, 4c - d; the factor 6 goes to
-  // the denominator of the field pair (rec_scale)
-  const double q0 = fma(2.0, u0, -b);
+  // 6 (q_k - f2): 5b - 2a = 9/4 b - 2 A0, 2c + b, 4c - d; the factor 6 goes
+  // to the denominator of the field pair (rec_scale)
+  const double q0 = fma(-2.0, A0, 2.25 * b);
   const double q1 = fma(2.0, c, b);
   const double q2 = fma(4.0, c, -d);
   num = fma(w0, q0, fma(w1, q1, w2 * q2));
@@ -537,12 +542,12 @@ constexpr double kB6L43 = -0.38419782506660333;
 __device__ __forceinline__ void cu6_nd(double f0, double f1, double f2, double f3, double f4,
                                        double f5, double e12, double& num, double& den) {
   const double a = f1 - f0, b = f2 - f1, c = f3 - f2, d = f4 - f3, e = f5 - f4;
-  const double t0 = b - a, u0 = fma(3.0, b, -a);
-  const double t1 = c - b, u1 = b + c;
-  const double t2 = d - c, u2 = fma(-3.0, c, d);
-  const double b0 = fma(13.0 * t0, t0, 3.0 * u0 * u0);   // 12 beta_0
-  const double b1 = fma(13.0 * t1, t1, 3.0 * u1 * u1);
-  const double b2 = fma(13.0 * t2, t2, 3.0 * u2 * u2);
+  // 12 beta_0..2 as the sums of squares of weno5_nd
+  const double A0 = fma(-1.375, b, a), B1 = fma(-0.625, c, b), D2 = fma(-1.375, c, d);
+  const double c975 = 9.75 * c * c;
+  const double b0 = fma(16.0 * A0, A0, (9.75 * b) * b);
+  const double b1 = fma(16.0 * B1, B1, c975);
+  const double b2 = fma(16.0 * D2, D2, c975);
   const double y4 = e;
   const double y3 = fma(kB6L43, e, d);
   const double y2 = fma(kB6L42, e, fma(kB6L32, d, c));
@@ -559,7 +564,7 @@ __device__ __forceinline__ void cu6_nd(double f0, double f1, double f2, double f
   const double w2 = fma(0.45 * 20.0, s2, t45) * (p01 * s3);
   const double w3 = fma(0.05 * 20.0, s3, t05) * (p01 * s2);
   // 6 (q_k - f2), as in weno5_nd; q_3: 6c - 5d + 2e
-  const double q0 = fma(2.0, u0, -b);
+  const double q0 = fma(-2.0, A0, 2.25 * b);
   const double q1 = fma(2.0, c, b);
   const double q2 = fma(4.0, c, -d);
   const double q3 = fma(6.0, c, fma(-5.0, d, 2.0 * e));
