@@ -809,14 +809,21 @@ __device__ __forceinline__ void conv_flux(const Params& p, const double* __restr
     double nUv[SW];
 #pragma unroll
     for (int m = 0; m < SW; ++m) nUv[m] = fma(-un, rho_m[m], QF(L::U + 1 + D, m - SO));
+    // the pressure terms p_m (l[m_n]/2 + (u_m/2) l[E]) of the three dense rows
+    // from one product per cell: with lE = Gam/(2c^2) and hl0 = -Gam u_n/(4c^2),
+    // the u -+ c rows take p_m (u_m/2 lE + hl0 -+ c/(4c^2)) and the entropy row
+    // exactly -2 p_m (u_m/2 lE + hl0)
+    const double lE = Gam * hic2, hl0 = -0.5 * Gam * un * hic2, dl = 0.5 * chc;
+    double pV[SW];
+#pragma unroll
+    for (int m = 0; m < SW; ++m) pV[m] = p_m[m] * fma(hun[m], lE, hl0);
     // u - c: l.U = (g.U - c (m_n - u_n rho)) / (2c^2)
     {
-      const double hlmn = 0.5 * (-Gam * un - c) * hic2, lE = Gam * hic2;
       const double ha = 0.5 * am;
 #pragma unroll
       for (int m = 0; m < SW; ++m) {
         const double LU = fma(-chc, nUv[m], gUh[m]);
-        const double pq = p_m[m] * fma(hun[m], lE, hlmn);
+        const double pq = fma(-dl, p_m[m], pV[m]);
         wp[m] = fma(hun[m] + ha, LU, pq);
         wm[m] = fma(hun[m] - ha, LU, pq);
       }
@@ -824,34 +831,32 @@ __device__ __forceinline__ void conv_flux(const Params& p, const double* __restr
     }
     // u + c
     {
-      const double hlmn = 0.5 * (-Gam * un + c) * hic2, lE = Gam * hic2;
       const double ha = 0.5 * ap;
 #pragma unroll
       for (int m = 0; m < SW; ++m) {
         const double LU = fma(chc, nUv[m], gUh[m]);
-        const double pq = p_m[m] * fma(hun[m], lE, hlmn);
+        const double pq = fma(dl, p_m[m], pV[m]);
         wp[m] = fma(hun[m] + ha, LU, pq);
         wm[m] = fma(hun[m] - ha, LU, pq);
       }
       ndp = rec_nd<REC>(wp, wm, e12c);
     }
     rec_div2<REC>(ndm, ndp, Fk_m, Fk_p);
-    // entropy: l = e_rho - g / c^2
-    {
-      const double hlmn = 0.5 * Gam * un * ic2, lE = -Gam * ic2;
-      const double ha = 0.5 * a0;
-#pragma unroll
-      for (int m = 0; m < SW; ++m) {
-        const double LU = fma(-2.0, gUh[m], rho_m[m]);
-        const double pq = p_m[m] * fma(hun[m], lE, hlmn);
-        wp[m] = fma(hun[m] + ha, LU, pq);
-        wm[m] = fma(hun[m] - ha, LU, pq);
-      }
-      nde = rec_nd<REC>(wp, wm, e12c);
-    }
+    // (u_m +- |u|max)/2, shared by the entropy row and the passive fields
     const double ha0 = 0.5 * a0;
 #pragma unroll
     for (int m = 0; m < SW; ++m) { hp0[m] = hun[m] + ha0; hm0[m] = hun[m] - ha0; }
+    // entropy: l = e_rho - g / c^2
+    {
+#pragma unroll
+      for (int m = 0; m < SW; ++m) {
+        const double LU = fma(-2.0, gUh[m], rho_m[m]);
+        const double pq = -2.0 * pV[m];
+        wp[m] = fma(hp0[m], LU, pq);
+        wm[m] = fma(hm0[m], LU, pq);
+      }
+      nde = rec_nd<REC>(wp, wm, e12c);
+    }
     // the entropy field shares its division with the first passive field
     if constexpr (NPASS > 0) rec_div2<REC>(nde, passive_nd(0), Fk_e, Fk_first);
     else Fk_e = rec_div1<REC>(nde);
