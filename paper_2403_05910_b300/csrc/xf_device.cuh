@@ -987,61 +987,78 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
   if (p.convective && p.positivity && dt > 0.0) pos_blend<DIM, NS, D>(p, q0, PC, sd, dt, Gout);
 
   if (p.viscous) {
-    // face values (-1, 9, 9, -1)/16, normal derivatives (1, -15, 15, -1)/(12 dx)
+    // face values (-1, 9, 9, -1)/16, normal derivatives (1, -15, 15, -1)/(12 dx).
+    // FI0 / FD0 leave out the factors 1/16 and 1/(12 dx); each product below
+    // takes them once (wi, wd, wid = wi wd).
     const double wi = 1.0 / 16.0;
     const double wd = p.inv_dx[D] * (1.0 / 12.0);
-#define FI(field) ((9.0 * (QF(field, 0) + QF(field, 1)) - (QF(field, -1) + QF(field, 2))) * wi)
-#define FD(field) ((15.0 * (QF(field, 1) - QF(field, 0)) - (QF(field, 2) - QF(field, -1))) * wd)
-    const double mu = FI(L::MU), ka = FI(L::KA), rf = FI(L::U), Tf = FI(L::T);
-    double uf[DIM], gr[DIM][DIM];
+    const double wid = wi * wd;
+#define FI0(field) (fma(9.0, QF(field, 0) + QF(field, 1), -(QF(field, -1) + QF(field, 2))))
+#define FD0(field) (fma(15.0, QF(field, 1) - QF(field, 0), -(QF(field, 2) - QF(field, -1))))
+#define FI(field) (FI0(field) * wi)
+#define FD(field) (FD0(field) * wd)
+    const double mu = FI(L::MU), rf = FI(L::U);
+    double gr[DIM][DIM];
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
-      uf[a] = FI(L::UN + a);
 #pragma unroll
       for (int b = 0; b < DIM; ++b) gr[a][b] = (b == D) ? FD(L::UN + a) : FI(L::GU + a * DIM + b);
     }
     double div = 0.0;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) div += gr[a][a];
-    double work = 0.0;
+    double work16 = 0.0;  // 16 sum_a tau_a u_a
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
       double tau = mu * (gr[D][a] + gr[a][D]);
       if (a == D) tau = fma(-2.0 / 3.0 * mu, div, tau);
       Gout[1 + a] -= tau;
-      work = fma(tau, uf[a], work);
+      work16 = fma(tau, FI0(L::UN + a), work16);
     }
     // species fluxes of Eq. 6 with the mixture correction: D_s = D for every
-    // species (diffusion = 0) or the face values of the cells' D_sm
-    double dY[NS], Yf[NS], Dsf[NS], corr = 0.0;
+    // species (diffusion = 0) or the face values of the cells' D_sm. With
+    // dY0 = 12 dx dY/dn, Yf0 = 16 Y_f, Ds0 = 16 D_s:
+    // J_s = -rho_f (D_s dY_s - Y_s corr) = nrf (Ds0 dY0_s - Yf0_s corr0),
+    // nrf = -rho_f wid, corr0 = wi sum_t Ds0_t dY0_t
+    double dY0[NS], Yf0[NS], Ds0[NS], corr0;
     if (p.diffusion == 1) {
+      double c = 0.0;
 #pragma unroll
       for (int s = 0; s < NS; ++s) {
-        dY[s] = FD(L::Y + s); Yf[s] = FI(L::Y + s); Dsf[s] = FI(L::DS + s);
-        corr = fma(Dsf[s], dY[s], corr);
+        dY0[s] = FD0(L::Y + s); Yf0[s] = FI0(L::Y + s); Ds0[s] = FI0(L::DS + s);
+        c = fma(Ds0[s], dY0[s], c);
       }
+      corr0 = c * wi;
     } else {
-      const double Df = FI(L::DF);
+      const double Df0 = FI0(L::DF);
       double sdY = 0.0;
 #pragma unroll
-      for (int s = 0; s < NS; ++s) { dY[s] = FD(L::Y + s); Yf[s] = FI(L::Y + s); sdY += dY[s]; Dsf[s] = Df; }
-      corr = Df * sdY;
+      for (int s = 0; s < NS; ++s) { dY0[s] = FD0(L::Y + s); Yf0[s] = FI0(L::Y + s); sdY += dY0[s]; Ds0[s] = Df0; }
+      corr0 = (Df0 * wi) * sdY;
     }
-    const TauPt tp = tau_of(p, Tf);
+    const double nrf = -rf * wid;
+    // h_s at the face temperature T_f = wi FI0(T)
+    TauPt tp;
+    {
+      const double tau = fma(FI0(L::T), wi * p.inv_span, -p.T_lo * p.inv_span);
+      tp.tc = fmin(fmax(tau, 0.0), 1.0);
+      tp.ext = p.span * (tau - tp.tc);
+    }
     double qd = 0.0;
     double J[NS];
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-      J[s] = -rf * fma(Dsf[s], dY[s], -Yf[s] * corr);
+      J[s] = nrf * fma(Ds0[s], dY0[s], -Yf0[s] * corr0);
       const double hs = h_s_in(p, s, tp);
       qd = fma(hs, J[s], qd);
     }
-    const double dT = FD(L::T);
-    Gout[IE] -= fma(ka, dT, work) - qd;
+    Gout[IE] -= fma(FI0(L::KA) * wid, FD0(L::T), fma(work16, wi, -qd));
 #pragma unroll
     for (int s = 0; s < NS - 1; ++s) Gout[IE + 1 + s] += J[s];
 #undef FI
 #undef FD
+#undef FI0
+#undef FD0
   }
 #undef QF
 #pragma unroll
