@@ -698,22 +698,25 @@ __device__ __forceinline__ void conv_flux(const Params& p, const double* __restr
 #pragma unroll
   for (int s = 0; s < NS; ++s) Yb[s] = fma(tL, QF(L::Y + s, 0), tR * QF(L::Y + s, 1));
   const TauPt tp = tau_of(p, Tb);
-  double es[NS], Rb = 0.0, cvb = 0.0;
+  double hs[NS], Rb = 0.0, cpb = 0.0;
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
-    const double cps = cp_s(p, s, tp.tc);
-    es[s] = h_s_in(p, s, tp) - p.r[s] * Tb;
+    hs[s] = h_s_in(p, s, tp);
     Rb = fma(Yb[s], p.r[s], Rb);
-    cvb = fma(Yb[s], cps - p.r[s], cvb);
+    cpb = fma(Yb[s], cp_s(p, s, tp.tc), cpb);
   }
+  const double cvb = cpb - Rb;
   // one division for Gamma = R/c_v and its inverse
   const double rRc = 1.0 / (Rb * cvb);
   const double Gam = Rb * Rb * rRc;
   const double hq2 = 0.5 * q2;
+  // phi_s = R_s T - Gamma (e_s - |u|^2/2) with e_s = h_s - R_s T:
+  // R_s (1 + Gamma) T - Gamma h_s + Gamma |u|^2/2
+  const double T1G = fma(Gam, Tb, Tb), Gq2 = Gam * hq2;
   double phi[NS], c2 = 0.0;
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
-    phi[s] = fma(p.r[s], Tb, -Gam * (es[s] - hq2));
+    phi[s] = fma(p.r[s], T1G, fma(-Gam, hs[s], Gq2));
     c2 = fma(Yb[s], phi[s], c2);
   }
   c2 = fma(Gam, Hb - q2, c2);
