@@ -309,7 +309,7 @@ __device__ __forceinline__ double rec_pair_fwd_adj(const double* wp, const doubl
 
 // d c_p,s / dT at a clamped tau (0 outside the polynomial range)
 __device__ __forceinline__ double dcp_s(const Params& p, int s, double T) {
-  const double tau = (T - p.T_lo) * p.inv_span;
+  const double tau = fma(T, p.inv_span, p.tau0);  // as tau_of
   if (!(tau > 0.0 && tau < 1.0)) return 0.0;
   const double* a = p.rcp[s];
   return fma(fma(fma(4.0 * a[4], tau, 3.0 * a[3]), tau, 2.0 * a[2]), tau, a[1]) * p.inv_span;
@@ -601,14 +601,7 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
       for (int s = 0; s < NS - 1; ++s) g = fma(gs[s], QF(L::U + IE + 1 + s, o), g);
       gUh[m] = g;
     }
-    const double eps12 = 12.0 * p.weno_eps;
-    double e12c[4];
-    if constexpr (REC == 7) {
-      const double e240 = 240.0 * p.weno_eps;
-      e12c[0] = e240 * kW7c0; e12c[1] = e240 * kW7c1; e12c[2] = e240 * kW7c2; e12c[3] = e240 * kW7c3;
-    } else {
-      e12c[0] = eps12 * kWc0; e12c[1] = eps12 * kWc1; e12c[2] = eps12 * kWc2; e12c[3] = eps12;
-    }
+    const double e12c[4] = {p.wenoe[0], p.wenoe[1], p.wenoe[2], p.wenoe[3]};
     const double chc = c * hic2;
     const double ha_m = 0.5 * am, ha_p = 0.5 * ap, ha0 = 0.5 * a0;
     const double hlmn_m = 0.5 * (-Gam * un - c) * hic2, hlmn_p = 0.5 * (-Gam * un + c) * hic2;

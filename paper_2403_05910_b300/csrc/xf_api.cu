@@ -327,6 +327,7 @@ xf_status fill_params(const xf_grid* g, const xf_thermo* th, const xf_opts* o, x
   p->T_lo = th->T_lo;
   p->span = th->T_hi - th->T_lo;
   p->inv_span = 1.0 / p->span;
+  p->tau0 = -th->T_lo * p->inv_span;
   for (int s = 0; s < N; ++s) {
     if (!(th->W[s] > 0.0)) return XF_ERR_ARG;
     const double r = Ru / th->W[s] / th->a_ref2;
@@ -358,6 +359,15 @@ xf_status fill_params(const xf_grid* g, const xf_thermo* th, const xf_opts* o, x
   p->inv_lewis = o->viscous ? 1.0 / th->lewis : 0.0;
   p->cfl = o->cfl;
   p->weno_eps = o->weno_eps;
+  if (o->weno == 7) {
+    const double e240 = 240.0 * o->weno_eps;
+    p->wenoe[0] = e240 * xf::kW7c0; p->wenoe[1] = e240 * xf::kW7c1;
+    p->wenoe[2] = e240 * xf::kW7c2; p->wenoe[3] = e240 * xf::kW7c3;
+  } else {
+    const double e12 = 12.0 * o->weno_eps;
+    p->wenoe[0] = e12 * xf::kWc0; p->wenoe[1] = e12 * xf::kWc1; p->wenoe[2] = e12 * xf::kWc2;
+    p->wenoe[3] = e12;
+  }
   p->weno = o->weno;
   p->newton_rtol = o->newton_rtol;
   p->newton_max = o->newton_max;

@@ -37,6 +37,7 @@ struct Params {
   double inv_dx[3];
   // thermo, dimensionless (R_s / a_ref^2 pre-multiplied)
   double T_lo, span, inv_span;
+  double tau0;            // -T_lo / span: tau = T inv_span + tau0
   double r[MAXN];         // R_s / a_ref^2
   double rcp[MAXN][5];    // r_s cp_j: c_p,s = sum_j rcp[s][j] tau^j
   double rh[MAXN][5];     // r_s span cp_j/(j+1): h_s = rhoff_s + sum_j rh[s][j] tau^(j+1)
@@ -52,6 +53,8 @@ struct Params {
   double fdsm;                   // rho_ref a_ref^3 L_ref: 1/D*_st = p* fdsm exp(-ln(p D_st))
   // numerics
   double cfl, weno_eps, newton_rtol;
+  double wenoe[4];   // epsilon terms of the reconstruction (rec_nd): 12 eps c_k
+                     // (k < 3) and 12 eps for WENO5 / CU6, 240 eps c_k for WENO7
   int viscous, convective, newton_max;
   int weno;          // 5: WENO5-JS, 6: WENO-CU6
   int positivity;    // positivity-preserving blend of the convective flux (Eq. 17-20)
@@ -108,7 +111,7 @@ struct TauPt {
   double ext;  // span * (tau - tc)
 };
 __device__ __forceinline__ TauPt tau_of(const Params& p, double T) {
-  double tau = (T - p.T_lo) * p.inv_span;
+  double tau = fma(T, p.inv_span, p.tau0);
   double tc = fmin(fmax(tau, 0.0), 1.0);
   TauPt r;
   r.tc = tc;
@@ -764,15 +767,7 @@ __device__ __forceinline__ void conv_flux(const Params& p, const double* __restr
     for (int s = 0; s < NS - 1; ++s) g = fma(gs[s], QF(L::U + IE + 1 + s, o), g);
     gUh[m] = g;
   }
-  const double eps12 = 12.0 * p.weno_eps;
-  double e12c[4];
-  if constexpr (REC == 7) {
-    const double e240 = 240.0 * p.weno_eps;
-    e12c[0] = e240 * kW7c0; e12c[1] = e240 * kW7c1;
-    e12c[2] = e240 * kW7c2; e12c[3] = e240 * kW7c3;
-  } else {
-    e12c[0] = eps12 * kWc0; e12c[1] = eps12 * kWc1; e12c[2] = eps12 * kWc2; e12c[3] = eps12;
-  }
+  const double e12c[4] = {p.wenoe[0], p.wenoe[1], p.wenoe[2], p.wenoe[3]};
   const double chc = c * hic2;
   // ---- PER: one characteristic field at a time. With w = (1/2)(l.F_m +- a l.U_m)
   //      and l.F_m = u_m (l.U_m) + p_m (l[m_n] + u_m l[E]):
@@ -1043,7 +1038,7 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
     // h_s at the face temperature T_f = wi FI0(T)
     TauPt tp;
     {
-      const double tau = fma(FI0(L::T), wi * p.inv_span, -p.T_lo * p.inv_span);
+      const double tau = fma(FI0(L::T), wi * p.inv_span, p.tau0);
       tp.tc = fmin(fmax(tau, 0.0), 1.0);
       tp.ext = p.span * (tau - tp.tc);
     }
