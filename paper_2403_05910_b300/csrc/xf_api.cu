@@ -328,6 +328,7 @@ xf_status fill_params(const xf_grid* g, const xf_thermo* th, const xf_opts* o, x
   p->span = th->T_hi - th->T_lo;
   p->inv_span = 1.0 / p->span;
   p->tau0 = -th->T_lo * p->inv_span;
+  for (int j = 0; j < 5; ++j) p->hsj[j] = p->span / (j + 1);
   for (int s = 0; s < N; ++s) {
     if (!(th->W[s] > 0.0)) return XF_ERR_ARG;
     const double r = Ru / th->W[s] / th->a_ref2;

@@ -38,6 +38,7 @@ struct Params {
   // thermo, dimensionless (R_s / a_ref^2 pre-multiplied)
   double T_lo, span, inv_span;
   double tau0;            // -T_lo / span: tau = T inv_span + tau0
+  double hsj[5];          // span / (j + 1): rh[s][j] = rcp[s][j] hsj[j]
   double r[MAXN];         // R_s / a_ref^2
   double rcp[MAXN][5];    // r_s cp_j: c_p,s = sum_j rcp[s][j] tau^j
   double rh[MAXN][5];     // r_s span cp_j/(j+1): h_s = rhoff_s + sum_j rh[s][j] tau^(j+1)
@@ -192,20 +193,19 @@ __device__ __forceinline__ void prim_cell(const Params& p, long long t, const do
     Y[NS - 1] = 1.0 - ysum;
     const double e = fma(E, irho, -0.5 * ke);
     // mixture polynomial coefficients: c_p(tau) = sum A_j tau^j,
-    // h(tau) = B + sum Ah_j tau^(j+1), R = Rm
+    // h(tau) = B + sum Ah_j tau^(j+1) with Ah_j = A_j span/(j+1), R = Rm
     double A[5], Ah[5], Rm = 0.0, B = 0.0;
 #pragma unroll
-    for (int jj = 0; jj < 5; ++jj) { A[jj] = 0.0; Ah[jj] = 0.0; }
+    for (int jj = 0; jj < 5; ++jj) A[jj] = 0.0;
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
       Rm = fma(Y[s], p.r[s], Rm);
       B = fma(Y[s], p.rhoff[s], B);
 #pragma unroll
-      for (int jj = 0; jj < 5; ++jj) {
-        A[jj] = fma(Y[s], p.rcp[s][jj], A[jj]);
-        Ah[jj] = fma(Y[s], p.rh[s][jj], Ah[jj]);
-      }
+      for (int jj = 0; jj < 5; ++jj) A[jj] = fma(Y[s], p.rcp[s][jj], A[jj]);
     }
+#pragma unroll
+    for (int jj = 0; jj < 5; ++jj) Ah[jj] = A[jj] * p.hsj[jj];
     // Newton (Eq. 21): T <- T + (e - e(T)) / c_v(T), stop at |dT| <= rtol T;
     // a non-positive iterate is replaced by half the previous one
     double T = ld(Tin + src);

@@ -37,6 +37,19 @@ def _dirs(rng, U, k, rel=1.0):
     return rng.normal(size=(k,) + U.shape) * sc * rel
 
 
+def _rhs_tol(name):
+    """Tolerance of an RHS-adjoint dot test on a case. The shock-bubble
+    states carry near-ties of the LLF maxima: the tanh tails of the bubble
+    interface make the ambient cells' |u -+ c| differ by one ulp (an oracle
+    scan of the 24x14 state finds two such faces for the 6-cell stencils and
+    one for WENO7's 8 cells, relative gaps 1.9e-16). Which cell is the maximum
+    there, and so which cell receives the one-sided derivative of alpha, is
+    decided by round-off that the GPU and the oracle need not share; the
+    flip moves the dot products by ~1e-9 relative. Those states are held to
+    1e-7, the rest (smooth fields, the shock tube) to 1e-10."""
+    return 1e-7 if name.startswith("sbi") else 1e-10
+
+
 def _dot_check(lhs, rhs, tol):
     lhs, rhs = np.asarray(lhs), np.asarray(rhs)
     assert np.all(np.abs(lhs - rhs) <= tol * (np.abs(rhs) + np.abs(lhs)).max()), (lhs, rhs)
@@ -61,7 +74,7 @@ def test_rhs_adjoint_matches_oracle_jvp(name):
     Ubar = Ub.cpu().numpy()
     lhs = [np.sum(Ubar * V[k]) for k in range(8)]
     rhs = [np.sum(W * JV[k]) for k in range(8)]
-    _dot_check(lhs, rhs, 1e-10)
+    _dot_check(lhs, rhs, _rhs_tol(name))
     s.close()
 
 
@@ -184,7 +197,7 @@ def test_rhs_adjoint_with_mixture_diffusion_matches_oracle_jvp(name):
     Ubar = Ub.cpu().numpy()
     lhs = [np.sum(Ubar * V[k]) for k in range(8)]
     rhs = [np.sum(W * JV[k]) for k in range(8)]
-    _dot_check(lhs, rhs, 1e-10)
+    _dot_check(lhs, rhs, _rhs_tol(name))
     s.close()
 
 
@@ -284,7 +297,7 @@ def test_rhs_adjoint_with_cu6_and_weno7_matches_oracle_jvp(name, weno):
     Ubar = Ub.cpu().numpy()
     lhs = [np.sum(Ubar * V[k]) for k in range(8)]
     rhs = [np.sum(W * JV[k]) for k in range(8)]
-    _dot_check(lhs, rhs, 1e-10)
+    _dot_check(lhs, rhs, _rhs_tol(name))
     s.close()
 
 
