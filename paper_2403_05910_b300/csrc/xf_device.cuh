@@ -110,14 +110,25 @@ __device__ __forceinline__ int map_axis(int i, int n, int lo, int hi, bool* flip
 struct TauPt {
   double tc;   // clamped tau
   double ext;  // span * (tau - tc)
+  bool in;     // tau in [0, 1] (then tc = tau, ext = 0)
 };
-__device__ __forceinline__ TauPt tau_of(const Params& p, double T) {
-  double tau = fma(T, p.inv_span, p.tau0);
-  double tc = fmin(fmax(tau, 0.0), 1.0);
+__device__ __forceinline__ TauPt tau_pt(const Params& p, double tau) {
   TauPt r;
-  r.tc = tc;
-  r.ext = p.span * (tau - tc);
+  // the range test on the bit pattern (non-negative doubles order as
+  // integers) keeps the common in-range case off the FP64 pipe
+  const long long b = __double_as_longlong(tau);
+  r.in = b >= 0 && b <= 0x3FF0000000000000LL;
+  if (r.in) {
+    r.tc = tau;
+    r.ext = 0.0;
+  } else {
+    r.tc = fmin(fmax(tau, 0.0), 1.0);
+    r.ext = p.span * (tau - r.tc);
+  }
   return r;
+}
+__device__ __forceinline__ TauPt tau_of(const Params& p, double T) {
+  return tau_pt(p, fma(T, p.inv_span, p.tau0));
 }
 __device__ __forceinline__ double cp_s(const Params& p, int s, double tc) {
   const double* a = p.rcp[s];
@@ -130,12 +141,12 @@ __device__ __forceinline__ double h_s(const Params& p, int s, const TauPt& t, do
 }
 
 // h_s alone: the c_p term of the linear continuation is evaluated only when T
-// lies outside [T_lo, T_hi] (ext != 0); inside, the result is the same bits.
+// lies outside [T_lo, T_hi]; inside (ext = 0), the result is the same bits.
 __device__ __forceinline__ double h_s_in(const Params& p, int s, const TauPt& t) {
   const double* a = p.rh[s];
   const double poly = fma(fma(fma(fma(a[4], t.tc, a[3]), t.tc, a[2]), t.tc, a[1]), t.tc, a[0]);
   const double h = fma(poly, t.tc, p.rhoff[s]);
-  return t.ext != 0.0 ? fma(cp_s(p, s, t.tc), t.ext, h) : h;
+  return t.in ? h : fma(cp_s(p, s, t.tc), t.ext, h);
 }
 
 // ------------------------------------------------------------ status ------
@@ -214,7 +225,7 @@ __device__ __forceinline__ void prim_cell(const Params& p, long long t, const do
       const TauPt tp = tau_of(p, T);
       const double cpm = fma(fma(fma(fma(A[4], tp.tc, A[3]), tp.tc, A[2]), tp.tc, A[1]), tp.tc, A[0]);
       const double hp = fma(fma(fma(fma(fma(Ah[4], tp.tc, Ah[3]), tp.tc, Ah[2]), tp.tc, Ah[1]), tp.tc, Ah[0]), tp.tc, B);
-      const double eT = fma(cpm, tp.ext, hp) - Rm * T;
+      const double eT = (tp.in ? hp : fma(cpm, tp.ext, hp)) - Rm * T;
       double Tn = T + (e - eT) / (cpm - Rm);
       if (!(Tn > 0.0)) Tn = 0.5 * T;
       conv = fabs(Tn - T) <= p.newton_rtol * Tn;
@@ -1036,12 +1047,7 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
     }
     const double nrf = -rf * wid;
     // h_s at the face temperature T_f = wi FI0(T)
-    TauPt tp;
-    {
-      const double tau = fma(FI0(L::T), wi * p.inv_span, p.tau0);
-      tp.tc = fmin(fmax(tau, 0.0), 1.0);
-      tp.ext = p.span * (tau - tp.tc);
-    }
+    const TauPt tp = tau_pt(p, fma(FI0(L::T), wi * p.inv_span, p.tau0));
     double qd = 0.0;
     double J[NS];
 #pragma unroll
