@@ -14,7 +14,7 @@ What it generates (the workloads of the XFluids paper, arXiv 2403.05910):
   the frozen-gamma Rankine-Hugoniot post-shock state of Eq. 33 and a bubble
   whose interface follows the tanh profile of Eq. 32 in molar fraction;
 * a batched ensemble of uneven 2D shock-bubble instances;
-* the 1D multicomponent diffusion case (Sec. VI.B, Table IV) with seeded
+* the 1D multicomponent diffusion case (Sec. IV.B, Table IV) with seeded
   binary diffusion fits for the mixture-averaged model of Eq. 25-26;
 * small smooth periodic fields used by the tests.
 
@@ -402,7 +402,7 @@ DIFF_Y = ((0.195, 0.591, 0.0, 0.214),           # fuel side
 
 def multicomponent_diffusion(n: int = 200, seed: int = 0, length: float = 0.05,
                              d: float = 0.0025, x0: float = 0.025) -> Case:
-    """1D multicomponent diffusion (Sec. VI.B, Eq. 30, Table IV) with synthetic
+    """1D multicomponent diffusion (Sec. IV.B, Eq. 30, Table IV) with synthetic
     species data: a periodic domain of ``length`` metres on ``n`` cells,
     p = 1 atm, u = 0, and T, Y_k = oxidizer value + (fuel - oxidizer) f(x) with
     f(x) = 1 - 0.5 exp(-(x - x0)^2/d^2) (reading: the printed exponent lost its

@@ -1,6 +1,6 @@
 """Mixture-averaged species diffusion (Eq. 25-26, xf_opts.diffusion = 1) on
 the GPU: parity with the oracle's model on the RHS, one step and ten steps,
-including the 1D multicomponent diffusion case of Sec. VI.B (Table IV,
+including the 1D multicomponent diffusion case of Sec. IV.B (Table IV,
 synthetic species); conservation over a long run of that case; the batched
 form with the model. Its adjoint is checked in test_gpu_adjoint.py.
 

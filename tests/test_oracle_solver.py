@@ -682,7 +682,7 @@ def test_dsm_rhs_is_invariant_under_species_relabelling():
 
 
 def test_multicomponent_diffusion_case_conserves_and_mixes():
-    """The 1D multicomponent diffusion case (Sec. VI.B, Table IV, synthetic
+    """The 1D multicomponent diffusion case (Sec. IV.B, Table IV, synthetic
     species, mixture-averaged D_sm): on the periodic domain every species'
     mass and the total energy are conserved to round-off, the fuel-side
     bump of CH4 decays monotonically, and the pressure stays uniform to
