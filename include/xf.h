@@ -279,6 +279,11 @@ xf_status xf_profile_read(xf_handle *h, double *ms, int64_t *launches);
  * in TFLOP/s counting an FMA as two flops. Synchronises the device. Used to
  * state the measured FP64 ceiling beside the nominal one. */
 xf_status xf_probe_fp64(int64_t iters, int blocks_per_sm, double *tflops);
+/* The reciprocal the kernels use in place of division (Newton-Raphson
+ * refinement of the hardware approximation; tooling, no counterpart in the
+ * paper): y[i] = that reciprocal of x[i] and ref[i] = the correctly rounded
+ * 1.0 / x[i], for device arrays of n doubles. Enqueued on `stream`. */
+xf_status xf_probe_rcp(const double *x, double *y, double *ref, int64_t n, void *stream);
 
 /* ---- Batched form: many independent 2D instances (uneven grids, N = 2..5)
  * advanced together. Each RK stage is ONE persistent cooperative kernel that

@@ -340,6 +340,7 @@ xf_status fill_params(const xf_grid* g, const xf_thermo* th, const xf_opts* o, x
     }
     p->rhoff[s] = r * th->h_off[s];
     p->invW[s] = 1.0 / th->W[s];
+    p->Wm[s] = th->W[s];
     if (o->viscous) {
       for (int j = 0; j < 4; ++j) {
         p->lnmu[s][j] = th->mu_coef[s * 4 + j];
@@ -510,6 +511,15 @@ void lincomb(const xf_handle* h, double a, const double* x, double b, const doub
              const double* z, double* out, cudaStream_t s) {
   const long long n = (long long)h->p.nv * h->p.cells;
   k_lincomb<<<blocks(n, 256), 256, 0, s>>>(n, a, x, b, y, c, z, out);
+}
+
+// rcp_nr beside the correctly rounded division, element by element
+__global__ void k_probe_rcp(const double* __restrict__ x, double* __restrict__ y,
+                            double* __restrict__ ref, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  y[i] = xf::rcp_nr(x[i]);
+  ref[i] = 1.0 / x[i];
 }
 
 __global__ void k_probe_fp64(double* out, long long iters, double a) {
@@ -1117,6 +1127,15 @@ xf_status xf_profile_read(xf_handle* h, double* ms, int64_t* launches) {
   }
   h->recs.clear();
   return st;
+}
+
+xf_status xf_probe_rcp(const double* x, double* y, double* ref, int64_t n, void* stream) {
+  if (!x || !y || !ref || n < 0) return XF_ERR_ARG;
+  if (n == 0) return XF_OK;
+  if (!is_device_ptr(x) || !is_device_ptr(y) || !is_device_ptr(ref)) return XF_ERR_ARG;
+  k_probe_rcp<<<blocks(n, 256), 256, 0, (cudaStream_t)stream>>>(x, y, ref, n);
+  XF_CUDA(cudaGetLastError());
+  return XF_OK;
 }
 
 xf_status xf_probe_fp64(int64_t iters, int blocks_per_sm, double* tflops) {

@@ -47,7 +47,7 @@ struct Params {
   double lnmu[MAXN][4], lnka[MAXN][4];
   double wA[MAXN][MAXN], wB[MAXN][MAXN];  // Wilke: A = (1+W_s/W_t)^-1/2 / sqrt 8, B = (W_t/W_s)^1/4
   double wAB[MAXN][MAXN], wABB[MAXN][MAXN];  // A B and A B^2
-  double invW[MAXN];
+  double invW[MAXN], Wm[MAXN];  // 1/W_s and W_s (kg/mol)
   double fmu, fka, inv_lewis;
   int diffusion;                 // 0: D = kappa/(rho c_p Le); 1: mixture-averaged D_sm (Eq. 26)
   double dbin[MAXN][MAXN][4];    // ln(p D_st [Pa m^2/s]) cubic in ln T (Eq. 25, form of Eq. 29)
@@ -85,6 +85,23 @@ struct Lay {
 };
 
 __device__ __forceinline__ double ld(const double* p) { return __ldg(p); }
+
+// 1/x by Newton-Raphson iteration for the reciprocal (M. J. Flynn, "On
+// division by functional iteration", IEEE Trans. Computers C-19, 1970),
+// started from the PTX approximation rcp.approx.ftz.f64: each step
+// y <- y + y (1 - x y) doubles the number of correct bits, two steps reach
+// double precision. For normal finite x (a subnormal x is flushed to zero,
+// x = 0 or +-inf give NaN): the hot-path divisors (densities, heat
+// capacities, WENO weight sums, mole-fraction sums) are all of that kind.
+// xf_probe_rcp compares it with the correctly rounded 1.0 / x.
+__device__ __forceinline__ double rcp_nr(double x) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  double e = fma(-x, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-x, y, 1.0);
+  return fma(y, e, y);
+}
 
 // max of two non-negative doubles through their ordered bit patterns (integer
 // pipe; the FP64 pipe is the scarce unit)
@@ -193,7 +210,7 @@ __device__ __forceinline__ void prim_cell(const Params& p, long long t, const do
 #pragma unroll
     for (int v = 0; v < NV; ++v) finite = finite && isfinite(u[v]);
     const double rho = u[0];
-    const double irho = 1.0 / rho;
+    const double irho = rcp_nr(rho);
     double vel[DIM], ke = 0.0;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) { vel[a] = u[1 + a] * irho; ke = fma(vel[a], vel[a], ke); }
@@ -226,7 +243,7 @@ __device__ __forceinline__ void prim_cell(const Params& p, long long t, const do
       const double cpm = fma(fma(fma(fma(A[4], tp.tc, A[3]), tp.tc, A[2]), tp.tc, A[1]), tp.tc, A[0]);
       const double hp = fma(fma(fma(fma(fma(Ah[4], tp.tc, Ah[3]), tp.tc, Ah[2]), tp.tc, Ah[1]), tp.tc, Ah[0]), tp.tc, B);
       const double eT = (tp.in ? hp : fma(cpm, tp.ext, hp)) - Rm * T;
-      double Tn = T + (e - eT) / (cpm - Rm);
+      double Tn = fma(e - eT, rcp_nr(cpm - Rm), T);
       if (!(Tn > 0.0)) Tn = 0.5 * T;
       conv = fabs(Tn - T) <= p.newton_rtol * Tn;
       T = Tn;
@@ -238,7 +255,8 @@ __device__ __forceinline__ void prim_cell(const Params& p, long long t, const do
     const double cvm = cpm - Rm;
     const double RT = Rm * T;
     const double pr = rho * RT;
-    const double c2 = cpm * RT / cvm;
+    const double icvm = rcp_nr(cvm);
+    const double c2 = cpm * RT * icvm;
     const double c = sqrt(c2);
     const double H = (E + pr) * irho;
     if (!finite || !(rho > 0.0) || !(pr > 0.0) || !(T > 0.0)) st |= 1u;
@@ -275,7 +293,7 @@ __device__ __forceinline__ void prim_cell(const Params& p, long long t, const do
         pre[0] = smu[0];
 #pragma unroll
         for (int k = 1; k < 2 * NS; ++k) pre[k] = pre[k - 1] * (k < NS ? smu[k] : ska[k - NS]);
-        double inv = 1.0 / pre[2 * NS - 1];
+        double inv = rcp_nr(pre[2 * NS - 1]);
 #pragma unroll
         for (int k = 2 * NS - 1; k > 0; --k) {
           const double v = k < NS ? smu[k] : ska[k - NS];
@@ -285,7 +303,7 @@ __device__ __forceinline__ void prim_cell(const Params& p, long long t, const do
         }
         ismu[0] = inv;
       }
-      const double ixs = 1.0 / xs;
+      const double ixs = rcp_nr(xs);
       // Wilke denominators sum_t X_t A_st (1 + r_st B_st)^2 with r_st = (a_s/a_t)^(1/2),
       // expanded: S0_s + 2 sqrt(a_s) S1_s + a_s S2_s, where S0_s = sum_t X_t A_st,
       // S1_s = sum_t X_t a_t^(-1/2) A_st B_st, S2_s = sum_t X_t a_t^(-1) A_st B_st^2
@@ -320,7 +338,7 @@ __device__ __forceinline__ void prim_cell(const Params& p, long long t, const do
         pre[0] = dm[0];
 #pragma unroll
         for (int k = 1; k < 2 * NS; ++k) pre[k] = pre[k - 1] * (k < NS ? dm[k] : dk[k - NS]);
-        double inv = 1.0 / pre[2 * NS - 1];
+        double inv = rcp_nr(pre[2 * NS - 1]);
         double idm[NS], idk[NS];
 #pragma unroll
         for (int k = 2 * NS - 1; k > 0; --k) {
@@ -338,7 +356,7 @@ __device__ __forceinline__ void prim_cell(const Params& p, long long t, const do
       }
       mu *= p.fmu;
       ka *= p.fka;
-      Dd = ka * p.inv_lewis / (rho * cpm);
+      Dd = ka * p.inv_lewis * rcp_nr(rho * cpm);
       q[L::MU * PC] = mu;
       q[L::KA * PC] = ka;
       q[L::DF * PC] = Dd;
@@ -349,12 +367,12 @@ __device__ __forceinline__ void prim_cell(const Params& p, long long t, const do
         double Xt[NS], xts = 0.0;
 #pragma unroll
         for (int s = 0; s < NS; ++s) { Xt[s] = fmax(X[s], 0.0) + 1e-12; xts += Xt[s]; }
-        const double ixts = 1.0 / xts;
+        const double ixts = rcp_nr(xts);
         double Wt = 0.0, XW[NS];
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
           Xt[s] *= ixts;
-          XW[s] = Xt[s] / p.invW[s];
+          XW[s] = Xt[s] * p.Wm[s];
           Wt += XW[s];
         }
         double den[NS];
@@ -371,7 +389,7 @@ __device__ __forceinline__ void prim_cell(const Params& p, long long t, const do
             den[tt] = fma(Xt[s], iD, den[tt]);
           }
         }
-        const double sc = 1.0 / (Wt * pr * p.fdsm);
+        const double sc = rcp_nr(Wt * pr * p.fdsm);
         double Dmax = 0.0;
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
@@ -379,7 +397,7 @@ __device__ __forceinline__ void prim_cell(const Params& p, long long t, const do
 #pragma unroll
           for (int tt = 0; tt < NS; ++tt)
             if (tt != s) num += XW[tt];
-          const double Ds = num * sc / den[s];
+          const double Ds = num * sc * rcp_nr(den[s]);
           q[(L::DS + s) * PC] = Ds;
           Dmax = fmax(Dmax, Ds);
         }
@@ -395,7 +413,7 @@ __device__ __forceinline__ void prim_cell(const Params& p, long long t, const do
         s_cfl = sc;
         if (p.viscous) {
           const double nu1 = (4.0 / 3.0) * mu * irho;
-          const double nu2 = ka * irho / cvm;
+          const double nu2 = ka * irho * icvm;
           s_nu = pmax(pmax(nu1, nu2), Dd);
         }
       }
@@ -667,14 +685,14 @@ template <int REC>
 __host__ __device__ constexpr double rec_scale() { return REC == 7 ? 1.0 : 6.0; }
 template <int REC>
 __device__ __forceinline__ double rec_div1(const RecND& x) {
-  return x.b + x.n / (rec_scale<REC>() * x.d);
+  return fma(x.n, rcp_nr(rec_scale<REC>() * x.d), x.b);
 }
 // two fields with one division: 1/d_x = d_y / (d_x d_y). The weights are
 // scaled by the indicators' products (section above), so d_x d_y stays far
 // inside the double range for any finite stencil data the solver meets.
 template <int REC>
 __device__ __forceinline__ void rec_div2(const RecND& x, const RecND& y, double& fx, double& fy) {
-  const double r = 1.0 / ((rec_scale<REC>() * x.d) * y.d);
+  const double r = rcp_nr((rec_scale<REC>() * x.d) * y.d);
   fx = fma(x.n, r * y.d, x.b);
   fy = fma(y.n, r * x.d, y.b);
 }
@@ -698,7 +716,7 @@ __device__ __forceinline__ void conv_flux(const Params& p, const double* __restr
 #define QF(field, m) ld(q0 + (long long)(field) * PC + (long long)(m) * sd)
   // ---- Roe-averaged face state (sqrt(rho) weights)
   const double sL = QF(L::SR, 0), sR = QF(L::SR, 1);
-  const double iw = 1.0 / (sL + sR);
+  const double iw = rcp_nr(sL + sR);
   const double tL = sL * iw, tR = sR * iw;
   double ub[DIM], q2 = 0.0;
 #pragma unroll
@@ -721,7 +739,7 @@ __device__ __forceinline__ void conv_flux(const Params& p, const double* __restr
   }
   const double cvb = cpb - Rb;
   // one division for Gamma = R/c_v and its inverse
-  const double rRc = 1.0 / (Rb * cvb);
+  const double rRc = rcp_nr(Rb * cvb);
   const double Gam = Rb * Rb * rRc;
   const double hq2 = 0.5 * q2;
   // phi_s = R_s T - Gamma (e_s - |u|^2/2) with e_s = h_s - R_s T:
