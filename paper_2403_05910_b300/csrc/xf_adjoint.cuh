@@ -82,7 +82,7 @@ __device__ __forceinline__ double weno5_pair_fwd_adj(const double* wp, const dou
   w5_fwd(wp[0], wp[1], wp[2], wp[3], wp[4], e12c, P);
   w5_fwd(wm[5], wm[4], wm[3], wm[2], wm[1], e12c, M);
   // both reciprocals from one division; F from them
-  const double rpm = 1.0 / (P.den * M.den);
+  const double rpm = rcp_nr(P.den * M.den);
   const double idp = rpm * M.den, idm = rpm * P.den;
   const double F = (wp[2] + wm[3]) + fma(P.num, idp, M.num * idm);
   double fb[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
@@ -278,7 +278,7 @@ __device__ __forceinline__ double rec_pair_fwd_adj(const double* wp, const doubl
     C6 P, M;
     c6_fwd(wp[0], wp[1], wp[2], wp[3], wp[4], wp[5], e4[3], P);
     c6_fwd(wm[5], wm[4], wm[3], wm[2], wm[1], wm[0], e4[3], M);
-    const double rpm = 1.0 / (P.den * M.den);
+    const double rpm = rcp_nr(P.den * M.den);
     const double idp = rpm * M.den, idm = rpm * P.den;
     const double F = (wp[2] + wm[3]) + fma(P.num, idp, M.num * idm);
     double fb[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, gb[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
@@ -293,7 +293,7 @@ __device__ __forceinline__ double rec_pair_fwd_adj(const double* wp, const doubl
     W7 P, M;
     w7_fwd(wp[0], wp[1], wp[2], wp[3], wp[4], wp[5], wp[6], e4, P);
     w7_fwd(wm[7], wm[6], wm[5], wm[4], wm[3], wm[2], wm[1], e4, M);
-    const double rpm = 1.0 / (P.den * M.den);
+    const double rpm = rcp_nr(P.den * M.den);
     const double idp = rpm * M.den, idm = rpm * P.den;
     const double F = (wp[3] + wm[4]) + fma(P.num, idp, M.num * idm);
     double fb[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, gb[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
@@ -315,8 +315,16 @@ __device__ __forceinline__ double dcp_s(const Params& p, int s, double T) {
   return fma(fma(fma(4.0 * a[4], tau, 3.0 * a[3]), tau, 2.0 * a[2]), tau, a[1]) * p.inv_span;
 }
 
+// Atomic scatter that skips exact zeros (+0 and -0: the bit pattern shifted
+// left by one is zero), tested on the integer pipe rather than with an FP64
+// compare.
 __device__ __forceinline__ void aadd(double* p, double v) {
-  if (v != 0.0) atomicAdd(p, v);
+  if ((__double_as_longlong(v) << 1) != 0) atomicAdd(p, v);
+}
+
+// a > b for non-negative doubles, on their bit patterns (integer pipe)
+__device__ __forceinline__ bool gt_nn(double a, double b) {
+  return __double_as_longlong(a) > __double_as_longlong(b);
 }
 
 
@@ -518,7 +526,7 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
     }
     // ================= forward recomputation =================
     const double sL = QF(L::SR, 0), sR = QF(L::SR, 1);
-    const double iw = 1.0 / (sL + sR);
+    const double iw = rcp_nr(sL + sR);
     const double tL = sL * iw, tR = sR * iw;
     double uL[DIM], uR[DIM], ub[DIM], q2 = 0.0;
 #pragma unroll
@@ -547,7 +555,7 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
       Rb = fma(Yb[s], p.r[s], Rb);
       cvb = fma(Yb[s], cps[s] - p.r[s], cvb);
     }
-    const double rRc = 1.0 / (Rb * cvb);
+    const double rRc = rcp_nr(Rb * cvb);
     const double Gam = Rb * Rb * rRc;
     const double hq2 = 0.5 * q2;
     double phi[NS], c2 = 0.0;
@@ -589,9 +597,9 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
       p_m[m] = QF(L::P, o);
       cmv[m] = QF(L::C, o);
       const double xm = fabs(unm[m] - cmv[m]), xp = fabs(unm[m] + cmv[m]), x0 = fabs(unm[m]);
-      if (m == 0 || xm > am) { am = xm; im = m; }
-      if (m == 0 || xp > ap) { ap = xp; ipp = m; }
-      if (m == 0 || x0 > a0) { a0 = x0; i0 = m; }
+      if (m == 0 || gt_nn(xm, am)) { am = xm; im = m; }
+      if (m == 0 || gt_nn(xp, ap)) { ap = xp; ipp = m; }
+      if (m == 0 || gt_nn(x0, a0)) { a0 = x0; i0 = m; }
       hun[m] = 0.5 * unm[m];
       double g = gr * rho_m[m];
 #pragma unroll
@@ -1088,9 +1096,9 @@ __device__ __forceinline__ void prim_adj_cell(const Params& p, long long t,
   }
   const double cvm = cpm - Rm, RT = Rm * T;
   // reciprocals: 1/rho and 1/c_p from one division, 1/c_v from another
-  const double irc = 1.0 / (rho * cpm);
+  const double irc = rcp_nr(rho * cpm);
   const double irho = cpm * irc, icpm = rho * irc;
-  const double icvm = 1.0 / cvm;
+  const double icvm = rcp_nr(cvm);
   // adjoint accumulators
   double ub[NV], Yb[NS], velb[DIM];
 #pragma unroll
@@ -1128,7 +1136,7 @@ __device__ __forceinline__ void prim_adj_cell(const Params& p, long long t,
       pre[0] = smu[0];
 #pragma unroll
       for (int k = 1; k < 2 * NS; ++k) pre[k] = pre[k - 1] * (k < NS ? smu[k] : ska[k - NS]);
-      double inv = 1.0 / pre[2 * NS - 1];
+      double inv = rcp_nr(pre[2 * NS - 1]);
 #pragma unroll
       for (int k = 2 * NS - 1; k > 0; --k) {
         const double v = k < NS ? smu[k] : ska[k - NS];
@@ -1138,7 +1146,7 @@ __device__ __forceinline__ void prim_adj_cell(const Params& p, long long t,
       }
       ismu[0] = inv;
     }
-    const double ixs = 1.0 / xs;
+    const double ixs = rcp_nr(xs);
 #pragma unroll
     for (int s = 0; s < NS; ++s) X[s] *= ixs;
     const double mtot = mub * p.fmu, ktot = kabar * p.fka;
@@ -1159,7 +1167,7 @@ __device__ __forceinline__ void prim_adj_cell(const Params& p, long long t,
         dm = fma(xa[tt], bm[tt] * bm[tt], dm);
         dk = fma(xa[tt], bk[tt] * bk[tt], dk);
       }
-      const double rd = 1.0 / (dm * dk);
+      const double rd = rcp_nr(dm * dk);
       const double idm = rd * dk, idk = rd * dm;
       const double sm2 = smu[s] * smu[s], sk2 = ska[s] * ska[s];
       const double tm = X[s] * sm2 * idm, tk = X[s] * sk2 * idk;
@@ -1191,9 +1199,9 @@ __device__ __forceinline__ void prim_adj_cell(const Params& p, long long t,
       double e[NP > 0 ? NP : 1], dl[NP > 0 ? NP : 1];
 #pragma unroll
       for (int s = 0; s < NS; ++s) { m[s] = fmax(X[s], 0.0) + 1e-12; xts += m[s]; den[s] = 0.0; }
-      const double ixts = 1.0 / xts;
+      const double ixts = rcp_nr(xts);
 #pragma unroll
-      for (int s = 0; s < NS; ++s) { Xt[s] = m[s] * ixts; XW[s] = Xt[s] / p.invW[s]; Wt += XW[s]; }
+      for (int s = 0; s < NS; ++s) { Xt[s] = m[s] * ixts; XW[s] = Xt[s] * p.Wm[s]; Wt += XW[s]; }
       {
         int k = 0;
 #pragma unroll
@@ -1208,7 +1216,7 @@ __device__ __forceinline__ void prim_adj_cell(const Params& p, long long t,
             den[tt] = fma(Xt[s], e[k], den[tt]);
           }
       }
-      const double sc = 1.0 / (Wt * pr * p.fdsm);
+      const double sc = rcp_nr(Wt * pr * p.fdsm);
       double numb[NS], denb[NS], nbs = 0.0, scb = 0.0;
 #pragma unroll
       for (int s = 0; s < NS; ++s) {
@@ -1216,7 +1224,7 @@ __device__ __forceinline__ void prim_adj_cell(const Params& p, long long t,
 #pragma unroll
         for (int tt = 0; tt < NS; ++tt)
           if (tt != s) num += XW[tt];
-        const double iden = 1.0 / den[s];
+        const double iden = rcp_nr(den[s]);
         const double Dsb = qb[(L::DS + s) * PC];
         const double Ds = num * sc * iden;
         numb[s] = Dsb * sc * iden;
@@ -1228,7 +1236,7 @@ __device__ __forceinline__ void prim_adj_cell(const Params& p, long long t,
       prb -= scb * sc / pr;
       double Xtb[NS];
 #pragma unroll
-      for (int s = 0; s < NS; ++s) Xtb[s] = (nbs - numb[s] + Wtb) / p.invW[s];
+      for (int s = 0; s < NS; ++s) Xtb[s] = (nbs - numb[s] + Wtb) * p.Wm[s];
       {
         int k = 0;
 #pragma unroll
@@ -1368,7 +1376,7 @@ k_mixing(const __grid_constant__ Params p, const double* __restrict__ U, int sp,
   const long long C = p.cells;
   double j = 0.0;
   if (c < C) {
-    const double rho = U[c], irho = 1.0 / rho;
+    const double rho = U[c], irho = rcp_nr(rho);
     double Y;
     if (sp < NS - 1) {
       Y = U[(DIM + 2 + sp) * C + c] * irho;
