@@ -85,12 +85,12 @@ __device__ __forceinline__ double weno5_pair_fwd_adj(const double* wp, const dou
   const double rpm = rcp_nr(P.den * M.den);
   const double idp = rpm * M.den, idm = rpm * P.den;
   const double F = (wp[2] + wm[3]) + fma(P.num, idp, M.num * idm);
-  double fb[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  double fb[5] = {-0.0, -0.0, -0.0, -0.0, -0.0};
   w5_rev(P, Fb * idp, -Fb * P.num * idp * idp, fb);
 #pragma unroll
   for (int k = 0; k < 5; ++k) wpb[k] += fb[k];
   wpb[2] += Fb;
-  double gb[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  double gb[5] = {-0.0, -0.0, -0.0, -0.0, -0.0};
   w5_rev(M, Fb * idm, -Fb * M.num * idm * idm, gb);
   wmb[5] += gb[0];
   wmb[4] += gb[1];
@@ -231,7 +231,7 @@ __device__ __forceinline__ void w7_rev(const W7& r, double nbar, double dbar, do
   const double s0b = fma(r1b, r.p23, p01b * r.s1), s1b = fma(r0b, r.p23, p01b * r.s0);
   const double s2b = fma(r3b, r.p01, p23b * r.s3), s3b = fma(r2b, r.p01, p23b * r.s2);
   const double Qb[4] = {kW7c0 * s0b, kW7c1 * s1b, kW7c2 * s2b, kW7c3 * s3b};
-  double xb[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  double xb[6] = {-0.0, -0.0, -0.0, -0.0, -0.0, -0.0};
   // z2 (indicators 0 and 2), z3 (1 and 3)
   xb[2] += 2.0 * kW7D3 * r.x2 * (Qb[0] + Qb[2]);
   xb[3] += 2.0 * kW7D3 * r.x3 * (Qb[1] + Qb[3]);
@@ -281,7 +281,7 @@ __device__ __forceinline__ double rec_pair_fwd_adj(const double* wp, const doubl
     const double rpm = rcp_nr(P.den * M.den);
     const double idp = rpm * M.den, idm = rpm * P.den;
     const double F = (wp[2] + wm[3]) + fma(P.num, idp, M.num * idm);
-    double fb[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, gb[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    double fb[6] = {-0.0, -0.0, -0.0, -0.0, -0.0, -0.0}, gb[6] = {-0.0, -0.0, -0.0, -0.0, -0.0, -0.0};
     c6_rev(P, Fb * idp, -Fb * P.num * idp * idp, fb);
     c6_rev(M, Fb * idm, -Fb * M.num * idm * idm, gb);
 #pragma unroll
@@ -296,7 +296,7 @@ __device__ __forceinline__ double rec_pair_fwd_adj(const double* wp, const doubl
     const double rpm = rcp_nr(P.den * M.den);
     const double idp = rpm * M.den, idm = rpm * P.den;
     const double F = (wp[3] + wm[4]) + fma(P.num, idp, M.num * idm);
-    double fb[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, gb[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    double fb[7] = {-0.0, -0.0, -0.0, -0.0, -0.0, -0.0, -0.0}, gb[7] = {-0.0, -0.0, -0.0, -0.0, -0.0, -0.0, -0.0};
     w7_rev(P, Fb * idp, -Fb * P.num * idp * idp, fb);
     w7_rev(M, Fb * idm, -Fb * M.num * idm * idm, gb);
 #pragma unroll
@@ -314,6 +314,10 @@ __device__ __forceinline__ double dcp_s(const Params& p, int s, double T) {
   const double* a = p.rcp[s];
   return fma(fma(fma(4.0 * a[4], tau, 3.0 * a[3]), tau, 2.0 * a[2]), tau, a[1]) * p.inv_span;
 }
+
+// Reverse-mode accumulators below start at -0.0, not +0.0: -0.0 + x is x for
+// every x (both zeros included), so the first accumulation folds away, while
+// +0.0 + x would have to be computed (it turns -0 into +0).
 
 // Atomic scatter that skips exact zeros (+0 and -0: the bit pattern shifted
 // left by one is zero), tested on the integer pipe rather than with an FP64
@@ -405,7 +409,7 @@ __device__ __forceinline__ void pos_blend_adj(const Params& p, const double* __r
     for (int v = 0; v < NV; ++v) Gc[v] = Gb[v];
     return;
   }
-  double thetab = 0.0, Flfb[NV];
+  double thetab = -0.0, Flfb[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     thetab = fma(Gh[v] - Flf[v], Gb[v], thetab);
@@ -414,7 +418,7 @@ __device__ __forceinline__ void pos_blend_adj(const Params& p, const double* __r
   }
   double Uab[NV], Ubb[NV];
 #pragma unroll
-  for (int v = 0; v < NV; ++v) { Uab[v] = 0.0; Ubb[v] = 0.0; }
+  for (int v = 0; v < NV; ++v) { Uab[v] = -0.0; Ubb[v] = -0.0; }
   if (live) {
     // theta = (lo - eps)/(lo - hi) with eps = pos_eps
     const double r = 1.0 / (lo_s - hi_s);
@@ -440,7 +444,7 @@ __device__ __forceinline__ void pos_blend_adj(const Params& p, const double* __r
     }
   }
   // F_LF = (F_a + F_b + alpha (U_a - U_b)) / 2
-  double alb = 0.0, unab = 0.0, unbb = 0.0;
+  double alb = -0.0, unab = -0.0, unbb = -0.0;
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     const double h = 0.5 * Flfb[v];
@@ -456,7 +460,7 @@ __device__ __forceinline__ void pos_blend_adj(const Params& p, const double* __r
   unab = fma(he, pa, unab);
   unbb = fma(he, pb, unbb);
   // alpha = max(|u_a| + c_a, |u_b| + c_b)
-  double cab = 0.0, cbb = 0.0;
+  double cab = -0.0, cbb = -0.0;
   if (sa >= sbv) {
     unab += una > 0.0 ? alb : (una < 0.0 ? -alb : 0.0);
     cab = alb;
@@ -528,7 +532,7 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
     const double sL = QF(L::SR, 0), sR = QF(L::SR, 1);
     const double iw = rcp_nr(sL + sR);
     const double tL = sL * iw, tR = sR * iw;
-    double uL[DIM], uR[DIM], ub[DIM], q2 = 0.0;
+    double uL[DIM], uR[DIM], ub[DIM], q2 = -0.0;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
       uL[a] = QF(L::UN + a, 0);
@@ -547,7 +551,7 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
       Yb[s] = fma(tL, YL[s], tR * YR[s]);
     }
     const TauPt tp = tau_of(p, Tb);
-    double es[NS], cps[NS], Rb = 0.0, cvb = 0.0;
+    double es[NS], cps[NS], Rb = -0.0, cvb = -0.0;
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
       cps[s] = cp_s(p, s, tp.tc);
@@ -558,7 +562,7 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
     const double rRc = rcp_nr(Rb * cvb);
     const double Gam = Rb * Rb * rRc;
     const double hq2 = 0.5 * q2;
-    double phi[NS], c2 = 0.0;
+    double phi[NS], c2 = -0.0;
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
       phi[s] = fma(p.r[s], Tb, -Gam * (es[s] - hq2));
@@ -627,17 +631,17 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
     const double Dlb = c * Gc[1 + D] + un * c * Gc[IE];
     double ubb[DIM], Ybb[NS];
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) ubb[a] = 0.0;
+    for (int a = 0; a < DIM; ++a) ubb[a] = -0.0;
 #pragma unroll
-    for (int s = 0; s < NS; ++s) Ybb[s] = 0.0;
-    double cb = 0.0, Hbb = 0.0, unb = 0.0, c2b = 0.0, iGamb = 0.0;
+    for (int s = 0; s < NS; ++s) Ybb[s] = -0.0;
+    double cb = -0.0, Hbb = -0.0, unb = -0.0, c2b = -0.0, iGamb = -0.0;
     const double Fmb = Sb - Dlb, Fpb = Sb + Dlb, Feb = Sb - c2 * iGam * Gc[IE];
     double Fm = 0.0, Fp = 0.0, Fe = 0.0;
     // per-field reverse; stencil adjoints accumulated here
     double rhob[SW], pb[SW], hunb[SW], gUhb[SW], mnb[SW];
 #pragma unroll
-    for (int m = 0; m < SW; ++m) { rhob[m] = 0.0; pb[m] = 0.0; hunb[m] = 0.0; gUhb[m] = 0.0; mnb[m] = 0.0; }
-    double hamb = 0.0, hapb = 0.0, ha0b = 0.0, chcb = 0.0, Gamb = 0.0, hic2b = 0.0, ic2b = 0.0;
+    for (int m = 0; m < SW; ++m) { rhob[m] = -0.0; pb[m] = -0.0; hunb[m] = -0.0; gUhb[m] = -0.0; mnb[m] = -0.0; }
+    double hamb = -0.0, hapb = -0.0, ha0b = -0.0, chcb = -0.0, Gamb = -0.0, hic2b = -0.0, ic2b = -0.0;
 #pragma unroll
     for (int fld = 0; fld < 3; ++fld) {
       const double ha = fld == 0 ? ha_m : (fld == 1 ? ha_p : ha0);
@@ -662,10 +666,12 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
         wp[m] = fma(hun[m] + ha, LU, pq);
         wm[m] = fma(hun[m] - ha, LU, pq);
       }
-      double wpb[SW] = {}, wmb[SW] = {};
+      double wpb[SW], wmb[SW];
+#pragma unroll
+      for (int m = 0; m < SW; ++m) { wpb[m] = -0.0; wmb[m] = -0.0; }
       const double F = rec_pair_fwd_adj<REC>(wp, wm, e12c, Fb, wpb, wmb);
       if (fld == 0) Fm = F; else if (fld == 1) Fp = F; else Fe = F;
-      double hab = 0.0, hlb = 0.0, lEb = 0.0;
+      double hab = -0.0, hlb = -0.0, lEb = -0.0;
 #pragma unroll
       for (int m = 0; m < SW; ++m) {
         // w+- = (hun +- ha) LU + p pqr: with s = wb+ + wb-, d = wb+ - wb-,
@@ -723,7 +729,7 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
     // tangential momenta and species (eigenvalue u, no pressure term)
     double hp0b[SW], hm0b[SW];
 #pragma unroll
-    for (int m = 0; m < SW; ++m) { hp0b[m] = 0.0; hm0b[m] = 0.0; }
+    for (int m = 0; m < SW; ++m) { hp0b[m] = -0.0; hm0b[m] = -0.0; }
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
       if (a == D) continue;
@@ -735,7 +741,9 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
         wp[m] = (hun[m] + ha0) * LUv[m];
         wm[m] = (hun[m] - ha0) * LUv[m];
       }
-      double wpb[SW] = {}, wmb[SW] = {};
+      double wpb[SW], wmb[SW];
+#pragma unroll
+      for (int m = 0; m < SW; ++m) { wpb[m] = -0.0; wmb[m] = -0.0; }
       const double Fk = rec_pair_fwd_adj<REC>(wp, wm, e12c, Fb, wpb, wmb);
       ubb[a] += Fk * Gc[IE];
 #pragma unroll
@@ -759,7 +767,9 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
         wp[m] = (hun[m] + ha0) * LUv[m];
         wm[m] = (hun[m] - ha0) * LUv[m];
       }
-      double wpb[SW] = {}, wmb[SW] = {};
+      double wpb[SW], wmb[SW];
+#pragma unroll
+      for (int m = 0; m < SW; ++m) { wpb[m] = -0.0; wmb[m] = -0.0; }
       const double Fk = rec_pair_fwd_adj<REC>(wp, wm, e12c, Fb, wpb, wmb);
       dphib[s] = -iGam * Fk * Gc[IE];
       iGamb -= dphi[s] * Fk * Gc[IE];
@@ -781,11 +791,11 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
     // stencil preparation
     cb += chcb * hic2;
     hic2b += chcb * c;
-    double grb = 0.0, gEb = 0.0, gmb[DIM], gsb[NS > 1 ? NS - 1 : 1];
+    double grb = -0.0, gEb = -0.0, gmb[DIM], gsb[NS > 1 ? NS - 1 : 1];
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) gmb[a] = 0.0;
+    for (int a = 0; a < DIM; ++a) gmb[a] = -0.0;
 #pragma unroll
-    for (int s = 0; s < NS - 1; ++s) gsb[s] = 0.0;
+    for (int s = 0; s < NS - 1; ++s) gsb[s] = -0.0;
 #pragma unroll
     for (int m = 0; m < SW; ++m) {
       const int o = m - SO;
@@ -809,7 +819,7 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
       QB(L::U, o, rhob[m]);
       QB(L::P, o, pb[m]);
       double unmb = 0.5 * hunb[m];
-      double cmb = 0.0;
+      double cmb = -0.0;
       if (m == im) { const double sg = unm[m] - cmv[m] > 0.0 ? 1.0 : (unm[m] - cmv[m] < 0.0 ? -1.0 : 0.0); unmb += 0.5 * hamb * sg; cmb -= 0.5 * hamb * sg; }
       if (m == ipp) { const double sg = unm[m] + cmv[m] > 0.0 ? 1.0 : (unm[m] + cmv[m] < 0.0 ? -1.0 : 0.0); unmb += 0.5 * hapb * sg; cmb += 0.5 * hapb * sg; }
       if (m == i0) { const double sg = unm[m] > 0.0 ? 1.0 : (unm[m] < 0.0 ? -1.0 : 0.0); unmb += 0.5 * ha0b * sg; }
@@ -824,7 +834,7 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
     }
     double phib[NS];
 #pragma unroll
-    for (int s = 0; s < NS; ++s) phib[s] = 0.0;
+    for (int s = 0; s < NS; ++s) phib[s] = -0.0;
 #pragma unroll
     for (int s = 0; s < NS - 1; ++s) {
       const double db = dphib[s] + gsb[s] * hic2;
@@ -842,7 +852,7 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
     double cvbb = iGamb * iRb, Rbb = -iGamb * iGam * iRb;
     c2b += cb * 0.5 * rsc;
     ubb[D] += unb;
-    double Tbb = 0.0, q2b = 0.0;
+    double Tbb = -0.0, q2b = -0.0;
     if (fallback) {
       QB(L::C, 0, c2b * cl);
       QB(L::C, 1, c2b * cr);
@@ -856,7 +866,7 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
       Hbb += c2b * Gam;
       q2b -= c2b * Gam;
     }
-    double hq2b = 0.0;
+    double hq2b = -0.0;
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
       Tbb += phib[s] * p.r[s];
@@ -875,7 +885,7 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
     }
 #pragma unroll
     for (int a = 0; a < DIM; ++a) ubb[a] += 2.0 * ub[a] * q2b;
-    double tLb = 0.0, tRb = 0.0;
+    double tLb = -0.0, tRb = -0.0;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
       QB(L::UN + a, 0, tL * ubb[a]);
@@ -922,7 +932,7 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
 #pragma unroll
       for (int b = 0; b < DIM; ++b) gr[a][b] = (b == D) ? FD(L::UN + a) : FI(L::GU + a * DIM + b);
     }
-    double div = 0.0;
+    double div = -0.0;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) div += gr[a][a];
     double tau[DIM];
@@ -933,7 +943,7 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
     }
     // species diffusivities at the face: the common D, or each species' D_sm
     // (mixture-averaged model)
-    double dY[NS], Yf[NS], Dsf[NS], corr = 0.0;
+    double dY[NS], Yf[NS], Dsf[NS], corr = -0.0;
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
       dY[s] = FD(L::Y + s);
@@ -945,7 +955,7 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
     const double dT = FD(L::T);
     // reverse: Gout[IE] -= ka dT + work - qd; Gout[1+a] -= tau_a; Gout[IE+1+s] += J_s
     const double workb = -Gb[IE], kab = -Gb[IE] * dT, dTb = -Gb[IE] * ka, qdb = Gb[IE];
-    double Tfb = 0.0, rfb = 0.0, corrb = 0.0, mub = 0.0, divb = 0.0;
+    double Tfb = -0.0, rfb = -0.0, corrb = -0.0, mub = -0.0, divb = -0.0;
     double dYb[NS], Yfb[NS], Dsfb[NS];
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
@@ -966,7 +976,7 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
       Dsfb[s] = fma(corrb, dY[s], Dsfb[s]);
       dYb[s] = fma(corrb, Dsf[s], dYb[s]);
     }
-    double Dfb = 0.0;
+    double Dfb = -0.0;
     if (p.diffusion != 1) {
 #pragma unroll
       for (int s = 0; s < NS; ++s) Dfb += Dsfb[s];
@@ -975,7 +985,7 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
 #pragma unroll
     for (int a = 0; a < DIM; ++a)
 #pragma unroll
-      for (int b = 0; b < DIM; ++b) grb[a][b] = 0.0;
+      for (int b = 0; b < DIM; ++b) grb[a][b] = -0.0;
     double ufb[DIM];
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
@@ -1085,7 +1095,7 @@ __device__ __forceinline__ void prim_adj_cell(const Params& p, long long t,
   for (int s = 0; s < NS; ++s) Y[s] = q[(L::Y + s) * PC];
   const double T = q[L::T * PC], pr = q[L::P * PC], c = q[L::C * PC];
   const TauPt tp = tau_of(p, T);
-  double Rm = 0.0, cpm = 0.0, dcpm = 0.0, es[NS], cps[NS];
+  double Rm = -0.0, cpm = -0.0, dcpm = -0.0, es[NS], cps[NS];
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
     cps[s] = cp_s(p, s, tp.tc);
@@ -1108,7 +1118,7 @@ __device__ __forceinline__ void prim_adj_cell(const Params& p, long long t,
 #pragma unroll
   for (int a = 0; a < DIM; ++a) velb[a] = qb[(L::UN + a) * PC];
   double Tb = qb[L::T * PC], prb = qb[L::P * PC], cb = qb[L::C * PC];
-  double rhob = 0.0, Eb = 0.0, irhob = 0.0, cpmb = 0.0, Rmb = 0.0;
+  double rhob = -0.0, Eb = -0.0, irhob = -0.0, cpmb = -0.0, Rmb = -0.0;
   if (p.viscous) {
     const double mub = qb[L::MU * PC], kab = qb[L::KA * PC], Db = qb[L::DF * PC];
     // D = ka / (Le rho cp)
@@ -1118,7 +1128,7 @@ __device__ __forceinline__ void prim_adj_cell(const Params& p, long long t,
     cpmb -= Db * Dd * icpm;
     // Wilke mixtures, recomputed
     const double lnT = log(T);
-    double smu[NS], ska[NS], ismu[NS], iska[NS], X[NS], xs = 0.0, dlm[NS], dlk[NS];
+    double smu[NS], ska[NS], ismu[NS], iska[NS], X[NS], xs = -0.0, dlm[NS], dlk[NS];
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
       const double lm = fma(fma(fma(p.lnmu[s][3], lnT, p.lnmu[s][2]), lnT, p.lnmu[s][1]), lnT, p.lnmu[s][0]);
@@ -1152,13 +1162,13 @@ __device__ __forceinline__ void prim_adj_cell(const Params& p, long long t,
     const double mtot = mub * p.fmu, ktot = kabar * p.fka;
     double Xb[NS], smub[NS], skab[NS], ismub[NS], iskab[NS];
 #pragma unroll
-    for (int s = 0; s < NS; ++s) { Xb[s] = 0.0; smub[s] = 0.0; skab[s] = 0.0; ismub[s] = 0.0; iskab[s] = 0.0; }
+    for (int s = 0; s < NS; ++s) { Xb[s] = -0.0; smub[s] = -0.0; skab[s] = -0.0; ismub[s] = -0.0; iskab[s] = -0.0; }
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
       // forward: b_t = 1 + sqrt(a_s / a_t) B_st, d_s = sum_t X_t A_st b_t^2,
       // term_s = X_s a_s / d_s (a = mu or kappa); the b_t and X_t A_st stay
       // in registers for the reverse
-      double bm[NS], bk[NS], xa[NS], dm = 0.0, dk = 0.0;
+      double bm[NS], bk[NS], xa[NS], dm = -0.0, dk = -0.0;
 #pragma unroll
       for (int tt = 0; tt < NS; ++tt) {
         bm[tt] = fma(smu[s] * ismu[tt], p.wB[s][tt], 1.0);
@@ -1188,17 +1198,17 @@ __device__ __forceinline__ void prim_adj_cell(const Params& p, long long t,
         iskab[tt] = fma(bkw, ska[s], iskab[tt]);
       }
     }
-    double lnTb = 0.0, xdot = 0.0;
+    double lnTb = -0.0, xdot = -0.0;
     if (p.diffusion == 1) {
       // mixture-averaged D_sm (Eq. 25-26), recomputed as in k_prim, then reversed:
       // X~ = (max(X, 0) + 1e-12)/sum, W~ = sum X~ W, e_st = exp(-l_st(ln T)) = p D_st^-1 (SI),
       // den_s = sum_{t!=s} X~_t e_st, num_s = sum_{t!=s} X~_t W_t,
       // D_s = num_s / (W~ den_s p* fdsm)
       constexpr int NP = NS * (NS - 1) / 2;
-      double m[NS], Xt[NS], XW[NS], den[NS], xts = 0.0, Wt = 0.0;
+      double m[NS], Xt[NS], XW[NS], den[NS], xts = -0.0, Wt = -0.0;
       double e[NP > 0 ? NP : 1], dl[NP > 0 ? NP : 1];
 #pragma unroll
-      for (int s = 0; s < NS; ++s) { m[s] = fmax(X[s], 0.0) + 1e-12; xts += m[s]; den[s] = 0.0; }
+      for (int s = 0; s < NS; ++s) { m[s] = fmax(X[s], 0.0) + 1e-12; xts += m[s]; den[s] = -0.0; }
       const double ixts = rcp_nr(xts);
 #pragma unroll
       for (int s = 0; s < NS; ++s) { Xt[s] = m[s] * ixts; XW[s] = Xt[s] * p.Wm[s]; Wt += XW[s]; }
@@ -1217,10 +1227,10 @@ __device__ __forceinline__ void prim_adj_cell(const Params& p, long long t,
           }
       }
       const double sc = rcp_nr(Wt * pr * p.fdsm);
-      double numb[NS], denb[NS], nbs = 0.0, scb = 0.0;
+      double numb[NS], denb[NS], nbs = -0.0, scb = -0.0;
 #pragma unroll
       for (int s = 0; s < NS; ++s) {
-        double num = 0.0;
+        double num = -0.0;
 #pragma unroll
         for (int tt = 0; tt < NS; ++tt)
           if (tt != s) num += XW[tt];
@@ -1249,7 +1259,7 @@ __device__ __forceinline__ void prim_adj_cell(const Params& p, long long t,
             lnTb -= eb * e[k] * dl[k];
           }
       }
-      double xtd = 0.0;
+      double xtd = -0.0;
 #pragma unroll
       for (int s = 0; s < NS; ++s) xtd = fma(Xtb[s], Xt[s], xtd);
 #pragma unroll
