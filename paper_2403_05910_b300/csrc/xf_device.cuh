@@ -1134,20 +1134,29 @@ __device__ __forceinline__ void update_cell(const Params& p, long long c,
     fz = c;
     sz = (long long)p.n[0] * p.n[1];
   }
+  // every input of this cell is read before any output is written: out may be
+  // Un or Us (in-place stages), but only at this cell, so the loads of all
+  // fields can be in flight together
+  double R[NV], un[NV], us[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
-    double R = -(ld(Gx + v * NFX + fx + 1) - ld(Gx + v * NFX + fx)) * p.inv_dx[0];
-    if (DIM > 1) R = fma(-(ld(Gy + v * NFY + fy + sy) - ld(Gy + v * NFY + fy)), p.inv_dx[1], R);
-    if (DIM > 2) R = fma(-(ld(Gz + v * NFZ + fz + sz) - ld(Gz + v * NFZ + fz)), p.inv_dx[2], R);
+    R[v] = -(ld(Gx + v * NFX + fx + 1) - ld(Gx + v * NFX + fx)) * p.inv_dx[0];
+    if (DIM > 1) R[v] = fma(-(ld(Gy + v * NFY + fy + sy) - ld(Gy + v * NFY + fy)), p.inv_dx[1], R[v]);
+    if (DIM > 2) R[v] = fma(-(ld(Gz + v * NFZ + fz + sz) - ld(Gz + v * NFZ + fz)), p.inv_dx[2], R[v]);
+    un[v] = mode >= 1 ? Un[v * C + c] : 0.0;
+    us[v] = mode >= 2 ? Us[v * C + c] : 0.0;
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
     double o;
     if (mode == 0) {
-      o = R;
+      o = R[v];
     } else if (mode == 1) {
-      o = fma(dt, R, Un[v * C + c]);
+      o = fma(dt, R[v], un[v]);
     } else if (mode == 2) {
-      o = fma(0.75, Un[v * C + c], 0.25 * fma(dt, R, Us[v * C + c]));
+      o = fma(0.75, un[v], 0.25 * fma(dt, R[v], us[v]));
     } else {
-      o = fma(1.0 / 3.0, Un[v * C + c], (2.0 / 3.0) * fma(dt, R, Us[v * C + c]));
+      o = fma(1.0 / 3.0, un[v], (2.0 / 3.0) * fma(dt, R[v], us[v]));
     }
     out[v * C + c] = o;
   }
