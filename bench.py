@@ -41,7 +41,7 @@ FACE_TRAFFIC_B_PER_FACE = {"aab342d14388773d": 294.0, "7aa2c6f72cd106cc": 294.2,
                            "f263a26a5971860e": 293.0,
                            "0602a26c075d3356": 293.1,
                            "dedb921fb50202ed": 293.5,
-                           "451cb69c9faafb9d": 292.8}
+                           "451cb69c9faafb9d": 292.8, "d015dec47061b893": 292.7}
 # bounded oracle samples of each workload (config index -> grid)
 CPU_SAMPLE_GRID = {2: (96, 48, 48), 1: (256, 128)}
 
