@@ -616,9 +616,18 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
     const double e12c[4] = {p.wenoe[0], p.wenoe[1], p.wenoe[2], p.wenoe[3]};
     const double chc = c * hic2;
     const double ha_m = 0.5 * am, ha_p = 0.5 * ap, ha0 = 0.5 * a0;
-    const double hlmn_m = 0.5 * (-Gam * un - c) * hic2, hlmn_p = 0.5 * (-Gam * un + c) * hic2;
-    const double lE_a = Gam * hic2;
-    const double hlmn_e = 0.5 * Gam * un * ic2, lE_e = -Gam * ic2;
+    // the pressure terms p_m (l[m_n]/2 + (u_m/2) l[E]) of the dense rows, as in
+    // conv_flux: one product pV per cell, -+ dl p_m for u -+ c, -2 pV for the
+    // entropy row; nUv (the normal momentum relative to the face velocity) is
+    // shared by u -+ c
+    const double lE = Gam * hic2, hl0 = -0.5 * Gam * un * hic2, dl = 0.5 * chc;
+    double nUv[SW], base[SW], pV[SW];
+#pragma unroll
+    for (int m = 0; m < SW; ++m) {
+      nUv[m] = fma(-un, rho_m[m], QF(L::U + 1 + D, m - SO));
+      base[m] = fma(hun[m], lE, hl0);
+      pV[m] = p_m[m] * base[m];
+    }
     double wp[SW], wm[SW];
     // ================= reverse =================
     // back-projection of the dense columns: adjoints of the reconstructed
@@ -642,27 +651,26 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
 #pragma unroll
     for (int m = 0; m < SW; ++m) { rhob[m] = -0.0; pb[m] = -0.0; hunb[m] = -0.0; gUhb[m] = -0.0; mnb[m] = -0.0; }
     double hamb = -0.0, hapb = -0.0, ha0b = -0.0, chcb = -0.0, Gamb = -0.0, hic2b = -0.0, ic2b = -0.0;
+    double pVb[SW], nUb[SW], dlb = -0.0;
+#pragma unroll
+    for (int m = 0; m < SW; ++m) { pVb[m] = -0.0; nUb[m] = -0.0; }
 #pragma unroll
     for (int fld = 0; fld < 3; ++fld) {
       const double ha = fld == 0 ? ha_m : (fld == 1 ? ha_p : ha0);
-      const double hl = fld == 0 ? hlmn_m : (fld == 1 ? hlmn_p : hlmn_e);
-      const double lE = fld == 2 ? lE_e : lE_a;
       const double Fb = fld == 0 ? Fmb : (fld == 1 ? Fpb : Feb);
       const double schc = fld == 0 ? -chc : chc;
-      double LUv[SW], nUv[SW], pqr[SW];
+      double LUv[SW];
 #pragma unroll
       for (int m = 0; m < SW; ++m) {
-        double LU, nU = 0.0;
+        double LU, pq;
         if (fld == 2) {
           LU = fma(-2.0, gUh[m], rho_m[m]);
+          pq = -2.0 * pV[m];
         } else {
-          nU = fma(-un, rho_m[m], QF(L::U + 1 + D, m - SO));
-          LU = fma(schc, nU, gUh[m]);
+          LU = fma(schc, nUv[m], gUh[m]);
+          pq = fma(fld == 0 ? -dl : dl, p_m[m], pV[m]);
         }
         LUv[m] = LU;
-        nUv[m] = nU;
-        pqr[m] = fma(hun[m], lE, hl);
-        const double pq = p_m[m] * pqr[m];
         wp[m] = fma(hun[m] + ha, LU, pq);
         wm[m] = fma(hun[m] - ha, LU, pq);
       }
@@ -671,47 +679,52 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
       for (int m = 0; m < SW; ++m) { wpb[m] = -0.0; wmb[m] = -0.0; }
       const double F = rec_pair_fwd_adj<REC>(wp, wm, e12c, Fb, wpb, wmb);
       if (fld == 0) Fm = F; else if (fld == 1) Fp = F; else Fe = F;
-      double hab = -0.0, hlb = -0.0, lEb = -0.0;
+      double hab = -0.0;
 #pragma unroll
       for (int m = 0; m < SW; ++m) {
-        // w+- = (hun +- ha) LU + p pqr: with s = wb+ + wb-, d = wb+ - wb-,
-        // LUb = hun s + ha d, hunb += s (LU + p lE), hab += d LU, pb += s pqr,
-        // and (lE, hl) take s p (hun, 1)
+        // w+- = (hun +- ha) LU + pq: with s = wb+ + wb-, d = wb+ - wb-,
+        // LUb = hun s + ha d, hunb += s LU, hab += d LU, and pq takes s
         const double sb = wpb[m] + wmb[m], db = wpb[m] - wmb[m];
         const double LUb = fma(hun[m], sb, ha * db);
-        hunb[m] = fma(sb, fma(p_m[m], lE, LUv[m]), hunb[m]);
+        hunb[m] = fma(sb, LUv[m], hunb[m]);
         hab = fma(db, LUv[m], hab);
-        pb[m] = fma(sb, pqr[m], pb[m]);
-        const double sp = sb * p_m[m];
-        lEb = fma(sp, hun[m], lEb);
-        hlb += sp;
         if (fld == 2) {
+          pVb[m] = fma(-2.0, sb, pVb[m]);
           rhob[m] += LUb;
           gUhb[m] = fma(-2.0, LUb, gUhb[m]);
         } else {
+          const double sdl = fld == 0 ? -dl : dl;
+          pVb[m] += sb;
+          pb[m] = fma(sdl, sb, pb[m]);
+          dlb = fma(fld == 0 ? -p_m[m] : p_m[m], sb, dlb);
           gUhb[m] += LUb;
           chcb = fma(fld == 0 ? -LUb : LUb, nUv[m], chcb);
-          const double nUb = schc * LUb;
-          mnb[m] += nUb;
-          unb = fma(-nUb, rho_m[m], unb);
-          rhob[m] = fma(-nUb, un, rhob[m]);
+          nUb[m] = fma(schc, LUb, nUb[m]);
         }
       }
-      if (fld == 2) {
-        ha0b += hab;
-        // hl = Gam un ic2 / 2, lE = -Gam ic2
-        Gamb += hlb * 0.5 * un * ic2 - lEb * ic2;
-        unb += hlb * 0.5 * Gam * ic2;
-        ic2b += hlb * 0.5 * Gam * un - lEb * Gam;
-      } else {
-        const double sgn = fld == 0 ? -1.0 : 1.0;
-        if (fld == 0) hamb += hab; else hapb += hab;
-        // hl = (-Gam un + sgn c) hic2 / 2, lE = Gam hic2
-        Gamb += hlb * (-0.5 * un * hic2) + lEb * hic2;
-        unb += hlb * (-0.5 * Gam * hic2);
-        cb += hlb * 0.5 * sgn * hic2;
-        hic2b += hlb * 0.5 * (-Gam * un + sgn * c) + lEb * Gam;
+      if (fld == 2) ha0b += hab;
+      else if (fld == 0) hamb += hab;
+      else hapb += hab;
+    }
+    // reverse of the shared terms: nU = m_n - u_n rho, pV = p base with
+    // base = hun lE + hl0; lE = Gam hic2, hl0 = -Gam un hic2 / 2, dl = chc / 2
+    {
+      double lEb = -0.0, hl0b = -0.0;
+#pragma unroll
+      for (int m = 0; m < SW; ++m) {
+        mnb[m] += nUb[m];
+        unb = fma(-nUb[m], rho_m[m], unb);
+        rhob[m] = fma(-nUb[m], un, rhob[m]);
+        pb[m] = fma(pVb[m], base[m], pb[m]);
+        const double bb = pVb[m] * p_m[m];
+        hunb[m] = fma(bb, lE, hunb[m]);
+        lEb = fma(bb, hun[m], lEb);
+        hl0b += bb;
       }
+      Gamb = fma(lEb, hic2, fma(hl0b, -0.5 * un * hic2, Gamb));
+      hic2b = fma(lEb, Gam, fma(hl0b, -0.5 * Gam * un, hic2b));
+      unb = fma(hl0b, -0.5 * Gam * hic2, unb);
+      chcb = fma(0.5, dlb, chcb);
     }
     // the back-projection terms that involve the reconstructed dense fields
     {
