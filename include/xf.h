@@ -15,8 +15,10 @@
  *     diffusivities of Eq. 25-26);
  *   - the conservative flux difference (Eq. 13) and the SSP-RK3 stages (Eq. 16).
  * On top: the reverse mode (vector-Jacobian products) of the RHS and of a
- * step, and a batched form that advances many 2D grids in one persistent
- * kernel per stage.
+ * step (the step's stage states recomputed, or taken from a taped step), a
+ * step of a host-resident state with the copies overlapped with the compute,
+ * and a batched form that advances many 2D grids in one persistent kernel
+ * per stage.
  *
  * Conventions (all entry points):
  *   - FP64 throughout. Field arrays are structure-of-arrays [n_v][nz][ny][nx]
