@@ -21,5 +21,13 @@ def build(force: bool = False) -> str:
     return LIB
 
 
+def compile_source(src: str, out: str) -> str:
+    """Compile an oracle source file ``src`` (e.g. a copy with a planted
+    mistake, made by a test) into the shared library ``out`` with the same
+    flags as the oracle itself."""
+    subprocess.check_call(["g++", *FLAGS, "-I", HERE, "-o", out, src])
+    return out
+
+
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv))

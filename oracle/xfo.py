@@ -34,40 +34,44 @@ class Params(C.Structure):
 _lib = None
 
 
+def load(path):
+    """Open an oracle library at ``path`` with the argument types of xfo.h."""
+    L = C.CDLL(path)
+    P = C.POINTER(Params)
+    dp = C.POINTER(C.c_double)
+    up = C.POINTER(C.c_uint32)
+    L.xfo_prim_to_cons.argtypes = [P, dp, dp, dp]
+    L.xfo_cons_to_prim.argtypes = [P, dp, dp, dp, up]
+    L.xfo_rhs.argtypes = [P, dp, dp, dp, up]
+    L.xfo_dt.argtypes = [P, dp, dp, up]
+    L.xfo_dt.restype = C.c_double
+    L.xfo_step_rk3.argtypes = [P, dp, dp, C.c_double, up]
+    L.xfo_step_rk3.restype = C.c_double
+    L.xfo_run_to.argtypes = [P, dp, dp, C.c_double, C.c_int, up]
+    L.xfo_thermo.argtypes = [P, C.c_double, dp, dp, dp, dp, dp, dp]
+    L.xfo_temperature.argtypes = [P, C.c_double, dp, C.c_double, C.POINTER(C.c_int), up]
+    L.xfo_temperature.restype = C.c_double
+    L.xfo_eigen.argtypes = [P, C.c_int, dp, dp, C.c_double, C.c_double, dp, dp, dp, dp, up]
+    L.xfo_flux.argtypes = [P, C.c_int, dp, C.c_double, dp, up]
+    L.xfo_weno5.argtypes = [dp]
+    L.xfo_weno5.restype = C.c_double
+    L.xfo_weno_cu6.argtypes = [dp, C.c_double]
+    L.xfo_weno_cu6.restype = C.c_double
+    L.xfo_species_diffusion.argtypes = [P, C.c_double, C.c_double, dp, dp]
+    L.xfo_weno7.argtypes = [dp, C.c_double]
+    L.xfo_weno7.restype = C.c_double
+    L.xfo_cu6_beta6.argtypes = [dp]
+    L.xfo_cu6_beta6.restype = C.c_double
+    L.xfo_transport.argtypes = [P, C.c_double, C.c_double, dp, dp, dp, dp]
+    L.xfo_rhs_jvp.argtypes = [P, dp, dp, dp, dp, dp, up]
+    L.xfo_rk3_jvp.argtypes = [P, dp, dp, dp, C.c_double, C.c_int, up]
+    return L
+
+
 def lib():
     global _lib
     if _lib is None:
-        path = _build.build()
-        L = C.CDLL(path)
-        P = C.POINTER(Params)
-        dp = C.POINTER(C.c_double)
-        up = C.POINTER(C.c_uint32)
-        L.xfo_prim_to_cons.argtypes = [P, dp, dp, dp]
-        L.xfo_cons_to_prim.argtypes = [P, dp, dp, dp, up]
-        L.xfo_rhs.argtypes = [P, dp, dp, dp, up]
-        L.xfo_dt.argtypes = [P, dp, dp, up]
-        L.xfo_dt.restype = C.c_double
-        L.xfo_step_rk3.argtypes = [P, dp, dp, C.c_double, up]
-        L.xfo_step_rk3.restype = C.c_double
-        L.xfo_run_to.argtypes = [P, dp, dp, C.c_double, C.c_int, up]
-        L.xfo_thermo.argtypes = [P, C.c_double, dp, dp, dp, dp, dp, dp]
-        L.xfo_temperature.argtypes = [P, C.c_double, dp, C.c_double, C.POINTER(C.c_int), up]
-        L.xfo_temperature.restype = C.c_double
-        L.xfo_eigen.argtypes = [P, C.c_int, dp, dp, C.c_double, C.c_double, dp, dp, dp, dp, up]
-        L.xfo_flux.argtypes = [P, C.c_int, dp, C.c_double, dp, up]
-        L.xfo_weno5.argtypes = [dp]
-        L.xfo_weno5.restype = C.c_double
-        L.xfo_weno_cu6.argtypes = [dp, C.c_double]
-        L.xfo_weno_cu6.restype = C.c_double
-        L.xfo_species_diffusion.argtypes = [P, C.c_double, C.c_double, dp, dp]
-        L.xfo_weno7.argtypes = [dp, C.c_double]
-        L.xfo_weno7.restype = C.c_double
-        L.xfo_cu6_beta6.argtypes = [dp]
-        L.xfo_cu6_beta6.restype = C.c_double
-        L.xfo_transport.argtypes = [P, C.c_double, C.c_double, dp, dp, dp, dp]
-        L.xfo_rhs_jvp.argtypes = [P, dp, dp, dp, dp, dp, up]
-        L.xfo_rk3_jvp.argtypes = [P, dp, dp, dp, C.c_double, C.c_int, up]
-        _lib = L
+        _lib = load(_build.build())
     return _lib
 
 
@@ -126,12 +130,14 @@ def params(case, viscous=None, convective=True, threads=0, newton_max=50,
 class Oracle:
     """Stateless helpers around one parameter block."""
 
-    def __init__(self, case, **kw):
+    def __init__(self, case, library=None, **kw):
+        """``library``: an oracle library opened with ``load`` (default: the
+        built oracle/libxfo.so)."""
         self.case = case
         self.p = params(case, **kw)
         self.nv = case.n_v
         self.cells = case.cells
-        self.L = lib()
+        self.L = lib() if library is None else library
 
     def prim_to_cons(self, prim=None):
         prim = np.ascontiguousarray(self.case.prim if prim is None else prim, dtype=np.float64)
