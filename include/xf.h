@@ -354,8 +354,12 @@ xf_status xf_barrier_probe(int64_t timeout_cycles, int extra_arrivals, uint32_t 
  *     `stream` and stores the device status bits (XF_FLAG_*) of this call.
  * Returns XF_ERR_ARG, with the required and available sizes in
  * xf_last_error(), when the grid's scratch exceeds the capacity (about
- * 4.5e4 cells in 3D with 5 species, 1e5 cells in 2D with 3 species), or for
- * non-device U / dUdt / T_guess.
+ * 4.5e4 cells in 3D with 5 species, 1e5 cells in 2D with 3 species); also
+ * XF_ERR_ARG, with xf_last_error() naming the cause, for null or non-device
+ * U / dUdt / T_guess and for invalid grid, thermo or options.
+ * The array is part of the library's device image: it is placed in device
+ * memory when the library's kernels are loaded on a device (at the latest on
+ * the first call), not by any call.
  * The first call on each device looks up the array's device address (with
  * that device current) and caches it; make that first call before any stream
  * capture. Every call on a device shares the one array and leaves its contents

@@ -1216,14 +1216,25 @@ int64_t xf_rhs_static_capacity_bytes(void) {
 xf_status xf_rhs_static(const xf_grid* grid, const xf_thermo* thermo, const xf_opts* opts,
                         const double* U, const double* T_guess, double* dUdt,
                         uint32_t* flags_out, void* stream) {
-  if (!U || !dUdt) return XF_ERR_ARG;
+  if (!U || !dUdt) {
+    g_err = "xf_rhs_static: U and dUdt must not be null";
+    return XF_ERR_ARG;
+  }
   xf::Params p;
   xf_status st = fill_params(grid, thermo, opts, &p);
-  if (st != XF_OK) return st;
+  if (st != XF_OK) {
+    g_err = "xf_rhs_static: invalid grid, thermo tables or options";
+    return st;
+  }
   Table tab;
-  if (!pick(p.dim, p.N, &tab)) return XF_ERR_ARG;
-  if (!is_device_ptr(U) || !is_device_ptr(dUdt) || (T_guess && !is_device_ptr(T_guess)))
+  if (!pick(p.dim, p.N, &tab)) {
+    g_err = "xf_rhs_static: unsupported dimension and species count";
     return XF_ERR_ARG;
+  }
+  if (!is_device_ptr(U) || !is_device_ptr(dUdt) || (T_guess && !is_device_ptr(T_guess))) {
+    g_err = "xf_rhs_static: U, dUdt and T_guess must be device pointers";
+    return XF_ERR_ARG;
+  }
   // scratch plan (in doubles): Q | G_x | G_y | G_z | T_in | T_out | dt | red[2] | flags
   long long nf[3] = {0, 0, 0};
   size_t need = nq_of(tab, p) * p.pcells;
