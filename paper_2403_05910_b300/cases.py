@@ -16,7 +16,8 @@ What it generates (the workloads of the XFluids paper, arXiv 2403.05910):
 * a batched ensemble of uneven 2D shock-bubble instances;
 * the 1D multicomponent diffusion case (Sec. IV.B, Table IV) with seeded
   binary diffusion fits for the mixture-averaged model of Eq. 25-26;
-* small smooth periodic fields used by the tests.
+* small smooth periodic fields used by the tests, and smooth seeded
+  perturbations of any case.
 
 Species data is synthetic (no thermochemistry tables exist offline):
 c_p/R(T) is a degree-4 polynomial in tau = (T - T_lo)/(T_hi - T_lo), drawn in
@@ -447,6 +448,37 @@ def uniform_state(dim: int, n: tuple, N: int, seed: int = 0, bc=BC_PERIODIC,
     bcs = tuple((bc, bc) if a < dim else (BC_TRANSMISSIVE, BC_TRANSMISSIVE) for a in range(3))
     return Case("uniform", dim, nn, (0.0,) * 3, (1.0,) * 3, bcs, sp,
                 R_U * 300.0 / 0.028, 1.0, 1.0, viscous, 0.5, np.ascontiguousarray(prim))
+
+
+def with_smooth_perturbation(case: Case, seed: int = 0, amp: float = 1e-3) -> Case:
+    """Copy of ``case`` whose density and pressure are multiplied by
+    1 + amp g and whose velocity components are shifted by amp g, each g a
+    fresh seeded sum of six plane waves (wave numbers U[0.5, 3] per unit
+    length of the unit cube the grid is mapped to, amplitudes U[-1, 1],
+    phases U[0, 2 pi], divided by six). Mass fractions are unchanged. Such a
+    state has no uniform region and no gas at rest, so no two stencil cells
+    share an LLF maximum by round-off."""
+    import dataclasses
+    rng = np.random.default_rng([seed, 77])
+    P = case.prim.copy()
+    nx, ny, nz = case.n
+    z, y, x = np.meshgrid((np.arange(nz) + 0.5) / nz, (np.arange(ny) + 0.5) / ny,
+                          (np.arange(nx) + 0.5) / nx, indexing="ij")
+
+    def field_():
+        g = np.zeros_like(x)
+        for _ in range(6):
+            k = rng.uniform(0.5, 3.0, 3)
+            g += rng.uniform(-1, 1) * np.sin(2 * np.pi * (k[0] * x + k[1] * y + k[2] * z)
+                                             + rng.uniform(0, 2 * np.pi))
+        return g.reshape(-1) / 6
+
+    d = case.dim
+    P[0] *= 1 + amp * field_()
+    for a in range(d):
+        P[1 + a] += amp * field_()
+    P[1 + d] *= 1 + amp * field_()
+    return dataclasses.replace(case, prim=P, name=case.name + "_perturbed")
 
 
 def smooth_periodic(dim: int, n: tuple, N: int, seed: int = 0, amp: float = 0.1,

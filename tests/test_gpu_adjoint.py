@@ -4,7 +4,11 @@ forward path.
 
 <w, J^T-product(v)> identities: for random directions V and weights W,
 sum(Ubar * V_k) computed by xf_rhs_adjoint (Ubar = J^T W) must equal
-sum(W * (J V_k)) from the oracle's dual-number JVP.
+sum(W * (J V_k)) from the oracle's dual-number JVP, to 1e-10 of the largest
+product. Directions vanish on the cells of the state's LLF near-ties
+(tests/llf_ties.py), where the two sides may hand the maximum's derivative
+to different cells of a tie; test_gpu_adjoint_elementwise.py compares those
+cells as groups.
 """
 import numpy as np
 import pytest
@@ -12,6 +16,7 @@ import pytest
 from paper_2403_05910_b300 import cases
 from oracle.xfo import Oracle
 
+import llf_ties
 from gpu_util import dev, gpu_solver
 
 pytestmark = pytest.mark.gpu
@@ -29,6 +34,7 @@ def _cases():
 
 
 CASES = _cases()
+TOL = 1e-10
 
 
 def _dirs(rng, U, k, rel=1.0):
@@ -37,17 +43,16 @@ def _dirs(rng, U, k, rel=1.0):
     return rng.normal(size=(k,) + U.shape) * sc * rel
 
 
-def _rhs_tol(name):
-    """Tolerance of an RHS-adjoint dot test on a case. The shock-bubble
-    states carry near-ties of the LLF maxima: the tanh tails of the bubble
-    interface make the ambient cells' |u -+ c| differ by one ulp (an oracle
-    scan of the 24x14 state finds two such faces for the 6-cell stencils and
-    one for WENO7's 8 cells, relative gaps 1.9e-16). Which cell is the maximum
-    there, and so which cell receives the one-sided derivative of alpha, is
-    decided by round-off that the GPU and the oracle need not share; the
-    flip moves the dot products by ~1e-9 relative. Those states are held to
-    1e-7, the rest (smooth fields, the shock tube) to 1e-10."""
-    return 1e-7 if name.startswith("sbi") else 1e-10
+def _off_ties(case, U, T, V, weno=5):
+    """V with every cell of an LLF near-tie of U (within 1e-13) set to zero:
+    the shock-bubble states hold such ties where the tanh tails of the
+    bubble interface make cells' |u -+ c| differ in the last bits, and which
+    of them receives alpha's one-sided derivative is decided by round-off
+    that the GPU and the oracle need not share. Returns V and the count."""
+    tied = set().union(*llf_ties.tie_groups(case, U, T, 1e-13, weno=weno) or [set()])
+    V = V.copy()
+    V[..., sorted(tied)] = 0.0
+    return V, len(tied)
 
 
 def _dot_check(lhs, rhs, tol):
@@ -62,7 +67,7 @@ def test_rhs_adjoint_matches_oracle_jvp(name):
     o = Oracle(case)
     U, T = o.prim_to_cons()
     rng = np.random.default_rng(11)
-    V = _dirs(rng, U, 8)
+    V, _ = _off_ties(case, U, T, _dirs(rng, U, 8))
     R, JV, _, st = o.rhs_jvp(U, V, T.copy())
     W = rng.normal(size=U.shape)
     s = gpu_solver(case)
@@ -74,24 +79,34 @@ def test_rhs_adjoint_matches_oracle_jvp(name):
     Ubar = Ub.cpu().numpy()
     lhs = [np.sum(Ubar * V[k]) for k in range(8)]
     rhs = [np.sum(W * JV[k]) for k in range(8)]
-    _dot_check(lhs, rhs, _rhs_tol(name))
+    _dot_check(lhs, rhs, TOL)
     s.close()
+
+
+PERTURBED = {
+    "sbi2d_n4_visc_perturbed": cases.with_smooth_perturbation(cases.config(4, n=(24, 14))),
+    "sbi3d_n5_visc_perturbed": cases.with_smooth_perturbation(cases.config(2, n=(12, 8, 8))),
+}
 
 
 @pytest.mark.parametrize("name,tol", [("smooth2d_n3_periodic", 1e-10),
                                       ("smooth1d_n4_inviscid", 1e-10),
-                                      ("tube1d_n2", 1e-9),
+                                      ("tube1d_n2", 1e-10),
+                                      ("sbi2d_n4_visc_perturbed", 1e-10),
+                                      ("sbi3d_n5_visc_perturbed", 1e-10),
                                       ("sbi2d_n4_visc", 1e-5),
                                       ("sbi3d_n5_visc", 1e-5)])
 def test_step_adjoint_matches_oracle_jvp(name, tol):
-    """Reverse of one RK3 step against the oracle's exact JVP. On smooth
-    fields this is a round-off identity. Shock-bubble states hold exact ties
-    of the LLF maxima in their uniform regions; after a stage, cells at the
-    edge of those regions carry near-ties that GPU and oracle (equal to ~1e-13)
-    can resolve to different cells, which moves a kink's one-sided derivative:
-    those states are held to 1e-5."""
+    """Reverse of one RK3 step against the oracle's exact JVP, a round-off
+    identity (1e-10) wherever the step is differentiable. The unperturbed
+    shock-bubble states are not: after the first stage their gas at rest
+    holds velocities of round-off size whose signs the GPU and the oracle
+    need not share (the kink of |u| at 0 in the LLF maxima; on the 64 x 32
+    workload about half of the cells of a patch disagree in sign), which
+    moves the kink's one-sided derivative; they are held to 1e-5, and their
+    smoothly perturbed versions (no gas at rest, no tie) to 1e-10."""
     import torch
-    case = CASES[name]
+    case = PERTURBED[name] if name in PERTURBED else CASES[name]
     o = Oracle(case)
     U, T = o.prim_to_cons()
     dt = 0.5 * o.dt(U, T.copy())
@@ -185,7 +200,7 @@ def test_rhs_adjoint_with_mixture_diffusion_matches_oracle_jvp(name):
     o = Oracle(case, diffusion=1)
     U, T = o.prim_to_cons()
     rng = np.random.default_rng(15)
-    V = _dirs(rng, U, 8)
+    V, _ = _off_ties(case, U, T, _dirs(rng, U, 8))
     R, JV, _, st = o.rhs_jvp(U, V, T.copy())
     W = rng.normal(size=U.shape)
     s = gpu_solver(case, diffusion=1)
@@ -197,7 +212,7 @@ def test_rhs_adjoint_with_mixture_diffusion_matches_oracle_jvp(name):
     Ubar = Ub.cpu().numpy()
     lhs = [np.sum(Ubar * V[k]) for k in range(8)]
     rhs = [np.sum(W * JV[k]) for k in range(8)]
-    _dot_check(lhs, rhs, _rhs_tol(name))
+    _dot_check(lhs, rhs, TOL)
     s.close()
 
 
@@ -241,9 +256,14 @@ def _rarefaction(n=120, uabs=2.0):
 def test_step_adjoint_with_positivity_blend_matches_oracle_jvp(name, tol):
     """Reverse of one RK3 step with the positivity-preserving blend (Eq. 17-20)
     against the oracle's exact JVP of its blended step. On the rarefaction
-    the blend acts (theta < 1 at the centre faces, checked); the shock-bubble
-    state carries the LLF near-ties of its uniform regions (as for the
-    unblended step)."""
+    the blend acts (theta < 1 at the centre faces, checked); near vacuum
+    theta is ill-conditioned, hence 1e-8. The shock-bubble state carries the
+    kinks of its gas at rest (as for the unblended step); its post-shock gas
+    holds none of the bubble species (their partial densities are zero, the
+    implied last one round-off), so the blend binds there on round-off-sized
+    species fluxes. No perturbed shock-bubble state is used: setting that gas
+    in motion makes those fluxes round-off on both sides, and which side's
+    theta binds is then decided by round-off alone."""
     import torch
     case = _rarefaction() if name == "rarefaction" else CASES[name]
     o = Oracle(case, positivity=True)
@@ -285,7 +305,7 @@ def test_rhs_adjoint_with_cu6_and_weno7_matches_oracle_jvp(name, weno):
     o = Oracle(case, weno=weno)
     U, T = o.prim_to_cons()
     rng = np.random.default_rng(18 + weno)
-    V = _dirs(rng, U, 8)
+    V, _ = _off_ties(case, U, T, _dirs(rng, U, 8), weno=weno)
     R, JV, _, st = o.rhs_jvp(U, V, T.copy())
     W = rng.normal(size=U.shape)
     s = gpu_solver(case, weno=weno)
@@ -297,7 +317,7 @@ def test_rhs_adjoint_with_cu6_and_weno7_matches_oracle_jvp(name, weno):
     Ubar = Ub.cpu().numpy()
     lhs = [np.sum(Ubar * V[k]) for k in range(8)]
     rhs = [np.sum(W * JV[k]) for k in range(8)]
-    _dot_check(lhs, rhs, _rhs_tol(name))
+    _dot_check(lhs, rhs, TOL)
     s.close()
 
 

@@ -37,8 +37,9 @@ def _smooth():
 
 
 # (case, options, dot-test tolerance): smooth states are round-off identities;
-# the shock-bubble state carries LLF near-ties (see the step-adjoint tests);
-# the rarefaction is blended near vacuum
+# the unperturbed shock-bubble states carry the kinks of their gas at rest
+# (see the step-adjoint tests), their perturbed versions none; the
+# rarefaction is blended near vacuum
 SETUPS = {
     "weno5": (_smooth, {}, 1e-10),
     "weno_cu6": (_smooth, {"weno": 6}, 1e-10),
@@ -48,6 +49,10 @@ SETUPS = {
     "positivity": (_rarefaction, {"positivity": True}, 1e-8),
     "sbi2d_n4_visc": (lambda: cases.config(4, n=(24, 14)), {}, 1e-5),
     "sbi3d_n5_visc": (lambda: cases.config(2, n=(12, 8, 8)), {}, 1e-5),
+    "sbi2d_n4_visc_perturbed": (
+        lambda: cases.with_smooth_perturbation(cases.config(4, n=(24, 14))), {}, 1e-10),
+    "sbi3d_n5_visc_perturbed": (
+        lambda: cases.with_smooth_perturbation(cases.config(2, n=(12, 8, 8))), {}, 1e-10),
 }
 
 
