@@ -29,19 +29,13 @@ WORKLOADS = {
     "sbi3d_n5": (2, None),
     "sbi2d_n3": (1, None),
 }
-FP64_NOMINAL_TFLOPS = 1.25   # B300 dense FP64 (nominal)
-# DRAM bytes per face of k_face from an ncu capture, keyed by the first 16 hex
-# digits of the sha256 of the kernel source it was taken on; any other source
-# reports traffic null (the counters no longer describe the kernel).
-FACE_TRAFFIC_B_PER_FACE = {"aab342d14388773d": 294.0, "7aa2c6f72cd106cc": 294.2,
-                           "69f88d1a3ee86fc1": 293.6, "e3f39384d86bd1a7": 293.2,
-                           "5117291dbdc4468e": 293.1, "5a85b98a1838b428": 293.1,
-                           "0f34872dcfaaaf05": 292.8, "c71f3e8407ad8c7a": 293.6,
-                           "16e94dc84f3a5109": 292.8, "2349bd5adee7afd2": 292.9,
-                           "f263a26a5971860e": 293.0,
-                           "0602a26c075d3356": 293.1,
-                           "dedb921fb50202ed": 293.5,
-                           "451cb69c9faafb9d": 292.8, "d015dec47061b893": 292.7}
+FP64_NOMINAL_TFLOPS = 1.25   # B300 dense FP64 (nominal), reported beside the measured probe
+# ncu figures of k_face on the 3D 5-species case (160x80x80, 1 launch, x faces):
+# DRAM bytes and executed FP64 flops (DFMA = 2) per face, valid only for the
+# kernel source they were taken on (first 16 hex digits of the sha256 of
+# xf_device.cuh); any other source reports them as null.
+FACE_NCU = {"source": "0000000000000000", "dram_bytes_per_face": None,
+            "fp64_flops_executed_per_face": None}
 # bounded oracle samples of each workload (config index -> grid)
 CPU_SAMPLE_GRID = {2: (96, 48, 48), 1: (256, 128)}
 
@@ -128,9 +122,10 @@ def _dist():
     return ws, rank, local
 
 
-def _cpu_baseline(cfg=2, steps=None, warmup=0, budget_s=15.0):
-    """Time the oracle on a bounded sample of the workload on the host cores."""
-    import numpy as np
+def _cpu_baseline(cfg=2, steps=5, warmup=1):
+    """Time the oracle on a bounded sample of the workload on the host cores:
+    ``warmup`` untimed steps, then ``steps`` steps timed one by one; the rate
+    is that of the median step (the spread of the steps beside it)."""
     from paper_2403_05910_b300 import cases
     from oracle.xfo import Oracle
     cores = len(os.sched_getaffinity(0))
@@ -139,23 +134,24 @@ def _cpu_baseline(cfg=2, steps=None, warmup=0, budget_s=15.0):
     o = Oracle(case, threads=cores)
     U, T = o.prim_to_cons()
     dt = o.dt(U, T)
-    for _ in range(warmup):
+    for _ in range(max(1, warmup)):
         o.step(U, T, dt)
-    n, t0 = 0, time.perf_counter()
-    while True:
+    times = []
+    for _ in range(max(3, steps)):
+        t0 = time.perf_counter()
         o.step(U, T, dt)
-        n += 1
-        el = time.perf_counter() - t0
-        if (steps is not None and n >= steps) or (steps is None and (el >= budget_s or n >= 20)):
-            break
-    val = case.cells * 3 * n / el
-    return {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{n} RK3 step(s) of the same setup ({case.name}) on a "
+        times.append(time.perf_counter() - t0)
+    med = statistics.median(times)
+    rate = [case.cells * 3 / t for t in times]
+    return {"value": case.cells * 3 / med, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{len(times)} RK3 steps timed one by one (median), after "
+                      f"{max(1, warmup)} untimed, of the same setup ({case.name}) on a "
                       f"{'x'.join(map(str, grid))} grid ({case.cells} cells)",
-            "seconds": el}
+            "grid": list(grid), "seconds": sum(times), "median_step_s": med,
+            "spread": [min(rate), max(rate)]}
 
 
-def _cpu_single_core(cfg=2, budget_s=6.0):
+def _cpu_single_core(cfg=2, steps=3):
     """The oracle on one host core (the kind of CPU figure GPU speed-ups are
     usually quoted against), on a smaller sample of the same workload."""
     from paper_2403_05910_b300 import cases
@@ -166,16 +162,16 @@ def _cpu_single_core(cfg=2, budget_s=6.0):
     U, T = o.prim_to_cons()
     dt = o.dt(U, T)
     o.step(U, T, dt)
-    n, t0 = 0, time.perf_counter()
-    while True:
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
         o.step(U, T, dt)
-        n += 1
-        el = time.perf_counter() - t0
-        if el >= budget_s or n >= 10:
-            break
-    return {"value": case.cells * 3 * n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n} RK3 step(s) on a {'x'.join(map(str, grid))} grid ({case.cells} cells)",
-            "seconds": el}
+        times.append(time.perf_counter() - t0)
+    med = statistics.median(times)
+    return {"value": case.cells * 3 / med, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} RK3 steps timed one by one (median) on a "
+                      f"{'x'.join(map(str, grid))} grid ({case.cells} cells)",
+            "seconds": sum(times)}
 
 
 def _config(case, ws):
@@ -209,12 +205,18 @@ def run_reference(args):
         return 0
     from oracle import build as ob
     ob.build()
-    cb = _cpu_baseline(WORKLOADS[args.workload][0], steps=args.steps, warmup=args.warmup)
+    cfg = WORKLOADS[args.workload][0]
+    cb = _cpu_baseline(cfg, steps=args.steps, warmup=args.warmup)
+    config = _config(_workload_meta(args), ws)
+    grid = "x".join(map(str, cb["grid"]))
+    config["workload"] += (f"; the oracle is timed on a {grid} sample of the same setup "
+                           f"(the rate per cell-stage does not depend on the grid size)")
+    config["timed_grid"] = grid
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * cb["seconds"] / args.steps, "higher_is_better": True,
+            "ms_per_step": 1e3 * cb["median_step_s"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": _config(_workload_meta(args), ws),
+            "config": config,
             "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -401,7 +403,7 @@ def _variants(args, dev, stream, case):
         face_tf = fl["face"] / case.dim / (face_ms / face_n * 1e-3) / 1e12
         out[name] = {"value": case.cells * 3 * steps / (ms * 1e-3), "unit": UNIT,
                      "ms_per_step": ms / steps, "steps": steps,
-                     "face_fp64_tflops": face_tf, "face_frac": face_tf / FP64_NOMINAL_TFLOPS,
+                     "face_fp64_tflops": face_tf, "face_frac_of_nominal": face_tf / FP64_NOMINAL_TFLOPS,
                      "flops_per_face": flops.face(case.dim, case.n_species, case.viscous,
                                                   kw.get("weno", 5), kw.get("positivity", False),
                                                   kw.get("diffusion", 0)),
@@ -471,9 +473,12 @@ def run_ours(args):
     import hashlib
     with open(os.path.join(ROOT, "paper_2403_05910_b300", "csrc", "xf_device.cuh"), "rb") as f:
         src_hash = hashlib.sha256(f.read()).hexdigest()[:16]
-    bpf = FACE_TRAFFIC_B_PER_FACE.get(src_hash)
-    traffic = None if bpf is None else bpf * (fl["face"] / flops.face(
-        case.dim, case.n_species, case.viscous)) / case.dim
+    faces_per_launch = fl["face"] / case.dim / flops.face(case.dim, case.n_species, case.viscous)
+    ncu_ok = FACE_NCU["source"] == src_hash
+    bpf = FACE_NCU["dram_bytes_per_face"] if ncu_ok else None
+    xpf = FACE_NCU["fp64_flops_executed_per_face"] if ncu_ok else None
+    traffic = None if bpf is None else bpf * faces_per_launch
+    executed = None if xpf is None else xpf * faces_per_launch / (face_ms / face_n * 1e-3) / 1e12
     peaks = _peaks()
     hbm = peaks.get("hbm_gbs", 6400.0)
     alg_bytes = sum(flops.hbm_bytes_per_cell_stage(case, st) for st in range(3)) / 3.0
@@ -513,10 +518,18 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": _config(case, ws),
             "roofline": {"bound": "alu", "kernel": "k_face (x, y, z face fluxes)",
-                         "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP64_NOMINAL_TFLOPS,
-                         "peak_note": "nominal B300 dense FP64; measured FMA probe beside it",
-                         "peak_probe": fp64_probe, "frac_of_probe": achieved / fp64_probe,
+                         "achieved": achieved, "peak": fp64_probe, "unit": "TFLOP/s",
+                         "frac": achieved / fp64_probe,
+                         "peak_note": "the library's FP64 FMA probe (independent DFMA "
+                                      "chains on every SM) measured in this run; achieved "
+                                      "counts the plain formulation's flops per face",
+                         "peak_nominal": FP64_NOMINAL_TFLOPS,
+                         "frac_of_nominal": achieved / FP64_NOMINAL_TFLOPS,
+                         "executed": executed,
+                         "frac_executed": None if executed is None else executed / fp64_probe,
+                         "executed_note": "ncu-counted FP64 flops per face of this source "
+                                          "(DFMA = 2) per launch duration; null when the "
+                                          "counters were taken on another source",
                          "flops_per_face": flops.face(case.dim, case.n_species, case.viscous),
                          "traffic": traffic, "traffic_unit": "B per launch",
                          "kernel_source": src_hash},
