@@ -370,6 +370,7 @@ xf_status fill_params(const xf_grid* g, const xf_thermo* th, const xf_opts* o, x
     p->wenoe[0] = e12 * xf::kWc0; p->wenoe[1] = e12 * xf::kWc1; p->wenoe[2] = e12 * xf::kWc2;
     p->wenoe[3] = e12;
   }
+  for (int k = 0; k < 4; ++k) p->wenoe4[k] = 0.25 * p->wenoe[k];
   p->weno = o->weno;
   p->newton_rtol = o->newton_rtol;
   p->newton_max = o->newton_max;

@@ -56,6 +56,10 @@ struct Params {
   double cfl, weno_eps, newton_rtol;
   double wenoe[4];   // epsilon terms of the reconstruction (rec_nd): 12 eps c_k
                      // (k < 3) and 12 eps for WENO5 / CU6, 240 eps c_k for WENO7
+  double wenoe4[4];  // the same divided by 4: for data scaled by -1/2 (the
+                     // reconstructions are homogeneous of degree one when eps
+                     // scales with the square of the data, exactly so for a
+                     // power-of-two factor)
   int viscous, convective, newton_max;
   int weno;          // 5: WENO5-JS, 6: WENO-CU6
   int positivity;    // positivity-preserving blend of the convective flux (Eq. 17-20)
@@ -797,6 +801,7 @@ __device__ __forceinline__ void conv_flux(const Params& p, const double* __restr
     gUh[m] = g;
   }
   const double e12c[4] = {p.wenoe[0], p.wenoe[1], p.wenoe[2], p.wenoe[3]};
+  const double e12q[4] = {p.wenoe4[0], p.wenoe4[1], p.wenoe4[2], p.wenoe4[3]};
   const double chc = c * hic2;
   // ---- PER: one characteristic field at a time. With w = (1/2)(l.F_m +- a l.U_m)
   //      and l.F_m = u_m (l.U_m) + p_m (l[m_n] + u_m l[E]):
@@ -850,9 +855,9 @@ __device__ __forceinline__ void conv_flux(const Params& p, const double* __restr
 #pragma unroll
       for (int m = 0; m < SW; ++m) {
         const double LU = fma(-chc, nUv[m], gUh[m]);
-        const double pq = fma(-dl, p_m[m], pV[m]);
-        wp[m] = fma(hun[m] + ha, LU, pq);
-        wm[m] = fma(hun[m] - ha, LU, pq);
+        const double X = fma(hun[m], LU, fma(-dl, p_m[m], pV[m]));
+        wp[m] = fma(ha, LU, X);
+        wm[m] = fma(-ha, LU, X);
       }
       ndm = rec_nd<REC>(wp, wm, e12c);
     }
@@ -862,9 +867,9 @@ __device__ __forceinline__ void conv_flux(const Params& p, const double* __restr
 #pragma unroll
       for (int m = 0; m < SW; ++m) {
         const double LU = fma(chc, nUv[m], gUh[m]);
-        const double pq = fma(dl, p_m[m], pV[m]);
-        wp[m] = fma(hun[m] + ha, LU, pq);
-        wm[m] = fma(hun[m] - ha, LU, pq);
+        const double X = fma(hun[m], LU, fma(dl, p_m[m], pV[m]));
+        wp[m] = fma(ha, LU, X);
+        wm[m] = fma(-ha, LU, X);
       }
       ndp = rec_nd<REC>(wp, wm, e12c);
     }
@@ -873,16 +878,18 @@ __device__ __forceinline__ void conv_flux(const Params& p, const double* __restr
     const double ha0 = 0.5 * a0;
 #pragma unroll
     for (int m = 0; m < SW; ++m) { hp0[m] = hun[m] + ha0; hm0[m] = hun[m] - ha0; }
-    // entropy: l = e_rho - g / c^2
+    // entropy: l = e_rho - g / c^2, w = (u_m/2 +- a/2)(rho - 2 g.U/(2c^2)) - 2 pV,
+    // reconstructed as -w/2 = (u_m/2 +- a/2)(g.U/(2c^2) - rho/2) + pV with
+    // eps/4 (bitwise -1/2 of the reconstruction of w: a power-of-two factor
+    // commutes with every rounding); Fk_eh is -Fk_e/2
     {
 #pragma unroll
       for (int m = 0; m < SW; ++m) {
-        const double LU = fma(-2.0, gUh[m], rho_m[m]);
-        const double pq = -2.0 * pV[m];
-        wp[m] = fma(hp0[m], LU, pq);
-        wm[m] = fma(hm0[m], LU, pq);
+        const double LUh = fma(-0.5, rho_m[m], gUh[m]);
+        wp[m] = fma(hp0[m], LUh, pV[m]);
+        wm[m] = fma(hm0[m], LUh, pV[m]);
       }
-      nde = rec_nd<REC>(wp, wm, e12c);
+      nde = rec_nd<REC>(wp, wm, e12q);
     }
     // the entropy field shares its division with the first passive field
     if constexpr (NPASS > 0) rec_div2<REC>(nde, passive_nd(0), Fk_e, Fk_first);
@@ -890,13 +897,13 @@ __device__ __forceinline__ void conv_flux(const Params& p, const double* __restr
   }
   // back-projection of the three dense right columns (Eq. 15)
   {
-    const double S = Fk_m + Fk_p + Fk_e;
+    const double S = fma(-2.0, Fk_e, Fk_m + Fk_p);
     const double Dl = Fk_p - Fk_m;
     Gout[0] = S;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) Gout[1 + a] = ub[a] * S;
     Gout[1 + D] = fma(c, Dl, Gout[1 + D]);
-    Gout[IE] = fma(Hb, S, fma(un * c, Dl, -c2 * iGam * Fk_e));
+    Gout[IE] = fma(Hb, S, fma(un * c, Dl, (c2 + c2) * iGam * Fk_e));
 #pragma unroll
     for (int s = 0; s < NS - 1; ++s) Gout[IE + 1 + s] = Yb[s] * S;
   }
@@ -1024,21 +1031,25 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
 #define FD0(field) (fma(15.0, QF(field, 1) - QF(field, 0), -(QF(field, 2) - QF(field, -1))))
 #define FI(field) (FI0(field) * wi)
 #define FD(field) (FD0(field) * wd)
-    const double mu = FI(L::MU), rf = FI(L::U);
-    double gr[DIM][DIM];
+    const double rf = FI(L::U);
+    // tau_Da (Eq. 3) = (mu/16) t16_a with t16_a = 16 (du_D/dx_a + du_a/dx_D)
+    // for a != D and t16_D = 16 (4/3 du_D/dx_D - 2/3 sum_{a != D} du_a/dx_a);
+    // FI0 of the nodal derivatives is 16 times their face value, FD0 of u is
+    // the normal derivative over wd, so rq = wd/wi weights the normal ones
+    const double mu16 = FI0(L::MU) * (wi * wi);
+    const double rq = 16.0 * wd;
+    double t16[DIM], tr = 0.0;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
-#pragma unroll
-      for (int b = 0; b < DIM; ++b) gr[a][b] = (b == D) ? FD(L::UN + a) : FI(L::GU + a * DIM + b);
+      if (a == D) continue;
+      t16[a] = fma(rq, FD0(L::UN + a), FI0(L::GU + D * DIM + a));
+      tr += FI0(L::GU + a * DIM + a);
     }
-    double div = 0.0;
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) div += gr[a][a];
+    t16[D] = fma((4.0 / 3.0) * rq, FD0(L::UN + D), (-2.0 / 3.0) * tr);
     double work16 = 0.0;  // 16 sum_a tau_a u_a
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
-      double tau = mu * (gr[D][a] + gr[a][D]);
-      if (a == D) tau = fma(-2.0 / 3.0 * mu, div, tau);
+      const double tau = mu16 * t16[a];
       Gout[1 + a] -= tau;
       work16 = fma(tau, FI0(L::UN + a), work16);
     }
