@@ -99,6 +99,7 @@ using UpdRFn = void (*)(const xf::Params&, const double*, const double*, const d
                         const double*, const double*, double*, const double*, int, long long,
                         long long, cudaStream_t);
 using FromPrimFn = void (*)(const xf::Params&, const double*, double*, double*, cudaStream_t);
+using GhostRFn = void (*)(const xf::Params&, double*, long long, long long, cudaStream_t);
 
 
 struct Table {
@@ -112,12 +113,14 @@ struct Table {
   int nq;
   XfAdjTable adj;  // reverse-mode launchers (xf_adjoint_launch.cu)
   PrimRFn prim_r;
+  GhostRFn ghost_r;
   FaceRFn face_r[3][3];  // [weno - 5][direction]
   UpdRFn update_r;
 };
 
 template <int DIM, int NS>
 struct Launch {
+  // primitive recovery of interior cells [b, e)
   static void prim_r(const xf::Params& p, const double* U, const double* Tin, double* Tout,
                      double* Q, uint32_t* fl, unsigned long long* red, int cfl, long long b,
                      long long e, cudaStream_t s) {
@@ -125,9 +128,15 @@ struct Launch {
     const int bs = bsize(e - b, 256);
     xf::k_prim<DIM, NS><<<blocks(e - b, bs), bs, 0, s>>>(p, U, Tin, Tout, Q, fl, red, cfl, b, e);
   }
+  // ghost cells among padded cells [b, e), copied from their interior images
+  static void ghost_r(const xf::Params& p, double* Q, long long b, long long e, cudaStream_t s) {
+    if (e <= b || p.pcells == p.cells) return;
+    xf::k_ghost<DIM, NS><<<blocks(e - b, 256), 256, 0, s>>>(p, Q, b, e);
+  }
   static void prim(const xf::Params& p, const double* U, const double* Tin, double* Tout,
                    double* Q, uint32_t* fl, unsigned long long* red, int cfl, cudaStream_t s) {
-    prim_r(p, U, Tin, Tout, Q, fl, red, cfl, 0, p.pcells, s);
+    prim_r(p, U, Tin, Tout, Q, fl, red, cfl, 0, p.cells, s);
+    ghost_r(p, Q, 0, p.pcells, s);
   }
   static void grad(const xf::Params& p, double* Q, cudaStream_t s) {
     const int bs = bsize(p.pcells, 256);
@@ -171,7 +180,7 @@ struct Launch {
   static Table table() {
     Table t{prim, grad, {face<0>, face<1>, face<2>}, {face<0, 6>, face<1, 6>, face<2, 6>},
             {face<0, 7>, face<1, 7>, face<2, 7>}, update, from_prim, xf::Lay<DIM, NS>::NQ,
-            XfAdjTable{}, prim_r,
+            XfAdjTable{}, prim_r, ghost_r,
             {{face_r<0>, face_r<1>, face_r<2>}, {face_r<0, 6>, face_r<1, 6>, face_r<2, 6>},
              {face_r<0, 7>, face_r<1, 7>, face_r<2, 7>}},
             update_r};
@@ -822,21 +831,22 @@ xf_status xf_step_rk3_host(xf_handle* h, const double* U_in, const double* T_in,
   }
   const bool cfl = !(dt > 0.0);
   if (!cfl) k_set_scalar<<<1, 1, 0, s>>>(h->dt, dt);
-  // stage 1: the primitive recovery of each slab's padded planes as soon as
-  // its upload lands; the ghost planes of axis a (which map onto any slab)
-  // after the last one
+  // stage 1: the primitive recovery of each slab's interior planes as soon
+  // as its upload lands, then the ghosts inside those planes (their images
+  // lie in the same plane); the ghost planes of axis a (whose images are on
+  // any slab) after the last one
   double* Tout = h->T[1 - h->tcur];
   for (int j = 0; j < S; ++j) {
     XF_CUDA(cudaStreamWaitEvent(s, ev[j], 0));
     timed(h, XF_PROF_PRIM, s, [&] {
       h->tab.prim_r(p, h->U, Tn, Tout, h->Q, h->flags, h->red, cfl ? 1 : 0,
-                    (sl.z(j) + sl.G) * sl.ps, (sl.z(j + 1) + sl.G) * sl.ps, s);
+                    sl.z(j) * sl.cs, sl.z(j + 1) * sl.cs, s);
+      h->tab.ghost_r(p, h->Q, (sl.z(j) + sl.G) * sl.ps, (sl.z(j + 1) + sl.G) * sl.ps, s);
     });
   }
   timed(h, XF_PROF_PRIM, s, [&] {
-    h->tab.prim_r(p, h->U, Tn, Tout, h->Q, h->flags, h->red, cfl ? 1 : 0, 0, sl.G * sl.ps, s);
-    h->tab.prim_r(p, h->U, Tn, Tout, h->Q, h->flags, h->red, cfl ? 1 : 0,
-                  (sl.n + sl.G) * sl.ps, p.pcells, s);
+    h->tab.ghost_r(p, h->Q, 0, sl.G * sl.ps, s);
+    h->tab.ghost_r(p, h->Q, (sl.n + sl.G) * sl.ps, p.pcells, s);
   });
   h->tcur = 1 - h->tcur;
   if (cfl) timed(h, XF_PROF_DT, s, [&] { k_dt_finalize<<<1, 1, 0, s>>>(p, h->red, h->dt, nullptr); });

@@ -321,18 +321,22 @@ __device__ __forceinline__ void prim_cell(const Params& p, long long t, const do
         xk1[s] = X[s] * iska[s];
         xk2[s] = xk1[s] * iska[s];
       }
+      // The diagonal t = s contributes exactly X_s (Phi_ss = 1: A_ss = 1/4,
+      // B_ss = 1), added once instead of through the five sums.
       double dm[NS], dk[NS];
 #pragma unroll
       for (int s = 0; s < NS; ++s) {
         double s0 = 0.0, m1 = 0.0, m2 = 0.0, k1 = 0.0, k2 = 0.0;
 #pragma unroll
         for (int tt = 0; tt < NS; ++tt) {
+          if (tt == s) continue;
           s0 = fma(X[tt], p.wA[s][tt], s0);
           m1 = fma(xm1[tt], p.wAB[s][tt], m1);
           m2 = fma(xm2[tt], p.wABB[s][tt], m2);
           k1 = fma(xk1[tt], p.wAB[s][tt], k1);
           k2 = fma(xk2[tt], p.wABB[s][tt], k2);
         }
+        s0 += X[s];
         dm[s] = fma(smu[s] * smu[s], m2, fma(2.0 * smu[s], m1, s0));
         dk[s] = fma(ska[s] * ska[s], k2, fma(2.0 * ska[s], k1, s0));
       }
@@ -451,18 +455,64 @@ __device__ __forceinline__ void block_max2(double s_cfl, double s_nu, unsigned l
   }
 }
 
-// Padded cells [t0, t1) (0 <= t0 <= t1 <= pcells; the whole box, or one slab
-// of planes of the slowest axis).
+// Interior cells [c0, c1) (0 <= c0 <= c1 <= cells; the whole grid, or one
+// slab of planes of the slowest axis), each written at its padded position.
+// The ghost layers are filled afterwards by k_ghost.
 template <int DIM, int NS>
 __global__ void __launch_bounds__(256)
 k_prim(const __grid_constant__ Params p, const double* __restrict__ U,
        const double* __restrict__ Tin, double* __restrict__ Tout,
        double* __restrict__ Q, uint32_t* __restrict__ flags,
-       unsigned long long* __restrict__ red, int do_cfl, long long t0, long long t1) {
-  const long long t = t0 + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+       unsigned long long* __restrict__ red, int do_cfl, long long c0, long long c1) {
+  const long long c = c0 + (long long)blockIdx.x * blockDim.x + threadIdx.x;
   double s_cfl = 0.0, s_nu = 0.0;
-  if (t < t1) prim_cell<DIM, NS>(p, t, U, Tin, Tout, Q, flags, do_cfl, s_cfl, s_nu);
+  if (c < c1) {
+    const unsigned cu = (unsigned)c, n0 = (unsigned)p.n[0], n1 = (unsigned)p.n[1];
+    const unsigned q = cu / n0;
+    const long long i = cu - q * n0, j = q % n1, k = q / n1;
+    const long long t = ((k + p.go[2]) * p.np[1] + (j + p.go[1])) * p.np[0] + (i + p.go[0]);
+    prim_cell<DIM, NS>(p, t, U, Tin, Tout, Q, flags, do_cfl, s_cfl, s_nu);
+  }
   if (do_cfl) block_max2(s_cfl, s_nu, red);
+}
+
+// Ghost cells among the padded cells [t0, t1): a copy of the per-cell fields
+// of the interior cell that the boundary conditions map them to, with the
+// normal velocity and momentum negated across a symmetric boundary -- bitwise
+// what prim_cell computes for the ghost itself from the mapped conserved
+// state (its Newton solve starts from the same warm start and the negation
+// commutes with every rounding), at the cost of a copy. The nodal gradients
+// are not copied: k_grad computes them over the whole padded block.
+template <int DIM, int NS>
+__global__ void __launch_bounds__(256)
+k_ghost(const __grid_constant__ Params p, double* __restrict__ Q, long long t0, long long t1) {
+  using L = Lay<DIM, NS>;
+  const long long t = t0 + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= t1) return;
+  const int ip = (int)(t % p.np[0]);
+  const int jp = (int)((t / p.np[0]) % p.np[1]);
+  const int kp = (int)(t / ((long long)p.np[0] * p.np[1]));
+  const int i = ip - p.go[0], j = jp - p.go[1], k = kp - p.go[2];
+  bool f[3] = {false, false, false};
+  const int si = map_axis(i, p.n[0], p.bc[0][0], p.bc[0][1], &f[0]);
+  const int sj = DIM > 1 ? map_axis(j, p.n[1], p.bc[1][0], p.bc[1][1], &f[1]) : 0;
+  const int sk = DIM > 2 ? map_axis(k, p.n[2], p.bc[2][0], p.bc[2][1], &f[2]) : 0;
+  if (si == i && sj == j && sk == k) return;  // interior
+  const long long PC = p.pcells;
+  const long long src = ((long long)(sk + p.go[2]) * p.np[1] + (sj + p.go[1])) * p.np[0] +
+                        (si + p.go[0]);
+#pragma unroll
+  for (int v = 0; v < L::GU; ++v) {
+    double x = Q[v * PC + src];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a)
+      if (f[a] && (v == L::U + 1 + a || v == L::UN + a)) x = -x;
+    Q[v * PC + t] = x;
+  }
+  if (p.diffusion == 1) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s) Q[(L::DS + s) * PC + t] = Q[(L::DS + s) * PC + src];
+  }
 }
 
 // dt from the reduced maxima: CFL / max sum_d (|u_d| + c)/dx_d, and the
