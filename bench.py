@@ -325,13 +325,64 @@ def _adjoint_vs_forward(args, dev, stream):
     grad = _gradient_timing(s, c, dt, dev, stream)
     st |= s.status()
     s.close()
+    options = {name: _adjoint_option(c, kw, dt, W, k, dev, stream) for name, kw in ADJ_OPTIONS}
     return {"workload": "sbi2d_n4_adjoint: 512x256, 4 species, viscous, fixed dt",
             "rhs_ms": f, "rhs_adjoint_ms": a, "rhs_ratio": a / f,
             "step_ms": fs, "step_adjoint_ms": at, "step_ratio": at / fs,
             "step_adjoint_recompute_ms": ar, "step_ratio_recompute": ar / fs,
             "note": "step adjoint from the taped stage states (xf_step_rk3_adjoint_tape); "
                     "the recompute form rebuilds the two intermediate stage states itself",
-            "gradient": grad, "status_flags": st}
+            "options": options, "gradient": grad, "status_flags": st}
+
+
+ADJ_OPTIONS = (("weno_cu6", {"weno": 6}), ("weno7", {"weno": 7}),
+               ("mixture_averaged_diffusion", {"diffusion": 1}),
+               ("weno5+positivity", {"positivity": True}))
+
+
+def _adjoint_option(c, kw, dt, W, k, dev, stream):
+    """One option of the path on the differentiated workload: RHS and RHS
+    adjoint, step and step adjoint (taped; with the blend, from the stage
+    states and the flux tape; and recomputing), in ms."""
+    import torch
+    from paper_2403_05910_b300 import cases
+    from paper_2403_05910_b300.xf import Solver
+    case = cases.with_binary_diffusion(c) if kw.get("diffusion") else c
+    s = Solver(case, **kw)
+    s.set_primitive(torch.from_numpy(c.prim).to(dev))
+    U = torch.empty((c.n_v, c.cells), dtype=torch.float64, device=dev)
+    s.get_state(U)
+    R, Ub = torch.empty_like(U), torch.zeros_like(U)
+
+    def timed(fn):
+        fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    f = timed(lambda: s.rhs(U, R))
+    a = timed(lambda: s.rhs_adjoint(U, W, Ub))
+    fs = timed(lambda: s.step(dt))
+    U1, U2 = torch.empty_like(U), torch.empty_like(U)
+    Fh = (torch.empty(s.tape_flux_len(), dtype=torch.float64, device=dev)
+          if kw.get("positivity") else None)
+    s.set_state(U)
+    s.step_tape(dt, U1, U2, Fhat=Fh)
+    s.set_state(U)
+    at = timed(lambda: s.step_adjoint_tape(dt, U1, U2, Ub, Fhat=Fh))
+    s.set_state(U)
+    ar = timed(lambda: s.step_adjoint(dt, Ub))
+    st = s.status()
+    s.close()
+    return {"rhs_ms": f, "rhs_adjoint_ms": a, "rhs_ratio": a / f, "step_ms": fs,
+            "step_adjoint_taped_ms": at, "step_ratio_taped": at / fs,
+            "step_adjoint_recompute_ms": ar, "step_ratio_recompute": ar / fs,
+            "flux_tape": Fh is not None, "status_flags": st}
 
 
 def _gradient_timing(s, c, dt, dev, stream):

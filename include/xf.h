@@ -247,6 +247,25 @@ xf_status xf_step_rk3_adjoint(xf_handle *h, double dt, double *U_bar, void *stre
 xf_status xf_step_rk3_tape(xf_handle *h, double dt, double *U1, double *U2, void *stream);
 xf_status xf_step_rk3_adjoint_tape(xf_handle *h, double dt, const double *U1, const double *U2,
                                    double *U_bar, void *stream);
+/* The taped pair above with a flux tape, for handles with the positivity-
+ * preserving blend (Eq. 17-20), whose reverse needs every face's unblended
+ * convective flux F_hat (Eq. 15) to reverse theta. xf_step_rk3_tape_flux is
+ * xf_step_rk3_tape that also writes F_hat of its three stages into Fhat
+ * (device, caller-owned, xf_tape_flux_len(h) doubles: stage by stage,
+ * direction by direction, each direction [n_v][faces] in the order of the
+ * face fluxes, faces i fastest); xf_step_rk3_adjoint_tape_flux is
+ * xf_step_rk3_adjoint_tape reading F_hat from that tape instead of
+ * recomputing it (same dt, U1, U2 and Fhat as the tape step wrote them; not
+ * checked). Without the blend the tape is written and not read. Results equal
+ * those of the pair above up to the order of the atomic adds. XF_ERR_ARG for
+ * null or non-device buffers, U1 == U2 or dt <= 0. xf_tape_flux_len returns
+ * -1 for a null handle. */
+int64_t xf_tape_flux_len(const xf_handle *h);
+xf_status xf_step_rk3_tape_flux(xf_handle *h, double dt, double *U1, double *U2, double *Fhat,
+                                void *stream);
+xf_status xf_step_rk3_adjoint_tape_flux(xf_handle *h, double dt, const double *U1,
+                                        const double *U2, const double *Fhat, double *U_bar,
+                                        void *stream);
 /* Mixing measure J = sum_cells Y_s (1 - Y_s) dV of species `species` (0-based)
  * for the state U: J_dev (device, one double) = J, U_bar = dJ/dU (overwritten). */
 xf_status xf_objective_mixing(xf_handle *h, const double *U, int species,

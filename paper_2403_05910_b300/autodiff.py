@@ -14,6 +14,10 @@ functions here only move device buffers between those calls:
   the re-run also keeps every step's two intermediate stage states
   (``xf_step_rk3_tape``, 2 ``every`` extra states per segment) and the reverse
   steps take them (``xf_step_rk3_adjoint_tape``) instead of recomputing them.
+  With the positivity-preserving blend the re-run also keeps every step's
+  flux tape (``xf_step_rk3_tape_flux``: the unblended convective face fluxes
+  of its three stages), which the reverse of the blend reads instead of
+  recomputing them.
 * ``MixingObjective``: J = sum Y_s (1 - Y_s) dV of one species.
 
 The time step is frozen (a fixed dt), so the discrete map is differentiable
@@ -91,15 +95,17 @@ class RK3Steps(torch.autograd.Function):
                 s.get_state(U, T)
                 if ctx.tape:
                     U1, U2 = _empty_state(s, dev), _empty_state(s, dev)
-                    s.step_tape(dt, U1, U2)
-                    states.append((U, T, U1, U2))
+                    Fh = (torch.empty(s.tape_flux_len(), dtype=torch.float64, device=dev)
+                          if s.positivity else None)
+                    s.step_tape(dt, U1, U2, Fhat=Fh)
+                    states.append((U, T, U1, U2, Fh))
                 else:
                     s.step(dt)
                     states.append((U, T))
             for st in reversed(states):
                 s.set_state(st[0], st[1])
                 if ctx.tape:
-                    s.step_adjoint_tape(dt, st[2], st[3], Ub)
+                    s.step_adjoint_tape(dt, st[2], st[3], Ub, Fhat=st[4])
                 else:
                     s.step_adjoint(dt, Ub)
         return Ub, None, None, None, None, None

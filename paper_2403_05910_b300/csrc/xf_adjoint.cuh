@@ -341,21 +341,30 @@ __device__ __forceinline__ bool gt_nn(double a, double b) {
 // theta is clipped at 0 or eps = lo, where theta is locally constant) and
 // through F_LF of Eq. 19 (alpha through the cell with the larger |u_d| + c)
 // to U, u_d, p and c of the two cells (scattered into Qb). Gc returns the
-// adjoint of F_hat (Gb itself when the blend is inactive).
+// adjoint of F_hat (Gb itself when the blend is inactive). With fh given,
+// F_hat is read from the flux tape (fh[v * fstride], written by the forward
+// step's k_face_tape) instead of being recomputed.
 template <int DIM, int NS, int D, int REC>
 __device__ __forceinline__ void pos_blend_adj(const Params& p, const double* __restrict__ q0,
                                               double* __restrict__ qb0, long long PC, long long sd,
-                                              double dt, const double* Gb, double* Gc) {
+                                              double dt, const double* Gb, double* Gc,
+                                              const double* __restrict__ fh = nullptr,
+                                              long long fstride = 0) {
   using L = Lay<DIM, NS>;
   constexpr int NV = L::NV;
   constexpr int IE = DIM + 1;
 #define QF(field, m) ld(q0 + (long long)(field) * PC + (long long)(m) * sd)
 #define QB(field, m, val) aadd(qb0 + (long long)(field) * PC + (long long)(m) * sd, (val))
   double Gh[NV];
+  if (fh) {
 #pragma unroll
-  for (int v = 0; v < NV; ++v) Gh[v] = 0.0;
-  uint32_t st = 0;
-  conv_flux<DIM, NS, D, REC>(p, q0, PC, sd, Gh, st);
+    for (int v = 0; v < NV; ++v) Gh[v] = ld(fh + v * fstride);
+  } else {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Gh[v] = 0.0;
+    uint32_t st = 0;
+    conv_flux<DIM, NS, D, REC>(p, q0, PC, sd, Gh, st);
+  }
   const double lam2 = 2.0 * DIM * dt * p.inv_dx[D];
   double Ua[NV], Ub[NV], Fa[NV], Fb[NV], Flf[NV];
 #pragma unroll
@@ -487,7 +496,8 @@ template <int DIM, int NS, int D, bool POS = false, int REC = 5>
 __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk,
                                          const double* __restrict__ Q,
                                          const double* __restrict__ Rbar, double scale,
-                                         double* __restrict__ Qb, double dt = 0.0) {
+                                         double* __restrict__ Qb, double dt = 0.0,
+                                         const double* __restrict__ Fh = nullptr) {
   using L = Lay<DIM, NS>;
   constexpr int NV = L::NV;
   constexpr int IE = DIM + 1;
@@ -523,7 +533,10 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
     // positivity-preserving blend inside an RK stage
     double Gc[NV];
     if constexpr (POS) {
-      pos_blend_adj<DIM, NS, D, REC>(p, q0, qb0, PC, sd, dt, Gb, Gc);
+      const long long nf0 = p.n[0] + (D == 0), nf1 = p.n[1] + (D == 1), nf2 = p.n[2] + (D == 2);
+      const long long f = ((long long)fk * nf1 + fj) * nf0 + fi;
+      pos_blend_adj<DIM, NS, D, REC>(p, q0, qb0, PC, sd, dt, Gb, Gc, Fh ? Fh + f : nullptr,
+                                     nf0 * nf1 * nf2);
     } else {
 #pragma unroll
       for (int v = 0; v < NV; ++v) Gc[v] = Gb[v];
@@ -1071,6 +1084,20 @@ k_face_adj_pos(const __grid_constant__ Params p, const double* __restrict__ Q,
   if (f >= (long long)nf0 * nf1 * nf2) return;
   face_adj<DIM, NS, D, true, REC>(p, (int)(f % nf0), (int)((f / nf0) % nf1),
                                   (int)(f / ((long long)nf0 * nf1)), Q, Rbar, scale, Qb, *dtp);
+}
+
+// the same reading the unblended convective fluxes of the forward step from
+// the flux tape Fh ([n_v][faces] of this direction and stage)
+template <int DIM, int NS, int D, int REC = 5>
+__global__ void __launch_bounds__(128)
+k_face_adj_pos_tape(const __grid_constant__ Params p, const double* __restrict__ Q,
+                    const double* __restrict__ Rbar, double scale, double* __restrict__ Qb,
+                    const double* __restrict__ dtp, const double* __restrict__ Fh) {
+  const int nf0 = p.n[0] + (D == 0), nf1 = p.n[1] + (D == 1), nf2 = p.n[2] + (D == 2);
+  const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= (long long)nf0 * nf1 * nf2) return;
+  face_adj<DIM, NS, D, true, REC>(p, (int)(f % nf0), (int)((f / nf0) % nf1),
+                                  (int)(f / ((long long)nf0 * nf1)), Q, Rbar, scale, Qb, *dtp, Fh);
 }
 
 // ================================================================ k_prim_adj

@@ -37,6 +37,17 @@ struct AdjLaunch {
                                                                          dt);
     }
   }
+  template <int D, int REC>
+  static void face_adj_pos_tape(const xf::Params& p, const double* Q, const double* Rb,
+                                double scale, double* Qb, const double* dt, const double* Fh,
+                                cudaStream_t s) {
+    if constexpr (D < DIM) {
+      const long long nf =
+          (long long)(p.n[0] + (D == 0)) * (p.n[1] + (D == 1)) * (p.n[2] + (D == 2));
+      xf::k_face_adj_pos_tape<DIM, NS, D, REC><<<blocks(nf, 128), 128, 0, s>>>(p, Q, Rb, scale,
+                                                                              Qb, dt, Fh);
+    }
+  }
   static void grad_adj(const xf::Params& p, double* Qb, cudaStream_t s) {
     xf::k_grad_adj<DIM, NS><<<blocks(p.pcells, 256), 256, 0, s>>>(p, Qb);
   }
@@ -60,6 +71,9 @@ struct AdjLaunch {
     t->face_adj_pos[R - 5][0] = face_adj_pos<0, R>;
     t->face_adj_pos[R - 5][1] = face_adj_pos<1, R>;
     t->face_adj_pos[R - 5][2] = face_adj_pos<2, R>;
+    t->face_adj_pos_tape[R - 5][0] = face_adj_pos_tape<0, R>;
+    t->face_adj_pos_tape[R - 5][1] = face_adj_pos_tape<1, R>;
+    t->face_adj_pos_tape[R - 5][2] = face_adj_pos_tape<2, R>;
 #if XF_ADJ_REC == 5
     t->grad_adj = grad_adj;
     t->prim_adj = prim_adj;

@@ -100,6 +100,8 @@ using UpdRFn = void (*)(const xf::Params&, const double*, const double*, const d
                         long long, cudaStream_t);
 using FromPrimFn = void (*)(const xf::Params&, const double*, double*, double*, cudaStream_t);
 using GhostRFn = void (*)(const xf::Params&, double*, long long, long long, cudaStream_t);
+using FaceTFn = void (*)(const xf::Params&, const double*, double*, uint32_t*, const double*,
+                         double*, cudaStream_t);
 
 
 struct Table {
@@ -116,6 +118,7 @@ struct Table {
   GhostRFn ghost_r;
   FaceRFn face_r[3][3];  // [weno - 5][direction]
   UpdRFn update_r;
+  FaceTFn face_tape[3][3];  // [weno - 5][direction]: also write the flux tape
 };
 
 template <int DIM, int NS>
@@ -158,6 +161,15 @@ struct Launch {
         (long long)(p.n[0] + (D == 0)) * (p.n[1] + (D == 1)) * (p.n[2] + (D == 2));
     face_r<D, REC>(p, Q, G, fl, dt, 0, nf, s);
   }
+  template <int D, int REC = 5>
+  static void face_tape(const xf::Params& p, const double* Q, double* G, uint32_t* fl,
+                        const double* dt, double* Fh, cudaStream_t s) {
+    if constexpr (D < DIM) {
+      const long long nf =
+          (long long)(p.n[0] + (D == 0)) * (p.n[1] + (D == 1)) * (p.n[2] + (D == 2));
+      xf::k_face_tape<DIM, NS, D, REC><<<blocks(nf, 128), 128, 0, s>>>(p, Q, G, fl, dt, Fh);
+    }
+  }
   static void update_r(const xf::Params& p, const double* Gx, const double* Gy, const double* Gz,
                        const double* Un, const double* Us, double* out, const double* dt,
                        int mode, long long b, long long e, cudaStream_t s) {
@@ -183,7 +195,10 @@ struct Launch {
             XfAdjTable{}, prim_r, ghost_r,
             {{face_r<0>, face_r<1>, face_r<2>}, {face_r<0, 6>, face_r<1, 6>, face_r<2, 6>},
              {face_r<0, 7>, face_r<1, 7>, face_r<2, 7>}},
-            update_r};
+            update_r,
+            {{face_tape<0>, face_tape<1>, face_tape<2>},
+             {face_tape<0, 6>, face_tape<1, 6>, face_tape<2, 6>},
+             {face_tape<0, 7>, face_tape<1, 7>, face_tape<2, 7>}}};
     xf_internal_adj_fill5(DIM, NS, &t.adj);
     xf_internal_adj_fill6(DIM, NS, &t.adj);
     xf_internal_adj_fill7(DIM, NS, &t.adj);
@@ -432,11 +447,21 @@ void timed(xf_handle* h, int slot, cudaStream_t s, F&& fn) {
   h->recs.push_back(r);
 }
 
+// Flux tape of one RK stage: the unblended convective fluxes of every face,
+// direction by direction, each [n_v][faces of that direction].
+long long tape_dir_off(const xf::Params& p, int d) {
+  long long off = 0;
+  for (int e = 0; e < d; ++e)
+    off += (long long)p.nv * (p.n[0] + (e == 0)) * (p.n[1] + (e == 1)) * (p.n[2] + (e == 2));
+  return off;
+}
+long long tape_stage_len(const xf::Params& p) { return tape_dir_off(p, p.dim); }
+
 // Primitive recovery + (viscous) nodal gradients + every face flux of Uin.
 // Inside an RK stage (`stepping`) the face kernels see the stage dt, which the
 // positivity-preserving blend needs; a plain RHS has no dt.
 xf_status stage_fluxes(xf_handle* h, const double* Uin, int do_cfl, cudaStream_t s,
-                       bool stepping = false) {
+                       bool stepping = false, double* Fh = nullptr) {
   const xf::Params& p = h->p;
   timed(h, XF_PROF_PRIM, s, [&] {
     h->tab.prim(p, Uin, h->T[h->tcur], h->T[1 - h->tcur], h->Q, h->flags, h->red, do_cfl, s);
@@ -448,8 +473,13 @@ xf_status stage_fluxes(xf_handle* h, const double* Uin, int do_cfl, cudaStream_t
   for (int d = 0; d < p.dim; ++d)
     timed(h, XF_PROF_FACE_X + d, s,
           [&] {
-            faces_of(h->tab, p.weno)[d](p, h->Q, h->G[d], h->flags, stepping ? h->dt : nullptr,
-                                        s);
+            if (Fh)
+              h->tab.face_tape[p.weno - 5][d](p, h->Q, h->G[d], h->flags,
+                                              stepping ? h->dt : nullptr,
+                                              Fh + tape_dir_off(p, d), s);
+            else
+              faces_of(h->tab, p.weno)[d](p, h->Q, h->G[d], h->flags,
+                                          stepping ? h->dt : nullptr, s);
           });
   XF_CUDA(cudaGetLastError());
   return XF_OK;
@@ -496,7 +526,7 @@ xf_status ensure_adjoint_buffers(xf_handle* h) {
 // RK stage's time step, for the reverse of the positivity blend.
 xf_status rhs_adjoint_impl(xf_handle* h, const double* U, const double* Rbar, double scale,
                            double* Ubar, cudaStream_t s, bool fields_ready = false,
-                           const double* dtp = nullptr) {
+                           const double* dtp = nullptr, const double* Fh = nullptr) {
   xf_status st = ensure_adjoint_buffers(h);
   if (st != XF_OK) return st;
   if (!fields_ready) {
@@ -508,7 +538,11 @@ xf_status rhs_adjoint_impl(xf_handle* h, const double* U, const double* Rbar, do
   for (int d = 0; d < p.dim; ++d)
     timed(h, XF_PROF_FACE_ADJ, s, [&] {
       const int r = p.weno - 5;
-      if (p.positivity && dtp) h->tab.adj.face_adj_pos[r][d](p, h->Q, Rbar, scale, h->Qb, dtp, s);
+      if (p.positivity && dtp && Fh)
+        h->tab.adj.face_adj_pos_tape[r][d](p, h->Q, Rbar, scale, h->Qb, dtp,
+                                           Fh + tape_dir_off(p, d), s);
+      else if (p.positivity && dtp)
+        h->tab.adj.face_adj_pos[r][d](p, h->Q, Rbar, scale, h->Qb, dtp, s);
       else h->tab.adj.face_adj[r][d](p, h->Q, Rbar, scale, h->Qb, s);
     });
   if (p.viscous) timed(h, XF_PROF_GRAD, s, [&] { h->tab.adj.grad_adj(p, h->Qb, s); });
@@ -770,24 +804,25 @@ xf_status xf_compute_dt(xf_handle* h, double* dt_dev, void* stream) {
 // One SSP-RK3 step. The stage states go to U1 and U2 when given (the taped
 // step), else both to the handle's stage buffer.
 static xf_status step_impl(xf_handle* h, double dt, double* dt_dev_out, cudaStream_t s,
-                           double* U1 = nullptr, double* U2 = nullptr) {
+                           double* U1 = nullptr, double* U2 = nullptr, double* Fhat = nullptr) {
   const xf::Params& p = h->p;
   const bool cfl = !(dt > 0.0);
   double* S1 = U1 ? U1 : h->Us;
   double* S2 = U2 ? U2 : h->Us;
+  const long long tl = tape_stage_len(p);
   if (!cfl) k_set_scalar<<<1, 1, 0, s>>>(h->dt, dt);
   // Eq. 16: three stages, U^n kept in U
-  xf_status st = stage_fluxes(h, h->U, cfl ? 1 : 0, s, true);
+  xf_status st = stage_fluxes(h, h->U, cfl ? 1 : 0, s, true, Fhat);
   if (st != XF_OK) return st;
   timed(h, XF_PROF_UPDATE, s, [&] {
     h->tab.update(p, h->G[0], h->G[1], h->G[2], h->U, h->U, S1, h->dt, 1, s);
   });
-  st = stage_fluxes(h, S1, 0, s, true);
+  st = stage_fluxes(h, S1, 0, s, true, Fhat ? Fhat + tl : nullptr);
   if (st != XF_OK) return st;
   timed(h, XF_PROF_UPDATE, s, [&] {
     h->tab.update(p, h->G[0], h->G[1], h->G[2], h->U, S1, S2, h->dt, 2, s);
   });
-  st = stage_fluxes(h, S2, 0, s, true);
+  st = stage_fluxes(h, S2, 0, s, true, Fhat ? Fhat + 2 * tl : nullptr);
   if (st != XF_OK) return st;
   timed(h, XF_PROF_UPDATE, s, [&] {
     h->tab.update(p, h->G[0], h->G[1], h->G[2], h->U, S2, h->U, h->dt, 3, s);
@@ -1048,11 +1083,13 @@ xf_status xf_step_rk3_tape(xf_handle* h, double dt, double* U1, double* U2, void
   return step_impl(h, dt, nullptr, (cudaStream_t)stream, U1, U2);
 }
 
-xf_status xf_step_rk3_adjoint_tape(xf_handle* h, double dt, const double* U1, const double* U2,
-                                   double* U_bar, void* stream) {
-  if (!h || !U1 || !U2 || !U_bar || !(dt > 0.0)) return XF_ERR_ARG;
-  if (!is_device_ptr(U1) || !is_device_ptr(U2) || !is_device_ptr(U_bar)) return XF_ERR_ARG;
-  cudaStream_t s = (cudaStream_t)stream;
+static xf_status step_adjoint_tape_impl(xf_handle* h, double dt, const double* U1,
+                                        const double* U2, const double* Fhat, double* U_bar,
+                                        cudaStream_t s) {
+  const long long tl = tape_stage_len(h->p);
+  const double* F0 = Fhat;
+  const double* F1 = Fhat ? Fhat + tl : nullptr;
+  const double* F2 = Fhat ? Fhat + 2 * tl : nullptr;
   xf_status st = ensure_adjoint_buffers(h);
   if (st != XF_OK) return st;
   st = ensure_stage_fields(h);
@@ -1073,18 +1110,45 @@ xf_status xf_step_rk3_adjoint_tape(xf_handle* h, double dt, const double* U1, co
   if (st != XF_OK) return st;
   // the reverse of xf_step_rk3_adjoint on those fields
   lincomb(h, 2.0 / 3.0, U_bar, 0.0, nullptr, 0.0, nullptr, h->B2, s);
-  st = rhs_adjoint_impl(h, U2, U_bar, 2.0 / 3.0 * dt, h->B2, s, true, h->dt);
+  st = rhs_adjoint_impl(h, U2, U_bar, 2.0 / 3.0 * dt, h->B2, s, true, h->dt, F2);
   if (st != XF_OK) return st;
   lincomb(h, 0.25, h->B2, 0.0, nullptr, 0.0, nullptr, h->B1, s);
   h->Q = h->QS[1];
-  st = rhs_adjoint_impl(h, U1, h->B2, 0.25 * dt, h->B1, s, true, h->dt);
+  st = rhs_adjoint_impl(h, U1, h->B2, 0.25 * dt, h->B1, s, true, h->dt, F1);
   if (st != XF_OK) return st;
   lincomb(h, 1.0 / 3.0, U_bar, 0.75, h->B2, 1.0, h->B1, U_bar, s);
   h->Q = h->QS[0];
-  st = rhs_adjoint_impl(h, h->U, h->B1, dt, U_bar, s, true, h->dt);
+  st = rhs_adjoint_impl(h, h->U, h->B1, dt, U_bar, s, true, h->dt, F0);
   if (st != XF_OK) return st;
   XF_CUDA(cudaGetLastError());
   return XF_OK;
+}
+
+xf_status xf_step_rk3_adjoint_tape(xf_handle* h, double dt, const double* U1, const double* U2,
+                                   double* U_bar, void* stream) {
+  if (!h || !U1 || !U2 || !U_bar || !(dt > 0.0)) return XF_ERR_ARG;
+  if (!is_device_ptr(U1) || !is_device_ptr(U2) || !is_device_ptr(U_bar)) return XF_ERR_ARG;
+  return step_adjoint_tape_impl(h, dt, U1, U2, nullptr, U_bar, (cudaStream_t)stream);
+}
+
+int64_t xf_tape_flux_len(const xf_handle* h) {
+  return h ? (int64_t)(3 * tape_stage_len(h->p)) : -1;
+}
+
+xf_status xf_step_rk3_tape_flux(xf_handle* h, double dt, double* U1, double* U2, double* Fhat,
+                                void* stream) {
+  if (!h || !U1 || !U2 || !Fhat || U1 == U2 || !(dt > 0.0)) return XF_ERR_ARG;
+  if (!is_device_ptr(U1) || !is_device_ptr(U2) || !is_device_ptr(Fhat)) return XF_ERR_ARG;
+  return step_impl(h, dt, nullptr, (cudaStream_t)stream, U1, U2, Fhat);
+}
+
+xf_status xf_step_rk3_adjoint_tape_flux(xf_handle* h, double dt, const double* U1,
+                                        const double* U2, const double* Fhat, double* U_bar,
+                                        void* stream) {
+  if (!h || !U1 || !U2 || !Fhat || !U_bar || !(dt > 0.0)) return XF_ERR_ARG;
+  if (!is_device_ptr(U1) || !is_device_ptr(U2) || !is_device_ptr(Fhat) || !is_device_ptr(U_bar))
+    return XF_ERR_ARG;
+  return step_adjoint_tape_impl(h, dt, U1, U2, Fhat, U_bar, (cudaStream_t)stream);
 }
 
 xf_status xf_objective_mixing(xf_handle* h, const double* U, int species, double* J_dev,

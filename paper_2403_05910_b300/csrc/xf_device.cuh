@@ -1043,10 +1043,13 @@ __device__ __forceinline__ void pos_blend(const Params& p, const double* __restr
 
 // Per-face body: face (fi, fj, fk) of direction D, i.e. between cells
 // idx - e_D and idx (fi in 0..n_0 when D = 0, and so on).
+// With Fh given, the face's unblended convective flux (Eq. 15, before the
+// blend and the viscous terms) also goes to Fh ([n_v][faces], Gf's layout).
 template <int DIM, int NS, int D, int REC = 5>
 __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk,
                                          const double* __restrict__ Q, double* __restrict__ Gf,
-                                         uint32_t* __restrict__ flags, double dt) {
+                                         uint32_t* __restrict__ flags, double dt,
+                                         double* __restrict__ Fh = nullptr) {
   using L = Lay<DIM, NS>;
   constexpr int NV = L::NV;
   constexpr int IE = DIM + 1;
@@ -1067,6 +1070,10 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
   uint32_t st = 0;
 
   if (p.convective) conv_flux<DIM, NS, D, REC>(p, q0, PC, sd, Gout, st);
+  if (Fh) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Fh[v * nfaces + f] = Gout[v];
+  }
 
   if (p.convective && p.positivity && dt > 0.0) pos_blend<DIM, NS, D>(p, q0, PC, sd, dt, Gout);
 
@@ -1160,6 +1167,21 @@ k_face(const __grid_constant__ Params p, const double* __restrict__ Q,
   if (f >= f1) return;
   face_one<DIM, NS, D, REC>(p, (int)(f % nf0), (int)((f / nf0) % nf1), (int)(f / ((long long)nf0 * nf1)),
                        Q, Gf, flags, dtp ? *dtp : 0.0);
+}
+
+// Every face of direction D as k_face, also writing the unblended convective
+// fluxes to Fh: the tape that the reverse of the positivity blend reads
+// (xf_step_rk3_tape_flux) instead of recomputing them.
+template <int DIM, int NS, int D, int REC = 5>
+__global__ void __launch_bounds__(128, XF_FACE_MIN_BLOCKS)
+k_face_tape(const __grid_constant__ Params p, const double* __restrict__ Q,
+            double* __restrict__ Gf, uint32_t* __restrict__ flags, const double* __restrict__ dtp,
+            double* __restrict__ Fh) {
+  const int nf0 = p.n[0] + (D == 0), nf1 = p.n[1] + (D == 1), nf2 = p.n[2] + (D == 2);
+  const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= (long long)nf0 * nf1 * nf2) return;
+  face_one<DIM, NS, D, REC>(p, (int)(f % nf0), (int)((f / nf0) % nf1), (int)(f / ((long long)nf0 * nf1)),
+                            Q, Gf, flags, dtp ? *dtp : 0.0, Fh);
 }
 
 // =============================================================== k_update ===

@@ -20,6 +20,8 @@ using XfFaceAdjFn = void (*)(const xf::Params&, const double*, const double*, do
                              cudaStream_t);
 using XfFaceAdjPosFn = void (*)(const xf::Params&, const double*, const double*, double, double*,
                                 const double*, cudaStream_t);
+using XfFaceAdjPosTFn = void (*)(const xf::Params&, const double*, const double*, double,
+                                 double*, const double*, const double*, cudaStream_t);
 using XfGradAdjFn = void (*)(const xf::Params&, double*, cudaStream_t);
 using XfCellAdjFn = void (*)(const xf::Params&, const double*, const double*, double*,
                              cudaStream_t);
@@ -28,6 +30,7 @@ using XfMixFn = void (*)(const xf::Params&, const double*, int, double, double*,
 struct XfAdjTable {
   XfFaceAdjFn face_adj[3][3];
   XfFaceAdjPosFn face_adj_pos[3][3];  // inside an RK stage with the positivity blend
+  XfFaceAdjPosTFn face_adj_pos_tape[3][3];  // the same, reading the flux tape
   XfGradAdjFn grad_adj;
   XfCellAdjFn prim_adj;
   XfCellAdjFn from_prim_adj;

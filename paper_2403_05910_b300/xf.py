@@ -53,7 +53,8 @@ EXPORTS = ["xf_create", "xf_destroy", "xf_nv", "xf_cells", "xf_set_state", "xf_s
            "xf_batch_set_state", "xf_batch_get_state", "xf_batch_step_rk3", "xf_batch_autotune",
            "xf_batch_config", "xf_batch_get_status", "xf_barrier_probe", "xf_batch_uses_graph",
            "xf_batch_num_candidates", "xf_rhs_adjoint", "xf_step_rk3_adjoint",
-           "xf_step_rk3_tape", "xf_step_rk3_adjoint_tape", "xf_objective_mixing",
+           "xf_step_rk3_tape", "xf_step_rk3_adjoint_tape", "xf_tape_flux_len",
+           "xf_step_rk3_tape_flux", "xf_step_rk3_adjoint_tape_flux", "xf_objective_mixing",
            "xf_set_primitive_adjoint"]
 PROF_SLOTS = 10
 PROF_NAMES = ["prim", "dt", "grad", "face_x", "face_y", "face_z", "update", "face_adj", "prim_adj",
@@ -95,6 +96,10 @@ def _load():
     L.xf_step_rk3_adjoint.argtypes = [vp, C.c_double, vp, vp]
     L.xf_step_rk3_tape.argtypes = [vp, C.c_double, vp, vp, vp]
     L.xf_step_rk3_adjoint_tape.argtypes = [vp, C.c_double, vp, vp, vp, vp]
+    L.xf_tape_flux_len.argtypes = [vp]
+    L.xf_tape_flux_len.restype = C.c_int64
+    L.xf_step_rk3_tape_flux.argtypes = [vp, C.c_double, vp, vp, vp, vp]
+    L.xf_step_rk3_adjoint_tape_flux.argtypes = [vp, C.c_double, vp, vp, vp, vp, vp]
     L.xf_objective_mixing.argtypes = [vp, vp, C.c_int, vp, vp, vp]
     L.xf_set_primitive_adjoint.argtypes = [vp, vp, vp, vp, vp]
     L.xf_batch_create.argtypes = [C.c_int, C.POINTER(Grid), C.POINTER(Thermo), C.POINTER(Opts),
@@ -209,6 +214,7 @@ class Solver:
         self.case = case
         self.nv = case.n_v
         self.cells = case.cells
+        self.positivity = bool(kw.get("positivity", False))
         h = C.c_void_p()
         check(lib.xf_create(C.byref(g), C.byref(t), C.byref(o), C.byref(h)), "xf_create")
         self.h = h
@@ -272,15 +278,30 @@ class Solver:
         check(lib.xf_step_rk3_adjoint(self.h, float(dt), ptr(U_bar), stream_ptr(stream)),
               "xf_step_rk3_adjoint")
 
-    def step_tape(self, dt, U1, U2, stream=None):
-        """One fixed-dt RK3 step that also writes its stage states U1, U2."""
-        check(lib.xf_step_rk3_tape(self.h, float(dt), ptr(U1), ptr(U2), stream_ptr(stream)),
-              "xf_step_rk3_tape")
+    def step_tape(self, dt, U1, U2, stream=None, Fhat=None):
+        """One fixed-dt RK3 step that also writes its stage states U1, U2 (and,
+        with Fhat, the unblended convective face fluxes of its stages)."""
+        if Fhat is None:
+            check(lib.xf_step_rk3_tape(self.h, float(dt), ptr(U1), ptr(U2), stream_ptr(stream)),
+                  "xf_step_rk3_tape")
+        else:
+            check(lib.xf_step_rk3_tape_flux(self.h, float(dt), ptr(U1), ptr(U2), ptr(Fhat),
+                                            stream_ptr(stream)), "xf_step_rk3_tape_flux")
 
-    def step_adjoint_tape(self, dt, U1, U2, U_bar, stream=None):
-        """step_adjoint with the stage states of step_tape given (U_bar in/out)."""
-        check(lib.xf_step_rk3_adjoint_tape(self.h, float(dt), ptr(U1), ptr(U2), ptr(U_bar),
-                                           stream_ptr(stream)), "xf_step_rk3_adjoint_tape")
+    def step_adjoint_tape(self, dt, U1, U2, U_bar, stream=None, Fhat=None):
+        """step_adjoint with the stage states of step_tape given (U_bar in/out),
+        and with its flux tape when Fhat is given."""
+        if Fhat is None:
+            check(lib.xf_step_rk3_adjoint_tape(self.h, float(dt), ptr(U1), ptr(U2), ptr(U_bar),
+                                               stream_ptr(stream)), "xf_step_rk3_adjoint_tape")
+        else:
+            check(lib.xf_step_rk3_adjoint_tape_flux(self.h, float(dt), ptr(U1), ptr(U2),
+                                                    ptr(Fhat), ptr(U_bar), stream_ptr(stream)),
+                  "xf_step_rk3_adjoint_tape_flux")
+
+    def tape_flux_len(self):
+        """Doubles of one step's flux tape (step_tape with Fhat)."""
+        return int(lib.xf_tape_flux_len(self.h))
 
     def objective_mixing(self, U, species, J_dev, U_bar, stream=None):
         check(lib.xf_objective_mixing(self.h, ptr(U), int(species), ptr(J_dev), ptr(U_bar),
