@@ -30,12 +30,13 @@ WORKLOADS = {
     "sbi2d_n3": (1, None),
 }
 FP64_NOMINAL_TFLOPS = 1.25   # B300 dense FP64 (nominal), reported beside the measured probe
-# ncu figures of k_face on the 3D 5-species case (160x80x80, 1 launch, x faces):
-# DRAM bytes and executed FP64 flops (DFMA = 2) per face, valid only for the
+# ncu figures of k_face on the 3D 5-species case (160x80x80, one launch per
+# direction; profiles/k_face_sbi3d_n5_160x80x80.md): DRAM bytes (mean of the
+# three directions) and executed FP64 flops (DFMA = 2) per face, valid only for the
 # kernel source they were taken on (first 16 hex digits of the sha256 of
 # xf_device.cuh); any other source reports them as null.
-FACE_NCU = {"source": "0000000000000000", "dram_bytes_per_face": None,
-            "fp64_flops_executed_per_face": None}
+FACE_NCU = {"source": "8719e608dc1de3d3", "dram_bytes_per_face": 304.5,
+            "fp64_flops_executed_per_face": 1973.0}
 # bounded oracle samples of each workload (config index -> grid)
 CPU_SAMPLE_GRID = {2: (96, 48, 48), 1: (256, 128)}
 
