@@ -513,7 +513,10 @@ def run_ours(args):
     status = s.status()
     cell_stages = case.cells * 3 * args.steps
     value = whole_job_rate(cell_stages, ms_all * 1e-3, ws)
+    # kernels launched: one per profiled region, plus the ghost-layer copy
+    # (k_ghost) that follows k_prim in each primitive-recovery region
     launches = sum(n for _, n in prof.values())
+    launches += prof.get("prim", (0.0, 0))[1]
 
     # ---- roofline of the dominant kernel class (the face-flux kernels)
     fl = flops.per_cell_stage(case)
@@ -562,7 +565,7 @@ def run_ours(args):
         if ws == 1 and not args.no_cpu_baseline:
             from oracle import build as ob
             ob.build()
-            cpu = _cpu_baseline(cfg)
+            cpu = _cpu_baseline(cfg, steps=5, warmup=3)
             cpu["single_core"] = _cpu_single_core(cfg)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
