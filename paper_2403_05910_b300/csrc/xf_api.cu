@@ -150,7 +150,7 @@ struct Launch {
                      const double* dt, long long b, long long e, cudaStream_t s) {
     if constexpr (D < DIM) {
       if (e <= b) return;
-      const int bs = bsize(e - b, 128);
+      const int bs = bsize(e - b, XF_FACE_THREADS);
       xf::k_face<DIM, NS, D, REC><<<blocks(e - b, bs), bs, 0, s>>>(p, Q, G, fl, dt, b, e);
     }
   }
@@ -167,7 +167,8 @@ struct Launch {
     if constexpr (D < DIM) {
       const long long nf =
           (long long)(p.n[0] + (D == 0)) * (p.n[1] + (D == 1)) * (p.n[2] + (D == 2));
-      xf::k_face_tape<DIM, NS, D, REC><<<blocks(nf, 128), 128, 0, s>>>(p, Q, G, fl, dt, Fh);
+      xf::k_face_tape<DIM, NS, D, REC><<<blocks(nf, XF_FACE_THREADS), XF_FACE_THREADS, 0, s>>>(
+          p, Q, G, fl, dt, Fh);
     }
   }
   static void update_r(const xf::Params& p, const double* Gx, const double* Gy, const double* Gz,

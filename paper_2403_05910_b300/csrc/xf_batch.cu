@@ -251,7 +251,7 @@ __global__ void k_barrier_probe(const __grid_constant__ BCtl c, unsigned expect)
 // per-cell fields of an instance (plus D_sm per species with the
 // mixture-averaged diffusion)
 int nq_of(const xf::Params& p) {
-  return 2 * p.N + 2 * p.dim + 9 + p.dim * p.dim + (p.diffusion ? p.N : 0);
+  return xf::lay_nq(p.dim, p.N) + (p.diffusion ? p.N : 0);
 }
 
 struct Candidate {

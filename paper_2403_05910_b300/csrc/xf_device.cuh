@@ -67,6 +67,12 @@ struct Params {
   double hmin2_over_2dim;
 };
 
+// Number of per-cell fields of Lay<dim, ns> (without the D_sm fields), for
+// host code that sizes the field block from runtime (dim, N).
+__host__ __device__ constexpr int lay_nq(int dim, int ns) {
+  return (dim + 1 + ns) + dim + 5 + ns + 5 + 1 + 3 + dim * dim;
+}
+
 // Padded per-cell field layout (SoA, stride pcells).
 template <int DIM, int NS>
 struct Lay {
@@ -79,13 +85,16 @@ struct Lay {
   static constexpr int H = SR + 1;      // total enthalpy
   static constexpr int T = H + 1;       // temperature (K)
   static constexpr int Y = T + 1;       // Y_1..Y_N
-  static constexpr int MU = Y + NS;     // mixture viscosity
+  static constexpr int AC = Y + NS;     // mixture c_p coefficients A_0..A_4 (c_p = sum A_j tau^j)
+  static constexpr int RM = AC + 5;     // mixture gas constant sum Y_s R_s
+  static constexpr int MU = RM + 1;     // mixture viscosity
   static constexpr int KA = MU + 1;     // mixture conductivity
   static constexpr int DF = KA + 1;     // diffusivity
   static constexpr int GU = DF + 1;     // nodal d u_a / d x_b at GU + a*DIM + b
   static constexpr int NQ = GU + DIM * DIM;
   static constexpr int DS = NQ;         // D_sm of species 1..N, present (and
                                         // allocated) only with diffusion = 1
+  static_assert(NQ == lay_nq(DIM, NS), "lay_nq must count the fields of Lay");
 };
 
 __device__ __forceinline__ double ld(const double* p) { return __ldg(p); }
@@ -276,6 +285,9 @@ __device__ __forceinline__ void prim_cell(const Params& p, long long t, const do
     q[L::T * PC] = T;
 #pragma unroll
     for (int s = 0; s < NS; ++s) q[(L::Y + s) * PC] = Y[s];
+#pragma unroll
+    for (int jj = 0; jj < 5; ++jj) q[(L::AC + jj) * PC] = A[jj];
+    q[L::RM * PC] = Rm;
     double mu = 0.0, ka = 0.0, Dd = 0.0;
     if (p.viscous) {
       // Eq. 29 fits; sqrt(mu_s) = exp(ln mu_s / 2) feeds the Wilke ratios (Eq. 22)
@@ -376,12 +388,13 @@ __device__ __forceinline__ void prim_cell(const Params& p, long long t, const do
 #pragma unroll
         for (int s = 0; s < NS; ++s) { Xt[s] = fmax(X[s], 0.0) + 1e-12; xts += Xt[s]; }
         const double ixts = rcp_nr(xts);
-        double Wt = 0.0, XW[NS];
+        // the sums of products are written as fused multiply-adds: the
+        // batched kernel compiles this body too and must give the same bits
+        double Wt = 0.0;
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
           Xt[s] *= ixts;
-          XW[s] = Xt[s] * p.Wm[s];
-          Wt += XW[s];
+          Wt = fma(Xt[s], p.Wm[s], Wt);
         }
         double den[NS];
 #pragma unroll
@@ -404,7 +417,7 @@ __device__ __forceinline__ void prim_cell(const Params& p, long long t, const do
           double num = 0.0;
 #pragma unroll
           for (int tt = 0; tt < NS; ++tt)
-            if (tt != s) num += XW[tt];
+            if (tt != s) num = fma(Xt[tt], p.Wm[tt], num);
           const double Ds = num * sc * rcp_nr(den[s]);
           q[(L::DS + s) * PC] = Ds;
           Dmax = fmax(Dmax, Ds);
@@ -591,15 +604,18 @@ __device__ __forceinline__ void weno5_nd(double f0, double f1, double f2, double
   const double s0 = fma((16.0 * kWc0) * A0, A0, fma((9.75 * kWc0) * b, b, e12c[0]));
   const double s1 = fma((16.0 * kWc1) * B1, B1, fma(9.75 * kWc1, cc, e12c[1]));
   const double s2 = fma((16.0 * kWc2) * D2, D2, fma(9.75 * kWc2, cc, e12c[2]));
-  const double p12 = s1 * s2, p02 = s0 * s2, p01 = s0 * s1;
-  const double w0 = p12 * p12, w1 = p02 * p02, w2 = p01 * p01;
   // 6 (q_k - f2): 5b - 2a = 9/4 b - 2 A0, 2c + b, 4c - d; the factor 6 goes
   // to the denominator of the field pair (rec_scale)
   const double q0 = fma(-2.0, A0, 2.25 * b);
   const double q1 = fma(2.0, c, b);
   const double q2 = fma(4.0, c, -d);
-  num = fma(w0, q0, fma(w1, q1, w2 * q2));
-  den = (w0 + w1) + w2;
+  // weights w_0 = (s_1 s_2)^2, w_1 = (s_0 s_2)^2, w_2 = (s_0 s_1)^2 with
+  // a_k = s_k^2 grouped as num = a_2 (a_1 q_0 + a_0 q_1) + a_0 a_1 q_2 and
+  // den = a_2 (a_0 + a_1) + a_0 a_1
+  const double a0 = s0 * s0, a1 = s1 * s1, a2 = s2 * s2;
+  const double a01 = a0 * a1;
+  num = fma(a2, fma(a1, q0, a0 * q1), a01 * q2);
+  den = fma(a2, a0 + a1, a01);
 }
 
 
@@ -753,8 +769,11 @@ __device__ __forceinline__ void rec_div2(const RecND& x, const RecND& y, double&
 
 // ================================================================= k_face ===
 // One thread per face of direction D (faces i = 0..n_D, left cell i-1).
+#ifndef XF_FACE_THREADS
+#define XF_FACE_THREADS 128
+#endif
 #ifndef XF_FACE_MIN_BLOCKS
-#define XF_FACE_MIN_BLOCKS 2
+#define XF_FACE_MIN_BLOCKS (256 / XF_FACE_THREADS)
 #endif
 // Convective face flux of Eq. 15 (Roe-averaged face state, PER projection,
 // LLF splitting of Eq. 14, reconstruction REC, back-projection) into Gout,
@@ -784,13 +803,16 @@ __device__ __forceinline__ void conv_flux(const Params& p, const double* __restr
 #pragma unroll
   for (int s = 0; s < NS; ++s) Yb[s] = fma(tL, QF(L::Y + s, 0), tR * QF(L::Y + s, 1));
   const TauPt tp = tau_of(p, Tb);
-  double hs[NS], Rb = 0.0, cpb = 0.0;
+  double hs[NS];
 #pragma unroll
-  for (int s = 0; s < NS; ++s) {
-    hs[s] = h_s_in(p, s, tp);
-    Rb = fma(Yb[s], p.r[s], Rb);
-    cpb = fma(Yb[s], cp_s(p, s, tp.tc), cpb);
-  }
+  for (int s = 0; s < NS; ++s) hs[s] = h_s_in(p, s, tp);
+  // R(Y) and c_p(Y, T) are linear in Y: their face values come from the two
+  // cells' mixture gas constants and c_p coefficients with the same weights
+  const double Rb = fma(tL, QF(L::RM, 0), tR * QF(L::RM, 1));
+  double Ab[5];
+#pragma unroll
+  for (int jj = 0; jj < 5; ++jj) Ab[jj] = fma(tL, QF(L::AC + jj, 0), tR * QF(L::AC + jj, 1));
+  const double cpb = fma(fma(fma(fma(Ab[4], tp.tc, Ab[3]), tp.tc, Ab[2]), tp.tc, Ab[1]), tp.tc, Ab[0]);
   const double cvb = cpb - Rb;
   // one division for Gamma = R/c_v and its inverse
   const double rRc = rcp_nr(Rb * cvb);
@@ -1106,8 +1128,11 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
     double work16 = 0.0;  // 16 sum_a tau_a u_a
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
+      // products that feed a sum are written as fused multiply-adds, here and
+      // below, so the batched kernel, which compiles this body too, gives the
+      // same bits
       const double tau = mu16 * t16[a];
-      Gout[1 + a] -= tau;
+      Gout[1 + a] = fma(-mu16, t16[a], Gout[1 + a]);
       work16 = fma(tau, FI0(L::UN + a), work16);
     }
     // species fluxes of Eq. 6 with the mixture correction: D_s = D for every
@@ -1135,16 +1160,16 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
     // h_s at the face temperature T_f = wi FI0(T)
     const TauPt tp = tau_pt(p, fma(FI0(L::T), wi * p.inv_span, p.tau0));
     double qd = 0.0;
-    double J[NS];
+    double Jn[NS];  // J_s / nrf
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-      J[s] = nrf * fma(Ds0[s], dY0[s], -Yf0[s] * corr0);
+      Jn[s] = fma(Ds0[s], dY0[s], -Yf0[s] * corr0);
       const double hs = h_s_in(p, s, tp);
-      qd = fma(hs, J[s], qd);
+      qd = fma(hs, nrf * Jn[s], qd);
     }
     Gout[IE] -= fma(FI0(L::KA) * wid, FD0(L::T), fma(work16, wi, -qd));
 #pragma unroll
-    for (int s = 0; s < NS - 1; ++s) Gout[IE + 1 + s] += J[s];
+    for (int s = 0; s < NS - 1; ++s) Gout[IE + 1 + s] = fma(nrf, Jn[s], Gout[IE + 1 + s]);
 #undef FI
 #undef FD
 #undef FI0
@@ -1158,7 +1183,7 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
 
 // Faces [f0, f1) of direction D in their (i fastest) order, f1 <= their count.
 template <int DIM, int NS, int D, int REC = 5>
-__global__ void __launch_bounds__(128, XF_FACE_MIN_BLOCKS)
+__global__ void __launch_bounds__(XF_FACE_THREADS, XF_FACE_MIN_BLOCKS)
 k_face(const __grid_constant__ Params p, const double* __restrict__ Q,
        double* __restrict__ Gf, uint32_t* __restrict__ flags, const double* __restrict__ dtp,
        long long f0, long long f1) {
@@ -1173,7 +1198,7 @@ k_face(const __grid_constant__ Params p, const double* __restrict__ Q,
 // fluxes to Fh: the tape that the reverse of the positivity blend reads
 // (xf_step_rk3_tape_flux) instead of recomputing them.
 template <int DIM, int NS, int D, int REC = 5>
-__global__ void __launch_bounds__(128, XF_FACE_MIN_BLOCKS)
+__global__ void __launch_bounds__(XF_FACE_THREADS, XF_FACE_MIN_BLOCKS)
 k_face_tape(const __grid_constant__ Params p, const double* __restrict__ Q,
             double* __restrict__ Gf, uint32_t* __restrict__ flags, const double* __restrict__ dtp,
             double* __restrict__ Fh) {
