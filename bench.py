@@ -152,6 +152,22 @@ def _cpu_baseline(cfg=2, steps=5, warmup=1):
             "spread": [min(rate), max(rate)]}
 
 
+def _cpu_baseline_as_reference_arm(args):
+    """The cpu_baseline leg, measured by running this script's reference arm
+    (``--impl reference``) in a process of its own, so that both legs time the
+    oracle in the same kind of process: one without torch or CUDA, whose
+    OpenMP runtime state differs from this one's."""
+    env = {k: v for k, v in os.environ.items()
+           if k not in ("RANK", "LOCAL_RANK", "WORLD_SIZE", "MASTER_ADDR", "MASTER_PORT")}
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--impl", "reference",
+                          "--steps", "5", "--warmup", "3", "--workload", args.workload],
+                         capture_output=True, text=True, env=env, check=True).stdout
+    line = json.loads(out.strip().splitlines()[-1])
+    cb = dict(line["cpu_baseline"])
+    cb["sample"] += "; run as this script's reference arm in a process of its own"
+    return cb
+
+
 def _cpu_single_core(cfg=2, steps=3):
     """The oracle on one host core (the kind of CPU figure GPU speed-ups are
     usually quoted against), on a smaller sample of the same workload."""
@@ -565,7 +581,7 @@ def run_ours(args):
         if ws == 1 and not args.no_cpu_baseline:
             from oracle import build as ob
             ob.build()
-            cpu = _cpu_baseline(cfg, steps=5, warmup=3)
+            cpu = _cpu_baseline_as_reference_arm(args)
             cpu["single_core"] = _cpu_single_core(cfg)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
