@@ -159,3 +159,25 @@ def test_full_ensemble_is_bitwise_identical_to_single_grid_steps():
         assert st == 0
         assert np.array_equal(Ug, Up), c.name
         assert np.array_equal(Tg, Tp), c.name
+
+
+def test_batch_with_periodic_instances_is_bitwise_single_grid():
+    """Periodic instances beside a shock-bubble one: the batched kernel
+    recomputes every ghost cell, the single-grid step copies the ghost layers
+    from their periodic, transmissive and symmetric images; the two agree bit
+    for bit."""
+    cs = [cases.smooth_periodic(2, (64, 32), 3, seed=4, amp=0.3),
+          cases.smooth_periodic(2, (48, 40), 4, seed=5, amp=0.3),
+          cases.smooth_periodic(2, (32, 32), 5, seed=6, amp=0.3)] + _instances(count=1, seed=9)
+    ins = _inputs(cs)
+    b = _batch(cs, ins)
+    for _ in range(3):
+        b.step(0.0)
+    got = _read(b, cs)
+    assert b.status() == 0
+    b.close()
+    for c, (U, T), (Ug, Tg) in zip(cs, ins, got):
+        Up, Tp, st = _plain(c, U, T, 3, 0.0)
+        assert st == 0
+        assert np.array_equal(Ug, Up), c.name
+        assert np.array_equal(Tg, Tp), c.name
