@@ -305,6 +305,12 @@ xf_status xf_probe_fp64(int64_t iters, int blocks_per_sm, double *tflops);
  * paper): y[i] = that reciprocal of x[i] and ref[i] = the correctly rounded
  * 1.0 / x[i], for device arrays of n doubles. Enqueued on `stream`. */
 xf_status xf_probe_rcp(const double *x, double *y, double *ref, int64_t n, void *stream);
+/* The exponential the primitive recovery uses for the transport fits
+ * (Tang's table-driven method; tooling, no counterpart in the paper):
+ * y[i] = that exp of x[i] and ref[i] = CUDA's exp(x[i]), for device arrays
+ * of n doubles. Enqueued on `stream`. XF_ERR_ARG for null or non-device
+ * arrays or n < 0. */
+xf_status xf_probe_exp(const double *x, double *y, double *ref, int64_t n, void *stream);
 
 /* ---- Batched form: many independent 2D instances (uneven grids, N = 2..5)
  * advanced together. Each RK stage is ONE persistent cooperative kernel that

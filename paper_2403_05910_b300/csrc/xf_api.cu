@@ -567,6 +567,15 @@ __global__ void k_probe_rcp(const double* __restrict__ x, double* __restrict__ y
   ref[i] = 1.0 / x[i];
 }
 
+// exp_t beside CUDA's exp, element by element
+__global__ void k_probe_exp(const double* __restrict__ x, double* __restrict__ y,
+                            double* __restrict__ ref, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  y[i] = xf::exp_t(x[i]);
+  ref[i] = exp(x[i]);
+}
+
 __global__ void k_probe_fp64(double* out, long long iters, double a) {
   double x0 = threadIdx.x * 1e-3, x1 = x0 + 1, x2 = x0 + 2, x3 = x0 + 3, x4 = x0 + 4,
          x5 = x0 + 5, x6 = x0 + 6, x7 = x0 + 7;
@@ -1210,6 +1219,15 @@ xf_status xf_probe_rcp(const double* x, double* y, double* ref, int64_t n, void*
   if (n == 0) return XF_OK;
   if (!is_device_ptr(x) || !is_device_ptr(y) || !is_device_ptr(ref)) return XF_ERR_ARG;
   k_probe_rcp<<<blocks(n, 256), 256, 0, (cudaStream_t)stream>>>(x, y, ref, n);
+  XF_CUDA(cudaGetLastError());
+  return XF_OK;
+}
+
+xf_status xf_probe_exp(const double* x, double* y, double* ref, int64_t n, void* stream) {
+  if (!x || !y || !ref || n < 0) return XF_ERR_ARG;
+  if (n == 0) return XF_OK;
+  if (!is_device_ptr(x) || !is_device_ptr(y) || !is_device_ptr(ref)) return XF_ERR_ARG;
+  k_probe_exp<<<blocks(n, 256), 256, 0, (cudaStream_t)stream>>>(x, y, ref, n);
   XF_CUDA(cudaGetLastError());
   return XF_OK;
 }

@@ -116,6 +116,61 @@ __device__ __forceinline__ double rcp_nr(double x) {
   return fma(y, e, y);
 }
 
+// 2^(j/64) for j = 0..63, each the double nearest the exact value (computed in
+// exact decimal arithmetic and checked to lie within half an ulp of it).
+static __device__ const double kExp2J64[64] = {
+    0x1.0000000000000p+0, 0x1.02c9a3e778061p+0, 0x1.059b0d3158574p+0,
+    0x1.0874518759bc8p+0, 0x1.0b5586cf9890fp+0, 0x1.0e3ec32d3d1a2p+0,
+    0x1.11301d0125b51p+0, 0x1.1429aaea92de0p+0, 0x1.172b83c7d517bp+0,
+    0x1.1a35beb6fcb75p+0, 0x1.1d4873168b9aap+0, 0x1.2063b88628cd6p+0,
+    0x1.2387a6e756238p+0, 0x1.26b4565e27cddp+0, 0x1.29e9df51fdee1p+0,
+    0x1.2d285a6e4030bp+0, 0x1.306fe0a31b715p+0, 0x1.33c08b26416ffp+0,
+    0x1.371a7373aa9cbp+0, 0x1.3a7db34e59ff7p+0, 0x1.3dea64c123422p+0,
+    0x1.4160a21f72e2ap+0, 0x1.44e086061892dp+0, 0x1.486a2b5c13cd0p+0,
+    0x1.4bfdad5362a27p+0, 0x1.4f9b2769d2ca7p+0, 0x1.5342b569d4f82p+0,
+    0x1.56f4736b527dap+0, 0x1.5ab07dd485429p+0, 0x1.5e76f15ad2148p+0,
+    0x1.6247eb03a5585p+0, 0x1.6623882552225p+0, 0x1.6a09e667f3bcdp+0,
+    0x1.6dfb23c651a2fp+0, 0x1.71f75e8ec5f74p+0, 0x1.75feb564267c9p+0,
+    0x1.7a11473eb0187p+0, 0x1.7e2f336cf4e62p+0, 0x1.82589994cce13p+0,
+    0x1.868d99b4492edp+0, 0x1.8ace5422aa0dbp+0, 0x1.8f1ae99157736p+0,
+    0x1.93737b0cdc5e5p+0, 0x1.97d829fde4e50p+0, 0x1.9c49182a3f090p+0,
+    0x1.a0c667b5de565p+0, 0x1.a5503b23e255dp+0, 0x1.a9e6b5579fdbfp+0,
+    0x1.ae89f995ad3adp+0, 0x1.b33a2b84f15fbp+0, 0x1.b7f76f2fb5e47p+0,
+    0x1.bcc1e904bc1d2p+0, 0x1.c199bdd85529cp+0, 0x1.c67f12e57d14bp+0,
+    0x1.cb720dcef9069p+0, 0x1.d072d4a07897cp+0, 0x1.d5818dcfba487p+0,
+    0x1.da9e603db3285p+0, 0x1.dfc97337b9b5fp+0, 0x1.e502ee78b3ff6p+0,
+    0x1.ea4afa2a490dap+0, 0x1.efa1bee615a27p+0, 0x1.f50765b6e4540p+0,
+    0x1.fa7c1819e90d8p+0,
+};
+
+// exp(x) for the transport fits by P. T. P. Tang's table-driven method
+// ("Table-driven implementation of the exponential function in IEEE
+// floating-point arithmetic", ACM Trans. Math. Software 15, 1989):
+// x = (64 m + j) ln2/64 + r with |r| <= ln2/128, and
+// exp(x) = 2^m 2^(j/64) e^r, e^r = 1 + r + r^2 (1/2 + r/6 + r^2/24 + r^3/120)
+// (the next Taylor term is below 4e-17 there). n = 64 m + j is rounded with
+// the 1.5 2^52 shift, r is formed with ln2/64 split into a leading double and
+// its remainder, 2^(j/64) comes from the table and 2^m is added to the
+// exponent on the integer pipe: 10 FP64 instructions. Within about one ulp
+// of exp (xf_probe_exp). |x| > 700 (outside the fits' range) takes exp.
+__device__ __forceinline__ double exp_t(double x) {
+  if (!(fabs(x) <= 700.0)) return exp(x);
+  constexpr double k64ln2 = 0x1.71547652b82fep+6;   // 64 / ln 2
+  constexpr double kL1 = 0x1.62e42fefa39efp-7;      // ln 2 / 64, leading part
+  constexpr double kL2 = 0x1.abc9e3b39803fp-62;     // ln 2 / 64 - kL1
+  constexpr double kShift = 6755399441055744.0;     // 1.5 * 2^52
+  const double t = fma(x, k64ln2, kShift);
+  const long long n = __double_as_longlong(t) - __double_as_longlong(kShift);
+  const double kd = t - kShift;
+  const double r = fma(kd, -kL2, fma(kd, -kL1, x));
+  const double q = fma(fma(fma(1.0 / 120.0, r, 1.0 / 24.0), r, 1.0 / 6.0), r, 0.5);
+  const double er1 = fma(r * r, q, r);               // e^r - 1
+  const double T = __ldg(kExp2J64 + (n & 63));
+  const double e = fma(T, er1, T);
+  return __longlong_as_double(__double_as_longlong(e) +
+                              (long long)((unsigned long long)(n >> 6) << 52));
+}
+
 // max of two non-negative doubles through their ordered bit patterns (integer
 // pipe; the FP64 pipe is the scarce unit)
 __device__ __forceinline__ double pmax(double a, double b) {
@@ -297,8 +352,8 @@ __device__ __forceinline__ void prim_cell(const Params& p, long long t, const do
       for (int s = 0; s < NS; ++s) {
         const double lm = fma(fma(fma(p.lnmu[s][3], lnT, p.lnmu[s][2]), lnT, p.lnmu[s][1]), lnT, p.lnmu[s][0]);
         const double lk = fma(fma(fma(p.lnka[s][3], lnT, p.lnka[s][2]), lnT, p.lnka[s][1]), lnT, p.lnka[s][0]);
-        smu[s] = exp(0.5 * lm);
-        ska[s] = exp(0.5 * lk);
+        smu[s] = exp_t(0.5 * lm);
+        ska[s] = exp_t(0.5 * lk);
         X[s] = Y[s] * p.invW[s];
         xs += X[s];
       }
@@ -405,7 +460,7 @@ __device__ __forceinline__ void prim_cell(const Params& p, long long t, const do
           for (int tt = s + 1; tt < NS; ++tt) {
             const double* b = p.dbin[s][tt];
             const double l = fma(fma(fma(b[3], lnT, b[2]), lnT, b[1]), lnT, b[0]);
-            const double iD = exp(-l);
+            const double iD = exp_t(-l);
             den[s] = fma(Xt[tt], iD, den[s]);
             den[tt] = fma(Xt[s], iD, den[tt]);
           }
