@@ -35,7 +35,7 @@ __device__ __forceinline__ void w5_fwd(double f0, double f1, double f2, double f
   r.a = f1 - f0; r.b = f2 - f1; r.c = f3 - f2; r.d = f4 - f3;
   r.A0 = fma(-1.375, r.b, r.a); r.B1 = fma(-0.625, r.c, r.b); r.D2 = fma(-1.375, r.c, r.d);
   const double cc = r.c * r.c;
-  r.s0 = fma((16.0 * kWc0) * r.A0, r.A0, fma((9.75 * kWc0) * r.b, r.b, e12c[0]));
+  r.s0 = fma(r.A0, r.A0, fma((9.75 * kWc0) * r.b, r.b, e12c[0]));  // 16 c_0 = 1
   r.s1 = fma((16.0 * kWc1) * r.B1, r.B1, fma(9.75 * kWc1, cc, e12c[1]));
   r.s2 = fma((16.0 * kWc2) * r.D2, r.D2, fma(9.75 * kWc2, cc, e12c[2]));
   r.p12 = r.s1 * r.s2; r.p02 = r.s0 * r.s2; r.p01 = r.s0 * r.s1;

@@ -638,17 +638,20 @@ k_grad(const __grid_constant__ Params p, double* __restrict__ Q) {
 // the weights unchanged -- and the nonlinear weights d_k/(eps + b_k)^2 are
 // scaled by prod_j (eps + b_j)^2, so no division is needed until the end.
 // The linear weights d = (0.1, 0.6, 0.3) are folded into the indicators:
-// with s_k scaled by c_k = (d_i d_j / d_k)^(1/4) ({i, j, k} = {0, 1, 2}),
-// (s_i s_j)^2 already carries the factor d_k. The candidates enter as q_k - f2.
+// with s_k scaled by c_k proportional to (d_i d_j / d_k)^(1/4)
+// ({i, j, k} = {0, 1, 2}), (s_i s_j)^2 already carries the factor d_k. The
+// common factor is chosen so that c_0 = 1/16: then c_1 = 1/(16 sqrt 6),
+// c_2 = 1/(16 sqrt 3), and the leading square of s_0 has coefficient 1.
+// The candidates enter as q_k - f2.
 // Each 12 b_k is a positive definite quadratic form in two differences,
 // evaluated as its LDL^T sum of squares (exact in these rationals):
 //   12 b_0 = 16 a^2 - 44 ab + 40 b^2 = 16 (a - 11/8 b)^2 + 39/4 b^2
 //   12 b_1 = 16 b^2 - 20 bc + 16 c^2 = 16 (b - 5/8 c)^2 + 39/4 c^2
 //   12 b_2 = 40 c^2 - 44 cd + 16 d^2 = 16 (d - 11/8 c)^2 + 39/4 c^2
 // (b_1 and b_2 share c^2).
-constexpr double kWc0 = 1.158292185288269;   // (0.6 * 0.3 / 0.1)^(1/4)
-constexpr double kWc1 = 0.4728708045015879;  // (0.1 * 0.3 / 0.6)^(1/4)
-constexpr double kWc2 = 0.668740304976422;   // (0.1 * 0.6 / 0.3)^(1/4)
+constexpr double kWc0 = 0.0625;               // 1/16
+constexpr double kWc1 = 0.02551551815399144;  // 1/(16 sqrt 6)
+constexpr double kWc2 = 0.03608439182435161;  // 1/(16 sqrt 3)
 
 // e12c[k] = 12 eps c_k (per face)
 __device__ __forceinline__ void weno5_nd(double f0, double f1, double f2, double f3, double f4,
@@ -656,7 +659,7 @@ __device__ __forceinline__ void weno5_nd(double f0, double f1, double f2, double
   const double a = f1 - f0, b = f2 - f1, c = f3 - f2, d = f4 - f3;
   const double A0 = fma(-1.375, b, a), B1 = fma(-0.625, c, b), D2 = fma(-1.375, c, d);
   const double cc = c * c;
-  const double s0 = fma((16.0 * kWc0) * A0, A0, fma((9.75 * kWc0) * b, b, e12c[0]));
+  const double s0 = fma(A0, A0, fma((9.75 * kWc0) * b, b, e12c[0]));  // 16 c_0 = 1
   const double s1 = fma((16.0 * kWc1) * B1, B1, fma(9.75 * kWc1, cc, e12c[1]));
   const double s2 = fma((16.0 * kWc2) * D2, D2, fma(9.75 * kWc2, cc, e12c[2]));
   // 6 (q_k - f2): 5b - 2a = 9/4 b - 2 A0, 2c + b, 4c - d; the factor 6 goes
@@ -900,12 +903,13 @@ __device__ __forceinline__ void conv_flux(const Params& p, const double* __restr
   //      The 1/2 of Eq. 14 and the 1/(2c^2) of the acoustic rows are folded
   //      into per-face coefficients.
   const double phiN = phi[NS - 1];
+  const double gE = Gam * hic2;
   double gm[DIM], dphi[NS > 1 ? NS - 1 : 1], gs[NS > 1 ? NS - 1 : 1];
 #pragma unroll
-  for (int a = 0; a < DIM; ++a) gm[a] = -Gam * ub[a] * hic2;
+  for (int a = 0; a < DIM; ++a) gm[a] = -ub[a] * gE;
 #pragma unroll
   for (int s = 0; s < NS - 1; ++s) { dphi[s] = phi[s] - phiN; gs[s] = dphi[s] * hic2; }
-  const double gr = phiN * hic2, gE = Gam * hic2;
+  const double gr = phiN * hic2;
   double rho_m[SW], p_m[SW], hun[SW], gUh[SW];
   double am = 0.0, ap = 0.0, a0 = 0.0;
 #pragma unroll
@@ -972,7 +976,7 @@ __device__ __forceinline__ void conv_flux(const Params& p, const double* __restr
     // from one product per cell: with lE = Gam/(2c^2) and hl0 = -Gam u_n/(4c^2),
     // the u -+ c rows take p_m (u_m/2 lE + hl0 -+ c/(4c^2)) and the entropy row
     // exactly -2 p_m (u_m/2 lE + hl0)
-    const double lE = Gam * hic2, hl0 = -0.5 * Gam * un * hic2, dl = 0.5 * chc;
+    const double lE = gE, hl0 = (-0.5 * un) * gE, dl = 0.5 * chc;
     double pV[SW];
 #pragma unroll
     for (int m = 0; m < SW; ++m) pV[m] = p_m[m] * fma(hun[m], lE, hl0);
@@ -1163,9 +1167,6 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
     const double wid = wi * wd;
 #define FI0(field) (fma(9.0, QF(field, 0) + QF(field, 1), -(QF(field, -1) + QF(field, 2))))
 #define FD0(field) (fma(15.0, QF(field, 1) - QF(field, 0), -(QF(field, 2) - QF(field, -1))))
-#define FI(field) (FI0(field) * wi)
-#define FD(field) (FD0(field) * wd)
-    const double rf = FI(L::U);
     // tau_Da (Eq. 3) = (mu/16) t16_a with t16_a = 16 (du_D/dx_a + du_a/dx_D)
     // for a != D and t16_D = 16 (4/3 du_D/dx_D - 2/3 sum_{a != D} du_a/dx_a);
     // FI0 of the nodal derivatives is 16 times their face value, FD0 of u is
@@ -1173,60 +1174,64 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
     const double mu16 = FI0(L::MU) * (wi * wi);
     const double rq = 16.0 * wd;
     double t16[DIM], tr = 0.0;
+    bool first = true;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
       if (a == D) continue;
       t16[a] = fma(rq, FD0(L::UN + a), FI0(L::GU + D * DIM + a));
-      tr += FI0(L::GU + a * DIM + a);
+      tr = first ? FI0(L::GU + a * DIM + a) : tr + FI0(L::GU + a * DIM + a);
+      first = false;
     }
     t16[D] = fma((4.0 / 3.0) * rq, FD0(L::UN + D), (-2.0 / 3.0) * tr);
-    double work16 = 0.0;  // 16 sum_a tau_a u_a
+    // 256 sum_a tau_a u_a / mu16 = sum_a t16_a FI0(u_a); products that feed
+    // a sum are written as fused multiply-adds, here and below, so the
+    // batched kernel, which compiles this body too, gives the same bits
+    double W = t16[0] * FI0(L::UN);
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
-      // products that feed a sum are written as fused multiply-adds, here and
-      // below, so the batched kernel, which compiles this body too, gives the
-      // same bits
-      const double tau = mu16 * t16[a];
       Gout[1 + a] = fma(-mu16, t16[a], Gout[1 + a]);
-      work16 = fma(tau, FI0(L::UN + a), work16);
+      if (a > 0) W = fma(t16[a], FI0(L::UN + a), W);
     }
-    // species fluxes of Eq. 6 with the mixture correction: D_s = D for every
-    // species (diffusion = 0) or the face values of the cells' D_sm. With
-    // dY0 = 12 dx dY/dn, Yf0 = 16 Y_f, Ds0 = 16 D_s:
-    // J_s = -rho_f (D_s dY_s - Y_s corr) = nrf (Ds0 dY0_s - Yf0_s corr0),
-    // nrf = -rho_f wid, corr0 = wi sum_t Ds0_t dY0_t
-    double dY0[NS], Yf0[NS], Ds0[NS], corr0;
+    // species fluxes of Eq. 6 with the mixture correction, J_s = nJ Jn_s.
+    // With dY0 = 12 dx dY/dn, Yf0 = 16 Y_f, Ds0 = 16 D_s and
+    // nrf = -rho_f wi wd: D_s = the face values of the cells' D_sm
+    // (diffusion = 1): Jn_s = Ds0 dY0_s - Yf0_s wi sum_t Ds0_t dY0_t,
+    // nJ = nrf; one D for every species (diffusion = 0):
+    // Jn_s = dY0_s - Yf0_s wi sum_t dY0_t, nJ = nrf Ds0
+    const double nrf = FI0(L::U) * (-wi * wid);
+    double Jn[NS], nJ;
     if (p.diffusion == 1) {
+      double dY0[NS], Yf0[NS], Ds0[NS];
       double c = 0.0;
 #pragma unroll
       for (int s = 0; s < NS; ++s) {
         dY0[s] = FD0(L::Y + s); Yf0[s] = FI0(L::Y + s); Ds0[s] = FI0(L::DS + s);
         c = fma(Ds0[s], dY0[s], c);
       }
-      corr0 = c * wi;
-    } else {
-      const double Df0 = FI0(L::DF);
-      double sdY = 0.0;
+      const double corr0 = c * wi;
 #pragma unroll
-      for (int s = 0; s < NS; ++s) { dY0[s] = FD0(L::Y + s); Yf0[s] = FI0(L::Y + s); sdY += dY0[s]; Ds0[s] = Df0; }
-      corr0 = (Df0 * wi) * sdY;
+      for (int s = 0; s < NS; ++s) Jn[s] = fma(Ds0[s], dY0[s], -Yf0[s] * corr0);
+      nJ = nrf;
+    } else {
+      double dY0[NS], Yf0[NS];
+#pragma unroll
+      for (int s = 0; s < NS; ++s) { dY0[s] = FD0(L::Y + s); Yf0[s] = FI0(L::Y + s); }
+      double sdY = dY0[0];
+#pragma unroll
+      for (int s = 1; s < NS; ++s) sdY += dY0[s];
+      const double corr = wi * sdY;
+#pragma unroll
+      for (int s = 0; s < NS; ++s) Jn[s] = fma(-corr, Yf0[s], dY0[s]);
+      nJ = nrf * FI0(L::DF);
     }
-    const double nrf = -rf * wid;
-    // h_s at the face temperature T_f = wi FI0(T)
+    // h_s at the face temperature T_f = wi FI0(T); qd = sum_s h_s J_s / nJ
     const TauPt tp = tau_pt(p, fma(FI0(L::T), wi * p.inv_span, p.tau0));
     double qd = 0.0;
-    double Jn[NS];  // J_s / nrf
 #pragma unroll
-    for (int s = 0; s < NS; ++s) {
-      Jn[s] = fma(Ds0[s], dY0[s], -Yf0[s] * corr0);
-      const double hs = h_s_in(p, s, tp);
-      qd = fma(hs, nrf * Jn[s], qd);
-    }
-    Gout[IE] -= fma(FI0(L::KA) * wid, FD0(L::T), fma(work16, wi, -qd));
+    for (int s = 0; s < NS; ++s) qd = fma(h_s_in(p, s, tp), Jn[s], qd);
+    Gout[IE] -= fma(FI0(L::KA) * wid, FD0(L::T), fma(mu16 * wi, W, -nJ * qd));
 #pragma unroll
-    for (int s = 0; s < NS - 1; ++s) Gout[IE + 1 + s] = fma(nrf, Jn[s], Gout[IE + 1 + s]);
-#undef FI
-#undef FD
+    for (int s = 0; s < NS - 1; ++s) Gout[IE + 1 + s] = fma(nJ, Jn[s], Gout[IE + 1 + s]);
 #undef FI0
 #undef FD0
   }
