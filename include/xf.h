@@ -366,8 +366,9 @@ xf_status xf_barrier_probe(int64_t timeout_cycles, int extra_arrivals, uint32_t 
  * hands all device memory to its own pool or caching allocator and forbids
  * other cudaMalloc calls, or a latency-critical loop where an allocation would
  * synchronise the device. It computes dUdt = L(U) exactly like xf_rhs, but
- * without a handle: its scratch (padded per-cell fields, face fluxes,
- * temperature warm start, status word) is one fixed array in the library's
+ * without a handle: its scratch (a device copy of the solver parameters,
+ * padded per-cell fields, face fluxes, temperature warm start, status word)
+ * is one fixed array in the library's
  * device memory, xf_rhs_static_capacity_bytes() bytes (32 MiB) per GPU, held
  * by every GPU that loads the library until the process exits. It calls no
  * cudaMalloc, cudaFree or other allocating routine.

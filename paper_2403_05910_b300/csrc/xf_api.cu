@@ -262,6 +262,7 @@ bool is_device_ptr(const void* ptr) {
 
 struct xf_handle {
   xf::Params p;
+  xf::Params* pdev = nullptr;  // p in device memory (p.dev)
   Table tab;
   int tcur = 0;  // which temperature buffer holds the latest warm start
   long long nf[3] = {0, 0, 0};
@@ -397,6 +398,10 @@ xf_status fill_params(const xf_grid* g, const xf_thermo* th, const xf_opts* o, x
   }
   for (int k = 0; k < 4; ++k) p->wenoe4[k] = 0.25 * p->wenoe[k];
   p->weno = o->weno;
+  for (int j = 0; j < 14; ++j) p->kface[j] = xf::kFaceCoef[j];
+  p->kface[14] = o->weno == 7 ? xf::rec_scale<7>() : xf::rec_scale<5>();
+  p->kface[15] = 0.0;
+  p->dev = nullptr;  // set by the owner of the struct
   p->newton_rtol = o->newton_rtol;
   p->newton_max = o->newton_max;
   p->viscous = o->viscous ? 1 : 0;
@@ -681,7 +686,8 @@ xf_status xf_create(const xf_grid* grid, const xf_thermo* thermo, const xf_opts*
     return true;
   };
   const size_t st_bytes = sizeof(double) * (size_t)p.nv * p.cells;
-  bool ok = alloc((void**)&h->U, st_bytes) && alloc((void**)&h->Us, st_bytes) &&
+  bool ok = alloc((void**)&h->pdev, sizeof(xf::Params)) &&
+            alloc((void**)&h->U, st_bytes) && alloc((void**)&h->Us, st_bytes) &&
             alloc((void**)&h->T[0], sizeof(double) * p.cells) &&
             alloc((void**)&h->T[1], sizeof(double) * p.cells) &&
             alloc((void**)&h->Q, sizeof(double) * nq_of(tab, p) * p.pcells) &&
@@ -697,12 +703,14 @@ xf_status xf_create(const xf_grid* grid, const xf_thermo* thermo, const xf_opts*
     g_err = "cudaMalloc failed";
     return XF_ERR_OOM;
   }
-  if (cudaMemset(h->red, 0, 2 * sizeof(unsigned long long)) != cudaSuccess ||
+  h->p.dev = h->pdev;
+  if (cudaMemcpy(h->pdev, &h->p, sizeof(xf::Params), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(h->red, 0, 2 * sizeof(unsigned long long)) != cudaSuccess ||
       cudaMemset(h->flags, 0, sizeof(uint32_t)) != cudaSuccess ||
       cudaMemset(h->dt, 0, sizeof(double)) != cudaSuccess ||
       cudaMemset(h->Q, 0, sizeof(double) * nq_of(tab, p) * p.pcells) != cudaSuccess) {
     xf_destroy(h);
-    g_err = "cudaMemset failed";
+    g_err = "cudaMemcpy or cudaMemset failed";
     return XF_ERR_CUDA;
   }
   k_fill<<<blocks(p.cells, 256), 256>>>(h->T[0], p.cells, 300.0);
@@ -717,6 +725,7 @@ xf_status xf_create(const xf_grid* grid, const xf_thermo* thermo, const xf_opts*
 
 void xf_destroy(xf_handle* h) {
   if (!h) return;
+  cudaFree(h->pdev);
   cudaFree(h->U);
   cudaFree(h->Us);
   cudaFree(h->T[0]);
@@ -1329,9 +1338,11 @@ xf_status xf_rhs_static(const xf_grid* grid, const xf_thermo* thermo, const xf_o
     g_err = "xf_rhs_static: U, dUdt and T_guess must be device pointers";
     return XF_ERR_ARG;
   }
-  // scratch plan (in doubles): Q | G_x | G_y | G_z | T_in | T_out | dt | red[2] | flags
+  // scratch plan (in doubles): Params | Q | G_x | G_y | G_z | T_in | T_out | dt | red[2] |
+  // flags, the Params slot rounded up to 256 bytes
+  constexpr size_t kParamSlot = (sizeof(xf::Params) + 255) / 256 * 32;
   long long nf[3] = {0, 0, 0};
-  size_t need = nq_of(tab, p) * p.pcells;
+  size_t need = kParamSlot + nq_of(tab, p) * p.pcells;
   for (int d = 0; d < p.dim; ++d) {
     nf[d] = (long long)(p.n[0] + (d == 0)) * (p.n[1] + (d == 1)) * (p.n[2] + (d == 2));
     need += (size_t)p.nv * nf[d];
@@ -1350,7 +1361,8 @@ xf_status xf_rhs_static(const xf_grid* grid, const xf_thermo* thermo, const xf_o
   st = static_scratch(&base);
   if (st != XF_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
-  double* Q = base;
+  p.dev = reinterpret_cast<const xf::Params*>(base);
+  double* Q = base + kParamSlot;
   double* cur = Q + nq_of(tab, p) * p.pcells;
   double* G[3] = {nullptr, nullptr, nullptr};
   for (int d = 0; d < p.dim; ++d) {
@@ -1362,7 +1374,9 @@ xf_status xf_rhs_static(const xf_grid* grid, const xf_thermo* thermo, const xf_o
   double* dt = Tout + p.cells;
   unsigned long long* red = reinterpret_cast<unsigned long long*>(dt + 1);
   uint32_t* flags = reinterpret_cast<uint32_t*>(dt + 3);
-  // the array keeps the previous call's contents: zero the accumulators
+  // the parameters' device copy (from pageable memory: staged before the call
+  // returns); the array keeps the previous call's contents: zero the accumulators
+  XF_CUDA(cudaMemcpyAsync(base, &p, sizeof(xf::Params), cudaMemcpyHostToDevice, s));
   XF_CUDA(cudaMemsetAsync(red, 0, 2 * sizeof(unsigned long long), s));
   XF_CUDA(cudaMemsetAsync(flags, 0, sizeof(uint32_t), s));
   if (T_guess) {

@@ -319,6 +319,7 @@ xf_status configure(xf_batch* b, int k) {
       I.fitems[D] = (long long)nf0 * nf1;
     }
     b->pre_face[i + 1] = b->pre_face[i] + I.fitems[0] + I.fitems[1];
+    I.p.dev = &b->dinst[i].p;  // the instance's parameters in the device array
   }
   XB_CUDA(cudaMemcpy(b->dinst, b->hinst.data(), sizeof(BInst) * b->n, cudaMemcpyHostToDevice));
   XB_CUDA(cudaMemcpy(b->dpre + 2 * (b->n + 1), b->pre_face.data(), sizeof(long long) * (b->n + 1),

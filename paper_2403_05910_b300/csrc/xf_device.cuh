@@ -60,11 +60,22 @@ struct Params {
                      // reconstructions are homogeneous of degree one when eps
                      // scales with the square of the data, exactly so for a
                      // power-of-two factor)
+  // the face kernel's fixed coefficients (kFaceCoef, then the field pair's
+  // division scale rec_scale), read through dev like the run constants above
+  double kface[16];
   int viscous, convective, newton_max;
   int weno;          // 5: WENO5-JS, 6: WENO-CU6
   int positivity;    // positivity-preserving blend of the convective flux (Eq. 17-20)
   double pos_eps;
   double hmin2_over_2dim;
+  // This struct's copy in device memory, set by its owner (a solver handle, a
+  // batch instance, the static scratch) before the first face launch. The
+  // face kernel reads its FP64 coefficients (kface, wenoe, wenoe4, r, rh,
+  // rhoff) from there: an FP64 instruction that takes a kernel parameter or a
+  // literal as an operand issues at about 84 % of the rate of one with
+  // register operands on this GPU, and values loaded from memory land in
+  // registers.
+  const Params* dev;
 };
 
 // Number of per-cell fields of Lay<dim, ns> (without the D_sm fields), for
@@ -113,6 +124,16 @@ __device__ __forceinline__ double rcp_nr(double x) {
   double e = fma(-x, y, 1.0);
   y = fma(y, e, y);
   e = fma(-x, y, 1.0);
+  return fma(y, e, y);
+}
+
+// rcp_nr with the constant 1 of its iteration passed in a register
+__device__ __forceinline__ double rcp_nr1(double x, double one) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  double e = fma(-x, y, one);
+  y = fma(y, e, y);
+  e = fma(-x, y, one);
   return fma(y, e, y);
 }
 
@@ -231,6 +252,17 @@ __device__ __forceinline__ double h_s_in(const Params& p, int s, const TauPt& t)
   const double* a = p.rh[s];
   const double poly = fma(fma(fma(fma(a[4], t.tc, a[3]), t.tc, a[2]), t.tc, a[1]), t.tc, a[0]);
   const double h = fma(poly, t.tc, p.rhoff[s]);
+  return t.in ? h : fma(cp_s(p, s, t.tc), t.ext, h);
+}
+
+// h_s_in with the coefficients read from the device copy of the parameters
+// (register operands; the same arithmetic)
+__device__ __forceinline__ double h_s_dev(const Params& p, int s, const TauPt& t) {
+  const double* a = p.dev->rh[s];
+  const double poly = fma(fma(fma(fma(__ldcg(a + 4), t.tc, __ldcg(a + 3)), t.tc, __ldcg(a + 2)),
+                              t.tc, __ldcg(a + 1)),
+                          t.tc, __ldcg(a + 0));
+  const double h = fma(poly, t.tc, __ldcg(p.dev->rhoff + s));
   return t.in ? h : fma(cp_s(p, s, t.tc), t.ext, h);
 }
 
@@ -653,20 +685,28 @@ constexpr double kWc0 = 0.0625;               // 1/16
 constexpr double kWc1 = 0.02551551815399144;  // 1/(16 sqrt 6)
 constexpr double kWc2 = 0.03608439182435161;  // 1/(16 sqrt 3)
 
-// e12c[k] = 12 eps c_k (per face)
+// The face kernel's fixed coefficients, in the order Params::kface holds
+// them: the WENO5 indicators' and candidates' (0-10, weno5_nd), the face
+// stencil's 9 and 15 (11, 12, face_one) and the Newton-Raphson 1 (13).
+constexpr double kFaceCoef[14] = {-1.375, -0.625, 9.75 * kWc0, 16.0 * kWc1, 9.75 * kWc1,
+                                  16.0 * kWc2, 9.75 * kWc2, -2.0, 2.25, 2.0, 4.0,
+                                  9.0, 15.0, 1.0};
+
+// K = kface in registers, E = {12 eps c_k} in device memory (per call)
 __device__ __forceinline__ void weno5_nd(double f0, double f1, double f2, double f3, double f4,
-                                         const double* e12c, double& num, double& den) {
+                                         const double* K, const double* E, double& num,
+                                         double& den) {
   const double a = f1 - f0, b = f2 - f1, c = f3 - f2, d = f4 - f3;
-  const double A0 = fma(-1.375, b, a), B1 = fma(-0.625, c, b), D2 = fma(-1.375, c, d);
+  const double A0 = fma(K[0], b, a), B1 = fma(K[1], c, b), D2 = fma(K[0], c, d);
   const double cc = c * c;
-  const double s0 = fma(A0, A0, fma((9.75 * kWc0) * b, b, e12c[0]));  // 16 c_0 = 1
-  const double s1 = fma((16.0 * kWc1) * B1, B1, fma(9.75 * kWc1, cc, e12c[1]));
-  const double s2 = fma((16.0 * kWc2) * D2, D2, fma(9.75 * kWc2, cc, e12c[2]));
+  const double s0 = fma(A0, A0, fma(K[2] * b, b, __ldcg(E + 0)));  // 16 c_0 = 1
+  const double s1 = fma(K[3] * B1, B1, fma(K[4], cc, __ldcg(E + 1)));
+  const double s2 = fma(K[5] * D2, D2, fma(K[6], cc, __ldcg(E + 2)));
   // 6 (q_k - f2): 5b - 2a = 9/4 b - 2 A0, 2c + b, 4c - d; the factor 6 goes
   // to the denominator of the field pair (rec_scale)
-  const double q0 = fma(-2.0, A0, 2.25 * b);
-  const double q1 = fma(2.0, c, b);
-  const double q2 = fma(4.0, c, -d);
+  const double q0 = fma(K[7], A0, K[8] * b);
+  const double q1 = fma(K[9], c, b);
+  const double q2 = fma(K[10], c, -d);
   // weights w_0 = (s_1 s_2)^2, w_1 = (s_0 s_2)^2, w_2 = (s_0 s_1)^2 with
   // a_k = s_k^2 grouped as num = a_2 (a_1 q_0 + a_0 q_1) + a_0 a_1 q_2 and
   // den = a_2 (a_0 + a_1) + a_0 a_1
@@ -785,12 +825,15 @@ __device__ __forceinline__ void weno7_nd(double f0, double f1, double f2, double
 // and the mirrored one of w^- about the face, as b + n/d with the division
 // left to the caller (two fields share one). Stencils: w^+ from i-2..i+2
 // (i-3..i+3 for WENO7, i-2..i+3 for CU6), w^- mirrored from i+3 (i+4).
-// e4 = {12 eps c_0, 12 eps c_1, 12 eps c_2, 12 eps} for 5 and 6, {240 eps c_k} for 7.
+// e4 = {12 eps c_0, 12 eps c_1, 12 eps c_2, 12 eps} for 5 and 6, {240 eps c_k}
+// for 7; WENO5 takes its coefficients K (registers) and its eps E (device
+// memory) instead.
 struct RecND {
   double b, n, d;
 };
 template <int REC>
-__device__ __forceinline__ RecND rec_nd(const double* wp, const double* wm, const double* e4) {
+__device__ __forceinline__ RecND rec_nd(const double* wp, const double* wm, const double* e4,
+                                        const double* K, const double* E) {
   double np, dp, nm, dm, b;
   if constexpr (REC == 7) {
     weno7_nd(wp[0], wp[1], wp[2], wp[3], wp[4], wp[5], wp[6], e4, np, dp);
@@ -801,8 +844,8 @@ __device__ __forceinline__ RecND rec_nd(const double* wp, const double* wm, cons
     cu6_nd(wm[5], wm[4], wm[3], wm[2], wm[1], wm[0], e4[3], nm, dm);
     b = wp[2] + wm[3];
   } else {
-    weno5_nd(wp[0], wp[1], wp[2], wp[3], wp[4], e4, np, dp);
-    weno5_nd(wm[5], wm[4], wm[3], wm[2], wm[1], e4, nm, dm);
+    weno5_nd(wp[0], wp[1], wp[2], wp[3], wp[4], K, E, np, dp);
+    weno5_nd(wm[5], wm[4], wm[3], wm[2], wm[1], K, E, nm, dm);
     b = wp[2] + wm[3];
   }
   return RecND{b, fma(np, dm, nm * dp), dp * dm};
@@ -811,16 +854,18 @@ __device__ __forceinline__ RecND rec_nd(const double* wp, const double* wm, cons
 // out at the division
 template <int REC>
 __host__ __device__ constexpr double rec_scale() { return REC == 7 ? 1.0 : 6.0; }
+// K[13] = 1, K[14] = rec_scale<REC>() (registers)
 template <int REC>
-__device__ __forceinline__ double rec_div1(const RecND& x) {
-  return fma(x.n, rcp_nr(rec_scale<REC>() * x.d), x.b);
+__device__ __forceinline__ double rec_div1(const RecND& x, const double* K) {
+  return fma(x.n, rcp_nr1(K[14] * x.d, K[13]), x.b);
 }
 // two fields with one division: 1/d_x = d_y / (d_x d_y). The weights are
 // scaled by the indicators' products (section above), so d_x d_y stays far
 // inside the double range for any finite stencil data the solver meets.
 template <int REC>
-__device__ __forceinline__ void rec_div2(const RecND& x, const RecND& y, double& fx, double& fy) {
-  const double r = rcp_nr((rec_scale<REC>() * x.d) * y.d);
+__device__ __forceinline__ void rec_div2(const RecND& x, const RecND& y, double& fx, double& fy,
+                                         const double* K) {
+  const double r = rcp_nr1((K[14] * x.d) * y.d, K[13]);
   fx = fma(x.n, r * y.d, x.b);
   fy = fma(y.n, r * x.d, y.b);
 }
@@ -847,7 +892,8 @@ __device__ __forceinline__ void conv_flux(const Params& p, const double* __restr
 #define QF(field, m) ld(q0 + (long long)(field) * PC + (long long)(m) * sd)
   // ---- Roe-averaged face state (sqrt(rho) weights)
   const double sL = QF(L::SR, 0), sR = QF(L::SR, 1);
-  const double iw = rcp_nr(sL + sR);
+  const double one = __ldcg(p.dev->kface + 13);
+  const double iw = rcp_nr1(sL + sR, one);
   const double tL = sL * iw, tR = sR * iw;
   double ub[DIM], q2 = 0.0;
 #pragma unroll
@@ -863,7 +909,7 @@ __device__ __forceinline__ void conv_flux(const Params& p, const double* __restr
   const TauPt tp = tau_of(p, Tb);
   double hs[NS];
 #pragma unroll
-  for (int s = 0; s < NS; ++s) hs[s] = h_s_in(p, s, tp);
+  for (int s = 0; s < NS; ++s) hs[s] = h_s_dev(p, s, tp);
   // R(Y) and c_p(Y, T) are linear in Y: their face values come from the two
   // cells' mixture gas constants and c_p coefficients with the same weights
   const double Rb = fma(tL, QF(L::RM, 0), tR * QF(L::RM, 1));
@@ -873,7 +919,7 @@ __device__ __forceinline__ void conv_flux(const Params& p, const double* __restr
   const double cpb = fma(fma(fma(fma(Ab[4], tp.tc, Ab[3]), tp.tc, Ab[2]), tp.tc, Ab[1]), tp.tc, Ab[0]);
   const double cvb = cpb - Rb;
   // one division for Gamma = R/c_v and its inverse
-  const double rRc = rcp_nr(Rb * cvb);
+  const double rRc = rcp_nr1(Rb * cvb, one);
   const double Gam = Rb * Rb * rRc;
   const double hq2 = 0.5 * q2;
   // phi_s = R_s T - Gamma (e_s - |u|^2/2) with e_s = h_s - R_s T:
@@ -882,7 +928,7 @@ __device__ __forceinline__ void conv_flux(const Params& p, const double* __restr
   double phi[NS], c2 = 0.0;
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
-    phi[s] = fma(p.r[s], T1G, fma(-Gam, hs[s], Gq2));
+    phi[s] = fma(__ldcg(p.dev->r + s), T1G, fma(-Gam, hs[s], Gq2));
     c2 = fma(Yb[s], phi[s], c2);
   }
   c2 = fma(Gam, Hb - q2, c2);
@@ -933,6 +979,11 @@ __device__ __forceinline__ void conv_flux(const Params& p, const double* __restr
   }
   const double e12c[4] = {p.wenoe[0], p.wenoe[1], p.wenoe[2], p.wenoe[3]};
   const double e12q[4] = {p.wenoe4[0], p.wenoe4[1], p.wenoe4[2], p.wenoe4[3]};
+  double K[15];
+#pragma unroll
+  for (int j = 0; j < 15; ++j) K[j] = __ldcg(p.dev->kface + j);
+  const double* Ec = p.dev->wenoe;
+  const double* Eq = p.dev->wenoe4;
   const double chc = c * hic2;
   // ---- PER: one characteristic field at a time. With w = (1/2)(l.F_m +- a l.U_m)
   //      and l.F_m = u_m (l.U_m) + p_m (l[m_n] + u_m l[E]):
@@ -962,7 +1013,7 @@ __device__ __forceinline__ void conv_flux(const Params& p, const double* __restr
         wm[m] = hm0[m] * LU;
       }
     }
-    return rec_nd<REC>(wp, wm, e12c);
+    return rec_nd<REC>(wp, wm, e12c, K, Ec);
   };
   double Fk_m, Fk_p, Fk_e, Fk_first = 0.0;
   {
@@ -990,7 +1041,7 @@ __device__ __forceinline__ void conv_flux(const Params& p, const double* __restr
         wp[m] = fma(ha, LU, X);
         wm[m] = fma(-ha, LU, X);
       }
-      ndm = rec_nd<REC>(wp, wm, e12c);
+      ndm = rec_nd<REC>(wp, wm, e12c, K, Ec);
     }
     // u + c
     {
@@ -1002,9 +1053,9 @@ __device__ __forceinline__ void conv_flux(const Params& p, const double* __restr
         wp[m] = fma(ha, LU, X);
         wm[m] = fma(-ha, LU, X);
       }
-      ndp = rec_nd<REC>(wp, wm, e12c);
+      ndp = rec_nd<REC>(wp, wm, e12c, K, Ec);
     }
-    rec_div2<REC>(ndm, ndp, Fk_m, Fk_p);
+    rec_div2<REC>(ndm, ndp, Fk_m, Fk_p, K);
     // (u_m +- |u|max)/2, shared by the entropy row and the passive fields
     const double ha0 = 0.5 * a0;
 #pragma unroll
@@ -1020,11 +1071,11 @@ __device__ __forceinline__ void conv_flux(const Params& p, const double* __restr
         wp[m] = fma(hp0[m], LUh, pV[m]);
         wm[m] = fma(hm0[m], LUh, pV[m]);
       }
-      nde = rec_nd<REC>(wp, wm, e12q);
+      nde = rec_nd<REC>(wp, wm, e12q, K, Eq);
     }
     // the entropy field shares its division with the first passive field
-    if constexpr (NPASS > 0) rec_div2<REC>(nde, passive_nd(0), Fk_e, Fk_first);
-    else Fk_e = rec_div1<REC>(nde);
+    if constexpr (NPASS > 0) rec_div2<REC>(nde, passive_nd(0), Fk_e, Fk_first, K);
+    else Fk_e = rec_div1<REC>(nde, K);
   }
   // back-projection of the three dense right columns (Eq. 15)
   {
@@ -1056,11 +1107,11 @@ __device__ __forceinline__ void conv_flux(const Params& p, const double* __restr
     const RecND x = passive_nd(k);
     if (k + 1 < NPASS) {
       double fx, fy;
-      rec_div2<REC>(x, passive_nd(k + 1), fx, fy);
+      rec_div2<REC>(x, passive_nd(k + 1), fx, fy, K);
       passive_add(k, fx);
       passive_add(k + 1, fy);
     } else {
-      passive_add(k, rec_div1<REC>(x));
+      passive_add(k, rec_div1<REC>(x, K));
     }
   }
 #undef QF
@@ -1165,8 +1216,9 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
     const double wi = 1.0 / 16.0;
     const double wd = p.inv_dx[D] * (1.0 / 12.0);
     const double wid = wi * wd;
-#define FI0(field) (fma(9.0, QF(field, 0) + QF(field, 1), -(QF(field, -1) + QF(field, 2))))
-#define FD0(field) (fma(15.0, QF(field, 1) - QF(field, 0), -(QF(field, 2) - QF(field, -1))))
+    const double k9 = __ldcg(p.dev->kface + 11), k15 = __ldcg(p.dev->kface + 12);
+#define FI0(field) (fma(k9, QF(field, 0) + QF(field, 1), -(QF(field, -1) + QF(field, 2))))
+#define FD0(field) (fma(k15, QF(field, 1) - QF(field, 0), -(QF(field, 2) - QF(field, -1))))
     // tau_Da (Eq. 3) = (mu/16) t16_a with t16_a = 16 (du_D/dx_a + du_a/dx_D)
     // for a != D and t16_D = 16 (4/3 du_D/dx_D - 2/3 sum_{a != D} du_a/dx_a);
     // FI0 of the nodal derivatives is 16 times their face value, FD0 of u is
@@ -1228,7 +1280,7 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
     const TauPt tp = tau_pt(p, fma(FI0(L::T), wi * p.inv_span, p.tau0));
     double qd = 0.0;
 #pragma unroll
-    for (int s = 0; s < NS; ++s) qd = fma(h_s_in(p, s, tp), Jn[s], qd);
+    for (int s = 0; s < NS; ++s) qd = fma(h_s_dev(p, s, tp), Jn[s], qd);
     Gout[IE] -= fma(FI0(L::KA) * wid, FD0(L::T), fma(mu16 * wi, W, -nJ * qd));
 #pragma unroll
     for (int s = 0; s < NS - 1; ++s) Gout[IE + 1 + s] = fma(nJ, Jn[s], Gout[IE + 1 + s]);
