@@ -63,18 +63,18 @@ struct Params {
   // the face kernel's fixed coefficients (kFaceCoef, then the field pair's
   // division scale rec_scale), read through dev like the run constants above
   double kface[16];
+  double kexp[8];    // kExpCoef (primitive recovery's exponentials)
   int viscous, convective, newton_max;
   int weno;          // 5: WENO5-JS, 6: WENO-CU6
   int positivity;    // positivity-preserving blend of the convective flux (Eq. 17-20)
   double pos_eps;
   double hmin2_over_2dim;
   // This struct's copy in device memory, set by its owner (a solver handle, a
-  // batch instance, the static scratch) before the first face launch. The
-  // face kernel reads its FP64 coefficients (kface, wenoe, wenoe4, r, rh,
-  // rhoff) from there: an FP64 instruction that takes a kernel parameter or a
-  // literal as an operand issues at about 84 % of the rate of one with
-  // register operands on this GPU, and values loaded from memory land in
-  // registers.
+  // batch instance, the static scratch) before the first launch. The face
+  // kernel and the primitive recovery read their FP64 coefficients from there:
+  // an FP64 instruction that takes a kernel parameter or a literal as an
+  // operand issues at about 84 % of the rate of one with register operands on
+  // this GPU, and values loaded from memory land in registers.
   const Params* dev;
 };
 
@@ -109,6 +109,9 @@ struct Lay {
 };
 
 __device__ __forceinline__ double ld(const double* p) { return __ldg(p); }
+// a coefficient read from the device copy of the parameters (Params::dev) into
+// a register
+__device__ __forceinline__ double rd(const double& x) { return __ldcg(&x); }
 
 // 1/x by Newton-Raphson iteration for the reciprocal (M. J. Flynn, "On
 // division by functional iteration", IEEE Trans. Computers C-19, 1970),
@@ -173,23 +176,34 @@ static __device__ const double kExp2J64[64] = {
 // the 1.5 2^52 shift, r is formed with ln2/64 split into a leading double and
 // its remainder, 2^(j/64) comes from the table and 2^m is added to the
 // exponent on the integer pipe: 10 FP64 instructions. Within about one ulp
-// of exp (xf_probe_exp). |x| > 700 (outside the fits' range) takes exp.
-__device__ __forceinline__ double exp_t(double x) {
-  if (!(fabs(x) <= 700.0)) return exp(x);
-  constexpr double k64ln2 = 0x1.71547652b82fep+6;   // 64 / ln 2
-  constexpr double kL1 = 0x1.62e42fefa39efp-7;      // ln 2 / 64, leading part
-  constexpr double kL2 = 0x1.abc9e3b39803fp-62;     // ln 2 / 64 - kL1
-  constexpr double kShift = 6755399441055744.0;     // 1.5 * 2^52
-  const double t = fma(x, k64ln2, kShift);
-  const long long n = __double_as_longlong(t) - __double_as_longlong(kShift);
-  const double kd = t - kShift;
-  const double r = fma(kd, -kL2, fma(kd, -kL1, x));
-  const double q = fma(fma(fma(1.0 / 120.0, r, 1.0 / 24.0), r, 1.0 / 6.0), r, 0.5);
+// of exp (xf_probe_exp). |x| > 700 (outside the fits' range; the test runs on
+// the bit pattern) takes exp.
+// Its constants, in the order exp_k takes them: 64/ln 2, the 1.5 2^52 shift,
+// -(ln 2/64) split into a leading double and its remainder, and the Taylor
+// coefficients 1/120, 1/24, 1/6, 1/2.
+#define XF_EXP_COEF                                                          \
+  0x1.71547652b82fep+6, 6755399441055744.0, -0x1.62e42fefa39efp-7, -0x1.abc9e3b39803fp-62, \
+      1.0 / 120.0, 1.0 / 24.0, 1.0 / 6.0, 0.5
+constexpr double kExpCoef[8] = {XF_EXP_COEF};
+// K = kExpCoef, as literals (exp_t) or loaded into registers (primitive
+// recovery, from the device copy of the parameters)
+__device__ __forceinline__ double exp_k(double x, const double* K) {
+  if (!((__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFLL) <= 0x4085E00000000000LL))  // |x| <= 700
+    return exp(x);
+  const double t = fma(x, K[0], K[1]);
+  const long long n = __double_as_longlong(t) - __double_as_longlong(6755399441055744.0);
+  const double kd = t - K[1];
+  const double r = fma(kd, K[3], fma(kd, K[2], x));
+  const double q = fma(fma(fma(K[4], r, K[5]), r, K[6]), r, K[7]);
   const double er1 = fma(r * r, q, r);               // e^r - 1
   const double T = __ldg(kExp2J64 + (n & 63));
   const double e = fma(T, er1, T);
   return __longlong_as_double(__double_as_longlong(e) +
                               (long long)((unsigned long long)(n >> 6) << 52));
+}
+__device__ __forceinline__ double exp_t(double x) {
+  const double K[8] = {XF_EXP_COEF};
+  return exp_k(x, K);
 }
 
 // max of two non-negative doubles through their ordered bit patterns (integer
@@ -309,8 +323,12 @@ __device__ __forceinline__ void prim_cell(const Params& p, long long t, const do
     bool finite = true;
 #pragma unroll
     for (int v = 0; v < NV; ++v) finite = finite && isfinite(u[v]);
+    // the FP64 coefficients below come from the parameters' device copy
+    // (register operands, Params::dev)
+    const Params& pd = *p.dev;
+    const double one = rd(pd.kface[13]), half = rd(pd.kexp[7]);
     const double rho = u[0];
-    const double irho = rcp_nr(rho);
+    const double irho = rcp_nr1(rho, one);
     double vel[DIM], ke = 0.0;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) { vel[a] = u[1 + a] * irho; ke = fma(vel[a], vel[a], ke); }
@@ -318,8 +336,8 @@ __device__ __forceinline__ void prim_cell(const Params& p, long long t, const do
     double Y[NS], ysum = 0.0;
 #pragma unroll
     for (int s = 0; s < NS - 1; ++s) { Y[s] = u[DIM + 2 + s] * irho; ysum += Y[s]; }
-    Y[NS - 1] = 1.0 - ysum;
-    const double e = fma(E, irho, -0.5 * ke);
+    Y[NS - 1] = one - ysum;
+    const double e = fma(E, irho, -(half * ke));
     // mixture polynomial coefficients: c_p(tau) = sum A_j tau^j,
     // h(tau) = B + sum Ah_j tau^(j+1) with Ah_j = A_j span/(j+1), R = Rm
     double A[5], Ah[5], Rm = 0.0, B = 0.0;
@@ -327,35 +345,36 @@ __device__ __forceinline__ void prim_cell(const Params& p, long long t, const do
     for (int jj = 0; jj < 5; ++jj) A[jj] = 0.0;
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-      Rm = fma(Y[s], p.r[s], Rm);
-      B = fma(Y[s], p.rhoff[s], B);
+      Rm = fma(Y[s], rd(pd.r[s]), Rm);
+      B = fma(Y[s], rd(pd.rhoff[s]), B);
 #pragma unroll
-      for (int jj = 0; jj < 5; ++jj) A[jj] = fma(Y[s], p.rcp[s][jj], A[jj]);
+      for (int jj = 0; jj < 5; ++jj) A[jj] = fma(Y[s], rd(pd.rcp[s][jj]), A[jj]);
     }
 #pragma unroll
-    for (int jj = 0; jj < 5; ++jj) Ah[jj] = A[jj] * p.hsj[jj];
+    for (int jj = 0; jj < 5; ++jj) Ah[jj] = A[jj] * rd(pd.hsj[jj]);
     // Newton (Eq. 21): T <- T + (e - e(T)) / c_v(T), stop at |dT| <= rtol T;
     // a non-positive iterate is replaced by half the previous one
     double T = ld(Tin + src);
+    const double isp = rd(pd.inv_span), tau0 = rd(pd.tau0), rtol = rd(pd.newton_rtol);
     bool conv = false;
     for (int it = 0; it < p.newton_max; ++it) {
-      const TauPt tp = tau_of(p, T);
+      const TauPt tp = tau_pt(p, fma(T, isp, tau0));
       const double cpm = fma(fma(fma(fma(A[4], tp.tc, A[3]), tp.tc, A[2]), tp.tc, A[1]), tp.tc, A[0]);
       const double hp = fma(fma(fma(fma(fma(Ah[4], tp.tc, Ah[3]), tp.tc, Ah[2]), tp.tc, Ah[1]), tp.tc, Ah[0]), tp.tc, B);
       const double eT = (tp.in ? hp : fma(cpm, tp.ext, hp)) - Rm * T;
-      double Tn = fma(e - eT, rcp_nr(cpm - Rm), T);
-      if (!(Tn > 0.0)) Tn = 0.5 * T;
-      conv = fabs(Tn - T) <= p.newton_rtol * Tn;
+      double Tn = fma(e - eT, rcp_nr1(cpm - Rm, one), T);
+      if (!(Tn > 0.0)) Tn = half * T;
+      conv = fabs(Tn - T) <= rtol * Tn;
       T = Tn;
       if (conv) break;
     }
     if (!conv) st |= 2u;
-    const TauPt tp = tau_of(p, T);
+    const TauPt tp = tau_pt(p, fma(T, isp, tau0));
     const double cpm = fma(fma(fma(fma(A[4], tp.tc, A[3]), tp.tc, A[2]), tp.tc, A[1]), tp.tc, A[0]);
     const double cvm = cpm - Rm;
     const double RT = Rm * T;
     const double pr = rho * RT;
-    const double icvm = rcp_nr(cvm);
+    const double icvm = rcp_nr1(cvm, one);
     const double c2 = cpm * RT * icvm;
     const double c = sqrt(c2);
     const double H = (E + pr) * irho;
@@ -379,14 +398,19 @@ __device__ __forceinline__ void prim_cell(const Params& p, long long t, const do
     if (p.viscous) {
       // Eq. 29 fits; sqrt(mu_s) = exp(ln mu_s / 2) feeds the Wilke ratios (Eq. 22)
       const double lnT = log(T);
+      double KX[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) KX[j] = rd(pd.kexp[j]);
       double smu[NS], ska[NS], ismu[NS], iska[NS], X[NS], xs = 0.0;
 #pragma unroll
       for (int s = 0; s < NS; ++s) {
-        const double lm = fma(fma(fma(p.lnmu[s][3], lnT, p.lnmu[s][2]), lnT, p.lnmu[s][1]), lnT, p.lnmu[s][0]);
-        const double lk = fma(fma(fma(p.lnka[s][3], lnT, p.lnka[s][2]), lnT, p.lnka[s][1]), lnT, p.lnka[s][0]);
-        smu[s] = exp_t(0.5 * lm);
-        ska[s] = exp_t(0.5 * lk);
-        X[s] = Y[s] * p.invW[s];
+        const double* fm = pd.lnmu[s];
+        const double* fk = pd.lnka[s];
+        const double lm = fma(fma(fma(rd(fm[3]), lnT, rd(fm[2])), lnT, rd(fm[1])), lnT, rd(fm[0]));
+        const double lk = fma(fma(fma(rd(fk[3]), lnT, rd(fk[2])), lnT, rd(fk[1])), lnT, rd(fk[0]));
+        smu[s] = exp_k(half * lm, KX);
+        ska[s] = exp_k(half * lk, KX);
+        X[s] = Y[s] * rd(pd.invW[s]);
         xs += X[s];
       }
       // the 2N reciprocals 1/sqrt(mu_s), 1/sqrt(kappa_s) from one division
@@ -396,7 +420,7 @@ __device__ __forceinline__ void prim_cell(const Params& p, long long t, const do
         pre[0] = smu[0];
 #pragma unroll
         for (int k = 1; k < 2 * NS; ++k) pre[k] = pre[k - 1] * (k < NS ? smu[k] : ska[k - NS]);
-        double inv = rcp_nr(pre[2 * NS - 1]);
+        double inv = rcp_nr1(pre[2 * NS - 1], one);
 #pragma unroll
         for (int k = 2 * NS - 1; k > 0; --k) {
           const double v = k < NS ? smu[k] : ska[k - NS];
@@ -406,7 +430,7 @@ __device__ __forceinline__ void prim_cell(const Params& p, long long t, const do
         }
         ismu[0] = inv;
       }
-      const double ixs = rcp_nr(xs);
+      const double ixs = rcp_nr1(xs, one);
       // Wilke denominators sum_t X_t A_st (1 + r_st B_st)^2 with r_st = (a_s/a_t)^(1/2),
       // expanded: S0_s + 2 sqrt(a_s) S1_s + a_s S2_s, where S0_s = sum_t X_t A_st,
       // S1_s = sum_t X_t a_t^(-1/2) A_st B_st, S2_s = sum_t X_t a_t^(-1) A_st B_st^2
@@ -429,15 +453,16 @@ __device__ __forceinline__ void prim_cell(const Params& p, long long t, const do
 #pragma unroll
         for (int tt = 0; tt < NS; ++tt) {
           if (tt == s) continue;
-          s0 = fma(X[tt], p.wA[s][tt], s0);
-          m1 = fma(xm1[tt], p.wAB[s][tt], m1);
-          m2 = fma(xm2[tt], p.wABB[s][tt], m2);
-          k1 = fma(xk1[tt], p.wAB[s][tt], k1);
-          k2 = fma(xk2[tt], p.wABB[s][tt], k2);
+          const double wab = rd(pd.wAB[s][tt]), wabb = rd(pd.wABB[s][tt]);
+          s0 = fma(X[tt], rd(pd.wA[s][tt]), s0);
+          m1 = fma(xm1[tt], wab, m1);
+          m2 = fma(xm2[tt], wabb, m2);
+          k1 = fma(xk1[tt], wab, k1);
+          k2 = fma(xk2[tt], wabb, k2);
         }
         s0 += X[s];
-        dm[s] = fma(smu[s] * smu[s], m2, fma(2.0 * smu[s], m1, s0));
-        dk[s] = fma(ska[s] * ska[s], k2, fma(2.0 * ska[s], k1, s0));
+        dm[s] = fma(smu[s] * smu[s], m2, fma(smu[s] + smu[s], m1, s0));
+        dk[s] = fma(ska[s] * ska[s], k2, fma(ska[s] + ska[s], k1, s0));
       }
       // the 2N Wilke denominators inverted with one division, as above
       {
@@ -445,7 +470,7 @@ __device__ __forceinline__ void prim_cell(const Params& p, long long t, const do
         pre[0] = dm[0];
 #pragma unroll
         for (int k = 1; k < 2 * NS; ++k) pre[k] = pre[k - 1] * (k < NS ? dm[k] : dk[k - NS]);
-        double inv = rcp_nr(pre[2 * NS - 1]);
+        double inv = rcp_nr1(pre[2 * NS - 1], one);
         double idm[NS], idk[NS];
 #pragma unroll
         for (int k = 2 * NS - 1; k > 0; --k) {
@@ -461,9 +486,9 @@ __device__ __forceinline__ void prim_cell(const Params& p, long long t, const do
           ka = fma(X[s] * (ska[s] * ska[s]), idk[s], ka);
         }
       }
-      mu *= p.fmu;
-      ka *= p.fka;
-      Dd = ka * p.inv_lewis * rcp_nr(rho * cpm);
+      mu *= rd(pd.fmu);
+      ka *= rd(pd.fka);
+      Dd = ka * rd(pd.inv_lewis) * rcp_nr1(rho * cpm, one);
       q[L::MU * PC] = mu;
       q[L::KA * PC] = ka;
       q[L::DF * PC] = Dd;
@@ -474,14 +499,14 @@ __device__ __forceinline__ void prim_cell(const Params& p, long long t, const do
         double Xt[NS], xts = 0.0;
 #pragma unroll
         for (int s = 0; s < NS; ++s) { Xt[s] = fmax(X[s], 0.0) + 1e-12; xts += Xt[s]; }
-        const double ixts = rcp_nr(xts);
+        const double ixts = rcp_nr1(xts, one);
         // the sums of products are written as fused multiply-adds: the
         // batched kernel compiles this body too and must give the same bits
         double Wt = 0.0;
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
           Xt[s] *= ixts;
-          Wt = fma(Xt[s], p.Wm[s], Wt);
+          Wt = fma(Xt[s], rd(pd.Wm[s]), Wt);
         }
         double den[NS];
 #pragma unroll
@@ -490,22 +515,22 @@ __device__ __forceinline__ void prim_cell(const Params& p, long long t, const do
         for (int s = 0; s < NS; ++s) {
 #pragma unroll
           for (int tt = s + 1; tt < NS; ++tt) {
-            const double* b = p.dbin[s][tt];
-            const double l = fma(fma(fma(b[3], lnT, b[2]), lnT, b[1]), lnT, b[0]);
-            const double iD = exp_t(-l);
+            const double* b = pd.dbin[s][tt];
+            const double l = fma(fma(fma(rd(b[3]), lnT, rd(b[2])), lnT, rd(b[1])), lnT, rd(b[0]));
+            const double iD = exp_k(-l, KX);
             den[s] = fma(Xt[tt], iD, den[s]);
             den[tt] = fma(Xt[s], iD, den[tt]);
           }
         }
-        const double sc = rcp_nr(Wt * pr * p.fdsm);
+        const double sc = rcp_nr1(Wt * pr * rd(pd.fdsm), one);
         double Dmax = 0.0;
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
           double num = 0.0;
 #pragma unroll
           for (int tt = 0; tt < NS; ++tt)
-            if (tt != s) num = fma(Xt[tt], p.Wm[tt], num);
-          const double Ds = num * sc * rcp_nr(den[s]);
+            if (tt != s) num = fma(Xt[tt], rd(pd.Wm[tt]), num);
+          const double Ds = num * sc * rcp_nr1(den[s], one);
           q[(L::DS + s) * PC] = Ds;
           Dmax = fmax(Dmax, Ds);
         }
@@ -557,9 +582,11 @@ __device__ __forceinline__ void block_max2(double s_cfl, double s_nu, unsigned l
 
 // Interior cells [c0, c1) (0 <= c0 <= c1 <= cells; the whole grid, or one
 // slab of planes of the slowest axis), each written at its padded position.
-// The ghost layers are filled afterwards by k_ghost.
+// The ghost layers are filled afterwards by k_ghost. Two blocks per SM (at
+// most 128 registers, a few spilled) ran 4.7 % faster than one block with
+// the 166 registers the compiler takes otherwise.
 template <int DIM, int NS>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
 k_prim(const __grid_constant__ Params p, const double* __restrict__ U,
        const double* __restrict__ Tin, double* __restrict__ Tout,
        double* __restrict__ Q, uint32_t* __restrict__ flags,
