@@ -60,9 +60,9 @@ struct Params {
                      // reconstructions are homogeneous of degree one when eps
                      // scales with the square of the data, exactly so for a
                      // power-of-two factor)
-  // the face kernel's fixed coefficients (kFaceCoef, then the field pair's
-  // division scale rec_scale), read through dev like the run constants above
-  double kface[16];
+  // the face kernel's fixed coefficients (kFaceCoef with the field pair's
+  // division scale rec_scale at 14), read through dev like the run constants
+  double kface[24];
   double kexp[8];    // kExpCoef (primitive recovery's exponentials)
   int viscous, convective, newton_max;
   int weno;          // 5: WENO5-JS, 6: WENO-CU6
@@ -714,10 +714,15 @@ constexpr double kWc2 = 0.03608439182435161;  // 1/(16 sqrt 3)
 
 // The face kernel's fixed coefficients, in the order Params::kface holds
 // them: the WENO5 indicators' and candidates' (0-10, weno5_nd), the face
-// stencil's 9 and 15 (11, 12, face_one) and the Newton-Raphson 1 (13).
-constexpr double kFaceCoef[14] = {-1.375, -0.625, 9.75 * kWc0, 16.0 * kWc1, 9.75 * kWc1,
-                                  16.0 * kWc2, 9.75 * kWc2, -2.0, 2.25, 2.0, 4.0,
-                                  9.0, 15.0, 1.0};
+// stencil's 9 and 15 (11, 12, face_one), the Newton-Raphson 1 (13), [14: the
+// division scale], 1/2 (15), and the viscous flux's 1/16, 1/12, 16, 4/3,
+// -2/3 and 1/256 (16-21, face_one).
+constexpr int kFaceCoefN = 22;
+constexpr double kFaceCoef[kFaceCoefN] = {-1.375, -0.625, 9.75 * kWc0, 16.0 * kWc1, 9.75 * kWc1,
+                                          16.0 * kWc2, 9.75 * kWc2, -2.0, 2.25, 2.0, 4.0,
+                                          9.0, 15.0, 1.0, 0.0, 0.5,
+                                          1.0 / 16.0, 1.0 / 12.0, 16.0, 4.0 / 3.0, -2.0 / 3.0,
+                                          1.0 / 256.0};
 
 // K = kface in registers, E = {12 eps c_k} in device memory (per call)
 __device__ __forceinline__ void weno5_nd(double f0, double f1, double f2, double f3, double f4,
@@ -919,7 +924,7 @@ __device__ __forceinline__ void conv_flux(const Params& p, const double* __restr
 #define QF(field, m) ld(q0 + (long long)(field) * PC + (long long)(m) * sd)
   // ---- Roe-averaged face state (sqrt(rho) weights)
   const double sL = QF(L::SR, 0), sR = QF(L::SR, 1);
-  const double one = __ldcg(p.dev->kface + 13);
+  const double one = __ldcg(p.dev->kface + 13), half = __ldcg(p.dev->kface + 15);
   const double iw = rcp_nr1(sL + sR, one);
   const double tL = sL * iw, tR = sR * iw;
   double ub[DIM], q2 = 0.0;
@@ -933,7 +938,7 @@ __device__ __forceinline__ void conv_flux(const Params& p, const double* __restr
   double Yb[NS];
 #pragma unroll
   for (int s = 0; s < NS; ++s) Yb[s] = fma(tL, QF(L::Y + s, 0), tR * QF(L::Y + s, 1));
-  const TauPt tp = tau_of(p, Tb);
+  const TauPt tp = tau_pt(p, fma(Tb, rd(p.dev->inv_span), rd(p.dev->tau0)));
   double hs[NS];
 #pragma unroll
   for (int s = 0; s < NS; ++s) hs[s] = h_s_dev(p, s, tp);
@@ -948,7 +953,7 @@ __device__ __forceinline__ void conv_flux(const Params& p, const double* __restr
   // one division for Gamma = R/c_v and its inverse
   const double rRc = rcp_nr1(Rb * cvb, one);
   const double Gam = Rb * Rb * rRc;
-  const double hq2 = 0.5 * q2;
+  const double hq2 = half * q2;
   // phi_s = R_s T - Gamma (e_s - |u|^2/2) with e_s = h_s - R_s T:
   // R_s (1 + Gamma) T - Gamma h_s + Gamma |u|^2/2
   const double T1G = fma(Gam, Tb, Tb), Gq2 = Gam * hq2;
@@ -967,7 +972,7 @@ __device__ __forceinline__ void conv_flux(const Params& p, const double* __restr
   const double rsc = rsqrt(c2);
   const double c = c2 * rsc;
   const double ic2 = rsc * rsc;
-  const double hic2 = 0.5 * ic2;
+  const double hic2 = half * ic2;
   const double iGam = cvb * cvb * rRc;
   const double un = ub[D];
   // ---- stencil m = i-SO..i+SO+1 (SW cells: i-2..i+3 for WENO5 and CU6,
@@ -995,7 +1000,7 @@ __device__ __forceinline__ void conv_flux(const Params& p, const double* __restr
     am = pmax(am, fabs(unm - cm));
     ap = pmax(ap, fabs(unm + cm));
     a0 = pmax(a0, fabs(unm));
-    hun[m] = 0.5 * unm;
+    hun[m] = half * unm;
     double g = gr * rho_m[m];
 #pragma unroll
     for (int a = 0; a < DIM; ++a) g = fma(gm[a], QF(L::U + 1 + a, o), g);
@@ -1054,13 +1059,13 @@ __device__ __forceinline__ void conv_flux(const Params& p, const double* __restr
     // from one product per cell: with lE = Gam/(2c^2) and hl0 = -Gam u_n/(4c^2),
     // the u -+ c rows take p_m (u_m/2 lE + hl0 -+ c/(4c^2)) and the entropy row
     // exactly -2 p_m (u_m/2 lE + hl0)
-    const double lE = gE, hl0 = (-0.5 * un) * gE, dl = 0.5 * chc;
+    const double lE = gE, hl0 = (-half * un) * gE, dl = half * chc;
     double pV[SW];
 #pragma unroll
     for (int m = 0; m < SW; ++m) pV[m] = p_m[m] * fma(hun[m], lE, hl0);
     // u - c: l.U = (g.U - c (m_n - u_n rho)) / (2c^2)
     {
-      const double ha = 0.5 * am;
+      const double ha = half * am;
 #pragma unroll
       for (int m = 0; m < SW; ++m) {
         const double LU = fma(-chc, nUv[m], gUh[m]);
@@ -1072,7 +1077,7 @@ __device__ __forceinline__ void conv_flux(const Params& p, const double* __restr
     }
     // u + c
     {
-      const double ha = 0.5 * ap;
+      const double ha = half * ap;
 #pragma unroll
       for (int m = 0; m < SW; ++m) {
         const double LU = fma(chc, nUv[m], gUh[m]);
@@ -1084,7 +1089,7 @@ __device__ __forceinline__ void conv_flux(const Params& p, const double* __restr
     }
     rec_div2<REC>(ndm, ndp, Fk_m, Fk_p, K);
     // (u_m +- |u|max)/2, shared by the entropy row and the passive fields
-    const double ha0 = 0.5 * a0;
+    const double ha0 = half * a0;
 #pragma unroll
     for (int m = 0; m < SW; ++m) { hp0[m] = hun[m] + ha0; hm0[m] = hun[m] - ha0; }
     // entropy: l = e_rho - g / c^2, w = (u_m/2 +- a/2)(rho - 2 g.U/(2c^2)) - 2 pV,
@@ -1094,7 +1099,7 @@ __device__ __forceinline__ void conv_flux(const Params& p, const double* __restr
     {
 #pragma unroll
       for (int m = 0; m < SW; ++m) {
-        const double LUh = fma(-0.5, rho_m[m], gUh[m]);
+        const double LUh = fma(-half, rho_m[m], gUh[m]);
         wp[m] = fma(hp0[m], LUh, pV[m]);
         wm[m] = fma(hm0[m], LUh, pV[m]);
       }
@@ -1106,7 +1111,7 @@ __device__ __forceinline__ void conv_flux(const Params& p, const double* __restr
   }
   // back-projection of the three dense right columns (Eq. 15)
   {
-    const double S = fma(-2.0, Fk_e, Fk_m + Fk_p);
+    const double S = fma(K[7], Fk_e, Fk_m + Fk_p);  // K[7] = -2
     const double Dl = Fk_p - Fk_m;
     Gout[0] = S;
 #pragma unroll
@@ -1239,19 +1244,21 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
   if (p.viscous) {
     // face values (-1, 9, 9, -1)/16, normal derivatives (1, -15, 15, -1)/(12 dx).
     // FI0 / FD0 leave out the factors 1/16 and 1/(12 dx); each product below
-    // takes them once (wi, wd, wid = wi wd).
-    const double wi = 1.0 / 16.0;
-    const double wd = p.inv_dx[D] * (1.0 / 12.0);
+    // takes them once (wi, wd, wid = wi wd). The constants come from the
+    // parameters' device copy (register operands).
+    const double* kf = p.dev->kface;
+    const double wi = rd(kf[16]);
+    const double wd = rd(p.dev->inv_dx[D]) * rd(kf[17]);
     const double wid = wi * wd;
-    const double k9 = __ldcg(p.dev->kface + 11), k15 = __ldcg(p.dev->kface + 12);
+    const double k9 = rd(kf[11]), k15 = rd(kf[12]);
 #define FI0(field) (fma(k9, QF(field, 0) + QF(field, 1), -(QF(field, -1) + QF(field, 2))))
 #define FD0(field) (fma(k15, QF(field, 1) - QF(field, 0), -(QF(field, 2) - QF(field, -1))))
     // tau_Da (Eq. 3) = (mu/16) t16_a with t16_a = 16 (du_D/dx_a + du_a/dx_D)
     // for a != D and t16_D = 16 (4/3 du_D/dx_D - 2/3 sum_{a != D} du_a/dx_a);
     // FI0 of the nodal derivatives is 16 times their face value, FD0 of u is
     // the normal derivative over wd, so rq = wd/wi weights the normal ones
-    const double mu16 = FI0(L::MU) * (wi * wi);
-    const double rq = 16.0 * wd;
+    const double mu16 = FI0(L::MU) * rd(kf[21]);  // wi wi
+    const double rq = rd(kf[18]) * wd;
     double t16[DIM], tr = 0.0;
     bool first = true;
 #pragma unroll
@@ -1261,7 +1268,7 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
       tr = first ? FI0(L::GU + a * DIM + a) : tr + FI0(L::GU + a * DIM + a);
       first = false;
     }
-    t16[D] = fma((4.0 / 3.0) * rq, FD0(L::UN + D), (-2.0 / 3.0) * tr);
+    t16[D] = fma(rd(kf[19]) * rq, FD0(L::UN + D), rd(kf[20]) * tr);  // 4/3, -2/3
     // 256 sum_a tau_a u_a / mu16 = sum_a t16_a FI0(u_a); products that feed
     // a sum are written as fused multiply-adds, here and below, so the
     // batched kernel, which compiles this body too, gives the same bits
@@ -1304,7 +1311,7 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
       nJ = nrf * FI0(L::DF);
     }
     // h_s at the face temperature T_f = wi FI0(T); qd = sum_s h_s J_s / nJ
-    const TauPt tp = tau_pt(p, fma(FI0(L::T), wi * p.inv_span, p.tau0));
+    const TauPt tp = tau_pt(p, fma(FI0(L::T), wi * rd(p.dev->inv_span), rd(p.dev->tau0)));
     double qd = 0.0;
 #pragma unroll
     for (int s = 0; s < NS; ++s) qd = fma(h_s_dev(p, s, tp), Jn[s], qd);
