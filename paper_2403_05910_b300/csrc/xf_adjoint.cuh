@@ -30,41 +30,45 @@ struct W5 {
   double num, den;
 };
 
+// K = Params::kface in registers, E = {12 eps c_k} in device memory (as
+// weno5_nd)
 __device__ __forceinline__ void w5_fwd(double f0, double f1, double f2, double f3, double f4,
-                                       const double* e12c, W5& r) {
+                                       const double* K, const double* E, W5& r) {
   r.a = f1 - f0; r.b = f2 - f1; r.c = f3 - f2; r.d = f4 - f3;
-  r.A0 = fma(-1.375, r.b, r.a); r.B1 = fma(-0.625, r.c, r.b); r.D2 = fma(-1.375, r.c, r.d);
+  r.A0 = fma(K[0], r.b, r.a); r.B1 = fma(K[1], r.c, r.b); r.D2 = fma(K[0], r.c, r.d);
   const double cc = r.c * r.c;
-  r.s0 = fma(r.A0, r.A0, fma((9.75 * kWc0) * r.b, r.b, e12c[0]));  // 16 c_0 = 1
-  r.s1 = fma((16.0 * kWc1) * r.B1, r.B1, fma(9.75 * kWc1, cc, e12c[1]));
-  r.s2 = fma((16.0 * kWc2) * r.D2, r.D2, fma(9.75 * kWc2, cc, e12c[2]));
+  r.s0 = fma(r.A0, r.A0, fma(K[2] * r.b, r.b, __ldcg(E + 0)));  // 16 c_0 = 1
+  r.s1 = fma(K[3] * r.B1, r.B1, fma(K[4], cc, __ldcg(E + 1)));
+  r.s2 = fma(K[5] * r.D2, r.D2, fma(K[6], cc, __ldcg(E + 2)));
   r.p12 = r.s1 * r.s2; r.p02 = r.s0 * r.s2; r.p01 = r.s0 * r.s1;
   r.w0 = r.p12 * r.p12; r.w1 = r.p02 * r.p02; r.w2 = r.p01 * r.p01;
-  r.q0 = fma(-2.0, r.A0, 2.25 * r.b);
-  r.q1 = fma(2.0, r.c, r.b);
-  r.q2 = fma(4.0, r.c, -r.d);
+  r.q0 = fma(K[7], r.A0, K[8] * r.b);
+  r.q1 = fma(K[9], r.c, r.b);
+  r.q2 = fma(K[10], r.c, -r.d);
   r.num = fma(r.w0, r.q0, fma(r.w1, r.q1, r.w2 * r.q2));
-  r.den = 6.0 * ((r.w0 + r.w1) + r.w2);
+  r.den = K[22] * ((r.w0 + r.w1) + r.w2);
 }
 
 // Reverse of one reconstruction: (nbar, dbar) for (num, den) -> fb[0..4] (added).
-__device__ __forceinline__ void w5_rev(const W5& r, double nbar, double dbar, double* fb) {
-  const double d6 = 6.0 * dbar;
+__device__ __forceinline__ void w5_rev(const W5& r, double nbar, double dbar, const double* K,
+                                       double* fb) {
+  const double d6 = K[22] * dbar;
   const double w0b = fma(nbar, r.q0, d6), w1b = fma(nbar, r.q1, d6), w2b = fma(nbar, r.q2, d6);
   const double q0b = nbar * r.w0, q1b = nbar * r.w1, q2b = nbar * r.w2;
-  const double p12b = 2.0 * w0b * r.p12, p02b = 2.0 * w1b * r.p02, p01b = 2.0 * w2b * r.p01;
+  const double p12b = (w0b + w0b) * r.p12, p02b = (w1b + w1b) * r.p02, p01b = (w2b + w2b) * r.p01;
   const double s0b = fma(p02b, r.s2, p01b * r.s1);
   const double s1b = fma(p12b, r.s2, p01b * r.s0);
   const double s2b = fma(p12b, r.s1, p02b * r.s0);
   // s_k = 16 c_k L_k^2 + 39/4 c_k x_k^2 + e; A0 = a - 11/8 b, B1 = b - 5/8 c,
   // D2 = d - 11/8 c; q0 = 9/4 b - 2 A0, q1 = 2c + b, q2 = 4c - d
-  const double A0b = fma((32.0 * kWc0) * r.A0, s0b, -2.0 * q0b);
-  const double B1b = (32.0 * kWc1) * r.B1 * s1b;
-  const double D2b = (32.0 * kWc2) * r.D2 * s2b;
+  // (K: 32 c_0 = 2, -1.375, -0.625, -2, 2.25, 2, 4, 32 c_1, 32 c_2, 19.5 c_k)
+  const double A0b = fma(r.A0 + r.A0, s0b, K[7] * q0b);
+  const double B1b = K[23] * r.B1 * s1b;
+  const double D2b = K[24] * r.D2 * s2b;
   const double ab = A0b;
-  const double bb = fma((19.5 * kWc0) * r.b, s0b, fma(2.25, q0b, fma(-1.375, A0b, B1b + q1b)));
-  const double cb = fma(r.c, fma(19.5 * kWc1, s1b, (19.5 * kWc2) * s2b),
-                        fma(2.0, q1b, fma(4.0, q2b, fma(-0.625, B1b, -1.375 * D2b))));
+  const double bb = fma(K[25] * r.b, s0b, fma(K[8], q0b, fma(K[0], A0b, B1b + q1b)));
+  const double cb = fma(r.c, fma(K[26], s1b, K[27] * s2b),
+                        fma(K[9], q1b, fma(K[10], q2b, fma(K[1], B1b, K[0] * D2b))));
   const double db = D2b - q2b;
   fb[0] -= ab;
   fb[1] += ab - bb;
@@ -76,22 +80,22 @@ __device__ __forceinline__ void w5_rev(const W5& r, double nbar, double dbar, do
 // One field's F = F^+ + F^- (as rec_nd with WENO5) and its reverse: returns F
 // and adds Fb dF/dw to wpb[0..5], wmb[0..5].
 __device__ __forceinline__ double weno5_pair_fwd_adj(const double* wp, const double* wm,
-                                                     const double* e12c, double Fb, double* wpb,
-                                                     double* wmb) {
+                                                     const double* K, const double* E, double Fb,
+                                                     double* wpb, double* wmb) {
   W5 P, M;
-  w5_fwd(wp[0], wp[1], wp[2], wp[3], wp[4], e12c, P);
-  w5_fwd(wm[5], wm[4], wm[3], wm[2], wm[1], e12c, M);
+  w5_fwd(wp[0], wp[1], wp[2], wp[3], wp[4], K, E, P);
+  w5_fwd(wm[5], wm[4], wm[3], wm[2], wm[1], K, E, M);
   // both reciprocals from one division; F from them
-  const double rpm = rcp_nr(P.den * M.den);
+  const double rpm = rcp_nr1(P.den * M.den, K[13]);
   const double idp = rpm * M.den, idm = rpm * P.den;
   const double F = (wp[2] + wm[3]) + fma(P.num, idp, M.num * idm);
   double fb[5] = {-0.0, -0.0, -0.0, -0.0, -0.0};
-  w5_rev(P, Fb * idp, -Fb * P.num * idp * idp, fb);
+  w5_rev(P, Fb * idp, -Fb * P.num * idp * idp, K, fb);
 #pragma unroll
   for (int k = 0; k < 5; ++k) wpb[k] += fb[k];
   wpb[2] += Fb;
   double gb[5] = {-0.0, -0.0, -0.0, -0.0, -0.0};
-  w5_rev(M, Fb * idm, -Fb * M.num * idm * idm, gb);
+  w5_rev(M, Fb * idm, -Fb * M.num * idm * idm, K, gb);
   wmb[5] += gb[0];
   wmb[4] += gb[1];
   wmb[3] += gb[2] + Fb;
@@ -267,13 +271,14 @@ __device__ __forceinline__ void w7_rev(const W7& r, double nbar, double dbar, do
 
 // One field's F = F^+ + F^- with the reconstruction REC and its reverse:
 // returns F and adds Fb dF/dw to wpb[0..SW-1], wmb[0..SW-1] (w^- mirrored).
-// e4 as in rec_nd.
+// e4, K and E as in rec_nd.
 template <int REC>
 __device__ __forceinline__ double rec_pair_fwd_adj(const double* wp, const double* wm,
-                                                   const double* e4, double Fb, double* wpb,
+                                                   const double* e4, const double* K,
+                                                   const double* E, double Fb, double* wpb,
                                                    double* wmb) {
   if constexpr (REC == 5) {
-    return weno5_pair_fwd_adj(wp, wm, e4, Fb, wpb, wmb);
+    return weno5_pair_fwd_adj(wp, wm, K, E, Fb, wpb, wmb);
   } else if constexpr (REC == 6) {
     C6 P, M;
     c6_fwd(wp[0], wp[1], wp[2], wp[3], wp[4], wp[5], e4[3], P);
@@ -627,6 +632,11 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
       gUh[m] = g;
     }
     const double e12c[4] = {p.wenoe[0], p.wenoe[1], p.wenoe[2], p.wenoe[3]};
+    // the reconstruction's coefficients as register operands (Params::dev)
+    double K[28];
+#pragma unroll
+    for (int j = 0; j < 28; ++j) K[j] = __ldcg(p.dev->kface + j);
+    const double* Ec = p.dev->wenoe;
     const double chc = c * hic2;
     const double ha_m = 0.5 * am, ha_p = 0.5 * ap, ha0 = 0.5 * a0;
     // the pressure terms p_m (l[m_n]/2 + (u_m/2) l[E]) of the dense rows, as in
@@ -690,7 +700,7 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
       double wpb[SW], wmb[SW];
 #pragma unroll
       for (int m = 0; m < SW; ++m) { wpb[m] = -0.0; wmb[m] = -0.0; }
-      const double F = rec_pair_fwd_adj<REC>(wp, wm, e12c, Fb, wpb, wmb);
+      const double F = rec_pair_fwd_adj<REC>(wp, wm, e12c, K, Ec, Fb, wpb, wmb);
       if (fld == 0) Fm = F; else if (fld == 1) Fp = F; else Fe = F;
       double hab = -0.0;
 #pragma unroll
@@ -770,7 +780,7 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
       double wpb[SW], wmb[SW];
 #pragma unroll
       for (int m = 0; m < SW; ++m) { wpb[m] = -0.0; wmb[m] = -0.0; }
-      const double Fk = rec_pair_fwd_adj<REC>(wp, wm, e12c, Fb, wpb, wmb);
+      const double Fk = rec_pair_fwd_adj<REC>(wp, wm, e12c, K, Ec, Fb, wpb, wmb);
       ubb[a] += Fk * Gc[IE];
 #pragma unroll
       for (int m = 0; m < SW; ++m) {
@@ -796,7 +806,7 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
       double wpb[SW], wmb[SW];
 #pragma unroll
       for (int m = 0; m < SW; ++m) { wpb[m] = -0.0; wmb[m] = -0.0; }
-      const double Fk = rec_pair_fwd_adj<REC>(wp, wm, e12c, Fb, wpb, wmb);
+      const double Fk = rec_pair_fwd_adj<REC>(wp, wm, e12c, K, Ec, Fb, wpb, wmb);
       dphib[s] = -iGam * Fk * Gc[IE];
       iGamb -= dphi[s] * Fk * Gc[IE];
 #pragma unroll

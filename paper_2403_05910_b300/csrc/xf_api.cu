@@ -398,7 +398,7 @@ xf_status fill_params(const xf_grid* g, const xf_thermo* th, const xf_opts* o, x
   }
   for (int k = 0; k < 4; ++k) p->wenoe4[k] = 0.25 * p->wenoe[k];
   p->weno = o->weno;
-  for (int j = 0; j < 24; ++j) p->kface[j] = j < xf::kFaceCoefN ? xf::kFaceCoef[j] : 0.0;
+  for (int j = 0; j < 32; ++j) p->kface[j] = j < xf::kFaceCoefN ? xf::kFaceCoef[j] : 0.0;
   p->kface[14] = o->weno == 7 ? xf::rec_scale<7>() : xf::rec_scale<5>();
   for (int j = 0; j < 8; ++j) p->kexp[j] = xf::kExpCoef[j];
   p->dev = nullptr;  // set by the owner of the struct

@@ -62,7 +62,7 @@ struct Params {
                      // power-of-two factor)
   // the face kernel's fixed coefficients (kFaceCoef with the field pair's
   // division scale rec_scale at 14), read through dev like the run constants
-  double kface[24];
+  double kface[32];
   double kexp[8];    // kExpCoef (primitive recovery's exponentials)
   int viscous, convective, newton_max;
   int weno;          // 5: WENO5-JS, 6: WENO-CU6
@@ -715,14 +715,17 @@ constexpr double kWc2 = 0.03608439182435161;  // 1/(16 sqrt 3)
 // The face kernel's fixed coefficients, in the order Params::kface holds
 // them: the WENO5 indicators' and candidates' (0-10, weno5_nd), the face
 // stencil's 9 and 15 (11, 12, face_one), the Newton-Raphson 1 (13), [14: the
-// division scale], 1/2 (15), and the viscous flux's 1/16, 1/12, 16, 4/3,
-// -2/3 and 1/256 (16-21, face_one).
-constexpr int kFaceCoefN = 22;
+// division scale], 1/2 (15), the viscous flux's 1/16, 1/12, 16, 4/3, -2/3
+// and 1/256 (16-21, face_one), and the WENO5 adjoint's 6, 32 c_1, 32 c_2,
+// 19.5 c_0, 19.5 c_1, 19.5 c_2 (22-27, w5_fwd / w5_rev).
+constexpr int kFaceCoefN = 28;
 constexpr double kFaceCoef[kFaceCoefN] = {-1.375, -0.625, 9.75 * kWc0, 16.0 * kWc1, 9.75 * kWc1,
                                           16.0 * kWc2, 9.75 * kWc2, -2.0, 2.25, 2.0, 4.0,
                                           9.0, 15.0, 1.0, 0.0, 0.5,
                                           1.0 / 16.0, 1.0 / 12.0, 16.0, 4.0 / 3.0, -2.0 / 3.0,
-                                          1.0 / 256.0};
+                                          1.0 / 256.0,
+                                          6.0, 32.0 * kWc1, 32.0 * kWc2, 19.5 * kWc0, 19.5 * kWc1,
+                                          19.5 * kWc2};
 
 // K = kface in registers, E = {12 eps c_k} in device memory (per call)
 __device__ __forceinline__ void weno5_nd(double f0, double f1, double f2, double f3, double f4,
