@@ -380,7 +380,7 @@ xf_status xf_barrier_probe(int64_t timeout_cycles, int extra_arrivals, uint32_t 
  *     `stream` and stores the device status bits (XF_FLAG_*) of this call.
  * Returns XF_ERR_ARG, with the required and available sizes in
  * xf_last_error(), when the grid's scratch exceeds the capacity (about
- * 4e4 cells in 3D with 5 species, 1e5 cells in 2D with 3 species); also
+ * 3.5e4 cells in 3D with 5 species, 8e4 cells in 2D with 3 species); also
  * XF_ERR_ARG, with xf_last_error() naming the cause, for null or non-device
  * U / dUdt / T_guess and for invalid grid, thermo or options.
  * The array is part of the library's device image: it is placed in device

@@ -81,7 +81,7 @@ struct Params {
 // Number of per-cell fields of Lay<dim, ns> (without the D_sm fields), for
 // host code that sizes the field block from runtime (dim, N).
 __host__ __device__ constexpr int lay_nq(int dim, int ns) {
-  return (dim + 1 + ns) + dim + 5 + ns + 5 + 1 + 3 + dim * dim;
+  return (dim + 1 + ns) + dim + 5 + ns + 5 + 1 + 3 + 3 * dim + dim * dim;
 }
 
 // Padded per-cell field layout (SoA, stride pcells).
@@ -101,7 +101,12 @@ struct Lay {
   static constexpr int MU = RM + 1;     // mixture viscosity
   static constexpr int KA = MU + 1;     // mixture conductivity
   static constexpr int DF = KA + 1;     // diffusivity
-  static constexpr int GU = DF + 1;     // nodal d u_a / d x_b at GU + a*DIM + b
+  // per axis a, for the face stencils of direction a: u_a/2, |u_a - c|/2 and
+  // |u_a + c|/2 (each cell sits in six stencils per direction)
+  static constexpr int HU = DF + 1;
+  static constexpr int AM = HU + DIM;
+  static constexpr int AP = AM + DIM;
+  static constexpr int GU = AP + DIM;   // nodal d u_a / d x_b at GU + a*DIM + b
   static constexpr int NQ = GU + DIM * DIM;
   static constexpr int DS = NQ;         // D_sm of species 1..N, present (and
                                         // allocated) only with diffusion = 1
@@ -394,6 +399,16 @@ __device__ __forceinline__ void prim_cell(const Params& p, long long t, const do
 #pragma unroll
     for (int jj = 0; jj < 5; ++jj) q[(L::AC + jj) * PC] = A[jj];
     q[L::RM * PC] = Rm;
+    {
+      const double hc = half * c;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        const double hu = half * vel[a];
+        q[(L::HU + a) * PC] = hu;
+        q[(L::AM + a) * PC] = fabs(hu - hc);
+        q[(L::AP + a) * PC] = fabs(hu + hc);
+      }
+    }
     double mu = 0.0, ka = 0.0, Dd = 0.0;
     if (p.viscous) {
       // Eq. 29 fits; sqrt(mu_s) = exp(ln mu_s / 2) feeds the Wilke ratios (Eq. 22)
@@ -605,7 +620,8 @@ k_prim(const __grid_constant__ Params p, const double* __restrict__ U,
 
 // Ghost cells among the padded cells [t0, t1): a copy of the per-cell fields
 // of the interior cell that the boundary conditions map them to, with the
-// normal velocity and momentum negated across a symmetric boundary -- bitwise
+// normal velocity and momentum negated across a symmetric boundary (and with
+// them the normal u/2, while |u - c|/2 and |u + c|/2 trade places) -- bitwise
 // what prim_cell computes for the ghost itself from the mapped conserved
 // state (its Newton solve starts from the same warm start and the negation
 // commutes with every rounding), at the cost of a copy. The nodal gradients
@@ -630,10 +646,16 @@ k_ghost(const __grid_constant__ Params p, double* __restrict__ Q, long long t0, 
                         (si + p.go[0]);
 #pragma unroll
   for (int v = 0; v < L::GU; ++v) {
-    double x = Q[v * PC + src];
+    int sv = v;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      if (f[a] && v == L::AM + a) sv = L::AP + a;
+      if (f[a] && v == L::AP + a) sv = L::AM + a;
+    }
+    double x = Q[sv * PC + src];
 #pragma unroll
     for (int a = 0; a < DIM; ++a)
-      if (f[a] && (v == L::U + 1 + a || v == L::UN + a)) x = -x;
+      if (f[a] && (v == L::U + 1 + a || v == L::UN + a || v == L::HU + a)) x = -x;
     Q[v * PC + t] = x;
   }
   if (p.diffusion == 1) {
@@ -980,9 +1002,10 @@ __device__ __forceinline__ void conv_flux(const Params& p, const double* __restr
   const double un = ub[D];
   // ---- stencil m = i-SO..i+SO+1 (SW cells: i-2..i+3 for WENO5 and CU6,
   //      i-3..i+4 for WENO7; offsets from the left cell). Per cell:
-  //      rho, p, u_n/2, g.U/(2c^2) and the LLF maxima of |u-c|, |u+c|, |u|.
-  //      The 1/2 of Eq. 14 and the 1/(2c^2) of the acoustic rows are folded
-  //      into per-face coefficients.
+  //      rho, p, u_n/2, g.U/(2c^2) and the LLF maxima of |u-c|/2, |u+c|/2,
+  //      |u|/2 (the halves stored by primitive recovery: exactly half the
+  //      maxima of |u-c|, |u+c|, |u|). The 1/2 of Eq. 14 and the 1/(2c^2)
+  //      of the acoustic rows are folded into per-face coefficients.
   const double phiN = phi[NS - 1];
   const double gE = Gam * hic2;
   double gm[DIM], dphi[NS > 1 ? NS - 1 : 1], gs[NS > 1 ? NS - 1 : 1];
@@ -992,18 +1015,16 @@ __device__ __forceinline__ void conv_flux(const Params& p, const double* __restr
   for (int s = 0; s < NS - 1; ++s) { dphi[s] = phi[s] - phiN; gs[s] = dphi[s] * hic2; }
   const double gr = phiN * hic2;
   double rho_m[SW], p_m[SW], hun[SW], gUh[SW];
-  double am = 0.0, ap = 0.0, a0 = 0.0;
+  double ham = 0.0, hap = 0.0, ha0 = 0.0;
 #pragma unroll
   for (int m = 0; m < SW; ++m) {
     const int o = m - SO;
     rho_m[m] = QF(L::U, o);
-    const double unm = QF(L::UN + D, o);
+    hun[m] = QF(L::HU + D, o);
     p_m[m] = QF(L::P, o);
-    const double cm = QF(L::C, o);
-    am = pmax(am, fabs(unm - cm));
-    ap = pmax(ap, fabs(unm + cm));
-    a0 = pmax(a0, fabs(unm));
-    hun[m] = half * unm;
+    ham = pmax(ham, QF(L::AM + D, o));
+    hap = pmax(hap, QF(L::AP + D, o));
+    ha0 = pmax(ha0, fabs(hun[m]));
     double g = gr * rho_m[m];
 #pragma unroll
     for (int a = 0; a < DIM; ++a) g = fma(gm[a], QF(L::U + 1 + a, o), g);
@@ -1068,7 +1089,7 @@ __device__ __forceinline__ void conv_flux(const Params& p, const double* __restr
     for (int m = 0; m < SW; ++m) pV[m] = p_m[m] * fma(hun[m], lE, hl0);
     // u - c: l.U = (g.U - c (m_n - u_n rho)) / (2c^2)
     {
-      const double ha = half * am;
+      const double ha = ham;
 #pragma unroll
       for (int m = 0; m < SW; ++m) {
         const double LU = fma(-chc, nUv[m], gUh[m]);
@@ -1080,7 +1101,7 @@ __device__ __forceinline__ void conv_flux(const Params& p, const double* __restr
     }
     // u + c
     {
-      const double ha = half * ap;
+      const double ha = hap;
 #pragma unroll
       for (int m = 0; m < SW; ++m) {
         const double LU = fma(chc, nUv[m], gUh[m]);
@@ -1092,7 +1113,6 @@ __device__ __forceinline__ void conv_flux(const Params& p, const double* __restr
     }
     rec_div2<REC>(ndm, ndp, Fk_m, Fk_p, K);
     // (u_m +- |u|max)/2, shared by the entropy row and the passive fields
-    const double ha0 = half * a0;
 #pragma unroll
     for (int m = 0; m < SW; ++m) { hp0[m] = hun[m] + ha0; hm0[m] = hun[m] - ha0; }
     // entropy: l = e_rho - g / c^2, w = (u_m/2 +- a/2)(rho - 2 g.U/(2c^2)) - 2 pV,
