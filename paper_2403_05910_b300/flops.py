@@ -16,12 +16,24 @@ NEWTON_ITER = 35    # one Newton temperature iteration on mixture coefficients
 NEWTON_ITERS = 3    # nominal iterations per cell with the warm start
 
 
+# Eigenvalue work of the LLF maxima that belongs to the cells, not the faces:
+# per stencil cell u_n - c, u_n + c and u_n/2 (6 cells x 3), and the halving
+# of the three maxima (3). Primitive recovery evaluates the per-cell part once
+# per cell and axis (LLF_CELL), so the face count leaves all of it out.
+LLF_FACE_MOVED = 6 * 3 + 3
+
+
 def face_convective(d: int, N: int, weno: int = 5) -> int:
-    """Roe state + PER projection + LLF + 2 reconstructions per field +
+    """Roe state + PER projection + LLF maxima + 2 reconstructions per field +
     back-projection. The projection is counted for the 6-cell stencil (the
     two extra cells of WENO7 are not counted: a lower bound)."""
     nv = d + N + 1
-    return 218 + 71 * d + 103 * N + 2 * RECON[weno] * nv
+    return 218 - LLF_FACE_MOVED + 71 * d + 103 * N + 2 * RECON[weno] * nv
+
+
+def llf_cell(d: int) -> int:
+    """Per cell: c/2, and per axis u/2, |u/2 - c/2|, |u/2 + c/2|."""
+    return 1 + 3 * d
 
 
 def face_positivity(d: int, N: int) -> int:
@@ -46,7 +58,7 @@ def face(d: int, N: int, viscous: bool, weno: int = 5, positivity: bool = False,
 def prim_cell(d: int, N: int, viscous: bool, diffusion: int = 0) -> int:
     """Primitive recovery (Newton, EOS, sound speed) + mixture transport
     (diffusion = 1 adds the binary fits, one exp per pair, and Eq. 26)."""
-    base = 21 + 24 * N + NEWTON_ITERS * NEWTON_ITER + 24
+    base = 21 + 24 * N + NEWTON_ITERS * NEWTON_ITER + 24 + llf_cell(d)
     dsm = (11 * N * (N - 1) // 2 + N * (N + 6)) if (viscous and diffusion) else 0
     return base + ((7 + 31 * N + 13 * N * N) if viscous else 0) + dsm
 
