@@ -593,7 +593,9 @@ def run_ours(args):
                          "frac": achieved / fp64_probe,
                          "peak_note": "the library's FP64 FMA probe (independent DFMA "
                                       "chains on every SM) measured in this run; achieved "
-                                      "counts the plain formulation's flops per face",
+                                      "counts the method's flops per face (flops.py: "
+                                      "per-cell eigenvalues of the LLF maxima count "
+                                      "per cell, not per face)",
                          "peak_nominal": FP64_NOMINAL_TFLOPS,
                          "frac_of_nominal": achieved / FP64_NOMINAL_TFLOPS,
                          "executed": executed,
