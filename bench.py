@@ -294,6 +294,32 @@ def _batched_vs_per_instance(args, dev, stream):
             "cuda_graph": graph, "status_flags": st_b}
 
 
+def _rounds_ms(fns, k, stream, reset=None, rounds=5):
+    """Per-call time (ms) of each function: in each of `rounds` rounds every
+    function in turn runs k times back to back between two CUDA events on the
+    launch stream (after `reset`, untimed, when given), so a clock change moves
+    all of them alike; the median round of each. One untimed call each first."""
+    import torch
+    for fn in fns:
+        if reset:
+            reset()
+        fn()
+    ts = [[] for _ in fns]
+    for _ in range(rounds):
+        for i, fn in enumerate(fns):
+            if reset:
+                reset()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(k):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts[i].append(e0.elapsed_time(e1) / k)
+    return [sorted(t)[len(t) // 2] for t in ts]
+
+
 def _adjoint_vs_forward(args, dev, stream):
     """The differentiated workload (2D shock-bubble, 512x256, 4 species): time
     of one RHS adjoint against one forward RHS, of one RK3-step adjoint
@@ -311,33 +337,20 @@ def _adjoint_vs_forward(args, dev, stream):
     s.compute_dt(dtd)
     dt = 0.9 * float(dtd.item())
     U = torch.empty((c.n_v, c.cells), dtype=torch.float64, device=dev)
-    s.get_state(U)
+    T0 = torch.empty(c.cells, dtype=torch.float64, device=dev)
+    s.get_state(U, T0)
     R = torch.empty_like(U)
     W = torch.randn(U.shape, dtype=torch.float64, generator=torch.Generator().manual_seed(0)).to(dev)
     Ub = torch.zeros_like(U)
 
-    def timed(fn, k):
-        fn()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(k):
-            fn()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / k
-
     k = max(args.steps, 5)
-    f = timed(lambda: s.rhs(U, R), k)
-    a = timed(lambda: s.rhs_adjoint(U, W, Ub), k)
-    fs = timed(lambda: s.step(dt), k)
-    s.set_state(U)
-    ar = timed(lambda: s.step_adjoint(dt, Ub), k)
+    reset = lambda: s.set_state(U, T0)   # the state and its warm start
+    f, a = _rounds_ms([lambda: s.rhs(U, R), lambda: s.rhs_adjoint(U, W, Ub)], k, stream)
     U1, U2 = torch.empty_like(U), torch.empty_like(U)
-    s.set_state(U)
+    reset()
     s.step_tape(dt, U1, U2)
-    s.set_state(U)
-    at = timed(lambda: s.step_adjoint_tape(dt, U1, U2, Ub), k)
+    fs, at, ar = _rounds_ms([lambda: s.step(dt), lambda: s.step_adjoint_tape(dt, U1, U2, Ub),
+                             lambda: s.step_adjoint(dt, Ub)], k, stream, reset)
     st = s.status()
     grad = _gradient_timing(s, c, dt, dev, stream)
     st |= s.status()
@@ -368,32 +381,20 @@ def _adjoint_option(c, kw, dt, W, k, dev, stream):
     s = Solver(case, **kw)
     s.set_primitive(torch.from_numpy(c.prim).to(dev))
     U = torch.empty((c.n_v, c.cells), dtype=torch.float64, device=dev)
-    s.get_state(U)
+    T0 = torch.empty(c.cells, dtype=torch.float64, device=dev)
+    s.get_state(U, T0)
     R, Ub = torch.empty_like(U), torch.zeros_like(U)
 
-    def timed(fn):
-        fn()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(k):
-            fn()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / k
-
-    f = timed(lambda: s.rhs(U, R))
-    a = timed(lambda: s.rhs_adjoint(U, W, Ub))
-    fs = timed(lambda: s.step(dt))
+    f, a = _rounds_ms([lambda: s.rhs(U, R), lambda: s.rhs_adjoint(U, W, Ub)], k, stream)
     U1, U2 = torch.empty_like(U), torch.empty_like(U)
     Fh = (torch.empty(s.tape_flux_len(), dtype=torch.float64, device=dev)
           if kw.get("positivity") else None)
-    s.set_state(U)
+    s.set_state(U, T0)
     s.step_tape(dt, U1, U2, Fhat=Fh)
-    s.set_state(U)
-    at = timed(lambda: s.step_adjoint_tape(dt, U1, U2, Ub, Fhat=Fh))
-    s.set_state(U)
-    ar = timed(lambda: s.step_adjoint(dt, Ub))
+    fs, at, ar = _rounds_ms([lambda: s.step(dt),
+                             lambda: s.step_adjoint_tape(dt, U1, U2, Ub, Fhat=Fh),
+                             lambda: s.step_adjoint(dt, Ub)], k, stream,
+                            lambda: s.set_state(U, T0))
     st = s.status()
     s.close()
     return {"rhs_ms": f, "rhs_adjoint_ms": a, "rhs_ratio": a / f, "step_ms": fs,

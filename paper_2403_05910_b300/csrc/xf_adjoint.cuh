@@ -1176,18 +1176,29 @@ __device__ __forceinline__ void prim_adj_cell(const Params& p, long long t,
     double kabar = fma(Db * p.inv_lewis, irc, kab);
     rhob -= Db * Dd * irho;
     cpmb -= Db * Dd * icpm;
-    // Wilke mixtures, recomputed
+    // Wilke mixtures (Eq. 22), recomputed in k_prim's expanded form: with
+    // r_s = sqrt(mu_s), d_s = S0_s + 2 r_s m1_s + r_s^2 m2_s, where
+    // S0_s = X_s + sum_{t!=s} X_t A_st, m1_s = sum_{t!=s} X_t r_t^-1 A_st B_st
+    // and m2_s = sum_{t!=s} X_t r_t^-2 A_st B_st^2 (Phi_ss = 1); the same with
+    // sqrt(kappa_s) for kappa. The coefficients come from the parameters'
+    // device copy (register operands), the exponentials from exp_k.
+    const Params& pd = *p.dev;
     const double lnT = log(T);
+    double KX[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) KX[j] = rd(pd.kexp[j]);
     double smu[NS], ska[NS], ismu[NS], iska[NS], X[NS], xs = -0.0, dlm[NS], dlk[NS];
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-      const double lm = fma(fma(fma(p.lnmu[s][3], lnT, p.lnmu[s][2]), lnT, p.lnmu[s][1]), lnT, p.lnmu[s][0]);
-      const double lk = fma(fma(fma(p.lnka[s][3], lnT, p.lnka[s][2]), lnT, p.lnka[s][1]), lnT, p.lnka[s][0]);
-      dlm[s] = fma(fma(3.0 * p.lnmu[s][3], lnT, 2.0 * p.lnmu[s][2]), lnT, p.lnmu[s][1]);
-      dlk[s] = fma(fma(3.0 * p.lnka[s][3], lnT, 2.0 * p.lnka[s][2]), lnT, p.lnka[s][1]);
-      smu[s] = exp(0.5 * lm);
-      ska[s] = exp(0.5 * lk);
-      X[s] = Y[s] * p.invW[s];
+      const double* fm = pd.lnmu[s];
+      const double* fk = pd.lnka[s];
+      const double lm = fma(fma(fma(rd(fm[3]), lnT, rd(fm[2])), lnT, rd(fm[1])), lnT, rd(fm[0]));
+      const double lk = fma(fma(fma(rd(fk[3]), lnT, rd(fk[2])), lnT, rd(fk[1])), lnT, rd(fk[0]));
+      dlm[s] = fma(fma(3.0 * rd(fm[3]), lnT, 2.0 * rd(fm[2])), lnT, rd(fm[1]));
+      dlk[s] = fma(fma(3.0 * rd(fk[3]), lnT, 2.0 * rd(fk[2])), lnT, rd(fk[1]));
+      smu[s] = exp_k(0.5 * lm, KX);
+      ska[s] = exp_k(0.5 * lk, KX);
+      X[s] = Y[s] * rd(pd.invW[s]);
       xs += X[s];
     }
     // the 2N reciprocals from one division (running products, as in k_prim)
@@ -1207,46 +1218,72 @@ __device__ __forceinline__ void prim_adj_cell(const Params& p, long long t,
       ismu[0] = inv;
     }
     const double ixs = rcp_nr(xs);
-#pragma unroll
-    for (int s = 0; s < NS; ++s) X[s] *= ixs;
-    const double mtot = mub * p.fmu, ktot = kabar * p.fka;
-    double Xb[NS], smub[NS], skab[NS], ismub[NS], iskab[NS];
-#pragma unroll
-    for (int s = 0; s < NS; ++s) { Xb[s] = -0.0; smub[s] = -0.0; skab[s] = -0.0; ismub[s] = -0.0; iskab[s] = -0.0; }
+    double xm1[NS], xm2[NS], xk1[NS], xk2[NS];
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-      // forward: b_t = 1 + sqrt(a_s / a_t) B_st, d_s = sum_t X_t A_st b_t^2,
-      // term_s = X_s a_s / d_s (a = mu or kappa); the b_t and X_t A_st stay
-      // in registers for the reverse
-      double bm[NS], bk[NS], xa[NS], dm = -0.0, dk = -0.0;
+      X[s] *= ixs;
+      xm1[s] = X[s] * ismu[s];
+      xm2[s] = xm1[s] * ismu[s];
+      xk1[s] = X[s] * iska[s];
+      xk2[s] = xk1[s] * iska[s];
+    }
+    const double mtot = mub * p.fmu, ktot = kabar * p.fka;
+    double Xb[NS], smub[NS], skab[NS], xm1b[NS], xm2b[NS], xk1b[NS], xk2b[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      Xb[s] = -0.0; smub[s] = -0.0; skab[s] = -0.0;
+      xm1b[s] = -0.0; xm2b[s] = -0.0; xk1b[s] = -0.0; xk2b[s] = -0.0;
+    }
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      double s0 = X[s], am1 = -0.0, am2 = -0.0, ak1 = -0.0, ak2 = -0.0;
 #pragma unroll
       for (int tt = 0; tt < NS; ++tt) {
-        bm[tt] = fma(smu[s] * ismu[tt], p.wB[s][tt], 1.0);
-        bk[tt] = fma(ska[s] * iska[tt], p.wB[s][tt], 1.0);
-        xa[tt] = X[tt] * p.wA[s][tt];
-        dm = fma(xa[tt], bm[tt] * bm[tt], dm);
-        dk = fma(xa[tt], bk[tt] * bk[tt], dk);
+        if (tt == s) continue;
+        const double wab = rd(pd.wAB[s][tt]), wabb = rd(pd.wABB[s][tt]);
+        s0 = fma(X[tt], rd(pd.wA[s][tt]), s0);
+        am1 = fma(xm1[tt], wab, am1);
+        am2 = fma(xm2[tt], wabb, am2);
+        ak1 = fma(xk1[tt], wab, ak1);
+        ak2 = fma(xk2[tt], wabb, ak2);
       }
-      const double rd = rcp_nr(dm * dk);
-      const double idm = rd * dk, idk = rd * dm;
-      const double sm2 = smu[s] * smu[s], sk2 = ska[s] * ska[s];
+      const double rs = smu[s], ks = ska[s];
+      const double sm2 = rs * rs, sk2 = ks * ks;
+      const double dm = fma(sm2, am2, fma(rs + rs, am1, s0));
+      const double dk = fma(sk2, ak2, fma(ks + ks, ak1, s0));
+      const double rdd = rcp_nr(dm * dk);
+      const double idm = rdd * dk, idk = rdd * dm;
+      // the mixture terms X_s a_s / d_s: their adjoints through X_s, r_s and d_s
       const double tm = X[s] * sm2 * idm, tk = X[s] * sk2 * idk;
       Xb[s] += fma(mtot * sm2, idm, ktot * sk2 * idk);
-      smub[s] += mtot * 2.0 * X[s] * smu[s] * idm;
-      skab[s] += ktot * 2.0 * X[s] * ska[s] * idk;
       const double dmb = -mtot * tm * idm, dkb = -ktot * tk * idk;
-      const double dmb2 = 2.0 * dmb, dkb2 = 2.0 * dkb;
+      // d term / d r_s = 2 X_s r_s / d_s, d d_s / d r_s = 2 (m1_s + r_s m2_s)
+      smub[s] += 2.0 * fma(mtot * X[s], rs * idm, dmb * fma(rs, am2, am1));
+      skab[s] += 2.0 * fma(ktot * X[s], ks * idk, dkb * fma(ks, ak2, ak1));
+      const double s0b = dmb + dkb;
+      const double m1b = 2.0 * dmb * rs, m2b = dmb * sm2;
+      const double k1b = 2.0 * dkb * ks, k2b = dkb * sk2;
+      Xb[s] += s0b;
 #pragma unroll
       for (int tt = 0; tt < NS; ++tt) {
-        Xb[tt] = fma(p.wA[s][tt], fma(dmb, bm[tt] * bm[tt], dkb * (bk[tt] * bk[tt])), Xb[tt]);
-        // adjoints of b_t, times B_st
-        const double bmw = dmb2 * xa[tt] * bm[tt] * p.wB[s][tt];
-        const double bkw = dkb2 * xa[tt] * bk[tt] * p.wB[s][tt];
-        smub[s] = fma(bmw, ismu[tt], smub[s]);
-        ismub[tt] = fma(bmw, smu[s], ismub[tt]);
-        skab[s] = fma(bkw, iska[tt], skab[s]);
-        iskab[tt] = fma(bkw, ska[s], iskab[tt]);
+        if (tt == s) continue;
+        const double wab = rd(pd.wAB[s][tt]), wabb = rd(pd.wABB[s][tt]);
+        Xb[tt] = fma(s0b, rd(pd.wA[s][tt]), Xb[tt]);
+        xm1b[tt] = fma(m1b, wab, xm1b[tt]);
+        xm2b[tt] = fma(m2b, wabb, xm2b[tt]);
+        xk1b[tt] = fma(k1b, wab, xk1b[tt]);
+        xk2b[tt] = fma(k2b, wabb, xk2b[tt]);
       }
+    }
+    // xm1 = X r^-1, xm2 = xm1 r^-1 (and with sqrt(kappa)): adjoints of X and r^-1
+    double ismub[NS], iskab[NS];
+#pragma unroll
+    for (int t = 0; t < NS; ++t) {
+      const double x1 = fma(xm2b[t], ismu[t], xm1b[t]);
+      const double y1 = fma(xk2b[t], iska[t], xk1b[t]);
+      ismub[t] = fma(xm2b[t], xm1[t], x1 * X[t]);
+      iskab[t] = fma(xk2b[t], xk1[t], y1 * X[t]);
+      Xb[t] = fma(x1, ismu[t], fma(y1, iska[t], Xb[t]));
     }
     double lnTb = -0.0, xdot = -0.0;
     if (p.diffusion == 1) {
@@ -1271,7 +1308,7 @@ __device__ __forceinline__ void prim_adj_cell(const Params& p, long long t,
             const double* bc = p.dbin[s][tt];
             const double l = fma(fma(fma(bc[3], lnT, bc[2]), lnT, bc[1]), lnT, bc[0]);
             dl[k] = fma(fma(3.0 * bc[3], lnT, 2.0 * bc[2]), lnT, bc[1]);
-            e[k] = exp(-l);
+            e[k] = exp_k(-l, KX);
             den[s] = fma(Xt[tt], e[k], den[s]);
             den[tt] = fma(Xt[s], e[k], den[tt]);
           }
