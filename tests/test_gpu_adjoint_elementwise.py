@@ -63,6 +63,11 @@ RHS_CASES = {
     "sbi2d_n4_weno7": (lambda: cases.config(4, n=(24, 14)), {"weno": 7}),
     "sbi2d_n4_dsm": (lambda: cases.with_binary_diffusion(cases.config(4, n=(24, 14)), seed=1),
                      {"diffusion": 1}),
+    # two species: the Wilke and D_sm sums over a single pair
+    "smooth2d_n2_periodic_visc": (lambda: cases.smooth_periodic(2, (14, 12), 2, seed=9, amp=0.3),
+                                  {}),
+    "smooth2d_n2_periodic_dsm": (lambda: cases.with_binary_diffusion(
+        cases.smooth_periodic(2, (14, 12), 2, seed=11, amp=0.3), seed=4), {"diffusion": 1}),
 }
 
 
