@@ -14,11 +14,13 @@
  * diffusion of Eq. 25-26.
  *
  * Parity unpinned vs the paper: the basis of the degenerate u-eigenspace
- * (xfo_eigen) and the multicomponent Roe average of the face state; the
- * paper's choices are in references it only cites. Both are pinned for
- * self-consistency only (L.R = I, A r = lambda r, the exact single-gas Roe
- * property), so results that depend on them match the paper's method up to
- * that choice.
+ * (xfo_eigen), the paper's choice being in references it only cites; it is
+ * pinned for self-consistency (L.R = I, A r = lambda r), so results that
+ * depend on it match the paper's method up to that choice. The
+ * multicomponent Roe average of the face state (also only cited) is pinned
+ * by what the mathematics fixes: it is an exact Roe matrix for mixtures of
+ * calorically perfect species (R diag(lambda) L dU = dF to round-off) and a
+ * consistent second-order linearisation when c_p,s depends on T.
  *
  * Only tests/, the smoke check and the CPU-baseline leg of the benchmark use
  * this library; the product path never links or calls it. It shares no code
