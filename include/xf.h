@@ -194,7 +194,9 @@ xf_status xf_step_rk3(xf_handle *h, double dt, double *dt_dev_out, void *stream)
  * (nullable) as by xf_get_state; results are bitwise those three calls'.
  * U_out may equal U_in. The copies run on a copy stream of the handle,
  * overlapped with the compute in up to 8 slabs of planes of the slowest axis
- * (dim - 1; slabs of >= 16 planes and >= 2^18 cells, else one): stage 1
+ * (dim - 1; slabs of >= 16 planes and >= 2^18 cells, else one; from 4 slabs
+ * on the first and the last are a quarter of the others, since their upload
+ * and read-back are the copies no compute hides): stage 1
  * recovers each slab's primitives as soon as its upload lands, and stage 3
  * sends each slab's U^{n+1} out as soon as its faces and update are done.
  * Pointers: host or device; overlap needs page-locked host memory. The call

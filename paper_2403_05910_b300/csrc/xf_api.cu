@@ -608,7 +608,8 @@ namespace {
 struct Slabs {
   int a = 0, S = 1, G = 0;
   long long n = 1, cs = 1, ps = 1;  // planes, interior / padded cells per plane
-  long long z(int j) const { return n * j / S; }
+  long long zb[9] = {0};            // slab j holds planes [zb[j], zb[j+1])
+  long long z(int j) const { return zb[j]; }
 };
 
 Slabs slabs_of(const xf::Params& p) {
@@ -623,6 +624,15 @@ Slabs slabs_of(const xf::Params& p) {
   long long S = std::min<long long>(8, sl.n / 16);
   S = std::min<long long>(S, p.cells >> 18);
   sl.S = (int)std::max<long long>(1, S);
+  // from 4 slabs on, the first and the last are a quarter of the others: the
+  // first slab's upload and the last one's read-back are the copies that no
+  // compute hides (each still >= 3 planes: n >= 16 S)
+  const long long m = sl.S - 2, units = 4 * m + 2;
+  for (int j = 0; j <= sl.S; ++j) {
+    long long u = j;
+    if (sl.S >= 4) u = j == 0 ? 0 : (j == sl.S ? units : 1 + 4 * (long long)(j - 1));
+    sl.zb[j] = sl.S >= 4 ? sl.n * u / units : sl.n * j / sl.S;
+  }
   return sl;
 }
 
