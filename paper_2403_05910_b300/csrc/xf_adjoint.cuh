@@ -978,14 +978,21 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
       if (a == D) tau[a] = fma(-2.0 / 3.0 * mu, div, tau[a]);
     }
     // species diffusivities at the face: the common D, or each species' D_sm
-    // (mixture-averaged model)
+    // (mixture-averaged model). With the common D the mixture correction
+    // D Y_s sum_t dY_t vanishes identically (sum_t Y_t = 1), as in the
+    // forward face, and is neither formed nor reversed.
+    const bool dsm = p.diffusion == 1;
     double dY[NS], Yf[NS], Dsf[NS], corr = -0.0;
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
       dY[s] = FD(L::Y + s);
-      Yf[s] = FI(L::Y + s);
-      Dsf[s] = p.diffusion == 1 ? FI(L::DS + s) : Df;
-      corr = fma(Dsf[s], dY[s], corr);
+      Dsf[s] = dsm ? FI(L::DS + s) : Df;
+      if (dsm) {
+        Yf[s] = FI(L::Y + s);
+        corr = fma(Dsf[s], dY[s], corr);
+      } else {
+        Yf[s] = -0.0;
+      }
     }
     const TauPt tp = tau_of(p, Tf);
     const double dT = FD(L::T);
@@ -995,22 +1002,28 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
     double dYb[NS], Yfb[NS], Dsfb[NS];
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-      const double J = -rf * fma(Dsf[s], dY[s], -Yf[s] * corr);
+      const double J = dsm ? -rf * fma(Dsf[s], dY[s], -Yf[s] * corr) : -rf * (Df * dY[s]);
       const double cps = cp_s(p, s, tp.tc);
       const double hs = h_s(p, s, tp, cps);
       double Jb = qdb * hs + (s < NS - 1 ? Gb[IE + 1 + s] : 0.0);
       Tfb += qdb * J * cps;
-      rfb -= Jb * (Dsf[s] * dY[s] - Yf[s] * corr);
+      rfb -= Jb * (dsm ? Dsf[s] * dY[s] - Yf[s] * corr : Df * dY[s]);
       Dsfb[s] = -Jb * rf * dY[s];
       dYb[s] = -Jb * rf * Dsf[s];
-      Yfb[s] = Jb * rf * corr;
-      corrb += Jb * rf * Yf[s];
+      if (dsm) {
+        Yfb[s] = Jb * rf * corr;
+        corrb += Jb * rf * Yf[s];
+      } else {
+        Yfb[s] = -0.0;
+      }
     }
-    // corr = sum_s D_s dY_s
+    // corr = sum_s D_s dY_s (mixture-averaged model only)
+    if (dsm) {
 #pragma unroll
-    for (int s = 0; s < NS; ++s) {
-      Dsfb[s] = fma(corrb, dY[s], Dsfb[s]);
-      dYb[s] = fma(corrb, Dsf[s], dYb[s]);
+      for (int s = 0; s < NS; ++s) {
+        Dsfb[s] = fma(corrb, dY[s], Dsfb[s]);
+        dYb[s] = fma(corrb, Dsf[s], dYb[s]);
+      }
     }
     double Dfb = -0.0;
     if (p.diffusion != 1) {
@@ -1060,7 +1073,7 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
       BD(L::Y + s, dYb[s]);
-      BI(L::Y + s, Yfb[s]);
+      if (dsm) BI(L::Y + s, Yfb[s]);
     }
 #undef FI
 #undef FD

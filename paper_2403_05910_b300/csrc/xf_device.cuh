@@ -1305,8 +1305,10 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
     // With dY0 = 12 dx dY/dn, Yf0 = 16 Y_f, Ds0 = 16 D_s and
     // nrf = -rho_f wi wd: D_s = the face values of the cells' D_sm
     // (diffusion = 1): Jn_s = Ds0 dY0_s - Yf0_s wi sum_t Ds0_t dY0_t,
-    // nJ = nrf; one D for every species (diffusion = 0):
-    // Jn_s = dY0_s - Yf0_s wi sum_t dY0_t, nJ = nrf Ds0
+    // nJ = nrf; one D for every species (diffusion = 0): the correction is
+    // D Y_s sum_t dY_t/dn = D Y_s d(sum_t Y_t)/dn, identically zero (Y_N is
+    // 1 - sum of the others, and the stencil is linear), so Jn_s = dY0_s,
+    // nJ = nrf Ds0
     const double nrf = FI0(L::U) * (-wi * wid);
     double Jn[NS], nJ;
     if (p.diffusion == 1) {
@@ -1322,15 +1324,8 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
       for (int s = 0; s < NS; ++s) Jn[s] = fma(Ds0[s], dY0[s], -Yf0[s] * corr0);
       nJ = nrf;
     } else {
-      double dY0[NS], Yf0[NS];
 #pragma unroll
-      for (int s = 0; s < NS; ++s) { dY0[s] = FD0(L::Y + s); Yf0[s] = FI0(L::Y + s); }
-      double sdY = dY0[0];
-#pragma unroll
-      for (int s = 1; s < NS; ++s) sdY += dY0[s];
-      const double corr = wi * sdY;
-#pragma unroll
-      for (int s = 0; s < NS; ++s) Jn[s] = fma(-corr, Yf0[s], dY0[s]);
+      for (int s = 0; s < NS; ++s) Jn[s] = FD0(L::Y + s);
       nJ = nrf * FI0(L::DF);
     }
     // h_s at the face temperature T_f = wi FI0(T); qd = sum_s h_s J_s / nJ
