@@ -985,7 +985,10 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
     double dY[NS], Yf[NS], Dsf[NS], corr = -0.0;
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-      dY[s] = FD(L::Y + s);
+      // the last species' flux enters neither a species row nor, in the
+      // difference form below, the heat flux: its gradient is needed only
+      // for the mixture correction
+      dY[s] = (dsm || s < NS - 1) ? FD(L::Y + s) : -0.0;
       Dsf[s] = dsm ? FI(L::DS + s) : Df;
       if (dsm) {
         Yf[s] = FI(L::Y + s);
@@ -996,17 +999,20 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
     }
     const TauPt tp = tau_of(p, Tf);
     const double dT = FD(L::T);
-    // reverse: Gout[IE] -= ka dT + work - qd; Gout[1+a] -= tau_a; Gout[IE+1+s] += J_s
+    // reverse: Gout[IE] -= ka dT + work - qd; Gout[1+a] -= tau_a; Gout[IE+1+s] += J_s.
+    // As in the forward face, qd = sum_{s<N} (h_s - h_N) J_s (sum_s J_s = 0),
+    // so the last species' J has no adjoint.
     const double workb = -Gb[IE], kab = -Gb[IE] * dT, dTb = -Gb[IE] * ka, qdb = Gb[IE];
     double Tfb = -0.0, rfb = -0.0, corrb = -0.0, mub = -0.0, divb = -0.0;
     double dYb[NS], Yfb[NS], Dsfb[NS];
+    Dsfb[NS - 1] = -0.0; dYb[NS - 1] = -0.0; Yfb[NS - 1] = -0.0;
 #pragma unroll
-    for (int s = 0; s < NS; ++s) {
+    for (int s = 0; s < NS - 1; ++s) {
       const double J = dsm ? -rf * fma(Dsf[s], dY[s], -Yf[s] * corr) : -rf * (Df * dY[s]);
-      const double cps = cp_s(p, s, tp.tc);
-      const double hs = h_s(p, s, tp, cps);
-      double Jb = qdb * hs + (s < NS - 1 ? Gb[IE + 1 + s] : 0.0);
-      Tfb += qdb * J * cps;
+      const double cpd = cpd_s_dev(p, s, tp.tc);
+      const double hd = hd_s_dev(p, s, tp);
+      double Jb = fma(qdb, hd, Gb[IE + 1 + s]);
+      Tfb += qdb * J * cpd;
       rfb -= Jb * (dsm ? Dsf[s] * dY[s] - Yf[s] * corr : Df * dY[s]);
       Dsfb[s] = -Jb * rf * dY[s];
       dYb[s] = -Jb * rf * Dsf[s];
@@ -1072,7 +1078,7 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
     }
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-      BD(L::Y + s, dYb[s]);
+      if (dsm || s < NS - 1) BD(L::Y + s, dYb[s]);
       if (dsm) BI(L::Y + s, Yfb[s]);
     }
 #undef FI

@@ -381,6 +381,16 @@ xf_status fill_params(const xf_grid* g, const xf_thermo* th, const xf_opts* o, x
       p->wAB[s][t] = p->wA[s][t] * p->wB[s][t];
       p->wABB[s][t] = p->wA[s][t] * p->wB[s][t] * p->wB[s][t];
     }
+  // coefficients of h_s - h_N and c_p,s - c_p,N (the face's heat flux by
+  // diffusion); zero beyond s = N - 2
+  for (int s = 0; s < xf::MAXN; ++s) {
+    const bool in = s < N - 1;
+    for (int j = 0; j < 5; ++j) {
+      p->rcpd[s][j] = in ? p->rcp[s][j] - p->rcp[N - 1][j] : 0.0;
+      p->rhd[s][j] = in ? p->rh[s][j] - p->rh[N - 1][j] : 0.0;
+    }
+    p->rhoffd[s] = in ? p->rhoff[s] - p->rhoff[N - 1] : 0.0;
+  }
   const double a_ref = std::sqrt(th->a_ref2);
   p->fmu = 1.0 / (th->rho_ref * a_ref * th->L_ref);
   p->fka = 1.0 / (th->rho_ref * a_ref * th->a_ref2 * th->L_ref);

@@ -43,6 +43,8 @@ struct Params {
   double rcp[MAXN][5];    // r_s cp_j: c_p,s = sum_j rcp[s][j] tau^j
   double rh[MAXN][5];     // r_s span cp_j/(j+1): h_s = rhoff_s + sum_j rh[s][j] tau^(j+1)
   double rhoff[MAXN];     // r_s h_off_s
+  // the same for h_s - h_N (s < N - 1): the face's heat flux by diffusion
+  double rcpd[MAXN][5], rhd[MAXN][5], rhoffd[MAXN];
   // transport
   double lnmu[MAXN][4], lnka[MAXN][4];
   double wA[MAXN][MAXN], wB[MAXN][MAXN];  // Wilke: A = (1+W_s/W_t)^-1/2 / sqrt 8, B = (W_t/W_s)^1/4
@@ -283,6 +285,28 @@ __device__ __forceinline__ double h_s_dev(const Params& p, int s, const TauPt& t
                           t.tc, __ldcg(a + 0));
   const double h = fma(poly, t.tc, __ldcg(p.dev->rhoff + s));
   return t.in ? h : fma(cp_s(p, s, t.tc), t.ext, h);
+}
+
+// c_p,s - c_p,N at the clamped tau, from the parameters' device copy
+__device__ __forceinline__ double cpd_s_dev(const Params& p, int s, double tc) {
+  const double* c = p.dev->rcpd[s];
+  return fma(fma(fma(fma(__ldcg(c + 4), tc, __ldcg(c + 3)), tc, __ldcg(c + 2)), tc,
+                 __ldcg(c + 1)),
+             tc, __ldcg(c + 0));
+}
+
+// h_s - h_N with the coefficients' differences from the parameters' device
+// copy (register operands; the linear continuation as in h_s_in)
+__device__ __forceinline__ double hd_s_dev(const Params& p, int s, const TauPt& t) {
+  const double* a = p.dev->rhd[s];
+  const double poly = fma(fma(fma(fma(__ldcg(a + 4), t.tc, __ldcg(a + 3)), t.tc, __ldcg(a + 2)),
+                              t.tc, __ldcg(a + 1)),
+                          t.tc, __ldcg(a + 0));
+  const double h = fma(poly, t.tc, __ldcg(p.dev->rhoffd + s));
+  if (t.in) return h;
+  const double* c = p.rcpd[s];
+  const double cpd = fma(fma(fma(fma(c[4], t.tc, c[3]), t.tc, c[2]), t.tc, c[1]), t.tc, c[0]);
+  return fma(cpd, t.ext, h);
 }
 
 // ------------------------------------------------------------ status ------
@@ -1328,11 +1352,13 @@ __device__ __forceinline__ void face_one(const Params& p, int fi, int fj, int fk
       for (int s = 0; s < NS; ++s) Jn[s] = FD0(L::Y + s);
       nJ = nrf * FI0(L::DF);
     }
-    // h_s at the face temperature T_f = wi FI0(T); qd = sum_s h_s J_s / nJ
+    // h_s at the face temperature T_f = wi FI0(T); qd = sum_s h_s J_s / nJ.
+    // Either model conserves mass, sum_s J_s = 0 (sum_s Y_s = 1 and the
+    // stencils are linear), so qd = sum_{s<N} (h_s - h_N) J_s / nJ
     const TauPt tp = tau_pt(p, fma(FI0(L::T), wi * rd(p.dev->inv_span), rd(p.dev->tau0)));
     double qd = 0.0;
 #pragma unroll
-    for (int s = 0; s < NS; ++s) qd = fma(h_s_dev(p, s, tp), Jn[s], qd);
+    for (int s = 0; s < NS - 1; ++s) qd = fma(hd_s_dev(p, s, tp), Jn[s], qd);
     Gout[IE] -= fma(FI0(L::KA) * wid, FD0(L::T), fma(mu16 * wi, W, -nJ * qd));
 #pragma unroll
     for (int s = 0; s < NS - 1; ++s) Gout[IE + 1 + s] = fma(nJ, Jn[s], Gout[IE + 1 + s]);
