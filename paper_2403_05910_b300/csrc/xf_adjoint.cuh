@@ -608,8 +608,11 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
 #pragma unroll
     for (int s = 0; s < NS - 1; ++s) { dphi[s] = phi[s] - phiN; gs[s] = dphi[s] * hic2; }
     const double gr = phiN * hic2, gE = Gam * hic2;
+    // the LLF maxima from the halves |u - c|/2, |u + c|/2, u/2 that primitive
+    // recovery stores (exact halves: the same arg-max cells and, halved, the
+    // same maxima as from |u - c|, |u + c|, |u|)
     double rho_m[SW], p_m[SW], hun[SW], gUh[SW], unm[SW], cmv[SW];
-    double am = 0.0, ap = 0.0, a0 = 0.0;
+    double ha_m = 0.0, ha_p = 0.0, ha0 = 0.0;
     int im = 0, ipp = 0, i0 = 0;
 #pragma unroll
     for (int m = 0; m < SW; ++m) {
@@ -618,11 +621,11 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
       unm[m] = QF(L::UN + D, o);
       p_m[m] = QF(L::P, o);
       cmv[m] = QF(L::C, o);
-      const double xm = fabs(unm[m] - cmv[m]), xp = fabs(unm[m] + cmv[m]), x0 = fabs(unm[m]);
-      if (m == 0 || gt_nn(xm, am)) { am = xm; im = m; }
-      if (m == 0 || gt_nn(xp, ap)) { ap = xp; ipp = m; }
-      if (m == 0 || gt_nn(x0, a0)) { a0 = x0; i0 = m; }
-      hun[m] = 0.5 * unm[m];
+      hun[m] = QF(L::HU + D, o);
+      const double xm = QF(L::AM + D, o), xp = QF(L::AP + D, o), x0 = fabs(hun[m]);
+      if (m == 0 || gt_nn(xm, ha_m)) { ha_m = xm; im = m; }
+      if (m == 0 || gt_nn(xp, ha_p)) { ha_p = xp; ipp = m; }
+      if (m == 0 || gt_nn(x0, ha0)) { ha0 = x0; i0 = m; }
       double g = gr * rho_m[m];
 #pragma unroll
       for (int a = 0; a < DIM; ++a) g = fma(gm[a], QF(L::U + 1 + a, o), g);
@@ -638,7 +641,6 @@ __device__ __forceinline__ void face_adj(const Params& p, int fi, int fj, int fk
     for (int j = 0; j < 28; ++j) K[j] = __ldcg(p.dev->kface + j);
     const double* Ec = p.dev->wenoe;
     const double chc = c * hic2;
-    const double ha_m = 0.5 * am, ha_p = 0.5 * ap, ha0 = 0.5 * a0;
     // the pressure terms p_m (l[m_n]/2 + (u_m/2) l[E]) of the dense rows, as in
     // conv_flux: one product pV per cell, -+ dl p_m for u -+ c, -2 pV for the
     // entropy row; nUv (the normal momentum relative to the face velocity) is
