@@ -390,6 +390,7 @@ xf_status fill_params(const xf_grid* g, const xf_thermo* th, const xf_opts* o, x
       p->rhd[s][j] = in ? p->rh[s][j] - p->rh[N - 1][j] : 0.0;
     }
     p->rhoffd[s] = in ? p->rhoff[s] - p->rhoff[N - 1] : 0.0;
+    p->rdN[s] = in ? p->r[s] - p->r[N - 1] : 0.0;
   }
   const double a_ref = std::sqrt(th->a_ref2);
   p->fmu = 1.0 / (th->rho_ref * a_ref * th->L_ref);

@@ -45,6 +45,7 @@ struct Params {
   double rhoff[MAXN];     // r_s h_off_s
   // the same for h_s - h_N (s < N - 1): the face's heat flux by diffusion
   double rcpd[MAXN][5], rhd[MAXN][5], rhoffd[MAXN];
+  double rdN[MAXN];        // r_s - r_N (s < N - 1): the face's phi_s - phi_N
   // transport
   double lnmu[MAXN][4], lnka[MAXN][4];
   double wA[MAXN][MAXN], wB[MAXN][MAXN];  // Wilke: A = (1+W_s/W_t)^-1/2 / sqrt 8, B = (W_t/W_s)^1/4
@@ -988,9 +989,11 @@ __device__ __forceinline__ void conv_flux(const Params& p, const double* __restr
 #pragma unroll
   for (int s = 0; s < NS; ++s) Yb[s] = fma(tL, QF(L::Y + s, 0), tR * QF(L::Y + s, 1));
   const TauPt tp = tau_pt(p, fma(Tb, rd(p.dev->inv_span), rd(p.dev->tau0)));
-  double hs[NS];
+  // h_N and h_s - h_N (s < N): the species' eigenvectors need phi_s - phi_N only
+  const double hN = h_s_dev(p, NS - 1, tp);
+  double hd[NS > 1 ? NS - 1 : 1];
 #pragma unroll
-  for (int s = 0; s < NS; ++s) hs[s] = h_s_dev(p, s, tp);
+  for (int s = 0; s < NS - 1; ++s) hd[s] = hd_s_dev(p, s, tp);
   // R(Y) and c_p(Y, T) are linear in Y: their face values come from the two
   // cells' mixture gas constants and c_p coefficients with the same weights
   const double Rb = fma(tL, QF(L::RM, 0), tR * QF(L::RM, 1));
@@ -1004,13 +1007,16 @@ __device__ __forceinline__ void conv_flux(const Params& p, const double* __restr
   const double Gam = Rb * Rb * rRc;
   const double hq2 = half * q2;
   // phi_s = R_s T - Gamma (e_s - |u|^2/2) with e_s = h_s - R_s T:
-  // R_s (1 + Gamma) T - Gamma h_s + Gamma |u|^2/2
+  // R_s (1 + Gamma) T - Gamma h_s + Gamma |u|^2/2; formed as phi_N and
+  // phi_s - phi_N = (R_s - R_N)(1 + Gamma) T - Gamma (h_s - h_N), and with
+  // sum_s Y_s = 1, sum_s Y_s phi_s = phi_N + sum_{s<N} Y_s (phi_s - phi_N)
   const double T1G = fma(Gam, Tb, Tb), Gq2 = Gam * hq2;
-  double phi[NS], c2 = 0.0;
+  const double phiN = fma(__ldcg(p.dev->r + NS - 1), T1G, fma(-Gam, hN, Gq2));
+  double dphi[NS > 1 ? NS - 1 : 1], c2 = phiN;
 #pragma unroll
-  for (int s = 0; s < NS; ++s) {
-    phi[s] = fma(__ldcg(p.dev->r + s), T1G, fma(-Gam, hs[s], Gq2));
-    c2 = fma(Yb[s], phi[s], c2);
+  for (int s = 0; s < NS - 1; ++s) {
+    dphi[s] = fma(__ldcg(p.dev->rdN + s), T1G, -Gam * hd[s]);
+    c2 = fma(Yb[s], dphi[s], c2);
   }
   c2 = fma(Gam, Hb - q2, c2);
   if (!(c2 > 0.0)) {
@@ -1030,13 +1036,12 @@ __device__ __forceinline__ void conv_flux(const Params& p, const double* __restr
   //      |u|/2 (the halves stored by primitive recovery: exactly half the
   //      maxima of |u-c|, |u+c|, |u|). The 1/2 of Eq. 14 and the 1/(2c^2)
   //      of the acoustic rows are folded into per-face coefficients.
-  const double phiN = phi[NS - 1];
   const double gE = Gam * hic2;
-  double gm[DIM], dphi[NS > 1 ? NS - 1 : 1], gs[NS > 1 ? NS - 1 : 1];
+  double gm[DIM], gs[NS > 1 ? NS - 1 : 1];
 #pragma unroll
   for (int a = 0; a < DIM; ++a) gm[a] = -ub[a] * gE;
 #pragma unroll
-  for (int s = 0; s < NS - 1; ++s) { dphi[s] = phi[s] - phiN; gs[s] = dphi[s] * hic2; }
+  for (int s = 0; s < NS - 1; ++s) gs[s] = dphi[s] * hic2;
   const double gr = phiN * hic2;
   double rho_m[SW], p_m[SW], hun[SW], gUh[SW];
   double ham = 0.0, hap = 0.0, ha0 = 0.0;
