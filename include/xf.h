@@ -313,6 +313,12 @@ xf_status xf_probe_rcp(const double *x, double *y, double *ref, int64_t n, void 
  * of n doubles. Enqueued on `stream`. XF_ERR_ARG for null or non-device
  * arrays or n < 0. */
 xf_status xf_probe_exp(const double *x, double *y, double *ref, int64_t n, void *stream);
+/* The logarithm the primitive recovery uses for the transport fits' ln T
+ * (Tang's table-driven method; tooling, no counterpart in the paper):
+ * y[i] = that log of x[i] and ref[i] = CUDA's log(x[i]), for device arrays
+ * of n doubles. Enqueued on `stream`. XF_ERR_ARG for null or non-device
+ * arrays or n < 0. */
+xf_status xf_probe_log(const double *x, double *y, double *ref, int64_t n, void *stream);
 
 /* ---- Batched form: many independent 2D instances (uneven grids, N = 2..5)
  * advanced together. Each RK stage is ONE persistent cooperative kernel that

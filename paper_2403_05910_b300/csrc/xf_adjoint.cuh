@@ -1204,7 +1204,10 @@ __device__ __forceinline__ void prim_adj_cell(const Params& p, long long t,
     // sqrt(kappa_s) for kappa. The coefficients come from the parameters'
     // device copy (register operands), the exponentials from exp_k.
     const Params& pd = *p.dev;
-    const double lnT = log(T);
+    double KL[9];
+#pragma unroll
+    for (int j = 0; j < 9; ++j) KL[j] = rd(pd.klog[j]);
+    const double lnT = log_k(T, KL);
     double KX[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) KX[j] = rd(pd.kexp[j]);

@@ -412,6 +412,7 @@ xf_status fill_params(const xf_grid* g, const xf_thermo* th, const xf_opts* o, x
   for (int j = 0; j < 32; ++j) p->kface[j] = j < xf::kFaceCoefN ? xf::kFaceCoef[j] : 0.0;
   p->kface[14] = o->weno == 7 ? xf::rec_scale<7>() : xf::rec_scale<5>();
   for (int j = 0; j < 8; ++j) p->kexp[j] = xf::kExpCoef[j];
+  for (int j = 0; j < 9; ++j) p->klog[j] = xf::kLogCoef[j];
   p->dev = nullptr;  // set by the owner of the struct
   p->newton_rtol = o->newton_rtol;
   p->newton_max = o->newton_max;
@@ -590,6 +591,15 @@ __global__ void k_probe_exp(const double* __restrict__ x, double* __restrict__ y
   if (i >= n) return;
   y[i] = xf::exp_t(x[i]);
   ref[i] = exp(x[i]);
+}
+
+// log_t beside CUDA's log, element by element
+__global__ void k_probe_log(const double* __restrict__ x, double* __restrict__ y,
+                            double* __restrict__ ref, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  y[i] = xf::log_t(x[i]);
+  ref[i] = log(x[i]);
 }
 
 __global__ void k_probe_fp64(double* out, long long iters, double a) {
@@ -1258,6 +1268,15 @@ xf_status xf_probe_exp(const double* x, double* y, double* ref, int64_t n, void*
   if (n == 0) return XF_OK;
   if (!is_device_ptr(x) || !is_device_ptr(y) || !is_device_ptr(ref)) return XF_ERR_ARG;
   k_probe_exp<<<blocks(n, 256), 256, 0, (cudaStream_t)stream>>>(x, y, ref, n);
+  XF_CUDA(cudaGetLastError());
+  return XF_OK;
+}
+
+xf_status xf_probe_log(const double* x, double* y, double* ref, int64_t n, void* stream) {
+  if (!x || !y || !ref || n < 0) return XF_ERR_ARG;
+  if (n == 0) return XF_OK;
+  if (!is_device_ptr(x) || !is_device_ptr(y) || !is_device_ptr(ref)) return XF_ERR_ARG;
+  k_probe_log<<<blocks(n, 256), 256, 0, (cudaStream_t)stream>>>(x, y, ref, n);
   XF_CUDA(cudaGetLastError());
   return XF_OK;
 }

@@ -48,7 +48,7 @@ EXPORTS = ["xf_create", "xf_destroy", "xf_nv", "xf_cells", "xf_set_state", "xf_s
            "xf_step_rk3_host",
            "xf_get_status",
            "xf_clear_status", "xf_status_str", "xf_last_error", "xf_profile_enable",
-           "xf_profile_read", "xf_probe_fp64", "xf_probe_rcp", "xf_probe_exp", "xf_rhs_static", "xf_rhs_static_capacity_bytes",
+           "xf_profile_read", "xf_probe_fp64", "xf_probe_rcp", "xf_probe_exp", "xf_probe_log", "xf_rhs_static", "xf_rhs_static_capacity_bytes",
            "xf_batch_create", "xf_batch_destroy", "xf_batch_size", "xf_batch_set_primitive",
            "xf_batch_set_state", "xf_batch_get_state", "xf_batch_step_rk3", "xf_batch_autotune",
            "xf_batch_config", "xf_batch_get_status", "xf_barrier_probe", "xf_batch_uses_graph",
@@ -90,6 +90,7 @@ def _load():
     L.xf_probe_fp64.argtypes = [C.c_int64, C.c_int, C.POINTER(C.c_double)]
     L.xf_probe_rcp.argtypes = [vp, vp, vp, C.c_int64, vp]
     L.xf_probe_exp.argtypes = [vp, vp, vp, C.c_int64, vp]
+    L.xf_probe_log.argtypes = [vp, vp, vp, C.c_int64, vp]
     L.xf_rhs_static.argtypes = [C.POINTER(Grid), C.POINTER(Thermo), C.POINTER(Opts), vp, vp, vp,
                                 C.POINTER(C.c_uint32), vp]
     L.xf_rhs_static_capacity_bytes.restype = C.c_int64
@@ -340,6 +341,12 @@ def probe_exp(x, y, ref, stream=None):
     """y = the kernels' exponential of x, ref = CUDA's exp(x) (device float64 tensors)."""
     check(lib.xf_probe_exp(ptr(x), ptr(y), ptr(ref), int(x.numel()), stream_ptr(stream)),
           "xf_probe_exp")
+
+
+def probe_log(x, y, ref, stream=None):
+    """y = the kernels' logarithm of x, ref = CUDA's log(x) (device float64 tensors)."""
+    check(lib.xf_probe_log(ptr(x), ptr(y), ptr(ref), int(x.numel()), stream_ptr(stream)),
+          "xf_probe_log")
 
 
 def rhs_static(case, U, dUdt, T=None, flags=True, stream=None, **kw):

@@ -90,6 +90,8 @@ def test_argument_errors_need_no_device():
     assert xf.lib.xf_probe_rcp(None, None, None, -1, None) == xf.XF_ERR_ARG
     assert xf.lib.xf_probe_exp(None, None, None, 16, None) == xf.XF_ERR_ARG
     assert xf.lib.xf_probe_exp(None, None, None, -1, None) == xf.XF_ERR_ARG
+    assert xf.lib.xf_probe_log(None, None, None, 16, None) == xf.XF_ERR_ARG
+    assert xf.lib.xf_probe_log(None, None, None, -1, None) == xf.XF_ERR_ARG
     assert xf.lib.xf_step_rk3_adjoint_tape(None, 1e-3, None, None, None, None) == xf.XF_ERR_ARG
     assert xf.lib.xf_tape_flux_len(None) == -1
     assert xf.lib.xf_step_rk3_tape_flux(None, 1e-3, None, None, None, None) == xf.XF_ERR_ARG
